@@ -1,0 +1,262 @@
+"""Plain FP64 CPU oracle of the SCF gravity step (test infrastructure).
+
+Only the test suite, ``__graft_entry__.smoke()`` and the CPU-baseline leg of
+``bench.py`` may import this package.  It is the slow, obviously-correct
+definition of what the CUDA path computes, written from the paper:
+
+* Eq. 1-3 (basis expansion, coefficients as a mass-weighted particle sum),
+* Eq. 4 with alpha = 1 (Hernquist-Ostriker Gegenbauer radial basis),
+* Sec. 2.1 (accelerating, non-rotating cluster frame; COM test particle),
+* App. A (Hernquist, NFW, Miyamoto-Nagai host components).
+
+The arithmetic lives in ``scf_oracle.c`` (plain C, double precision, long
+double for the host tidal difference).  This module compiles it with gcc on
+first use and wraps it with ctypes; numpy arrays in, numpy arrays out.
+
+Array conventions (shared with the CUDA path by specification, not by code):
+positions ``(N, 4)`` = (x, y, z, m); velocities ``(N, 4)`` = (vx, vy, vz, 0);
+accelerations ``(N, 4)`` = (ax, ay, az, potential); coefficients ``A`` =
+``[S | T]`` with ``(nmax+1) * (lmax+1)(lmax+2)/2`` entries each, index
+``n * N_lm + l(l+1)/2 + m``.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "scf_oracle.c")
+_LIB = os.path.join(_HERE, "liboracle.so")
+_lock = threading.Lock()
+_lib = None
+
+HOST_HERNQUIST = 1
+HOST_NFW = 2
+HOST_MN = 3
+
+
+class _HostComp(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int), ("M", ctypes.c_double), ("a", ctypes.c_double), ("b", ctypes.c_double)]
+
+
+class _Host(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int), ("G", ctypes.c_double), ("c", _HostComp * 8)]
+
+
+def build(force: bool = False) -> str:
+    """Compile ``scf_oracle.c`` into ``liboracle.so`` (gcc, -O2, no fast-math)."""
+    with _lock:
+        stale = (not os.path.exists(_LIB)) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC)
+        if force or stale:
+            tmp = _LIB + f".{os.getpid()}.tmp"
+            cmd = ["gcc", "-O2", "-fPIC", "-shared", "-fopenmp", "-std=c11", "-o", tmp, _SRC, "-lm"]
+            subprocess.run(cmd, check=True)
+            os.replace(tmp, _LIB)
+    return _LIB
+
+
+def _load():
+    global _lib
+    if _lib is not None:
+        return _lib
+    build()
+    lib = ctypes.CDLL(_LIB)
+    d, i, i64, p = ctypes.c_double, ctypes.c_int, ctypes.c_int64, ctypes.c_void_p
+    sig = {
+        "or_gegenbauer": (d, [i, d, d]),
+        "or_plm": (d, [i, i, d]),
+        "or_dplm_dtheta": (d, [i, i, d]),
+        "or_mplm_over_sin": (d, [i, i, d]),
+        "or_nlm2": (d, [i, i]),
+        "or_knl": (d, [i, i]),
+        "or_inl": (d, [i, i, d]),
+        "or_phi_nl": (d, [i, i, d, d]),
+        "or_phi_nl_over_r": (d, [i, i, d, d]),
+        "or_dphi_nl_dr": (d, [i, i, d, d]),
+        "or_rho_nl": (d, [i, i, d, d]),
+        "or_coeffs": (None, [i64, p, p, i, i, d, p]),
+        "or_field": (None, [i64, p, p, i, i, d, d, p]),
+        "or_host_accel": (None, [p, p, p, p]),
+        "or_tidal": (None, [p, p, p, p]),
+        "or_forces": (None, [i64, p, p, p, p, i, i, d, d, p]),
+        "or_step": (None, [i64, p, p, p, p, p, i, i, d, d, d, i, p, p]),
+        "or_direct": (None, [i64, p, i64, p, d, p]),
+        "or_power_l": (None, [p, i, i, d, p]),
+        "or_num_threads": (i, []),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(lib, name)
+        f.restype = res
+        f.argtypes = args
+    _lib = lib
+    return lib
+
+
+def _ptr(a):
+    return None if a is None else a.ctypes.data_as(ctypes.c_void_p)
+
+
+def _f64(a, shape=None):
+    a = np.ascontiguousarray(a, dtype=np.float64)
+    if shape is not None and a.shape != shape:
+        raise ValueError(f"expected shape {shape}, got {a.shape}")
+    return a
+
+
+def n_lm(lmax: int) -> int:
+    return (lmax + 1) * (lmax + 2) // 2
+
+
+def n_coef(nmax: int, lmax: int) -> int:
+    """Length of one of the S or T halves of a coefficient vector."""
+    return (nmax + 1) * n_lm(lmax)
+
+
+def idx(n: int, l: int, m: int, lmax: int) -> int:
+    return n * n_lm(lmax) + l * (l + 1) // 2 + m
+
+
+def host_struct(components, G: float = 1.0):
+    """``components``: iterable of ``(kind, M, a, b)`` tuples (b unused except MN)."""
+    h = _Host()
+    comps = list(components)
+    if len(comps) > 8:
+        raise ValueError("at most 8 host components")
+    h.n = len(comps)
+    h.G = G
+    for k, (kind, M, a, b) in enumerate(comps):
+        h.c[k].kind, h.c[k].M, h.c[k].a, h.c[k].b = int(kind), float(M), float(a), float(b)
+    return h
+
+
+# ---------------------------------------------------------------- scalars
+def gegenbauer(n, alpha, xi):
+    return _load().or_gegenbauer(int(n), float(alpha), float(xi))
+
+
+def plm(l, m, x):
+    return _load().or_plm(int(l), int(m), float(x))
+
+
+def dplm_dtheta(l, m, costh):
+    return _load().or_dplm_dtheta(int(l), int(m), float(costh))
+
+
+def mplm_over_sin(l, m, costh):
+    return _load().or_mplm_over_sin(int(l), int(m), float(costh))
+
+
+def nlm2(l, m):
+    return _load().or_nlm2(int(l), int(m))
+
+
+def knl(n, l):
+    return _load().or_knl(int(n), int(l))
+
+
+def inl(n, l, b):
+    return _load().or_inl(int(n), int(l), float(b))
+
+
+def phi_nl(n, l, b, r):
+    return _load().or_phi_nl(int(n), int(l), float(b), float(r))
+
+
+def phi_nl_over_r(n, l, b, r):
+    return _load().or_phi_nl_over_r(int(n), int(l), float(b), float(r))
+
+
+def dphi_nl_dr(n, l, b, r):
+    return _load().or_dphi_nl_dr(int(n), int(l), float(b), float(r))
+
+
+def rho_nl(n, l, b, r):
+    return _load().or_rho_nl(int(n), int(l), float(b), float(r))
+
+
+# ---------------------------------------------------------------- arrays
+def coeffs(pos, nmax, lmax, b, mask=None):
+    """Real-form coefficients ``[S | T]`` of Eq. 3b for ``pos`` (N, 4)."""
+    pos = _f64(pos)
+    n = pos.shape[0]
+    m = None if mask is None else np.ascontiguousarray(mask, dtype=np.uint8)
+    A = np.zeros(2 * n_coef(nmax, lmax))
+    _load().or_coeffs(n, _ptr(pos), _ptr(m), int(nmax), int(lmax), float(b), _ptr(A))
+    return A
+
+
+def field(pos, A, nmax, lmax, b, G=1.0):
+    """(N, 4) = (ax, ay, az, potential) of the expansion at ``pos[:, :3]``."""
+    pos = _f64(pos)
+    A = _f64(A)
+    out = np.zeros((pos.shape[0], 4))
+    _load().or_field(pos.shape[0], _ptr(pos), _ptr(A), int(nmax), int(lmax), float(b), float(G), _ptr(out))
+    return out
+
+
+def host_accel(host, x):
+    x = _f64(x)
+    a = np.zeros(3)
+    pot = np.zeros(1)
+    _load().or_host_accel(ctypes.byref(host), _ptr(x), _ptr(a), _ptr(pot))
+    return a, float(pot[0])
+
+
+def tidal(host, R, x):
+    R = _f64(R)
+    x = _f64(x)
+    a = np.zeros(3)
+    _load().or_tidal(ctypes.byref(host), _ptr(R), _ptr(x), _ptr(a))
+    return a
+
+
+def forces(pos, A, nmax, lmax, b, G=1.0, com=None, host=None):
+    pos = _f64(pos)
+    A = _f64(A)
+    out = np.zeros((pos.shape[0], 4))
+    c = None if com is None else _f64(com)
+    hp = None if host is None else ctypes.byref(host)
+    _load().or_forces(pos.shape[0], _ptr(pos), _ptr(A), _ptr(c), hp, int(nmax), int(lmax), float(b), float(G),
+                      _ptr(out))
+    return out
+
+
+def step(pos, vel, acc, nmax, lmax, b, dt, nsteps, G=1.0, com=None, host=None, A_frozen=None):
+    """Kick-drift-kick leapfrog; returns new ``(pos, vel, acc, com, A_last)``.
+
+    ``acc`` must hold the acceleration at ``pos`` (from :func:`forces`)."""
+    pos = _f64(pos).copy()
+    vel = _f64(vel).copy()
+    acc = _f64(acc).copy()
+    com = np.zeros(6) if com is None else _f64(com).copy()
+    A_out = np.zeros(2 * n_coef(nmax, lmax))
+    hp = None if host is None else ctypes.byref(host)
+    Af = None if A_frozen is None else _f64(A_frozen)
+    _load().or_step(pos.shape[0], _ptr(pos), _ptr(vel), _ptr(acc), _ptr(com), hp, int(nmax), int(lmax), float(b),
+                    float(G), float(dt), int(nsteps), _ptr(Af), _ptr(A_out))
+    return pos, vel, acc, com, A_out
+
+
+def direct(src, tgt, G=1.0):
+    """Unsoftened direct-summation (ax, ay, az, potential) at ``tgt`` from ``src``."""
+    src = _f64(src)
+    tgt = _f64(tgt)
+    out = np.zeros((tgt.shape[0], 4))
+    _load().or_direct(src.shape[0], _ptr(src), tgt.shape[0], _ptr(tgt), float(G), _ptr(out))
+    return out
+
+
+def power_l(A, nmax, lmax, b):
+    """E_l = sum_{n,m} |a_nlm|^2 in the bi-orthonormal normalisation of Eq. 3a."""
+    A = _f64(A)
+    El = np.zeros(lmax + 1)
+    _load().or_power_l(_ptr(A), int(nmax), int(lmax), float(b), _ptr(El))
+    return El
+
+
+def num_threads() -> int:
+    return int(_load().or_num_threads())

@@ -1,0 +1,509 @@
+/*
+ * Plain FP64 CPU oracle for the self-consistent-field (SCF) gravity step of
+ * the basis-expansion N-body method (KRIOS II, arXiv:2602.13385).
+ *
+ * TEST INFRASTRUCTURE ONLY.  This file is the slow, obviously-correct
+ * definition the CUDA path is checked against.  Only the test suite, the smoke
+ * check and the benchmark's CPU-baseline leg may load it.  It shares no code,
+ * header, table or constant with the CUDA library.
+ *
+ * What it computes, and where the paper defines it:
+ *   - Eq. 1a/1b: potential and density as sums of a_nlm times basis functions.
+ *   - Eq. 2:     separable basis psi_nlm = U_n^l(r) Y_l^m(theta, phi).
+ *   - Eq. 3a/3b: coefficients from a mass-weighted particle sum,
+ *                a_nlm = -sum_k m_k psi*_nlm(r_k).
+ *   - Eq. 4:     Zhao (1996) radial family; alpha = 1 is the Hernquist-Ostriker
+ *                (1992) Gegenbauer basis used here.
+ *   - Sec. 2 ("N individual, embarrassingly parallel integrations"): every
+ *                particle is moved in -grad psi_SCF.
+ *   - Sec. 2.1:  accelerating, non-rotating cluster frame whose origin follows
+ *                a centre-of-mass test particle in the host potential.
+ *   - App. A:    Hernquist, NFW and Miyamoto-Nagai host components.
+ *
+ * Conventions (the paper's normalisation is a bi-orthonormal basis with a
+ * leading minus in Eq. 3a; the reading below is the same expansion written
+ * with the Hernquist-Ostriker normalisation I_nl):
+ *   s = r/b, xi = (s-1)/(s+1), alpha_l = 2l + 3/2
+ *   Phi_nl(r) = -(1/b) s^l (1+s)^-(2l+1) C_n^(alpha_l)(xi)          (G = 1)
+ *   rho_nl(r) = K_nl/(2 pi b^3) s^(l-1) (1+s)^-(2l+3) C_n^(alpha_l)(xi)
+ *   K_nl      = n(n+4l+3)/2 + (l+1)(2l+1)
+ *   I_nl      = int r^2 rho_nl Phi_nl dr
+ *   Real form of the coefficients (S = cosine part, T = sine part):
+ *   S_nlm = (2-delta_m0)/I_nl N_lm^2 sum_k w_k m_k Phi_nl(r_k) P_l^m(cos th_k) cos(m ph_k)
+ *   T_nlm = (2-delta_m0)/I_nl N_lm^2 sum_k w_k m_k Phi_nl(r_k) P_l^m(cos th_k) sin(m ph_k)
+ *   N_lm^2 = (2l+1)/(4 pi) (l-m)!/(l+m)!, P_l^m with the Condon-Shortley phase.
+ *   psi(x) = G sum_nl Phi_nl(r) sum_m P_l^m(cos th) [S_nlm cos(m ph) + T_nlm sin(m ph)]
+ *
+ * Coefficient storage: A = [S | T], each (nmax+1) * (lmax+1)(lmax+2)/2 doubles,
+ * index (n, l, m) -> n * N_lm + l(l+1)/2 + m; T_nl0 is stored as 0.
+ * Particle storage: 4 doubles per particle, (x, y, z, m) for positions,
+ * (vx, vy, vz, unused) for velocities, (ax, ay, az, potential) for accelerations.
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+#define OR_PI 3.14159265358979323846
+
+/* ------------------------------------------------------------------------ */
+/* Special functions (textbook recurrences)                                 */
+/* ------------------------------------------------------------------------ */
+
+/* Gegenbauer polynomial C_n^alpha(xi) by the three-term recurrence
+ * n C_n = 2 (n + alpha - 1) xi C_{n-1} - (n + 2 alpha - 2) C_{n-2}. */
+double or_gegenbauer(int n, double alpha, double xi) {
+  if (n < 0) return 0.0;
+  double c_prev = 1.0;
+  if (n == 0) return c_prev;
+  double c = 2.0 * alpha * xi;
+  for (int k = 2; k <= n; ++k) {
+    double c_next = (2.0 * (k + alpha - 1.0) * xi * c - (k + 2.0 * alpha - 2.0) * c_prev) / k;
+    c_prev = c;
+    c = c_next;
+  }
+  return c;
+}
+
+/* Associated Legendre function P_l^m(cos th), 0 <= m <= l, including the
+ * Condon-Shortley phase (-1)^m, from c = cos th and s = sin th >= 0:
+ *   P_m^m = (-1)^m (2m-1)!! s^m,  P_{m+1}^m = c (2m+1) P_m^m,
+ *   (l-m) P_l^m = c (2l-1) P_{l-1}^m - (l+m-1) P_{l-2}^m.
+ * Taking s separately (rather than sqrt(1 - c^2)) keeps full accuracy next to
+ * the z axis. */
+static double plm_cs(int l, int m, double c, double s) {
+  if (m < 0 || m > l) return 0.0;
+  double pmm = 1.0;
+  for (int i = 1; i <= m; ++i) pmm *= -(2.0 * i - 1.0) * s;
+  if (l == m) return pmm;
+  double pmmp1 = c * (2.0 * m + 1.0) * pmm;
+  if (l == m + 1) return pmmp1;
+  double pll = 0.0;
+  for (int ll = m + 2; ll <= l; ++ll) {
+    pll = (c * (2.0 * ll - 1.0) * pmmp1 - (ll + m - 1.0) * pmm) / (ll - m);
+    pmm = pmmp1;
+    pmmp1 = pll;
+  }
+  return pll;
+}
+
+static double sin_from_cos(double x) { return sqrt(fmax(0.0, (1.0 - x) * (1.0 + x))); }
+
+double or_plm(int l, int m, double x) { return plm_cs(l, m, x, sin_from_cos(x)); }
+
+/* dP_l^m(cos th)/d th, from the identity
+ *   dP_l^m/dth = (P_l^{m+1} - (l+m)(l-m+1) P_l^{m-1}) / 2   (m >= 1),
+ *   dP_l^0/dth = P_l^1,
+ * which involves no division by sin(th) and so holds on the z axis. */
+static double dplm_dtheta_cs(int l, int m, double c, double s) {
+  if (m == 0) return plm_cs(l, 1, c, s);
+  return 0.5 * (plm_cs(l, m + 1, c, s) - (double)(l + m) * (l - m + 1) * plm_cs(l, m - 1, c, s));
+}
+
+/* m P_l^m(cos th) / sin(th) for m >= 1, from the identity
+ *   m P_l^m / sin th = -(P_{l+1}^{m+1} + (l-m+1)(l-m+2) P_{l+1}^{m-1}) / 2,
+ * finite on the z axis. */
+static double mplm_over_sin_cs(int l, int m, double c, double s) {
+  if (m == 0) return 0.0;
+  return -0.5 * (plm_cs(l + 1, m + 1, c, s) + (double)(l - m + 1) * (l - m + 2) * plm_cs(l + 1, m - 1, c, s));
+}
+
+double or_dplm_dtheta(int l, int m, double costh) { return dplm_dtheta_cs(l, m, costh, sin_from_cos(costh)); }
+double or_mplm_over_sin(int l, int m, double costh) { return mplm_over_sin_cs(l, m, costh, sin_from_cos(costh)); }
+
+/* N_lm^2 = (2l+1)/(4 pi) (l-m)!/(l+m)! */
+double or_nlm2(int l, int m) {
+  double ratio = 1.0;
+  for (int k = l - m + 1; k <= l + m; ++k) ratio /= (double)k;
+  return (2.0 * l + 1.0) / (4.0 * OR_PI) * ratio;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Hernquist-Ostriker radial basis (Eq. 4 with alpha = 1)                   */
+/* ------------------------------------------------------------------------ */
+
+double or_knl(int n, int l) { return 0.5 * n * (n + 4.0 * l + 3.0) + (l + 1.0) * (2.0 * l + 1.0); }
+
+/* Closed form of I_nl = int_0^inf r^2 rho_nl Phi_nl dr:
+ *   I_nl = -K_nl Gamma(n+4l+3) / (2^(8l+6) n! (n+2l+3/2) Gamma(2l+3/2)^2) / b. */
+double or_inl(int n, int l, double b) {
+  double lg = lgamma(n + 4.0 * l + 3.0) - (8.0 * l + 6.0) * log(2.0) - lgamma(n + 1.0) -
+              log(n + 2.0 * l + 1.5) - 2.0 * lgamma(2.0 * l + 1.5);
+  return -or_knl(n, l) * exp(lg) / b;
+}
+
+double or_phi_nl(int n, int l, double b, double r) {
+  double s = r / b, xi = (s - 1.0) / (s + 1.0);
+  return -(1.0 / b) * pow(s, l) * pow(1.0 + s, -(2.0 * l + 1.0)) * or_gegenbauer(n, 2.0 * l + 1.5, xi);
+}
+
+/* Phi_nl(r) / r for l >= 1 (finite at r = 0). */
+double or_phi_nl_over_r(int n, int l, double b, double r) {
+  double s = r / b, xi = (s - 1.0) / (s + 1.0);
+  return -(1.0 / (b * b)) * pow(s, l - 1) * pow(1.0 + s, -(2.0 * l + 1.0)) * or_gegenbauer(n, 2.0 * l + 1.5, xi);
+}
+
+/* dPhi_nl/dr using dC_n^a/dxi = 2a C_{n-1}^{a+1} and dxi/ds = 2/(1+s)^2. */
+double or_dphi_nl_dr(int n, int l, double b, double r) {
+  double s = r / b, xi = (s - 1.0) / (s + 1.0), alpha = 2.0 * l + 1.5;
+  double cn = or_gegenbauer(n, alpha, xi);
+  double dcn = 2.0 * alpha * or_gegenbauer(n - 1, alpha + 1.0, xi);
+  double q = 1.0 / (1.0 + s);
+  double sl = pow(s, l), qpow = pow(q, 2.0 * l + 1.0);
+  double t1 = (l > 0) ? l * pow(s, l - 1) * qpow * cn : 0.0;
+  double t2 = -(2.0 * l + 1.0) * sl * qpow * q * cn;
+  double t3 = sl * qpow * dcn * 2.0 * q * q;
+  return -(1.0 / (b * b)) * (t1 + t2 + t3);
+}
+
+double or_rho_nl(int n, int l, double b, double r) {
+  double s = r / b, xi = (s - 1.0) / (s + 1.0);
+  return or_knl(n, l) / (2.0 * OR_PI * b * b * b) * pow(s, l - 1.0) * pow(1.0 + s, -(2.0 * l + 3.0)) *
+         or_gegenbauer(n, 2.0 * l + 1.5, xi);
+}
+
+/* ------------------------------------------------------------------------ */
+/* Coefficients (Eq. 3b, real form)                                         */
+/* ------------------------------------------------------------------------ */
+
+static int nlm_count(int lmax) { return (lmax + 1) * (lmax + 2) / 2; }
+static int lm_index(int l, int m) { return l * (l + 1) / 2 + m; }
+
+/* Neumaier compensated accumulation. */
+static void neu_add(double* sum, double* comp, double v) {
+  double t = *sum + v;
+  if (fabs(*sum) >= fabs(v)) *comp += (*sum - t) + v;
+  else *comp += (v - t) + *sum;
+  *sum = t;
+}
+
+/* Spherical angles of a point; at r = 0 the point is given theta = 0, phi = 0
+ * (only l = 0 terms are non-zero there, so the choice does not matter).
+ * sin(theta) comes from the cylindrical radius, not from cos(theta). */
+static void sph(double x, double y, double z, double* r, double* costh, double* sinth, double* phi) {
+  *r = sqrt(x * x + y * y + z * z);
+  *costh = (*r > 0.0) ? z / *r : 1.0;
+  *sinth = (*r > 0.0) ? sqrt(x * x + y * y) / *r : 0.0;
+  if (*costh > 1.0) *costh = 1.0;
+  if (*costh < -1.0) *costh = -1.0;
+  if (*sinth > 1.0) *sinth = 1.0;
+  *phi = atan2(y, x);
+}
+
+#define OR_CHUNKS 64
+
+/* A = [S | T] for the particles with mask[k] != 0 (mask NULL: all). */
+void or_coeffs(int64_t n_part, const double* pos, const uint8_t* mask, int nmax, int lmax, double b, double* A) {
+  const int nn = nmax + 1, nlm = nlm_count(lmax), nc = nn * nlm;
+  /* Fixed particle chunks summed in chunk order: the result does not depend
+   * on the number of threads. */
+  double* part = (double*)calloc((size_t)OR_CHUNKS * 4 * nc, sizeof(double));
+#pragma omp parallel for schedule(dynamic, 1)
+  for (int ch = 0; ch < OR_CHUNKS; ++ch) {
+    int64_t k0 = n_part * ch / OR_CHUNKS, k1 = n_part * (ch + 1) / OR_CHUNKS;
+    double* ssum = part + (size_t)ch * 4 * nc;
+    double* scmp = ssum + nc;
+    double* tsum = ssum + 2 * nc;
+    double* tcmp = ssum + 3 * nc;
+    double* phinl = (double*)malloc(sizeof(double) * nn * (lmax + 1));
+    double* plm = (double*)malloc(sizeof(double) * nlm);
+    for (int64_t k = k0; k < k1; ++k) {
+      if (mask && !mask[k]) continue;
+      const double* p = pos + 4 * k;
+      double r, costh, sinth, phi;
+      sph(p[0], p[1], p[2], &r, &costh, &sinth, &phi);
+      for (int n = 0; n <= nmax; ++n)
+        for (int l = 0; l <= lmax; ++l) phinl[n * (lmax + 1) + l] = or_phi_nl(n, l, b, r);
+      for (int l = 0; l <= lmax; ++l)
+        for (int m = 0; m <= l; ++m) plm[lm_index(l, m)] = plm_cs(l, m, costh, sinth);
+      for (int n = 0; n <= nmax; ++n)
+        for (int l = 0; l <= lmax; ++l)
+          for (int m = 0; m <= l; ++m) {
+            double w = p[3] * phinl[n * (lmax + 1) + l] * plm[lm_index(l, m)];
+            int i = n * nlm + lm_index(l, m);
+            neu_add(&ssum[i], &scmp[i], w * cos(m * phi));
+            if (m > 0) neu_add(&tsum[i], &tcmp[i], w * sin(m * phi));
+          }
+    }
+    free(phinl);
+    free(plm);
+  }
+  for (int i = 0; i < nc; ++i) {
+    double s = 0.0, sc = 0.0, t = 0.0, tc = 0.0;
+    for (int ch = 0; ch < OR_CHUNKS; ++ch) {
+      const double* q = part + (size_t)ch * 4 * nc;
+      neu_add(&s, &sc, q[i] + q[nc + i]);
+      neu_add(&t, &tc, q[2 * nc + i] + q[3 * nc + i]);
+    }
+    A[i] = s + sc;
+    A[nc + i] = t + tc;
+  }
+  free(part);
+  for (int n = 0; n <= nmax; ++n)
+    for (int l = 0; l <= lmax; ++l) {
+      double inl = or_inl(n, l, b);
+      for (int m = 0; m <= l; ++m) {
+        double f = (m == 0 ? 1.0 : 2.0) / inl * or_nlm2(l, m);
+        int i = n * nlm + lm_index(l, m);
+        A[i] *= f;
+        A[nc + i] = (m == 0) ? 0.0 : A[nc + i] * f;
+      }
+    }
+}
+
+/* ------------------------------------------------------------------------ */
+/* Potential and acceleration of the expansion (Eq. 1a; a = -grad psi)      */
+/* ------------------------------------------------------------------------ */
+
+/* Spherical components of -grad psi:
+ *   a_r  = -sum dPhi_nl/dr  sum_m P_l^m        [S cos + T sin]
+ *   a_th = -sum Phi_nl/r    sum_m dP_l^m/dth   [S cos + T sin]
+ *   a_ph = -sum Phi_nl/r    sum_m m P_l^m/sin  [-S sin + T cos]
+ * On the z axis phi = 0 is used (the field is smooth there and the formulas
+ * above are finite).  At r = 0 the l = 0 radial term has no direction and is
+ * dropped (its limit depends on the direction of approach); the l = 1 terms
+ * give the finite gradient there and l >= 2 terms vanish. */
+static void field_one(const double* x3, const double* A, int nmax, int lmax, double b, double G, double* out4) {
+  const int nlm = nlm_count(lmax), nc = (nmax + 1) * nlm;
+  double r, costh, sinth, phi;
+  sph(x3[0], x3[1], x3[2], &r, &costh, &sinth, &phi);
+  double pot = 0.0, ar = 0.0, ath = 0.0, aph = 0.0;
+  for (int l = 0; l <= lmax; ++l) {
+    for (int n = 0; n <= nmax; ++n) {
+      double phi_nl = or_phi_nl(n, l, b, r);
+      double dphi = or_dphi_nl_dr(n, l, b, r);
+      double phi_r = (l >= 1) ? or_phi_nl_over_r(n, l, b, r) : 0.0;
+      for (int m = 0; m <= l; ++m) {
+        int i = n * nlm + lm_index(l, m);
+        double S = A[i], T = A[nc + i];
+        double cm = cos(m * phi), sm = sin(m * phi);
+        double ang = S * cm + T * sm;
+        double plm = plm_cs(l, m, costh, sinth);
+        pot += phi_nl * plm * ang;
+        if (!(r == 0.0 && l == 0)) ar -= dphi * plm * ang;
+        if (l >= 1) {
+          ath -= phi_r * dplm_dtheta_cs(l, m, costh, sinth) * ang;
+          aph -= phi_r * mplm_over_sin_cs(l, m, costh, sinth) * (-S * sm + T * cm);
+        }
+      }
+    }
+  }
+  double cph = cos(phi), sph_ = sin(phi);
+  out4[0] = G * (ar * sinth * cph + ath * costh * cph - aph * sph_);
+  out4[1] = G * (ar * sinth * sph_ + ath * costh * sph_ + aph * cph);
+  out4[2] = G * (ar * costh - ath * sinth);
+  out4[3] = G * pot;
+}
+
+void or_field(int64_t n_part, const double* pos, const double* A, int nmax, int lmax, double b, double G, double* acc) {
+#pragma omp parallel for schedule(static)
+  for (int64_t k = 0; k < n_part; ++k) field_one(pos + 4 * k, A, nmax, lmax, b, G, acc + 4 * k);
+}
+
+/* ------------------------------------------------------------------------ */
+/* Host potential (App. A): Hernquist, NFW, Miyamoto-Nagai                  */
+/* ------------------------------------------------------------------------ */
+
+enum { OR_HOST_HERNQUIST = 1, OR_HOST_NFW = 2, OR_HOST_MN = 3 };
+
+typedef struct {
+  int kind;
+  double M; /* Hernquist: total mass; NFW: scale mass M_NFW; MN: disk mass */
+  double a; /* Hernquist: scale radius; NFW: r_s; MN: scale length a */
+  double b; /* MN: scale height b; unused otherwise */
+} or_host_comp;
+
+typedef struct {
+  int n;
+  double G;
+  or_host_comp c[8];
+} or_host;
+
+/* Potential and acceleration of the host at x (long double throughout). */
+static void host_eval_l(const or_host* h, const long double* x, long double* a, long double* pot) {
+  long double ax = 0, ay = 0, az = 0, ps = 0;
+  long double r2 = x[0] * x[0] + x[1] * x[1] + x[2] * x[2];
+  long double r = sqrtl(r2);
+  for (int i = 0; i < h->n; ++i) {
+    const or_host_comp* c = &h->c[i];
+    long double GM = (long double)h->G * c->M;
+    if (c->kind == OR_HOST_HERNQUIST) {
+      /* psi = -GM/(r+a); f_r = -G M_enc/r^2 = -GM/(r+a)^2 */
+      long double A = c->a;
+      ps += -GM / (r + A);
+      if (r > 0) {
+        long double fr = -GM / ((r + A) * (r + A));
+        ax += fr * x[0] / r; ay += fr * x[1] / r; az += fr * x[2] / r;
+      }
+    } else if (c->kind == OR_HOST_NFW) {
+      /* psi = -GM ln(1+r/rs)/r; M_enc = M g(r/rs), g(u) = ln(1+u) - u/(1+u) */
+      long double rs = c->a;
+      if (r > 0) {
+        long double u = r / rs;
+        ps += -GM * log1pl(u) / r;
+        long double g = log1pl(u) - u / (1 + u);
+        long double fr = -GM * g / r2;
+        ax += fr * x[0] / r; ay += fr * x[1] / r; az += fr * x[2] / r;
+      } else {
+        ps += -GM / rs;
+      }
+    } else if (c->kind == OR_HOST_MN) {
+      /* psi = -GM / sqrt(R^2 + z_ab^2), z_ab = sqrt(z^2+b^2) + a */
+      long double A = c->a, B = c->b;
+      long double zb = sqrtl(x[2] * x[2] + B * B);
+      long double zab = zb + A;
+      long double D2 = x[0] * x[0] + x[1] * x[1] + zab * zab;
+      long double D = sqrtl(D2);
+      long double D3 = D2 * D;
+      ps += -GM / D;
+      ax += -GM * x[0] / D3;
+      ay += -GM * x[1] / D3;
+      az += -GM * x[2] * zab / (zb * D3);
+    }
+  }
+  a[0] = ax; a[1] = ay; a[2] = az;
+  *pot = ps;
+}
+
+void or_host_accel(const or_host* h, const double* x, double* a, double* pot) {
+  long double xl[3] = {x[0], x[1], x[2]}, al[3], pl;
+  host_eval_l(h, xl, al, &pl);
+  a[0] = (double)al[0]; a[1] = (double)al[1]; a[2] = (double)al[2];
+  if (pot) *pot = (double)pl;
+}
+
+/* Tidal acceleration in the accelerating, non-rotating cluster frame
+ * (Sec. 2.1): a_host(R + x) - a_host(R), evaluated and differenced in long
+ * double so the cancellation between the two terms costs nothing. */
+void or_tidal(const or_host* h, const double* R, const double* x, double* a) {
+  long double p[3] = {(long double)R[0] + x[0], (long double)R[1] + x[1], (long double)R[2] + x[2]};
+  long double q[3] = {R[0], R[1], R[2]};
+  long double ap[3], aq[3], pp, pq;
+  host_eval_l(h, p, ap, &pp);
+  host_eval_l(h, q, aq, &pq);
+  for (int i = 0; i < 3; ++i) a[i] = (double)(ap[i] - aq[i]);
+}
+
+/* acc = -grad psi_SCF (coefficients A) + tidal term (host may be NULL). */
+void or_forces(int64_t n_part, const double* pos, const double* A, const double* com, const or_host* host, int nmax,
+               int lmax, double b, double G, double* acc) {
+  or_field(n_part, pos, A, nmax, lmax, b, G, acc);
+  if (host && host->n > 0) {
+#pragma omp parallel for schedule(static)
+    for (int64_t k = 0; k < n_part; ++k) {
+      double t[3];
+      or_tidal(host, com, pos + 4 * k, t);
+      acc[4 * k + 0] += t[0];
+      acc[4 * k + 1] += t[1];
+      acc[4 * k + 2] += t[2];
+    }
+  }
+}
+
+/* ------------------------------------------------------------------------ */
+/* Kick-drift-kick leapfrog with the centre-of-mass orbit in lock-step      */
+/* ------------------------------------------------------------------------ */
+
+/* Advances nsteps of size dt.  On entry acc holds the acceleration at pos
+ * (e.g. from or_forces); on exit it holds the acceleration at the new pos.
+ * com = (R, V) of the cluster frame in the host frame; it moves with the same
+ * kick-drift-kick in the host field alone (Sec. 2.1).  The coefficients are
+ * recomputed from the particles at every force evaluation unless A_frozen is
+ * given, in which case the potential is static.  A_out (nullable) receives
+ * the last coefficients used. */
+void or_step(int64_t n_part, double* pos, double* vel, double* acc, double* com, const or_host* host, int nmax,
+             int lmax, double b, double G, double dt, int nsteps, const double* A_frozen, double* A_out) {
+  const int nc = (nmax + 1) * nlm_count(lmax);
+  double* A = (double*)malloc(sizeof(double) * 2 * nc);
+  int has_host = host && host->n > 0;
+  double aR[3] = {0, 0, 0};
+  if (has_host) or_host_accel(host, com, aR, NULL);
+  for (int st = 0; st < nsteps; ++st) {
+    for (int64_t k = 0; k < n_part; ++k) {
+      double* p = pos + 4 * k;
+      double* v = vel + 4 * k;
+      const double* a = acc + 4 * k;
+      for (int d = 0; d < 3; ++d) {
+        v[d] += 0.5 * dt * a[d];
+        p[d] += dt * v[d];
+      }
+    }
+    if (has_host) {
+      for (int d = 0; d < 3; ++d) {
+        com[3 + d] += 0.5 * dt * aR[d];
+        com[d] += dt * com[3 + d];
+      }
+    }
+    if (A_frozen) memcpy(A, A_frozen, sizeof(double) * 2 * nc);
+    else or_coeffs(n_part, pos, NULL, nmax, lmax, b, A);
+    or_forces(n_part, pos, A, com, host, nmax, lmax, b, G, acc);
+    if (has_host) {
+      or_host_accel(host, com, aR, NULL);
+      for (int d = 0; d < 3; ++d) com[3 + d] += 0.5 * dt * aR[d];
+    }
+    for (int64_t k = 0; k < n_part; ++k) {
+      double* v = vel + 4 * k;
+      const double* a = acc + 4 * k;
+      for (int d = 0; d < 3; ++d) v[d] += 0.5 * dt * a[d];
+    }
+  }
+  if (A_out) memcpy(A_out, A, sizeof(double) * 2 * nc);
+  free(A);
+}
+
+/* ------------------------------------------------------------------------ */
+/* Direct summation (the comparison of Sec. 5.1 / Fig. 10)                  */
+/* ------------------------------------------------------------------------ */
+
+/* Newtonian potential and acceleration at n_tgt points from the n_src
+ * particles (no softening; a source at the target's own position is skipped). */
+void or_direct(int64_t n_src, const double* src, int64_t n_tgt, const double* tgt, double G, double* out) {
+#pragma omp parallel for schedule(static)
+  for (int64_t i = 0; i < n_tgt; ++i) {
+    double ax = 0, ay = 0, az = 0, ps = 0;
+    for (int64_t j = 0; j < n_src; ++j) {
+      double dx = src[4 * j] - tgt[4 * i], dy = src[4 * j + 1] - tgt[4 * i + 1], dz = src[4 * j + 2] - tgt[4 * i + 2];
+      double d2 = dx * dx + dy * dy + dz * dz;
+      if (d2 == 0.0) continue;
+      double d = sqrt(d2);
+      double w = G * src[4 * j + 3] / (d2 * d);
+      ax += w * dx; ay += w * dy; az += w * dz;
+      ps -= G * src[4 * j + 3] / d;
+    }
+    out[4 * i] = ax; out[4 * i + 1] = ay; out[4 * i + 2] = az; out[4 * i + 3] = ps;
+  }
+}
+
+/* Power in each l of the expansion, E_l = sum_{n,m} |a_nlm|^2 (Sec. 5.2), with
+ * a_nlm the coefficients of the bi-orthonormal basis of Eq. 3a.  In terms of
+ * the real form: the orthonormal-harmonic coefficient is A_nl0 = S_nl0/N_l0
+ * and, for m > 0, |A_nlm|^2 = |A_nl,-m|^2 = (S^2 + T^2)/(4 N_lm^2); the
+ * bi-orthonormal basis rescales each by sqrt(|I_nl|). */
+void or_power_l(const double* A, int nmax, int lmax, double b, double* El) {
+  const int nlm = nlm_count(lmax), nc = (nmax + 1) * nlm;
+  for (int l = 0; l <= lmax; ++l) {
+    double e = 0.0;
+    for (int n = 0; n <= nmax; ++n) {
+      double inl = fabs(or_inl(n, l, b));
+      for (int m = 0; m <= l; ++m) {
+        int i = n * nlm + lm_index(l, m);
+        double n2 = or_nlm2(l, m);
+        if (m == 0) e += inl * A[i] * A[i] / n2;
+        else e += inl * 2.0 * (A[i] * A[i] + A[nc + i] * A[nc + i]) / (4.0 * n2);
+      }
+    }
+    El[l] = e;
+  }
+}
+
+int or_num_threads(void) {
+#ifdef _OPENMP
+  return omp_get_max_threads();
+#else
+  return 1;
+#endif
+}
