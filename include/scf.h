@@ -1,0 +1,180 @@
+/*
+ * scf.h — C ABI of the GB300 self-consistent-field (SCF) gravity step.
+ *
+ * The method is the basis-expansion N-body scheme of KRIOS II
+ * (arXiv:2602.13385, Sec. 2): the cluster potential is expanded in a
+ * bi-orthogonal basis (Eq. 1a-2), the expansion coefficients are a
+ * mass-weighted sum over particles (Eq. 3b), every particle moves in the
+ * expansion's field plus the tidal field of an analytic host galaxy (Sec. 2.1,
+ * App. A), and the radial basis is the Zhao family of Eq. 4 at alpha = 1
+ * (Hernquist-Ostriker Gegenbauer basis), in units with G given by the caller
+ * (Henon units: G = 1).
+ *
+ * All compute runs in CUDA kernels on one GPU (sm_103a).  The library does not
+ * fall back to the CPU: every call that cannot run on the device returns an
+ * error code.
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * Coefficients.  Real form of the expansion:
+ *   psi(x) = G sum_{n,l} Phi_nl(r) sum_{m=0..l} P_l^m(cos th) [S_nlm cos(m ph) + T_nlm sin(m ph)]
+ *   Phi_nl(r) = -(1/b) s^l (1+s)^-(2l+1) C_n^(2l+3/2)((s-1)/(s+1)),  s = r/b,
+ *   S_nlm, T_nlm = (2 - delta_m0)/I_nl N_lm^2 sum_k w_k m_k Phi_nl(r_k) P_l^m(cos th_k) {cos, sin}(m ph_k)
+ * with P_l^m carrying the Condon-Shortley phase, N_lm^2 = (2l+1)/(4 pi)
+ * (l-m)!/(l+m)! and I_nl = int r^2 rho_nl Phi_nl dr the Hernquist-Ostriker
+ * normalisation.  This is Eq. 3b with the paper's bi-orthonormal basis
+ * rescaled by sqrt|I_nl|; the potential is identical.
+ * A coefficient vector is [S | T], each half NC = (nmax+1)(lmax+1)(lmax+2)/2
+ * doubles, entry (n, l, m) at n*(lmax+1)(lmax+2)/2 + l(l+1)/2 + m.  T_nl0 = 0.
+ * With several progenitors the vectors are stacked: [n_prog][2*NC].
+ *
+ * Particles.  Device pointers, 4 components per particle, 16-byte aligned,
+ * particles of progenitor p at indices [offsets[p], offsets[p+1]):
+ *   pos = (x, y, z, m) in the cluster frame (origin at the cluster centre R),
+ *   vel = (vx, vy, vz, unused), velocities relative to the frame,
+ *   acc = (ax, ay, az, psi_SCF) — acceleration incl. the tidal term; the 4th
+ *         component is the expansion's potential only.
+ * Element type: double for SCF_FP64, float for SCF_MIXED.
+ *
+ * Centre of mass.  com = [n_prog][6] doubles (R, V) in the host frame (device
+ * pointer), always double precision.
+ *
+ * Streams and ownership.  Every call enqueues work on the stream given to
+ * scf_init and returns without waiting, except scf_status and scf_free.  The
+ * caller owns all particle, coefficient and centre buffers; the handle owns
+ * its workspace (block partials, block maps, a coefficient buffer, the status
+ * word), allocated once in scf_init.  No call allocates after scf_init.
+ *
+ * Errors.  Every entry point returns 0 (SCF_OK) or a negative SCF_ERR_* code;
+ * scf_strerror gives a static description.  Device-side problems (non-finite
+ * positions) set bits of a status word read by scf_status; kernels never trap.
+ */
+#ifndef SCF_GB300_H
+#define SCF_GB300_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- return codes ---- */
+#define SCF_OK 0
+#define SCF_ERR_INVALID_ARG (-1)   /* a size, count, offset or option is out of range */
+#define SCF_ERR_NULL_POINTER (-2)  /* a required pointer is NULL */
+#define SCF_ERR_MISALIGNED (-3)    /* a particle pointer is not 16-byte aligned */
+#define SCF_ERR_UNSUPPORTED (-4)   /* alpha != 1, lmax/nmax beyond the compiled limits */
+#define SCF_ERR_CUDA (-5)          /* a CUDA runtime call or kernel launch failed */
+#define SCF_ERR_OUT_OF_MEMORY (-6) /* workspace allocation failed in scf_init */
+#define SCF_ERR_DEVICE_STATUS (-7) /* scf_status found device-side problems */
+
+/* ---- device status bits (scf_status) ---- */
+#define SCF_STATUS_NONFINITE_POS 1 /* a particle position was NaN/Inf; it was skipped */
+#define SCF_STATUS_NONFINITE_ACC 2 /* an acceleration came out NaN/Inf */
+
+/* ---- limits of the compiled kernels ---- */
+#define SCF_MAX_LMAX 12
+#define SCF_MAX_NMAX 40
+#define SCF_MAX_HOST_COMPONENTS 8
+
+/* ---- precision (Sec. 2 leaves it open) ---- */
+#define SCF_FP64 0  /* every step in double precision */
+#define SCF_MIXED 1 /* basis and field in float; coefficient sums, centre orbit and tidal term in double */
+
+/* ---- host components (App. A); parameters in the caller's units ---- */
+#define SCF_HOST_HERNQUIST 1 /* M = total mass, a = scale radius:  psi = -G M / (r + a)            */
+#define SCF_HOST_NFW 2       /* M = scale mass M_NFW, a = r_s:     psi = -G M ln(1 + r/r_s) / r     */
+#define SCF_HOST_MN 3        /* M, a = scale length, b = height:   psi = -G M / sqrt(R^2 + (sqrt(z^2+b^2)+a)^2) */
+
+typedef struct scf_host_component {
+  int kind;
+  double M, a, b;
+} scf_host_component;
+
+typedef struct scf_config {
+  int nmax;          /* radial truncation, 0 <= nmax <= SCF_MAX_NMAX */
+  int lmax;          /* angular truncation, 0 <= lmax <= SCF_MAX_LMAX */
+  double alpha;      /* Zhao exponent of Eq. 4; must be 1 (Hernquist-Ostriker basis) */
+  double b;          /* basis scale length b of Eq. 4 (> 0); per-progenitor values may override */
+  double G;          /* gravitational constant (1 in Henon units) */
+  double dt;         /* leapfrog step for scf_step */
+  int precision;     /* SCF_FP64 or SCF_MIXED */
+  int n_host;        /* number of host components, 0 = isolated cluster (no tidal term) */
+  scf_host_component host[SCF_MAX_HOST_COMPONENTS];
+} scf_config;
+
+typedef struct scf_handle scf_handle;
+
+/* Creates a handle for n_prog progenitors (independent clusters sharing the
+ * configuration) whose particles occupy [offsets[p], offsets[p+1]) of every
+ * particle array.
+ *   cfg        host pointer, copied.
+ *   offsets    host pointer to n_prog+1 non-decreasing int64, offsets[0] = 0.
+ *   b_per_prog host pointer to n_prog basis scales, or NULL to use cfg->b.
+ *   stream     a cudaStream_t (NULL = legacy default stream) on the current device.
+ * Allocates the workspace on the current device and writes the handle to *out.
+ * Errors: SCF_ERR_NULL_POINTER, SCF_ERR_INVALID_ARG, SCF_ERR_UNSUPPORTED,
+ * SCF_ERR_OUT_OF_MEMORY, SCF_ERR_CUDA; *out is untouched on error. */
+int scf_init(const scf_config* cfg, int n_prog, const int64_t* offsets, const double* b_per_prog, void* stream,
+             scf_handle** out);
+
+/* Expansion coefficients of Eq. 3b for every progenitor: the particle sum
+ * (kernel 1: per-block partial sums) followed by a deterministic fixed-order
+ * reduction and the normalisation (kernel 2).  Bitwise reproducible for a
+ * given handle.
+ *   pos   device, particle positions (see Particles).
+ *   mask  device, one byte per particle, 0 = leave out of the sum; NULL = all.
+ *   A_out device, [n_prog][2*NC] doubles.
+ * Errors: SCF_ERR_NULL_POINTER, SCF_ERR_MISALIGNED, SCF_ERR_CUDA. */
+int scf_coeffs(scf_handle* h, const void* pos, const uint8_t* mask, double* A_out);
+
+/* Acceleration -grad psi_SCF (Eq. 1a) at every particle from the given
+ * coefficients, plus the tidal acceleration of the accelerating, non-rotating
+ * cluster frame (Sec. 2.1) a_host(R + x) - a_host(R) when the configuration
+ * has host components.
+ *   pos  device positions; A device [n_prog][2*NC] doubles;
+ *   com  device [n_prog][6] doubles (only R is read); may be NULL without host;
+ *   acc  device output (see Particles).
+ * Errors: SCF_ERR_NULL_POINTER, SCF_ERR_MISALIGNED, SCF_ERR_CUDA. */
+int scf_forces(scf_handle* h, const void* pos, const double* A, const double* com, void* acc);
+
+/* nsteps kick-drift-kick leapfrog steps of size cfg->dt.  Each step: half
+ * kick and drift of every particle, the same for the centre orbit R, V in
+ * the host field (double precision), coefficients of the new positions
+ * (all particles), accelerations at the new positions, half kick.
+ *   pos, vel, acc device particle arrays, updated in place.  On entry acc
+ *                 must hold the acceleration at pos (from scf_forces or the
+ *                 previous scf_step); on return it holds the one at the new pos.
+ *   com           device [n_prog][6] doubles, updated in place (may be NULL
+ *                 without host components).
+ * The coefficients of the last step can be read with scf_last_coeffs.
+ * Errors: SCF_ERR_NULL_POINTER, SCF_ERR_MISALIGNED, SCF_ERR_INVALID_ARG
+ * (nsteps < 0), SCF_ERR_CUDA. */
+int scf_step(scf_handle* h, void* pos, void* vel, void* acc, double* com, int nsteps);
+
+/* Copies (device to device, on the handle's stream) the coefficients used by
+ * the last force evaluation of scf_step into A_out ([n_prog][2*NC] doubles). */
+int scf_last_coeffs(scf_handle* h, double* A_out);
+
+/* Synchronises the handle's stream, writes the accumulated device status bits
+ * (SCF_STATUS_*) to *status (may be NULL) and clears them.  Returns
+ * SCF_ERR_DEVICE_STATUS if any bit was set, SCF_ERR_CUDA if the stream
+ * reported an error, else SCF_OK. */
+int scf_status(scf_handle* h, int* status);
+
+/* Number of kernel launches one call of each entry point makes (for
+ * accounting): which = 0 coeffs, 1 forces, 2 one step. */
+int scf_launches_per_call(const scf_handle* h, int which);
+
+/* Releases the workspace (synchronising the stream first) and the handle.
+ * NULL is accepted. */
+int scf_free(scf_handle* h);
+
+/* Static description of a return code. */
+const char* scf_strerror(int code);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SCF_GB300_H */

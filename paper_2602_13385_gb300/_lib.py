@@ -1,0 +1,165 @@
+"""ctypes binding of the C ABI in include/scf.h (argument marshalling only).
+
+Every function here has the name of the C entry point it calls and does no
+arithmetic of its own: it turns tensors into device pointers, checks that
+they are CUDA tensors of the expected dtype, and raises :class:`ScfError` on
+a non-zero return code.  The library is built in-tree (``build.py``); when it
+cannot be loaded the import fails loudly — there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+from . import build as _build
+
+SCF_FP64 = 0
+SCF_MIXED = 1
+SCF_HOST_HERNQUIST = 1
+SCF_HOST_NFW = 2
+SCF_HOST_MN = 3
+SCF_MAX_LMAX = 12
+SCF_MAX_NMAX = 40
+SCF_MAX_HOST_COMPONENTS = 8
+SCF_STATUS_NONFINITE_POS = 1
+SCF_STATUS_NONFINITE_ACC = 2
+
+ERRORS = {
+    -1: "SCF_ERR_INVALID_ARG",
+    -2: "SCF_ERR_NULL_POINTER",
+    -3: "SCF_ERR_MISALIGNED",
+    -4: "SCF_ERR_UNSUPPORTED",
+    -5: "SCF_ERR_CUDA",
+    -6: "SCF_ERR_OUT_OF_MEMORY",
+    -7: "SCF_ERR_DEVICE_STATUS",
+}
+
+# every symbol include/scf.h declares
+EXPORTS = ["scf_init", "scf_coeffs", "scf_forces", "scf_step", "scf_last_coeffs", "scf_status",
+           "scf_launches_per_call", "scf_free", "scf_strerror"]
+
+
+class ScfError(RuntimeError):
+    def __init__(self, code: int, where: str):
+        self.code = code
+        super().__init__(f"{where}: {ERRORS.get(code, code)} ({strerror(code)})")
+
+
+class scf_host_component(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int), ("M", ctypes.c_double), ("a", ctypes.c_double), ("b", ctypes.c_double)]
+
+
+class scf_config(ctypes.Structure):
+    _fields_ = [("nmax", ctypes.c_int), ("lmax", ctypes.c_int), ("alpha", ctypes.c_double), ("b", ctypes.c_double),
+                ("G", ctypes.c_double), ("dt", ctypes.c_double), ("precision", ctypes.c_int),
+                ("n_host", ctypes.c_int), ("host", scf_host_component * SCF_MAX_HOST_COMPONENTS)]
+
+
+_lib = None
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load(build: bool = True) -> ctypes.CDLL:
+    """Loads libscf.so (building it first when missing or stale)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if build:
+        _build.build()
+    if not os.path.exists(_build.LIB):
+        raise ImportError(f"libscf.so missing at {_build.LIB}; run paper_2602_13385_gb300.build")
+    lib = ctypes.CDLL(_build.LIB)
+    vp, i, i64p, dp = ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_double)
+    lib.scf_init.argtypes = [ctypes.POINTER(scf_config), i, i64p, dp, vp, ctypes.POINTER(vp)]
+    lib.scf_coeffs.argtypes = [vp, vp, vp, vp]
+    lib.scf_forces.argtypes = [vp, vp, vp, vp, vp]
+    lib.scf_step.argtypes = [vp, vp, vp, vp, vp, i]
+    lib.scf_last_coeffs.argtypes = [vp, vp]
+    lib.scf_status.argtypes = [vp, ctypes.POINTER(i)]
+    lib.scf_launches_per_call.argtypes = [vp, i]
+    lib.scf_free.argtypes = [vp]
+    lib.scf_strerror.argtypes = [i]
+    lib.scf_strerror.restype = ctypes.c_char_p
+    for name in EXPORTS:
+        if name != "scf_strerror":
+            getattr(lib, name).restype = ctypes.c_int
+    _lib = lib
+    return lib
+
+
+def _ptr(x, dtype=None):
+    """Device pointer of a CUDA tensor (or an int / None passed through)."""
+    if x is None:
+        return None
+    if isinstance(x, int):
+        return ctypes.c_void_p(x)
+    import torch
+    if not isinstance(x, torch.Tensor):
+        raise TypeError(f"expected a torch tensor, got {type(x)}")
+    if not x.is_cuda:
+        raise ValueError("the SCF library takes CUDA tensors only (no CPU path)")
+    if not x.is_contiguous():
+        raise ValueError("tensor must be contiguous")
+    if dtype is not None and x.dtype != dtype:
+        raise TypeError(f"expected {dtype}, got {x.dtype}")
+    return ctypes.c_void_p(x.data_ptr())
+
+
+def _check(rc: int, where: str):
+    if rc != 0:
+        raise ScfError(rc, where)
+
+
+def strerror(code: int) -> str:
+    return load(build=False).scf_strerror(int(code)).decode() if _lib is not None else str(code)
+
+
+def scf_init(cfg: scf_config, offsets, b_per_prog=None, stream: int = 0):
+    lib = load()
+    n_prog = len(offsets) - 1
+    off = (ctypes.c_int64 * len(offsets))(*[int(o) for o in offsets])
+    bp = None if b_per_prog is None else (ctypes.c_double * n_prog)(*[float(b) for b in b_per_prog])
+    h = ctypes.c_void_p()
+    _check(lib.scf_init(ctypes.byref(cfg), n_prog, off, bp, ctypes.c_void_p(stream), ctypes.byref(h)), "scf_init")
+    return h
+
+
+def scf_coeffs(h, pos, mask, A_out):
+    import torch
+    _check(load().scf_coeffs(h, _ptr(pos), _ptr(mask, torch.uint8), _ptr(A_out, torch.float64)), "scf_coeffs")
+
+
+def scf_forces(h, pos, A, com, acc):
+    import torch
+    _check(load().scf_forces(h, _ptr(pos), _ptr(A, torch.float64), _ptr(com, torch.float64), _ptr(acc)),
+           "scf_forces")
+
+
+def scf_step(h, pos, vel, acc, com, nsteps: int):
+    import torch
+    _check(load().scf_step(h, _ptr(pos), _ptr(vel), _ptr(acc), _ptr(com, torch.float64), int(nsteps)), "scf_step")
+
+
+def scf_last_coeffs(h, A_out):
+    import torch
+    _check(load().scf_last_coeffs(h, _ptr(A_out, torch.float64)), "scf_last_coeffs")
+
+
+def scf_status(h):
+    """Returns (return code, status bits); does not raise on device status."""
+    st = ctypes.c_int(0)
+    rc = load().scf_status(h, ctypes.byref(st))
+    if rc not in (0, -7):
+        raise ScfError(rc, "scf_status")
+    return rc, st.value
+
+
+def scf_launches_per_call(h, which: int) -> int:
+    return int(load().scf_launches_per_call(h, int(which)))
+
+
+def scf_free(h):
+    _check(load().scf_free(h), "scf_free")

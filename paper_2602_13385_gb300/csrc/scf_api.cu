@@ -1,0 +1,380 @@
+// C ABI of the SCF gravity step (declared in include/scf.h): argument
+// validation, workspace ownership, block maps and kernel launches.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <mutex>
+#include <new>
+#include <vector>
+
+#include "../../include/scf.h"
+#include "scf_device.cuh"
+#include "scf_internal.h"
+
+struct scf_handle {
+  scf_config cfg;
+  int n_prog = 0;
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  int nlm = 0, nc = 0;
+  int64_t n_total = 0;
+  // kernel 1 / 2
+  ScfLaunchInfo k1{};
+  int k1_blocks = 0;
+  int* d_blk1_prog = nullptr;
+  int64_t* d_blk1_begin = nullptr;
+  int64_t* d_blk1_end = nullptr;
+  int* d_prog_blk_off = nullptr;
+  // kernel 3
+  ScfLaunchInfo k3{};
+  int k3_blocks = 0;
+  int* d_blk3_prog = nullptr;
+  int64_t* d_blk3_begin = nullptr;
+  int64_t* d_blk3_end = nullptr;
+  // buffers
+  double* d_partials = nullptr;
+  double* d_A = nullptr;
+  double* d_norm = nullptr;
+  double* d_b = nullptr;
+  unsigned* d_status = nullptr;
+  void* d_base = nullptr;
+  ScfHostParams host{};
+};
+
+namespace {
+
+std::mutex g_const_mutex;
+std::vector<bool> g_const_ready;
+
+int upload_tables_once(int device) {
+  std::lock_guard<std::mutex> lock(g_const_mutex);
+  if ((int)g_const_ready.size() <= device) g_const_ready.resize(device + 1, false);
+  if (g_const_ready[device]) return SCF_OK;
+  ScfConst* t = new (std::nothrow) ScfConst;
+  if (!t) return SCF_ERR_OUT_OF_MEMORY;
+  scf_make_const(t);
+  cudaError_t e1 = scf_upload_const_coeffs(t);
+  cudaError_t e2 = scf_upload_const_forces(t);
+  delete t;
+  if (e1 != cudaSuccess || e2 != cudaSuccess) return SCF_ERR_CUDA;
+  g_const_ready[device] = true;
+  return SCF_OK;
+}
+
+bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
+
+size_t round_up(size_t x) { return (x + 255) & ~size_t(255); }
+
+int check_config(const scf_config* c) {
+  if (c->nmax < 0 || c->lmax < 0 || c->n_host < 0 || c->n_host > SCF_MAX_HOST_COMPONENTS) return SCF_ERR_INVALID_ARG;
+  if (c->nmax > SCF_MAX_NMAX || c->lmax > SCF_MAX_LMAX) return SCF_ERR_UNSUPPORTED;
+  if (c->alpha != 1.0) return SCF_ERR_UNSUPPORTED;
+  if (c->precision != SCF_FP64 && c->precision != SCF_MIXED) return SCF_ERR_INVALID_ARG;
+  if (!std::isfinite(c->G) || !std::isfinite(c->dt) || !std::isfinite(c->b)) return SCF_ERR_INVALID_ARG;
+  for (int i = 0; i < c->n_host; ++i) {
+    const scf_host_component& h = c->host[i];
+    if (h.kind != SCF_HOST_HERNQUIST && h.kind != SCF_HOST_NFW && h.kind != SCF_HOST_MN) return SCF_ERR_INVALID_ARG;
+    if (!(h.a > 0.0) || !std::isfinite(h.M) || !std::isfinite(h.a)) return SCF_ERR_INVALID_ARG;
+    if (h.kind == SCF_HOST_MN && !(h.b >= 0.0 && std::isfinite(h.b))) return SCF_ERR_INVALID_ARG;
+  }
+  return SCF_OK;
+}
+
+int cuda_fail(cudaError_t e) { return e == cudaSuccess ? SCF_OK : SCF_ERR_CUDA; }
+
+K1Args k1_args(scf_handle* h, void* pos, void* vel, const void* acc, const uint8_t* mask, int mode) {
+  K1Args a{};
+  a.pos = pos;
+  a.vel = vel;
+  a.acc = acc;
+  a.mask = mask;
+  a.partials = h->d_partials;
+  a.blk_prog = h->d_blk1_prog;
+  a.blk_begin = h->d_blk1_begin;
+  a.blk_end = h->d_blk1_end;
+  a.b_prog = h->d_b;
+  a.nmax = h->cfg.nmax;
+  a.lmax = h->cfg.lmax;
+  a.nc = h->nc;
+  a.nlm = h->nlm;
+  a.mode = mode;
+  a.dt = h->cfg.dt;
+  a.status = h->d_status;
+  return a;
+}
+
+K2Args k2_args(scf_handle* h, double* A_out, double* com, int mode) {
+  K2Args a{};
+  a.partials = h->d_partials;
+  a.prog_blk_off = h->d_prog_blk_off;
+  a.norm = h->d_norm;
+  a.A_out = A_out;
+  a.nc = h->nc;
+  a.n_prog = h->n_prog;
+  a.mode = mode;
+  a.dt = h->cfg.dt;
+  a.com = com;
+  a.host = h->host;
+  return a;
+}
+
+K3Args k3_args(scf_handle* h, const void* pos, void* vel, void* acc, const double* A, const double* com, int mode) {
+  K3Args a{};
+  a.pos = pos;
+  a.vel = vel;
+  a.acc = acc;
+  a.A = A;
+  a.com = com;
+  a.blk_prog = h->d_blk3_prog;
+  a.blk_begin = h->d_blk3_begin;
+  a.blk_end = h->d_blk3_end;
+  a.b_prog = h->d_b;
+  a.nmax = h->cfg.nmax;
+  a.lmax = h->cfg.lmax;
+  a.nc = h->nc;
+  a.nlm = h->nlm;
+  a.mode = mode;
+  a.G = h->cfg.G;
+  a.dt = h->cfg.dt;
+  a.host = h->host;
+  a.status = h->d_status;
+  return a;
+}
+
+int run_coeffs(scf_handle* h, void* pos, void* vel, const void* acc, const uint8_t* mask, double* A_out, double* com,
+               int mode) {
+  if (h->k1_blocks > 0) {
+    K1Args a = k1_args(h, pos, vel, acc, mask, mode);
+    if (scf_k1_launch(h->cfg.precision, a, h->k1_blocks, h->k1, h->stream) != cudaSuccess) return SCF_ERR_CUDA;
+  }
+  K2Args b = k2_args(h, A_out, com, mode);
+  return cuda_fail(scf_k2_launch(b, h->stream));
+}
+
+int run_forces(scf_handle* h, const void* pos, void* vel, void* acc, const double* A, const double* com, int mode) {
+  if (h->k3_blocks == 0) return SCF_OK;
+  K3Args a = k3_args(h, pos, vel, acc, A, com, mode);
+  return cuda_fail(scf_k3_launch(h->cfg.precision, a, h->k3_blocks, h->k3, h->stream));
+}
+
+}  // namespace
+
+extern "C" {
+
+int scf_init(const scf_config* cfg, int n_prog, const int64_t* offsets, const double* b_per_prog, void* stream,
+             scf_handle** out) {
+  if (!cfg || !offsets || !out) return SCF_ERR_NULL_POINTER;
+  int rc = check_config(cfg);
+  if (rc != SCF_OK) return rc;
+  if (n_prog < 1 || offsets[0] != 0) return SCF_ERR_INVALID_ARG;
+  for (int p = 0; p < n_prog; ++p)
+    if (offsets[p + 1] < offsets[p]) return SCF_ERR_INVALID_ARG;
+  std::vector<double> bs(n_prog);
+  for (int p = 0; p < n_prog; ++p) {
+    bs[p] = b_per_prog ? b_per_prog[p] : cfg->b;
+    if (!(bs[p] > 0.0) || !std::isfinite(bs[p])) return SCF_ERR_INVALID_ARG;
+  }
+
+  scf_handle* h = new (std::nothrow) scf_handle;
+  if (!h) return SCF_ERR_OUT_OF_MEMORY;
+  h->cfg = *cfg;
+  h->n_prog = n_prog;
+  h->stream = reinterpret_cast<cudaStream_t>(stream);
+  h->nlm = (cfg->lmax + 1) * (cfg->lmax + 2) / 2;
+  h->nc = (cfg->nmax + 1) * h->nlm;
+  h->n_total = offsets[n_prog];
+  h->host.n = cfg->n_host;
+  for (int i = 0; i < cfg->n_host; ++i) {
+    h->host.kind[i] = cfg->host[i].kind;
+    h->host.GM[i] = cfg->G * cfg->host[i].M;
+    h->host.a[i] = cfg->host[i].a;
+    h->host.b[i] = cfg->host[i].b;
+  }
+  auto fail = [&](int code) {
+    if (h->d_base) cudaFree(h->d_base);
+    delete h;
+    return code;
+  };
+  if (cudaGetDevice(&h->device) != cudaSuccess) return fail(SCF_ERR_CUDA);
+  rc = upload_tables_once(h->device);
+  if (rc != SCF_OK) return fail(rc);
+  int n_sm = 0;
+  if (cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, h->device) != cudaSuccess) return fail(SCF_ERR_CUDA);
+
+  // kernel 1 block map: contiguous particle ranges of whole tiles, one
+  // progenitor per block, about one wave of resident blocks in total.
+  int bps1 = 0, bps3 = 0;
+  if (scf_k1_prepare(cfg->precision, cfg->lmax, cfg->nmax, &h->k1, &bps1) != cudaSuccess) return fail(SCF_ERR_CUDA);
+  if (scf_k3_prepare(cfg->precision, cfg->lmax, cfg->nmax, &h->k3, &bps3) != cudaSuccess) return fail(SCF_ERR_CUDA);
+  if (bps1 < 1 || bps3 < 1) return fail(SCF_ERR_UNSUPPORTED);
+  const int64_t tp = h->k1.threads;
+  int64_t total_tiles = 0;
+  std::vector<int64_t> tiles(n_prog);
+  for (int p = 0; p < n_prog; ++p) {
+    tiles[p] = (offsets[p + 1] - offsets[p] + tp - 1) / tp;
+    total_tiles += tiles[p];
+  }
+  const int64_t slots = (int64_t)n_sm * bps1;
+  const int64_t tpb = std::max<int64_t>(1, (total_tiles + slots - 1) / slots);
+  std::vector<int> blk1_prog, prog_blk_off(n_prog + 1, 0);
+  std::vector<int64_t> blk1_begin, blk1_end;
+  for (int p = 0; p < n_prog; ++p) {
+    prog_blk_off[p] = (int)blk1_prog.size();
+    for (int64_t t0 = 0; t0 < tiles[p]; t0 += tpb) {
+      blk1_prog.push_back(p);
+      blk1_begin.push_back(offsets[p] + t0 * tp);
+      blk1_end.push_back(std::min(offsets[p] + (t0 + tpb) * tp, offsets[p + 1]));
+    }
+  }
+  prog_blk_off[n_prog] = (int)blk1_prog.size();
+  h->k1_blocks = (int)blk1_prog.size();
+  // kernel 3 block map: one thread per particle, one progenitor per block.
+  const int64_t tb = h->k3.threads;
+  std::vector<int> blk3_prog;
+  std::vector<int64_t> blk3_begin, blk3_end;
+  for (int p = 0; p < n_prog; ++p)
+    for (int64_t k = offsets[p]; k < offsets[p + 1]; k += tb) {
+      blk3_prog.push_back(p);
+      blk3_begin.push_back(k);
+      blk3_end.push_back(std::min(k + tb, offsets[p + 1]));
+    }
+  h->k3_blocks = (int)blk3_prog.size();
+
+  // one allocation for the whole workspace
+  const size_t nb1 = std::max<size_t>(1, blk1_prog.size()), nb3 = std::max<size_t>(1, blk3_prog.size());
+  size_t off = 0;
+  auto take = [&](size_t bytes) {
+    size_t o = off;
+    off += round_up(bytes);
+    return o;
+  };
+  const size_t o_part = take(sizeof(double) * 2 * (size_t)h->nc * nb1);
+  const size_t o_A = take(sizeof(double) * 2 * (size_t)h->nc * n_prog);
+  const size_t o_norm = take(sizeof(double) * 2 * (size_t)h->nc);
+  const size_t o_b = take(sizeof(double) * n_prog);
+  const size_t o_b1p = take(sizeof(int) * nb1);
+  const size_t o_b1b = take(sizeof(int64_t) * nb1);
+  const size_t o_b1e = take(sizeof(int64_t) * nb1);
+  const size_t o_pbo = take(sizeof(int) * (n_prog + 1));
+  const size_t o_b3p = take(sizeof(int) * nb3);
+  const size_t o_b3b = take(sizeof(int64_t) * nb3);
+  const size_t o_b3e = take(sizeof(int64_t) * nb3);
+  const size_t o_st = take(sizeof(unsigned) * 4);
+  if (cudaMalloc(&h->d_base, off) != cudaSuccess) {
+    cudaGetLastError();
+    return fail(SCF_ERR_OUT_OF_MEMORY);
+  }
+  char* base = static_cast<char*>(h->d_base);
+  h->d_partials = reinterpret_cast<double*>(base + o_part);
+  h->d_A = reinterpret_cast<double*>(base + o_A);
+  h->d_norm = reinterpret_cast<double*>(base + o_norm);
+  h->d_b = reinterpret_cast<double*>(base + o_b);
+  h->d_blk1_prog = reinterpret_cast<int*>(base + o_b1p);
+  h->d_blk1_begin = reinterpret_cast<int64_t*>(base + o_b1b);
+  h->d_blk1_end = reinterpret_cast<int64_t*>(base + o_b1e);
+  h->d_prog_blk_off = reinterpret_cast<int*>(base + o_pbo);
+  h->d_blk3_prog = reinterpret_cast<int*>(base + o_b3p);
+  h->d_blk3_begin = reinterpret_cast<int64_t*>(base + o_b3b);
+  h->d_blk3_end = reinterpret_cast<int64_t*>(base + o_b3e);
+  h->d_status = reinterpret_cast<unsigned*>(base + o_st);
+
+  std::vector<double> norm(2 * (size_t)h->nc);
+  scf_make_norm(cfg->nmax, cfg->lmax, norm.data());
+  bool ok = true;
+  auto put = [&](void* dst, const void* src, size_t bytes) {
+    if (bytes && cudaMemcpy(dst, src, bytes, cudaMemcpyHostToDevice) != cudaSuccess) ok = false;
+  };
+  put(h->d_norm, norm.data(), sizeof(double) * norm.size());
+  put(h->d_b, bs.data(), sizeof(double) * n_prog);
+  put(h->d_blk1_prog, blk1_prog.data(), sizeof(int) * blk1_prog.size());
+  put(h->d_blk1_begin, blk1_begin.data(), sizeof(int64_t) * blk1_begin.size());
+  put(h->d_blk1_end, blk1_end.data(), sizeof(int64_t) * blk1_end.size());
+  put(h->d_prog_blk_off, prog_blk_off.data(), sizeof(int) * prog_blk_off.size());
+  put(h->d_blk3_prog, blk3_prog.data(), sizeof(int) * blk3_prog.size());
+  put(h->d_blk3_begin, blk3_begin.data(), sizeof(int64_t) * blk3_begin.size());
+  put(h->d_blk3_end, blk3_end.data(), sizeof(int64_t) * blk3_end.size());
+  if (cudaMemset(h->d_status, 0, sizeof(unsigned) * 4) != cudaSuccess) ok = false;
+  if (cudaMemset(h->d_A, 0, sizeof(double) * 2 * (size_t)h->nc * n_prog) != cudaSuccess) ok = false;
+  if (!ok) return fail(SCF_ERR_CUDA);
+  *out = h;
+  return SCF_OK;
+}
+
+int scf_coeffs(scf_handle* h, const void* pos, const uint8_t* mask, double* A_out) {
+  if (!h || !A_out || (!pos && h->n_total > 0)) return SCF_ERR_NULL_POINTER;
+  if (!aligned16(pos)) return SCF_ERR_MISALIGNED;
+  return run_coeffs(h, const_cast<void*>(pos), nullptr, nullptr, mask, A_out, nullptr, SCF_MODE_COEFFS);
+}
+
+int scf_forces(scf_handle* h, const void* pos, const double* A, const double* com, void* acc) {
+  if (!h || !A || ((!pos || !acc) && h->n_total > 0)) return SCF_ERR_NULL_POINTER;
+  if (h->host.n > 0 && !com) return SCF_ERR_NULL_POINTER;
+  if (!aligned16(pos) || !aligned16(acc)) return SCF_ERR_MISALIGNED;
+  return run_forces(h, pos, nullptr, acc, A, com, SCF_MODE_COEFFS);
+}
+
+int scf_step(scf_handle* h, void* pos, void* vel, void* acc, double* com, int nsteps) {
+  if (!h) return SCF_ERR_NULL_POINTER;
+  if (nsteps < 0) return SCF_ERR_INVALID_ARG;
+  if ((!pos || !vel || !acc) && h->n_total > 0) return SCF_ERR_NULL_POINTER;
+  if (h->host.n > 0 && !com) return SCF_ERR_NULL_POINTER;
+  if (!aligned16(pos) || !aligned16(vel) || !aligned16(acc)) return SCF_ERR_MISALIGNED;
+  for (int st = 0; st < nsteps; ++st) {
+    int rc = run_coeffs(h, pos, vel, acc, nullptr, h->d_A, com, SCF_MODE_STEP);
+    if (rc != SCF_OK) return rc;
+    rc = run_forces(h, pos, vel, acc, h->d_A, com, SCF_MODE_STEP);
+    if (rc != SCF_OK) return rc;
+  }
+  return SCF_OK;
+}
+
+int scf_last_coeffs(scf_handle* h, double* A_out) {
+  if (!h || !A_out) return SCF_ERR_NULL_POINTER;
+  return cuda_fail(cudaMemcpyAsync(A_out, h->d_A, sizeof(double) * 2 * (size_t)h->nc * h->n_prog,
+                                   cudaMemcpyDeviceToDevice, h->stream));
+}
+
+int scf_status(scf_handle* h, int* status) {
+  if (!h) return SCF_ERR_NULL_POINTER;
+  unsigned word = 0;
+  if (cudaMemcpyAsync(&word, h->d_status, sizeof(unsigned), cudaMemcpyDeviceToHost, h->stream) != cudaSuccess)
+    return SCF_ERR_CUDA;
+  if (cudaStreamSynchronize(h->stream) != cudaSuccess) return SCF_ERR_CUDA;
+  if (cudaMemsetAsync(h->d_status, 0, sizeof(unsigned), h->stream) != cudaSuccess) return SCF_ERR_CUDA;
+  if (status) *status = (int)word;
+  return word ? SCF_ERR_DEVICE_STATUS : SCF_OK;
+}
+
+int scf_launches_per_call(const scf_handle* h, int which) {
+  if (!h) return SCF_ERR_NULL_POINTER;
+  const int k1 = h->k1_blocks > 0 ? 1 : 0, k3 = h->k3_blocks > 0 ? 1 : 0;
+  if (which == 0) return k1 + 1;
+  if (which == 1) return k3;
+  if (which == 2) return k1 + 1 + k3;
+  return SCF_ERR_INVALID_ARG;
+}
+
+int scf_free(scf_handle* h) {
+  if (!h) return SCF_OK;
+  int rc = SCF_OK;
+  if (cudaStreamSynchronize(h->stream) != cudaSuccess) rc = SCF_ERR_CUDA;
+  if (h->d_base && cudaFree(h->d_base) != cudaSuccess) rc = SCF_ERR_CUDA;
+  delete h;
+  return rc;
+}
+
+const char* scf_strerror(int code) {
+  switch (code) {
+    case SCF_OK: return "ok";
+    case SCF_ERR_INVALID_ARG: return "invalid argument (size, count, offset or option out of range)";
+    case SCF_ERR_NULL_POINTER: return "required pointer is NULL";
+    case SCF_ERR_MISALIGNED: return "particle pointer is not 16-byte aligned";
+    case SCF_ERR_UNSUPPORTED: return "unsupported configuration (alpha != 1 or nmax/lmax above the compiled limits)";
+    case SCF_ERR_CUDA: return "CUDA runtime error";
+    case SCF_ERR_OUT_OF_MEMORY: return "workspace allocation failed";
+    case SCF_ERR_DEVICE_STATUS: return "device reported non-finite particle data";
+    default: return "unknown error code";
+  }
+}
+
+}  // extern "C"

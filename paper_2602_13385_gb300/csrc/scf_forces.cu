@@ -1,0 +1,267 @@
+// Kernel 3: acceleration of the expansion (Eq. 1a, a = -grad psi) at every
+// particle, plus the tidal acceleration of the accelerating, non-rotating
+// cluster frame (Sec. 2.1), and in step mode the closing half kick.
+//
+// One thread per particle.  The block's progenitor coefficients are turned
+// into F_nlm = -G {S,T}_nlm / (b N_lm) and staged in shared memory; every
+// thread then runs, for each l, the Gegenbauer recurrences for alpha_l and
+// alpha_l + 1 in n and accumulates, for m = 0..l,
+//   Z0 = sum_n F_nlm C_n^alpha(xi),  Z1 = sum_n F_nlm C_{n-1}^{alpha+1}(xi)
+// (cosine and sine parts), from which
+//   G_lm   = s^l q^(2l+1) Z0                               (potential),
+//   G_lm/r = (1/b) s^(l-1) q^(2l+1) Z0                     (l >= 1),
+//   G'_lm  = (1/b) [(l s^(l-1) q^(2l+1) - (2l+1) s^l q^(2l+2)) Z0 + 4 alpha s^l q^(2l+3) Z1]
+// and the Cartesian gradient is assembled with the identities listed in
+// scf_device.cuh.  No division by r or sin(theta) appears, so particles at
+// the origin or on the z axis need no special case (at r = 0 the l = 0 term,
+// whose direction is undefined there, contributes nothing).
+#include "scf_device.cuh"
+#include "scf_internal.h"
+
+static __constant__ ScfConst c_tab;
+
+cudaError_t scf_upload_const_forces(const ScfConst* t) { return cudaMemcpyToSymbol(c_tab, t, sizeof(ScfConst)); }
+
+namespace {
+
+template <typename T> struct Vec4;
+template <> struct Vec4<double> { using type = ScfD4; };
+template <> struct Vec4<float> { using type = float4; };
+
+template <typename T> __device__ __forceinline__ T tgA(int l, int n) { return sizeof(T) == 8 ? (T)c_tab.gA[l][n] : (T)c_tab.gAf[l][n]; }
+template <typename T> __device__ __forceinline__ T tgB(int l, int n) { return sizeof(T) == 8 ? (T)c_tab.gB[l][n] : (T)c_tab.gBf[l][n]; }
+template <typename T> __device__ __forceinline__ T thA(int l, int n) { return sizeof(T) == 8 ? (T)c_tab.hA[l][n] : (T)c_tab.hAf[l][n]; }
+template <typename T> __device__ __forceinline__ T thB(int l, int n) { return sizeof(T) == 8 ? (T)c_tab.hB[l][n] : (T)c_tab.hBf[l][n]; }
+template <typename T> __device__ __forceinline__ T tla(int i) { return sizeof(T) == 8 ? (T)c_tab.la[i] : (T)c_tab.laf[i]; }
+template <typename T> __device__ __forceinline__ T tlb(int i) { return sizeof(T) == 8 ? (T)c_tab.lb[i] : (T)c_tab.lbf[i]; }
+template <typename T> __device__ __forceinline__ T tlk(int i) { return sizeof(T) == 8 ? (T)c_tab.lk[i] : (T)c_tab.lkf[i]; }
+template <typename T> __device__ __forceinline__ T tlsub(int l) { return sizeof(T) == 8 ? (T)c_tab.lsub[l] : (T)c_tab.lsubf[l]; }
+template <typename T> __device__ __forceinline__ T tldiag(int l) { return sizeof(T) == 8 ? (T)c_tab.ldiag[l] : (T)c_tab.ldiagf[l]; }
+
+constexpr int K3_TB = 128;
+
+template <typename T, int LMAX>
+__global__ void __launch_bounds__(K3_TB) k3_forces(K3Args a) {
+  using V4 = typename Vec4<T>::type;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* F = reinterpret_cast<T*>(smem_raw);  // [2*NC] force coefficients of this block's progenitor
+  __shared__ double s_R[3], s_aR[3];
+  const int tid = threadIdx.x;
+  const int prog = a.blk_prog[blockIdx.x];
+  const double b = a.b_prog[prog];
+  {
+    const double* A = a.A + (size_t)prog * 2 * a.nc;
+    const double f = -a.G / b;
+    for (int i = tid; i < 2 * a.nc; i += K3_TB) {
+      const int j = i < a.nc ? i : i - a.nc;
+      const int lm = j % a.nlm;
+      F[i] = (T)(f * A[i] * c_tab.inv_nlm[lm]);
+    }
+  }
+  const bool has_host = a.host.n > 0 && a.com != nullptr;
+  if (tid == 0) {
+    s_R[0] = s_R[1] = s_R[2] = 0.0;
+    s_aR[0] = s_aR[1] = s_aR[2] = 0.0;
+    if (has_host) {
+      const double* c = a.com + 6 * prog;
+      s_R[0] = c[0];
+      s_R[1] = c[1];
+      s_R[2] = c[2];
+      scf_host_accel(a.host, c[0], c[1], c[2], s_aR[0], s_aR[1], s_aR[2]);
+    }
+  }
+  __syncthreads();
+
+  const int64_t k = a.blk_begin[blockIdx.x] + tid;
+  if (k >= a.blk_end[blockIdx.x]) return;
+  const V4 p = reinterpret_cast<const V4*>(a.pos)[k];
+  const bool finite = scf_finite3(p.x, p.y, p.z);
+  if (!finite) atomicOr(a.status, 1u);
+  const T x = finite ? p.x : (T)0, y = finite ? p.y : (T)0, z = finite ? p.z : (T)0;
+
+  const T binv = (T)(1.0 / b);
+  const T r = sqrt(x * x + y * y + z * z);
+  const T rinv = r > (T)0 ? (T)1 / r : (T)0;
+  const T u = x * rinv, v = y * rinv, c = z * rinv;
+  const T s = r * binv;
+  const T q = (T)1 / ((T)1 + s);
+  const T xi = (T)1 - (T)2 * q;
+  const T sq2 = s * q * q;
+
+  T Wc[LMAX + 1], Ws[LMAX + 1];
+  Wc[0] = 1;
+  Ws[0] = 0;
+#pragma unroll
+  for (int m = 1; m <= LMAX; ++m) {
+    Wc[m] = Wc[m - 1] * u - Ws[m - 1] * v;
+    Ws[m] = Wc[m - 1] * v + Ws[m - 1] * u;
+  }
+  T P[LMAX + 1], P1[LMAX + 1], P2[LMAX + 1];
+  T An = 0, Ax = 0, Ay = 0, Az = 0, pot = 0;
+  T slq = q;        // s^l q^(2l+1)
+  T sl1q = q * q * q;  // s^(l-1) q^(2l+1) for l >= 1 (set at l = 1)
+  const int NN = a.nmax + 1;
+  const T* Fc = F;
+  const T* Fs = F + a.nc;
+
+#pragma unroll
+  for (int l = 0; l <= LMAX; ++l) {
+    if (l > a.lmax) break;
+#pragma unroll
+    for (int m = 0; m + 2 <= l; ++m) P[m] = tla<T>(scf_lm(l, m)) * c * P1[m] - tlb<T>(scf_lm(l, m)) * P2[m];
+    if (l >= 1) P[l - 1] = tlsub<T>(l) * c * P1[l - 1];
+    P[l] = tldiag<T>(l);
+
+    T Z0c[LMAX + 1], Z0s[LMAX + 1], Z1c[LMAX + 1], Z1s[LMAX + 1];
+    const int lm0 = scf_lm(l, 0);
+#pragma unroll
+    for (int m = 0; m <= l; ++m) {
+      Z0c[m] = Fc[lm0 + m];  // n = 0: C_0 = 1
+      Z0s[m] = Fs[lm0 + m];
+      Z1c[m] = 0;
+      Z1s[m] = 0;
+    }
+    {
+      T cm1 = 0, c0 = 1;  // C^alpha_{n-2}, C^alpha_{n-1}
+      T dm1 = 0, d0 = 1;  // C^{alpha+1}_{n-2}, C^{alpha+1}_{n-1}
+      for (int n = 1; n < NN; ++n) {
+        const T cn = tgA<T>(l, n) * xi * c0 - tgB<T>(l, n) * cm1;
+        const int o = n * a.nlm + lm0;
+#pragma unroll
+        for (int m = 0; m <= l; ++m) {
+          const T fc = Fc[o + m], fs = Fs[o + m];
+          Z0c[m] += fc * cn;
+          Z0s[m] += fs * cn;
+          Z1c[m] += fc * d0;
+          Z1s[m] += fs * d0;
+        }
+        const T dn = thA<T>(l, n) * xi * d0 - thB<T>(l, n) * dm1;
+        cm1 = c0;
+        c0 = cn;
+        dm1 = d0;
+        d0 = dn;
+      }
+    }
+    // radial prefactors
+    const T al4 = (T)(4.0 * (2.0 * l + 1.5));
+    const T k1 = (l >= 1) ? binv * sl1q : (T)0;                                  // G/r per Z0
+    const T k2a = binv * ((l >= 1 ? (T)l * sl1q : (T)0) - (T)(2 * l + 1) * slq * q);  // G' per Z0
+    const T k2b = binv * al4 * slq * q * q;                                       // G' per Z1
+#pragma unroll
+    for (int m = 0; m <= l; ++m) {
+      const T g0c = slq * Z0c[m], g0s = slq * Z0s[m];
+      const T g1c = k1 * Z0c[m], g1s = k1 * Z0s[m];
+      const T g2c = k2a * Z0c[m] + k2b * Z1c[m], g2s = k2a * Z0s[m] + k2b * Z1s[m];
+      const T E = g1c * Wc[m] + g1s * Ws[m];
+      const T D = g2c * Wc[m] + g2s * Ws[m];
+      const T Pl = P[m];
+      const T Pd = (m < l) ? -tlk<T>(scf_lm(l, m)) * P[m + 1] : (T)0;
+      pot += Pl * (g0c * Wc[m] + g0s * Ws[m]);
+      An += Pl * D - (c * Pd + (T)m * Pl) * E;
+      Az += Pd * E;
+      if (m >= 1) {
+        Ax += (T)m * Pl * (g1c * Wc[m - 1] + g1s * Ws[m - 1]);
+        Ay -= (T)m * Pl * (g1c * Ws[m - 1] - g1s * Wc[m - 1]);
+      }
+    }
+    slq *= sq2;
+    if (l >= 1) sl1q *= sq2;
+#pragma unroll
+    for (int m = 0; m <= l; ++m) {
+      P2[m] = P1[m];
+      P1[m] = P[m];
+    }
+  }
+  // a = -grad psi (G and the sign of the basis are folded into F)
+  double gx = -(double)(An * u + Ax);
+  double gy = -(double)(An * v + Ay);
+  double gz = -(double)(An * c + Az);
+  if (has_host) {
+    // a_host(R + x) - a_host(R), double precision
+    double hx, hy, hz;
+    scf_host_accel(a.host, s_R[0] + (double)p.x, s_R[1] + (double)p.y, s_R[2] + (double)p.z, hx, hy, hz);
+    gx += hx - s_aR[0];
+    gy += hy - s_aR[1];
+    gz += hz - s_aR[2];
+  }
+  if (!(isfinite(gx) && isfinite(gy) && isfinite(gz))) atomicOr(a.status, 2u);
+  V4 out;
+  out.x = (T)gx;
+  out.y = (T)gy;
+  out.z = (T)gz;
+  out.w = pot;
+  reinterpret_cast<V4*>(a.acc)[k] = out;
+  if (a.mode == SCF_MODE_STEP) {
+    V4* vel4 = reinterpret_cast<V4*>(a.vel);
+    V4 vv = vel4[k];
+    const T h = (T)(0.5 * a.dt);
+    vv.x += h * out.x;
+    vv.y += h * out.y;
+    vv.z += h * out.z;
+    vel4[k] = vv;
+  }
+}
+
+template <typename T>
+struct K3 {
+  template <int LMAX>
+  struct At {
+    static void* fn() { return (void*)k3_forces<T, LMAX>; }
+    static void launch(const K3Args& a, int blocks, size_t smem, cudaStream_t s) {
+      k3_forces<T, LMAX><<<blocks, K3_TB, smem, s>>>(a);
+    }
+  };
+};
+template <int L> using K3D = K3<double>::At<L>;
+template <int L> using K3F = K3<float>::At<L>;
+
+int lmax_bucket(int lmax) {
+  if (lmax <= 2) return 2;
+  if (lmax <= 4) return 4;
+  if (lmax <= 6) return 6;
+  if (lmax <= 8) return 8;
+  if (lmax <= 10) return 10;
+  return 12;
+}
+
+template <template <int> class K, typename Fn>
+auto dispatch_lmax(int lmax, Fn&& f) {
+  switch (lmax_bucket(lmax)) {
+    case 2: return f(K<2>());
+    case 4: return f(K<4>());
+    case 6: return f(K<6>());
+    case 8: return f(K<8>());
+    case 10: return f(K<10>());
+    default: return f(K<12>());
+  }
+}
+
+template <template <int> class K>
+cudaError_t prepare_t(int lmax, int nmax, size_t elem, ScfLaunchInfo* info, int* blocks_per_sm) {
+  const int nlm = (lmax + 1) * (lmax + 2) / 2, nc = (nmax + 1) * nlm;
+  return dispatch_lmax<K>(lmax, [&](auto k) -> cudaError_t {
+    using KK = decltype(k);
+    info->threads = K3_TB;
+    info->smem = elem * 2 * (size_t)nc;
+    cudaError_t e = cudaFuncSetAttribute(KK::fn(), cudaFuncAttributeMaxDynamicSharedMemorySize, (int)info->smem);
+    if (e != cudaSuccess) return e;
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, KK::fn(), info->threads, info->smem);
+  });
+}
+
+}  // namespace
+
+cudaError_t scf_k3_prepare(int precision, int lmax, int nmax, ScfLaunchInfo* info, int* blocks_per_sm) {
+  if (precision == 1) return prepare_t<K3F>(lmax, nmax, sizeof(float), info, blocks_per_sm);
+  return prepare_t<K3D>(lmax, nmax, sizeof(double), info, blocks_per_sm);
+}
+
+cudaError_t scf_k3_launch(int precision, const K3Args& a, int blocks, const ScfLaunchInfo& info, cudaStream_t s) {
+  auto go = [&](auto k) -> int {
+    decltype(k)::launch(a, blocks, info.smem, s);
+    return 0;
+  };
+  if (precision == 1) dispatch_lmax<K3F>(a.lmax, go);
+  else dispatch_lmax<K3D>(a.lmax, go);
+  return cudaGetLastError();
+}

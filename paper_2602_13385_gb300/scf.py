@@ -1,0 +1,135 @@
+"""User-facing API of the SCF gravity step on one GPU.
+
+PyTorch supplies device memory and the stream; every step of the method runs
+in the CUDA kernels of ``libscf.so`` through the C ABI (``_lib``).
+
+Layouts (see include/scf.h): positions ``(N, 4)`` = (x, y, z, m), velocities
+``(N, 4)``, accelerations ``(N, 4)`` = (ax, ay, az, psi_SCF), float64 for
+``precision="fp64"`` and float32 for ``precision="mixed"``; coefficients
+``(n_prog, 2*NC)`` float64 = [S | T]; centre ``(n_prog, 6)`` float64 = (R, V).
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass, field
+
+import torch
+
+from . import _lib
+
+HOST_HERNQUIST = _lib.SCF_HOST_HERNQUIST
+HOST_NFW = _lib.SCF_HOST_NFW
+HOST_MN = _lib.SCF_HOST_MN
+
+
+def n_lm(lmax: int) -> int:
+    return (lmax + 1) * (lmax + 2) // 2
+
+
+def n_coef(nmax: int, lmax: int) -> int:
+    """Entries of one half (S or T) of a coefficient vector."""
+    return (nmax + 1) * n_lm(lmax)
+
+
+@dataclass
+class Config:
+    nmax: int
+    lmax: int
+    b: float
+    G: float = 1.0
+    dt: float = 0.01
+    precision: str = "fp64"           # "fp64" or "mixed"
+    host: list = field(default_factory=list)   # [(kind, M, a, b)], kinds HOST_*
+    alpha: float = 1.0
+
+    def to_c(self) -> _lib.scf_config:
+        c = _lib.scf_config()
+        c.nmax, c.lmax, c.alpha, c.b, c.G, c.dt = self.nmax, self.lmax, self.alpha, self.b, self.G, self.dt
+        c.precision = {"fp64": _lib.SCF_FP64, "mixed": _lib.SCF_MIXED}[self.precision]
+        if len(self.host) > _lib.SCF_MAX_HOST_COMPONENTS:
+            raise ValueError("too many host components")
+        c.n_host = len(self.host)
+        for i, (kind, M, a, b) in enumerate(self.host):
+            c.host[i].kind, c.host[i].M, c.host[i].a, c.host[i].b = int(kind), float(M), float(a), float(b)
+        return c
+
+    @property
+    def dtype(self) -> torch.dtype:
+        return torch.float64 if self.precision == "fp64" else torch.float32
+
+
+class SCF:
+    """A handle on the GPU: one or more progenitors sharing a configuration.
+
+    ``offsets``: progenitor boundaries (length n_prog+1, offsets[0] = 0), or
+    ``n`` for a single cluster.  ``b_per_prog`` overrides ``config.b``."""
+
+    def __init__(self, config: Config, n: int | None = None, offsets=None, b_per_prog=None,
+                 device: torch.device | int | None = None, stream: torch.cuda.Stream | None = None):
+        if offsets is None:
+            if n is None:
+                raise ValueError("give n or offsets")
+            offsets = [0, int(n)]
+        self.config = config
+        self.offsets = [int(o) for o in offsets]
+        self.n_prog = len(self.offsets) - 1
+        self.n = self.offsets[-1]
+        self.nc = n_coef(config.nmax, config.lmax)
+        self.device = torch.device("cuda", torch.cuda.current_device() if device is None else
+                                   torch.device(device).index or 0)
+        with torch.cuda.device(self.device):
+            self.stream = stream or torch.cuda.current_stream(self.device)
+            self._h = _lib.scf_init(config.to_c(), self.offsets, b_per_prog, self.stream.cuda_stream)
+
+    # -- allocation helpers (PyTorch owns the memory)
+    def new_coeffs(self) -> torch.Tensor:
+        return torch.zeros((self.n_prog, 2 * self.nc), dtype=torch.float64, device=self.device)
+
+    def new_particles(self) -> torch.Tensor:
+        return torch.zeros((self.n, 4), dtype=self.config.dtype, device=self.device)
+
+    def _check_particles(self, t: torch.Tensor, name: str):
+        if t.shape != (self.n, 4):
+            raise ValueError(f"{name} must have shape ({self.n}, 4), got {tuple(t.shape)}")
+        if t.dtype != self.config.dtype:
+            raise TypeError(f"{name} must be {self.config.dtype}, got {t.dtype}")
+
+    # -- the entry points
+    def coeffs(self, pos: torch.Tensor, mask: torch.Tensor | None = None, out: torch.Tensor | None = None):
+        self._check_particles(pos, "pos")
+        out = self.new_coeffs() if out is None else out
+        _lib.scf_coeffs(self._h, pos, mask, out)
+        return out
+
+    def forces(self, pos: torch.Tensor, A: torch.Tensor, com: torch.Tensor | None = None,
+               out: torch.Tensor | None = None):
+        self._check_particles(pos, "pos")
+        out = self.new_particles() if out is None else out
+        _lib.scf_forces(self._h, pos, A, com, out)
+        return out
+
+    def step(self, pos, vel, acc, com=None, nsteps: int = 1):
+        for t, nm in ((pos, "pos"), (vel, "vel"), (acc, "acc")):
+            self._check_particles(t, nm)
+        _lib.scf_step(self._h, pos, vel, acc, com, nsteps)
+
+    def last_coeffs(self, out: torch.Tensor | None = None):
+        out = self.new_coeffs() if out is None else out
+        _lib.scf_last_coeffs(self._h, out)
+        return out
+
+    def status(self):
+        return _lib.scf_status(self._h)
+
+    def launches_per_call(self, which: str) -> int:
+        return _lib.scf_launches_per_call(self._h, {"coeffs": 0, "forces": 1, "step": 2}[which])
+
+    def close(self):
+        if getattr(self, "_h", None) is not None:
+            _lib.scf_free(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

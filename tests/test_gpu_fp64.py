@@ -1,0 +1,195 @@
+"""Parity of the FP64 CUDA path with the FP64 oracle (relative error <= 1e-10).
+
+Error metrics (the reading of the 1e-10 target):
+* coefficients: max |A_gpu - A_oracle| / max |A_oracle| over all (n, l, m);
+* accelerations: per particle |a_gpu - a_oracle| / max(|a_oracle|, 1e-6 median |a|).
+"""
+import numpy as np
+import pytest
+
+import oracle
+import workloads
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-10
+
+
+@pytest.fixture(scope="module")
+def scf():
+    if not torch.cuda.is_available():
+        pytest.skip("needs a GPU")
+    import paper_2602_13385_gb300 as pkg
+    return pkg
+
+
+def coef_err(A, B):
+    return float(np.max(np.abs(np.asarray(A) - np.asarray(B))) / np.max(np.abs(B)))
+
+
+def acc_err(a, b):
+    na = np.linalg.norm(b[:, :3], axis=1)
+    floor = max(1e-6 * np.median(na), 1e-300)
+    return np.linalg.norm(a[:, :3] - b[:, :3], axis=1) / np.maximum(na, floor)
+
+
+def dev(x):
+    return torch.tensor(np.ascontiguousarray(x), device="cuda")
+
+
+def make(scf, nmax, lmax, b, n=None, offsets=None, host=(), dt=0.01, b_per_prog=None, precision="fp64"):
+    cfg = scf.Config(nmax=nmax, lmax=lmax, b=b, dt=dt, host=list(host), precision=precision)
+    return scf.SCF(cfg, n=n, offsets=offsets, b_per_prog=b_per_prog)
+
+
+def check_status(sim):
+    rc, st = sim.status()
+    assert rc == 0 and st == 0, (rc, st)
+
+
+@pytest.mark.parametrize("n,nmax,lmax", [(5000, 10, 6), (1, 4, 3), (129, 6, 2), (3001, 20, 8), (777, 12, 12),
+                                         (500, 0, 0), (400, 3, 11)])
+def test_coefficients_match_oracle(scf, n, nmax, lmax):
+    pos, _ = workloads.plummer(n, seed=100 + n)
+    b = 0.3
+    sim = make(scf, nmax, lmax, b, n=n)
+    A = sim.coeffs(dev(pos)).cpu().numpy()[0]
+    check_status(sim)
+    A_ref = oracle.coeffs(pos, nmax, lmax, b)
+    assert coef_err(A, A_ref) < TOL
+
+
+def test_coefficients_with_mask_and_special_points(scf):
+    pos, _ = workloads.plummer(2000, seed=5)
+    pos[0, :3] = 0.0                 # origin
+    pos[1, :3] = [0.0, 0.0, 0.4]     # north pole
+    pos[2, :3] = [0.0, 0.0, -1.2]    # south pole
+    pos[3, :3] = [1e-9, -2e-9, 0.7]  # next to the axis
+    mask = (np.arange(2000) % 5 != 2).astype(np.uint8)
+    sim = make(scf, 8, 6, 0.35, n=2000)
+    A = sim.coeffs(dev(pos), mask=dev(mask)).cpu().numpy()[0]
+    check_status(sim)
+    assert coef_err(A, oracle.coeffs(pos, 8, 6, 0.35, mask=mask)) < TOL
+
+
+def test_coefficients_are_deterministic(scf):
+    pos, _ = workloads.plummer(20000, seed=6)
+    sim = make(scf, 20, 8, 0.3, n=20000)
+    p = dev(pos)
+    A1 = sim.coeffs(p).cpu().numpy()
+    A2 = sim.coeffs(p).cpu().numpy()
+    assert np.array_equal(A1, A2)
+
+
+@pytest.mark.parametrize("nmax,lmax", [(10, 6), (20, 8), (20, 10)])
+def test_forces_match_oracle(scf, nmax, lmax):
+    pos, _ = workloads.plummer(3000, seed=7)
+    tgt, _ = workloads.plummer(1500, seed=8)
+    tgt[0, :3] = 0.0
+    tgt[1, :3] = [0.0, 0.0, 0.5]
+    tgt[2, :3] = [0.0, 0.0, -0.25]
+    tgt[3, :3] = [40.0, -30.0, 10.0]   # far outside
+    b = 0.3
+    A_ref = oracle.coeffs(pos, nmax, lmax, b)
+    sim = make(scf, nmax, lmax, b, n=len(tgt))
+    acc = sim.forces(dev(tgt), dev(A_ref[None])).cpu().numpy()
+    check_status(sim)
+    ref = oracle.forces(tgt, A_ref, nmax, lmax, b)
+    assert acc_err(acc, ref).max() < TOL
+    assert np.max(np.abs(acc[:, 3] - ref[:, 3]) / np.abs(ref[:, 3])) < TOL
+
+
+def test_forces_with_host_tidal_term(scf):
+    wl = workloads.king_circular(n=3000, seed=9, nsteps=1)
+    A_ref = oracle.coeffs(wl.pos, wl.nmax, wl.lmax, wl.b)
+    host = oracle.host_struct(wl.host)
+    ref = oracle.forces(wl.pos, A_ref, wl.nmax, wl.lmax, wl.b, com=wl.com, host=host)
+    sim = make(scf, wl.nmax, wl.lmax, wl.b, n=wl.n, host=wl.host)
+    acc = sim.forces(dev(wl.pos), dev(A_ref[None]), com=dev(wl.com[None])).cpu().numpy()
+    check_status(sim)
+    assert acc_err(acc, ref).max() < TOL
+    # the tidal part on its own (small next to the cluster's field) also matches
+    tid_ref = ref[:, :3] - oracle.field(wl.pos, A_ref, wl.nmax, wl.lmax, wl.b)[:, :3]
+    sim0 = make(scf, wl.nmax, wl.lmax, wl.b, n=wl.n)
+    tid = acc[:, :3] - sim0.forces(dev(wl.pos), dev(A_ref[None])).cpu().numpy()[:, :3]
+    rel = np.linalg.norm(tid - tid_ref, axis=1) / np.linalg.norm(tid_ref, axis=1)
+    assert np.median(rel) < 1e-8
+
+
+@pytest.mark.parametrize("with_host", [False, True])
+def test_leapfrog_steps_match_oracle(scf, with_host):
+    if with_host:
+        wl = workloads.king_circular(n=2048, seed=11, nsteps=10)
+    else:
+        wl = workloads.plummer_isolated(n=2048, seed=12)
+    host = oracle.host_struct(wl.host) if with_host else None
+    com = wl.com if with_host else np.zeros(6)
+    A0 = oracle.coeffs(wl.pos, wl.nmax, wl.lmax, wl.b)
+    acc0 = oracle.forces(wl.pos, A0, wl.nmax, wl.lmax, wl.b, com=com, host=host)
+    sim = make(scf, wl.nmax, wl.lmax, wl.b, n=wl.n, host=wl.host if with_host else (), dt=wl.dt)
+    p, v, a, c = dev(wl.pos), dev(wl.vel), dev(acc0), dev(com[None])
+    rp, rv, ra, rc = wl.pos, wl.vel, acc0, com
+    for _ in range(10):                       # step by step (N-body is chaotic: <= 10 steps)
+        sim.step(p, v, a, com=c if with_host else None, nsteps=1)
+        rp, rv, ra, rc, rA = oracle.step(rp, rv, ra, wl.nmax, wl.lmax, wl.b, wl.dt, 1, com=rc, host=host)
+        assert np.max(np.abs(p.cpu().numpy()[:, :3] - rp[:, :3])) < TOL * np.max(np.abs(rp[:, :3]))
+        assert np.max(np.abs(v.cpu().numpy()[:, :3] - rv[:, :3])) < TOL * np.max(np.abs(rv[:, :3]))
+        assert acc_err(a.cpu().numpy(), ra).max() < TOL
+        assert coef_err(sim.last_coeffs().cpu().numpy()[0], rA) < TOL
+        if with_host:
+            assert np.max(np.abs(c.cpu().numpy()[0] - rc)) < 1e-12 * np.max(np.abs(rc))
+    check_status(sim)
+
+
+def test_batched_progenitors_match_independent_oracles(scf):
+    sizes = [700, 0, 1, 2048, 131]
+    pos_l, b_l = [], []
+    for i, n in enumerate(sizes):
+        p, _ = workloads.plummer(max(n, 1), seed=20 + i)
+        pos_l.append(p[:n])
+        b_l.append(0.25 + 0.05 * i)
+    offsets = np.concatenate([[0], np.cumsum(sizes)])
+    pos = np.concatenate(pos_l)
+    nmax, lmax = 8, 5
+    sim = make(scf, nmax, lmax, 0.3, offsets=offsets, b_per_prog=b_l)
+    A = sim.coeffs(dev(pos)).cpu().numpy()
+    acc = sim.forces(dev(pos), dev(A)).cpu().numpy()
+    check_status(sim)
+    for i, n in enumerate(sizes):
+        A_ref = oracle.coeffs(pos_l[i], nmax, lmax, b_l[i])
+        if n == 0:
+            assert np.all(A[i] == 0)
+            continue
+        assert coef_err(A[i], A_ref) < TOL
+        ref = oracle.forces(pos_l[i], A[i], nmax, lmax, b_l[i])
+        assert acc_err(acc[offsets[i]:offsets[i + 1]], ref).max() < TOL
+
+
+def test_nonfinite_position_is_flagged_not_trapped(scf):
+    pos, _ = workloads.plummer(300, seed=30)
+    pos[17, 0] = np.nan
+    sim = make(scf, 4, 3, 0.3, n=300)
+    A = sim.coeffs(dev(pos)).cpu().numpy()[0]
+    rc, st = sim.status()
+    assert rc == -7 and st & 1
+    good = np.delete(pos, 17, axis=0)
+    assert coef_err(A, oracle.coeffs(good, 4, 3, 0.3)) < TOL
+    assert sim.status() == (0, 0)      # cleared
+
+
+def test_full_size_king_circular_coefficients_and_sampled_forces(scf):
+    """The bench workload (N = 1e5, nmax = 20, lmax = 8, host) in the launch
+    configuration the benchmark uses: full coefficient vector against the
+    oracle and accelerations at 400 sampled particles."""
+    wl = workloads.king_circular()
+    sim = make(scf, wl.nmax, wl.lmax, wl.b, n=wl.n, host=wl.host, dt=wl.dt)
+    p = dev(wl.pos)
+    A = sim.coeffs(p).cpu().numpy()[0]
+    A_ref = oracle.coeffs(wl.pos, wl.nmax, wl.lmax, wl.b)
+    assert coef_err(A, A_ref) < TOL
+    acc = sim.forces(p, dev(A_ref[None]), com=dev(wl.com[None])).cpu().numpy()
+    check_status(sim)
+    idx = np.random.default_rng(0).choice(wl.n, 400, replace=False)
+    ref = oracle.forces(wl.pos[idx], A_ref, wl.nmax, wl.lmax, wl.b, com=wl.com, host=oracle.host_struct(wl.host))
+    assert acc_err(acc[idx], ref).max() < TOL
