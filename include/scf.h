@@ -166,6 +166,18 @@ int scf_status(scf_handle* h, int* status);
  * accounting): which = 0 coeffs, 1 forces, 2 one step. */
 int scf_launches_per_call(const scf_handle* h, int which);
 
+/* Kernel timing with CUDA events recorded on the handle's stream around each
+ * launch (the tracing of the three kernels).  scf_profile(h, 1) creates a
+ * pool of event pairs (up to 4096 launches) and starts recording;
+ * scf_profile(h, 0) stops recording and releases the pool.  Call it outside
+ * the sections being timed: it creates CUDA events.
+ * scf_profile_read synchronises the stream, writes the summed device time
+ * in milliseconds and the number of recorded launches of kernel 1, 2 and 3
+ * into ms[3] and launches[3] (host pointers; either may be NULL) and clears
+ * the record.  Errors: SCF_ERR_NULL_POINTER, SCF_ERR_CUDA. */
+int scf_profile(scf_handle* h, int enable);
+int scf_profile_read(scf_handle* h, double* ms, int64_t* launches);
+
 /* Releases the workspace (synchronising the stream first) and the handle.
  * NULL is accepted. */
 int scf_free(scf_handle* h);

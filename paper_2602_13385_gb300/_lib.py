@@ -36,7 +36,7 @@ ERRORS = {
 
 # every symbol include/scf.h declares
 EXPORTS = ["scf_init", "scf_coeffs", "scf_forces", "scf_step", "scf_last_coeffs", "scf_status",
-           "scf_launches_per_call", "scf_free", "scf_strerror"]
+           "scf_launches_per_call", "scf_profile", "scf_profile_read", "scf_free", "scf_strerror"]
 
 
 class ScfError(RuntimeError):
@@ -80,6 +80,8 @@ def load(build: bool = True) -> ctypes.CDLL:
     lib.scf_last_coeffs.argtypes = [vp, vp]
     lib.scf_status.argtypes = [vp, ctypes.POINTER(i)]
     lib.scf_launches_per_call.argtypes = [vp, i]
+    lib.scf_profile.argtypes = [vp, i]
+    lib.scf_profile_read.argtypes = [vp, dp, ctypes.POINTER(ctypes.c_int64)]
     lib.scf_free.argtypes = [vp]
     lib.scf_strerror.argtypes = [i]
     lib.scf_strerror.restype = ctypes.c_char_p
@@ -159,6 +161,18 @@ def scf_status(h):
 
 def scf_launches_per_call(h, which: int) -> int:
     return int(load().scf_launches_per_call(h, int(which)))
+
+
+def scf_profile(h, enable: bool):
+    _check(load().scf_profile(h, 1 if enable else 0), "scf_profile")
+
+
+def scf_profile_read(h):
+    """Returns ([ms_k1, ms_k2, ms_k3], [launches_k1, launches_k2, launches_k3])."""
+    ms = (ctypes.c_double * 3)()
+    n = (ctypes.c_int64 * 3)()
+    _check(load().scf_profile_read(h, ms, n), "scf_profile_read")
+    return list(ms), list(n)
 
 
 def scf_free(h):

@@ -39,6 +39,11 @@ struct scf_handle {
   unsigned* d_status = nullptr;
   void* d_base = nullptr;
   ScfHostParams host{};
+  // launch timing (scf_profile)
+  bool prof_on = false;
+  std::vector<cudaEvent_t> prof_ev;   // pairs (start, stop)
+  std::vector<int> prof_kind;         // kernel index of each recorded pair
+  int prof_used = 0;                  // pairs recorded
 };
 
 namespace {
@@ -81,6 +86,29 @@ int check_config(const scf_config* c) {
 }
 
 int cuda_fail(cudaError_t e) { return e == cudaSuccess ? SCF_OK : SCF_ERR_CUDA; }
+
+constexpr int kProfPairs = 4096;
+
+// Runs `launch` and, when profiling, brackets it with a recorded event pair.
+template <typename F>
+cudaError_t timed(scf_handle* h, int kind, F&& launch) {
+  const bool rec = h->prof_on && h->prof_used < kProfPairs;
+  if (rec) cudaEventRecord(h->prof_ev[2 * h->prof_used], h->stream);
+  cudaError_t e = launch();
+  if (rec) {
+    cudaEventRecord(h->prof_ev[2 * h->prof_used + 1], h->stream);
+    h->prof_kind[h->prof_used++] = kind;
+  }
+  return e;
+}
+
+void prof_release(scf_handle* h) {
+  for (cudaEvent_t e : h->prof_ev) cudaEventDestroy(e);
+  h->prof_ev.clear();
+  h->prof_kind.clear();
+  h->prof_used = 0;
+  h->prof_on = false;
+}
 
 K1Args k1_args(scf_handle* h, void* pos, void* vel, const void* acc, const uint8_t* mask, int mode) {
   K1Args a{};
@@ -145,16 +173,18 @@ int run_coeffs(scf_handle* h, void* pos, void* vel, const void* acc, const uint8
                int mode) {
   if (h->k1_blocks > 0) {
     K1Args a = k1_args(h, pos, vel, acc, mask, mode);
-    if (scf_k1_launch(h->cfg.precision, a, h->k1_blocks, h->k1, h->stream) != cudaSuccess) return SCF_ERR_CUDA;
+    if (timed(h, 0, [&] { return scf_k1_launch(h->cfg.precision, a, h->k1_blocks, h->k1, h->stream); }) !=
+        cudaSuccess)
+      return SCF_ERR_CUDA;
   }
   K2Args b = k2_args(h, A_out, com, mode);
-  return cuda_fail(scf_k2_launch(b, h->stream));
+  return cuda_fail(timed(h, 1, [&] { return scf_k2_launch(b, h->stream); }));
 }
 
 int run_forces(scf_handle* h, const void* pos, void* vel, void* acc, const double* A, const double* com, int mode) {
   if (h->k3_blocks == 0) return SCF_OK;
   K3Args a = k3_args(h, pos, vel, acc, A, com, mode);
-  return cuda_fail(scf_k3_launch(h->cfg.precision, a, h->k3_blocks, h->k3, h->stream));
+  return cuda_fail(timed(h, 2, [&] { return scf_k3_launch(h->cfg.precision, a, h->k3_blocks, h->k3, h->stream); }));
 }
 
 }  // namespace
@@ -354,10 +384,51 @@ int scf_launches_per_call(const scf_handle* h, int which) {
   return SCF_ERR_INVALID_ARG;
 }
 
+int scf_profile(scf_handle* h, int enable) {
+  if (!h) return SCF_ERR_NULL_POINTER;
+  if (!enable) {
+    if (cudaStreamSynchronize(h->stream) != cudaSuccess) return SCF_ERR_CUDA;
+    prof_release(h);
+    return SCF_OK;
+  }
+  if (h->prof_ev.empty()) {
+    h->prof_ev.resize(2 * kProfPairs, nullptr);
+    h->prof_kind.resize(kProfPairs, 0);
+    for (auto& e : h->prof_ev)
+      if (cudaEventCreate(&e) != cudaSuccess) {
+        prof_release(h);
+        return SCF_ERR_CUDA;
+      }
+  }
+  h->prof_used = 0;
+  h->prof_on = true;
+  return SCF_OK;
+}
+
+int scf_profile_read(scf_handle* h, double* ms, int64_t* launches) {
+  if (!h) return SCF_ERR_NULL_POINTER;
+  double t[3] = {0, 0, 0};
+  int64_t n[3] = {0, 0, 0};
+  if (cudaStreamSynchronize(h->stream) != cudaSuccess) return SCF_ERR_CUDA;
+  for (int i = 0; i < h->prof_used; ++i) {
+    float e = 0.f;
+    if (cudaEventElapsedTime(&e, h->prof_ev[2 * i], h->prof_ev[2 * i + 1]) != cudaSuccess) return SCF_ERR_CUDA;
+    t[h->prof_kind[i]] += e;
+    n[h->prof_kind[i]] += 1;
+  }
+  h->prof_used = 0;
+  for (int k = 0; k < 3; ++k) {
+    if (ms) ms[k] = t[k];
+    if (launches) launches[k] = n[k];
+  }
+  return SCF_OK;
+}
+
 int scf_free(scf_handle* h) {
   if (!h) return SCF_OK;
   int rc = SCF_OK;
   if (cudaStreamSynchronize(h->stream) != cudaSuccess) rc = SCF_ERR_CUDA;
+  prof_release(h);
   if (h->d_base && cudaFree(h->d_base) != cudaSuccess) rc = SCF_ERR_CUDA;
   delete h;
   return rc;

@@ -123,6 +123,13 @@ class SCF:
     def launches_per_call(self, which: str) -> int:
         return _lib.scf_launches_per_call(self._h, {"coeffs": 0, "forces": 1, "step": 2}[which])
 
+    def profile(self, enable: bool = True):
+        _lib.scf_profile(self._h, enable)
+
+    def profile_read(self):
+        """([ms of kernel 1, 2, 3], [launch counts]) since the last read."""
+        return _lib.scf_profile_read(self._h)
+
     def close(self):
         if getattr(self, "_h", None) is not None:
             _lib.scf_free(self._h)
