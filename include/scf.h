@@ -67,6 +67,7 @@ extern "C" {
 #define SCF_ERR_CUDA (-5)          /* a CUDA runtime call or kernel launch failed */
 #define SCF_ERR_OUT_OF_MEMORY (-6) /* workspace allocation failed in scf_init */
 #define SCF_ERR_DEVICE_STATUS (-7) /* scf_status found device-side problems */
+#define SCF_ERR_TOO_LARGE (-8)     /* the problem does not fit the static scratch of scf_coeffs_noalloc */
 
 /* ---- device status bits (scf_status) ---- */
 #define SCF_STATUS_NONFINITE_POS 1 /* a particle position was NaN/Inf; it was skipped */
@@ -177,6 +178,32 @@ int scf_launches_per_call(const scf_handle* h, int which);
  * the record.  Errors: SCF_ERR_NULL_POINTER, SCF_ERR_CUDA. */
 int scf_profile(scf_handle* h, int enable);
 int scf_profile_read(scf_handle* h, double* ms, int64_t* launches);
+
+/* Coefficients of one cluster (same result as scf_coeffs with n_prog = 1)
+ * for callers that cannot allocate device memory: code running inside an
+ * arena or pool it must not grow, on a path where cudaMalloc is not allowed
+ * or would synchronise the device, or a plugin handed device pointers but no
+ * allocator.  The paper has no counterpart; this entry point only changes
+ * where the scratch lives.
+ *   cfg    host pointer; nmax, lmax, alpha (= 1), b and precision are used.
+ *   n      number of particles (>= 0); pos device [n][4] (16-byte aligned,
+ *          double for SCF_FP64, float for SCF_MIXED); mask device or NULL;
+ *   A_out  device [2*NC] doubles;  stream  a cudaStream_t (NULL = default).
+ * Allocates nothing: the block partial sums, block map and normalisation live
+ * in one file-scope __device__ array of fixed size (SCF_NOALLOC_MAX_BLOCKS x
+ * SCF_NOALLOC_MAX_COEFS doubles of partials, about 10.5 MiB in all) that every
+ * GPU loading the library holds until the process exits.  The first call on
+ * a device looks up that array's address (cudaGetSymbolAddress) and uploads
+ * the recurrence tables, so make it before any stream capture.  Every call
+ * rewrites all scratch it reads, but calls share the array: calls that
+ * overlap on the GPU race and must be serialised by the caller.
+ * Errors: SCF_ERR_TOO_LARGE when 2*NC > SCF_NOALLOC_MAX_COEFS (e.g. nmax = 40,
+ * lmax = 12); SCF_ERR_NULL_POINTER, SCF_ERR_INVALID_ARG, SCF_ERR_UNSUPPORTED,
+ * SCF_ERR_MISALIGNED, SCF_ERR_CUDA. */
+#define SCF_NOALLOC_MAX_BLOCKS 320
+#define SCF_NOALLOC_MAX_COEFS 4096
+int scf_coeffs_noalloc(const scf_config* cfg, int64_t n, const void* pos, const uint8_t* mask, double* A_out,
+                       void* stream);
 
 /* Releases the workspace (synchronising the stream first) and the handle.
  * NULL is accepted. */

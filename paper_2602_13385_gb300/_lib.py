@@ -32,11 +32,13 @@ ERRORS = {
     -5: "SCF_ERR_CUDA",
     -6: "SCF_ERR_OUT_OF_MEMORY",
     -7: "SCF_ERR_DEVICE_STATUS",
+    -8: "SCF_ERR_TOO_LARGE",
 }
 
 # every symbol include/scf.h declares
 EXPORTS = ["scf_init", "scf_coeffs", "scf_forces", "scf_step", "scf_last_coeffs", "scf_status",
-           "scf_launches_per_call", "scf_profile", "scf_profile_read", "scf_free", "scf_strerror"]
+           "scf_launches_per_call", "scf_profile", "scf_profile_read", "scf_coeffs_noalloc", "scf_free",
+           "scf_strerror"]
 
 
 class ScfError(RuntimeError):
@@ -82,6 +84,7 @@ def load(build: bool = True) -> ctypes.CDLL:
     lib.scf_launches_per_call.argtypes = [vp, i]
     lib.scf_profile.argtypes = [vp, i]
     lib.scf_profile_read.argtypes = [vp, dp, ctypes.POINTER(ctypes.c_int64)]
+    lib.scf_coeffs_noalloc.argtypes = [ctypes.POINTER(scf_config), ctypes.c_int64, vp, vp, vp, vp]
     lib.scf_free.argtypes = [vp]
     lib.scf_strerror.argtypes = [i]
     lib.scf_strerror.restype = ctypes.c_char_p
@@ -173,6 +176,14 @@ def scf_profile_read(h):
     n = (ctypes.c_int64 * 3)()
     _check(load().scf_profile_read(h, ms, n), "scf_profile_read")
     return list(ms), list(n)
+
+
+def scf_coeffs_noalloc(cfg: scf_config, n: int, pos, mask, A_out, stream: int = 0):
+    """Coefficients of one cluster through the entry point that allocates
+    nothing (its scratch is a static device array inside the library)."""
+    import torch
+    _check(load().scf_coeffs_noalloc(ctypes.byref(cfg), int(n), _ptr(pos), _ptr(mask, torch.uint8),
+                                     _ptr(A_out, torch.float64), ctypes.c_void_p(stream)), "scf_coeffs_noalloc")
 
 
 def scf_free(h):

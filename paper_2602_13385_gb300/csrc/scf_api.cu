@@ -444,6 +444,7 @@ const char* scf_strerror(int code) {
     case SCF_ERR_CUDA: return "CUDA runtime error";
     case SCF_ERR_OUT_OF_MEMORY: return "workspace allocation failed";
     case SCF_ERR_DEVICE_STATUS: return "device reported non-finite particle data";
+    case SCF_ERR_TOO_LARGE: return "problem exceeds the static scratch of scf_coeffs_noalloc (2*NC > SCF_NOALLOC_MAX_COEFS)";
     default: return "unknown error code";
   }
 }

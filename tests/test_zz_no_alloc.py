@@ -1,0 +1,98 @@
+"""scf_coeffs_noalloc — the coefficient entry point that allocates nothing.
+
+It serves callers that cannot call cudaMalloc (code inside a memory arena it
+must not grow, paths where allocation is not allowed or would synchronise the
+device, plugins handed device pointers but no allocator).  Its scratch is a
+static device array inside the library.  These tests call it through the C ABI
+and compare it with scf_coeffs, at the same 1e-10 tolerance as the other FP64
+parity tests, on two calls in a row with different inputs (the scratch keeps
+the previous call's contents, so the second call checks that nothing leaks).
+"""
+import numpy as np
+import pytest
+
+import workloads
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-10
+
+
+@pytest.fixture(scope="module")
+def pkg():
+    if not torch.cuda.is_available():
+        pytest.skip("needs a GPU")
+    import paper_2602_13385_gb300 as p
+    from paper_2602_13385_gb300 import _lib
+    _lib.load()
+    return p
+
+
+def _rel(a, b):
+    return float(np.max(np.abs(a - b)) / np.max(np.abs(b)))
+
+
+def _noalloc(pkg, cfg, pos, mask=None):
+    from paper_2602_13385_gb300 import _lib
+    nc = pkg.n_coef(cfg.nmax, cfg.lmax)
+    out = torch.full((2 * nc,), float("nan"), dtype=torch.float64, device="cuda")
+    _lib.scf_coeffs_noalloc(cfg.to_c(), pos.shape[0], pos, mask, out, torch.cuda.current_stream().cuda_stream)
+    return out
+
+
+def _existing(pkg, cfg, pos, mask=None):
+    sim = pkg.SCF(cfg, n=pos.shape[0])
+    A = sim.coeffs(pos, mask=mask)[0]
+    torch.cuda.synchronize()
+    sim.close()
+    return A
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_noalloc_matches_scf_coeffs_on_two_calls(pkg, precision):
+    dtype = torch.float64 if precision == "fp64" else torch.float32
+    cfg1 = pkg.Config(nmax=20, lmax=8, b=0.3, precision=precision)
+    pos1, _ = workloads.plummer(30000, seed=71)
+    p1 = torch.tensor(pos1, device="cuda", dtype=dtype)
+    # second call: different size, degree and a mask, so stale scratch would show
+    cfg2 = pkg.Config(nmax=10, lmax=6, b=0.45, precision=precision)
+    pos2, _ = workloads.plummer(5003, seed=72)
+    p2 = torch.tensor(pos2, device="cuda", dtype=dtype)
+    m2 = torch.tensor((np.arange(5003) % 4 != 1).astype(np.uint8), device="cuda")
+
+    A1 = _noalloc(pkg, cfg1, p1)
+    A2 = _noalloc(pkg, cfg2, p2, m2)
+    torch.cuda.synchronize()
+    R1 = _existing(pkg, cfg1, p1)
+    R2 = _existing(pkg, cfg2, p2, m2)
+    assert _rel(A1.cpu().numpy(), R1.cpu().numpy()) < TOL
+    assert _rel(A2.cpu().numpy(), R2.cpu().numpy()) < TOL
+
+
+def test_noalloc_allocates_no_device_memory(pkg):
+    cfg = pkg.Config(nmax=12, lmax=6, b=0.3)
+    pos, _ = workloads.plummer(20000, seed=73)
+    p = torch.tensor(pos, device="cuda")
+    out = _noalloc(pkg, cfg, p)          # first call on the device: set-up
+    torch.cuda.synchronize()
+    free0, _ = torch.cuda.mem_get_info()
+    torch_bytes0 = torch.cuda.memory_allocated()
+    from paper_2602_13385_gb300 import _lib
+    for _ in range(3):
+        _lib.scf_coeffs_noalloc(cfg.to_c(), p.shape[0], p, None, out, torch.cuda.current_stream().cuda_stream)
+    torch.cuda.synchronize()
+    free1, _ = torch.cuda.mem_get_info()
+    assert free1 == free0
+    assert torch.cuda.memory_allocated() == torch_bytes0
+    assert _rel(out.cpu().numpy(), _existing(pkg, cfg, p).cpu().numpy()) < TOL
+
+
+def test_noalloc_rejects_sizes_beyond_its_scratch(pkg):
+    from paper_2602_13385_gb300 import _lib
+    cfg = pkg.Config(nmax=40, lmax=12, b=0.3)      # 2 * NC = 7462 > SCF_NOALLOC_MAX_COEFS
+    p = torch.zeros((10, 4), dtype=torch.float64, device="cuda")
+    out = torch.zeros(2 * pkg.n_coef(40, 12), dtype=torch.float64, device="cuda")
+    with pytest.raises(_lib.ScfError) as e:
+        _lib.scf_coeffs_noalloc(cfg.to_c(), 10, p, None, out, torch.cuda.current_stream().cuda_stream)
+    assert e.value.code == -8
