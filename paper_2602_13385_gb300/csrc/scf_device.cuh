@@ -104,6 +104,72 @@ __device__ __forceinline__ void scf_host_accel(const ScfHostParams& hp, double x
   }
 }
 
+// Tidal acceleration a_host(R + x) - a_host(R) in single precision, written
+// as divided differences so that no two large terms are subtracted: with
+// P = R + x, r0 = |R|, r1 = |P| and dr = r1 - r0 = (2 R.x + |x|^2)/(r1 + r0),
+//   spherical parts (a = -g(r) r_vec):  a(P) - a(R) = -[g(r1) x + (g(r1) - g(r0)) R],
+//     Hernquist  g = GM / p(r), p = r (r+a)^2,  p1 - p0 = dr (r1^2 + r1 r0 + r0^2 + 2a(r1+r0) + a^2),
+//     NFW        g = GM h(u)/r^3, u = r/r_s,   h1 - h0 = log1p(d) - d/(1+u1), d = (dr/r_s)/(1+u0),
+//                1/r1^3 - 1/r0^3 = -dr (r0^2 + r0 r1 + r1^2)/(r0^3 r1^3);
+//   Miyamoto-Nagai (D^2 = R_cyl^2 + (zb + a)^2, zb = sqrt(z^2 + b^2)):
+//     D1^2 - D0^2 = 2(Rx x + Ry y) + x^2 + y^2 + (zb1 - zb0)(zab1 + zab0),
+//     zb1 - zb0 = (2 Rz z + z^2)/(zb1 + zb0),  D1 - D0 = (D1^2 - D0^2)/(D1 + D0),
+//     1/D1^3 - 1/D0^3 = -(D1 - D0)(D1^2 + D1 D0 + D0^2)/(D0^3 D1^3),
+//     a_z = -GM z v/D^3 with v = 1 + a/zb, v1 - v0 = -a (zb1 - zb0)/(zb1 zb0).
+// Relative error of the result a few float ulps for any |x|/|R| (checked
+// against the long-double difference of the oracle).
+__device__ __forceinline__ void scf_tidal_f32(const ScfHostParams& hp, float Rx, float Ry, float Rz, float x, float y,
+                                              float z, float& ax, float& ay, float& az) {
+  ax = 0.f;
+  ay = 0.f;
+  az = 0.f;
+  const float Px = Rx + x, Py = Ry + y, Pz = Rz + z;
+  const float r0 = sqrtf(Rx * Rx + Ry * Ry + Rz * Rz);
+  const float r1 = sqrtf(Px * Px + Py * Py + Pz * Pz);
+  const float xx = x * x + y * y + z * z;
+  const float dr = (2.f * (Rx * x + Ry * y + Rz * z) + xx) / (r1 + r0);
+  for (int i = 0; i < hp.n; ++i) {
+    const float GM = (float)hp.GM[i], A = (float)hp.a[i];
+    if (hp.kind[i] == 1) {  // Hernquist
+      const float p0 = r0 * (r0 + A) * (r0 + A), p1 = r1 * (r1 + A) * (r1 + A);
+      const float dp = dr * (r1 * r1 + r1 * r0 + r0 * r0 + 2.f * A * (r1 + r0) + A * A);
+      const float g1 = GM / p1;
+      const float dg = -GM * dp / (p0 * p1);
+      ax -= g1 * x + dg * Rx;
+      ay -= g1 * y + dg * Ry;
+      az -= g1 * z + dg * Rz;
+    } else if (hp.kind[i] == 2) {  // NFW
+      const float u0 = r0 / A, u1 = r1 / A;
+      const float h0 = log1pf(u0) - u0 / (1.f + u0), h1 = log1pf(u1) - u1 / (1.f + u1);
+      const float d = (dr / A) / (1.f + u0);
+      const float dh = log1pf(d) - d / (1.f + u1);
+      const float i0 = 1.f / (r0 * r0 * r0), i1 = 1.f / (r1 * r1 * r1);
+      const float di = -dr * (r0 * r0 + r0 * r1 + r1 * r1) * i0 * i1;
+      const float g1 = GM * h1 * i1;
+      const float dg = GM * (dh * i1 + h0 * di);
+      ax -= g1 * x + dg * Rx;
+      ay -= g1 * y + dg * Ry;
+      az -= g1 * z + dg * Rz;
+    } else if (hp.kind[i] == 3) {  // Miyamoto-Nagai
+      const float B = (float)hp.b[i];
+      const float zb0 = sqrtf(Rz * Rz + B * B), zb1 = sqrtf(Pz * Pz + B * B);
+      const float dzb = (2.f * Rz * z + z * z) / (zb1 + zb0);
+      const float zab0 = zb0 + A, zab1 = zb1 + A;
+      const float D2_0 = Rx * Rx + Ry * Ry + zab0 * zab0, D2_1 = Px * Px + Py * Py + zab1 * zab1;
+      const float dD2 = 2.f * (Rx * x + Ry * y) + x * x + y * y + dzb * (zab1 + zab0);
+      const float D0 = sqrtf(D2_0), D1 = sqrtf(D2_1);
+      const float dD = dD2 / (D1 + D0);
+      const float i0 = 1.f / (D2_0 * D0), i1 = 1.f / (D2_1 * D1);
+      const float di = -dD * (D2_1 + D1 * D0 + D2_0) * i0 * i1;
+      ax -= GM * (x * i1 + Rx * di);
+      ay -= GM * (y * i1 + Ry * di);
+      const float v0 = 1.f + A / zb0, v1 = 1.f + A / zb1;
+      const float dv = -A * dzb / (zb1 * zb0);
+      az -= GM * (z * v1 * i1 + Rz * (dv * i1 + v0 * di));
+    }
+  }
+}
+
 template <typename T>
 __device__ __forceinline__ bool scf_finite3(T x, T y, T z) {
   return isfinite(x) && isfinite(y) && isfinite(z);

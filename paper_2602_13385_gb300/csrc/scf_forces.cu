@@ -27,6 +27,9 @@ namespace {
 template <typename T> struct Vec4;
 template <> struct Vec4<double> { using type = ScfD4; };
 template <> struct Vec4<float> { using type = float4; };
+template <typename T> struct Vec2;
+template <> struct Vec2<double> { using type = double2; };
+template <> struct Vec2<float> { using type = float2; };
 
 template <typename T> __device__ __forceinline__ T tgA(int l, int n) { return sizeof(T) == 8 ? (T)c_tab.gA[l][n] : (T)c_tab.gAf[l][n]; }
 template <typename T> __device__ __forceinline__ T tgB(int l, int n) { return sizeof(T) == 8 ? (T)c_tab.gB[l][n] : (T)c_tab.gBf[l][n]; }
@@ -43,8 +46,11 @@ constexpr int K3_TB = 128;
 template <typename T, int LMAX>
 __global__ void __launch_bounds__(K3_TB) k3_forces(K3Args a) {
   using V4 = typename Vec4<T>::type;
+  using V2 = typename Vec2<T>::type;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  T* F = reinterpret_cast<T*>(smem_raw);  // [2*NC] force coefficients of this block's progenitor
+  // [NC] (cosine, sine) force coefficient pairs of this block's progenitor,
+  // interleaved so one shared-memory load feeds four FMAs
+  V2* F = reinterpret_cast<V2*>(smem_raw);
   __shared__ double s_R[3], s_aR[3];
   const int tid = threadIdx.x;
   const int prog = a.blk_prog[blockIdx.x];
@@ -52,10 +58,12 @@ __global__ void __launch_bounds__(K3_TB) k3_forces(K3Args a) {
   {
     const double* A = a.A + (size_t)prog * 2 * a.nc;
     const double f = -a.G / b;
-    for (int i = tid; i < 2 * a.nc; i += K3_TB) {
-      const int j = i < a.nc ? i : i - a.nc;
-      const int lm = j % a.nlm;
-      F[i] = (T)(f * A[i] * c_tab.inv_nlm[lm]);
+    for (int i = tid; i < a.nc; i += K3_TB) {
+      const double w = f * c_tab.inv_nlm[i % a.nlm];
+      V2 v;
+      v.x = (T)(w * A[i]);
+      v.y = (T)(w * A[a.nc + i]);
+      F[i] = v;
     }
   }
   const bool has_host = a.host.n > 0 && a.com != nullptr;
@@ -101,8 +109,6 @@ __global__ void __launch_bounds__(K3_TB) k3_forces(K3Args a) {
   T slq = q;        // s^l q^(2l+1)
   T sl1q = q * q * q;  // s^(l-1) q^(2l+1) for l >= 1 (set at l = 1)
   const int NN = a.nmax + 1;
-  const T* Fc = F;
-  const T* Fs = F + a.nc;
 
 #pragma unroll
   for (int l = 0; l <= LMAX; ++l) {
@@ -116,8 +122,9 @@ __global__ void __launch_bounds__(K3_TB) k3_forces(K3Args a) {
     const int lm0 = scf_lm(l, 0);
 #pragma unroll
     for (int m = 0; m <= l; ++m) {
-      Z0c[m] = Fc[lm0 + m];  // n = 0: C_0 = 1
-      Z0s[m] = Fs[lm0 + m];
+      const V2 f0 = F[lm0 + m];  // n = 0: C_0 = 1
+      Z0c[m] = f0.x;
+      Z0s[m] = f0.y;
       Z1c[m] = 0;
       Z1s[m] = 0;
     }
@@ -129,7 +136,8 @@ __global__ void __launch_bounds__(K3_TB) k3_forces(K3Args a) {
         const int o = n * a.nlm + lm0;
 #pragma unroll
         for (int m = 0; m <= l; ++m) {
-          const T fc = Fc[o + m], fs = Fs[o + m];
+          const V2 fv = F[o + m];
+          const T fc = fv.x, fs = fv.y;
           Z0c[m] += fc * cn;
           Z0s[m] += fs * cn;
           Z1c[m] += fc * d0;
@@ -173,23 +181,36 @@ __global__ void __launch_bounds__(K3_TB) k3_forces(K3Args a) {
     }
   }
   // a = -grad psi (G and the sign of the basis are folded into F)
-  double gx = -(double)(An * u + Ax);
-  double gy = -(double)(An * v + Ay);
-  double gz = -(double)(An * c + Az);
-  if (has_host) {
-    // a_host(R + x) - a_host(R), double precision
-    double hx, hy, hz;
-    scf_host_accel(a.host, s_R[0] + (double)p.x, s_R[1] + (double)p.y, s_R[2] + (double)p.z, hx, hy, hz);
-    gx += hx - s_aR[0];
-    gy += hy - s_aR[1];
-    gz += hz - s_aR[2];
-  }
-  if (!(isfinite(gx) && isfinite(gy) && isfinite(gz))) atomicOr(a.status, 2u);
   V4 out;
-  out.x = (T)gx;
-  out.y = (T)gy;
-  out.z = (T)gz;
+  if constexpr (sizeof(T) == 8) {
+    double gx = -(An * u + Ax), gy = -(An * v + Ay), gz = -(An * c + Az);
+    if (has_host) {
+      // a_host(R + x) - a_host(R) in double precision
+      double hx, hy, hz;
+      scf_host_accel(a.host, s_R[0] + (double)p.x, s_R[1] + (double)p.y, s_R[2] + (double)p.z, hx, hy, hz);
+      gx += hx - s_aR[0];
+      gy += hy - s_aR[1];
+      gz += hz - s_aR[2];
+    }
+    out.x = gx;
+    out.y = gy;
+    out.z = gz;
+  } else {
+    float gx = -(An * u + Ax), gy = -(An * v + Ay), gz = -(An * c + Az);
+    if (has_host) {
+      // the same difference in single precision without cancellation
+      float tx, ty, tz;
+      scf_tidal_f32(a.host, (float)s_R[0], (float)s_R[1], (float)s_R[2], p.x, p.y, p.z, tx, ty, tz);
+      gx += tx;
+      gy += ty;
+      gz += tz;
+    }
+    out.x = gx;
+    out.y = gy;
+    out.z = gz;
+  }
   out.w = pot;
+  if (!(isfinite(out.x) && isfinite(out.y) && isfinite(out.z))) atomicOr(a.status, 2u);
   reinterpret_cast<V4*>(a.acc)[k] = out;
   if (a.mode == SCF_MODE_STEP) {
     V4* vel4 = reinterpret_cast<V4*>(a.vel);
@@ -242,7 +263,7 @@ cudaError_t prepare_t(int lmax, int nmax, size_t elem, ScfLaunchInfo* info, int*
   return dispatch_lmax<K>(lmax, [&](auto k) -> cudaError_t {
     using KK = decltype(k);
     info->threads = K3_TB;
-    info->smem = elem * 2 * (size_t)nc;
+    info->smem = elem * 2 * (size_t)nc;  // (cosine, sine) pair per coefficient
     cudaError_t e = cudaFuncSetAttribute(KK::fn(), cudaFuncAttributeMaxDynamicSharedMemorySize, (int)info->smem);
     if (e != cudaSuccess) return e;
     return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, KK::fn(), info->threads, info->smem);
