@@ -34,6 +34,8 @@ struct scf_handle {
   // buffers
   double* d_partials = nullptr;
   double* d_A = nullptr;
+  void* d_F = nullptr;          // [n_prog][NC] force-coefficient pairs (float2 or double2)
+  double* d_aR = nullptr;       // [n_prog][4] a_host(R)
   double* d_norm = nullptr;
   double* d_b = nullptr;
   unsigned* d_status = nullptr;
@@ -133,6 +135,12 @@ K1Args k1_args(scf_handle* h, void* pos, void* vel, const void* acc, const uint8
 
 K2Args k2_args(scf_handle* h, double* A_out, double* com, int mode) {
   K2Args a{};
+  a.nlm = h->nlm;
+  a.F_out = h->d_F;
+  a.f32 = h->cfg.precision == SCF_MIXED;
+  a.b_prog = h->d_b;
+  a.G = h->cfg.G;
+  a.aR_out = h->d_aR;
   a.partials = h->d_partials;
   a.prog_blk_off = h->d_prog_blk_off;
   a.norm = h->d_norm;
@@ -146,12 +154,13 @@ K2Args k2_args(scf_handle* h, double* A_out, double* com, int mode) {
   return a;
 }
 
-K3Args k3_args(scf_handle* h, const void* pos, void* vel, void* acc, const double* A, const double* com, int mode) {
+K3Args k3_args(scf_handle* h, const void* pos, void* vel, void* acc, const double* com, int mode) {
   K3Args a{};
   a.pos = pos;
   a.vel = vel;
   a.acc = acc;
-  a.A = A;
+  a.F = h->d_F;
+  a.aR = h->d_aR;
   a.com = com;
   a.blk_prog = h->d_blk3_prog;
   a.blk_begin = h->d_blk3_begin;
@@ -181,9 +190,27 @@ int run_coeffs(scf_handle* h, void* pos, void* vel, const void* acc, const uint8
   return cuda_fail(timed(h, 1, [&] { return scf_k2_launch(b, h->stream); }));
 }
 
-int run_forces(scf_handle* h, const void* pos, void* vel, void* acc, const double* A, const double* com, int mode) {
+// Force coefficients F and a_host(R) from caller-supplied coefficients.
+int run_prep(scf_handle* h, const double* A, const double* com) {
+  PrepArgs p{};
+  p.A = A;
+  p.com = com;
+  p.F_out = h->d_F;
+  p.f32 = h->cfg.precision == SCF_MIXED;
+  p.b_prog = h->d_b;
+  p.G = h->cfg.G;
+  p.aR_out = h->d_aR;
+  p.nc = h->nc;
+  p.nlm = h->nlm;
+  p.n_prog = h->n_prog;
+  p.host = h->host;
+  return cuda_fail(timed(h, 1, [&] { return scf_prep_launch(p, h->stream); }));
+}
+
+// Kernel 3 on the handle's F / a_host(R) (from kernel 2 or run_prep).
+int run_forces(scf_handle* h, const void* pos, void* vel, void* acc, const double* com, int mode) {
   if (h->k3_blocks == 0) return SCF_OK;
-  K3Args a = k3_args(h, pos, vel, acc, A, com, mode);
+  K3Args a = k3_args(h, pos, vel, acc, com, mode);
   return cuda_fail(timed(h, 2, [&] { return scf_k3_launch(h->cfg.precision, a, h->k3_blocks, h->k3, h->stream); }));
 }
 
@@ -237,7 +264,7 @@ int scf_init(const scf_config* cfg, int n_prog, const int64_t* offsets, const do
   if (scf_k1_prepare(cfg->precision, cfg->lmax, cfg->nmax, &h->k1, &bps1) != cudaSuccess) return fail(SCF_ERR_CUDA);
   if (scf_k3_prepare(cfg->precision, cfg->lmax, cfg->nmax, &h->k3, &bps3) != cudaSuccess) return fail(SCF_ERR_CUDA);
   if (bps1 < 1 || bps3 < 1) return fail(SCF_ERR_UNSUPPORTED);
-  const int64_t tp = h->k1.threads;
+  const int64_t tp = h->k1.tile;
   int64_t total_tiles = 0;
   std::vector<int64_t> tiles(n_prog);
   for (int p = 0; p < n_prog; ++p) {
@@ -259,7 +286,7 @@ int scf_init(const scf_config* cfg, int n_prog, const int64_t* offsets, const do
   prog_blk_off[n_prog] = (int)blk1_prog.size();
   h->k1_blocks = (int)blk1_prog.size();
   // kernel 3 block map: one thread per particle, one progenitor per block.
-  const int64_t tb = h->k3.threads;
+  const int64_t tb = h->k3.tile;
   std::vector<int> blk3_prog;
   std::vector<int64_t> blk3_begin, blk3_end;
   for (int p = 0; p < n_prog; ++p)
@@ -280,6 +307,8 @@ int scf_init(const scf_config* cfg, int n_prog, const int64_t* offsets, const do
   };
   const size_t o_part = take(sizeof(double) * 2 * (size_t)h->nc * nb1);
   const size_t o_A = take(sizeof(double) * 2 * (size_t)h->nc * n_prog);
+  const size_t o_F = take(sizeof(double) * 2 * (size_t)h->nc * n_prog);
+  const size_t o_aR = take(sizeof(double) * 4 * (size_t)n_prog);
   const size_t o_norm = take(sizeof(double) * 2 * (size_t)h->nc);
   const size_t o_b = take(sizeof(double) * n_prog);
   const size_t o_b1p = take(sizeof(int) * nb1);
@@ -297,6 +326,8 @@ int scf_init(const scf_config* cfg, int n_prog, const int64_t* offsets, const do
   char* base = static_cast<char*>(h->d_base);
   h->d_partials = reinterpret_cast<double*>(base + o_part);
   h->d_A = reinterpret_cast<double*>(base + o_A);
+  h->d_F = reinterpret_cast<void*>(base + o_F);
+  h->d_aR = reinterpret_cast<double*>(base + o_aR);
   h->d_norm = reinterpret_cast<double*>(base + o_norm);
   h->d_b = reinterpret_cast<double*>(base + o_b);
   h->d_blk1_prog = reinterpret_cast<int*>(base + o_b1p);
@@ -340,7 +371,9 @@ int scf_forces(scf_handle* h, const void* pos, const double* A, const double* co
   if (!h || !A || ((!pos || !acc) && h->n_total > 0)) return SCF_ERR_NULL_POINTER;
   if (h->host.n > 0 && !com) return SCF_ERR_NULL_POINTER;
   if (!aligned16(pos) || !aligned16(acc)) return SCF_ERR_MISALIGNED;
-  return run_forces(h, pos, nullptr, acc, A, com, SCF_MODE_COEFFS);
+  int rc = run_prep(h, A, com);
+  if (rc != SCF_OK) return rc;
+  return run_forces(h, pos, nullptr, acc, com, SCF_MODE_COEFFS);
 }
 
 int scf_step(scf_handle* h, void* pos, void* vel, void* acc, double* com, int nsteps) {
@@ -352,7 +385,7 @@ int scf_step(scf_handle* h, void* pos, void* vel, void* acc, double* com, int ns
   for (int st = 0; st < nsteps; ++st) {
     int rc = run_coeffs(h, pos, vel, acc, nullptr, h->d_A, com, SCF_MODE_STEP);
     if (rc != SCF_OK) return rc;
-    rc = run_forces(h, pos, vel, acc, h->d_A, com, SCF_MODE_STEP);
+    rc = run_forces(h, pos, vel, acc, com, SCF_MODE_STEP);
     if (rc != SCF_OK) return rc;
   }
   return SCF_OK;
@@ -379,7 +412,7 @@ int scf_launches_per_call(const scf_handle* h, int which) {
   if (!h) return SCF_ERR_NULL_POINTER;
   const int k1 = h->k1_blocks > 0 ? 1 : 0, k3 = h->k3_blocks > 0 ? 1 : 0;
   if (which == 0) return k1 + 1;
-  if (which == 1) return k3;
+  if (which == 1) return 1 + k3;
   if (which == 2) return k1 + 1 + k3;
   return SCF_ERR_INVALID_ARG;
 }

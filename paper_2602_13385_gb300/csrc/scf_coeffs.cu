@@ -209,18 +209,66 @@ __device__ void com_kdk(const ScfHostParams& hp, double* c, double dt) {
   c[5] += 0.5 * dt * az;
 }
 
+__device__ __forceinline__ void write_force_pair(void* F, int f32, size_t i, double c, double s) {
+  if (f32) reinterpret_cast<float2*>(F)[i] = make_float2((float)c, (float)s);
+  else reinterpret_cast<double2*>(F)[i] = make_double2(c, s);
+}
+
+// One warp per (cosine, sine) coefficient pair of one progenitor: lane j
+// sums the partials of blocks j, j+32, ... in order, then a fixed shuffle
+// tree combines the lanes, so the result is the same on every run.
 __global__ void k2_reduce(K2Args a) {
   const int p = blockIdx.y;
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < 2 * a.nc) {
+  const int lane = threadIdx.x & 31;
+  const int i = blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5);
+  if (i < a.nc) {
     const int b0 = a.prog_blk_off[p], b1 = a.prog_blk_off[p + 1];
-    const double* src = a.partials + (size_t)b0 * 2 * a.nc + i;
-    double s = 0.0;
-    for (int b = b0; b < b1; ++b, src += 2 * a.nc) s += *src;
-    a.A_out[(size_t)p * 2 * a.nc + i] = s * a.norm[i];
+    const size_t stride = 2 * (size_t)a.nc;
+    double sc = 0.0, ss = 0.0;
+    for (int b = b0 + lane; b < b1; b += 32) {
+      const double* src = a.partials + (size_t)b * stride + i;
+      sc += src[0];
+      ss += src[a.nc];
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      sc += __shfl_xor_sync(0xffffffffu, sc, o);
+      ss += __shfl_xor_sync(0xffffffffu, ss, o);
+    }
+    if (lane == 0) {
+      const double S = sc * a.norm[i], T = ss * a.norm[a.nc + i];
+      double* A = a.A_out + (size_t)p * stride;
+      A[i] = S;
+      A[a.nc + i] = T;
+      if (a.F_out) {
+        const double w = -a.G / a.b_prog[p] * c_tab.inv_nlm[i % a.nlm];
+        write_force_pair(a.F_out, a.f32, (size_t)p * a.nc + i, w * S, w * T);
+      }
+    }
   }
-  if (a.mode == SCF_MODE_STEP && a.host.n > 0 && blockIdx.x == 0 && threadIdx.x == 0 && a.com != nullptr)
-    com_kdk(a.host, a.com + 6 * p, a.dt);
+  if (blockIdx.x == 0 && threadIdx.x == 0 && a.host.n > 0 && a.com != nullptr) {
+    double* c = a.com + 6 * p;
+    if (a.mode == SCF_MODE_STEP) com_kdk(a.host, c, a.dt);
+    if (a.aR_out) {
+      double* r = a.aR_out + 4 * p;
+      scf_host_accel(a.host, c[0], c[1], c[2], r[0], r[1], r[2]);
+    }
+  }
+}
+
+__global__ void k_prep(PrepArgs a) {
+  const int p = blockIdx.y;
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < a.nc) {
+    const double* A = a.A + (size_t)p * 2 * a.nc;
+    const double w = -a.G / a.b_prog[p] * c_tab.inv_nlm[i % a.nlm];
+    write_force_pair(a.F_out, a.f32, (size_t)p * a.nc + i, w * A[i], w * A[a.nc + i]);
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0 && a.host.n > 0 && a.com != nullptr) {
+    const double* c = a.com + 6 * p;
+    double* r = a.aR_out + 4 * p;
+    scf_host_accel(a.host, c[0], c[1], c[2], r[0], r[1], r[2]);
+  }
 }
 
 template <typename T>
@@ -266,6 +314,8 @@ static cudaError_t k1_prepare_t(int lmax, int nmax, ScfLaunchInfo* info, int* bl
   return dispatch_lmax<K>(lmax, [&](auto k) -> cudaError_t {
     using KK = decltype(k);
     info->threads = 128;
+    info->tile = 128;
+    info->variant = 0;
     info->smem = KK::smem(nmax, nc);
     cudaError_t e = cudaFuncSetAttribute(KK::fn(), cudaFuncAttributeMaxDynamicSharedMemorySize, (int)info->smem);
     if (e != cudaSuccess) return e;
@@ -289,7 +339,13 @@ cudaError_t scf_k1_launch(int precision, const K1Args& a, int blocks, const ScfL
 }
 
 cudaError_t scf_k2_launch(const K2Args& a, cudaStream_t s) {
-  dim3 grid((2 * a.nc + 127) / 128, a.n_prog);
-  k2_reduce<<<grid, 128, 0, s>>>(a);
+  dim3 grid((a.nc + 7) / 8, a.n_prog);  // 8 warps per block, one pair per warp
+  k2_reduce<<<grid, 256, 0, s>>>(a);
+  return cudaGetLastError();
+}
+
+cudaError_t scf_prep_launch(const PrepArgs& a, cudaStream_t s) {
+  dim3 grid((a.nc + 127) / 128, a.n_prog);
+  k_prep<<<grid, 128, 0, s>>>(a);
   return cudaGetLastError();
 }

@@ -56,27 +56,13 @@ __global__ void __launch_bounds__(K3_TB) k3_forces(K3Args a) {
   const int prog = a.blk_prog[blockIdx.x];
   const double b = a.b_prog[prog];
   {
-    const double* A = a.A + (size_t)prog * 2 * a.nc;
-    const double f = -a.G / b;
-    for (int i = tid; i < a.nc; i += K3_TB) {
-      const double w = f * c_tab.inv_nlm[i % a.nlm];
-      V2 v;
-      v.x = (T)(w * A[i]);
-      v.y = (T)(w * A[a.nc + i]);
-      F[i] = v;
-    }
+    const V2* Fg = reinterpret_cast<const V2*>(a.F) + (size_t)prog * a.nc;
+    for (int i = tid; i < a.nc; i += K3_TB) F[i] = Fg[i];
   }
   const bool has_host = a.host.n > 0 && a.com != nullptr;
-  if (tid == 0) {
-    s_R[0] = s_R[1] = s_R[2] = 0.0;
-    s_aR[0] = s_aR[1] = s_aR[2] = 0.0;
-    if (has_host) {
-      const double* c = a.com + 6 * prog;
-      s_R[0] = c[0];
-      s_R[1] = c[1];
-      s_R[2] = c[2];
-      scf_host_accel(a.host, c[0], c[1], c[2], s_aR[0], s_aR[1], s_aR[2]);
-    }
+  if (tid < 3) {
+    s_R[tid] = has_host ? a.com[6 * prog + tid] : 0.0;
+    s_aR[tid] = has_host ? a.aR[4 * prog + tid] : 0.0;
   }
   __syncthreads();
 
@@ -263,6 +249,8 @@ cudaError_t prepare_t(int lmax, int nmax, size_t elem, ScfLaunchInfo* info, int*
   return dispatch_lmax<K>(lmax, [&](auto k) -> cudaError_t {
     using KK = decltype(k);
     info->threads = K3_TB;
+    info->tile = K3_TB;
+    info->variant = 0;
     info->smem = elem * 2 * (size_t)nc;  // (cosine, sine) pair per coefficient
     cudaError_t e = cudaFuncSetAttribute(KK::fn(), cudaFuncAttributeMaxDynamicSharedMemorySize, (int)info->smem);
     if (e != cudaSuccess) return e;

@@ -34,10 +34,30 @@ struct K2Args {
   const int* prog_blk_off;  // [n_prog+1]
   const double* norm;       // [2*NC]
   double* A_out;            // [n_prog][2*NC]
-  int nc, n_prog;
+  int nc, n_prog, nlm;
   int mode;
   double dt;
   double* com;              // [n_prog][6] (step mode with host)
+  ScfHostParams host;
+  // optional: force coefficients F = -G {S,T} / (b N_lm) as (cos, sin) pairs
+  // of the field kernel's element type, and a_host(R) per progenitor
+  void* F_out;              // [n_prog][NC] float2 (f32) or double2, or null
+  int f32;                  // element type of F_out
+  const double* b_prog;
+  double G;
+  double* aR_out;           // [n_prog][4], or null
+};
+
+// Force coefficients and a_host(R) from given coefficients (scf_forces).
+struct PrepArgs {
+  const double* A;          // [n_prog][2*NC]
+  const double* com;        // [n_prog][6] or null
+  void* F_out;
+  int f32;
+  const double* b_prog;
+  double G;
+  double* aR_out;
+  int nc, nlm, n_prog;
   ScfHostParams host;
 };
 
@@ -46,8 +66,9 @@ struct K3Args {
   const void* pos;
   void* vel;
   void* acc;
-  const double* A;          // [n_prog][2*NC]
-  const double* com;        // [n_prog][6] or null
+  const void* F;            // [n_prog][NC] (cos, sin) force-coefficient pairs
+  const double* com;        // [n_prog][6] or null (R is read)
+  const double* aR;         // [n_prog][4] a_host(R)
   const int* blk_prog;
   const int64_t* blk_begin;
   const int64_t* blk_end;
@@ -60,8 +81,10 @@ struct K3Args {
 };
 
 struct ScfLaunchInfo {
-  int threads;
-  size_t smem;
+  int threads;   // threads per block
+  int tile;      // particles per tile (block ranges are whole tiles)
+  size_t smem;   // dynamic shared memory per block
+  int variant;   // kernel variant chosen by the prepare call
 };
 
 void scf_make_norm(int nmax, int lmax, double* norm);
@@ -77,4 +100,5 @@ cudaError_t scf_k3_prepare(int precision, int lmax, int nmax, ScfLaunchInfo* inf
 
 cudaError_t scf_k1_launch(int precision, const K1Args& a, int blocks, const ScfLaunchInfo& info, cudaStream_t s);
 cudaError_t scf_k2_launch(const K2Args& a, cudaStream_t s);
+cudaError_t scf_prep_launch(const PrepArgs& a, cudaStream_t s);
 cudaError_t scf_k3_launch(int precision, const K3Args& a, int blocks, const ScfLaunchInfo& info, cudaStream_t s);

@@ -128,9 +128,9 @@ extern "C" int scf_coeffs_noalloc(const scf_config* cfg, int64_t n, const void* 
   if (scf_k1_prepare(cfg->precision, cfg->lmax, cfg->nmax, &info, &bps) != cudaSuccess || bps < 1) return SCF_ERR_CUDA;
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
 
-  // Block map: whole tiles of info.threads particles, about one wave of
+  // Block map: whole tiles of info.tile particles, about one wave of
   // resident blocks, at most as many blocks as the scratch holds partials for.
-  const int64_t tp = info.threads;
+  const int64_t tp = info.tile;
   const int64_t tiles = (n + tp - 1) / tp;
   int64_t max_blocks = std::min<int64_t>(SCF_NOALLOC_MAX_BLOCKS, SCF_NOALLOC_MAX_COEFS * (int64_t)SCF_NOALLOC_MAX_BLOCKS / (2 * nc));
   max_blocks = std::min<int64_t>(max_blocks, (int64_t)d->n_sm * bps);
@@ -165,6 +165,7 @@ extern "C" int scf_coeffs_noalloc(const scf_config* cfg, int64_t n, const void* 
   r.norm = sc->norm;
   r.A_out = A_out;
   r.nc = nc;
+  r.nlm = nlm;
   r.n_prog = 1;
   r.mode = SCF_MODE_COEFFS;
   return scf_k2_launch(r, s) == cudaSuccess ? SCF_OK : SCF_ERR_CUDA;

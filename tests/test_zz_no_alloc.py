@@ -4,9 +4,11 @@ It serves callers that cannot call cudaMalloc (code inside a memory arena it
 must not grow, paths where allocation is not allowed or would synchronise the
 device, plugins handed device pointers but no allocator).  Its scratch is a
 static device array inside the library.  These tests call it through the C ABI
-and compare it with scf_coeffs, at the same 1e-10 tolerance as the other FP64
-parity tests, on two calls in a row with different inputs (the scratch keeps
-the previous call's contents, so the second call checks that nothing leaks).
+and compare it with scf_coeffs on two calls in a row with different inputs
+(the scratch keeps the previous call's contents, so the second call checks
+that nothing leaks), at the tolerances the other parity tests use: 1e-10 in
+double precision, 1e-6 in mixed precision (the two entry points split the
+particles into different numbers of blocks, which changes float rounding).
 """
 import numpy as np
 import pytest
@@ -17,6 +19,7 @@ torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
 TOL = 1e-10
+TOL_BY_PRECISION = {"fp64": 1e-10, "mixed": 1e-6}
 
 
 @pytest.fixture(scope="module")
@@ -66,8 +69,9 @@ def test_noalloc_matches_scf_coeffs_on_two_calls(pkg, precision):
     torch.cuda.synchronize()
     R1 = _existing(pkg, cfg1, p1)
     R2 = _existing(pkg, cfg2, p2, m2)
-    assert _rel(A1.cpu().numpy(), R1.cpu().numpy()) < TOL
-    assert _rel(A2.cpu().numpy(), R2.cpu().numpy()) < TOL
+    tol = TOL_BY_PRECISION[precision]
+    assert _rel(A1.cpu().numpy(), R1.cpu().numpy()) < tol
+    assert _rel(A2.cpu().numpy(), R2.cpu().numpy()) < tol
 
 
 def test_noalloc_allocates_no_device_memory(pkg):
