@@ -153,6 +153,12 @@ int scf_forces(scf_handle* h, const void* pos, const double* A, const double* co
  * (nsteps < 0), SCF_ERR_CUDA. */
 int scf_step(scf_handle* h, void* pos, void* vel, void* acc, double* com, int nsteps);
 
+/* Handle options.  SCF_OPT_GRAPHS: 1 (default) = scf_step replays a captured
+ * CUDA graph per step where it can, 0 = plain kernel launches.
+ * Errors: SCF_ERR_NULL_POINTER, SCF_ERR_INVALID_ARG (unknown option). */
+#define SCF_OPT_GRAPHS 1
+int scf_set_option(scf_handle* h, int option, int value);
+
 /* Copies (device to device, on the handle's stream) the coefficients used by
  * the last force evaluation of scf_step into A_out ([n_prog][2*NC] doubles). */
 int scf_last_coeffs(scf_handle* h, double* A_out);

@@ -37,8 +37,9 @@ ERRORS = {
 
 # every symbol include/scf.h declares
 EXPORTS = ["scf_init", "scf_coeffs", "scf_forces", "scf_step", "scf_last_coeffs", "scf_status",
-           "scf_launches_per_call", "scf_profile", "scf_profile_read", "scf_coeffs_noalloc", "scf_free",
-           "scf_strerror"]
+           "scf_launches_per_call", "scf_profile", "scf_profile_read", "scf_coeffs_noalloc", "scf_set_option",
+           "scf_free", "scf_strerror"]
+SCF_OPT_GRAPHS = 1
 
 
 class ScfError(RuntimeError):
@@ -85,6 +86,7 @@ def load(build: bool = True) -> ctypes.CDLL:
     lib.scf_profile.argtypes = [vp, i]
     lib.scf_profile_read.argtypes = [vp, dp, ctypes.POINTER(ctypes.c_int64)]
     lib.scf_coeffs_noalloc.argtypes = [ctypes.POINTER(scf_config), ctypes.c_int64, vp, vp, vp, vp]
+    lib.scf_set_option.argtypes = [vp, i, i]
     lib.scf_free.argtypes = [vp]
     lib.scf_strerror.argtypes = [i]
     lib.scf_strerror.restype = ctypes.c_char_p
@@ -184,6 +186,10 @@ def scf_coeffs_noalloc(cfg: scf_config, n: int, pos, mask, A_out, stream: int = 
     import torch
     _check(load().scf_coeffs_noalloc(ctypes.byref(cfg), int(n), _ptr(pos), _ptr(mask, torch.uint8),
                                      _ptr(A_out, torch.float64), ctypes.c_void_p(stream)), "scf_coeffs_noalloc")
+
+
+def scf_set_option(h, option: int, value: int):
+    _check(load().scf_set_option(h, int(option), int(value)), "scf_set_option")
 
 
 def scf_free(h):

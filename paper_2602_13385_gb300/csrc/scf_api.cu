@@ -41,6 +41,10 @@ struct scf_handle {
   unsigned* d_status = nullptr;
   void* d_base = nullptr;
   ScfHostParams host{};
+  // CUDA graph of one scf_step step, keyed by the caller's buffers
+  bool graphs = true;
+  cudaGraphExec_t step_exec = nullptr;
+  const void* step_key[4] = {nullptr, nullptr, nullptr, nullptr};
   // launch timing (scf_profile)
   bool prof_on = false;
   std::vector<cudaEvent_t> prof_ev;   // pairs (start, stop)
@@ -376,19 +380,83 @@ int scf_forces(scf_handle* h, const void* pos, const double* A, const double* co
   return run_forces(h, pos, nullptr, acc, com, SCF_MODE_COEFFS);
 }
 
+namespace {
+
+int launch_step(scf_handle* h, void* pos, void* vel, void* acc, double* com) {
+  int rc = run_coeffs(h, pos, vel, acc, nullptr, h->d_A, com, SCF_MODE_STEP);
+  if (rc != SCF_OK) return rc;
+  return run_forces(h, pos, vel, acc, com, SCF_MODE_STEP);
+}
+
+void drop_graph(scf_handle* h) {
+  if (h->step_exec) cudaGraphExecDestroy(h->step_exec);
+  h->step_exec = nullptr;
+  for (auto& k : h->step_key) k = nullptr;
+}
+
+// Captures one step on the handle's stream into an executable graph.  Returns
+// false (and leaves the handle without a graph) when the stream cannot be
+// captured, e.g. the legacy default stream.
+bool capture_step(scf_handle* h, void* pos, void* vel, void* acc, double* com) {
+  drop_graph(h);
+  if (h->stream == nullptr || h->stream == cudaStreamLegacy) return false;
+  if (cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  const int rc = launch_step(h, pos, vel, acc, com);
+  cudaGraph_t g = nullptr;
+  const cudaError_t e = cudaStreamEndCapture(h->stream, &g);
+  bool ok = rc == SCF_OK && e == cudaSuccess && g != nullptr &&
+            cudaGraphInstantiate(&h->step_exec, g, 0) == cudaSuccess;
+  if (g) cudaGraphDestroy(g);
+  if (!ok) {
+    cudaGetLastError();
+    h->step_exec = nullptr;
+    return false;
+  }
+  h->step_key[0] = pos;
+  h->step_key[1] = vel;
+  h->step_key[2] = acc;
+  h->step_key[3] = com;
+  return true;
+}
+
+}  // namespace
+
 int scf_step(scf_handle* h, void* pos, void* vel, void* acc, double* com, int nsteps) {
   if (!h) return SCF_ERR_NULL_POINTER;
   if (nsteps < 0) return SCF_ERR_INVALID_ARG;
   if ((!pos || !vel || !acc) && h->n_total > 0) return SCF_ERR_NULL_POINTER;
   if (h->host.n > 0 && !com) return SCF_ERR_NULL_POINTER;
   if (!aligned16(pos) || !aligned16(vel) || !aligned16(acc)) return SCF_ERR_MISALIGNED;
+  if (nsteps == 0) return SCF_OK;
+  // one graph launch per step when the stream can be captured (the kernels
+  // and their arguments are the same every step); plain launches otherwise
+  if (h->graphs && !h->prof_on) {
+    const bool same = h->step_exec && h->step_key[0] == pos && h->step_key[1] == vel && h->step_key[2] == acc &&
+                      h->step_key[3] == com;
+    if (same || capture_step(h, pos, vel, acc, com)) {
+      for (int st = 0; st < nsteps; ++st)
+        if (cudaGraphLaunch(h->step_exec, h->stream) != cudaSuccess) return SCF_ERR_CUDA;
+      return SCF_OK;
+    }
+  }
   for (int st = 0; st < nsteps; ++st) {
-    int rc = run_coeffs(h, pos, vel, acc, nullptr, h->d_A, com, SCF_MODE_STEP);
-    if (rc != SCF_OK) return rc;
-    rc = run_forces(h, pos, vel, acc, com, SCF_MODE_STEP);
+    const int rc = launch_step(h, pos, vel, acc, com);
     if (rc != SCF_OK) return rc;
   }
   return SCF_OK;
+}
+
+int scf_set_option(scf_handle* h, int option, int value) {
+  if (!h) return SCF_ERR_NULL_POINTER;
+  if (option == SCF_OPT_GRAPHS) {
+    h->graphs = value != 0;
+    if (!h->graphs) drop_graph(h);
+    return SCF_OK;
+  }
+  return SCF_ERR_INVALID_ARG;
 }
 
 int scf_last_coeffs(scf_handle* h, double* A_out) {
@@ -462,6 +530,7 @@ int scf_free(scf_handle* h) {
   int rc = SCF_OK;
   if (cudaStreamSynchronize(h->stream) != cudaSuccess) rc = SCF_ERR_CUDA;
   prof_release(h);
+  drop_graph(h);
   if (h->d_base && cudaFree(h->d_base) != cudaSuccess) rc = SCF_ERR_CUDA;
   delete h;
   return rc;

@@ -123,6 +123,11 @@ class SCF:
     def launches_per_call(self, which: str) -> int:
         return _lib.scf_launches_per_call(self._h, {"coeffs": 0, "forces": 1, "step": 2}[which])
 
+    def use_graphs(self, enable: bool = True):
+        """scf_step replays a captured CUDA graph per step (default) or launches
+        the kernels directly."""
+        _lib.scf_set_option(self._h, _lib.SCF_OPT_GRAPHS, 1 if enable else 0)
+
     def profile(self, enable: bool = True):
         _lib.scf_profile(self._h, enable)
 

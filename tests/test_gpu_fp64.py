@@ -193,3 +193,29 @@ def test_full_size_king_circular_coefficients_and_sampled_forces(scf):
     idx = np.random.default_rng(0).choice(wl.n, 400, replace=False)
     ref = oracle.forces(wl.pos[idx], A_ref, wl.nmax, wl.lmax, wl.b, com=wl.com, host=oracle.host_struct(wl.host))
     assert acc_err(acc[idx], ref).max() < TOL
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_graph_replay_matches_plain_launches(scf, precision):
+    """scf_step on a non-default stream replays one captured CUDA graph per
+    step; the state must be bitwise the same as with plain launches."""
+    wl = workloads.progenitor_batch(n_prog=3, seed=60, n_range=(500, 3000), nsteps=1)
+    dt = torch.float64 if precision == "fp64" else torch.float32
+    out = []
+    for graphs in (True, False):
+        stream = torch.cuda.Stream()
+        with torch.cuda.stream(stream):
+            cfg = scf.Config(nmax=8, lmax=6, b=wl.b, dt=wl.dt, precision=precision, host=list(wl.host))
+            sim = scf.SCF(cfg, offsets=wl.offsets, b_per_prog=wl.b_per_prog, stream=stream)
+            sim.use_graphs(graphs)
+            p = torch.tensor(wl.pos, device="cuda", dtype=dt)
+            v = torch.tensor(wl.vel, device="cuda", dtype=dt)
+            c = torch.tensor(wl.com_per_prog, device="cuda", dtype=torch.float64)
+            a = sim.forces(p, sim.coeffs(p), com=c)
+            sim.step(p, v, a, com=c, nsteps=3)
+            sim.step(p, v, a, com=c, nsteps=4)       # replays the same graph
+        stream.synchronize()
+        out.append([t.cpu().numpy() for t in (p, v, a, c)])
+        assert sim.status() == (0, 0)
+    for x, y in zip(*out):
+        assert np.array_equal(x, y)
