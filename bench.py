@@ -256,6 +256,7 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", choices=sorted(WORKLOADS), default=DEFAULT_WORKLOAD)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-autotune", action="store_true", help="keep the default kernel shapes")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
@@ -290,6 +291,10 @@ def main():
     c = torch.tensor(coms, device=dev, dtype=torch.float64)
     use_com = c if wl.host else None
     a = sim.forces(p, sim.coeffs(p), com=use_com)
+    tuning = None
+    if not args.no_autotune:
+        # untimed set-up: the library's autotuner picks the kernel shapes
+        tuning = sim.autotune(p, com=use_com, acc=torch.empty_like(a), reps=3, cache=False)
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
     stream = sim.stream
 
@@ -382,6 +387,8 @@ def main():
         "data": "synthetic (seeded sample, see config.workload)",
         "config": workload_config(wl, precision, args.workload),
         "roofline": roofline, "e2e": e2e, "gpu_launches": int(sum(kcount)), "clocks": clocks,
+        "kernel_shapes": dict(sim.tiles(), autotuned=tuning is not None,
+                              candidates_ms=None if tuning is None else tuning["ms"]),
         "src_hash": src_hash(),
     }
     if rank == 0 and world == 1 and not args.no_cpu_baseline:

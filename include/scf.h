@@ -153,11 +153,33 @@ int scf_forces(scf_handle* h, const void* pos, const double* A, const double* co
  * (nsteps < 0), SCF_ERR_CUDA. */
 int scf_step(scf_handle* h, void* pos, void* vel, void* acc, double* com, int nsteps);
 
-/* Handle options.  SCF_OPT_GRAPHS: 1 (default) = scf_step replays a captured
- * CUDA graph per step where it can, 0 = plain kernel launches.
- * Errors: SCF_ERR_NULL_POINTER, SCF_ERR_INVALID_ARG (unknown option). */
+/* Handle options.
+ *   SCF_OPT_GRAPHS    1 (default) = scf_step replays a captured CUDA graph per
+ *                     step where it can, 0 = plain kernel launches.
+ *   SCF_OPT_K1_TILE   particles per tile (= threads per block) of the
+ *                     coefficient kernel: 64, 128 (default) or 256.
+ *   SCF_OPT_K3_BLOCK  threads per block of the field kernel: 64, 128
+ *                     (default) or 256.
+ * Setting a tile or block size synchronises the stream and rewrites the block
+ * maps in the workspace (sized in scf_init for every allowed value).
+ * Errors: SCF_ERR_NULL_POINTER, SCF_ERR_INVALID_ARG (unknown option or value),
+ * SCF_ERR_UNSUPPORTED (the size does not fit this configuration), SCF_ERR_CUDA. */
 #define SCF_OPT_GRAPHS 1
+#define SCF_OPT_K1_TILE 2
+#define SCF_OPT_K3_BLOCK 3
 int scf_set_option(scf_handle* h, int option, int value);
+int scf_get_option(const scf_handle* h, int option, int* value);
+
+/* Autotuner: times every allowed SCF_OPT_K1_TILE with the coefficient pass
+ * and every SCF_OPT_K3_BLOCK with the field pass (2 warm-up + reps timed calls
+ * each, CUDA events on the handle's stream) on the caller's particles, and
+ * keeps the fastest of each.  pos, com as for scf_forces; acc is overwritten.
+ * ms_out (host, nullable) receives the 6 average times in milliseconds
+ * (tiles 64, 128, 256 of kernel 1, then blocks 64, 128, 256 of kernel 3; 0 for
+ * a size that does not fit).  Synchronises the stream; creates CUDA events.
+ * Errors: SCF_ERR_NULL_POINTER, SCF_ERR_MISALIGNED, SCF_ERR_INVALID_ARG
+ * (reps < 1), SCF_ERR_CUDA. */
+int scf_autotune(scf_handle* h, const void* pos, const double* com, void* acc, int reps, double* ms_out);
 
 /* Copies (device to device, on the handle's stream) the coefficients used by
  * the last force evaluation of scf_step into A_out ([n_prog][2*NC] doubles). */

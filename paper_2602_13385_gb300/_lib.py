@@ -38,8 +38,10 @@ ERRORS = {
 # every symbol include/scf.h declares
 EXPORTS = ["scf_init", "scf_coeffs", "scf_forces", "scf_step", "scf_last_coeffs", "scf_status",
            "scf_launches_per_call", "scf_profile", "scf_profile_read", "scf_coeffs_noalloc", "scf_set_option",
-           "scf_free", "scf_strerror"]
+           "scf_get_option", "scf_autotune", "scf_free", "scf_strerror"]
 SCF_OPT_GRAPHS = 1
+SCF_OPT_K1_TILE = 2
+SCF_OPT_K3_BLOCK = 3
 
 
 class ScfError(RuntimeError):
@@ -87,6 +89,8 @@ def load(build: bool = True) -> ctypes.CDLL:
     lib.scf_profile_read.argtypes = [vp, dp, ctypes.POINTER(ctypes.c_int64)]
     lib.scf_coeffs_noalloc.argtypes = [ctypes.POINTER(scf_config), ctypes.c_int64, vp, vp, vp, vp]
     lib.scf_set_option.argtypes = [vp, i, i]
+    lib.scf_get_option.argtypes = [vp, i, ctypes.POINTER(i)]
+    lib.scf_autotune.argtypes = [vp, vp, vp, vp, i, dp]
     lib.scf_free.argtypes = [vp]
     lib.scf_strerror.argtypes = [i]
     lib.scf_strerror.restype = ctypes.c_char_p
@@ -190,6 +194,21 @@ def scf_coeffs_noalloc(cfg: scf_config, n: int, pos, mask, A_out, stream: int = 
 
 def scf_set_option(h, option: int, value: int):
     _check(load().scf_set_option(h, int(option), int(value)), "scf_set_option")
+
+
+def scf_get_option(h, option: int) -> int:
+    v = ctypes.c_int(0)
+    _check(load().scf_get_option(h, int(option), ctypes.byref(v)), "scf_get_option")
+    return v.value
+
+
+def scf_autotune(h, pos, com, acc, reps: int = 5):
+    """Times the allowed tile/block sizes and keeps the fastest; returns the six
+    average times (ms): kernel-1 tiles 64/128/256, kernel-3 blocks 64/128/256."""
+    import torch
+    ms = (ctypes.c_double * 6)()
+    _check(load().scf_autotune(h, _ptr(pos), _ptr(com, torch.float64), _ptr(acc), int(reps), ms), "scf_autotune")
+    return list(ms)
 
 
 def scf_free(h):

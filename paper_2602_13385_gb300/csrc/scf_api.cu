@@ -18,6 +18,9 @@ struct scf_handle {
   cudaStream_t stream = nullptr;
   int nlm = 0, nc = 0;
   int64_t n_total = 0;
+  int n_sm = 0;
+  std::vector<int64_t> offsets;
+  size_t cap_blk1 = 0, cap_blk3 = 0;  // block-map capacity (largest candidate)
   // kernel 1 / 2
   ScfLaunchInfo k1{};
   int k1_blocks = 0;
@@ -73,6 +76,12 @@ int upload_tables_once(int device) {
 }
 
 bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
+
+void drop_graph(scf_handle* h) {
+  if (h->step_exec) cudaGraphExecDestroy(h->step_exec);
+  h->step_exec = nullptr;
+  for (auto& k : h->step_key) k = nullptr;
+}
 
 size_t round_up(size_t x) { return (x + 255) & ~size_t(255); }
 
@@ -218,6 +227,97 @@ int run_forces(scf_handle* h, const void* pos, void* vel, void* acc, const doubl
   return cuda_fail(timed(h, 2, [&] { return scf_k3_launch(h->cfg.precision, a, h->k3_blocks, h->k3, h->stream); }));
 }
 
+// Kernel 1 block map: contiguous ranges of whole tiles, one progenitor per
+// block, about one wave of resident blocks in total.
+struct Map1 {
+  std::vector<int> prog, prog_off;
+  std::vector<int64_t> begin, end;
+};
+Map1 make_map1(const std::vector<int64_t>& off, int n_prog, int64_t tp, int64_t slots) {
+  Map1 m;
+  m.prog_off.assign(n_prog + 1, 0);
+  int64_t total = 0;
+  std::vector<int64_t> tiles(n_prog);
+  for (int p = 0; p < n_prog; ++p) {
+    tiles[p] = (off[p + 1] - off[p] + tp - 1) / tp;
+    total += tiles[p];
+  }
+  const int64_t tpb = std::max<int64_t>(1, (total + slots - 1) / slots);
+  for (int p = 0; p < n_prog; ++p) {
+    m.prog_off[p] = (int)m.prog.size();
+    for (int64_t t0 = 0; t0 < tiles[p]; t0 += tpb) {
+      m.prog.push_back(p);
+      m.begin.push_back(off[p] + t0 * tp);
+      m.end.push_back(std::min(off[p] + (t0 + tpb) * tp, off[p + 1]));
+    }
+  }
+  m.prog_off[n_prog] = (int)m.prog.size();
+  return m;
+}
+
+// Kernel 3 block map: one thread per particle, one progenitor per block.
+struct Map3 {
+  std::vector<int> prog;
+  std::vector<int64_t> begin, end;
+};
+Map3 make_map3(const std::vector<int64_t>& off, int n_prog, int64_t tb) {
+  Map3 m;
+  for (int p = 0; p < n_prog; ++p)
+    for (int64_t k = off[p]; k < off[p + 1]; k += tb) {
+      m.prog.push_back(p);
+      m.begin.push_back(k);
+      m.end.push_back(std::min(k + tb, off[p + 1]));
+    }
+  return m;
+}
+
+bool put(void* dst, const void* src, size_t bytes) {
+  return bytes == 0 || cudaMemcpy(dst, src, bytes, cudaMemcpyHostToDevice) == cudaSuccess;
+}
+
+// Selects kernel 1's particle tile: launch info, block map, upload.
+int use_k1(scf_handle* h, int tp) {
+  ScfLaunchInfo info{};
+  int bps = 0;
+  if (scf_k1_prepare(h->cfg.precision, h->cfg.lmax, h->cfg.nmax, tp, &info, &bps) != cudaSuccess || bps < 1) {
+    cudaGetLastError();
+    return SCF_ERR_UNSUPPORTED;
+  }
+  Map1 m = make_map1(h->offsets, h->n_prog, info.tile, (int64_t)h->n_sm * bps);
+  if (m.prog.size() > h->cap_blk1) return SCF_ERR_UNSUPPORTED;
+  bool ok = put(h->d_blk1_prog, m.prog.data(), sizeof(int) * m.prog.size()) &&
+            put(h->d_blk1_begin, m.begin.data(), sizeof(int64_t) * m.begin.size()) &&
+            put(h->d_blk1_end, m.end.data(), sizeof(int64_t) * m.end.size()) &&
+            put(h->d_prog_blk_off, m.prog_off.data(), sizeof(int) * m.prog_off.size());
+  if (!ok) return SCF_ERR_CUDA;
+  h->k1 = info;
+  h->k1_blocks = (int)m.prog.size();
+  drop_graph(h);
+  return SCF_OK;
+}
+
+// Selects kernel 3's block size: launch info, block map, upload.
+int use_k3(scf_handle* h, int tb) {
+  ScfLaunchInfo info{};
+  int bps = 0;
+  if (scf_k3_prepare(h->cfg.precision, h->cfg.lmax, h->cfg.nmax, tb, &info, &bps) != cudaSuccess || bps < 1) {
+    cudaGetLastError();
+    return SCF_ERR_UNSUPPORTED;
+  }
+  Map3 m = make_map3(h->offsets, h->n_prog, info.tile);
+  if (m.prog.size() > h->cap_blk3) return SCF_ERR_UNSUPPORTED;
+  bool ok = put(h->d_blk3_prog, m.prog.data(), sizeof(int) * m.prog.size()) &&
+            put(h->d_blk3_begin, m.begin.data(), sizeof(int64_t) * m.begin.size()) &&
+            put(h->d_blk3_end, m.end.data(), sizeof(int64_t) * m.end.size());
+  if (!ok) return SCF_ERR_CUDA;
+  h->k3 = info;
+  h->k3_blocks = (int)m.prog.size();
+  drop_graph(h);
+  return SCF_OK;
+}
+
+const int kTiles[3] = {64, 128, 256};
+
 }  // namespace
 
 extern "C" {
@@ -259,50 +359,25 @@ int scf_init(const scf_config* cfg, int n_prog, const int64_t* offsets, const do
   if (cudaGetDevice(&h->device) != cudaSuccess) return fail(SCF_ERR_CUDA);
   rc = upload_tables_once(h->device);
   if (rc != SCF_OK) return fail(rc);
-  int n_sm = 0;
-  if (cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, h->device) != cudaSuccess) return fail(SCF_ERR_CUDA);
+  if (cudaDeviceGetAttribute(&h->n_sm, cudaDevAttrMultiProcessorCount, h->device) != cudaSuccess)
+    return fail(SCF_ERR_CUDA);
+  h->offsets.assign(offsets, offsets + n_prog + 1);
 
-  // kernel 1 block map: contiguous particle ranges of whole tiles, one
-  // progenitor per block, about one wave of resident blocks in total.
-  int bps1 = 0, bps3 = 0;
-  if (scf_k1_prepare(cfg->precision, cfg->lmax, cfg->nmax, &h->k1, &bps1) != cudaSuccess) return fail(SCF_ERR_CUDA);
-  if (scf_k3_prepare(cfg->precision, cfg->lmax, cfg->nmax, &h->k3, &bps3) != cudaSuccess) return fail(SCF_ERR_CUDA);
-  if (bps1 < 1 || bps3 < 1) return fail(SCF_ERR_UNSUPPORTED);
-  const int64_t tp = h->k1.tile;
-  int64_t total_tiles = 0;
-  std::vector<int64_t> tiles(n_prog);
-  for (int p = 0; p < n_prog; ++p) {
-    tiles[p] = (offsets[p + 1] - offsets[p] + tp - 1) / tp;
-    total_tiles += tiles[p];
-  }
-  const int64_t slots = (int64_t)n_sm * bps1;
-  const int64_t tpb = std::max<int64_t>(1, (total_tiles + slots - 1) / slots);
-  std::vector<int> blk1_prog, prog_blk_off(n_prog + 1, 0);
-  std::vector<int64_t> blk1_begin, blk1_end;
-  for (int p = 0; p < n_prog; ++p) {
-    prog_blk_off[p] = (int)blk1_prog.size();
-    for (int64_t t0 = 0; t0 < tiles[p]; t0 += tpb) {
-      blk1_prog.push_back(p);
-      blk1_begin.push_back(offsets[p] + t0 * tp);
-      blk1_end.push_back(std::min(offsets[p] + (t0 + tpb) * tp, offsets[p + 1]));
+  // Capacity of the block maps: the largest any candidate tile can need.
+  for (int tp : kTiles) {
+    ScfLaunchInfo info{};
+    int bps = 0;
+    if (scf_k1_prepare(cfg->precision, cfg->lmax, cfg->nmax, tp, &info, &bps) != cudaSuccess || bps < 1) {
+      cudaGetLastError();
+      continue;
     }
+    h->cap_blk1 = std::max(h->cap_blk1, make_map1(h->offsets, n_prog, info.tile, (int64_t)h->n_sm * bps).prog.size());
   }
-  prog_blk_off[n_prog] = (int)blk1_prog.size();
-  h->k1_blocks = (int)blk1_prog.size();
-  // kernel 3 block map: one thread per particle, one progenitor per block.
-  const int64_t tb = h->k3.tile;
-  std::vector<int> blk3_prog;
-  std::vector<int64_t> blk3_begin, blk3_end;
-  for (int p = 0; p < n_prog; ++p)
-    for (int64_t k = offsets[p]; k < offsets[p + 1]; k += tb) {
-      blk3_prog.push_back(p);
-      blk3_begin.push_back(k);
-      blk3_end.push_back(std::min(k + tb, offsets[p + 1]));
-    }
-  h->k3_blocks = (int)blk3_prog.size();
+  h->cap_blk3 = make_map3(h->offsets, n_prog, 64).prog.size();
+  if (h->cap_blk1 == 0 && h->n_total > 0) return fail(SCF_ERR_UNSUPPORTED);
 
   // one allocation for the whole workspace
-  const size_t nb1 = std::max<size_t>(1, blk1_prog.size()), nb3 = std::max<size_t>(1, blk3_prog.size());
+  const size_t nb1 = std::max<size_t>(1, h->cap_blk1), nb3 = std::max<size_t>(1, h->cap_blk3);
   size_t off = 0;
   auto take = [&](size_t bytes) {
     size_t o = off;
@@ -345,22 +420,16 @@ int scf_init(const scf_config* cfg, int n_prog, const int64_t* offsets, const do
 
   std::vector<double> norm(2 * (size_t)h->nc);
   scf_make_norm(cfg->nmax, cfg->lmax, norm.data());
-  bool ok = true;
-  auto put = [&](void* dst, const void* src, size_t bytes) {
-    if (bytes && cudaMemcpy(dst, src, bytes, cudaMemcpyHostToDevice) != cudaSuccess) ok = false;
-  };
-  put(h->d_norm, norm.data(), sizeof(double) * norm.size());
-  put(h->d_b, bs.data(), sizeof(double) * n_prog);
-  put(h->d_blk1_prog, blk1_prog.data(), sizeof(int) * blk1_prog.size());
-  put(h->d_blk1_begin, blk1_begin.data(), sizeof(int64_t) * blk1_begin.size());
-  put(h->d_blk1_end, blk1_end.data(), sizeof(int64_t) * blk1_end.size());
-  put(h->d_prog_blk_off, prog_blk_off.data(), sizeof(int) * prog_blk_off.size());
-  put(h->d_blk3_prog, blk3_prog.data(), sizeof(int) * blk3_prog.size());
-  put(h->d_blk3_begin, blk3_begin.data(), sizeof(int64_t) * blk3_begin.size());
-  put(h->d_blk3_end, blk3_end.data(), sizeof(int64_t) * blk3_end.size());
-  if (cudaMemset(h->d_status, 0, sizeof(unsigned) * 4) != cudaSuccess) ok = false;
-  if (cudaMemset(h->d_A, 0, sizeof(double) * 2 * (size_t)h->nc * n_prog) != cudaSuccess) ok = false;
+  bool ok = put(h->d_norm, norm.data(), sizeof(double) * norm.size()) &&
+            put(h->d_b, bs.data(), sizeof(double) * n_prog) &&
+            cudaMemset(h->d_status, 0, sizeof(unsigned) * 4) == cudaSuccess &&
+            cudaMemset(h->d_A, 0, sizeof(double) * 2 * (size_t)h->nc * n_prog) == cudaSuccess;
   if (!ok) return fail(SCF_ERR_CUDA);
+  // default shapes: 128-particle tiles and 128-thread blocks (scf_autotune may change them)
+  rc = use_k1(h, 128);
+  if (rc != SCF_OK) return fail(rc);
+  rc = use_k3(h, 128);
+  if (rc != SCF_OK) return fail(rc);
   *out = h;
   return SCF_OK;
 }
@@ -386,12 +455,6 @@ int launch_step(scf_handle* h, void* pos, void* vel, void* acc, double* com) {
   int rc = run_coeffs(h, pos, vel, acc, nullptr, h->d_A, com, SCF_MODE_STEP);
   if (rc != SCF_OK) return rc;
   return run_forces(h, pos, vel, acc, com, SCF_MODE_STEP);
-}
-
-void drop_graph(scf_handle* h) {
-  if (h->step_exec) cudaGraphExecDestroy(h->step_exec);
-  h->step_exec = nullptr;
-  for (auto& k : h->step_key) k = nullptr;
 }
 
 // Captures one step on the handle's stream into an executable graph.  Returns
@@ -456,7 +519,79 @@ int scf_set_option(scf_handle* h, int option, int value) {
     if (!h->graphs) drop_graph(h);
     return SCF_OK;
   }
+  if (option == SCF_OPT_K1_TILE || option == SCF_OPT_K3_BLOCK) {
+    if (value != 64 && value != 128 && value != 256) return SCF_ERR_INVALID_ARG;
+    if (cudaStreamSynchronize(h->stream) != cudaSuccess) return SCF_ERR_CUDA;
+    return option == SCF_OPT_K1_TILE ? use_k1(h, value) : use_k3(h, value);
+  }
   return SCF_ERR_INVALID_ARG;
+}
+
+int scf_get_option(const scf_handle* h, int option, int* value) {
+  if (!h || !value) return SCF_ERR_NULL_POINTER;
+  if (option == SCF_OPT_GRAPHS) *value = h->graphs ? 1 : 0;
+  else if (option == SCF_OPT_K1_TILE) *value = h->k1.tile;
+  else if (option == SCF_OPT_K3_BLOCK) *value = h->k3.threads;
+  else return SCF_ERR_INVALID_ARG;
+  return SCF_OK;
+}
+
+int scf_autotune(scf_handle* h, const void* pos, const double* com, void* acc, int reps, double* ms_out) {
+  if (!h) return SCF_ERR_NULL_POINTER;
+  if ((!pos || !acc) && h->n_total > 0) return SCF_ERR_NULL_POINTER;
+  if (h->host.n > 0 && !com) return SCF_ERR_NULL_POINTER;
+  if (!aligned16(pos) || !aligned16(acc)) return SCF_ERR_MISALIGNED;
+  if (reps < 1) return SCF_ERR_INVALID_ARG;
+  if (h->n_total == 0) return SCF_OK;
+  const bool prof = h->prof_on;
+  h->prof_on = false;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) return SCF_ERR_CUDA;
+  int rc = SCF_OK;
+  auto time_it = [&](auto&& work, double* ms) -> int {
+    for (int w = 0; w < 2; ++w)
+      if ((rc = work()) != SCF_OK) return rc;
+    cudaEventRecord(e0, h->stream);
+    for (int r = 0; r < reps; ++r)
+      if ((rc = work()) != SCF_OK) return rc;
+    cudaEventRecord(e1, h->stream);
+    if (cudaEventSynchronize(e1) != cudaSuccess) return SCF_ERR_CUDA;
+    float t = 0.f;
+    cudaEventElapsedTime(&t, e0, e1);
+    *ms = t / reps;
+    return SCF_OK;
+  };
+  void* p = const_cast<void*>(pos);
+  double best1 = 1e30, best3 = 1e30;
+  int tp_best = h->k1.tile, tb_best = h->k3.threads;
+  for (int i = 0; i < 3 && rc == SCF_OK; ++i) {
+    if (use_k1(h, kTiles[i]) != SCF_OK) continue;
+    double ms = 0.0;
+    rc = time_it([&] { return run_coeffs(h, p, nullptr, nullptr, nullptr, h->d_A, nullptr, SCF_MODE_COEFFS); }, &ms);
+    if (ms_out) ms_out[i] = ms;
+    if (rc == SCF_OK && ms < best1) {
+      best1 = ms;
+      tp_best = kTiles[i];
+    }
+  }
+  if (rc == SCF_OK) rc = use_k1(h, tp_best);
+  if (rc == SCF_OK) rc = run_coeffs(h, p, nullptr, nullptr, nullptr, h->d_A, nullptr, SCF_MODE_COEFFS);
+  if (rc == SCF_OK) rc = run_prep(h, h->d_A, com);
+  for (int i = 0; i < 3 && rc == SCF_OK; ++i) {
+    if (use_k3(h, kTiles[i]) != SCF_OK) continue;
+    double ms = 0.0;
+    rc = time_it([&] { return run_forces(h, pos, nullptr, acc, com, SCF_MODE_COEFFS); }, &ms);
+    if (ms_out) ms_out[3 + i] = ms;
+    if (rc == SCF_OK && ms < best3) {
+      best3 = ms;
+      tb_best = kTiles[i];
+    }
+  }
+  if (rc == SCF_OK) rc = use_k3(h, tb_best);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  h->prof_on = prof;
+  return rc;
 }
 
 int scf_last_coeffs(scf_handle* h, double* A_out) {

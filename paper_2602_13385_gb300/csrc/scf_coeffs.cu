@@ -60,11 +60,8 @@ template <> struct BlockAcc<float> {
   __device__ static double value(const float2* a, int i) { return (double)a[i].x + (double)a[i].y; }
 };
 
-template <typename T> constexpr int k1_tp() { return 128; }
-
-template <typename T, int LMAX>
-__global__ void __launch_bounds__(128) k1_partials(K1Args a) {
-  constexpr int TP = k1_tp<T>();
+template <typename T, int LMAX, int TP>
+__global__ void __launch_bounds__(TP) k1_partials(K1Args a) {
   constexpr int YS = 2 * LMAX + 1;
   using V4 = typename Vec4<T>::type;
   using Acc = BlockAcc<T>;
@@ -185,10 +182,10 @@ __global__ void __launch_bounds__(128) k1_partials(K1Args a) {
   for (int i = tid; i < 2 * a.nc; i += TP) out[i] = Acc::value(acc, i);
 }
 
-template <typename T, int LMAX>
+template <typename T, int LMAX, int TP>
 size_t k1_smem(int nmax, int nc) {
   using Slot = typename BlockAcc<T>::slot;
-  return sizeof(Slot) * 2 * (size_t)nc + sizeof(T) * (size_t)k1_tp<T>() * ((nmax + 1) + (2 * LMAX + 1));
+  return sizeof(Slot) * 2 * (size_t)nc + sizeof(T) * (size_t)TP * ((nmax + 1) + (2 * LMAX + 1));
 }
 
 // ---------------------------------------------------------------------------
@@ -271,19 +268,14 @@ __global__ void k_prep(PrepArgs a) {
   }
 }
 
-template <typename T>
-struct K1 {
-  template <int LMAX>
-  struct At {
-    static void* fn() { return (void*)k1_partials<T, LMAX>; }
-    static size_t smem(int nmax, int nc) { return k1_smem<T, LMAX>(nmax, nc); }
-    static void launch(const K1Args& a, int blocks, size_t smem, cudaStream_t s) {
-      k1_partials<T, LMAX><<<blocks, k1_tp<T>(), smem, s>>>(a);
-    }
-  };
+template <typename T, int TP, int LMAX>
+struct K1At {
+  static void* fn() { return (void*)k1_partials<T, LMAX, TP>; }
+  static size_t smem(int nmax, int nc) { return k1_smem<T, LMAX, TP>(nmax, nc); }
+  static void launch(const K1Args& a, int blocks, size_t smem, cudaStream_t s) {
+    k1_partials<T, LMAX, TP><<<blocks, TP, smem, s>>>(a);
+  }
 };
-template <int L> using K1D = K1<double>::At<L>;
-template <int L> using K1F = K1<float>::At<L>;
 
 int lmax_bucket(int lmax) {
   if (lmax <= 2) return 2;
@@ -294,38 +286,50 @@ int lmax_bucket(int lmax) {
   return 12;
 }
 
-template <template <int> class K, typename F>
+template <typename T, int TP, typename F>
 auto dispatch_lmax(int lmax, F&& f) {
   switch (lmax_bucket(lmax)) {
-    case 2: return f(K<2>());
-    case 4: return f(K<4>());
-    case 6: return f(K<6>());
-    case 8: return f(K<8>());
-    case 10: return f(K<10>());
-    default: return f(K<12>());
+    case 2: return f(K1At<T, TP, 2>());
+    case 4: return f(K1At<T, TP, 4>());
+    case 6: return f(K1At<T, TP, 6>());
+    case 8: return f(K1At<T, TP, 8>());
+    case 10: return f(K1At<T, TP, 10>());
+    default: return f(K1At<T, TP, 12>());
+  }
+}
+
+// Kernel 1 instantiations: particle tiles of 64, 128 or 256 (the autotuner's choices).
+template <typename T, typename F>
+auto dispatch_k1(int tp, int lmax, F&& f) {
+  switch (tp) {
+    case 64: return dispatch_lmax<T, 64>(lmax, f);
+    case 256: return dispatch_lmax<T, 256>(lmax, f);
+    default: return dispatch_lmax<T, 128>(lmax, f);
   }
 }
 
 }  // namespace
 
-template <template <int> class K>
-static cudaError_t k1_prepare_t(int lmax, int nmax, ScfLaunchInfo* info, int* blocks_per_sm) {
+template <typename T>
+static cudaError_t k1_prepare_t(int lmax, int nmax, int tp, ScfLaunchInfo* info, int* blocks_per_sm) {
   const int nlm = (lmax + 1) * (lmax + 2) / 2, nc = (nmax + 1) * nlm;
-  return dispatch_lmax<K>(lmax, [&](auto k) -> cudaError_t {
+  if (tp != 64 && tp != 128 && tp != 256) return cudaErrorInvalidValue;
+  return dispatch_k1<T>(tp, lmax, [&](auto k) -> cudaError_t {
     using KK = decltype(k);
-    info->threads = 128;
-    info->tile = 128;
+    info->threads = tp;
+    info->tile = tp;
     info->variant = 0;
     info->smem = KK::smem(nmax, nc);
+    if (info->smem > 227 * 1024) return cudaErrorInvalidConfiguration;
     cudaError_t e = cudaFuncSetAttribute(KK::fn(), cudaFuncAttributeMaxDynamicSharedMemorySize, (int)info->smem);
     if (e != cudaSuccess) return e;
     return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, KK::fn(), info->threads, info->smem);
   });
 }
 
-cudaError_t scf_k1_prepare(int precision, int lmax, int nmax, ScfLaunchInfo* info, int* blocks_per_sm) {
-  if (precision == 1) return k1_prepare_t<K1F>(lmax, nmax, info, blocks_per_sm);
-  return k1_prepare_t<K1D>(lmax, nmax, info, blocks_per_sm);
+cudaError_t scf_k1_prepare(int precision, int lmax, int nmax, int tp, ScfLaunchInfo* info, int* blocks_per_sm) {
+  if (precision == 1) return k1_prepare_t<float>(lmax, nmax, tp, info, blocks_per_sm);
+  return k1_prepare_t<double>(lmax, nmax, tp, info, blocks_per_sm);
 }
 
 cudaError_t scf_k1_launch(int precision, const K1Args& a, int blocks, const ScfLaunchInfo& info, cudaStream_t s) {
@@ -333,8 +337,8 @@ cudaError_t scf_k1_launch(int precision, const K1Args& a, int blocks, const ScfL
     decltype(k)::launch(a, blocks, info.smem, s);
     return 0;
   };
-  if (precision == 1) dispatch_lmax<K1F>(a.lmax, go);
-  else dispatch_lmax<K1D>(a.lmax, go);
+  if (precision == 1) dispatch_k1<float>(info.tile, a.lmax, go);
+  else dispatch_k1<double>(info.tile, a.lmax, go);
   return cudaGetLastError();
 }
 

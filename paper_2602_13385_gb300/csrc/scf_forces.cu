@@ -41,9 +41,7 @@ template <typename T> __device__ __forceinline__ T tlk(int i) { return sizeof(T)
 template <typename T> __device__ __forceinline__ T tlsub(int l) { return sizeof(T) == 8 ? (T)c_tab.lsub[l] : (T)c_tab.lsubf[l]; }
 template <typename T> __device__ __forceinline__ T tldiag(int l) { return sizeof(T) == 8 ? (T)c_tab.ldiag[l] : (T)c_tab.ldiagf[l]; }
 
-constexpr int K3_TB = 128;
-
-template <typename T, int LMAX>
+template <typename T, int LMAX, int K3_TB>
 __global__ void __launch_bounds__(K3_TB) k3_forces(K3Args a) {
   using V4 = typename Vec4<T>::type;
   using V2 = typename Vec2<T>::type;
@@ -209,18 +207,13 @@ __global__ void __launch_bounds__(K3_TB) k3_forces(K3Args a) {
   }
 }
 
-template <typename T>
-struct K3 {
-  template <int LMAX>
-  struct At {
-    static void* fn() { return (void*)k3_forces<T, LMAX>; }
-    static void launch(const K3Args& a, int blocks, size_t smem, cudaStream_t s) {
-      k3_forces<T, LMAX><<<blocks, K3_TB, smem, s>>>(a);
-    }
-  };
+template <typename T, int TB, int LMAX>
+struct K3At {
+  static void* fn() { return (void*)k3_forces<T, LMAX, TB>; }
+  static void launch(const K3Args& a, int blocks, size_t smem, cudaStream_t s) {
+    k3_forces<T, LMAX, TB><<<blocks, TB, smem, s>>>(a);
+  }
 };
-template <int L> using K3D = K3<double>::At<L>;
-template <int L> using K3F = K3<float>::At<L>;
 
 int lmax_bucket(int lmax) {
   if (lmax <= 2) return 2;
@@ -231,27 +224,38 @@ int lmax_bucket(int lmax) {
   return 12;
 }
 
-template <template <int> class K, typename Fn>
+template <typename T, int TB, typename Fn>
 auto dispatch_lmax(int lmax, Fn&& f) {
   switch (lmax_bucket(lmax)) {
-    case 2: return f(K<2>());
-    case 4: return f(K<4>());
-    case 6: return f(K<6>());
-    case 8: return f(K<8>());
-    case 10: return f(K<10>());
-    default: return f(K<12>());
+    case 2: return f(K3At<T, TB, 2>());
+    case 4: return f(K3At<T, TB, 4>());
+    case 6: return f(K3At<T, TB, 6>());
+    case 8: return f(K3At<T, TB, 8>());
+    case 10: return f(K3At<T, TB, 10>());
+    default: return f(K3At<T, TB, 12>());
   }
 }
 
-template <template <int> class K>
-cudaError_t prepare_t(int lmax, int nmax, size_t elem, ScfLaunchInfo* info, int* blocks_per_sm) {
+// Kernel 3 instantiations: blocks of 64, 128 or 256 threads (the autotuner's choices).
+template <typename T, typename Fn>
+auto dispatch_k3(int tb, int lmax, Fn&& f) {
+  switch (tb) {
+    case 64: return dispatch_lmax<T, 64>(lmax, f);
+    case 256: return dispatch_lmax<T, 256>(lmax, f);
+    default: return dispatch_lmax<T, 128>(lmax, f);
+  }
+}
+
+template <typename T>
+cudaError_t prepare_t(int lmax, int nmax, int tb, ScfLaunchInfo* info, int* blocks_per_sm) {
   const int nlm = (lmax + 1) * (lmax + 2) / 2, nc = (nmax + 1) * nlm;
-  return dispatch_lmax<K>(lmax, [&](auto k) -> cudaError_t {
+  if (tb != 64 && tb != 128 && tb != 256) return cudaErrorInvalidValue;
+  return dispatch_k3<T>(tb, lmax, [&](auto k) -> cudaError_t {
     using KK = decltype(k);
-    info->threads = K3_TB;
-    info->tile = K3_TB;
+    info->threads = tb;
+    info->tile = tb;
     info->variant = 0;
-    info->smem = elem * 2 * (size_t)nc;  // (cosine, sine) pair per coefficient
+    info->smem = sizeof(T) * 2 * (size_t)nc;  // (cosine, sine) pair per coefficient
     cudaError_t e = cudaFuncSetAttribute(KK::fn(), cudaFuncAttributeMaxDynamicSharedMemorySize, (int)info->smem);
     if (e != cudaSuccess) return e;
     return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, KK::fn(), info->threads, info->smem);
@@ -260,9 +264,9 @@ cudaError_t prepare_t(int lmax, int nmax, size_t elem, ScfLaunchInfo* info, int*
 
 }  // namespace
 
-cudaError_t scf_k3_prepare(int precision, int lmax, int nmax, ScfLaunchInfo* info, int* blocks_per_sm) {
-  if (precision == 1) return prepare_t<K3F>(lmax, nmax, sizeof(float), info, blocks_per_sm);
-  return prepare_t<K3D>(lmax, nmax, sizeof(double), info, blocks_per_sm);
+cudaError_t scf_k3_prepare(int precision, int lmax, int nmax, int tb, ScfLaunchInfo* info, int* blocks_per_sm) {
+  if (precision == 1) return prepare_t<float>(lmax, nmax, tb, info, blocks_per_sm);
+  return prepare_t<double>(lmax, nmax, tb, info, blocks_per_sm);
 }
 
 cudaError_t scf_k3_launch(int precision, const K3Args& a, int blocks, const ScfLaunchInfo& info, cudaStream_t s) {
@@ -270,7 +274,7 @@ cudaError_t scf_k3_launch(int precision, const K3Args& a, int blocks, const ScfL
     decltype(k)::launch(a, blocks, info.smem, s);
     return 0;
   };
-  if (precision == 1) dispatch_lmax<K3F>(a.lmax, go);
-  else dispatch_lmax<K3D>(a.lmax, go);
+  if (precision == 1) dispatch_k3<float>(info.threads, a.lmax, go);
+  else dispatch_k3<double>(info.threads, a.lmax, go);
   return cudaGetLastError();
 }

@@ -95,8 +95,9 @@ cudaError_t scf_upload_const_forces(const ScfConst* t);
 
 // Launch configuration (threads, dynamic shared memory) of each kernel for
 // the given sizes; sets the shared-memory attribute of the instantiation.
-cudaError_t scf_k1_prepare(int precision, int lmax, int nmax, ScfLaunchInfo* info, int* blocks_per_sm);
-cudaError_t scf_k3_prepare(int precision, int lmax, int nmax, ScfLaunchInfo* info, int* blocks_per_sm);
+// tp: kernel 1 particle tile (64, 128, 256); tb: kernel 3 block size (64, 128, 256).
+cudaError_t scf_k1_prepare(int precision, int lmax, int nmax, int tp, ScfLaunchInfo* info, int* blocks_per_sm);
+cudaError_t scf_k3_prepare(int precision, int lmax, int nmax, int tb, ScfLaunchInfo* info, int* blocks_per_sm);
 
 cudaError_t scf_k1_launch(int precision, const K1Args& a, int blocks, const ScfLaunchInfo& info, cudaStream_t s);
 cudaError_t scf_k2_launch(const K2Args& a, cudaStream_t s);

@@ -125,7 +125,8 @@ extern "C" int scf_coeffs_noalloc(const scf_config* cfg, int64_t n, const void* 
   if (rc != SCF_OK) return rc;
   ScfLaunchInfo info{};
   int bps = 0;
-  if (scf_k1_prepare(cfg->precision, cfg->lmax, cfg->nmax, &info, &bps) != cudaSuccess || bps < 1) return SCF_ERR_CUDA;
+  if (scf_k1_prepare(cfg->precision, cfg->lmax, cfg->nmax, 128, &info, &bps) != cudaSuccess || bps < 1)
+    return SCF_ERR_CUDA;
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
 
   // Block map: whole tiles of info.tile particles, about one wave of

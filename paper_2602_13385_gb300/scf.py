@@ -10,11 +10,15 @@ Layouts (see include/scf.h): positions ``(N, 4)`` = (x, y, z, m), velocities
 """
 from __future__ import annotations
 
+import json
+import os
 from dataclasses import dataclass, field
 
 import torch
 
 from . import _lib
+
+_CACHE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "_autotune_cache.json")
 
 HOST_HERNQUIST = _lib.SCF_HOST_HERNQUIST
 HOST_NFW = _lib.SCF_HOST_NFW
@@ -122,6 +126,49 @@ class SCF:
 
     def launches_per_call(self, which: str) -> int:
         return _lib.scf_launches_per_call(self._h, {"coeffs": 0, "forces": 1, "step": 2}[which])
+
+    def tiles(self) -> dict:
+        """Current kernel shapes: coefficient-kernel tile and field-kernel block."""
+        return {"k1_tile": _lib.scf_get_option(self._h, _lib.SCF_OPT_K1_TILE),
+                "k3_block": _lib.scf_get_option(self._h, _lib.SCF_OPT_K3_BLOCK)}
+
+    def set_tiles(self, k1_tile: int | None = None, k3_block: int | None = None):
+        if k1_tile is not None:
+            _lib.scf_set_option(self._h, _lib.SCF_OPT_K1_TILE, int(k1_tile))
+        if k3_block is not None:
+            _lib.scf_set_option(self._h, _lib.SCF_OPT_K3_BLOCK, int(k3_block))
+
+    def _tune_key(self) -> str:
+        n = max(self.n, 1)
+        n2 = float(f"{n:.2g}")          # shapes are chosen per problem-size bucket
+        return "|".join(str(x) for x in (torch.cuda.get_device_name(self.device), self.config.precision,
+                                         self.config.nmax, self.config.lmax, n2, self.n_prog))
+
+    def autotune(self, pos, com=None, acc=None, reps: int = 5, cache: bool = True) -> dict:
+        """Chooses the kernel shapes by timing every allowed size on ``pos``
+        (scf_autotune); with ``cache`` the choice is stored per GPU, precision,
+        (nmax, lmax), problem-size bucket and progenitor count, and reused."""
+        key = self._tune_key()
+        table = {}
+        if cache and os.path.exists(_CACHE):
+            try:
+                with open(_CACHE) as f:
+                    table = json.load(f)
+            except (OSError, ValueError):
+                table = {}
+        if cache and key in table:
+            self.set_tiles(**{k: table[key][k] for k in ("k1_tile", "k3_block")})
+            return dict(table[key], cached=True)
+        acc = self.new_particles() if acc is None else acc
+        ms = _lib.scf_autotune(self._h, pos, com, acc, reps)
+        result = dict(self.tiles(), ms=ms)
+        if cache:
+            table[key] = result
+            tmp = _CACHE + f".{os.getpid()}.tmp"
+            with open(tmp, "w") as f:
+                json.dump(table, f, indent=1)
+            os.replace(tmp, _CACHE)
+        return dict(result, cached=False)
 
     def use_graphs(self, enable: bool = True):
         """scf_step replays a captured CUDA graph per step (default) or launches

@@ -219,3 +219,44 @@ def test_graph_replay_matches_plain_launches(scf, precision):
         assert sim.status() == (0, 0)
     for x, y in zip(*out):
         assert np.array_equal(x, y)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_every_tile_and_block_size_matches_oracle(scf, precision):
+    """The autotuner chooses among these shapes, so each must be correct."""
+    wl = workloads.king_circular(n=3000, seed=61, nsteps=1)
+    dt = torch.float64 if precision == "fp64" else torch.float32
+    pos = wl.pos if precision == "fp64" else wl.pos.astype(np.float32).astype(np.float64)
+    A_ref = oracle.coeffs(pos, wl.nmax, wl.lmax, wl.b)
+    ref = oracle.forces(pos, A_ref, wl.nmax, wl.lmax, wl.b, com=wl.com, host=oracle.host_struct(wl.host))
+    sim = make(scf, wl.nmax, wl.lmax, wl.b, n=wl.n, host=wl.host, precision=precision)
+    p = torch.tensor(wl.pos, device="cuda", dtype=dt)
+    c = dev(wl.com[None])
+    tol_A = TOL if precision == "fp64" else 1e-4
+    tol_a = TOL if precision == "fp64" else 1e-5
+    for size in (64, 128, 256):
+        sim.set_tiles(k1_tile=size, k3_block=size)
+        assert sim.tiles() == {"k1_tile": size, "k3_block": size}
+        A = sim.coeffs(p).cpu().numpy()[0]
+        acc = sim.forces(p, dev(A_ref[None]), com=c).cpu().double().numpy()
+        assert coef_err(A, A_ref) < tol_A
+        e = acc_err(acc, ref)
+        assert (e.max() if precision == "fp64" else np.median(e)) < tol_a
+    check_status(sim)
+
+
+def test_autotune_picks_a_valid_shape_and_keeps_results(scf, tmp_path, monkeypatch):
+    import paper_2602_13385_gb300.scf as scf_mod
+    monkeypatch.setattr(scf_mod, "_CACHE", str(tmp_path / "tune.json"))
+    wl = workloads.king_circular(n=20000, seed=62, nsteps=1)
+    sim = make(scf, wl.nmax, wl.lmax, wl.b, n=wl.n, host=wl.host)
+    p, c = dev(wl.pos), dev(wl.com[None])
+    before = sim.coeffs(p).cpu().numpy()
+    res = sim.autotune(p, com=c, reps=2)
+    assert res["k1_tile"] in (64, 128, 256) and res["k3_block"] in (64, 128, 256) and not res["cached"]
+    assert all(t >= 0 for t in res["ms"]) and min(res["ms"]) > 0
+    after = sim.coeffs(p).cpu().numpy()
+    assert coef_err(after, before) < 1e-13       # only the summation grouping may change
+    sim2 = make(scf, wl.nmax, wl.lmax, wl.b, n=wl.n, host=wl.host)
+    res2 = sim2.autotune(p, com=c)
+    assert res2["cached"] and sim2.tiles() == sim.tiles()
