@@ -82,6 +82,9 @@ def _load():
         "or_field": (None, [i64, p, p, i, i, d, d, p]),
         "or_host_accel": (None, [p, p, p, p]),
         "or_tidal": (None, [p, p, p, p]),
+        "or_tidal_tensor": (None, [p, i64, p, p]),
+        "or_host_accel_many": (None, [p, i64, p, p]),
+        "or_tidal_many": (None, [p, p, i64, p, p]),
         "or_forces": (None, [i64, p, p, p, p, i, i, d, d, p]),
         "or_step": (None, [i64, p, p, p, p, p, i, i, d, d, d, i, p, p]),
         "or_direct": (None, [i64, p, i64, p, d, p]),
@@ -211,6 +214,31 @@ def tidal(host, R, x):
     x = _f64(x)
     a = np.zeros(3)
     _load().or_tidal(ctypes.byref(host), _ptr(R), _ptr(x), _ptr(a))
+    return a
+
+
+def tidal_tensor(host, P):
+    """Tidal tensors d a_host / dx (App. A) at points ``P`` (n, 3) -> (n, 3, 3)."""
+    P = _f64(np.atleast_2d(P))
+    T = np.zeros((P.shape[0], 3, 3))
+    _load().or_tidal_tensor(ctypes.byref(host), P.shape[0], _ptr(P), _ptr(T))
+    return T
+
+
+def host_accel_many(host, P):
+    """Host acceleration at points ``P`` (n, 3) -> (n, 3)."""
+    P = _f64(np.atleast_2d(P))
+    a = np.zeros((P.shape[0], 3))
+    _load().or_host_accel_many(ctypes.byref(host), P.shape[0], _ptr(P), _ptr(a))
+    return a
+
+
+def tidal_many(host, R, pos):
+    """a_host(R + x_k) - a_host(R) for particles ``pos`` (n, 4) -> (n, 3)."""
+    R = _f64(R)[:3].copy()
+    pos = _f64(pos)
+    a = np.zeros((pos.shape[0], 3))
+    _load().or_tidal_many(ctypes.byref(host), _ptr(R), pos.shape[0], _ptr(pos), _ptr(a))
     return a
 
 

@@ -388,6 +388,104 @@ void or_tidal(const or_host* h, const double* R, const double* x, double* a) {
   for (int i = 0; i < 3; ++i) a[i] = (double)(ap[i] - aq[i]);
 }
 
+/* Tidal tensor T_ij = d a_i / d x_j of the host at x (App. A), long double.
+ * Spherical components (Hernquist, NFW): a = f_r(r) x/r, so
+ *   T = (f_r/r) (I - n n^T) + (d f_r/dr) n n^T,
+ * with, from App. A,
+ *   Hernquist: f_r = -GM/(r+a)^2,            d f_r/dr = 2GM/(r+a)^3
+ *              (the printed 2GM (r/a)^3 / (r^3 (1+r/a)^3) is the same),
+ *   NFW:       f_r = -GM g(u)/r^2, u = r/r_s, d f_r/dr = (2GM g/r^3) (1 - u^2 / (2 g (1+u)^2)).
+ * Miyamoto-Nagai (cylindrical R, z; z_ab = sqrt(z^2+b^2) + a, D^2 = R^2 + z_ab^2):
+ *   f_R = -GM R/D^3,  f_z = -GM z z_ab/(sqrt(z^2+b^2) D^3),
+ *   d f_R/dR = 3GM R^2/D^5 - GM/D^3,
+ *   d f_R/dz = d f_z/dR = 3GM z R z_ab/(sqrt(z^2+b^2) D^5),
+ *   d f_z/dz = 3GM z^2 z_ab^2/((z^2+b^2) D^5) - GM z^2/((z^2+b^2) D^3)
+ *              + GM z^2 z_ab/((z^2+b^2)^(3/2) D^3) - GM z_ab/(sqrt(z^2+b^2) D^3),
+ * and a_x = f_R x/R, a_y = f_R y/R, a_z = f_z give the Cartesian entries
+ *   T_xx = f_R'' x^2/R^2 + (f_R/R) y^2/R^2   (f_R'' = d f_R/dR), T_xy = (f_R'' - f_R/R) x y/R^2,
+ *   T_xz = (d f_R/dz) x/R, T_zz = d f_z/dz, and the symmetric counterparts,
+ * where f_R/R = -GM/D^3 and (d f_R/dz)/R stay finite on the axis. */
+static void tidal_tensor_l(const or_host* h, const long double* x, long double* T) {
+  for (int i = 0; i < 9; ++i) T[i] = 0;
+  const long double r2 = x[0] * x[0] + x[1] * x[1] + x[2] * x[2];
+  const long double r = sqrtl(r2);
+  for (int i = 0; i < h->n; ++i) {
+    const or_host_comp* c = &h->c[i];
+    const long double GM = (long double)h->G * c->M;
+    if (c->kind == OR_HOST_HERNQUIST || c->kind == OR_HOST_NFW) {
+      if (!(r > 0)) continue;
+      long double fr, dfr;
+      if (c->kind == OR_HOST_HERNQUIST) {
+        const long double ra = r + c->a;
+        fr = -GM / (ra * ra);
+        dfr = 2 * GM / (ra * ra * ra);
+      } else {
+        const long double u = r / c->a;
+        const long double g = log1pl(u) - u / (1 + u);
+        fr = -GM * g / r2;
+        dfr = 2 * GM * g / (r2 * r) * (1 - u * u / (2 * g * (1 + u) * (1 + u)));
+      }
+      const long double n[3] = {x[0] / r, x[1] / r, x[2] / r};
+      for (int a = 0; a < 3; ++a)
+        for (int b = 0; b < 3; ++b) T[3 * a + b] += (fr / r) * ((a == b) - n[a] * n[b]) + dfr * n[a] * n[b];
+    } else if (c->kind == OR_HOST_MN) {
+      const long double A = c->a, B = c->b;
+      const long double R2 = x[0] * x[0] + x[1] * x[1];
+      const long double z = x[2];
+      const long double zb2 = z * z + B * B, zb = sqrtl(zb2);
+      const long double zab = zb + A;
+      const long double D2 = R2 + zab * zab, D = sqrtl(D2), D3 = D2 * D, D5 = D3 * D2;
+      const long double fR_over_R = -GM / D3;
+      const long double dfRdR = 3 * GM * R2 / D5 - GM / D3;
+      const long double dfRdz_over_R = 3 * GM * z * zab / (zb * D5);
+      const long double dfzdz = 3 * GM * z * z * zab * zab / (zb2 * D5) - GM * z * z / (zb2 * D3) +
+                                GM * z * z * zab / (zb2 * zb * D3) - GM * zab / (zb * D3);
+      /* T_xx = dfRdR x^2/R^2 + (f_R/R) y^2/R^2 etc.; on the axis (R = 0) the
+       * horizontal block is (f_R/R) I, since dfRdR -> f_R/R there */
+      long double cxx, cyy, cxy;
+      if (R2 > 0) {
+        cxx = (dfRdR * x[0] * x[0] + fR_over_R * x[1] * x[1]) / R2;
+        cyy = (dfRdR * x[1] * x[1] + fR_over_R * x[0] * x[0]) / R2;
+        cxy = (dfRdR - fR_over_R) * x[0] * x[1] / R2;
+      } else {
+        cxx = cyy = fR_over_R;
+        cxy = 0;
+      }
+      T[0] += cxx;
+      T[4] += cyy;
+      T[1] += cxy;
+      T[3] += cxy;
+      T[2] += dfRdz_over_R * x[0];
+      T[6] += dfRdz_over_R * x[0];
+      T[5] += dfRdz_over_R * x[1];
+      T[7] += dfRdz_over_R * x[1];
+      T[8] += dfzdz;
+    }
+  }
+}
+
+/* Tidal tensors at n points P = [n][3] into T = [n][9] (row-major). */
+void or_tidal_tensor(const or_host* h, int64_t n, const double* P, double* T) {
+#pragma omp parallel for schedule(static)
+  for (int64_t k = 0; k < n; ++k) {
+    long double x[3] = {P[3 * k], P[3 * k + 1], P[3 * k + 2]}, t[9];
+    tidal_tensor_l(h, x, t);
+    for (int i = 0; i < 9; ++i) T[9 * k + i] = (double)t[i];
+  }
+}
+
+/* Host acceleration at n points P = [n][3] into a = [n][3]. */
+void or_host_accel_many(const or_host* h, int64_t n, const double* P, double* a) {
+#pragma omp parallel for schedule(static)
+  for (int64_t k = 0; k < n; ++k) or_host_accel(h, P + 3 * k, a + 3 * k, NULL);
+}
+
+/* Tidal accelerations a_host(R + x_k) - a_host(R) for particles pos = [n][4]. */
+void or_tidal_many(const or_host* h, const double* R, int64_t n, const double* pos, double* a) {
+#pragma omp parallel for schedule(static)
+  for (int64_t k = 0; k < n; ++k) or_tidal(h, R, pos + 4 * k, a + 3 * k);
+}
+
 /* acc = -grad psi_SCF (coefficients A) + tidal term (host may be NULL). */
 void or_forces(int64_t n_part, const double* pos, const double* A, const double* com, const or_host* host, int nmax,
                int lmax, double b, double G, double* acc) {
