@@ -68,6 +68,7 @@ extern "C" {
 #define SCF_ERR_OUT_OF_MEMORY (-6) /* workspace allocation failed in scf_init */
 #define SCF_ERR_DEVICE_STATUS (-7) /* scf_status found device-side problems */
 #define SCF_ERR_TOO_LARGE (-8)     /* the problem does not fit the static scratch of scf_coeffs_noalloc */
+#define SCF_ERR_ADJOINT_FP64 (-9)  /* scf_adjoint_level called on a mixed-precision handle */
 
 /* ---- device status bits (scf_status) ---- */
 #define SCF_STATUS_NONFINITE_POS 1 /* a particle position was NaN/Inf; it was skipped */
@@ -180,6 +181,44 @@ int scf_get_option(const scf_handle* h, int option, int* value);
  * Errors: SCF_ERR_NULL_POINTER, SCF_ERR_MISALIGNED, SCF_ERR_INVALID_ARG
  * (reps < 1), SCF_ERR_CUDA. */
 int scf_autotune(scf_handle* h, const void* pos, const double* com, void* acc, int reps, double* ms_out);
+
+/* One level of the reverse (adjoint) sweep through scf_step, in double
+ * precision.  Differentiates the kick-drift-kick of Sec. 2.1, with
+ *   a_k(x, R) = f(x_k; A(x)) + a_host(R + x_k) - a_host(R),
+ * A(x) the coefficients of Eq. 3b (every particle's mass m_k = pos.w
+ * counted, no mask) and the centre (R, V) stepped by the host alone.
+ * Let a forward run hold states x_t, com_t (t = 0..T, after t calls of
+ * scf_step with one step each).  Reverse sweep, for t = T down to 0:
+ *   scf_adjoint_level(h, x_t, com_t, w_t, t > 0, xbar, vbar, combar, thetabar)
+ * with w_T = w_0 = dt/2 and w_t = dt otherwise (a(x_t) enters the closing
+ * kick of step t and the opening kick of step t+1).  Before the first call
+ * xbar, vbar, combar hold dL/dx_T, dL/dv_T, dL/d(R_T, V_T) and thetabar 0;
+ * after the last call they hold dL/dx_0, dL/dv_0, dL/d(R_0, V_0) and
+ * dL/d(GM_c, a_c).  One call does, with d_k = w_t vbar_k:
+ *   xbar_k += (da_k/dx_k)^T d_k      (Hessian of the expansion potential at
+ *                                     fixed coefficients, plus T(R + x_k) d_k),
+ *   xbar_k += m_k f(x_k; A^J),  A^J = sum_i (dB(x_i)/dx_i) d_i   (through A),
+ *   Rbar += sum_k (T(R + x_k) - T(R)) d_k + w_t T(R) Vbar,
+ *   thetabar += the same pull-back through the host parameters,
+ * then, if drift != 0, undoes the drift: vbar += dt xbar, Vbar += dt Rbar.
+ * T is the host's tidal tensor (the Jacobian of a_host).
+ *   pos       device [N][4] doubles, x_t with masses (as for scf_step).
+ *   com       device [n_prog][6], (R_t, V_t); NULL allowed without host.
+ *   weight    w_t;  drift  0 at t = 0, else 1.
+ *   xbar, vbar  device [N][4] doubles, updated (4th component untouched).
+ *   combar    device [n_prog][6] doubles (Rbar, Vbar), updated.
+ *   thetabar  device [n_prog][2*n_host] doubles, per progenitor and host
+ *             component c: (dL/dGM_c, dL/da_c) accumulated, with GM_c = G M_c
+ *             and a_c the scale length of App. A (NFW r_s, Hernquist a,
+ *             Miyamoto-Nagai a); summing over progenitors is the caller's.
+ * Derivatives are exact up to rounding (dual numbers in the kernels); at a
+ * particle exactly at r = 0 the own-position term of l = 1 is taken as 0.
+ * Overwrites the handle's coefficient buffer (scf_last_coeffs) and the
+ * captured step graph.  Launches 6 kernels (5 without host components).
+ * Errors: SCF_ERR_ADJOINT_FP64, SCF_ERR_NULL_POINTER, SCF_ERR_MISALIGNED,
+ * SCF_ERR_INVALID_ARG (weight not finite), SCF_ERR_UNSUPPORTED, SCF_ERR_CUDA. */
+int scf_adjoint_level(scf_handle* h, const void* pos, const double* com, double weight, int drift, void* xbar,
+                      void* vbar, double* combar, double* thetabar);
 
 /* Copies (device to device, on the handle's stream) the coefficients used by
  * the last force evaluation of scf_step into A_out ([n_prog][2*NC] doubles). */

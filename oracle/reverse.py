@@ -107,7 +107,6 @@ def level(x, R, V_bar, d, w, nmax, lmax, b, G=1.0, host_components=()):
     the increments of xbar (n, 3), of Rbar (3,), and of the host-parameter
     adjoint (n_host, 2) = (d/dGM_c, d/da_c); V_bar is the centre's velocity
     adjoint at this level."""
-    n = x.shape[0]
     A = coeffs(x, nmax, lmax, b)
     dx = jvp_field(x, A, d, nmax, lmax, b, G)                       # own position
     AJ = jvp_coeffs(x, d, nmax, lmax, b)
@@ -120,10 +119,8 @@ def level(x, R, V_bar, d, w, nmax, lmax, b, G=1.0, host_components=()):
         TP = tidal_tensor(host, P)
         TR = tidal_tensor(host, R[:3])[0]
         dx += np.einsum("kij,kj->ki", TP, d)
-        u = w * V_bar - d.sum(axis=0)
         dR = np.einsum("kij,kj->i", TP - TR[None], d) + w * TR @ V_bar
         for c, comp in enumerate(host_components):
-            GM = G * comp[1]
             one = _single(comp, G, M=1.0 / G)                        # the component with GM = 1
             dth[c, 0] = np.sum(d * tidal_many(one, R, x)) + w * host_accel_many(one, R[:3])[0] @ V_bar
 
@@ -133,8 +130,6 @@ def level(x, R, V_bar, d, w, nmax, lmax, b, G=1.0, host_components=()):
 
             da = 1e-3 * comp[2]
             dth[c, 1] = sum(cf * D(comp[2] + j * da) for j, cf in _FD) / (12.0 * da)
-            del GM
-        del u
     return dx, dR, dth
 
 

@@ -33,12 +33,13 @@ ERRORS = {
     -6: "SCF_ERR_OUT_OF_MEMORY",
     -7: "SCF_ERR_DEVICE_STATUS",
     -8: "SCF_ERR_TOO_LARGE",
+    -9: "SCF_ERR_ADJOINT_FP64",
 }
 
 # every symbol include/scf.h declares
 EXPORTS = ["scf_init", "scf_coeffs", "scf_forces", "scf_step", "scf_last_coeffs", "scf_status",
            "scf_launches_per_call", "scf_profile", "scf_profile_read", "scf_coeffs_noalloc", "scf_set_option",
-           "scf_get_option", "scf_autotune", "scf_free", "scf_strerror"]
+           "scf_get_option", "scf_autotune", "scf_adjoint_level", "scf_free", "scf_strerror"]
 SCF_OPT_GRAPHS = 1
 SCF_OPT_K1_TILE = 2
 SCF_OPT_K3_BLOCK = 3
@@ -91,6 +92,7 @@ def load(build: bool = True) -> ctypes.CDLL:
     lib.scf_set_option.argtypes = [vp, i, i]
     lib.scf_get_option.argtypes = [vp, i, ctypes.POINTER(i)]
     lib.scf_autotune.argtypes = [vp, vp, vp, vp, i, dp]
+    lib.scf_adjoint_level.argtypes = [vp, vp, vp, ctypes.c_double, i, vp, vp, vp, vp]
     lib.scf_free.argtypes = [vp]
     lib.scf_strerror.argtypes = [i]
     lib.scf_strerror.restype = ctypes.c_char_p
@@ -209,6 +211,15 @@ def scf_autotune(h, pos, com, acc, reps: int = 5):
     ms = (ctypes.c_double * 6)()
     _check(load().scf_autotune(h, _ptr(pos), _ptr(com, torch.float64), _ptr(acc), int(reps), ms), "scf_autotune")
     return list(ms)
+
+
+def scf_adjoint_level(h, pos, com, weight: float, drift: bool, xbar, vbar, combar, thetabar):
+    """One level of the reverse sweep (see include/scf.h)."""
+    import torch
+    f64 = torch.float64
+    _check(load().scf_adjoint_level(h, _ptr(pos, f64), _ptr(com, f64), float(weight), 1 if drift else 0,
+                                    _ptr(xbar, f64), _ptr(vbar, f64), _ptr(combar, f64), _ptr(thetabar, f64)),
+           "scf_adjoint_level")
 
 
 def scf_free(h):

@@ -48,6 +48,11 @@ struct scf_handle {
   bool graphs = true;
   cudaGraphExec_t step_exec = nullptr;
   const void* step_key[4] = {nullptr, nullptr, nullptr, nullptr};
+  // adjoint: per-block tidal partials (double-precision handles only) and
+  // the dual kernels' launch shapes (set by the first scf_adjoint_level call)
+  double* d_adj_part = nullptr;       // [k3 blocks][SCF_ADJ_Q]
+  ScfLaunchInfo k1d{}, k3d{};
+  bool adj_ready = false;
   // launch timing (scf_profile)
   bool prof_on = false;
   std::vector<cudaEvent_t> prof_ev;   // pairs (start, stop)
@@ -69,8 +74,9 @@ int upload_tables_once(int device) {
   scf_make_const(t);
   cudaError_t e1 = scf_upload_const_coeffs(t);
   cudaError_t e2 = scf_upload_const_forces(t);
+  cudaError_t e3 = scf_upload_const_adjoint(t);
   delete t;
-  if (e1 != cudaSuccess || e2 != cudaSuccess) return SCF_ERR_CUDA;
+  if (e1 != cudaSuccess || e2 != cudaSuccess || e3 != cudaSuccess) return SCF_ERR_CUDA;
   g_const_ready[device] = true;
   return SCF_OK;
 }
@@ -398,6 +404,7 @@ int scf_init(const scf_config* cfg, int n_prog, const int64_t* offsets, const do
   const size_t o_b3b = take(sizeof(int64_t) * nb3);
   const size_t o_b3e = take(sizeof(int64_t) * nb3);
   const size_t o_st = take(sizeof(unsigned) * 4);
+  const size_t o_adj = cfg->precision == SCF_FP64 ? take(sizeof(double) * SCF_ADJ_Q * nb3) : off;
   if (cudaMalloc(&h->d_base, off) != cudaSuccess) {
     cudaGetLastError();
     return fail(SCF_ERR_OUT_OF_MEMORY);
@@ -417,6 +424,7 @@ int scf_init(const scf_config* cfg, int n_prog, const int64_t* offsets, const do
   h->d_blk3_begin = reinterpret_cast<int64_t*>(base + o_b3b);
   h->d_blk3_end = reinterpret_cast<int64_t*>(base + o_b3e);
   h->d_status = reinterpret_cast<unsigned*>(base + o_st);
+  if (cfg->precision == SCF_FP64) h->d_adj_part = reinterpret_cast<double*>(base + o_adj);
 
   std::vector<double> norm(2 * (size_t)h->nc);
   scf_make_norm(cfg->nmax, cfg->lmax, norm.data());
@@ -594,6 +602,75 @@ int scf_autotune(scf_handle* h, const void* pos, const double* com, void* acc, i
   return rc;
 }
 
+int scf_adjoint_level(scf_handle* h, const void* pos, const double* com, double weight, int drift, void* xbar,
+                      void* vbar, double* combar, double* thetabar) {
+  if (!h) return SCF_ERR_NULL_POINTER;
+  if (h->cfg.precision != SCF_FP64) return SCF_ERR_ADJOINT_FP64;
+  if ((!pos || !xbar || !vbar) && h->n_total > 0) return SCF_ERR_NULL_POINTER;
+  if (h->host.n > 0 && (!com || !combar || !thetabar)) return SCF_ERR_NULL_POINTER;
+  if (!aligned16(pos) || !aligned16(xbar) || !aligned16(vbar)) return SCF_ERR_MISALIGNED;
+  if (!std::isfinite(weight)) return SCF_ERR_INVALID_ARG;
+  if (h->n_total == 0) return SCF_OK;
+  if (!h->adj_ready) {
+    int bps = 0;
+    if (scf_k1_dual_prepare(h->cfg.lmax, h->cfg.nmax, &h->k1d, &bps) != cudaSuccess || bps < 1 ||
+        scf_k3_dual_prepare(h->cfg.lmax, h->cfg.nmax, &h->k3d, &bps) != cudaSuccess || bps < 1) {
+      cudaGetLastError();
+      return SCF_ERR_UNSUPPORTED;
+    }
+    h->adj_ready = true;
+  }
+  drop_graph(h);  // the sweep rewrites the force coefficients a captured step reads
+  void* p = const_cast<void*>(pos);
+  const bool host = h->host.n > 0;
+  AdjArgs adj{};
+  adj.xbar = xbar;
+  adj.vbar = vbar;
+  adj.weight = weight;
+  adj.drift = drift ? 1 : 0;
+  adj.part = h->d_adj_part;
+  // 1. coefficients and force coefficients at x_t
+  int rc = run_coeffs(h, p, nullptr, nullptr, nullptr, h->d_A, nullptr, SCF_MODE_COEFFS);
+  if (rc != SCF_OK) return rc;
+  // 2. own-position term and tidal partials (dual numbers)
+  if (h->k3_blocks > 0) {
+    K3Args a = k3_args(h, pos, nullptr, nullptr, host ? com : nullptr, SCF_MODE_ADJ_DUAL);
+    a.adj = adj;
+    if (scf_k3_dual_launch(a, h->k3_blocks, h->k3d, h->stream) != cudaSuccess) return SCF_ERR_CUDA;
+  }
+  // 3. centre orbit and host parameters
+  if (host) {
+    ComAdjArgs c{};
+    c.part = h->d_adj_part;
+    c.blk3_prog = h->d_blk3_prog;
+    c.n_blocks = h->k3_blocks;
+    c.com = com;
+    c.combar = combar;
+    c.thetabar = thetabar;
+    c.n_prog = h->n_prog;
+    c.weight = weight;
+    c.dt = h->cfg.dt;
+    c.drift = adj.drift;
+    c.host = h->host;
+    if (scf_com_adj_launch(c, h->stream) != cudaSuccess) return SCF_ERR_CUDA;
+  }
+  // 4. A^J = sum_i d_i . grad B(x_i) (dual numbers, unit weights), normalised by kernel 2
+  if (h->k1_blocks > 0) {
+    K1Args a = k1_args(h, p, nullptr, nullptr, nullptr, SCF_MODE_ADJ_DUAL);
+    a.adj = adj;
+    if (scf_k1_dual_launch(a, h->k1_blocks, h->k1d, h->stream) != cudaSuccess) return SCF_ERR_CUDA;
+  }
+  K2Args b = k2_args(h, h->d_A, nullptr, SCF_MODE_COEFFS);
+  if (scf_k2_launch(b, h->stream) != cudaSuccess) return SCF_ERR_CUDA;
+  // 5. xbar_k += m_k f(x_k; A^J), then the drift is undone
+  if (h->k3_blocks > 0) {
+    K3Args a = k3_args(h, pos, nullptr, nullptr, nullptr, SCF_MODE_ADJ_J);
+    a.adj = adj;
+    if (scf_k3_launch(SCF_FP64, a, h->k3_blocks, h->k3, h->stream) != cudaSuccess) return SCF_ERR_CUDA;
+  }
+  return SCF_OK;
+}
+
 int scf_last_coeffs(scf_handle* h, double* A_out) {
   if (!h || !A_out) return SCF_ERR_NULL_POINTER;
   return cuda_fail(cudaMemcpyAsync(A_out, h->d_A, sizeof(double) * 2 * (size_t)h->nc * h->n_prog,
@@ -681,6 +758,7 @@ const char* scf_strerror(int code) {
     case SCF_ERR_CUDA: return "CUDA runtime error";
     case SCF_ERR_OUT_OF_MEMORY: return "workspace allocation failed";
     case SCF_ERR_DEVICE_STATUS: return "device reported non-finite particle data";
+    case SCF_ERR_ADJOINT_FP64: return "the adjoint needs a double-precision (SCF_FP64) handle";
     case SCF_ERR_TOO_LARGE: return "problem exceeds the static scratch of scf_coeffs_noalloc (2*NC > SCF_NOALLOC_MAX_COEFS)";
     default: return "unknown error code";
   }

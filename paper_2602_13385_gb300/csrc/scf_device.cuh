@@ -56,6 +56,40 @@ struct ScfHostParams {
   double GM[SCF_HOST_CAP], a[SCF_HOST_CAP], b[SCF_HOST_CAP];
 };
 
+// Forward-mode dual number (value, derivative) in double precision: the
+// adjoint kernels evaluate the same formulas on duals to get exact
+// directional derivatives (Hessian-vector products) of the expansion and of
+// the host potential.
+struct Dual {
+  double v, d;
+  __host__ __device__ Dual() : v(0.0), d(0.0) {}
+  __host__ __device__ Dual(double x) : v(x), d(0.0) {}
+  __host__ __device__ Dual(double x, double dx) : v(x), d(dx) {}
+};
+__host__ __device__ inline Dual operator+(Dual a, Dual b) { return Dual(a.v + b.v, a.d + b.d); }
+__host__ __device__ inline Dual operator-(Dual a, Dual b) { return Dual(a.v - b.v, a.d - b.d); }
+__host__ __device__ inline Dual operator-(Dual a) { return Dual(-a.v, -a.d); }
+__host__ __device__ inline Dual operator*(Dual a, Dual b) { return Dual(a.v * b.v, a.d * b.v + a.v * b.d); }
+__host__ __device__ inline Dual operator/(Dual a, Dual b) {
+  const double q = a.v / b.v;
+  return Dual(q, (a.d - q * b.d) / b.v);
+}
+__host__ __device__ inline Dual operator*(Dual a, double b) { return Dual(a.v * b, a.d * b); }
+__host__ __device__ inline Dual operator*(double a, Dual b) { return Dual(a * b.v, a * b.d); }
+__host__ __device__ inline Dual& operator+=(Dual& a, Dual b) { return a = a + b; }
+__host__ __device__ inline Dual& operator-=(Dual& a, Dual b) { return a = a - b; }
+__host__ __device__ inline Dual& operator*=(Dual& a, Dual b) { return a = a * b; }
+__host__ __device__ inline bool operator>(Dual a, Dual b) { return a.v > b.v; }
+__host__ __device__ inline bool operator<(Dual a, Dual b) { return a.v < b.v; }
+__device__ inline Dual sqrt(Dual a) {
+  const double s = ::sqrt(a.v);
+  return Dual(s, s > 0.0 ? 0.5 * a.d / s : 0.0);
+}
+__device__ inline Dual log1p(Dual a) { return Dual(::log1p(a.v), a.d / (1.0 + a.v)); }
+__device__ inline bool isfinite(Dual a) { return ::isfinite(a.v) && ::isfinite(a.d); }
+__device__ inline double value_of(Dual a) { return a.v; }
+__device__ inline double value_of(double a) { return a; }
+
 // Four doubles with the 16-byte alignment the ABI promises for particle arrays.
 struct __align__(16) ScfD4 {
   double x, y, z, w;
@@ -67,41 +101,58 @@ __host__ __device__ constexpr int scf_lm(int l, int m) { return l * (l + 1) / 2 
 //   Hernquist: f_r = -GM/(r+a)^2;  NFW: f_r = -GM [ln(1+u) - u/(1+u)]/r^2, u = r/r_s;
 //   Miyamoto-Nagai: f_R = -GM R/D^3, f_z = -GM z z_ab/(sqrt(z^2+b^2) D^3),
 //   z_ab = sqrt(z^2+b^2) + a, D^2 = R^2 + z_ab^2.
+// One host component's acceleration; N is double or Dual (for derivatives).
+template <typename N>
+__device__ __forceinline__ void scf_host_comp_accel(int kind, N GM, N A, N B, N x, N y, N z, N& ax, N& ay, N& az) {
+  ax = N(0.0);
+  ay = N(0.0);
+  az = N(0.0);
+  if (kind == 1 || kind == 2) {
+    const N r2 = x * x + y * y + z * z;
+    if (!(r2 > N(0.0))) return;
+    const N r = sqrt(r2);
+    const N rinv = N(1.0) / r;
+    N f;
+    if (kind == 1) {  // Hernquist
+      const N ra = r + A;
+      f = -GM / (ra * ra) * rinv;
+    } else {  // NFW
+      const N u = r / A;
+      const N g = log1p(u) - u / (N(1.0) + u);
+      f = -GM * g * rinv * rinv * rinv;
+    }
+    ax = f * x;
+    ay = f * y;
+    az = f * z;
+  } else if (kind == 3) {  // Miyamoto-Nagai
+    const N zb = sqrt(z * z + B * B);
+    const N zab = zb + A;
+    const N D2 = x * x + y * y + zab * zab;
+    const N D3 = D2 * sqrt(D2);
+    const N f = -GM / D3;
+    ax = f * x;
+    ay = f * y;
+    az = f * z * zab / zb;
+  }
+}
+
+template <typename N>
+__device__ __forceinline__ void scf_host_accel_t(const ScfHostParams& hp, N x, N y, N z, N& ax, N& ay, N& az) {
+  ax = N(0.0);
+  ay = N(0.0);
+  az = N(0.0);
+  for (int i = 0; i < hp.n; ++i) {
+    N cx, cy, cz;
+    scf_host_comp_accel<N>(hp.kind[i], N(hp.GM[i]), N(hp.a[i]), N(hp.b[i]), x, y, z, cx, cy, cz);
+    ax += cx;
+    ay += cy;
+    az += cz;
+  }
+}
+
 __device__ __forceinline__ void scf_host_accel(const ScfHostParams& hp, double x, double y, double z, double& ax,
                                                double& ay, double& az) {
-  ax = 0.0;
-  ay = 0.0;
-  az = 0.0;
-  const double r2 = x * x + y * y + z * z;
-  const double r = sqrt(r2);
-  const double rinv = r > 0.0 ? 1.0 / r : 0.0;
-  for (int i = 0; i < hp.n; ++i) {
-    const double GM = hp.GM[i], A = hp.a[i];
-    if (hp.kind[i] == 1) {  // Hernquist
-      const double ra = r + A;
-      const double f = -GM / (ra * ra) * rinv;
-      ax += f * x;
-      ay += f * y;
-      az += f * z;
-    } else if (hp.kind[i] == 2) {  // NFW
-      const double u = r / A;
-      const double g = log1p(u) - u / (1.0 + u);
-      const double f = -GM * g * rinv * rinv * rinv;
-      ax += f * x;
-      ay += f * y;
-      az += f * z;
-    } else if (hp.kind[i] == 3) {  // Miyamoto-Nagai
-      const double B = hp.b[i];
-      const double zb = sqrt(z * z + B * B);
-      const double zab = zb + A;
-      const double D2 = x * x + y * y + zab * zab;
-      const double D3 = D2 * sqrt(D2);
-      const double f = -GM / D3;
-      ax += f * x;
-      ay += f * y;
-      az += f * z * zab / zb;
-    }
-  }
+  scf_host_accel_t<double>(hp, x, y, z, ax, ay, az);
 }
 
 // Tidal acceleration a_host(R + x) - a_host(R) in single precision, written

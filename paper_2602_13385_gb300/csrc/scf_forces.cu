@@ -195,6 +195,27 @@ __global__ void __launch_bounds__(K3_TB) k3_forces(K3Args a) {
   }
   out.w = pot;
   if (!(isfinite(out.x) && isfinite(out.y) && isfinite(out.z))) atomicOr(a.status, 2u);
+  if constexpr (sizeof(T) == 8) {
+    if (a.mode == SCF_MODE_ADJ_J) {
+      // adjoint through the coefficients: F holds the field of A^J, so
+      // xbar_k += m_k f(x_k; A^J); then the drift x_t = x_{t-1} + dt v is undone
+      ScfD4* xb = reinterpret_cast<ScfD4*>(a.adj.xbar) + k;
+      ScfD4 X = *xb;
+      X.x += p.w * out.x;
+      X.y += p.w * out.y;
+      X.z += p.w * out.z;
+      *xb = X;
+      if (a.adj.drift) {
+        ScfD4* vb = reinterpret_cast<ScfD4*>(a.adj.vbar) + k;
+        ScfD4 V = *vb;
+        V.x += a.dt * X.x;
+        V.y += a.dt * X.y;
+        V.z += a.dt * X.z;
+        *vb = V;
+      }
+      return;
+    }
+  }
   reinterpret_cast<V4*>(a.acc)[k] = out;
   if (a.mode == SCF_MODE_STEP) {
     V4* vel4 = reinterpret_cast<V4*>(a.vel);

@@ -7,7 +7,29 @@
 
 #include "scf_device.cuh"
 
-enum ScfMode { SCF_MODE_COEFFS = 0, SCF_MODE_STEP = 1 };
+enum ScfMode {
+  SCF_MODE_COEFFS = 0,   // plain evaluation
+  SCF_MODE_STEP = 1,     // with the leapfrog kick (and drift in kernel 1)
+  SCF_MODE_ADJ_J = 2,    // kernel 3 (double): xbar += m f(x; J), then vbar += dt xbar
+  SCF_MODE_ADJ_DUAL = 3  // dual numbers along d = weight * vbar (scf_adjoint.cu)
+};
+
+// Adjoint state of the particles used by the adjoint modes.  At level t of the
+// reverse sweep the acceleration a(x_t) is pulled back along d_k = weight * vbar_k
+// (weight = dt/2 at the first and last level, dt in between: a(x_t) feeds the
+// closing kick of step t and the opening kick of step t+1).
+struct AdjArgs {
+  void* xbar;            // [N][4] double, adjoint of positions (updated)
+  void* vbar;            // [N][4] double, adjoint of velocities (read; updated by ADJ_J with drift)
+  double weight;
+  int drift;             // 1: after the pull-back, undo the drift (vbar += dt xbar)
+  double* part;          // kernel 3 dual mode: per-block partial sums [blocks][SCF_ADJ_Q]
+};
+
+// Per-block adjoint partials of the tidal term, over the block's particles k
+// (P_k = R + x_k): sum d_k (3), sum T(P_k) d_k (3), then per host component c
+// sum d_k . a_c(P_k)/GM_c and sum d_k . da_c(P_k)/d(scale length a_c).
+#define SCF_ADJ_Q (6 + 2 * SCF_HOST_CAP)
 
 // Kernel 1: per-block partial sums of the coefficients (optionally after the
 // half kick + drift of a leapfrog step).
@@ -25,6 +47,7 @@ struct K1Args {
   int mode;
   double dt;
   unsigned* status;
+  AdjArgs adj;
 };
 
 // Kernel 2: fixed-order reduction of the partials, normalisation, and the
@@ -78,6 +101,21 @@ struct K3Args {
   double G, dt;
   ScfHostParams host;
   unsigned* status;
+  AdjArgs adj;
+};
+
+// Adjoint of the tidal term and of the centre orbit at one level of the reverse sweep.
+struct ComAdjArgs {
+  const double* part;        // kernel 3 dual-mode partials [blocks][SCF_ADJ_Q]
+  const int* blk3_prog;      // progenitor of each kernel 3 block
+  int n_blocks;
+  const double* com;         // [n_prog][6] centre state at this level
+  double* combar;            // [n_prog][6] adjoint of (R, V), updated
+  double* thetabar;          // [n_prog][2 n_host] adjoint of (GM_c, a_c), accumulated
+  int n_prog;
+  double weight, dt;
+  int drift;
+  ScfHostParams host;
 };
 
 struct ScfLaunchInfo {
@@ -89,9 +127,19 @@ struct ScfLaunchInfo {
 
 void scf_make_norm(int nmax, int lmax, double* norm);
 
+cudaError_t scf_com_adj_launch(const ComAdjArgs& a, cudaStream_t s);
+// Dual-number kernels of the adjoint (double precision).  Both loop over their
+// block's particle range, so they run on the block maps of kernels 1 and 3
+// whatever tile those were built for.
+cudaError_t scf_k1_dual_prepare(int lmax, int nmax, ScfLaunchInfo* info, int* blocks_per_sm);
+cudaError_t scf_k1_dual_launch(const K1Args& a, int blocks, const ScfLaunchInfo& info, cudaStream_t s);
+cudaError_t scf_k3_dual_prepare(int lmax, int nmax, ScfLaunchInfo* info, int* blocks_per_sm);
+cudaError_t scf_k3_dual_launch(const K3Args& a, int blocks, const ScfLaunchInfo& info, cudaStream_t s);
+
 // Each kernel translation unit keeps its own copy of the constant tables.
 cudaError_t scf_upload_const_coeffs(const ScfConst* t);
 cudaError_t scf_upload_const_forces(const ScfConst* t);
+cudaError_t scf_upload_const_adjoint(const ScfConst* t);
 
 // Launch configuration (threads, dynamic shared memory) of each kernel for
 // the given sizes; sets the shared-memory attribute of the instantiation.

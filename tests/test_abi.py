@@ -45,7 +45,7 @@ def test_library_targets_sm103a():
 
 
 def test_strerror_is_static_text(lib):
-    for code in range(0, -8, -1):
+    for code in range(0, -10, -1):
         s = lib.scf_strerror(code)
         assert isinstance(s, bytes) and len(s) > 0
     assert lib.scf_strerror(-99) == b"unknown error code"
@@ -89,4 +89,5 @@ def test_null_handle_is_rejected(lib):
     assert lib.scf_forces(None, None, None, None, None) == -2
     assert lib.scf_step(None, None, None, None, None, 1) == -2
     assert lib.scf_status(None, None) == -2
+    assert lib.scf_adjoint_level(None, None, None, 0.005, 1, None, None, None, None) == -2
     assert lib.scf_free(None) == 0

@@ -1,0 +1,238 @@
+"""The hand-written adjoint (scf_adjoint_level, adjoint.SCFRun) on the GPU.
+
+* One level against the oracle's reverse mode (oracle/reverse.py, itself
+  pinned against finite differences): xbar, vbar, the centre adjoint and the
+  host-parameter adjoint to 1e-8 relative (the oracle takes its directional
+  derivatives by fourth-order differences, good to about 1e-10).
+* The whole checkpointed sweep through SCFRun against the oracle's sweep.
+* Dot-product test <J u, g> = <u, J^T g> with J u from central differences of
+  the GPU's own forward run, along a random direction in one input block at a
+  time (positions, velocities, centre, host parameters).
+* The differentiable workload at full size (King W0 = 6, N = 1e5, eccentric
+  orbit, 500 steps, checkpoints every 50, stream-track loss): the adjoint
+  gradient with respect to M_vir, r_s and the six initial centre coordinates
+  against central differences with h = 1e-4 relative, all in FP64.  The
+  second-order difference quotient itself carries a truncation error of order
+  h^2 times the loss curvature; the largest disagreement measured on a GB300
+  was 3.8e-7 (X_0), the bound is 1e-5.
+"""
+import numpy as np
+import pytest
+
+import workloads
+from oracle import reverse
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def pkg():
+    if not torch.cuda.is_available():
+        pytest.skip("needs a GPU")
+    import paper_2602_13385_gb300 as p
+    return p
+
+
+def cuda64(x):
+    return torch.tensor(np.ascontiguousarray(x), dtype=torch.float64, device="cuda")
+
+
+def rel(a, b):
+    return float(np.max(np.abs(a - b)) / max(np.max(np.abs(b)), 1e-300))
+
+
+def small_case(n, seed, host=True):
+    pos, vel = workloads.plummer(n, seed=seed)
+    b = workloads.basis_scale(workloads.half_mass_radius(pos))
+    wl = workloads.king_eccentric(n=256, seed=5, nsteps=1)
+    comps = list(wl.host) if host else []
+    com = wl.com.copy() if host else np.zeros(6)
+    return pos, vel, com, comps, b
+
+
+@pytest.mark.parametrize("host", [True, False])
+def test_one_level_matches_oracle(pkg, host):
+    from paper_2602_13385_gb300 import _lib
+    nmax, lmax, dt = 8, 4, 0.01
+    pos, _, com, comps, b = small_case(3000, 21, host)
+    rng = np.random.default_rng(3)
+    xbar0 = rng.normal(size=(pos.shape[0], 3))
+    vbar0 = rng.normal(size=(pos.shape[0], 3))
+    combar0 = rng.normal(size=6)
+    w = dt
+    cfg = pkg.Config(nmax=nmax, lmax=lmax, b=b, dt=dt, host=comps)
+    sim = pkg.SCF(cfg, n=pos.shape[0])
+    xb = cuda64(np.c_[xbar0, np.zeros(len(pos))])
+    vb = cuda64(np.c_[vbar0, np.zeros(len(pos))])
+    cb = cuda64(combar0[None])
+    th = torch.zeros((1, max(2 * len(comps), 1)), dtype=torch.float64, device="cuda")
+    _lib.scf_adjoint_level(sim._h, cuda64(pos), cuda64(com[None]) if host else None, w, True, xb, vb,
+                           cb if host else None, th if host else None)
+    assert sim.status() == (0, 0)
+    dx, dR, dth = reverse.level(pos, com, combar0[3:], w * vbar0, w, nmax, lmax, b, 1.0, comps)
+    ref_x = xbar0 + dx
+    ref_v = vbar0 + dt * ref_x
+    got_x = xb.cpu().numpy()[:, :3]
+    got_v = vb.cpu().numpy()[:, :3]
+    print(f"level (host={host}): xbar {rel(got_x - xbar0, dx):.2e}, vbar {rel(got_v, ref_v):.2e}")
+    assert rel(got_x - xbar0, dx) < 1e-8
+    assert rel(got_v, ref_v) < 1e-8
+    assert np.all(xb.cpu().numpy()[:, 3] == 0)
+    if host:
+        ref_R = combar0[:3] + dR
+        ref_V = combar0[3:] + dt * ref_R
+        got_c = cb.cpu().numpy()[0]
+        print(f"  Rbar {rel(got_c[:3] - combar0[:3], dR):.2e}, theta {rel(th.cpu().numpy()[0], dth.ravel()):.2e}")
+        assert rel(got_c[:3] - combar0[:3], dR) < 1e-8
+        assert rel(got_c[3:], ref_V) < 1e-8
+        got_th = th.cpu().numpy()[0].reshape(-1, 2)
+        for c in range(len(comps)):
+            for q in range(2):
+                assert abs(got_th[c, q] - dth[c, q]) < 1e-8 * abs(dth[c, q]) + 1e-15, (c, q)
+
+
+def _linear_loss(out, gx, gv, gc):
+    p, v, c = out
+    return (p[:, :3] * gx).sum() + (v[:, :3] * gv).sum() + (c.reshape(-1) * gc).sum()
+
+
+def test_sweep_matches_oracle(pkg):
+    nmax, lmax, dt, nsteps = 8, 4, 0.01, 6
+    pos, vel, com, comps, b = small_case(2000, 22)
+    rng = np.random.default_rng(4)
+    gx = rng.normal(size=(pos.shape[0], 3))
+    gv = rng.normal(size=(pos.shape[0], 3))
+    gc = rng.normal(size=6)
+    cfg = pkg.Config(nmax=nmax, lmax=lmax, b=b, dt=dt, host=comps)
+    spec = pkg.adjoint.RunSpec(cfg, nsteps=nsteps, checkpoint_every=4)   # segments of 4 and 2 steps
+    p0 = cuda64(pos).requires_grad_()
+    v0 = cuda64(vel).requires_grad_()
+    c0 = cuda64(com).requires_grad_()
+    hp = pkg.adjoint.host_params_of(cfg, "cuda").requires_grad_()
+    L = _linear_loss(pkg.adjoint.run(p0, v0, c0, hp, spec), cuda64(gx), cuda64(gv), cuda64(gc))
+    L.backward()
+    X, C, *_ = reverse.forward(pos, vel, com, nmax, lmax, b, dt, nsteps, 1.0, comps)
+    xb, vb, cb, th = reverse.sweep(X, C, gx, gv, gc, nmax, lmax, b, dt, 1.0, comps)
+    e = {"x0": rel(p0.grad.cpu().numpy()[:, :3], xb), "v0": rel(v0.grad.cpu().numpy()[:, :3], vb),
+         "com0": rel(c0.grad.cpu().numpy(), cb),
+         "M": rel(hp.grad.cpu().numpy()[:, 0], th[:, 0]), "a": rel(hp.grad.cpu().numpy()[:, 1], th[:, 1])}
+    print("sweep vs oracle:", {k: f"{v:.1e}" for k, v in e.items()})
+    assert all(v < 1e-8 for v in e.values()), e
+    assert np.all(p0.grad.cpu().numpy()[:, 3] == 0)
+
+
+@pytest.mark.parametrize("block", ["positions", "velocities", "centre", "host"])
+def test_dot_product_with_forward_differences(pkg, block):
+    """<J u, g> from fourth-order central differences of the GPU forward run
+    equals <u, J^T g> from the adjoint, for a random direction u in one input
+    block at a time.  Each block's step sits where the difference quotient has
+    converged (truncation and rounding both below 1e-9 of the result), found by
+    halving the step; the host block has a far smaller derivative than the
+    loss itself, so rounding limits its difference quotient to about 1e-6."""
+    nmax, lmax, dt, nsteps = 10, 6, 0.01, 20
+    pos, vel, com, comps, b = small_case(4000, 23)
+    rng = np.random.default_rng(5)
+    g = [cuda64(rng.normal(size=(pos.shape[0], 3))), cuda64(rng.normal(size=(pos.shape[0], 3))),
+         cuda64(rng.normal(size=6))]
+    cfg = pkg.Config(nmax=nmax, lmax=lmax, b=b, dt=dt, host=comps)
+    spec = pkg.adjoint.RunSpec(cfg, nsteps=nsteps, checkpoint_every=8)
+    hp0 = pkg.adjoint.host_params_of(cfg, "cuda")
+    zero4 = np.zeros((pos.shape[0], 4))
+    u = {"positions": zero4.copy(), "velocities": zero4.copy(), "centre": np.zeros(6),
+         "host": np.zeros(hp0.shape)}
+    if block in ("positions", "velocities"):
+        u[block][:, :3] = rng.normal(size=(pos.shape[0], 3))
+    elif block == "centre":
+        u[block] = rng.normal(size=6) * np.r_[np.full(3, np.linalg.norm(com[:3])), np.full(3, np.linalg.norm(com[3:]))]
+    else:
+        u[block] = rng.normal(size=hp0.shape) * hp0.cpu().numpy()     # relative perturbation of every parameter
+    step, tol = {"positions": (6e-5 * b, 1e-8), "velocities": (2.5e-4 * b, 1e-8), "centre": (1e-6, 1e-8),
+                 "host": (1e-4, 1e-5)}[block]
+
+    def loss_at(s):
+        with torch.no_grad():
+            out = pkg.adjoint.run(cuda64(pos + s * u["positions"]), cuda64(vel + s * u["velocities"]),
+                                  cuda64(com + s * u["centre"]), hp0 + s * cuda64(u["host"]), spec)
+            return float(_linear_loss(out, *g))
+    jvp = (-loss_at(2 * step) + 8 * loss_at(step) - 8 * loss_at(-step) + loss_at(-2 * step)) / (12 * step)
+    p0 = cuda64(pos).requires_grad_()
+    v0 = cuda64(vel).requires_grad_()
+    c0 = cuda64(com).requires_grad_()
+    hp = hp0.clone().requires_grad_()
+    _linear_loss(pkg.adjoint.run(p0, v0, c0, hp, spec), *g).backward()
+    grad = {"positions": p0.grad, "velocities": v0.grad, "centre": c0.grad, "host": hp.grad}[block]
+    vjp = float((grad * cuda64(u[block])).sum())
+    print(f"dot-product test, {block}: <Ju,g> = {jvp:+.12e}, <u,J^T g> = {vjp:+.12e}, "
+          f"rel {abs(jvp - vjp) / abs(jvp):.1e}")
+    assert abs(jvp - vjp) < tol * abs(jvp)
+
+
+def test_differentiable_workload_full_size(pkg):
+    """King W0 = 6, N = 1e5, eccentric orbit, 500 steps, checkpoints every 50;
+    gradient of the stream-track loss w.r.t. NFW M_vir and r_s and the initial
+    centre (R_0, V_0) against central differences, h = 1e-4 relative."""
+    wl = workloads.king_eccentric()
+    units = wl.units
+    cfg = pkg.Config(nmax=wl.nmax, lmax=wl.lmax, b=wl.b, dt=wl.dt, host=list(wl.host))
+    spec = pkg.adjoint.RunSpec(cfg, nsteps=wl.nsteps, checkpoint_every=50)
+    pos0, vel0 = cuda64(wl.pos), cuda64(wl.vel)
+    com0 = cuda64(wl.com)
+    Mvir0, rs0 = 1e12, 20e3                       # Msun, pc
+    nfw = [i for i, h in enumerate(wl.host) if h[0] == pkg.HOST_NFW][0]
+    hp_base = pkg.adjoint.host_params_of(cfg, "cuda")
+
+    def host_params(Mvir, rs):
+        M = pkg.adjoint.nfw_scale_mass(Mvir, rs) / units.M_msun
+        a = rs / units.rv_pc
+        hp = hp_base.clone()
+        row = torch.stack([M, a]).reshape(1, 2)
+        return torch.cat([hp[:nfw], row, hp[nfw + 1:]])
+
+    # the fixed selection: 1% highest-energy particles at t = 0, nearest track points at t = T
+    sim = pkg.SCF(cfg, n=wl.n)
+    pot0 = sim.forces(pos0, sim.coeffs(pos0), com0[None])[:, 3]
+    sim.close()
+    idx = pkg.adjoint.escaper_set(pot0, vel0)
+    t64 = lambda v: torch.tensor(v, dtype=torch.float64, device="cuda")
+    with torch.no_grad():
+        pT, vT, cT = pkg.adjoint.run(pos0, vel0, com0, host_params(t64(Mvir0), t64(rs0)), spec)
+    track = cuda64(workloads.reference_track(cT[:3].cpu().numpy(), cT[3:].cpu().numpy(), seed=50))
+    assign = pkg.adjoint.nearest_track_point(cT[:3] + pT[idx, :3], track)
+
+    def loss(Mvir, rs, c0):
+        pT, vT, cT = pkg.adjoint.run(pos0, vel0, c0, host_params(Mvir, rs), spec)
+        return pkg.adjoint.stream_track_loss(pT, cT, idx, track, assign)
+
+    Mv = t64(Mvir0).requires_grad_()
+    rs = t64(rs0).requires_grad_()
+    c0 = com0.clone().requires_grad_()
+    L = loss(Mv, rs, c0)
+    L.backward()
+    L = L.detach()
+    grads = [float(Mv.grad), float(rs.grad)] + c0.grad.cpu().tolist()
+    fd = []
+    with torch.no_grad():
+        for j in range(8):
+            if j == 0:
+                h = 1e-4 * Mvir0
+                f = lambda s: float(loss(t64(Mvir0 + s), t64(rs0), com0))
+            elif j == 1:
+                h = 1e-4 * rs0
+                f = lambda s: float(loss(t64(Mvir0), t64(rs0 + s), com0))
+            else:
+                k = j - 2
+                scale = torch.linalg.norm(com0[:3] if k < 3 else com0[3:]).item()
+                h = 1e-4 * scale
+                e = torch.zeros(6, dtype=torch.float64, device="cuda")
+                e[k] = 1.0
+                f = lambda s, e=e: float(loss(t64(Mvir0), t64(rs0), com0 + s * e))
+            fd.append((f(h) - f(-h)) / (2 * h))
+    names = ["M_vir", "r_s", "X0", "Y0", "Z0", "VX0", "VY0", "VZ0"]
+    errs = []
+    for nm, g_, f_ in zip(names, grads, fd):
+        e = abs(g_ - f_) / max(abs(f_), 1e-300)
+        errs.append(e)
+        print(f"  dL/d{nm}: adjoint {g_:+.10e}  central difference {f_:+.10e}  rel {e:.1e}")
+    print(f"loss {L.item():.6e}, {len(idx)} particles, max rel error {max(errs):.1e}")
+    assert max(errs) < 1e-5

@@ -376,6 +376,37 @@ def plummer_eccentric(n: int = 1_000_000, seed: int = 3, nsteps: int = 2000) -> 
     return Workload(f"plummer_n{n}_eccentric", pos, vel, 20, 10, basis_scale(rh), 0.01, nsteps, host, com, units)
 
 
+def king_eccentric(n: int = 100_000, seed: int = 5, nsteps: int = 500) -> Workload:
+    """The differentiable run: King W0 = 6 cluster (1e5 Msun, r_h = 3 pc) on
+    the 5-20 kpc eccentric orbit in the NFW + MN + Hernquist host; nmax = 20,
+    lmax = 8, dt = 0.01, 500 steps (checkpointed every 50 by the caller)."""
+    pos, vel = king(n, 6.0, seed)
+    rh = half_mass_radius(pos)
+    units = Units(1e5, 3.0 / rh)
+    host = host_in_units(galaxy_host_physical(), units)
+    com = _com_from_orbit(_orbit_ics()["eccentric_5_20kpc"], units)
+    return Workload(f"king_w6_n{n}_eccentric", pos, vel, 20, 8, basis_scale(rh), 0.01, nsteps, host, com, units)
+
+
+def reference_track(R, V, n_points: int = 256, half_length: float = 50.0, sigma: float = 2.0, seed: int = 50):
+    """Seeded synthetic reference track for the stream-track loss: ``n_points``
+    points along the direction of motion V through R, spanning
+    +-``half_length`` (length units), each displaced by seeded Gaussian
+    offsets of width ``sigma`` perpendicular to V.  Returns (n_points, 3)."""
+    rng = np.random.default_rng(seed)
+    R = np.asarray(R, dtype=np.float64)[:3]
+    t = np.asarray(V, dtype=np.float64)[:3]
+    t = t / np.linalg.norm(t)
+    e1 = np.cross(t, [0.0, 0.0, 1.0])
+    if np.linalg.norm(e1) < 1e-8:
+        e1 = np.cross(t, [1.0, 0.0, 0.0])
+    e1 /= np.linalg.norm(e1)
+    e2 = np.cross(t, e1)
+    s = np.linspace(-half_length, half_length, n_points)
+    off = rng.normal(0.0, sigma, size=(n_points, 2))
+    return R[None] + s[:, None] * t[None] + off[:, :1] * e1[None] + off[:, 1:] * e2[None]
+
+
 def progenitor_batch(n_prog: int = 10, seed: int = 40, n_range=(2e4, 5e5), nsteps: int = 2000,
                      scale: float = 1.0) -> Workload:
     """Batch of progenitors with N log-uniform in ``n_range`` (times ``scale``)
