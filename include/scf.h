@@ -161,6 +161,12 @@ int scf_step(scf_handle* h, void* pos, void* vel, void* acc, double* com, int ns
  *                     coefficient kernel: 64, 128 (default) or 256.
  *   SCF_OPT_K3_BLOCK  threads per block of the field kernel: 64, 128
  *                     (default) or 256.
+ *   SCF_OPT_K1_VARIANT 0 = the coefficient kernel with one thread per output
+ *                     and SCF_OPT_K1_TILE particles per tile (the double-
+ *                     precision default); 1 = the register-tiled kernel
+ *                     (7 x 8 output tiles per thread over 64-particle
+ *                     tiles; SCF_MIXED only, its default).  Reading
+ *                     SCF_OPT_K1_TILE gives 0 while variant 1 is in use.
  * Setting a tile or block size synchronises the stream and rewrites the block
  * maps in the workspace (sized in scf_init for every allowed value).
  * Errors: SCF_ERR_NULL_POINTER, SCF_ERR_INVALID_ARG (unknown option or value),
@@ -168,16 +174,18 @@ int scf_step(scf_handle* h, void* pos, void* vel, void* acc, double* com, int ns
 #define SCF_OPT_GRAPHS 1
 #define SCF_OPT_K1_TILE 2
 #define SCF_OPT_K3_BLOCK 3
+#define SCF_OPT_K1_VARIANT 4
 int scf_set_option(scf_handle* h, int option, int value);
 int scf_get_option(const scf_handle* h, int option, int* value);
 
 /* Autotuner: times every allowed SCF_OPT_K1_TILE with the coefficient pass
  * and every SCF_OPT_K3_BLOCK with the field pass (2 warm-up + reps timed calls
  * each, CUDA events on the handle's stream) on the caller's particles, and
- * keeps the fastest of each.  pos, com as for scf_forces; acc is overwritten.
- * ms_out (host, nullable) receives the 6 average times in milliseconds
- * (tiles 64, 128, 256 of kernel 1, then blocks 64, 128, 256 of kernel 3; 0 for
- * a size that does not fit).  Synchronises the stream; creates CUDA events.
+ * keeps the fastest of each (in SCF_MIXED the register-tiled kernel 1 is a
+ * fourth candidate).  pos, com as for scf_forces; acc is overwritten.
+ * ms_out (host, nullable) receives 7 average times in milliseconds
+ * (tiles 64, 128, 256 of kernel 1, then blocks 64, 128, 256 of kernel 3, then
+ * the register-tiled kernel 1; 0 for a shape that does not fit or apply).  Synchronises the stream; creates CUDA events.
  * Errors: SCF_ERR_NULL_POINTER, SCF_ERR_MISALIGNED, SCF_ERR_INVALID_ARG
  * (reps < 1), SCF_ERR_CUDA. */
 int scf_autotune(scf_handle* h, const void* pos, const double* com, void* acc, int reps, double* ms_out);

@@ -43,6 +43,7 @@ EXPORTS = ["scf_init", "scf_coeffs", "scf_forces", "scf_step", "scf_last_coeffs"
 SCF_OPT_GRAPHS = 1
 SCF_OPT_K1_TILE = 2
 SCF_OPT_K3_BLOCK = 3
+SCF_OPT_K1_VARIANT = 4
 
 
 class ScfError(RuntimeError):
@@ -205,10 +206,11 @@ def scf_get_option(h, option: int) -> int:
 
 
 def scf_autotune(h, pos, com, acc, reps: int = 5):
-    """Times the allowed tile/block sizes and keeps the fastest; returns the six
-    average times (ms): kernel-1 tiles 64/128/256, kernel-3 blocks 64/128/256."""
+    """Times the allowed kernel shapes and keeps the fastest; returns the seven
+    average times (ms): kernel-1 tiles 64/128/256, kernel-3 blocks 64/128/256,
+    then the register-tiled kernel 1 (0 where a shape does not apply)."""
     import torch
-    ms = (ctypes.c_double * 6)()
+    ms = (ctypes.c_double * 7)()
     _check(load().scf_autotune(h, _ptr(pos), _ptr(com, torch.float64), _ptr(acc), int(reps), ms), "scf_autotune")
     return list(ms)
 

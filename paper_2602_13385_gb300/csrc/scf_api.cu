@@ -21,6 +21,7 @@ struct scf_handle {
   int n_sm = 0;
   std::vector<int64_t> offsets;
   size_t cap_blk1 = 0, cap_blk3 = 0;  // block-map capacity (largest candidate)
+  size_t cap_rows = 0;                 // partial rows of 2*NC 8-byte entries (largest candidate)
   // kernel 1 / 2
   ScfLaunchInfo k1{};
   int k1_blocks = 0;
@@ -170,6 +171,7 @@ K2Args k2_args(scf_handle* h, double* A_out, double* com, int mode) {
   a.dt = h->cfg.dt;
   a.com = com;
   a.host = h->host;
+  a.sub = h->k1.variant == 1 ? h->k1.sub * h->k1.win : 0;
   return a;
 }
 
@@ -281,16 +283,39 @@ bool put(void* dst, const void* src, size_t bytes) {
   return bytes == 0 || cudaMemcpy(dst, src, bytes, cudaMemcpyHostToDevice) == cudaSuccess;
 }
 
-// Selects kernel 1's particle tile: launch info, block map, upload.
-int use_k1(scf_handle* h, int tp) {
-  ScfLaunchInfo info{};
-  int bps = 0;
-  if (scf_k1_prepare(h->cfg.precision, h->cfg.lmax, h->cfg.nmax, tp, &info, &bps) != cudaSuccess || bps < 1) {
+// Kernel 1 launch shape: the simple kernel with a particle tile of 64, 128
+// or 256 (tp), or the register-tiled single-precision kernel (tp = 0).
+int k1_shape(const scf_config& cfg, int tp, ScfLaunchInfo* info, int* bps) {
+  cudaError_t e = tp == 0 ? scf_k1_tiled_prepare(cfg.lmax, cfg.nmax, info, bps)
+                          : scf_k1_prepare(cfg.precision, cfg.lmax, cfg.nmax, tp, info, bps);
+  if (e != cudaSuccess || *bps < 1) {
     cudaGetLastError();
     return SCF_ERR_UNSUPPORTED;
   }
+  return SCF_OK;
+}
+
+// Partial rows in units of 2*NC doubles: one per block, or for the
+// register-tiled kernel sub * win float rows per block (two per double row).
+size_t k1_rows(const ScfLaunchInfo& info, size_t blocks) {
+  return info.variant == 1 ? (blocks * info.sub * info.win + 1) / 2 : blocks;
+}
+
+int64_t longest_block(const Map1& m) {
+  int64_t n = 0;
+  for (size_t b = 0; b < m.prog.size(); ++b) n = std::max(n, m.end[b] - m.begin[b]);
+  return n;
+}
+
+// Selects kernel 1's shape: launch info, block map, upload.
+int use_k1(scf_handle* h, int tp) {
+  if (tp == 0 && h->cfg.precision != SCF_MIXED) return SCF_ERR_UNSUPPORTED;
+  ScfLaunchInfo info{};
+  int bps = 0;
+  if (k1_shape(h->cfg, tp, &info, &bps) != SCF_OK) return SCF_ERR_UNSUPPORTED;
   Map1 m = make_map1(h->offsets, h->n_prog, info.tile, (int64_t)h->n_sm * bps);
-  if (m.prog.size() > h->cap_blk1) return SCF_ERR_UNSUPPORTED;
+  if (info.variant == 1) info.win = scf_k1_windows(longest_block(m), info);
+  if (m.prog.size() > h->cap_blk1 || k1_rows(info, m.prog.size()) > h->cap_rows) return SCF_ERR_UNSUPPORTED;
   bool ok = put(h->d_blk1_prog, m.prog.data(), sizeof(int) * m.prog.size()) &&
             put(h->d_blk1_begin, m.begin.data(), sizeof(int64_t) * m.begin.size()) &&
             put(h->d_blk1_end, m.end.data(), sizeof(int64_t) * m.end.size()) &&
@@ -369,28 +394,31 @@ int scf_init(const scf_config* cfg, int n_prog, const int64_t* offsets, const do
     return fail(SCF_ERR_CUDA);
   h->offsets.assign(offsets, offsets + n_prog + 1);
 
-  // Capacity of the block maps: the largest any candidate tile can need.
-  for (int tp : kTiles) {
+  // Capacity of the block maps and partial rows: the largest any candidate shape can need.
+  for (int tp : {64, 128, 256, 0}) {
+    if (tp == 0 && cfg->precision != SCF_MIXED) continue;
     ScfLaunchInfo info{};
     int bps = 0;
-    if (scf_k1_prepare(cfg->precision, cfg->lmax, cfg->nmax, tp, &info, &bps) != cudaSuccess || bps < 1) {
-      cudaGetLastError();
-      continue;
-    }
-    h->cap_blk1 = std::max(h->cap_blk1, make_map1(h->offsets, n_prog, info.tile, (int64_t)h->n_sm * bps).prog.size());
+    if (k1_shape(*cfg, tp, &info, &bps) != SCF_OK) continue;
+    const Map1 m = make_map1(h->offsets, n_prog, info.tile, (int64_t)h->n_sm * bps);
+    const size_t blocks = m.prog.size();
+    if (info.variant == 1) info.win = scf_k1_windows(longest_block(m), info);
+    h->cap_blk1 = std::max(h->cap_blk1, blocks);
+    h->cap_rows = std::max(h->cap_rows, k1_rows(info, blocks));
   }
   h->cap_blk3 = make_map3(h->offsets, n_prog, 64).prog.size();
   if (h->cap_blk1 == 0 && h->n_total > 0) return fail(SCF_ERR_UNSUPPORTED);
 
   // one allocation for the whole workspace
   const size_t nb1 = std::max<size_t>(1, h->cap_blk1), nb3 = std::max<size_t>(1, h->cap_blk3);
+  const size_t nrows = std::max<size_t>(1, h->cap_rows);
   size_t off = 0;
   auto take = [&](size_t bytes) {
     size_t o = off;
     off += round_up(bytes);
     return o;
   };
-  const size_t o_part = take(sizeof(double) * 2 * (size_t)h->nc * nb1);
+  const size_t o_part = take(sizeof(double) * 2 * (size_t)h->nc * nrows);
   const size_t o_A = take(sizeof(double) * 2 * (size_t)h->nc * n_prog);
   const size_t o_F = take(sizeof(double) * 2 * (size_t)h->nc * n_prog);
   const size_t o_aR = take(sizeof(double) * 4 * (size_t)n_prog);
@@ -433,8 +461,11 @@ int scf_init(const scf_config* cfg, int n_prog, const int64_t* offsets, const do
             cudaMemset(h->d_status, 0, sizeof(unsigned) * 4) == cudaSuccess &&
             cudaMemset(h->d_A, 0, sizeof(double) * 2 * (size_t)h->nc * n_prog) == cudaSuccess;
   if (!ok) return fail(SCF_ERR_CUDA);
-  // default shapes: 128-particle tiles and 128-thread blocks (scf_autotune may change them)
-  rc = use_k1(h, 128);
+  // default shapes: the register-tiled kernel 1 in mixed precision (128-particle
+  // tiles of the simple kernel in double precision) and 128-thread kernel 3
+  // blocks; scf_autotune may change them
+  rc = cfg->precision == SCF_MIXED ? use_k1(h, 0) : SCF_ERR_UNSUPPORTED;
+  if (rc != SCF_OK) rc = use_k1(h, 128);
   if (rc != SCF_OK) return fail(rc);
   rc = use_k3(h, 128);
   if (rc != SCF_OK) return fail(rc);
@@ -532,13 +563,19 @@ int scf_set_option(scf_handle* h, int option, int value) {
     if (cudaStreamSynchronize(h->stream) != cudaSuccess) return SCF_ERR_CUDA;
     return option == SCF_OPT_K1_TILE ? use_k1(h, value) : use_k3(h, value);
   }
+  if (option == SCF_OPT_K1_VARIANT) {
+    if (value != 0 && value != 1) return SCF_ERR_INVALID_ARG;
+    if (cudaStreamSynchronize(h->stream) != cudaSuccess) return SCF_ERR_CUDA;
+    return use_k1(h, value == 1 ? 0 : 128);
+  }
   return SCF_ERR_INVALID_ARG;
 }
 
 int scf_get_option(const scf_handle* h, int option, int* value) {
   if (!h || !value) return SCF_ERR_NULL_POINTER;
   if (option == SCF_OPT_GRAPHS) *value = h->graphs ? 1 : 0;
-  else if (option == SCF_OPT_K1_TILE) *value = h->k1.tile;
+  else if (option == SCF_OPT_K1_TILE) *value = h->k1.variant == 1 ? 0 : h->k1.tile;
+  else if (option == SCF_OPT_K1_VARIANT) *value = h->k1.variant;
   else if (option == SCF_OPT_K3_BLOCK) *value = h->k3.threads;
   else return SCF_ERR_INVALID_ARG;
   return SCF_OK;
@@ -571,15 +608,19 @@ int scf_autotune(scf_handle* h, const void* pos, const double* com, void* acc, i
   };
   void* p = const_cast<void*>(pos);
   double best1 = 1e30, best3 = 1e30;
-  int tp_best = h->k1.tile, tb_best = h->k3.threads;
-  for (int i = 0; i < 3 && rc == SCF_OK; ++i) {
-    if (use_k1(h, kTiles[i]) != SCF_OK) continue;
+  int tp_best = h->k1.variant == 1 ? 0 : h->k1.tile, tb_best = h->k3.threads;
+  if (ms_out)
+    for (int i = 0; i < 7; ++i) ms_out[i] = 0.0;
+  const int k1_candidates[4] = {64, 128, 256, 0};
+  const int k1_slot[4] = {0, 1, 2, 6};
+  for (int i = 0; i < 4 && rc == SCF_OK; ++i) {
+    if (use_k1(h, k1_candidates[i]) != SCF_OK) continue;
     double ms = 0.0;
     rc = time_it([&] { return run_coeffs(h, p, nullptr, nullptr, nullptr, h->d_A, nullptr, SCF_MODE_COEFFS); }, &ms);
-    if (ms_out) ms_out[i] = ms;
+    if (ms_out) ms_out[k1_slot[i]] = ms;
     if (rc == SCF_OK && ms < best1) {
       best1 = ms;
-      tp_best = kTiles[i];
+      tp_best = k1_candidates[i];
     }
   }
   if (rc == SCF_OK) rc = use_k1(h, tp_best);

@@ -9,6 +9,7 @@
 // it to the block's running sums.  The sums leave the block as one partial
 // vector per block; kernel 2 adds the partials of each progenitor in block
 // order, so the result does not depend on scheduling.
+#include <algorithm>
 #include <cstdio>
 
 #include "scf_device.cuh"
@@ -189,6 +190,406 @@ size_t k1_smem(int nmax, int nc) {
 }
 
 // ---------------------------------------------------------------------------
+// Kernel 1, register-tiled single-precision form.
+//
+// Per degree l the coefficient pass is the contraction
+//   S_hat[n][mm] = sum_p R[p][l][n] Y[p][l][mm]
+// over particles p, with only (nmax+1)(2l+1) outputs.  Reading both operands
+// from shared memory for every FMA (the form above) ties it to shared-memory
+// bandwidth: one wavefront per operand against four FMA instructions per
+// clock.  Here every worker thread owns one 7 x 8 tile of outputs (degree l,
+// seven radial orders, eight angular columns) for the block's lifetime, and
+// one of `sub` particle sub-groups; per group of four particles it reads
+// 7 + 8 float4 rows and issues 224 FMAs into registers.
+//
+// The basis of each 60-particle tile is staged as rows [l][n] (the scaled
+// Gegenbauer values Ch_n(xi) = C_n(xi) / gscale[l][n], see ScfConst) and
+// [chunk (l, mm / 8)][mm % 8] (angular factors m s^l q^(2l+1) Pb_lm C_m and
+// ... Pb_lm S_m), particle index fastest; the constant gscale is applied when
+// the sums are flushed.  Eight warps compute it, four threads
+// per particle: thread set q runs the Gegenbauer chains of the degrees
+// l = q, q+4, q+8, ... and the Legendre columns of the orders m = q, q+4, ...
+// interleaved, so its recurrence constants are warp-uniform and its chains
+// independent.  Two blocks share an SM, so one block's basis phase overlaps
+// the other's contraction.
+//
+// Every WINDOW_TILES tiles, and at the end, a worker stores its register sums
+// (at most 64 x 16 single-precision terms each) into its own slot for
+// that window and starts again from zero, so no sum grows long in single
+// precision and nothing is read back; kernel 2 adds the slots of all windows,
+// sub-groups and blocks in double precision in a fixed order.  Rows and
+// columns of a tile beyond nmax or 2l read padding or the next degree's rows
+// and are never written out.
+// ---------------------------------------------------------------------------
+namespace tiled {
+constexpr int TP = 60;           // particles per tile (two basis halves of 30 lanes)
+constexpr int TPP = TP;          // staged row stride in floats: 15 float4s, an odd number, so
+                                 // float4 reads of rows that differ mod 8 hit different bank groups
+constexpr int TN = 7, TM = 8;    // output tile: radial orders x angular columns
+constexpr int BASIS_WARPS = 8;   // 2 particle halves x 4 chain sets
+constexpr int WINDOW_TILES = 64; // tiles summed in registers before a window's sums are stored
+constexpr int MAX_THREADS = 256;
+
+__host__ __device__ inline int n_chunks(int nn) { return (nn + TN - 1) / TN; }
+__host__ __device__ inline int m_chunks(int l) { return (2 * l + 1 + TM - 1) / TM; }
+inline int n_items(int nmax, int lmax) {
+  int c = 0;
+  for (int l = 0; l <= lmax; ++l) c += m_chunks(l);
+  return c * n_chunks(nmax + 1);
+}
+// Angular rows are stored by output chunk: chunk k = (l, mm / TM) occupies the
+// TM rows starting at 9k (one spare row per chunk), so the chunks that the
+// lanes of a warp read together start in different bank groups.
+constexpr int YCH = TM + 1;
+__host__ __device__ constexpr int chunk_base(int l) {  // chunks of the degrees below l
+  int k = 0;
+  for (int i = 0; i < l; ++i) k += (2 * i + 1 + TM - 1) / TM;
+  return k;
+}
+__host__ __device__ constexpr int y_row(int l, int mm) { return YCH * (chunk_base(l) + mm / TM) + mm % TM; }
+inline size_t smem_bytes(int nmax, int lmax) {
+  const size_t rows = (size_t)(lmax + 1) * (nmax + 1) + (TN - 1) + (size_t)YCH * chunk_base(lmax + 1);
+  return sizeof(float) * TPP * rows;
+}
+
+// Stores a worker's register sums (times the constant gscale of the staged
+// C_n) into its window slot and clears them; zero = true stores zeros.
+__device__ __forceinline__ void store_tile(float (&acc)[TN][TM], float* __restrict__ out, bool zero, int l, int n0,
+                                           int mm0, int nn, int nlm, int nc) {
+#pragma unroll
+  for (int j = 0; j < TM; ++j) {
+    const int mm = mm0 + j;
+    const int col = mm <= l ? scf_lm(l, mm) : nc + scf_lm(l, mm - l);
+    const bool jok = mm <= 2 * l;
+#pragma unroll
+    for (int i = 0; i < TN; ++i) {
+      if (jok && n0 + i < nn) out[(n0 + i) * nlm + col] = zero ? 0.f : acc[i][j] * c_tab.gscalef[l][n0 + i];
+      acc[i][j] = 0.f;
+    }
+  }
+}
+
+// Basis of one particle for thread set q (runtime degrees and orders): the
+// chains l = q + 4j (radial rows) and m = q + 4j (Legendre columns, angular rows).
+template <int NCH>
+struct BasisGeneric {
+  static __device__ __forceinline__ void run(int q, float* Rs, float* Ys, int t, int NN, int L, float mass, float u,
+                                             float v, float c, float qv, float xi, float sq2) {
+      // radial chains of the degrees l = q + 4j: R[l][n] = Ch_n(xi)
+    {
+      float c0[NCH], cm1[NCH];
+#pragma unroll
+      for (int j = 0; j < NCH; ++j) {
+        c0[j] = 1.f;
+        cm1[j] = 0.f;
+        const int l = q + 4 * j;
+        if (l <= L) Rs[(l * NN) * TPP + t] = 1.f;
+      }
+      for (int n = 1; n < NN; ++n) {
+#pragma unroll
+        for (int j = 0; j < NCH; ++j) {
+          const int l = q + 4 * j;
+          if (l <= L) {
+            const float cn = fmaf(-c_tab.gbetaf[l][n], cm1[j], xi * c0[j]);
+            cm1[j] = c0[j];
+            c0[j] = cn;
+            Rs[(l * NN + n) * TPP + t] = cn;
+          }
+        }
+      }
+    }
+    // Legendre columns of the orders m = q + 4j, times W_m = (u + i v)^m and
+    // the radial prefactor m s^l q^(2l+1)
+    {
+      float wc = 1.f, ws = 0.f, pw = mass * qv;
+      for (int i = 0; i < q; ++i) {
+        const float tc = wc * u - ws * v;
+        ws = wc * v + ws * u;
+        wc = tc;
+        pw *= sq2;
+      }
+      const float w2c = u * u - v * v, w2s = 2.f * u * v;
+      const float w4c = w2c * w2c - w2s * w2s, w4s = 2.f * w2c * w2s;
+      const float s2 = sq2 * sq2, s4 = s2 * s2;
+      float Wc[NCH], Ws[NCH], P1[NCH], P2[NCH], pre[NCH];
+#pragma unroll
+      for (int j = 0; j < NCH; ++j) {
+        Wc[j] = wc;
+        Ws[j] = ws;
+        pre[j] = pw;   // m s^m q^(2m+1) at l = m
+        const float tc = wc * w4c - ws * w4s;
+        ws = wc * w4s + ws * w4c;
+        wc = tc;
+        pw *= s4;
+        P1[j] = 0.f;
+        P2[j] = 0.f;
+      }
+      for (int l = q; l <= L; ++l) {
+#pragma unroll
+        for (int j = 0; j < NCH; ++j) {
+          const int m = q + 4 * j;
+          if (m <= l) {
+            float P;
+            if (l == m) P = c_tab.ldiagf[l];
+            else if (l == m + 1) P = c_tab.lsubf[l] * c * P1[j];
+            else P = c_tab.laf[scf_lm(l, m)] * c * P1[j] - c_tab.lbf[scf_lm(l, m)] * P2[j];
+            P2[j] = P1[j];
+            P1[j] = P;
+            const float Pp = P * pre[j];
+            pre[j] *= sq2;
+            Ys[y_row(l, m) * TPP + t] = Pp * Wc[j];
+            if (m >= 1) Ys[y_row(l, l + m) * TPP + t] = Pp * Ws[j];
+          }
+        }
+      }
+    }
+  }
+};
+
+// The same with the shape fixed at compile time: every recurrence constant is
+// an immediate constant-bank operand and every staged row an immediate offset.
+template <int Q, int NN, int L>
+__device__ __forceinline__ void basis_fixed(float* Rs, float* Ys, int t, float mass, float u, float v, float c,
+                                            float qv, float xi, float sq2) {
+  constexpr int NJ = Q <= L ? (L - Q) / 4 + 1 : 0;
+  if constexpr (NJ > 0) {
+    // radial rows Ch_n(xi) of the degrees l = Q + 4j
+    float c0[NJ], cm1[NJ];
+#pragma unroll
+    for (int j = 0; j < NJ; ++j) {
+      c0[j] = 1.f;
+      cm1[j] = 0.f;
+      Rs[((Q + 4 * j) * NN) * TPP + t] = 1.f;
+    }
+#pragma unroll
+    for (int n = 1; n < NN; ++n) {
+#pragma unroll
+      for (int j = 0; j < NJ; ++j) {
+        const int l = Q + 4 * j;
+        const float cn = fmaf(-c_tab.gbetaf[l][n], cm1[j], xi * c0[j]);
+        cm1[j] = c0[j];
+        c0[j] = cn;
+        Rs[(l * NN + n) * TPP + t] = cn;
+      }
+    }
+    // angular rows m s^l q^(2l+1) Pb_lm {C_m, S_m} of the orders m = Q + 4j
+    float wc = 1.f, ws = 0.f, pw = mass * qv;
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+      const float tc = wc * u - ws * v;
+      ws = wc * v + ws * u;
+      wc = tc;
+      pw *= sq2;
+    }
+    const float w2c = u * u - v * v, w2s = 2.f * u * v;
+    const float w4c = w2c * w2c - w2s * w2s, w4s = 2.f * w2c * w2s;
+    const float s2 = sq2 * sq2, s4 = s2 * s2;
+    float Wc[NJ], Ws[NJ], P1[NJ], P2[NJ], pre[NJ];
+#pragma unroll
+    for (int j = 0; j < NJ; ++j) {
+      Wc[j] = wc;
+      Ws[j] = ws;
+      pre[j] = pw;
+      const float tc = wc * w4c - ws * w4s;
+      ws = wc * w4s + ws * w4c;
+      wc = tc;
+      pw *= s4;
+      P1[j] = 0.f;
+      P2[j] = 0.f;
+    }
+#pragma unroll
+    for (int l = Q; l <= L; ++l) {
+#pragma unroll
+      for (int j = 0; j < NJ; ++j) {
+        const int m = Q + 4 * j;
+        if (m <= l) {
+          float P;
+          if (l == m) P = c_tab.ldiagf[l];
+          else if (l == m + 1) P = c_tab.lsubf[l] * c * P1[j];
+          else P = c_tab.laf[scf_lm(l, m)] * c * P1[j] - c_tab.lbf[scf_lm(l, m)] * P2[j];
+          P2[j] = P1[j];
+          P1[j] = P;
+          const float Pp = P * pre[j];
+          pre[j] *= sq2;
+          Ys[y_row(l, m) * TPP + t] = Pp * Wc[j];
+          if (m >= 1) Ys[y_row(l, l + m) * TPP + t] = Pp * Ws[j];
+        }
+      }
+    }
+  }
+}
+
+template <int NN_, int L_>
+struct BasisFixed {
+  static __device__ __forceinline__ void run(int q, float* Rs, float* Ys, int t, int, int, float mass, float u,
+                                             float v, float c, float qv, float xi, float sq2) {
+    switch (q) {  // warp-uniform
+      case 0: basis_fixed<0, NN_, L_>(Rs, Ys, t, mass, u, v, c, qv, xi, sq2); break;
+      case 1: basis_fixed<1, NN_, L_>(Rs, Ys, t, mass, u, v, c, qv, xi, sq2); break;
+      case 2: basis_fixed<2, NN_, L_>(Rs, Ys, t, mass, u, v, c, qv, xi, sq2); break;
+      default: basis_fixed<3, NN_, L_>(Rs, Ys, t, mass, u, v, c, qv, xi, sq2); break;
+    }
+  }
+};
+
+// 128 registers: each quarter of the SM holds 16384, i.e. four warps of 128
+// registers, so two blocks of 8 warps share an SM; the 56 accumulators and
+// 7 float4 operands fit without spilling.
+template <class B>  // basis policy: BasisGeneric<NCH> or BasisFixed<NN, L>
+__global__ void __maxnreg__(128) k1_tiled(K1Args a) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int NN = a.nmax + 1, L = a.lmax;
+  const int rR = (L + 1) * NN;
+  float* Rs = reinterpret_cast<float*>(smem_raw);  // [rR + TN - 1][TPP]
+  float* Ys = Rs + (rR + TN - 1) * TPP;            // [YCH * chunks][TPP]
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  // padding rows and the angular rows past 2l of each degree's last chunk are never written by the basis
+  for (int i = tid; i < (TN - 1) * TPP; i += blockDim.x) Rs[rR * TPP + i] = 0.f;
+  for (int i = tid; i < YCH * chunk_base(L + 1) * TPP; i += blockDim.x) Ys[i] = 0.f;
+  __syncthreads();
+
+  // contraction role: item (l, c, d) = output tile, sgrp = particle sub-group
+  const bool worker = tid < a.items * a.sub;
+  const int item = tid % a.items, sgrp = tid / a.items;
+  int il = 0, ic = 0, id = 0;
+  {
+    const int ncn = n_chunks(NN);
+    int r = item;
+    for (int l = 0; l <= L; ++l) {
+      const int cnt = m_chunks(l) * ncn;
+      if (r < cnt) {
+        il = l;
+        id = r / ncn;
+        ic = r - id * ncn;
+        break;
+      }
+      r -= cnt;
+    }
+  }
+  const int n0 = ic * TN, mm0 = id * TM;
+  const float* Rrow = Rs + (il * NN + n0) * TPP;
+  const float* Yrow = Ys + y_row(il, mm0) * TPP;
+  float acc[TN][TM];
+#pragma unroll
+  for (int i = 0; i < TN; ++i)
+#pragma unroll
+    for (int j = 0; j < TM; ++j) acc[i][j] = 0.f;
+  // window slots of this worker: rows (block, sub-group, window) of 2 NC floats
+  float* out = reinterpret_cast<float*>(a.partials) + ((size_t)blockIdx.x * a.sub + sgrp) * a.win * 2 * a.nc;
+  int win = 0;
+
+  const int prog = a.blk_prog[blockIdx.x];
+  const float binv = (float)(1.0 / a.b_prog[prog]);
+  const int64_t k_begin = a.blk_begin[blockIdx.x], k_end = a.blk_end[blockIdx.x];
+  float4* pos4 = reinterpret_cast<float4*>(a.pos);
+  const bool step = a.mode == SCF_MODE_STEP;
+  int tiles = 0;
+  for (int64_t base = k_begin; base < k_end; base += TP) {
+    const bool last = base + TP >= k_end;
+    // ---- basis of the tile
+    float4 p_new = make_float4(0.f, 0.f, 0.f, 0.f), v_new = p_new;
+    if (warp < BASIS_WARPS && lane < TP / 2) {
+      const int t = (warp & 1) * (TP / 2) + lane;
+      const int q = warp >> 1;
+      const int64_t k = base + t;
+      float x = 0.f, y = 0.f, z = 0.f, mass = 0.f;
+      if (k < k_end) {
+        float4 p = pos4[k];
+        if (step) {
+          float4 v = reinterpret_cast<float4*>(a.vel)[k];
+          const float4 g = reinterpret_cast<const float4*>(a.acc)[k];
+          const float h = (float)(0.5 * a.dt), dt = (float)a.dt;
+          v.x += h * g.x;
+          v.y += h * g.y;
+          v.z += h * g.z;
+          p.x += dt * v.x;
+          p.y += dt * v.y;
+          p.z += dt * v.z;
+          p_new = p;
+          v_new = v;
+        }
+        if (scf_finite3(p.x, p.y, p.z) && isfinite(p.w)) {
+          x = p.x;
+          y = p.y;
+          z = p.z;
+          mass = (a.mask == nullptr || a.mask[k]) ? p.w : 0.f;
+        } else if (q == 0) {
+          atomicOr(a.status, 1u);
+        }
+      }
+      const float r = sqrtf(x * x + y * y + z * z);
+      const float rinv = r > 0.f ? 1.f / r : 0.f;
+      const float u = x * rinv, v = y * rinv, c = z * rinv;
+      const float s = r * binv;
+      const float qv = 1.f / (1.f + s);
+      const float xi = 1.f - 2.f * qv;
+      const float sq2 = s * qv * qv;
+      B::run(q, Rs, Ys, t, NN, L, mass, u, v, c, qv, xi, sq2);
+    }
+    __syncthreads();
+    if (step && warp < 2 && lane < TP / 2) {  // chain set 0 writes the kicked and drifted state back
+      const int64_t k = base + warp * (TP / 2) + lane;
+      if (k < k_end) {
+        pos4[k] = p_new;
+        reinterpret_cast<float4*>(a.vel)[k] = v_new;
+      }
+    }
+    // ---- contraction of the tile into the register tiles
+    if (worker) {
+      for (int g = sgrp; g < TP / 4; g += a.sub) {
+        const int t0 = 4 * g;
+        float4 rv[TN];
+#pragma unroll
+        for (int i = 0; i < TN; ++i) rv[i] = *reinterpret_cast<const float4*>(Rrow + i * TPP + t0);
+#pragma unroll
+        for (int j = 0; j < TM; ++j) {
+          const float4 yv = *reinterpret_cast<const float4*>(Yrow + j * TPP + t0);
+#pragma unroll
+          for (int i = 0; i < TN; ++i) {
+            acc[i][j] = fmaf(rv[i].x, yv.x, acc[i][j]);
+            acc[i][j] = fmaf(rv[i].y, yv.y, acc[i][j]);
+            acc[i][j] = fmaf(rv[i].z, yv.z, acc[i][j]);
+            acc[i][j] = fmaf(rv[i].w, yv.w, acc[i][j]);
+          }
+        }
+      }
+      if (++tiles == a.win_tiles || last) {
+        store_tile(acc, out + (size_t)win * 2 * a.nc, false, il, n0, mm0, NN, a.nlm, a.nc);
+        ++win;
+        tiles = 0;
+      }
+    }
+    __syncthreads();
+  }
+  if (worker)  // windows this block did not fill (fewer tiles than the longest block)
+    for (; win < a.win; ++win) store_tile(acc, out + (size_t)win * 2 * a.nc, true, il, n0, mm0, NN, a.nlm, a.nc);
+}
+
+template <class B>
+struct K1Tiled {
+  static void* fn() { return (void*)k1_tiled<B>; }
+  static void launch(const K1Args& a, int blocks, int threads, size_t smem, cudaStream_t s) {
+    k1_tiled<B><<<blocks, threads, smem, s>>>(a);
+  }
+};
+
+// Shapes with a compile-time basis: (nmax, lmax) = (20, 10), (20, 8), (10, 6);
+// every other shape runs the runtime-indexed basis.
+template <typename F>
+auto dispatch_tiled(int nmax, int lmax, F&& f) {
+  if (nmax == 20 && lmax == 10) return f(K1Tiled<BasisFixed<21, 10>>());
+  if (nmax == 20 && lmax == 8) return f(K1Tiled<BasisFixed<21, 8>>());
+  if (nmax == 10 && lmax == 6) return f(K1Tiled<BasisFixed<11, 6>>());
+  switch ((lmax + 4) / 4) {
+    case 1: return f(K1Tiled<BasisGeneric<1>>());
+    case 2: return f(K1Tiled<BasisGeneric<2>>());
+    case 3: return f(K1Tiled<BasisGeneric<3>>());
+    default: return f(K1Tiled<BasisGeneric<4>>());
+  }
+}
+}  // namespace tiled
+
+// ---------------------------------------------------------------------------
 // kernel 2
 // ---------------------------------------------------------------------------
 __device__ void com_kdk(const ScfHostParams& hp, double* c, double dt) {
@@ -211,39 +612,60 @@ __device__ __forceinline__ void write_force_pair(void* F, int f32, size_t i, dou
   else reinterpret_cast<double2*>(F)[i] = make_double2(c, s);
 }
 
-// One warp per (cosine, sine) coefficient pair of one progenitor: lane j
-// sums the partials of blocks j, j+32, ... in order, then a fixed shuffle
-// tree combines the lanes, so the result is the same on every run.
-__global__ void k2_reduce(K2Args a) {
+// 32 consecutive coefficient pairs per block (threadIdx.x) times 8 row
+// slices (threadIdx.y): slice y adds the rows y, y + 8, ... of the progenitor
+// in order, reading 32 consecutive entries of a row at a time, and slice
+// sums are then added in the order of y, so the result is the same on every
+// run.
+constexpr int K2_SLICES = 8;
+__global__ void __launch_bounds__(32 * K2_SLICES) k2_reduce(K2Args a) {
+  __shared__ double s_c[K2_SLICES][32], s_s[K2_SLICES][32];
   const int p = blockIdx.y;
-  const int lane = threadIdx.x & 31;
-  const int i = blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5);
+  const int x = threadIdx.x, y = threadIdx.y;
+  const int i = blockIdx.x * 32 + x;
+  const size_t stride = 2 * (size_t)a.nc;
+  double sc = 0.0, ss = 0.0;
   if (i < a.nc) {
-    const int b0 = a.prog_blk_off[p], b1 = a.prog_blk_off[p + 1];
-    const size_t stride = 2 * (size_t)a.nc;
-    double sc = 0.0, ss = 0.0;
-    for (int b = b0 + lane; b < b1; b += 32) {
-      const double* src = a.partials + (size_t)b * stride + i;
-      sc += src[0];
-      ss += src[a.nc];
-    }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-      sc += __shfl_xor_sync(0xffffffffu, sc, o);
-      ss += __shfl_xor_sync(0xffffffffu, ss, o);
-    }
-    if (lane == 0) {
-      const double S = sc * a.norm[i], T = ss * a.norm[a.nc + i];
-      double* A = a.A_out + (size_t)p * stride;
-      A[i] = S;
-      A[a.nc + i] = T;
-      if (a.F_out) {
-        const double w = -a.G / a.b_prog[p] * c_tab.inv_nlm[i % a.nlm];
-        write_force_pair(a.F_out, a.f32, (size_t)p * a.nc + i, w * S, w * T);
+    if (a.sub == 0) {  // double rows, one per block
+      const int r0 = a.prog_blk_off[p], r1 = a.prog_blk_off[p + 1];
+      for (int r = r0 + y; r < r1; r += K2_SLICES) {
+        const double* src = a.partials + (size_t)r * stride + i;
+        sc += src[0];
+        ss += src[a.nc];
+      }
+    } else {  // float rows, a.sub per block; T_nl0 is not stored
+      int lm = i % a.nlm, l = 0;
+      while ((l + 1) * (l + 2) / 2 <= lm) ++l;
+      const bool has_t = lm != scf_lm(l, 0);
+      const float* P = reinterpret_cast<const float*>(a.partials);
+      const int r0 = a.prog_blk_off[p] * a.sub, r1 = a.prog_blk_off[p + 1] * a.sub;
+      for (int r = r0 + y; r < r1; r += K2_SLICES) {
+        sc += (double)P[(size_t)r * stride + i];
+        if (has_t) ss += (double)P[(size_t)r * stride + a.nc + i];
       }
     }
   }
-  if (blockIdx.x == 0 && threadIdx.x == 0 && a.host.n > 0 && a.com != nullptr) {
+  s_c[y][x] = sc;
+  s_s[y][x] = ss;
+  __syncthreads();
+  if (y == 0 && i < a.nc) {
+    sc = s_c[0][x];
+    ss = s_s[0][x];
+#pragma unroll
+    for (int k = 1; k < K2_SLICES; ++k) {
+      sc += s_c[k][x];
+      ss += s_s[k][x];
+    }
+    const double S = sc * a.norm[i], T = ss * a.norm[a.nc + i];
+    double* A = a.A_out + (size_t)p * stride;
+    A[i] = S;
+    A[a.nc + i] = T;
+    if (a.F_out) {
+      const double w = -a.G / a.b_prog[p] * c_tab.inv_nlm[i % a.nlm];
+      write_force_pair(a.F_out, a.f32, (size_t)p * a.nc + i, w * S, w * T);
+    }
+  }
+  if (blockIdx.x == 0 && x == 0 && y == 0 && a.host.n > 0 && a.com != nullptr) {
     double* c = a.com + 6 * p;
     if (a.mode == SCF_MODE_STEP) com_kdk(a.host, c, a.dt);
     if (a.aR_out) {
@@ -332,7 +754,49 @@ cudaError_t scf_k1_prepare(int precision, int lmax, int nmax, int tp, ScfLaunchI
   return k1_prepare_t<double>(lmax, nmax, tp, info, blocks_per_sm);
 }
 
+cudaError_t scf_k1_tiled_prepare(int lmax, int nmax, ScfLaunchInfo* info, int* blocks_per_sm) {
+  using namespace tiled;
+  const int items = n_items(nmax, lmax);
+  if (items > MAX_THREADS) return cudaErrorInvalidConfiguration;
+  const int sub = std::min(TP / 4, std::max(1, MAX_THREADS / items));
+  info->items = items;
+  info->sub = sub;
+  info->threads = std::max(BASIS_WARPS * 32, 32 * ((items * sub + 31) / 32));
+  info->tile = TP;
+  info->variant = 1;
+  info->win = 1;  // set from the block map by the caller (scf_k1_windows)
+  info->win_tiles = WINDOW_TILES;
+  info->smem = smem_bytes(nmax, lmax);
+  if (info->smem > 227 * 1024) return cudaErrorInvalidConfiguration;
+  return dispatch_tiled(nmax, lmax, [&](auto k) -> cudaError_t {
+    using KK = decltype(k);
+    cudaError_t e = cudaFuncSetAttribute(KK::fn(), cudaFuncAttributeMaxDynamicSharedMemorySize, (int)info->smem);
+    if (e != cudaSuccess) return e;
+    // two ~100 KB blocks per SM need the largest shared-memory carveout
+    e = cudaFuncSetAttribute(KK::fn(), cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared);
+    if (e != cudaSuccess) return e;
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, KK::fn(), info->threads, info->smem);
+  });
+}
+
+int scf_k1_windows(int64_t max_particles_per_block, const ScfLaunchInfo& info) {
+  const int64_t tiles = (max_particles_per_block + info.tile - 1) / info.tile;
+  return (int)std::max<int64_t>(1, (tiles + info.win_tiles - 1) / info.win_tiles);
+}
+
 cudaError_t scf_k1_launch(int precision, const K1Args& a, int blocks, const ScfLaunchInfo& info, cudaStream_t s) {
+  if (info.variant == 1) {
+    K1Args b = a;
+    b.items = info.items;
+    b.sub = info.sub;
+    b.win = info.win;
+    b.win_tiles = info.win_tiles;
+    tiled::dispatch_tiled(a.nmax, a.lmax, [&](auto k) -> int {
+      decltype(k)::launch(b, blocks, info.threads, info.smem, s);
+      return 0;
+    });
+    return cudaGetLastError();
+  }
   auto go = [&](auto k) -> int {
     decltype(k)::launch(a, blocks, info.smem, s);
     return 0;
@@ -343,8 +807,8 @@ cudaError_t scf_k1_launch(int precision, const K1Args& a, int blocks, const ScfL
 }
 
 cudaError_t scf_k2_launch(const K2Args& a, cudaStream_t s) {
-  dim3 grid((a.nc + 7) / 8, a.n_prog);  // 8 warps per block, one pair per warp
-  k2_reduce<<<grid, 256, 0, s>>>(a);
+  dim3 grid((a.nc + 31) / 32, a.n_prog);
+  k2_reduce<<<grid, dim3(32, K2_SLICES), 0, s>>>(a);
   return cudaGetLastError();
 }
 

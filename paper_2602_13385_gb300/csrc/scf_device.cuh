@@ -44,6 +44,12 @@ struct ScfConst {
   float laf[SCF_NLM_CAP], lbf[SCF_NLM_CAP], lkf[SCF_NLM_CAP];
   float lsubf[SCF_LMAX_CAP + 1], ldiagf[SCF_LMAX_CAP + 1];
   double inv_nlm[SCF_NLM_CAP];  // 1 / N_lm
+  // Scaled Gegenbauer polynomials for the register-tiled coefficient kernel:
+  // Ch_n = C_n / gscale[l][n] with gscale[l][n] = gA[l][1] ... gA[l][n] obey
+  // Ch_n = xi Ch_{n-1} - gbeta[l][n] Ch_{n-2}, Ch_0 = 1, Ch_1 = xi,
+  // gbeta[l][n] = gB[l][n] / (gA[l][n] gA[l][n-1]) (one multiply and one FMA a step).
+  float gbetaf[SCF_LMAX_CAP + 1][SCF_NMAX_CAP + 1];
+  float gscalef[SCF_LMAX_CAP + 1][SCF_NMAX_CAP + 1];
 };
 
 // Host-side generation of the tables (scf_tables.cu).

@@ -48,6 +48,10 @@ struct K1Args {
   double dt;
   unsigned* status;
   AdjArgs adj;
+  // register-tiled single-precision kernel: contraction items, particle
+  // sub-groups per block, windows per block and tiles per window (partials
+  // are then float rows, sub * win per block)
+  int items, sub, win, win_tiles;
 };
 
 // Kernel 2: fixed-order reduction of the partials, normalisation, and the
@@ -69,6 +73,9 @@ struct K2Args {
   const double* b_prog;
   double G;
   double* aR_out;           // [n_prog][4], or null
+  // partials layout: sub == 0: [blocks][2*NC] doubles; sub > 0: [blocks][sub][2*NC]
+  // floats without the T_nl0 entries (read as 0)
+  int sub;
 };
 
 // Force coefficients and a_host(R) from given coefficients (scf_forces).
@@ -122,7 +129,11 @@ struct ScfLaunchInfo {
   int threads;   // threads per block
   int tile;      // particles per tile (block ranges are whole tiles)
   size_t smem;   // dynamic shared memory per block
-  int variant;   // kernel variant chosen by the prepare call
+  int variant;   // kernel variant chosen by the prepare call (1: register-tiled single precision)
+  int items;     // variant 1: 7 x 8 contraction items per particle sub-group
+  int sub;       // variant 1: particle sub-groups per block
+  int win;       // variant 1: windows per block (partial rows per block = sub * win)
+  int win_tiles; // variant 1: tiles per window
 };
 
 void scf_make_norm(int nmax, int lmax, double* norm);
@@ -145,6 +156,11 @@ cudaError_t scf_upload_const_adjoint(const ScfConst* t);
 // the given sizes; sets the shared-memory attribute of the instantiation.
 // tp: kernel 1 particle tile (64, 128, 256); tb: kernel 3 block size (64, 128, 256).
 cudaError_t scf_k1_prepare(int precision, int lmax, int nmax, int tp, ScfLaunchInfo* info, int* blocks_per_sm);
+// Register-tiled single-precision kernel 1 (info->variant = 1).
+cudaError_t scf_k1_tiled_prepare(int lmax, int nmax, ScfLaunchInfo* info, int* blocks_per_sm);
+// Windows per block of the register-tiled kernel for a block map whose
+// longest block has the given number of particles.
+int scf_k1_windows(int64_t max_particles_per_block, const ScfLaunchInfo& info);
 cudaError_t scf_k3_prepare(int precision, int lmax, int nmax, int tb, ScfLaunchInfo* info, int* blocks_per_sm);
 
 cudaError_t scf_k1_launch(int precision, const K1Args& a, int blocks, const ScfLaunchInfo& info, cudaStream_t s);

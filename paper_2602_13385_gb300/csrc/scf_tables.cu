@@ -23,7 +23,11 @@ void scf_make_const(ScfConst* t) {
         B[n] = (n + 2.0 * a - 2.0) / n;
       }
     }
+    double scale = 1.0;
     for (int n = 0; n <= SCF_NMAX_CAP; ++n) {
+      if (n >= 1) scale *= t->gA[l][n];
+      t->gscalef[l][n] = (float)scale;
+      t->gbetaf[l][n] = n >= 2 ? (float)(t->gB[l][n] / (t->gA[l][n] * t->gA[l][n - 1])) : 0.f;
       t->gAf[l][n] = (float)t->gA[l][n];
       t->gBf[l][n] = (float)t->gB[l][n];
       t->hAf[l][n] = (float)t->hA[l][n];

@@ -128,13 +128,20 @@ class SCF:
         return _lib.scf_launches_per_call(self._h, {"coeffs": 0, "forces": 1, "step": 2}[which])
 
     def tiles(self) -> dict:
-        """Current kernel shapes: coefficient-kernel tile and field-kernel block."""
+        """Current kernel shapes: coefficient-kernel tile (0 = the register-tiled
+        kernel of mixed precision) and field-kernel block."""
         return {"k1_tile": _lib.scf_get_option(self._h, _lib.SCF_OPT_K1_TILE),
                 "k3_block": _lib.scf_get_option(self._h, _lib.SCF_OPT_K3_BLOCK)}
 
     def set_tiles(self, k1_tile: int | None = None, k3_block: int | None = None):
+        """``k1_tile``: 64, 128 or 256 particles per tile of the one-thread-per-
+        output coefficient kernel, or 0 for the register-tiled kernel (mixed
+        precision only); ``k3_block``: 64, 128 or 256 threads per field block."""
         if k1_tile is not None:
-            _lib.scf_set_option(self._h, _lib.SCF_OPT_K1_TILE, int(k1_tile))
+            if int(k1_tile) == 0:
+                _lib.scf_set_option(self._h, _lib.SCF_OPT_K1_VARIANT, 1)
+            else:
+                _lib.scf_set_option(self._h, _lib.SCF_OPT_K1_TILE, int(k1_tile))
         if k3_block is not None:
             _lib.scf_set_option(self._h, _lib.SCF_OPT_K3_BLOCK, int(k3_block))
 

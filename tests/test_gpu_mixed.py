@@ -171,3 +171,34 @@ def test_full_size_eccentric_mixed_workload(scf):
     assert eA < 1e-6
     assert np.median(e) < 1e-5
     assert sim.status() == (0, 0)
+
+
+@pytest.mark.parametrize("nmax,lmax,n,masked", [(0, 0, 17, False), (10, 6, 1, False), (10, 6, 63, False),
+                                                (10, 6, 65, True), (20, 8, 5003, False), (20, 10, 30000, True),
+                                                (40, 12, 4099, False), (3, 1, 1000, False)])
+def test_register_tiled_kernel_matches_oracle_and_simple_kernel(scf, nmax, lmax, n, masked):
+    """The register-tiled coefficient kernel (the mixed-precision default) on
+    ragged sizes (a partial last tile, a single particle, orders that leave
+    partly filled 7 x 8 output tiles, nmax = 40 with six radial chunks)
+    against the oracle and against the one-thread-per-output kernel."""
+    pos, _ = workloads.plummer(max(n, 2), seed=300 + n)
+    pos = pos[:n]
+    b = workloads.basis_scale(workloads.half_mass_radius(pos)) if n > 4 else 0.3
+    mask = (np.arange(n) % 3 != 1).astype(np.uint8) if masked else None
+    cfg = scf.Config(nmax=nmax, lmax=lmax, b=b, precision="mixed")
+    sim = scf.SCF(cfg, n=n)
+    assert sim.tiles()["k1_tile"] == 0          # register-tiled kernel by default
+    p = f32(pos)
+    m = None if mask is None else torch.tensor(mask, device="cuda")
+    A_tiled = sim.coeffs(p, mask=m).cpu().numpy()[0]
+    sim.set_tiles(k1_tile=128)
+    A_simple = sim.coeffs(p, mask=m).cpu().numpy()[0]
+    ref = oracle.coeffs(pos.astype(np.float32).astype(np.float64), nmax, lmax, b, mask=mask)
+    e_or, _ = coef_errs(A_tiled, ref, nmax, lmax)
+    e_si, _ = coef_errs(A_tiled, A_simple, nmax, lmax)
+    nc = oracle.n_coef(nmax, lmax)
+    t_m0 = [nc + oracle.idx(k, l, 0, lmax) for k in range(nmax + 1) for l in range(lmax + 1)]
+    print(f"tiled kernel ({nmax},{lmax}) N={n}: vs oracle {e_or:.2e}, vs simple kernel {e_si:.2e}")
+    assert e_or < 1e-6 and e_si < 1e-6
+    assert np.all(A_tiled[t_m0] == 0)          # T_nl0 is identically zero
+    assert sim.status() == (0, 0)

@@ -4,7 +4,8 @@ It serves callers that cannot call cudaMalloc (code inside a memory arena it
 must not grow, paths where allocation is not allowed or would synchronise the
 device, plugins handed device pointers but no allocator).  Its scratch is a
 static device array inside the library.  These tests call it through the C ABI
-and compare it with scf_coeffs on two calls in a row with different inputs
+and compare it with scf_coeffs (on the same coefficient kernel) on two calls
+in a row with different inputs
 (the scratch keeps the previous call's contents, so the second call checks
 that nothing leaks), at the tolerances the other parity tests use: 1e-10 in
 double precision, 1e-6 in mixed precision (the two entry points split the
@@ -46,6 +47,10 @@ def _noalloc(pkg, cfg, pos, mask=None):
 
 def _existing(pkg, cfg, pos, mask=None):
     sim = pkg.SCF(cfg, n=pos.shape[0])
+    # scf_coeffs_noalloc runs the one-thread-per-output coefficient kernel;
+    # compare with scf_coeffs on that kernel (mixed precision defaults to the
+    # register-tiled one, whose float rounding differs)
+    sim.set_tiles(k1_tile=128)
     A = sim.coeffs(pos, mask=mask)[0]
     torch.cuda.synchronize()
     sim.close()
