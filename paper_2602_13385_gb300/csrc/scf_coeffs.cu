@@ -612,37 +612,51 @@ __device__ __forceinline__ void write_force_pair(void* F, int f32, size_t i, dou
   else reinterpret_cast<double2*>(F)[i] = make_double2(c, s);
 }
 
-// 32 consecutive coefficient pairs per block (threadIdx.x) times 8 row
-// slices (threadIdx.y): slice y adds the rows y, y + 8, ... of the progenitor
-// in order, reading 32 consecutive entries of a row at a time, and slice
-// sums are then added in the order of y, so the result is the same on every
-// run.
-constexpr int K2_SLICES = 8;
-__global__ void __launch_bounds__(32 * K2_SLICES) k2_reduce(K2Args a) {
-  __shared__ double s_c[K2_SLICES][32], s_s[K2_SLICES][32];
+// K2_X consecutive coefficient pairs per block (threadIdx.x) times K2_SLICES
+// row slices (threadIdx.y): slice y adds the rows y, y + K2_SLICES, ... of
+// the progenitor in order, reading K2_X consecutive entries of a row at a
+// time, and the slice sums are then added in the order of y, so the result
+// is the same on every run.  Many slices keep enough loads in flight to
+// stream the partials (a few rows per thread) with a one-progenitor grid.
+constexpr int K2_X = 16, K2_SLICES = 64;
+__global__ void __launch_bounds__(K2_X * K2_SLICES) k2_reduce(K2Args a) {
+  __shared__ double s_c[K2_SLICES][K2_X], s_s[K2_SLICES][K2_X];
   const int p = blockIdx.y;
   const int x = threadIdx.x, y = threadIdx.y;
-  const int i = blockIdx.x * 32 + x;
+  const int i = blockIdx.x * K2_X + x;
   const size_t stride = 2 * (size_t)a.nc;
   double sc = 0.0, ss = 0.0;
   if (i < a.nc) {
     if (a.sub == 0) {  // double rows, one per block
       const int r0 = a.prog_blk_off[p], r1 = a.prog_blk_off[p + 1];
+#pragma unroll 4
       for (int r = r0 + y; r < r1; r += K2_SLICES) {
         const double* src = a.partials + (size_t)r * stride + i;
         sc += src[0];
         ss += src[a.nc];
       }
     } else {  // float rows, a.sub per block; T_nl0 is not stored
+      // a slice's rows are added as an unevaluated float pair (hi, lo) with an
+      // error-free two-sum: single-precision arithmetic (the FP64 pipe is 1/64
+      // of the FP32 one) at about twice single precision
       int lm = i % a.nlm, l = 0;
       while ((l + 1) * (l + 2) / 2 <= lm) ++l;
       const bool has_t = lm != scf_lm(l, 0);
       const float* P = reinterpret_cast<const float*>(a.partials);
       const int r0 = a.prog_blk_off[p] * a.sub, r1 = a.prog_blk_off[p + 1] * a.sub;
+      float ch = 0.f, cl = 0.f, th = 0.f, tl = 0.f;
+      auto two_sum = [](float& hi, float& lo, float v) {
+        const float s = hi + v, bp = s - hi;
+        lo += (hi - (s - bp)) + (v - bp);
+        hi = s;
+      };
+#pragma unroll 4
       for (int r = r0 + y; r < r1; r += K2_SLICES) {
-        sc += (double)P[(size_t)r * stride + i];
-        if (has_t) ss += (double)P[(size_t)r * stride + a.nc + i];
+        two_sum(ch, cl, P[(size_t)r * stride + i]);
+        if (has_t) two_sum(th, tl, P[(size_t)r * stride + a.nc + i]);
       }
+      sc = (double)ch + (double)cl;
+      ss = (double)th + (double)tl;
     }
   }
   s_c[y][x] = sc;
@@ -807,8 +821,8 @@ cudaError_t scf_k1_launch(int precision, const K1Args& a, int blocks, const ScfL
 }
 
 cudaError_t scf_k2_launch(const K2Args& a, cudaStream_t s) {
-  dim3 grid((a.nc + 31) / 32, a.n_prog);
-  k2_reduce<<<grid, dim3(32, K2_SLICES), 0, s>>>(a);
+  dim3 grid((a.nc + K2_X - 1) / K2_X, a.n_prog);
+  k2_reduce<<<grid, dim3(K2_X, K2_SLICES), 0, s>>>(a);
   return cudaGetLastError();
 }
 
