@@ -257,6 +257,11 @@ def main():
     ap.add_argument("--workload", choices=sorted(WORKLOADS), default=DEFAULT_WORKLOAD)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-autotune", action="store_true", help="keep the default kernel shapes")
+    ap.add_argument("--tiles", default=None,
+                    help="K1,K3: fixed kernel shapes instead of the autotuner (K1 = 0 for the register-tiled "
+                         "coefficient kernel, else 64/128/256 particles per tile; K3 = 64/128/256 threads)")
+    ap.add_argument("--n", type=int, default=None,
+                    help="particle count of a smaller case of the same workload (for profiling captures)")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
@@ -279,7 +284,7 @@ def main():
             dist.barrier()
 
     from paper_2602_13385_gb300 import SCF, Config
-    wl, precision = build_workload(args.workload)
+    wl, precision = build_workload(args.workload, args.n)
     dtype = torch.float64 if precision == "fp64" else torch.float32
     cfg = Config(nmax=wl.nmax, lmax=wl.lmax, b=wl.b, dt=wl.dt, precision=precision, host=list(wl.host))
     offsets = [0, wl.n] if wl.offsets is None else list(wl.offsets)
@@ -292,7 +297,10 @@ def main():
     use_com = c if wl.host else None
     a = sim.forces(p, sim.coeffs(p), com=use_com)
     tuning = None
-    if not args.no_autotune:
+    if args.tiles:
+        k1t, k3b = (int(x) for x in args.tiles.split(","))
+        sim.set_tiles(k1_tile=k1t, k3_block=k3b)
+    elif not args.no_autotune:
         # untimed set-up: the library's autotuner picks the kernel shapes
         tuning = sim.autotune(p, com=use_com, acc=torch.empty_like(a), reps=3, cache=False)
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)

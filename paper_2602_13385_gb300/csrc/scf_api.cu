@@ -41,6 +41,7 @@ struct scf_handle {
   void* d_F = nullptr;          // [n_prog][NC] force-coefficient pairs (float2 or double2)
   double* d_aR = nullptr;       // [n_prog][4] a_host(R)
   double* d_norm = nullptr;
+  void* d_kscale = nullptr;     // [NC] scale pairs of kernel 3 (element type of the precision)
   double* d_b = nullptr;
   unsigned* d_status = nullptr;
   void* d_base = nullptr;
@@ -182,6 +183,7 @@ K3Args k3_args(scf_handle* h, const void* pos, void* vel, void* acc, const doubl
   a.acc = acc;
   a.F = h->d_F;
   a.aR = h->d_aR;
+  a.kscale = h->d_kscale;
   a.com = com;
   a.blk_prog = h->d_blk3_prog;
   a.blk_begin = h->d_blk3_begin;
@@ -423,6 +425,7 @@ int scf_init(const scf_config* cfg, int n_prog, const int64_t* offsets, const do
   const size_t o_F = take(sizeof(double) * 2 * (size_t)h->nc * n_prog);
   const size_t o_aR = take(sizeof(double) * 4 * (size_t)n_prog);
   const size_t o_norm = take(sizeof(double) * 2 * (size_t)h->nc);
+  const size_t o_ksc = take(sizeof(double) * 2 * (size_t)h->nc);
   const size_t o_b = take(sizeof(double) * n_prog);
   const size_t o_b1p = take(sizeof(int) * nb1);
   const size_t o_b1b = take(sizeof(int64_t) * nb1);
@@ -443,6 +446,7 @@ int scf_init(const scf_config* cfg, int n_prog, const int64_t* offsets, const do
   h->d_F = reinterpret_cast<void*>(base + o_F);
   h->d_aR = reinterpret_cast<double*>(base + o_aR);
   h->d_norm = reinterpret_cast<double*>(base + o_norm);
+  h->d_kscale = reinterpret_cast<void*>(base + o_ksc);
   h->d_b = reinterpret_cast<double*>(base + o_b);
   h->d_blk1_prog = reinterpret_cast<int*>(base + o_b1p);
   h->d_blk1_begin = reinterpret_cast<int64_t*>(base + o_b1b);
@@ -454,9 +458,13 @@ int scf_init(const scf_config* cfg, int n_prog, const int64_t* offsets, const do
   h->d_status = reinterpret_cast<unsigned*>(base + o_st);
   if (cfg->precision == SCF_FP64) h->d_adj_part = reinterpret_cast<double*>(base + o_adj);
 
-  std::vector<double> norm(2 * (size_t)h->nc);
+  std::vector<double> norm(2 * (size_t)h->nc), ksc(2 * (size_t)h->nc);
   scf_make_norm(cfg->nmax, cfg->lmax, norm.data());
-  bool ok = put(h->d_norm, norm.data(), sizeof(double) * norm.size()) &&
+  scf_make_kscale(cfg->nmax, cfg->lmax, ksc.data());
+  std::vector<float> ksc_f(ksc.begin(), ksc.end());
+  const bool ksc_ok = cfg->precision == SCF_MIXED ? put(h->d_kscale, ksc_f.data(), sizeof(float) * ksc_f.size())
+                                                  : put(h->d_kscale, ksc.data(), sizeof(double) * ksc.size());
+  bool ok = ksc_ok && put(h->d_norm, norm.data(), sizeof(double) * norm.size()) &&
             put(h->d_b, bs.data(), sizeof(double) * n_prog) &&
             cudaMemset(h->d_status, 0, sizeof(unsigned) * 4) == cudaSuccess &&
             cudaMemset(h->d_A, 0, sizeof(double) * 2 * (size_t)h->nc * n_prog) == cudaSuccess;

@@ -50,6 +50,11 @@ struct ScfConst {
   // gbeta[l][n] = gB[l][n] / (gA[l][n] gA[l][n-1]) (one multiply and one FMA a step).
   float gbetaf[SCF_LMAX_CAP + 1][SCF_NMAX_CAP + 1];
   float gscalef[SCF_LMAX_CAP + 1][SCF_NMAX_CAP + 1];
+  // The same scaling for both families in the field kernel: Ch (alpha) and
+  // Dh (alpha + 1, scale hscale = hA[l][1] ... hA[l][n], step hbeta).
+  double gbeta[SCF_LMAX_CAP + 1][SCF_NMAX_CAP + 1], gscale[SCF_LMAX_CAP + 1][SCF_NMAX_CAP + 1];
+  double hbeta[SCF_LMAX_CAP + 1][SCF_NMAX_CAP + 1], hscale[SCF_LMAX_CAP + 1][SCF_NMAX_CAP + 1];
+  float hbetaf[SCF_LMAX_CAP + 1][SCF_NMAX_CAP + 1], hscalef[SCF_LMAX_CAP + 1][SCF_NMAX_CAP + 1];
 };
 
 // Host-side generation of the tables (scf_tables.cu).

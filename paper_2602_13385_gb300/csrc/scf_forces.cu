@@ -2,12 +2,15 @@
 // particle, plus the tidal acceleration of the accelerating, non-rotating
 // cluster frame (Sec. 2.1), and in step mode the closing half kick.
 //
-// One thread per particle.  The block's progenitor coefficients are turned
-// into F_nlm = -G {S,T}_nlm / (b N_lm) and staged in shared memory; every
-// thread then runs, for each l, the Gegenbauer recurrences for alpha_l and
-// alpha_l + 1 in n and accumulates, for m = 0..l,
+// One thread per particle.  The block's force coefficients
+// F_nlm = -G {S,T}_nlm / (b N_lm) are staged in shared memory as 4-vectors
+// (F gscale[l][n], F hscale[l][n-1]) of the cosine and sine parts; every
+// thread then runs, for each l, the scaled Gegenbauer recurrences
+//   Ch_n = xi Ch_{n-1} - gbeta[l][n] Ch_{n-2},  Dh_n = xi Dh_{n-1} - hbeta[l][n] Dh_{n-2}
+// (Ch_n = C_n^alpha / gscale, Dh_n = C_n^{alpha+1} / hscale: one multiply and
+// one FMA a step, see ScfConst) and accumulates, for m = 0..l,
 //   Z0 = sum_n F_nlm C_n^alpha(xi),  Z1 = sum_n F_nlm C_{n-1}^{alpha+1}(xi)
-// (cosine and sine parts), from which
+// as sums of the scaled coefficients times Ch_n and Dh_{n-1}, from which
 //   G_lm   = s^l q^(2l+1) Z0                               (potential),
 //   G_lm/r = (1/b) s^(l-1) q^(2l+1) Z0                     (l >= 1),
 //   G'_lm  = (1/b) [(l s^(l-1) q^(2l+1) - (2l+1) s^l q^(2l+2)) Z0 + 4 alpha s^l q^(2l+3) Z1]
@@ -31,31 +34,39 @@ template <typename T> struct Vec2;
 template <> struct Vec2<double> { using type = double2; };
 template <> struct Vec2<float> { using type = float2; };
 
-template <typename T> __device__ __forceinline__ T tgA(int l, int n) { return sizeof(T) == 8 ? (T)c_tab.gA[l][n] : (T)c_tab.gAf[l][n]; }
-template <typename T> __device__ __forceinline__ T tgB(int l, int n) { return sizeof(T) == 8 ? (T)c_tab.gB[l][n] : (T)c_tab.gBf[l][n]; }
-template <typename T> __device__ __forceinline__ T thA(int l, int n) { return sizeof(T) == 8 ? (T)c_tab.hA[l][n] : (T)c_tab.hAf[l][n]; }
-template <typename T> __device__ __forceinline__ T thB(int l, int n) { return sizeof(T) == 8 ? (T)c_tab.hB[l][n] : (T)c_tab.hBf[l][n]; }
 template <typename T> __device__ __forceinline__ T tla(int i) { return sizeof(T) == 8 ? (T)c_tab.la[i] : (T)c_tab.laf[i]; }
 template <typename T> __device__ __forceinline__ T tlb(int i) { return sizeof(T) == 8 ? (T)c_tab.lb[i] : (T)c_tab.lbf[i]; }
 template <typename T> __device__ __forceinline__ T tlk(int i) { return sizeof(T) == 8 ? (T)c_tab.lk[i] : (T)c_tab.lkf[i]; }
 template <typename T> __device__ __forceinline__ T tlsub(int l) { return sizeof(T) == 8 ? (T)c_tab.lsub[l] : (T)c_tab.lsubf[l]; }
 template <typename T> __device__ __forceinline__ T tldiag(int l) { return sizeof(T) == 8 ? (T)c_tab.ldiag[l] : (T)c_tab.ldiagf[l]; }
+template <typename T> __device__ __forceinline__ T tgbeta(int l, int n) { return sizeof(T) == 8 ? (T)c_tab.gbeta[l][n] : (T)c_tab.gbetaf[l][n]; }
+template <typename T> __device__ __forceinline__ T thbeta(int l, int n) { return sizeof(T) == 8 ? (T)c_tab.hbeta[l][n] : (T)c_tab.hbetaf[l][n]; }
 
 template <typename T, int LMAX, int K3_TB>
 __global__ void __launch_bounds__(K3_TB) k3_forces(K3Args a) {
   using V4 = typename Vec4<T>::type;
   using V2 = typename Vec2<T>::type;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  // [NC] (cosine, sine) force coefficient pairs of this block's progenitor,
-  // interleaved so one shared-memory load feeds four FMAs
-  V2* F = reinterpret_cast<V2*>(smem_raw);
+  // [NC] scaled (cosine, sine) force coefficients of this block's progenitor:
+  // (Fc gscale_n, Fs gscale_n, Fc hscale_{n-1}, Fs hscale_{n-1}), so one
+  // shared-memory load feeds the four FMAs of an (n, l, m)
+  V4* F = reinterpret_cast<V4*>(smem_raw);
   __shared__ double s_R[3], s_aR[3];
   const int tid = threadIdx.x;
   const int prog = a.blk_prog[blockIdx.x];
   const double b = a.b_prog[prog];
   {
     const V2* Fg = reinterpret_cast<const V2*>(a.F) + (size_t)prog * a.nc;
-    for (int i = tid; i < a.nc; i += K3_TB) F[i] = Fg[i];
+    const V2* Sg = reinterpret_cast<const V2*>(a.kscale);
+    for (int i = tid; i < a.nc; i += K3_TB) {
+      const V2 f = Fg[i], sc = Sg[i];
+      V4 q;
+      q.x = f.x * sc.x;
+      q.y = f.y * sc.x;
+      q.z = f.x * sc.y;
+      q.w = f.y * sc.y;
+      F[i] = q;
+    }
   }
   const bool has_host = a.host.n > 0 && a.com != nullptr;
   if (tid < 3) {
@@ -106,28 +117,27 @@ __global__ void __launch_bounds__(K3_TB) k3_forces(K3Args a) {
     const int lm0 = scf_lm(l, 0);
 #pragma unroll
     for (int m = 0; m <= l; ++m) {
-      const V2 f0 = F[lm0 + m];  // n = 0: C_0 = 1
+      const V4 f0 = F[lm0 + m];  // n = 0: Ch_0 = 1, no Dh_{-1} term
       Z0c[m] = f0.x;
       Z0s[m] = f0.y;
       Z1c[m] = 0;
       Z1s[m] = 0;
     }
     {
-      T cm1 = 0, c0 = 1;  // C^alpha_{n-2}, C^alpha_{n-1}
-      T dm1 = 0, d0 = 1;  // C^{alpha+1}_{n-2}, C^{alpha+1}_{n-1}
+      T cm1 = 0, c0 = 1;  // Ch_{n-2}, Ch_{n-1}
+      T dm1 = 0, d0 = 1;  // Dh_{n-2}, Dh_{n-1}
       for (int n = 1; n < NN; ++n) {
-        const T cn = tgA<T>(l, n) * xi * c0 - tgB<T>(l, n) * cm1;
+        const T cn = xi * c0 - tgbeta<T>(l, n) * cm1;
         const int o = n * a.nlm + lm0;
 #pragma unroll
         for (int m = 0; m <= l; ++m) {
-          const V2 fv = F[o + m];
-          const T fc = fv.x, fs = fv.y;
-          Z0c[m] += fc * cn;
-          Z0s[m] += fs * cn;
-          Z1c[m] += fc * d0;
-          Z1s[m] += fs * d0;
+          const V4 fv = F[o + m];
+          Z0c[m] += fv.x * cn;
+          Z0s[m] += fv.y * cn;
+          Z1c[m] += fv.z * d0;
+          Z1s[m] += fv.w * d0;
         }
-        const T dn = thA<T>(l, n) * xi * d0 - thB<T>(l, n) * dm1;
+        const T dn = xi * d0 - thbeta<T>(l, n) * dm1;
         cm1 = c0;
         c0 = cn;
         dm1 = d0;
@@ -276,7 +286,7 @@ cudaError_t prepare_t(int lmax, int nmax, int tb, ScfLaunchInfo* info, int* bloc
     info->threads = tb;
     info->tile = tb;
     info->variant = 0;
-    info->smem = sizeof(T) * 2 * (size_t)nc;  // (cosine, sine) pair per coefficient
+    info->smem = sizeof(T) * 4 * (size_t)nc;  // scaled (cosine, sine) x (alpha, alpha + 1) per coefficient
     cudaError_t e = cudaFuncSetAttribute(KK::fn(), cudaFuncAttributeMaxDynamicSharedMemorySize, (int)info->smem);
     if (e != cudaSuccess) return e;
     return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, KK::fn(), info->threads, info->smem);

@@ -99,6 +99,7 @@ struct K3Args {
   const void* F;            // [n_prog][NC] (cos, sin) force-coefficient pairs
   const double* com;        // [n_prog][6] or null (R is read)
   const double* aR;         // [n_prog][4] a_host(R)
+  const void* kscale;       // [NC] (gscale[l][n], hscale[l][n-1]) pairs of the element type
   const int* blk_prog;
   const int64_t* blk_begin;
   const int64_t* blk_end;
@@ -137,6 +138,9 @@ struct ScfLaunchInfo {
 };
 
 void scf_make_norm(int nmax, int lmax, double* norm);
+// Per-coefficient scale pairs (gscale[l][n], hscale[l][n-1]; 0 at n = 0) of the
+// field kernel's scaled recurrences, as doubles ([NC][2]).
+void scf_make_kscale(int nmax, int lmax, double* kscale);
 
 cudaError_t scf_com_adj_launch(const ComAdjArgs& a, cudaStream_t s);
 // Dual-number kernels of the adjoint (double precision).  Both loop over their

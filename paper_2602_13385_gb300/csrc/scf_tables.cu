@@ -23,11 +23,20 @@ void scf_make_const(ScfConst* t) {
         B[n] = (n + 2.0 * a - 2.0) / n;
       }
     }
-    double scale = 1.0;
+    double scale = 1.0, hs = 1.0;
     for (int n = 0; n <= SCF_NMAX_CAP; ++n) {
-      if (n >= 1) scale *= t->gA[l][n];
+      if (n >= 1) {
+        scale *= t->gA[l][n];
+        hs *= t->hA[l][n];
+      }
+      t->gscale[l][n] = scale;
+      t->hscale[l][n] = hs;
+      t->gbeta[l][n] = n >= 2 ? t->gB[l][n] / (t->gA[l][n] * t->gA[l][n - 1]) : 0.0;
+      t->hbeta[l][n] = n >= 2 ? t->hB[l][n] / (t->hA[l][n] * t->hA[l][n - 1]) : 0.0;
       t->gscalef[l][n] = (float)scale;
-      t->gbetaf[l][n] = n >= 2 ? (float)(t->gB[l][n] / (t->gA[l][n] * t->gA[l][n - 1])) : 0.f;
+      t->hscalef[l][n] = (float)hs;
+      t->gbetaf[l][n] = (float)t->gbeta[l][n];
+      t->hbetaf[l][n] = (float)t->hbeta[l][n];
       t->gAf[l][n] = (float)t->gA[l][n];
       t->gBf[l][n] = (float)t->gB[l][n];
       t->hAf[l][n] = (float)t->hA[l][n];
@@ -83,4 +92,18 @@ void scf_make_norm(int nmax, int lmax, double* norm /* 2*NC */) {
         norm[nc + i] = (m == 0) ? 0.0 : f;
       }
     }
+}
+
+void scf_make_kscale(int nmax, int lmax, double* kscale) {
+  ScfConst* t = new ScfConst;
+  scf_make_const(t);
+  const int nlm = (lmax + 1) * (lmax + 2) / 2;
+  for (int n = 0; n <= nmax; ++n)
+    for (int l = 0; l <= lmax; ++l)
+      for (int m = 0; m <= l; ++m) {
+        const int i = n * nlm + scf_lm(l, m);
+        kscale[2 * i] = t->gscale[l][n];
+        kscale[2 * i + 1] = n >= 1 ? t->hscale[l][n - 1] : 0.0;
+      }
+  delete t;
 }
