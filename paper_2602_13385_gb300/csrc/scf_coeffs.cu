@@ -3,8 +3,10 @@
 //
 // Kernel 1 works on tiles of TP particles, one thread per particle in the
 // basis phase.  For each degree l the block stages, in shared memory, the
-// radial factors R[t][n] = m_t s^l q^(2l+1) C_n(xi_t) and the angular factors
-// Y[t][mm] = Pb_lm C_m (mm = m) or Pb_lm S_m (mm = l + m), then every thread
+// radial factors R[t][n] = Ch_n(xi_t) (the scaled Gegenbauer values
+// C_n / gscale[l][n], one multiply and one FMA a step) and the angular factors
+// Y[t][mm] = m_t s^l q^(2l+1) Pb_lm C_m (mm = m) or ... Pb_lm S_m (mm = l + m);
+// the constant gscale is applied when the block writes its sums.  Then every thread
 // contracts a slice of the (n, mm) outputs over the tile's particles and adds
 // it to the block's running sums.  The sums leave the block as one partial
 // vector per block; kernel 2 adds the partials of each progenitor in block
@@ -25,12 +27,9 @@ template <typename T> struct Vec4;
 template <> struct Vec4<double> { using type = ScfD4; };
 template <> struct Vec4<float> { using type = float4; };
 
-template <typename T> __device__ __forceinline__ T tab_gA(int l, int n);
-template <> __device__ __forceinline__ double tab_gA<double>(int l, int n) { return c_tab.gA[l][n]; }
-template <> __device__ __forceinline__ float tab_gA<float>(int l, int n) { return c_tab.gAf[l][n]; }
-template <typename T> __device__ __forceinline__ T tab_gB(int l, int n);
-template <> __device__ __forceinline__ double tab_gB<double>(int l, int n) { return c_tab.gB[l][n]; }
-template <> __device__ __forceinline__ float tab_gB<float>(int l, int n) { return c_tab.gBf[l][n]; }
+template <typename T> __device__ __forceinline__ T tab_gbeta(int l, int n);
+template <> __device__ __forceinline__ double tab_gbeta<double>(int l, int n) { return c_tab.gbeta[l][n]; }
+template <> __device__ __forceinline__ float tab_gbeta<float>(int l, int n) { return c_tab.gbetaf[l][n]; }
 template <typename T> __device__ __forceinline__ T tab_la(int i) { return sizeof(T) == 8 ? (T)c_tab.la[i] : (T)c_tab.laf[i]; }
 template <typename T> __device__ __forceinline__ T tab_lb(int i) { return sizeof(T) == 8 ? (T)c_tab.lb[i] : (T)c_tab.lbf[i]; }
 template <typename T> __device__ __forceinline__ T tab_lsub(int l) { return sizeof(T) == 8 ? (T)c_tab.lsub[l] : (T)c_tab.lsubf[l]; }
@@ -138,25 +137,25 @@ __global__ void __launch_bounds__(TP) k1_partials(K1Args a) {
         P[m] = tab_la<T>(scf_lm(l, m)) * c * P1[m] - tab_lb<T>(scf_lm(l, m)) * P2[m];
       if (l >= 1) P[l - 1] = tab_lsub<T>(l) * c * P1[l - 1];
       P[l] = tab_ldiag<T>(l);
-      // radial factors
+      // radial factors: scaled Gegenbauer values Ch_n = C_n / gscale[l][n]
       {
         T cm1 = 0, c0 = 1;
         T* Rt = R + tid * NN;
-        Rt[0] = pre;
+        Rt[0] = 1;
         for (int n = 1; n < NN; ++n) {
-          const T cn = tab_gA<T>(l, n) * xi * c0 - tab_gB<T>(l, n) * cm1;
+          const T cn = xi * c0 - tab_gbeta<T>(l, n) * cm1;
           cm1 = c0;
           c0 = cn;
-          Rt[n] = pre * cn;
+          Rt[n] = cn;
         }
       }
-      // angular factors
+      // angular factors, carrying the radial prefactor m_k s^l q^(2l+1)
       {
         T* Yt = Y + tid * YS;
 #pragma unroll
-        for (int m = 0; m <= l; ++m) Yt[m] = P[m] * Wc[m];
+        for (int m = 0; m <= l; ++m) Yt[m] = (pre * P[m]) * Wc[m];
 #pragma unroll
-        for (int m = 1; m <= l; ++m) Yt[l + m] = P[m] * Ws[m];
+        for (int m = 1; m <= l; ++m) Yt[l + m] = (pre * P[m]) * Ws[m];
       }
       __syncthreads();
       // contraction over the tile's particles
@@ -180,7 +179,13 @@ __global__ void __launch_bounds__(TP) k1_partials(K1Args a) {
   }
   __syncthreads();
   double* out = a.partials + (size_t)blockIdx.x * 2 * a.nc;
-  for (int i = tid; i < 2 * a.nc; i += TP) out[i] = Acc::value(acc, i);
+  for (int i = tid; i < 2 * a.nc; i += TP) {
+    const int ii = i < a.nc ? i : i - a.nc;
+    const int n = ii / a.nlm, lm = ii - n * a.nlm;
+    int l = 0;
+    while ((l + 1) * (l + 2) / 2 <= lm) ++l;
+    out[i] = Acc::value(acc, i) * c_tab.gscale[l][n];  // undo the scaling of the staged C_n
+  }
 }
 
 template <typename T, int LMAX, int TP>
