@@ -55,6 +55,9 @@ struct ScfConst {
   double gbeta[SCF_LMAX_CAP + 1][SCF_NMAX_CAP + 1], gscale[SCF_LMAX_CAP + 1][SCF_NMAX_CAP + 1];
   double hbeta[SCF_LMAX_CAP + 1][SCF_NMAX_CAP + 1], hscale[SCF_LMAX_CAP + 1][SCF_NMAX_CAP + 1];
   float hbetaf[SCF_LMAX_CAP + 1][SCF_NMAX_CAP + 1], hscalef[SCF_LMAX_CAP + 1][SCF_NMAX_CAP + 1];
+  // hscale[l][n-1] / gscale[l][n] (0 at n = 0): lets the single-precision field
+  // kernel use one scaled coefficient F gscale_n for both families
+  float hratiof[SCF_LMAX_CAP + 1][SCF_NMAX_CAP + 1];
 };
 
 // Host-side generation of the tables (scf_tables.cu).

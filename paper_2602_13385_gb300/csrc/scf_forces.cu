@@ -47,10 +47,15 @@ __global__ void __launch_bounds__(K3_TB) k3_forces(K3Args a) {
   using V4 = typename Vec4<T>::type;
   using V2 = typename Vec2<T>::type;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  // [NC] scaled (cosine, sine) force coefficients of this block's progenitor:
-  // (Fc gscale_n, Fs gscale_n, Fc hscale_{n-1}, Fs hscale_{n-1}), so one
-  // shared-memory load feeds the four FMAs of an (n, l, m)
+  // [NC] scaled (cosine, sine) force coefficients of this block's progenitor,
+  // one shared-memory load for the four FMAs of an (n, l, m).  Double:
+  // (Fc gscale_n, Fs gscale_n, Fc hscale_{n-1}, Fs hscale_{n-1}).  Single:
+  // (Fc gscale_n, Fs gscale_n) only, the alpha + 1 family taking the
+  // per-(l, n) ratio hratio = hscale_{n-1} / gscale_n on its recurrence value
+  // instead (8 instead of 16 bytes per load).
+  constexpr bool kF2 = sizeof(T) == 4;
   V4* F = reinterpret_cast<V4*>(smem_raw);
+  V2* F2 = reinterpret_cast<V2*>(smem_raw);
   __shared__ double s_R[3], s_aR[3];
   const int tid = threadIdx.x;
   const int prog = a.blk_prog[blockIdx.x];
@@ -60,12 +65,16 @@ __global__ void __launch_bounds__(K3_TB) k3_forces(K3Args a) {
     const V2* Sg = reinterpret_cast<const V2*>(a.kscale);
     for (int i = tid; i < a.nc; i += K3_TB) {
       const V2 f = Fg[i], sc = Sg[i];
-      V4 q;
-      q.x = f.x * sc.x;
-      q.y = f.y * sc.x;
-      q.z = f.x * sc.y;
-      q.w = f.y * sc.y;
-      F[i] = q;
+      if constexpr (kF2) {
+        F2[i] = V2{f.x * sc.x, f.y * sc.x};
+      } else {
+        V4 q;
+        q.x = f.x * sc.x;
+        q.y = f.y * sc.x;
+        q.z = f.x * sc.y;
+        q.w = f.y * sc.y;
+        F[i] = q;
+      }
     }
   }
   const bool has_host = a.host.n > 0 && a.com != nullptr;
@@ -116,10 +125,16 @@ __global__ void __launch_bounds__(K3_TB) k3_forces(K3Args a) {
     T Z0c[LMAX + 1], Z0s[LMAX + 1], Z1c[LMAX + 1], Z1s[LMAX + 1];
     const int lm0 = scf_lm(l, 0);
 #pragma unroll
-    for (int m = 0; m <= l; ++m) {
-      const V4 f0 = F[lm0 + m];  // n = 0: Ch_0 = 1, no Dh_{-1} term
-      Z0c[m] = f0.x;
-      Z0s[m] = f0.y;
+    for (int m = 0; m <= l; ++m) {  // n = 0: Ch_0 = 1, no Dh_{-1} term
+      if constexpr (kF2) {
+        const V2 f0 = F2[lm0 + m];
+        Z0c[m] = f0.x;
+        Z0s[m] = f0.y;
+      } else {
+        const V4 f0 = F[lm0 + m];
+        Z0c[m] = f0.x;
+        Z0s[m] = f0.y;
+      }
       Z1c[m] = 0;
       Z1s[m] = 0;
     }
@@ -129,13 +144,25 @@ __global__ void __launch_bounds__(K3_TB) k3_forces(K3Args a) {
       for (int n = 1; n < NN; ++n) {
         const T cn = xi * c0 - tgbeta<T>(l, n) * cm1;
         const int o = n * a.nlm + lm0;
+        if constexpr (kF2) {
+          const T dd = d0 * c_tab.hratiof[l][n];
 #pragma unroll
-        for (int m = 0; m <= l; ++m) {
-          const V4 fv = F[o + m];
-          Z0c[m] += fv.x * cn;
-          Z0s[m] += fv.y * cn;
-          Z1c[m] += fv.z * d0;
-          Z1s[m] += fv.w * d0;
+          for (int m = 0; m <= l; ++m) {
+            const V2 fv = F2[o + m];
+            Z0c[m] += fv.x * cn;
+            Z0s[m] += fv.y * cn;
+            Z1c[m] += fv.x * dd;
+            Z1s[m] += fv.y * dd;
+          }
+        } else {
+#pragma unroll
+          for (int m = 0; m <= l; ++m) {
+            const V4 fv = F[o + m];
+            Z0c[m] += fv.x * cn;
+            Z0s[m] += fv.y * cn;
+            Z1c[m] += fv.z * d0;
+            Z1s[m] += fv.w * d0;
+          }
         }
         const T dn = xi * d0 - thbeta<T>(l, n) * dm1;
         cm1 = c0;
@@ -286,7 +313,8 @@ cudaError_t prepare_t(int lmax, int nmax, int tb, ScfLaunchInfo* info, int* bloc
     info->threads = tb;
     info->tile = tb;
     info->variant = 0;
-    info->smem = sizeof(T) * 4 * (size_t)nc;  // scaled (cosine, sine) x (alpha, alpha + 1) per coefficient
+    // scaled (cosine, sine) per coefficient; double also the alpha + 1 family's
+    info->smem = sizeof(T) * (sizeof(T) == 4 ? 2 : 4) * (size_t)nc;
     cudaError_t e = cudaFuncSetAttribute(KK::fn(), cudaFuncAttributeMaxDynamicSharedMemorySize, (int)info->smem);
     if (e != cudaSuccess) return e;
     return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, KK::fn(), info->threads, info->smem);

@@ -36,6 +36,7 @@ void scf_make_const(ScfConst* t) {
       t->gscalef[l][n] = (float)scale;
       t->hscalef[l][n] = (float)hs;
       t->gbetaf[l][n] = (float)t->gbeta[l][n];
+      t->hratiof[l][n] = n >= 1 ? (float)(t->hscale[l][n - 1] / t->gscale[l][n]) : 0.f;
       t->hbetaf[l][n] = (float)t->hbeta[l][n];
       t->gAf[l][n] = (float)t->gA[l][n];
       t->gBf[l][n] = (float)t->gB[l][n];
