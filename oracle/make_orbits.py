@@ -8,7 +8,7 @@ kpc (km/s)^2 / Msun:
 * ``circular_8kpc``: R = (8, 0, 0) kpc in the disk plane, V = (0, v_c, 0) with
   v_c = sqrt(R |a_R|).
 * ``eccentric_5_20kpc``: starts at apocentre 20 kpc in the direction of the
-  paper's "Eccentric Test" initial position (Table B.2), moving along +y like
+  paper's "Eccentric Test" initial position (Table A3), moving along +y like
   that orbit; the speed is root-found so that the pericentre is 5 kpc.
 * ``batch``: seeded orbits with pericentre ~ U(3, 20) kpc and apocentre ~
   U(max(peri, 10), 40) kpc in random orbital planes, root-found the same way.
@@ -83,7 +83,7 @@ def main():
     R = [8.0, 0.0, 0.0]
     out["circular_8kpc"] = {"R_kpc": R, "V_kms": [0.0, vcirc(h, R), 0.0]}
 
-    d = np.array([4.04231677, 0.0, 19.58670971])   # Table B.2, Eccentric Test position
+    d = np.array([4.04231677, 0.0, 19.58670971])   # Table A3, Eccentric Test position
     R = 20.0 * d / np.linalg.norm(d)
     v, pmin, pmax = solve_speed(h, R, np.array([0.0, 1.0, 0.0]), 5.0, t_max=1.0)
     out["eccentric_5_20kpc"] = {"R_kpc": R.tolist(), "V_kms": [0.0, v, 0.0], "peri_kpc": pmin, "apo_kpc": pmax}

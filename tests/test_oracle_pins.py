@@ -384,7 +384,7 @@ def test_host_forces_are_minus_gradient():
 
 def test_host_potentials_match_paper_table1():
     """E and L_z' of Orbits 0-9 (Table 1) from their initial conditions
-    (Table B.2) in MilkyWayPotential2022 (Table A.1)."""
+    (Table A3) in MilkyWayPotential2022 (Table A2)."""
     rows = np.loadtxt(os.path.join(GOLDEN, "mw2022_orbits.txt"))
     h = _host_phys(workloads.mw2022_physical(), workloads.G_PC_KMS2_MSUN * 1e-3)
     for row in rows:
@@ -397,7 +397,7 @@ def test_host_potentials_match_paper_table1():
 
 
 def test_unit_conversion_matches_nbody_input_deck():
-    # App. B: the deck's 202.0992878224309 pc/Myr is the 197.61111164 km/s of Table B.2.
+    # App. B: the deck's 202.0992878224309 pc/Myr is the 197.61111164 km/s of Table A3.
     assert 197.61111164 * workloads.KMS_TO_PC_MYR == pytest.approx(202.0992878224309, rel=1e-9)
 
 
