@@ -408,7 +408,7 @@ int scf_init(const scf_config* cfg, int n_prog, const int64_t* offsets, const do
     h->cap_blk1 = std::max(h->cap_blk1, blocks);
     h->cap_rows = std::max(h->cap_rows, k1_rows(info, blocks));
   }
-  h->cap_blk3 = make_map3(h->offsets, n_prog, 64).prog.size();
+  h->cap_blk3 = make_map3(h->offsets, n_prog, 32).prog.size();  // smallest kernel 3 tile (64 threads, split)
   if (h->cap_blk1 == 0 && h->n_total > 0) return fail(SCF_ERR_UNSUPPORTED);
 
   // one allocation for the whole workspace

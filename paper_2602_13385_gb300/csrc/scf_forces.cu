@@ -2,7 +2,8 @@
 // particle, plus the tidal acceleration of the accelerating, non-rotating
 // cluster frame (Sec. 2.1), and in step mode the closing half kick.
 //
-// One thread per particle.  The block's force coefficients
+// One thread per particle (two in double precision, see the degree split
+// below).  The block's force coefficients
 // F_nlm = -G {S,T}_nlm / (b N_lm) are staged in shared memory as 4-vectors
 // (F gscale[l][n], F hscale[l][n-1]) of the cosine and sine parts; every
 // thread then runs, for each l, the scaled Gegenbauer recurrences
@@ -84,11 +85,39 @@ __global__ void __launch_bounds__(K3_TB) k3_forces(K3Args a) {
   }
   __syncthreads();
 
-  const int64_t k = a.blk_begin[blockIdx.x] + tid;
-  if (k >= a.blk_end[blockIdx.x]) return;
-  const V4 p = reinterpret_cast<const V4*>(a.pos)[k];
+  // Double precision splits each particle's degrees between two warps: warps
+  // of the first half take l >= Ls (and finish the particle), warps of the
+  // second half l < Ls, with Ls chosen so that both halves have about the
+  // same sum of (l + 1) (the work of a degree).  Twice as many, half as long
+  // warp tasks fill the 2 FP64 units per SM more evenly at the end of the
+  // grid.  The branch on a degree's owner is uniform across a warp.
+  constexpr int SPLIT = sizeof(T) == 8 ? 2 : 1;
+  constexpr int PPB = K3_TB / SPLIT;  // particles per block
+  const int half = tid / PPB;
+  const int pidx = tid - half * PPB;
+  const int64_t k = a.blk_begin[blockIdx.x] + pidx;
+  const bool live = k < a.blk_end[blockIdx.x];
+  if (SPLIT == 1 && !live) return;
+  int Ls = 0;
+  if constexpr (SPLIT == 2) {
+    const int tot = (a.lmax + 1) * (a.lmax + 2) / 2;
+    int best = tot;
+    for (int c = 0; c <= a.lmax + 1; ++c) {
+      const int d = abs(c * (c + 1) - tot);
+      if (d < best) {
+        best = d;
+        Ls = c;
+      }
+    }
+  }
+  V4 p;
+  if (live) {
+    p = reinterpret_cast<const V4*>(a.pos)[k];
+  } else {
+    p.x = p.y = p.z = p.w = (T)0;
+  }
   const bool finite = scf_finite3(p.x, p.y, p.z);
-  if (!finite) atomicOr(a.status, 1u);
+  if (!finite && half == 0) atomicOr(a.status, 1u);
   const T x = finite ? p.x : (T)0, y = finite ? p.y : (T)0, z = finite ? p.z : (T)0;
 
   const T binv = (T)(1.0 / b);
@@ -117,11 +146,13 @@ __global__ void __launch_bounds__(K3_TB) k3_forces(K3Args a) {
 #pragma unroll
   for (int l = 0; l <= LMAX; ++l) {
     if (l > a.lmax) break;
+    if (SPLIT == 2 && half == 1 && l >= Ls) break;
 #pragma unroll
     for (int m = 0; m + 2 <= l; ++m) P[m] = tla<T>(scf_lm(l, m)) * c * P1[m] - tlb<T>(scf_lm(l, m)) * P2[m];
     if (l >= 1) P[l - 1] = tlsub<T>(l) * c * P1[l - 1];
     P[l] = tldiag<T>(l);
 
+    if (SPLIT == 1 || (half == 0) == (l >= Ls)) {
     T Z0c[LMAX + 1], Z0s[LMAX + 1], Z1c[LMAX + 1], Z1s[LMAX + 1];
     const int lm0 = scf_lm(l, 0);
 #pragma unroll
@@ -193,6 +224,7 @@ __global__ void __launch_bounds__(K3_TB) k3_forces(K3Args a) {
         Ay -= (T)m * Pl * (g1c * Ws[m - 1] - g1s * Wc[m - 1]);
       }
     }
+    }  // degree owned by this half
     slq *= sq2;
     if (l >= 1) sl1q *= sq2;
 #pragma unroll
@@ -200,6 +232,23 @@ __global__ void __launch_bounds__(K3_TB) k3_forces(K3Args a) {
       P2[m] = P1[m];
       P1[m] = P[m];
     }
+  }
+  if constexpr (SPLIT == 2) {  // the first half adds the second half's sums
+    __shared__ T s_part[5][PPB];
+    if (half == 1) {
+      s_part[0][pidx] = An;
+      s_part[1][pidx] = Ax;
+      s_part[2][pidx] = Ay;
+      s_part[3][pidx] = Az;
+      s_part[4][pidx] = pot;
+    }
+    __syncthreads();
+    if (half == 1 || !live) return;
+    An += s_part[0][pidx];
+    Ax += s_part[1][pidx];
+    Ay += s_part[2][pidx];
+    Az += s_part[3][pidx];
+    pot += s_part[4][pidx];
   }
   // a = -grad psi (G and the sign of the basis are folded into F)
   V4 out;
@@ -311,7 +360,7 @@ cudaError_t prepare_t(int lmax, int nmax, int tb, ScfLaunchInfo* info, int* bloc
   return dispatch_k3<T>(tb, lmax, [&](auto k) -> cudaError_t {
     using KK = decltype(k);
     info->threads = tb;
-    info->tile = tb;
+    info->tile = sizeof(T) == 8 ? tb / 2 : tb;  // double: two warps share a particle (split degrees)
     info->variant = 0;
     // scaled (cosine, sine) per coefficient; double also the alpha + 1 family's
     info->smem = sizeof(T) * (sizeof(T) == 4 ? 2 : 4) * (size_t)nc;
