@@ -86,6 +86,7 @@ def _load():
         "or_host_accel_many": (None, [p, i64, p, p]),
         "or_tidal_many": (None, [p, p, i64, p, p]),
         "or_forces": (None, [i64, p, p, p, p, i, i, d, d, p]),
+        "or_energy": (None, [i64, p, p, p, p, p, i, i, d, d, p]),
         "or_step": (None, [i64, p, p, p, p, p, i, i, d, d, d, i, p, p]),
         "or_direct": (None, [i64, p, i64, p, d, p]),
         "or_power_l": (None, [p, i, i, d, p]),
@@ -250,6 +251,20 @@ def forces(pos, A, nmax, lmax, b, G=1.0, com=None, host=None):
     hp = None if host is None else ctypes.byref(host)
     _load().or_forces(pos.shape[0], _ptr(pos), _ptr(A), _ptr(c), hp, int(nmax), int(lmax), float(b), float(G),
                       _ptr(out))
+    return out
+
+
+def energy(pos, vel, A, nmax, lmax, b, G=1.0, com=None, host=None):
+    """(K, W, U, K + W + U): kinetic, self (1/2 sum m psi_SCF) and tidal
+    energy of the particles in the cluster frame (see or_energy)."""
+    pos = _f64(pos)
+    vel = _f64(vel)
+    A = _f64(A)
+    out = np.zeros(4)
+    c = None if com is None else _f64(com)
+    hp = None if host is None else ctypes.byref(host)
+    _load().or_energy(pos.shape[0], _ptr(pos), _ptr(vel), _ptr(A), _ptr(c), hp, int(nmax), int(lmax), float(b),
+                      float(G), _ptr(out))
     return out
 
 

@@ -486,6 +486,47 @@ void or_tidal_many(const or_host* h, const double* R, int64_t n, const double* p
   for (int64_t k = 0; k < n; ++k) or_tidal(h, R, pos + 4 * k, a + 3 * k);
 }
 
+/* Energy of a cluster in its accelerating, non-rotating frame (Sec. 2.1),
+ * for particles pos/vel and expansion coefficients A (Eq. 1a):
+ *   out[0] = K = sum_k 1/2 m_k |v_k|^2
+ *   out[1] = W = 1/2 sum_k m_k psi_SCF(x_k)   (self energy; the factor 1/2
+ *            because psi_SCF is the particles' own field)
+ *   out[2] = U = sum_k m_k phi_tid(x_k), phi_tid(x) = psi_host(R + x) - psi_host(R) + x . a_host(R),
+ *            the potential of the frame's tidal acceleration a_host(R + x) - a_host(R)
+ *            (0 without a host; evaluated in long double)
+ *   out[3] = K + W + U.
+ * Sums run in particle order in long double. */
+void or_energy(int64_t n_part, const double* pos, const double* vel, const double* A, const double* com,
+               const or_host* host, int nmax, int lmax, double b, double G, double* out) {
+  double* f = (double*)malloc(sizeof(double) * 4 * (n_part > 0 ? n_part : 1));
+  or_field(n_part, pos, A, nmax, lmax, b, G, f);
+  const int has_host = host && host->n > 0 && com;
+  long double aR[3] = {0, 0, 0}, pR = 0;
+  if (has_host) {
+    long double R[3] = {com[0], com[1], com[2]};
+    host_eval_l(host, R, aR, &pR);
+  }
+  long double K = 0, W = 0, U = 0;
+  for (int64_t k = 0; k < n_part; ++k) {
+    const double* x = pos + 4 * k;
+    const double* v = vel + 4 * k;
+    const long double m = x[3];
+    K += 0.5L * m * ((long double)v[0] * v[0] + (long double)v[1] * v[1] + (long double)v[2] * v[2]);
+    W += 0.5L * m * f[4 * k + 3];
+    if (has_host) {
+      long double P[3] = {(long double)com[0] + x[0], (long double)com[1] + x[1], (long double)com[2] + x[2]};
+      long double aP[3], pP;
+      host_eval_l(host, P, aP, &pP);
+      U += m * (pP - pR + x[0] * aR[0] + x[1] * aR[1] + x[2] * aR[2]);
+    }
+  }
+  free(f);
+  out[0] = (double)K;
+  out[1] = (double)W;
+  out[2] = (double)U;
+  out[3] = (double)(K + W + U);
+}
+
 /* acc = -grad psi_SCF (coefficients A) + tidal term (host may be NULL). */
 void or_forces(int64_t n_part, const double* pos, const double* A, const double* com, const or_host* host, int nmax,
                int lmax, double b, double G, double* acc) {
