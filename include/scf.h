@@ -228,6 +228,22 @@ int scf_autotune(scf_handle* h, const void* pos, const double* com, void* acc, i
 int scf_adjoint_level(scf_handle* h, const void* pos, const double* com, double weight, int drift, void* xbar,
                       void* vbar, double* combar, double* thetabar);
 
+/* Energy diagnostic of every progenitor in its accelerating, non-rotating
+ * frame (Sec. 2.1), in double precision whatever the handle's precision:
+ *   E_out[p][0] = K = sum_k 1/2 m_k |v_k|^2
+ *   E_out[p][1] = W = 1/2 sum_k m_k psi_SCF(x_k), psi_SCF read from acc.w
+ *   E_out[p][2] = U = sum_k m_k [psi_host(R + x_k) - psi_host(R) + x_k . a_host(R)]
+ *                 (the potential of the frame's tidal acceleration; 0 without host)
+ *   E_out[p][3] = K + W + U
+ * pos, vel, acc are the state layouts of scf_step (element type of the
+ * precision); acc must hold the accelerations and potential at pos, as
+ * scf_step and scf_forces leave them.  com as for scf_step (NULL allowed
+ * without host components).  E_out is a device [n_prog][4] doubles.  The sums
+ * run in a fixed order, so repeated calls give the same bits.  For an
+ * isolated cluster K + W is the energy the self-consistent system conserves.
+ * Errors: SCF_ERR_NULL_POINTER, SCF_ERR_MISALIGNED, SCF_ERR_CUDA. */
+int scf_energy(scf_handle* h, const void* pos, const void* vel, const void* acc, const double* com, double* E_out);
+
 /* Copies (device to device, on the handle's stream) the coefficients used by
  * the last force evaluation of scf_step into A_out ([n_prog][2*NC] doubles). */
 int scf_last_coeffs(scf_handle* h, double* A_out);

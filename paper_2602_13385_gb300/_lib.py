@@ -39,7 +39,7 @@ ERRORS = {
 # every symbol include/scf.h declares
 EXPORTS = ["scf_init", "scf_coeffs", "scf_forces", "scf_step", "scf_last_coeffs", "scf_status",
            "scf_launches_per_call", "scf_profile", "scf_profile_read", "scf_coeffs_noalloc", "scf_set_option",
-           "scf_get_option", "scf_autotune", "scf_adjoint_level", "scf_free", "scf_strerror"]
+           "scf_get_option", "scf_autotune", "scf_adjoint_level", "scf_energy", "scf_free", "scf_strerror"]
 SCF_OPT_GRAPHS = 1
 SCF_OPT_K1_TILE = 2
 SCF_OPT_K3_BLOCK = 3
@@ -94,6 +94,7 @@ def load(build: bool = True) -> ctypes.CDLL:
     lib.scf_get_option.argtypes = [vp, i, ctypes.POINTER(i)]
     lib.scf_autotune.argtypes = [vp, vp, vp, vp, i, dp]
     lib.scf_adjoint_level.argtypes = [vp, vp, vp, ctypes.c_double, i, vp, vp, vp, vp]
+    lib.scf_energy.argtypes = [vp, vp, vp, vp, vp, vp]
     lib.scf_free.argtypes = [vp]
     lib.scf_strerror.argtypes = [i]
     lib.scf_strerror.restype = ctypes.c_char_p
@@ -222,6 +223,13 @@ def scf_adjoint_level(h, pos, com, weight: float, drift: bool, xbar, vbar, comba
     _check(load().scf_adjoint_level(h, _ptr(pos, f64), _ptr(com, f64), float(weight), 1 if drift else 0,
                                     _ptr(xbar, f64), _ptr(vbar, f64), _ptr(combar, f64), _ptr(thetabar, f64)),
            "scf_adjoint_level")
+
+
+def scf_energy(h, pos, vel, acc, com, E_out):
+    """Kinetic, self, tidal and total energy per progenitor (see include/scf.h)."""
+    import torch
+    _check(load().scf_energy(h, _ptr(pos), _ptr(vel), _ptr(acc), _ptr(com, torch.float64),
+                             _ptr(E_out, torch.float64)), "scf_energy")
 
 
 def scf_free(h):

@@ -53,6 +53,7 @@ struct scf_handle {
   // adjoint: per-block tidal partials (double-precision handles only) and
   // the dual kernels' launch shapes (set by the first scf_adjoint_level call)
   double* d_adj_part = nullptr;       // [k3 blocks][SCF_ADJ_Q]
+  double* d_en_part = nullptr;        // [k3 blocks][4] energy partials
   ScfLaunchInfo k1d{}, k3d{};
   bool adj_ready = false;
   // launch timing (scf_profile)
@@ -435,6 +436,7 @@ int scf_init(const scf_config* cfg, int n_prog, const int64_t* offsets, const do
   const size_t o_b3b = take(sizeof(int64_t) * nb3);
   const size_t o_b3e = take(sizeof(int64_t) * nb3);
   const size_t o_st = take(sizeof(unsigned) * 4);
+  const size_t o_en = take(sizeof(double) * 4 * nb3);
   const size_t o_adj = cfg->precision == SCF_FP64 ? take(sizeof(double) * SCF_ADJ_Q * nb3) : off;
   if (cudaMalloc(&h->d_base, off) != cudaSuccess) {
     cudaGetLastError();
@@ -456,6 +458,7 @@ int scf_init(const scf_config* cfg, int n_prog, const int64_t* offsets, const do
   h->d_blk3_begin = reinterpret_cast<int64_t*>(base + o_b3b);
   h->d_blk3_end = reinterpret_cast<int64_t*>(base + o_b3e);
   h->d_status = reinterpret_cast<unsigned*>(base + o_st);
+  h->d_en_part = reinterpret_cast<double*>(base + o_en);
   if (cfg->precision == SCF_FP64) h->d_adj_part = reinterpret_cast<double*>(base + o_adj);
 
   std::vector<double> norm(2 * (size_t)h->nc), ksc(2 * (size_t)h->nc);
@@ -718,6 +721,28 @@ int scf_adjoint_level(scf_handle* h, const void* pos, const double* com, double 
     if (scf_k3_launch(SCF_FP64, a, h->k3_blocks, h->k3, h->stream) != cudaSuccess) return SCF_ERR_CUDA;
   }
   return SCF_OK;
+}
+
+int scf_energy(scf_handle* h, const void* pos, const void* vel, const void* acc, const double* com, double* E_out) {
+  if (!h || !E_out) return SCF_ERR_NULL_POINTER;
+  if ((!pos || !vel || !acc) && h->n_total > 0) return SCF_ERR_NULL_POINTER;
+  if (h->host.n > 0 && !com) return SCF_ERR_NULL_POINTER;
+  if (!aligned16(pos) || !aligned16(vel) || !aligned16(acc)) return SCF_ERR_MISALIGNED;
+  EnergyArgs a{};
+  a.pos = pos;
+  a.vel = vel;
+  a.acc = acc;
+  a.com = com;
+  a.blk_prog = h->d_blk3_prog;
+  a.blk_begin = h->d_blk3_begin;
+  a.blk_end = h->d_blk3_end;
+  a.n_blocks = h->k3_blocks;
+  a.n_prog = h->n_prog;
+  a.f32 = h->cfg.precision == SCF_MIXED;
+  a.host = h->host;
+  a.part = h->d_en_part;
+  a.E_out = E_out;
+  return cuda_fail(scf_energy_launch(a, h->stream));
 }
 
 int scf_last_coeffs(scf_handle* h, double* A_out) {

@@ -169,6 +169,26 @@ __device__ __forceinline__ void scf_host_accel(const ScfHostParams& hp, double x
   scf_host_accel_t<double>(hp, x, y, z, ax, ay, az);
 }
 
+// Potential of the analytic host (App. A) at (x, y, z), double precision:
+//   Hernquist -GM/(r+a);  NFW -GM ln(1 + r/r_s)/r (-GM/r_s at r = 0);
+//   Miyamoto-Nagai -GM/sqrt(R^2 + (sqrt(z^2+b^2) + a)^2).
+__device__ __forceinline__ double scf_host_pot(const ScfHostParams& hp, double x, double y, double z) {
+  double psi = 0.0;
+  const double r = sqrt(x * x + y * y + z * z);
+  for (int i = 0; i < hp.n; ++i) {
+    const double GM = hp.GM[i], A = hp.a[i];
+    if (hp.kind[i] == 1) {
+      psi -= GM / (r + A);
+    } else if (hp.kind[i] == 2) {
+      psi -= r > 0.0 ? GM * log1p(r / A) / r : GM / A;
+    } else if (hp.kind[i] == 3) {
+      const double zab = sqrt(z * z + hp.b[i] * hp.b[i]) + A;
+      psi -= GM / sqrt(x * x + y * y + zab * zab);
+    }
+  }
+  return psi;
+}
+
 // Tidal acceleration a_host(R + x) - a_host(R) in single precision, written
 // as divided differences so that no two large terms are subtracted: with
 // P = R + x, r0 = |R|, r1 = |P| and dr = r1 - r0 = (2 R.x + |x|^2)/(r1 + r0),

@@ -126,6 +126,24 @@ struct ComAdjArgs {
   ScfHostParams host;
 };
 
+// Energy diagnostic (scf_energy.cu): per kernel-3 block partial sums of the
+// kinetic, self and tidal energy, then a fixed-order sum per progenitor.
+struct EnergyArgs {
+  const void* pos;
+  const void* vel;
+  const void* acc;           // acc.w = psi_SCF at pos
+  const double* com;         // [n_prog][6] or null
+  const int* blk_prog;
+  const int64_t* blk_begin;
+  const int64_t* blk_end;
+  int n_blocks, n_prog;
+  int f32;                   // particle arrays are float4 (mixed) or double4
+  ScfHostParams host;
+  double* part;              // [n_blocks][4]
+  double* E_out;             // [n_prog][4]
+};
+cudaError_t scf_energy_launch(const EnergyArgs& a, cudaStream_t s);
+
 struct ScfLaunchInfo {
   int threads;   // threads per block
   int tile;      // particles per tile (block ranges are whole tiles)

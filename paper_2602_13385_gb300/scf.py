@@ -116,6 +116,16 @@ class SCF:
             self._check_particles(t, nm)
         _lib.scf_step(self._h, pos, vel, acc, com, nsteps)
 
+    def energy(self, pos, vel, acc, com=None, out: torch.Tensor | None = None):
+        """(n_prog, 4) float64 = (kinetic, self, tidal, total) energy per
+        progenitor in its frame; ``acc`` must hold the accelerations and
+        potential at ``pos`` (as ``step`` and ``forces`` leave them)."""
+        for t, nm in ((pos, "pos"), (vel, "vel"), (acc, "acc")):
+            self._check_particles(t, nm)
+        out = torch.empty((self.n_prog, 4), dtype=torch.float64, device=self.device) if out is None else out
+        _lib.scf_energy(self._h, pos, vel, acc, com, out)
+        return out
+
     def last_coeffs(self, out: torch.Tensor | None = None):
         out = self.new_coeffs() if out is None else out
         _lib.scf_last_coeffs(self._h, out)

@@ -90,4 +90,5 @@ def test_null_handle_is_rejected(lib):
     assert lib.scf_step(None, None, None, None, None, 1) == -2
     assert lib.scf_status(None, None) == -2
     assert lib.scf_adjoint_level(None, None, None, 0.005, 1, None, None, None, None) == -2
+    assert lib.scf_energy(None, None, None, None, None, None) == -2
     assert lib.scf_free(None) == 0
