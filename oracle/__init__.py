@@ -293,6 +293,80 @@ def direct(src, tgt, G=1.0):
     return out
 
 
+# ---------------------------------------------------------------- escape physics
+def boundedness(pos, vel, G=1.0, kin=0.5, frac=0.999):
+    """Energy-based boundedness and the radius of the coefficient set (Sec. 2.3).
+
+    Particle i is bound when its cluster-frame energy
+    ``E_i = kin |v_i|^2 - sum_{j != i} G m_j / |r_i - r_j|`` is negative, the
+    sum being the unsoftened direct summation over every particle of the
+    progenitor (coincident pairs are skipped like the self term).  The
+    footnote of Sec. 2.3 prints ``kin = 1``; the standard specific energy
+    has ``kin = 1/2`` (the default).  ``r_x`` is the smallest radius that
+    encloses the fraction ``frac`` of the bound particles, i.e. the k-th
+    smallest cluster-frame radius among them with ``k = ceil(frac n_bound)``;
+    the particles that enter Eq. 3b are those with ``r <= r_x``.  With no
+    bound particle ``r_x = 0``.  Radii are compared through
+    ``r^2 = (x x + y y) + z z`` in double precision.
+
+    Returns ``(E, bound, r_x^2, mask, M_bound)``.
+    """
+    pos = _f64(pos)
+    vel = _f64(vel)
+    n = pos.shape[0]
+    if n == 0:
+        return np.zeros(0), np.zeros(0, bool), 0.0, np.zeros(0, bool), 0.0
+    v2 = vel[:, 0] * vel[:, 0] + vel[:, 1] * vel[:, 1] + vel[:, 2] * vel[:, 2]
+    E = kin * v2 + direct(pos, pos, G)[:, 3]
+    bound = E < 0.0
+    x, y, z = pos[:, 0], pos[:, 1], pos[:, 2]
+    r2 = x * x + y * y + z * z
+    nb = int(bound.sum())
+    if nb == 0:
+        rx2 = 0.0
+    else:
+        k = max(1, int(np.ceil(frac * float(nb))))
+        rx2 = float(np.sort(r2[bound])[min(k, nb) - 1])
+    mask = r2 <= rx2
+    return E, bound, rx2, mask, float(pos[bound, 3].sum())
+
+
+def tidal_scales(host, R, M_c, eta=1.0 / 400.0, G=1.0):
+    """Tidal tensor, its eigenvalues, the tidal radius and the integration
+    timestep at centre positions ``R`` (n, 3) for cluster masses ``M_c`` (n,).
+
+    * ``T_ij = -d^2 psi_host / dx_i dx_j`` (Sec. 2.3, App. A), here the
+      derivative of the host acceleration (``tidal_tensor``);
+    * eigenvalues ``l1 >= l2 >= l3`` (numpy's symmetric eigensolver);
+    * tidal radius ``r_t = (G M_c / l1e)^(1/3)`` with
+      ``l1e = l1 - (l2 + l3)/2`` (Sec. 4.1, footnote on generic orbits);
+      infinite when ``l1e <= 0``;
+    * integration timestep ``dt_int = sqrt(eta) (|T|_F^2 / 6)^(-1/4)``
+      (Sec. 2.3, with the Frobenius norm).
+
+    Returns an (n, 16) array laid out as ``T`` (row-major, 9), ``l1, l2, l3``,
+    ``|T|_F``, ``l1e``, ``r_t``, ``dt_int``.
+    """
+    R = _f64(np.atleast_2d(R))[:, :3].copy()
+    M_c = _f64(np.atleast_1d(M_c))
+    T = tidal_tensor(host, R)
+    out = np.zeros((R.shape[0], 16))
+    for i in range(R.shape[0]):
+        Ts = 0.5 * (T[i] + T[i].T)
+        lam = np.sort(np.linalg.eigvalsh(Ts))[::-1]
+        fro = float(np.sqrt(np.sum(T[i] * T[i])))
+        l1e = lam[0] - 0.5 * (lam[1] + lam[2])
+        r_t = (G * M_c[i] / l1e) ** (1.0 / 3.0) if l1e > 0 else np.inf
+        dt_int = np.sqrt(eta) * (fro * fro / 6.0) ** (-0.25) if fro > 0 else np.inf
+        out[i, :9] = T[i].reshape(9)
+        out[i, 9:12] = lam
+        out[i, 12] = fro
+        out[i, 13] = l1e
+        out[i, 14] = r_t
+        out[i, 15] = dt_int
+    return out
+
+
 def power_l(A, nmax, lmax, b):
     """E_l = sum_{n,m} |a_nlm|^2 in the bi-orthonormal normalisation of Eq. 3a."""
     A = _f64(A)
