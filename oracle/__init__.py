@@ -87,7 +87,7 @@ def _load():
         "or_tidal_many": (None, [p, p, i64, p, p]),
         "or_forces": (None, [i64, p, p, p, p, i, i, d, d, p]),
         "or_energy": (None, [i64, p, p, p, p, p, i, i, d, d, p]),
-        "or_step": (None, [i64, p, p, p, p, p, i, i, d, d, d, i, p, p]),
+        "or_step": (None, [i64, p, p, p, p, p, i, i, d, d, d, i, p, p, p]),
         "or_direct": (None, [i64, p, i64, p, d, p]),
         "or_power_l": (None, [p, i, i, d, p]),
         "or_num_threads": (i, []),
@@ -268,10 +268,11 @@ def energy(pos, vel, A, nmax, lmax, b, G=1.0, com=None, host=None):
     return out
 
 
-def step(pos, vel, acc, nmax, lmax, b, dt, nsteps, G=1.0, com=None, host=None, A_frozen=None):
+def step(pos, vel, acc, nmax, lmax, b, dt, nsteps, G=1.0, com=None, host=None, A_frozen=None, mask=None):
     """Kick-drift-kick leapfrog; returns new ``(pos, vel, acc, com, A_last)``.
 
-    ``acc`` must hold the acceleration at ``pos`` (from :func:`forces`)."""
+    ``acc`` must hold the acceleration at ``pos`` (from :func:`forces`);
+    ``mask`` (optional, per particle) is the coefficient set of Eq. 3b."""
     pos = _f64(pos).copy()
     vel = _f64(vel).copy()
     acc = _f64(acc).copy()
@@ -279,8 +280,9 @@ def step(pos, vel, acc, nmax, lmax, b, dt, nsteps, G=1.0, com=None, host=None, A
     A_out = np.zeros(2 * n_coef(nmax, lmax))
     hp = None if host is None else ctypes.byref(host)
     Af = None if A_frozen is None else _f64(A_frozen)
+    mk = None if mask is None else np.ascontiguousarray(mask, dtype=np.uint8)
     _load().or_step(pos.shape[0], _ptr(pos), _ptr(vel), _ptr(acc), _ptr(com), hp, int(nmax), int(lmax), float(b),
-                    float(G), float(dt), int(nsteps), _ptr(Af), _ptr(A_out))
+                    float(G), float(dt), int(nsteps), _ptr(Af), _ptr(mk), _ptr(A_out))
     return pos, vel, acc, com, A_out
 
 
@@ -365,6 +367,45 @@ def tidal_scales(host, R, M_c, eta=1.0 / 400.0, G=1.0):
         out[i, 14] = r_t
         out[i, 15] = dt_int
     return out
+
+
+def evolve(pos, vel, acc, nmax, lmax, b, dt, nsteps, G=1.0, com=None, host=None, kin=0.5, frac=0.999,
+           eta=1.0 / 400.0, max_steps=1000):
+    """Leapfrog with the escape physics of Sec. 2.3.  At the start of every
+    integration timestep: the boundedness test and the coefficient set
+    r <= r_x (:func:`boundedness`), the field of that set at the current
+    positions, and the length of the integration timestep, dt_int of
+    :func:`tidal_scales` at the current centre with the bound mass as M_c,
+    taken as ``clamp(floor(dt_int / dt), 1, max_steps)`` leapfrog steps
+    (``max_steps`` without a host; fewer at the end).
+
+    Returns ``(pos, vel, acc, com, bound, mask, stats, n_int)`` with ``bound``,
+    ``mask`` and ``stats = (n_bound, M_bound, r_x, set size)`` as of the start
+    of the last integration timestep."""
+    pos = _f64(pos).copy()
+    vel = _f64(vel).copy()
+    com = np.zeros(6) if com is None else _f64(com).copy()
+    has_host = host is not None and host.n > 0
+    done, n_int = 0, 0
+    bound = mask = None
+    stats = np.zeros(4)
+    while done < nsteps:
+        E, bound, rx2, mask, Mb = boundedness(pos, vel, G, kin, frac)
+        stats = np.array([bound.sum(), Mb, np.sqrt(rx2), mask.sum()], dtype=np.float64)
+        A = coeffs(pos, nmax, lmax, b, mask=mask)
+        acc = forces(pos, A, nmax, lmax, b, G, com=com if has_host else None, host=host if has_host else None)
+        k = max_steps
+        if has_host:
+            dt_int = tidal_scales(host, com[:3], np.array([Mb]), eta, G)[0, 15]
+            ks = np.floor(dt_int / dt)
+            if ks < k:
+                k = 1 if ks < 1 else int(ks)
+        k = min(k, nsteps - done)
+        pos, vel, acc, com, _ = step(pos, vel, acc, nmax, lmax, b, dt, k, G, com=com if has_host else None,
+                                     host=host if has_host else None, mask=mask)
+        done += k
+        n_int += 1
+    return pos, vel, acc, com, bound, mask, stats, n_int
 
 
 def power_l(A, nmax, lmax, b):

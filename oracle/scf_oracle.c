@@ -552,10 +552,13 @@ void or_forces(int64_t n_part, const double* pos, const double* A, const double*
  * com = (R, V) of the cluster frame in the host frame; it moves with the same
  * kick-drift-kick in the host field alone (Sec. 2.1).  The coefficients are
  * recomputed from the particles at every force evaluation unless A_frozen is
- * given, in which case the potential is static.  A_out (nullable) receives
- * the last coefficients used. */
+ * given, in which case the potential is static.  mask (nullable) is the
+ * coefficient set: only particles with mask[k] != 0 enter Eq. 3b, every
+ * particle moves in the field (Sec. 2.3).  A_out (nullable) receives the last
+ * coefficients used. */
 void or_step(int64_t n_part, double* pos, double* vel, double* acc, double* com, const or_host* host, int nmax,
-             int lmax, double b, double G, double dt, int nsteps, const double* A_frozen, double* A_out) {
+             int lmax, double b, double G, double dt, int nsteps, const double* A_frozen, const uint8_t* mask,
+             double* A_out) {
   const int nc = (nmax + 1) * nlm_count(lmax);
   double* A = (double*)malloc(sizeof(double) * 2 * nc);
   int has_host = host && host->n > 0;
@@ -578,7 +581,7 @@ void or_step(int64_t n_part, double* pos, double* vel, double* acc, double* com,
       }
     }
     if (A_frozen) memcpy(A, A_frozen, sizeof(double) * 2 * nc);
-    else or_coeffs(n_part, pos, NULL, nmax, lmax, b, A);
+    else or_coeffs(n_part, pos, mask, nmax, lmax, b, A);
     or_forces(n_part, pos, A, com, host, nmax, lmax, b, G, acc);
     if (has_host) {
       or_host_accel(host, com, aR, NULL);

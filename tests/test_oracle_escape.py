@@ -14,6 +14,11 @@
   dt_int = sqrt(eta) sqrt(R^3 / GM) (Sec. 2.3, Sec. 4.1 footnote); the trace
   of the tidal tensor is -4 pi G rho_host (Poisson's equation) for each host
   component.
+* The evolve schedule (Sec. 2.3): with every star bound and inside r_x it is
+  the plain leapfrog bit for bit; an unbound star beyond r_x leaves the
+  cluster's evolution bit for bit unchanged (and changes it when left in the
+  coefficient sum); on a circular orbit about a point mass, where dt_int is
+  constant and known in closed form, the run splits into ceil(n / k) pieces.
 """
 import math
 
@@ -135,3 +140,58 @@ def test_tidal_trace_is_minus_four_pi_G_rho(kind, M, a, b):
         assert abs(tr + 4 * math.pi * _rho(kind, M, a, b, P)) < 1e-10 * scale, (i, tr)
         assert abs(out[i, 9:12].sum() - tr) < 1e-10 * scale
         assert out[i, 9] >= out[i, 10] >= out[i, 11]
+
+
+# ---------------------------------------------------------------- the evolve schedule
+def test_evolve_without_escapers_is_the_plain_leapfrog():
+    # every particle bound and inside r_100: the coefficient set is everything,
+    # so refreshing at every integration timestep changes nothing
+    pos, vel = workloads.plummer(256, seed=15)
+    b = workloads.basis_scale(workloads.half_mass_radius(pos))
+    nmax, lmax, dt = 4, 2, 0.01
+    assert oracle.boundedness(pos, vel, frac=1.0)[3].all()
+    acc = oracle.forces(pos, oracle.coeffs(pos, nmax, lmax, b), nmax, lmax, b)
+    p1, v1, a1, _, _ = oracle.step(pos, vel, acc, nmax, lmax, b, dt, 7)
+    p2, v2, a2, _, bound, mask, stats, n_int = oracle.evolve(pos, vel, acc, nmax, lmax, b, dt, 7, frac=1.0,
+                                                             max_steps=3)
+    assert n_int == 3 and mask.all() and stats[3] == 256
+    assert np.array_equal(p1, p2) and np.array_equal(v1, v2) and np.array_equal(a1, a2)
+
+
+def test_escaper_beyond_r_x_does_not_feed_back():
+    # an unbound star far outside r_x is left out of Eq. 3b, so the cluster
+    # evolves exactly as without it; with the star in the coefficients it would not
+    pos, vel = workloads.plummer(384, seed=16)
+    b = workloads.basis_scale(workloads.half_mass_radius(pos))
+    nmax, lmax, dt, n = 4, 2, 0.01, 384
+    D = 40.0
+    v_esc = math.sqrt(2.0 / D)
+    p_e = np.vstack([pos, [[0.0, 0.0, D, 1.0 / n]]])
+    v_e = np.vstack([vel, [[0.0, 0.0, 3.0 * v_esc, 0.0]]])
+    E = oracle.boundedness(pos, vel)[0]
+    assert np.min(np.abs(E)) > 1e-2 * (1.0 / n) * 40   # no marginal star the escaper's potential could flip
+    acc = oracle.forces(pos, oracle.coeffs(pos, nmax, lmax, b), nmax, lmax, b)
+    acc_e = oracle.forces(p_e, oracle.coeffs(p_e, nmax, lmax, b, mask=np.r_[np.ones(n), 0]), nmax, lmax, b)
+    r1 = oracle.evolve(pos, vel, acc, nmax, lmax, b, dt, 6, max_steps=2)
+    r2 = oracle.evolve(p_e, v_e, acc_e, nmax, lmax, b, dt, 6, max_steps=2)
+    assert not r2[4][-1] and not r2[5][-1]
+    assert np.array_equal(r1[0], r2[0][:n]) and np.array_equal(r1[1], r2[1][:n])
+    assert r1[6][0] == r2[6][0] and r1[6][2] == r2[6][2]
+    p3 = oracle.step(p_e, v_e, acc_e, nmax, lmax, b, dt, 6)[0]        # escaper left in the sum
+    assert np.max(np.abs(p3[:n] - r1[0])) > 1e-12
+
+
+def test_integration_timestep_count_on_a_circular_orbit():
+    # point-mass host: dt_int = sqrt(eta) sqrt(R^3 / GM) is constant on a circular
+    # orbit; with dt_int / dt = 7.4 the run is split into ceil(30 / 7) pieces
+    GM, eta, dt = 1.0e4, 1.0 / 400.0, 0.01
+    R = (7.4 * dt / math.sqrt(eta)) ** (2.0 / 3.0) * GM ** (1.0 / 3.0)
+    host = oracle.host_struct([(oracle.HOST_HERNQUIST, GM, 1e-9 * R, 0.0)])
+    com = np.array([R, 0.0, 0.0, 0.0, math.sqrt(GM / R), 0.0])
+    pos, vel = workloads.plummer(128, seed=17)
+    b = workloads.basis_scale(workloads.half_mass_radius(pos))
+    acc = oracle.forces(pos, oracle.coeffs(pos, 2, 1, b), 2, 1, b, com=com, host=host)
+    out = oracle.evolve(pos, vel, acc, 2, 1, b, dt, 30, com=com, host=host, eta=eta)
+    assert out[7] == 5
+    ts = oracle.tidal_scales(host, out[3][:3], np.array([1.0]), eta)[0]
+    assert 7.0 < ts[15] / dt < 8.0
