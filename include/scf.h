@@ -40,7 +40,9 @@
  * pointer), always double precision.
  *
  * Streams and ownership.  Every call enqueues work on the stream given to
- * scf_init and returns without waiting, except scf_status and scf_free.  The
+ * scf_init and returns without waiting, except those whose description says
+ * they synchronise (scf_status, scf_free, scf_autotune, scf_set_option,
+ * scf_set_mask, scf_evolve).  The
  * caller owns all particle, coefficient and centre buffers; the handle owns
  * its workspace (block partials, block maps, a coefficient buffer, the status
  * word), allocated once in scf_init.  No call allocates after scf_init.
@@ -243,6 +245,79 @@ int scf_adjoint_level(scf_handle* h, const void* pos, const double* com, double 
  * isolated cluster K + W is the energy the self-consistent system conserves.
  * Errors: SCF_ERR_NULL_POINTER, SCF_ERR_MISALIGNED, SCF_ERR_CUDA. */
 int scf_energy(scf_handle* h, const void* pos, const void* vel, const void* acc, const double* com, double* E_out);
+
+/* ---- Escape physics (Sec. 2.3; Sec. 4.1 footnote on the tidal radius) ---- */
+
+/* Boundedness of every particle and the coefficient set of Eq. 3b.
+ * Particle i of progenitor p is bound when its cluster-frame energy
+ *   E_i = kin |v_i|^2 - sum_{j != i, j in p} G m_j / |x_i - x_j|
+ * is negative (unsoftened direct summation over all particles of p; pairs at
+ * zero separation and pairs with a non-finite separation add nothing, so a
+ * particle with a non-finite position is never bound).  The footnote of
+ * Sec. 2.3 prints kin = 1; kin = 1/2 is the standard specific energy.
+ * r_x is the energy-based Lagrange radius: the k-th smallest cluster-frame
+ * radius among p's bound particles, k = ceil(frac n_bound) (r_x = 0 when none
+ * is bound); the coefficient set is r <= r_x (frac = 0.999 in the paper).
+ * Radii are compared as r^2 = (x x + y y) + z z in double precision.
+ * In double precision the pair sums are double; in mixed precision each pair
+ * term and blocks of 64 of them are float, added in double.
+ *   pos, vel   device [N][4] in the handle's element type (16-byte aligned)
+ *   kin        > 0 and finite;  frac in (0, 1]
+ *   E_out      device [N] doubles (E_i), or NULL
+ *   bound_out  device [N] bytes, 1 = bound (required when N > 0)
+ *   mask_out   device [N] bytes, 1 = r <= r_x, or NULL
+ *   stats_out  device [n_prog][4] doubles: n_bound, bound mass, r_x, size of the set
+ * All sums have a fixed order (bitwise reproducible).  Cost O(sum_p N_p^2).
+ * The workspace for it (8 (S+1) N bytes, S <= 16 pair-sum segments) is
+ * reserved by scf_init.
+ * Errors: SCF_ERR_NULL_POINTER, SCF_ERR_MISALIGNED, SCF_ERR_INVALID_ARG, SCF_ERR_CUDA. */
+int scf_bound(scf_handle* h, const void* pos, const void* vel, double kin, double frac, double* E_out,
+              uint8_t* bound_out, uint8_t* mask_out, double* stats_out);
+
+/* Tidal scales of every progenitor at its centre R = com[p][0..2] (Sec. 2.3):
+ *   out[p][0..8]  T_ij = -d^2 psi_host / dx_i dx_j (row-major), from the host components
+ *   out[p][9..11] eigenvalues l1 >= l2 >= l3 of T
+ *   out[p][12]    |T|_F (Frobenius norm)
+ *   out[p][13]    l1e = l1 - (l2 + l3)/2
+ *   out[p][14]    r_t = (G M_c[p] / l1e)^(1/3) (Sec. 4.1 footnote); +inf when l1e <= 0;
+ *                 0 when M_c is NULL
+ *   out[p][15]    dt_int = sqrt(eta) (|T|_F^2 / 6)^(-1/4); +inf without host
+ * com: device [n_prog][6] (NULL allowed without host components: R = 0);
+ * M_c: device [n_prog] cluster masses or NULL; eta > 0 (1/400 in the paper);
+ * out: device [n_prog][16] doubles.
+ * Errors: SCF_ERR_NULL_POINTER, SCF_ERR_INVALID_ARG, SCF_ERR_CUDA. */
+int scf_tidal(scf_handle* h, const double* com, const double* M_c, double eta, double* out);
+
+/* Sets the coefficient set used by scf_step's coefficient pass: a device
+ * [N] byte mask (1 = the particle enters Eq. 3b), or NULL for all particles
+ * (the default).  The handle keeps the pointer, not the bytes; the caller
+ * keeps the buffer alive and may rewrite it between calls.  Changing the
+ * pointer synchronises the stream and drops the captured step. */
+int scf_set_mask(scf_handle* h, const uint8_t* mask);
+
+typedef struct scf_escape_params {
+  double kin;     /* kinetic factor of the boundedness test (0.5, or 1 as printed) */
+  double frac;    /* the coefficient set is r <= r_x of this fraction (0.999) */
+  double eta;     /* integration-timestep parameter (1/400) */
+  int max_steps;  /* most leapfrog steps per integration timestep (>= 1) */
+} scf_escape_params;
+
+/* nsteps leapfrog steps with the escape physics of Sec. 2.3.  At the start of
+ * every integration timestep: scf_bound (bound flags, the mask r <= r_x and
+ * stats, into the caller's buffers), the mask becomes the step's coefficient
+ * set (scf_set_mask), acc is recomputed at the current positions from that
+ * set, and the next integration timestep is the smallest dt_int of scf_tidal
+ * at the current centres with M_c = the bound mass; it runs
+ * clamp(floor(dt_int / dt), 1, max_steps) steps of scf_step (fewer at the
+ * end; max_steps without host components).  Reads dt_int back once per
+ * integration timestep (a stream synchronisation).  On return the step mask
+ * stays set to `mask`, bound/mask/stats describe the state at the start of
+ * the last integration timestep, and *n_refresh (if not NULL) is the number
+ * of integration timesteps.  Buffers as for scf_step and scf_bound.
+ * Errors: those of scf_step and scf_bound; SCF_ERR_INVALID_ARG for a bad
+ * parameter or dt <= 0. */
+int scf_evolve(scf_handle* h, void* pos, void* vel, void* acc, double* com, int nsteps, const scf_escape_params* ep,
+               uint8_t* bound, uint8_t* mask, double* stats, int* n_refresh);
 
 /* Copies (device to device, on the handle's stream) the coefficients used by
  * the last force evaluation of scf_step into A_out ([n_prog][2*NC] doubles). */

@@ -39,7 +39,8 @@ ERRORS = {
 # every symbol include/scf.h declares
 EXPORTS = ["scf_init", "scf_coeffs", "scf_forces", "scf_step", "scf_last_coeffs", "scf_status",
            "scf_launches_per_call", "scf_profile", "scf_profile_read", "scf_coeffs_noalloc", "scf_set_option",
-           "scf_get_option", "scf_autotune", "scf_adjoint_level", "scf_energy", "scf_free", "scf_strerror"]
+           "scf_get_option", "scf_autotune", "scf_adjoint_level", "scf_energy", "scf_bound", "scf_tidal",
+           "scf_set_mask", "scf_evolve", "scf_free", "scf_strerror"]
 SCF_OPT_GRAPHS = 1
 SCF_OPT_K1_TILE = 2
 SCF_OPT_K3_BLOCK = 3
@@ -54,6 +55,11 @@ class ScfError(RuntimeError):
 
 class scf_host_component(ctypes.Structure):
     _fields_ = [("kind", ctypes.c_int), ("M", ctypes.c_double), ("a", ctypes.c_double), ("b", ctypes.c_double)]
+
+
+class scf_escape_params(ctypes.Structure):
+    _fields_ = [("kin", ctypes.c_double), ("frac", ctypes.c_double), ("eta", ctypes.c_double),
+                ("max_steps", ctypes.c_int)]
 
 
 class scf_config(ctypes.Structure):
@@ -95,6 +101,12 @@ def load(build: bool = True) -> ctypes.CDLL:
     lib.scf_autotune.argtypes = [vp, vp, vp, vp, i, dp]
     lib.scf_adjoint_level.argtypes = [vp, vp, vp, ctypes.c_double, i, vp, vp, vp, vp]
     lib.scf_energy.argtypes = [vp, vp, vp, vp, vp, vp]
+    d = ctypes.c_double
+    lib.scf_bound.argtypes = [vp, vp, vp, d, d, vp, vp, vp, vp]
+    lib.scf_tidal.argtypes = [vp, vp, vp, d, vp]
+    lib.scf_set_mask.argtypes = [vp, vp]
+    lib.scf_evolve.argtypes = [vp, vp, vp, vp, vp, i, ctypes.POINTER(scf_escape_params), vp, vp, vp,
+                               ctypes.POINTER(i)]
     lib.scf_free.argtypes = [vp]
     lib.scf_strerror.argtypes = [i]
     lib.scf_strerror.restype = ctypes.c_char_p
@@ -230,6 +242,36 @@ def scf_energy(h, pos, vel, acc, com, E_out):
     import torch
     _check(load().scf_energy(h, _ptr(pos), _ptr(vel), _ptr(acc), _ptr(com, torch.float64),
                              _ptr(E_out, torch.float64)), "scf_energy")
+
+
+def scf_bound(h, pos, vel, kin: float, frac: float, E_out, bound_out, mask_out, stats_out):
+    import torch
+    _check(load().scf_bound(h, _ptr(pos), _ptr(vel), float(kin), float(frac), _ptr(E_out, torch.float64),
+                            _ptr(bound_out, torch.uint8), _ptr(mask_out, torch.uint8),
+                            _ptr(stats_out, torch.float64)), "scf_bound")
+
+
+def scf_tidal(h, com, M_c, eta: float, out):
+    import torch
+    _check(load().scf_tidal(h, _ptr(com, torch.float64), _ptr(M_c, torch.float64), float(eta),
+                            _ptr(out, torch.float64)), "scf_tidal")
+
+
+def scf_set_mask(h, mask):
+    import torch
+    _check(load().scf_set_mask(h, _ptr(mask, torch.uint8)), "scf_set_mask")
+
+
+def scf_evolve(h, pos, vel, acc, com, nsteps: int, kin: float, frac: float, eta: float, max_steps: int,
+               bound, mask, stats) -> int:
+    """Returns the number of integration timesteps."""
+    import torch
+    ep = scf_escape_params(float(kin), float(frac), float(eta), int(max_steps))
+    n = ctypes.c_int(0)
+    _check(load().scf_evolve(h, _ptr(pos), _ptr(vel), _ptr(acc), _ptr(com, torch.float64), int(nsteps),
+                             ctypes.byref(ep), _ptr(bound, torch.uint8), _ptr(mask, torch.uint8),
+                             _ptr(stats, torch.float64), ctypes.byref(n)), "scf_evolve")
+    return n.value
 
 
 def scf_free(h):

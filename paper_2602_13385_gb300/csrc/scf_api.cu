@@ -10,6 +10,7 @@
 #include "../../include/scf.h"
 #include "scf_device.cuh"
 #include "scf_internal.h"
+#include "scf_escape.h"
 
 struct scf_handle {
   scf_config cfg;
@@ -54,6 +55,14 @@ struct scf_handle {
   // the dual kernels' launch shapes (set by the first scf_adjoint_level call)
   double* d_adj_part = nullptr;       // [k3 blocks][SCF_ADJ_Q]
   double* d_en_part = nullptr;        // [k3 blocks][4] energy partials
+  // escape physics: particle offsets, pair-sum segments, radius keys, tidal scales
+  int64_t* d_off = nullptr;              // [n_prog+1]
+  double* d_bpart = nullptr;             // [bound_split][n_total]
+  unsigned long long* d_key = nullptr;   // [n_total]
+  double* d_tid = nullptr;               // [n_prog][16]
+  int bound_split = 1;
+  int64_t bound_chunks = 0;              // pair-kernel i-blocks of the largest progenitor
+  const uint8_t* step_mask = nullptr;    // coefficient set of scf_step (scf_set_mask)
   ScfLaunchInfo k1d{}, k3d{};
   bool adj_ready = false;
   // launch timing (scf_profile)
@@ -438,6 +447,20 @@ int scf_init(const scf_config* cfg, int n_prog, const int64_t* offsets, const do
   const size_t o_st = take(sizeof(unsigned) * 4);
   const size_t o_en = take(sizeof(double) * 4 * nb3);
   const size_t o_adj = cfg->precision == SCF_FP64 ? take(sizeof(double) * SCF_ADJ_Q * nb3) : off;
+  {
+    const int64_t chunk = scf_bound_chunk();
+    int64_t chunks = 0;
+    for (int p = 0; p < n_prog; ++p) {
+      const int64_t c = (h->offsets[p + 1] - h->offsets[p] + chunk - 1) / chunk;
+      chunks += c;
+      h->bound_chunks = std::max(h->bound_chunks, c);
+    }
+    h->bound_split = scf_bound_split(chunks, h->n_sm);
+  }
+  const size_t o_off = take(sizeof(int64_t) * (n_prog + 1));
+  const size_t o_bpart = take(sizeof(double) * (size_t)h->bound_split * (size_t)h->n_total);
+  const size_t o_key = take(sizeof(unsigned long long) * (size_t)h->n_total);
+  const size_t o_tid = take(sizeof(double) * 16 * (size_t)n_prog);
   if (cudaMalloc(&h->d_base, off) != cudaSuccess) {
     cudaGetLastError();
     return fail(SCF_ERR_OUT_OF_MEMORY);
@@ -460,6 +483,10 @@ int scf_init(const scf_config* cfg, int n_prog, const int64_t* offsets, const do
   h->d_status = reinterpret_cast<unsigned*>(base + o_st);
   h->d_en_part = reinterpret_cast<double*>(base + o_en);
   if (cfg->precision == SCF_FP64) h->d_adj_part = reinterpret_cast<double*>(base + o_adj);
+  h->d_off = reinterpret_cast<int64_t*>(base + o_off);
+  h->d_bpart = reinterpret_cast<double*>(base + o_bpart);
+  h->d_key = reinterpret_cast<unsigned long long*>(base + o_key);
+  h->d_tid = reinterpret_cast<double*>(base + o_tid);
 
   std::vector<double> norm(2 * (size_t)h->nc), ksc(2 * (size_t)h->nc);
   scf_make_norm(cfg->nmax, cfg->lmax, norm.data());
@@ -469,6 +496,7 @@ int scf_init(const scf_config* cfg, int n_prog, const int64_t* offsets, const do
                                                   : put(h->d_kscale, ksc.data(), sizeof(double) * ksc.size());
   bool ok = ksc_ok && put(h->d_norm, norm.data(), sizeof(double) * norm.size()) &&
             put(h->d_b, bs.data(), sizeof(double) * n_prog) &&
+            put(h->d_off, h->offsets.data(), sizeof(int64_t) * (n_prog + 1)) &&
             cudaMemset(h->d_status, 0, sizeof(unsigned) * 4) == cudaSuccess &&
             cudaMemset(h->d_A, 0, sizeof(double) * 2 * (size_t)h->nc * n_prog) == cudaSuccess;
   if (!ok) return fail(SCF_ERR_CUDA);
@@ -502,7 +530,7 @@ int scf_forces(scf_handle* h, const void* pos, const double* A, const double* co
 namespace {
 
 int launch_step(scf_handle* h, void* pos, void* vel, void* acc, double* com) {
-  int rc = run_coeffs(h, pos, vel, acc, nullptr, h->d_A, com, SCF_MODE_STEP);
+  int rc = run_coeffs(h, pos, vel, acc, h->step_mask, h->d_A, com, SCF_MODE_STEP);
   if (rc != SCF_OK) return rc;
   return run_forces(h, pos, vel, acc, com, SCF_MODE_STEP);
 }
@@ -743,6 +771,113 @@ int scf_energy(scf_handle* h, const void* pos, const void* vel, const void* acc,
   a.part = h->d_en_part;
   a.E_out = E_out;
   return cuda_fail(scf_energy_launch(a, h->stream));
+}
+
+int scf_bound(scf_handle* h, const void* pos, const void* vel, double kin, double frac, double* E_out,
+              uint8_t* bound_out, uint8_t* mask_out, double* stats_out) {
+  if (!h || !stats_out) return SCF_ERR_NULL_POINTER;
+  if ((!pos || !vel || !bound_out) && h->n_total > 0) return SCF_ERR_NULL_POINTER;
+  if (!aligned16(pos) || !aligned16(vel)) return SCF_ERR_MISALIGNED;
+  if (!(kin > 0.0) || !std::isfinite(kin) || !(frac > 0.0 && frac <= 1.0)) return SCF_ERR_INVALID_ARG;
+  BoundArgs a{};
+  a.pos = pos;
+  a.vel = vel;
+  a.prog_off = h->d_off;
+  a.n_prog = h->n_prog;
+  a.n_total = h->n_total;
+  a.f32 = h->cfg.precision == SCF_MIXED;
+  a.split = h->bound_split;
+  a.G = h->cfg.G;
+  a.kin = kin;
+  a.frac = frac;
+  a.part = h->d_bpart;
+  a.key = h->d_key;
+  a.E_out = E_out;
+  a.bound = bound_out;
+  a.mask = mask_out;
+  a.stats = stats_out;
+  return cuda_fail(scf_bound_launch(a, h->bound_chunks, h->stream));
+}
+
+namespace {
+
+int launch_tidal(scf_handle* h, const double* com, const double* M_c, int M_stride, double eta, double* out) {
+  TidalArgs a{};
+  a.com = com;
+  a.M_c = M_c;
+  a.M_stride = M_stride;
+  a.n_prog = h->n_prog;
+  a.G = h->cfg.G;
+  a.eta = eta;
+  a.host = h->host;
+  a.out = out;
+  return cuda_fail(scf_tidal_launch(a, h->stream));
+}
+
+}  // namespace
+
+int scf_tidal(scf_handle* h, const double* com, const double* M_c, double eta, double* out) {
+  if (!h || !out) return SCF_ERR_NULL_POINTER;
+  if (h->host.n > 0 && !com) return SCF_ERR_NULL_POINTER;
+  if (!(eta > 0.0) || !std::isfinite(eta)) return SCF_ERR_INVALID_ARG;
+  return launch_tidal(h, com, M_c, 1, eta, out);
+}
+
+int scf_set_mask(scf_handle* h, const uint8_t* mask) {
+  if (!h) return SCF_ERR_NULL_POINTER;
+  if (mask != h->step_mask) {
+    // the captured step holds the old pointer
+    if (cudaStreamSynchronize(h->stream) != cudaSuccess) return SCF_ERR_CUDA;
+    drop_graph(h);
+    h->step_mask = mask;
+  }
+  return SCF_OK;
+}
+
+int scf_evolve(scf_handle* h, void* pos, void* vel, void* acc, double* com, int nsteps, const scf_escape_params* ep,
+               uint8_t* bound, uint8_t* mask, double* stats, int* n_refresh) {
+  if (!h || !ep || !stats) return SCF_ERR_NULL_POINTER;
+  if ((!pos || !vel || !acc || !bound || !mask) && h->n_total > 0) return SCF_ERR_NULL_POINTER;
+  if (h->host.n > 0 && !com) return SCF_ERR_NULL_POINTER;
+  if (!aligned16(pos) || !aligned16(vel) || !aligned16(acc)) return SCF_ERR_MISALIGNED;
+  if (nsteps < 0 || ep->max_steps < 1 || !(ep->eta > 0.0) || !std::isfinite(ep->eta) || !(h->cfg.dt > 0.0))
+    return SCF_ERR_INVALID_ARG;
+  if (!(ep->kin > 0.0) || !std::isfinite(ep->kin) || !(ep->frac > 0.0 && ep->frac <= 1.0)) return SCF_ERR_INVALID_ARG;
+  int rc = scf_set_mask(h, mask);
+  if (rc != SCF_OK) return rc;
+  std::vector<double> tid(16 * (size_t)h->n_prog);
+  int done = 0, refreshes = 0;
+  while (done < nsteps) {
+    // boundedness and the coefficient set r <= r_x
+    rc = scf_bound(h, pos, vel, ep->kin, ep->frac, nullptr, bound, mask, stats);
+    if (rc != SCF_OK) return rc;
+    // the field of the new set at the current positions (the next opening kick uses it)
+    rc = run_coeffs(h, pos, nullptr, nullptr, mask, h->d_A, nullptr, SCF_MODE_COEFFS);
+    if (rc == SCF_OK) rc = run_prep(h, h->d_A, com);
+    if (rc == SCF_OK) rc = run_forces(h, pos, nullptr, acc, com, SCF_MODE_COEFFS);
+    if (rc != SCF_OK) return rc;
+    // leapfrog steps up to the next integration timestep (the shortest over progenitors)
+    int k = ep->max_steps;
+    if (h->host.n > 0) {
+      rc = launch_tidal(h, com, stats + 1, 4, ep->eta, h->d_tid);
+      if (rc != SCF_OK) return rc;
+      if (cudaMemcpyAsync(tid.data(), h->d_tid, sizeof(double) * tid.size(), cudaMemcpyDeviceToHost, h->stream) !=
+              cudaSuccess ||
+          cudaStreamSynchronize(h->stream) != cudaSuccess)
+        return SCF_ERR_CUDA;
+      double dmin = HUGE_VAL;
+      for (int p = 0; p < h->n_prog; ++p) dmin = std::min(dmin, tid[16 * (size_t)p + 15]);
+      const double ks = std::floor(dmin / h->cfg.dt);
+      if (ks < (double)k) k = ks < 1.0 ? 1 : (int)ks;
+    }
+    k = std::min(k, nsteps - done);
+    rc = scf_step(h, pos, vel, acc, com, k);
+    if (rc != SCF_OK) return rc;
+    done += k;
+    ++refreshes;
+  }
+  if (n_refresh) *n_refresh = refreshes;
+  return SCF_OK;
 }
 
 int scf_last_coeffs(scf_handle* h, double* A_out) {

@@ -1,0 +1,332 @@
+// Escape physics of the cluster (Sec. 2.3; Sec. 4.1 footnote on r_t):
+//
+// * boundedness: particle i is bound when kin |v_i|^2 - sum_{j != i} G m_j / r_ij < 0
+//   in the cluster frame, the sum an unsoftened direct summation over every
+//   particle of its progenitor;
+// * the energy-based Lagrange radius r_x: the k-th smallest cluster-frame radius
+//   among the bound particles, k = ceil(frac n_bound); the coefficient set of
+//   Eq. 3b is r <= r_x;
+// * tidal scales at the centre R: T_ij = -d^2 psi_host/dx_i dx_j, its eigenvalues,
+//   the tidal radius r_t = (G M_c / (l1 - (l2 + l3)/2))^(1/3) and the
+//   integration timestep dt_int = sqrt(eta) (|T|_F^2 / 6)^(-1/4).
+//
+// Kernels:
+//   k_bound_pairs  O(N^2) pair sums.  Grid (i-chunk, progenitor, j-segment):
+//                  each block stages its j-segment through shared memory in
+//                  tiles and keeps two i-particles per thread in registers.
+//                  Single precision sums blocks of 64 pair terms in float and
+//                  adds them in double; double precision is double throughout.
+//                  Each block writes one double per particle and segment.
+//   k_bound_finish one thread per particle: adds the segments in order, forms
+//                  E_i and the bound flag, and the radius key (bits of r^2).
+//   k_select       one block per progenitor: bound count and mass, radix
+//                  selection of the k-th smallest key (8 passes of 8 bits over
+//                  shared-memory histograms of integer counts), the mask.
+//   k_tidal        one thread per progenitor.
+// Every sum has a fixed order, so results are bitwise reproducible.
+#include <cstdint>
+#include <math_constants.h>
+
+#include "scf_device.cuh"
+#include "scf_escape.h"
+
+namespace {
+
+constexpr int kPairThreads = 128;
+constexpr int kPairI = 2;         // i-particles per thread
+constexpr int kPairSub = 64;      // pair terms summed in the element type before the double add
+constexpr int kSelectThreads = 1024;
+
+template <typename V4>
+struct Elem;
+template <>
+struct Elem<float4> {
+  using T = float;
+};
+template <>
+struct Elem<ScfD4> {
+  using T = double;
+};
+
+__device__ __forceinline__ float inv_sqrt(float x) { return rsqrtf(x); }
+__device__ __forceinline__ double inv_sqrt(double x) { return rsqrt(x); }
+
+template <typename V4>
+__global__ void __launch_bounds__(kPairThreads) k_bound_pairs(BoundArgs a) {
+  using T = typename Elem<V4>::T;
+  __shared__ V4 s_j[kPairThreads];
+  const V4* pos = reinterpret_cast<const V4*>(a.pos);
+  for (int p = blockIdx.y; p < a.n_prog; p += gridDim.y) {
+    const int64_t o0 = a.prog_off[p], o1 = a.prog_off[p + 1];
+    const int64_t ib = o0 + (int64_t)blockIdx.x * (kPairThreads * kPairI);
+    if (ib >= o1) continue;  // the same for every thread of the block
+    const int64_t seg = (o1 - o0 + a.split - 1) / a.split;
+    const int64_t j0 = min(o1, o0 + (int64_t)blockIdx.z * seg), j1 = min(o1, j0 + seg);
+    T xi[kPairI], yi[kPairI], zi[kPairI];
+    double acc[kPairI];
+#pragma unroll
+    for (int q = 0; q < kPairI; ++q) {
+      const int64_t i = ib + threadIdx.x + q * kPairThreads;
+      const V4 pi = i < o1 ? pos[i] : V4{};
+      xi[q] = pi.x;
+      yi[q] = pi.y;
+      zi[q] = pi.z;
+      acc[q] = 0.0;
+    }
+    for (int64_t jb = j0; jb < j1; jb += kPairThreads) {
+      const int cnt = (int)min((int64_t)kPairThreads, j1 - jb);
+      __syncthreads();
+      if ((int)threadIdx.x < cnt) s_j[threadIdx.x] = pos[jb + threadIdx.x];
+      __syncthreads();
+      for (int s = 0; s < cnt; s += kPairSub) {
+        const int e = min(cnt, s + kPairSub);
+        T part[kPairI];
+#pragma unroll
+        for (int q = 0; q < kPairI; ++q) part[q] = T(0);
+#pragma unroll 4
+        for (int jj = s; jj < e; ++jj) {
+          const V4 pj = s_j[jj];
+#pragma unroll
+          for (int q = 0; q < kPairI; ++q) {
+            const T dx = pj.x - xi[q], dy = pj.y - yi[q], dz = pj.z - zi[q];
+            const T r2 = dx * dx + dy * dy + dz * dz;
+            // the self pair (and any coincident pair, and non-finite r2) adds nothing
+            const T ri = r2 > T(0) ? inv_sqrt(r2) : T(0);
+            part[q] += pj.w * ri;
+          }
+        }
+#pragma unroll
+        for (int q = 0; q < kPairI; ++q) acc[q] += (double)part[q];
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < kPairI; ++q) {
+      const int64_t i = ib + threadIdx.x + q * kPairThreads;
+      if (i < o1) a.part[(size_t)blockIdx.z * (size_t)a.n_total + (size_t)i] = acc[q];
+    }
+  }
+}
+
+template <typename V4>
+__global__ void k_bound_finish(BoundArgs a) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= a.n_total) return;
+  double pot = 0.0;
+  for (int s = 0; s < a.split; ++s) pot += a.part[(size_t)s * (size_t)a.n_total + (size_t)i];
+  const V4 v = reinterpret_cast<const V4*>(a.vel)[i];
+  const V4 p = reinterpret_cast<const V4*>(a.pos)[i];
+  const double vx = v.x, vy = v.y, vz = v.z;
+  const double E = a.kin * (vx * vx + vy * vy + vz * vz) - a.G * pot;
+  if (a.E_out) a.E_out[i] = E;
+  a.bound[i] = E < 0.0 ? 1 : 0;
+  // r^2 = (x x + y y) + z z without contraction, the same rounding as a plain
+  // evaluation of that expression; for r^2 >= 0 its bits order like its value
+  const double x = p.x, y = p.y, z = p.z;
+  const double r2 = __dadd_rn(__dadd_rn(__dmul_rn(x, x), __dmul_rn(y, y)), __dmul_rn(z, z));
+  a.key[i] = (unsigned long long)__double_as_longlong(r2);
+}
+
+template <typename V4>
+__global__ void __launch_bounds__(kSelectThreads) k_select(BoundArgs a) {
+  constexpr int NW = kSelectThreads / 32;
+  __shared__ unsigned s_hist[256];
+  __shared__ double s_m[NW];
+  __shared__ unsigned long long s_c[NW];
+  __shared__ unsigned long long s_prefix, s_krem, s_nb;
+  __shared__ double s_mb;
+  const int p = blockIdx.x, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int64_t o0 = a.prog_off[p], o1 = a.prog_off[p + 1];
+  const V4* pos = reinterpret_cast<const V4*>(a.pos);
+  const uint8_t* bound = a.bound;
+  const unsigned long long* key = a.key;
+
+  // bound count and bound mass (fixed order: thread strides, shuffle tree, warps in order)
+  unsigned long long c = 0;
+  double m = 0.0;
+  for (int64_t k = o0 + tid; k < o1; k += kSelectThreads)
+    if (bound[k]) {
+      ++c;
+      m += (double)pos[k].w;
+    }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    c += __shfl_xor_sync(0xffffffffu, c, o);
+    m += __shfl_xor_sync(0xffffffffu, m, o);
+  }
+  if (lane == 0) {
+    s_c[warp] = c;
+    s_m[warp] = m;
+  }
+  __syncthreads();
+  if (tid == 0) {
+    unsigned long long nb = 0;
+    double mb = 0.0;
+    for (int w = 0; w < NW; ++w) {
+      nb += s_c[w];
+      mb += s_m[w];
+    }
+    unsigned long long k = 0;
+    if (nb > 0) {
+      const double kk = ceil(a.frac * (double)nb);
+      k = kk < 1.0 ? 1ull : (unsigned long long)kk;
+      if (k > nb) k = nb;
+    }
+    s_nb = nb;
+    s_mb = mb;
+    s_krem = k;
+    s_prefix = 0ull;
+  }
+  __syncthreads();
+  const unsigned long long nb = s_nb;
+
+  // radix selection of the k-th smallest key among the bound particles
+  if (nb > 0) {
+    for (int pass = 0; pass < 8; ++pass) {
+      const int shift = 56 - 8 * pass;
+      const unsigned long long hi = pass == 0 ? 0ull : (~0ull << (shift + 8));
+      for (int d = tid; d < 256; d += kSelectThreads) s_hist[d] = 0u;
+      __syncthreads();
+      const unsigned long long prefix = s_prefix;
+      for (int64_t k = o0 + tid; k < o1; k += kSelectThreads) {
+        if (!bound[k]) continue;
+        const unsigned long long kk = key[k];
+        if ((kk & hi) == prefix) atomicAdd(&s_hist[(kk >> shift) & 255ull], 1u);
+      }
+      __syncthreads();
+      if (tid == 0) {
+        const unsigned long long krem = s_krem;
+        unsigned long long cum = 0;
+        for (int d = 0; d < 256; ++d) {
+          const unsigned long long hd = s_hist[d];
+          if (cum + hd >= krem) {
+            s_prefix = prefix | ((unsigned long long)d << shift);
+            s_krem = krem - cum;
+            break;
+          }
+          cum += hd;
+        }
+      }
+      __syncthreads();
+    }
+  }
+  // key of r_x^2 (0 = the bits of +0.0 when nothing is bound)
+  const unsigned long long kx = nb > 0 ? s_prefix : 0ull;
+
+  // the coefficient set r <= r_x, and its size
+  unsigned long long cm = 0;
+  for (int64_t k = o0 + tid; k < o1; k += kSelectThreads) {
+    const bool in = key[k] <= kx;
+    if (a.mask) a.mask[k] = in ? 1 : 0;
+    cm += in ? 1ull : 0ull;
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) cm += __shfl_xor_sync(0xffffffffu, cm, o);
+  __syncthreads();
+  if (lane == 0) s_c[warp] = cm;
+  __syncthreads();
+  if (tid == 0) {
+    unsigned long long n_in = 0;
+    for (int w = 0; w < NW; ++w) n_in += s_c[w];
+    double* st = a.stats + 4 * (size_t)p;
+    st[0] = (double)nb;
+    st[1] = s_mb;
+    st[2] = sqrt(__longlong_as_double((long long)kx));
+    st[3] = (double)n_in;
+  }
+}
+
+// Eigenvalues l1 >= l2 >= l3 of a symmetric 3x3 matrix S (row-major) by the
+// trigonometric solution of its characteristic cubic (Smith, Comm. ACM 4, 168,
+// 1961): with q = tr S / 3 and p = sqrt(tr((S - qI)^2) / 6), the eigenvalues
+// are q + 2p cos(phi + 2 pi j / 3), phi = acos(det((S - qI)/p) / 2) / 3.
+__device__ void sym3_eigen(const double* S, double* lam) {
+  const double p1 = S[1] * S[1] + S[2] * S[2] + S[5] * S[5];
+  const double q = (S[0] + S[4] + S[8]) / 3.0;
+  if (p1 == 0.0) {
+    double d0 = S[0], d1 = S[4], d2 = S[8], t;
+    if (d0 < d1) { t = d0; d0 = d1; d1 = t; }
+    if (d1 < d2) { t = d1; d1 = d2; d2 = t; }
+    if (d0 < d1) { t = d0; d0 = d1; d1 = t; }
+    lam[0] = d0;
+    lam[1] = d1;
+    lam[2] = d2;
+    return;
+  }
+  const double a0 = S[0] - q, a4 = S[4] - q, a8 = S[8] - q;
+  const double p2 = a0 * a0 + a4 * a4 + a8 * a8 + 2.0 * p1;
+  const double p = sqrt(p2 / 6.0);
+  const double b0 = a0 / p, b4 = a4 / p, b8 = a8 / p, b1 = S[1] / p, b2 = S[2] / p, b5 = S[5] / p;
+  const double det = b0 * (b4 * b8 - b5 * b5) - b1 * (b1 * b8 - b5 * b2) + b2 * (b1 * b5 - b4 * b2);
+  double r = 0.5 * det;
+  r = r < -1.0 ? -1.0 : (r > 1.0 ? 1.0 : r);
+  const double phi = acos(r) / 3.0;
+  const double two_pi_3 = 2.0943951023931954923;  // 2 pi / 3
+  lam[0] = q + 2.0 * p * cos(phi);
+  lam[2] = q + 2.0 * p * cos(phi + two_pi_3);
+  lam[1] = 3.0 * q - lam[0] - lam[2];
+}
+
+__global__ void k_tidal(TidalArgs a) {
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= a.n_prog) return;
+  double R[3] = {0.0, 0.0, 0.0};
+  if (a.com)
+    for (int i = 0; i < 3; ++i) R[i] = a.com[6 * (size_t)p + i];
+  double T[9];
+  for (int j = 0; j < 3; ++j) {  // column j: derivative of a_host along x_j (dual numbers)
+    Dual x(R[0], j == 0 ? 1.0 : 0.0), y(R[1], j == 1 ? 1.0 : 0.0), z(R[2], j == 2 ? 1.0 : 0.0);
+    Dual ax, ay, az;
+    scf_host_accel_t<Dual>(a.host, x, y, z, ax, ay, az);
+    T[0 + j] = ax.d;
+    T[3 + j] = ay.d;
+    T[6 + j] = az.d;
+  }
+  double S[9], lam[3], fro2 = 0.0;
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j) {
+      S[3 * i + j] = 0.5 * (T[3 * i + j] + T[3 * j + i]);
+      fro2 += T[3 * i + j] * T[3 * i + j];
+    }
+  sym3_eigen(S, lam);
+  const double fro = sqrt(fro2);
+  const double l1e = lam[0] - 0.5 * (lam[1] + lam[2]);
+  const double Mc = a.M_c ? a.M_c[(size_t)p * a.M_stride] : 0.0;
+  double* o = a.out + 16 * (size_t)p;
+  for (int i = 0; i < 9; ++i) o[i] = T[i];
+  o[9] = lam[0];
+  o[10] = lam[1];
+  o[11] = lam[2];
+  o[12] = fro;
+  o[13] = l1e;
+  o[14] = l1e > 0.0 ? cbrt(a.G * Mc / l1e) : CUDART_INF;
+  o[15] = fro > 0.0 ? sqrt(a.eta) / sqrt(fro / sqrt(6.0)) : CUDART_INF;
+}
+
+}  // namespace
+
+int scf_bound_split(int64_t i_chunks, int n_sm) {
+  if (i_chunks <= 0) return 1;
+  const int64_t s = (4 * (int64_t)n_sm + i_chunks - 1) / i_chunks;
+  return (int)(s < 1 ? 1 : (s > kBoundMaxSplit ? kBoundMaxSplit : s));
+}
+
+int64_t scf_bound_chunk() { return kPairThreads * kPairI; }
+
+cudaError_t scf_bound_launch(const BoundArgs& a, int64_t max_chunks, cudaStream_t s) {
+  if (a.n_total > 0 && max_chunks > 0) {
+    const dim3 grid((unsigned)max_chunks, (unsigned)(a.n_prog < 65535 ? a.n_prog : 65535), (unsigned)a.split);
+    if (a.f32) k_bound_pairs<float4><<<grid, kPairThreads, 0, s>>>(a);
+    else k_bound_pairs<ScfD4><<<grid, kPairThreads, 0, s>>>(a);
+    const unsigned fb = (unsigned)((a.n_total + 255) / 256);
+    if (a.f32) k_bound_finish<float4><<<fb, 256, 0, s>>>(a);
+    else k_bound_finish<ScfD4><<<fb, 256, 0, s>>>(a);
+  }
+  if (a.f32) k_select<float4><<<a.n_prog, kSelectThreads, 0, s>>>(a);
+  else k_select<ScfD4><<<a.n_prog, kSelectThreads, 0, s>>>(a);
+  return cudaGetLastError();
+}
+
+cudaError_t scf_tidal_launch(const TidalArgs& a, cudaStream_t s) {
+  k_tidal<<<(a.n_prog + 127) / 128, 128, 0, s>>>(a);
+  return cudaGetLastError();
+}

@@ -1,0 +1,49 @@
+// Internal interface of the escape-physics kernels (scf_escape.cu): the
+// boundedness test, the energy-based Lagrange radius with its coefficient-set
+// mask, and the tidal scales at the cluster centre (Sec. 2.3).  Not part of
+// the public ABI.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "scf_device.cuh"
+
+// Upper bound on the number of j-segments the pair kernel splits each
+// progenitor into (more blocks when the progenitors are small).
+constexpr int kBoundMaxSplit = 16;
+
+struct BoundArgs {
+  const void* pos;             // [N][4] float (mixed) or double
+  const void* vel;             // [N][4]
+  const int64_t* prog_off;     // [n_prog + 1] particle offsets
+  int n_prog;
+  int64_t n_total;
+  int f32;                     // particle arrays are float4
+  int split;                   // j-segments per progenitor
+  double G, kin, frac;
+  double* part;                // [split][N] partial sums of m_j / r_ij
+  unsigned long long* key;     // [N] bits of r^2
+  double* E_out;               // [N] energies, or null
+  uint8_t* bound;              // [N] 1 = bound
+  uint8_t* mask;               // [N] 1 = r <= r_x, or null
+  double* stats;               // [n_prog][4] = (n_bound, M_bound, r_x, n_in_set)
+};
+
+struct TidalArgs {
+  const double* com;           // [n_prog][6] centre (R, V), or null (R = 0)
+  const double* M_c;           // cluster masses with stride M_stride, or null (r_t = 0)
+  int M_stride;
+  int n_prog;
+  double G, eta;
+  ScfHostParams host;
+  double* out;                 // [n_prog][16]
+};
+
+// j-segments per progenitor for a block map of i_chunks blocks in total.
+int scf_bound_split(int64_t i_chunks, int n_sm);
+// i-particles per block of the pair kernel.
+int64_t scf_bound_chunk();
+// max_chunks: i-blocks of the largest progenitor.
+cudaError_t scf_bound_launch(const BoundArgs& a, int64_t max_chunks, cudaStream_t s);
+cudaError_t scf_tidal_launch(const TidalArgs& a, cudaStream_t s);

@@ -126,6 +126,50 @@ class SCF:
         _lib.scf_energy(self._h, pos, vel, acc, com, out)
         return out
 
+    # -- escape physics (Sec. 2.3)
+    def bound(self, pos, vel, kin: float = 0.5, frac: float = 0.999, energies: bool = False):
+        """Boundedness by direct summation and the coefficient set r <= r_x.
+        Returns ``(bound, mask, stats, E)``: uint8 ``(N,)`` flags, uint8 ``(N,)``
+        mask, float64 ``(n_prog, 4)`` = (n_bound, bound mass, r_x, set size),
+        and float64 ``(N,)`` energies when ``energies`` (else None)."""
+        for t, nm in ((pos, "pos"), (vel, "vel")):
+            self._check_particles(t, nm)
+        b = torch.empty(self.n, dtype=torch.uint8, device=self.device)
+        m = torch.empty(self.n, dtype=torch.uint8, device=self.device)
+        st = torch.empty((self.n_prog, 4), dtype=torch.float64, device=self.device)
+        E = torch.empty(self.n, dtype=torch.float64, device=self.device) if energies else None
+        _lib.scf_bound(self._h, pos, vel, kin, frac, E, b, m, st)
+        return b, m, st, E
+
+    def tidal(self, com=None, M_c=None, eta: float = 1.0 / 400.0):
+        """(n_prog, 16) float64: tidal tensor (9), eigenvalues (3), Frobenius
+        norm, l1e, r_t and dt_int at the centres (see scf_tidal)."""
+        out = torch.empty((self.n_prog, 16), dtype=torch.float64, device=self.device)
+        _lib.scf_tidal(self._h, com, M_c, eta, out)
+        return out
+
+    def set_mask(self, mask=None):
+        """Coefficient set of ``step`` (uint8 ``(N,)`` tensor kept alive by the
+        caller), or None for every particle."""
+        self._mask_ref = mask
+        _lib.scf_set_mask(self._h, mask)
+
+    def evolve(self, pos, vel, acc, com=None, nsteps: int = 1, kin: float = 0.5, frac: float = 0.999,
+               eta: float = 1.0 / 400.0, max_steps: int = 1000):
+        """``nsteps`` leapfrog steps with boundedness, the r <= r_x coefficient
+        set and the tidal integration timestep (scf_evolve).  Returns
+        ``(bound, mask, stats, n_int)`` as of the last integration timestep."""
+        for t, nm in ((pos, "pos"), (vel, "vel"), (acc, "acc")):
+            self._check_particles(t, nm)
+        if getattr(self, "_evolve_bufs", None) is None:
+            self._evolve_bufs = (torch.empty(self.n, dtype=torch.uint8, device=self.device),
+                                 torch.empty(self.n, dtype=torch.uint8, device=self.device),
+                                 torch.empty((self.n_prog, 4), dtype=torch.float64, device=self.device))
+        b, m, st = self._evolve_bufs
+        self._mask_ref = m
+        n_int = _lib.scf_evolve(self._h, pos, vel, acc, com, nsteps, kin, frac, eta, max_steps, b, m, st)
+        return b, m, st, n_int
+
     def last_coeffs(self, out: torch.Tensor | None = None):
         out = self.new_coeffs() if out is None else out
         _lib.scf_last_coeffs(self._h, out)

@@ -91,4 +91,8 @@ def test_null_handle_is_rejected(lib):
     assert lib.scf_status(None, None) == -2
     assert lib.scf_adjoint_level(None, None, None, 0.005, 1, None, None, None, None) == -2
     assert lib.scf_energy(None, None, None, None, None, None) == -2
+    assert lib.scf_bound(None, None, None, 0.5, 0.999, None, None, None, None) == -2
+    assert lib.scf_tidal(None, None, None, 0.0025, None) == -2
+    assert lib.scf_set_mask(None, None) == -2
+    assert lib.scf_evolve(None, None, None, None, None, 1, None, None, None, None, None) == -2
     assert lib.scf_free(None) == 0
