@@ -376,6 +376,19 @@ def plummer_eccentric(n: int = 1_000_000, seed: int = 3, nsteps: int = 2000) -> 
     return Workload(f"plummer_n{n}_eccentric", pos, vel, 20, 10, basis_scale(rh), 0.01, nsteps, host, com, units)
 
 
+def plummer_stream(n: int = 100_000, seed: int = 6, nsteps: int = 6000) -> Workload:
+    """Stream-forming run: a tidally filling Plummer cluster (2e5 Msun, r_h =
+    20 pc, so about a tenth of its mass lies beyond the Jacobi radius at the
+    5 kpc pericentre) on the 5-20 kpc eccentric orbit, starting at apocentre;
+    nmax = 10, lmax = 5 (the paper's fiducial stream model), dt = 0.01."""
+    pos, vel = plummer(n, seed)
+    rh = half_mass_radius(pos)
+    units = Units(2e5, 20.0 / rh)
+    host = host_in_units(galaxy_host_physical(), units)
+    com = _com_from_orbit(_orbit_ics()["eccentric_5_20kpc"], units)
+    return Workload(f"plummer_rh20_n{n}_stream", pos, vel, 10, 5, basis_scale(rh), 0.01, nsteps, host, com, units)
+
+
 def king_eccentric(n: int = 100_000, seed: int = 5, nsteps: int = 500) -> Workload:
     """The differentiable run: King W0 = 6 cluster (1e5 Msun, r_h = 3 pc) on
     the 5-20 kpc eccentric orbit in the NFW + MN + Hernquist host; nmax = 20,
