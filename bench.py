@@ -68,10 +68,14 @@ def per_particle_bytes(elem):
     return 5 * rec, 4 * rec      # kernel 1: r pos,vel,acc w pos,vel; kernel 3: r pos,vel w acc,vel
 
 
+# sources that decide the code and launch shapes of the three step kernels
+STEP_SOURCES = ["scf_api.cu", "scf_coeffs.cu", "scf_device.cuh", "scf_forces.cu", "scf_internal.h", "scf_tables.cu"]
+
+
 def src_hash():
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_2602_13385_gb300", "csrc")
-    for fn in sorted(os.listdir(csrc)):
+    for fn in STEP_SOURCES:
         with open(os.path.join(csrc, fn), "rb") as f:
             h.update(f.read())
     return h.hexdigest()[:16]

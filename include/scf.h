@@ -246,7 +246,7 @@ int scf_adjoint_level(scf_handle* h, const void* pos, const double* com, double 
  * Errors: SCF_ERR_NULL_POINTER, SCF_ERR_MISALIGNED, SCF_ERR_CUDA. */
 int scf_energy(scf_handle* h, const void* pos, const void* vel, const void* acc, const double* com, double* E_out);
 
-/* ---- Escape physics (Sec. 2.3; Sec. 4.1 footnote on the tidal radius) ---- */
+/* ---- Escape physics (Sec. 2.2; Sec. 3.1 footnote on the tidal radius) ---- */
 
 /* Boundedness of every particle and the coefficient set of Eq. 3b.
  * Particle i of progenitor p is bound when its cluster-frame energy
@@ -254,13 +254,16 @@ int scf_energy(scf_handle* h, const void* pos, const void* vel, const void* acc,
  * is negative (unsoftened direct summation over all particles of p; pairs at
  * zero separation and pairs with a non-finite separation add nothing, so a
  * particle with a non-finite position is never bound).  The footnote of
- * Sec. 2.3 prints kin = 1; kin = 1/2 is the standard specific energy.
+ * Sec. 2.2 prints kin = 1; kin = 1/2 is the standard specific energy.
  * r_x is the energy-based Lagrange radius: the k-th smallest cluster-frame
  * radius among p's bound particles, k = ceil(frac n_bound) (r_x = 0 when none
  * is bound); the coefficient set is r <= r_x (frac = 0.999 in the paper).
  * Radii are compared as r^2 = (x x + y y) + z z in double precision.
- * In double precision the pair sums are double; in mixed precision each pair
- * term and blocks of 64 of them are float, added in double.
+ * In double precision the pair sums are double and 1/r is the single-
+ * precision estimate refined by one Newton step (relative error < 2e-13);
+ * pairs whose r^2 lies outside the normal float range [1.18e-38, 3.40e38]
+ * then add nothing.  In mixed precision each pair term and blocks of 64 of
+ * them are float, added in double.
  *   pos, vel   device [N][4] in the handle's element type (16-byte aligned)
  *   kin        > 0 and finite;  frac in (0, 1]
  *   E_out      device [N] doubles (E_i), or NULL
@@ -274,12 +277,12 @@ int scf_energy(scf_handle* h, const void* pos, const void* vel, const void* acc,
 int scf_bound(scf_handle* h, const void* pos, const void* vel, double kin, double frac, double* E_out,
               uint8_t* bound_out, uint8_t* mask_out, double* stats_out);
 
-/* Tidal scales of every progenitor at its centre R = com[p][0..2] (Sec. 2.3):
+/* Tidal scales of every progenitor at its centre R = com[p][0..2] (Sec. 2.2):
  *   out[p][0..8]  T_ij = -d^2 psi_host / dx_i dx_j (row-major), from the host components
  *   out[p][9..11] eigenvalues l1 >= l2 >= l3 of T
  *   out[p][12]    |T|_F (Frobenius norm)
  *   out[p][13]    l1e = l1 - (l2 + l3)/2
- *   out[p][14]    r_t = (G M_c[p] / l1e)^(1/3) (Sec. 4.1 footnote); +inf when l1e <= 0;
+ *   out[p][14]    r_t = (G M_c[p] / l1e)^(1/3) (Sec. 3.1 footnote); +inf when l1e <= 0;
  *                 0 when M_c is NULL
  *   out[p][15]    dt_int = sqrt(eta) (|T|_F^2 / 6)^(-1/4); +inf without host
  * com: device [n_prog][6] (NULL allowed without host components: R = 0);
@@ -302,7 +305,7 @@ typedef struct scf_escape_params {
   int max_steps;  /* most leapfrog steps per integration timestep (>= 1) */
 } scf_escape_params;
 
-/* nsteps leapfrog steps with the escape physics of Sec. 2.3.  At the start of
+/* nsteps leapfrog steps with the escape physics of Sec. 2.2.  At the start of
  * every integration timestep: scf_bound (bound flags, the mask r <= r_x and
  * stats, into the caller's buffers), the mask becomes the step's coefficient
  * set (scf_set_mask), acc is recomputed at the current positions from that

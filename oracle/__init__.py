@@ -297,13 +297,13 @@ def direct(src, tgt, G=1.0):
 
 # ---------------------------------------------------------------- escape physics
 def boundedness(pos, vel, G=1.0, kin=0.5, frac=0.999):
-    """Energy-based boundedness and the radius of the coefficient set (Sec. 2.3).
+    """Energy-based boundedness and the radius of the coefficient set (Sec. 2.2).
 
     Particle i is bound when its cluster-frame energy
     ``E_i = kin |v_i|^2 - sum_{j != i} G m_j / |r_i - r_j|`` is negative, the
     sum being the unsoftened direct summation over every particle of the
     progenitor (coincident pairs are skipped like the self term).  The
-    footnote of Sec. 2.3 prints ``kin = 1``; the standard specific energy
+    footnote of Sec. 2.2 prints ``kin = 1``; the standard specific energy
     has ``kin = 1/2`` (the default).  ``r_x`` is the smallest radius that
     encloses the fraction ``frac`` of the bound particles, i.e. the k-th
     smallest cluster-frame radius among them with ``k = ceil(frac n_bound)``;
@@ -337,14 +337,14 @@ def tidal_scales(host, R, M_c, eta=1.0 / 400.0, G=1.0):
     """Tidal tensor, its eigenvalues, the tidal radius and the integration
     timestep at centre positions ``R`` (n, 3) for cluster masses ``M_c`` (n,).
 
-    * ``T_ij = -d^2 psi_host / dx_i dx_j`` (Sec. 2.3, App. A), here the
+    * ``T_ij = -d^2 psi_host / dx_i dx_j`` (Sec. 2.2, App. A), here the
       derivative of the host acceleration (``tidal_tensor``);
     * eigenvalues ``l1 >= l2 >= l3`` (numpy's symmetric eigensolver);
     * tidal radius ``r_t = (G M_c / l1e)^(1/3)`` with
-      ``l1e = l1 - (l2 + l3)/2`` (Sec. 4.1, footnote on generic orbits);
+      ``l1e = l1 - (l2 + l3)/2`` (Sec. 3.1, footnote on generic orbits);
       infinite when ``l1e <= 0``;
     * integration timestep ``dt_int = sqrt(eta) (|T|_F^2 / 6)^(-1/4)``
-      (Sec. 2.3, with the Frobenius norm).
+      (Sec. 2.2, with the Frobenius norm).
 
     Returns an (n, 16) array laid out as ``T`` (row-major, 9), ``l1, l2, l3``,
     ``|T|_F``, ``l1e``, ``r_t``, ``dt_int``.
@@ -371,7 +371,7 @@ def tidal_scales(host, R, M_c, eta=1.0 / 400.0, G=1.0):
 
 def evolve(pos, vel, acc, nmax, lmax, b, dt, nsteps, G=1.0, com=None, host=None, kin=0.5, frac=0.999,
            eta=1.0 / 400.0, max_steps=1000):
-    """Leapfrog with the escape physics of Sec. 2.3.  At the start of every
+    """Leapfrog with the escape physics of Sec. 2.2.  At the start of every
     integration timestep: the boundedness test and the coefficient set
     r <= r_x (:func:`boundedness`), the field of that set at the current
     positions, and the length of the integration timestep, dt_int of

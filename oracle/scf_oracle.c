@@ -554,7 +554,7 @@ void or_forces(int64_t n_part, const double* pos, const double* A, const double*
  * recomputed from the particles at every force evaluation unless A_frozen is
  * given, in which case the potential is static.  mask (nullable) is the
  * coefficient set: only particles with mask[k] != 0 enter Eq. 3b, every
- * particle moves in the field (Sec. 2.3).  A_out (nullable) receives the last
+ * particle moves in the field (Sec. 2.2).  A_out (nullable) receives the last
  * coefficients used. */
 void or_step(int64_t n_part, double* pos, double* vel, double* acc, double* com, const or_host* host, int nmax,
              int lmax, double b, double G, double dt, int nsteps, const double* A_frozen, const uint8_t* mask,
@@ -598,7 +598,7 @@ void or_step(int64_t n_part, double* pos, double* vel, double* acc, double* com,
 }
 
 /* ------------------------------------------------------------------------ */
-/* Direct summation (the comparison of Sec. 5.1 / Fig. 10)                  */
+/* Direct summation (the comparison of Sec. 4.1 / Fig. 11)                  */
 /* ------------------------------------------------------------------------ */
 
 /* Newtonian potential and acceleration at n_tgt points from the n_src
@@ -620,7 +620,7 @@ void or_direct(int64_t n_src, const double* src, int64_t n_tgt, const double* tg
   }
 }
 
-/* Power in each l of the expansion, E_l = sum_{n,m} |a_nlm|^2 (Sec. 5.2), with
+/* Power in each l of the expansion, E_l = sum_{n,m} |a_nlm|^2 (Sec. 4.2), with
  * a_nlm the coefficients of the bi-orthonormal basis of Eq. 3a.  In terms of
  * the real form: the orthonormal-harmonic coefficient is A_nl0 = S_nl0/N_l0
  * and, for m > 0, |A_nlm|^2 = |A_nl,-m|^2 = (S^2 + T^2)/(4 N_lm^2); the

@@ -448,7 +448,7 @@ int scf_init(const scf_config* cfg, int n_prog, const int64_t* offsets, const do
   const size_t o_en = take(sizeof(double) * 4 * nb3);
   const size_t o_adj = cfg->precision == SCF_FP64 ? take(sizeof(double) * SCF_ADJ_Q * nb3) : off;
   {
-    const int64_t chunk = scf_bound_chunk();
+    const int64_t chunk = scf_bound_chunk(cfg->precision == SCF_MIXED);
     int64_t chunks = 0;
     for (int p = 0; p < n_prog; ++p) {
       const int64_t c = (h->offsets[p + 1] - h->offsets[p] + chunk - 1) / chunk;

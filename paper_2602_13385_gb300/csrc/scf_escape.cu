@@ -1,4 +1,4 @@
-// Escape physics of the cluster (Sec. 2.3; Sec. 4.1 footnote on r_t):
+// Escape physics of the cluster (Sec. 2.2; Sec. 3.1 footnote on r_t):
 //
 // * boundedness: particle i is bound when kin |v_i|^2 - sum_{j != i} G m_j / r_ij < 0
 //   in the cluster frame, the sum an unsoftened direct summation over every
@@ -13,10 +13,13 @@
 // Kernels:
 //   k_bound_pairs  O(N^2) pair sums.  Grid (i-chunk, progenitor, j-segment):
 //                  each block stages its j-segment through shared memory in
-//                  tiles and keeps two i-particles per thread in registers.
-//                  Single precision sums blocks of 64 pair terms in float and
-//                  adds them in double; double precision is double throughout.
-//                  Each block writes one double per particle and segment.
+//                  tiles and keeps four (float) or two (double) i-particles
+//                  per thread in registers.  Single precision sums blocks of
+//                  64 pair terms in float and adds them in double.  Double
+//                  precision is double throughout except 1/r: the single-
+//                  precision estimate refined by one Newton step in double
+//                  (relative error below 2e-13).  Each block writes one double
+//                  per particle and segment.
 //   k_bound_finish one thread per particle: adds the segments in order, forms
 //                  E_i and the bound flag, and the radius key (bits of r^2).
 //   k_select       one block per progenitor: bound count and mass, radix
@@ -33,7 +36,6 @@
 namespace {
 
 constexpr int kPairThreads = 128;
-constexpr int kPairI = 2;         // i-particles per thread
 constexpr int kPairSub = 64;      // pair terms summed in the element type before the double add
 constexpr int kSelectThreads = 1024;
 
@@ -42,18 +44,30 @@ struct Elem;
 template <>
 struct Elem<float4> {
   using T = float;
+  static constexpr int I = 4;     // i-particles per thread
 };
 template <>
 struct Elem<ScfD4> {
   using T = double;
+  static constexpr int I = 2;
 };
 
-__device__ __forceinline__ float inv_sqrt(float x) { return rsqrtf(x); }
-__device__ __forceinline__ double inv_sqrt(double x) { return rsqrt(x); }
+// 1/sqrt(r2) of a pair; 0 for a pair that adds nothing (r2 zero, not finite,
+// or outside the normal single-precision range [1.18e-38, 3.40e38]).
+__device__ __forceinline__ float pair_inv_r(float r2) { return r2 > 0.f ? rsqrtf(r2) : 0.f; }
+__device__ __forceinline__ double pair_inv_r(double r2) {
+  // one Newton-Raphson step for y = r2^(-1/2), y <- y (3/2 - (r2/2) y^2), from the
+  // single-precision estimate: a relative error e becomes -(3/2) e^2
+  const float f = __double2float_rn(r2);
+  const double y = (double)rsqrtf(f);
+  const double yn = y * fma(-0.5 * r2, y * y, 1.5);
+  return (f >= 1.17549435e-38f && f <= 3.40282347e38f) ? yn : 0.0;
+}
 
 template <typename V4>
 __global__ void __launch_bounds__(kPairThreads) k_bound_pairs(BoundArgs a) {
   using T = typename Elem<V4>::T;
+  constexpr int kPairI = Elem<V4>::I;
   __shared__ V4 s_j[kPairThreads];
   const V4* pos = reinterpret_cast<const V4*>(a.pos);
   for (int p = blockIdx.y; p < a.n_prog; p += gridDim.y) {
@@ -91,7 +105,7 @@ __global__ void __launch_bounds__(kPairThreads) k_bound_pairs(BoundArgs a) {
             const T dx = pj.x - xi[q], dy = pj.y - yi[q], dz = pj.z - zi[q];
             const T r2 = dx * dx + dy * dy + dz * dz;
             // the self pair (and any coincident pair, and non-finite r2) adds nothing
-            const T ri = r2 > T(0) ? inv_sqrt(r2) : T(0);
+            const T ri = pair_inv_r(r2);
             part[q] += pj.w * ri;
           }
         }
@@ -310,7 +324,7 @@ int scf_bound_split(int64_t i_chunks, int n_sm) {
   return (int)(s < 1 ? 1 : (s > kBoundMaxSplit ? kBoundMaxSplit : s));
 }
 
-int64_t scf_bound_chunk() { return kPairThreads * kPairI; }
+int64_t scf_bound_chunk(int f32) { return kPairThreads * (f32 ? Elem<float4>::I : Elem<ScfD4>::I); }
 
 cudaError_t scf_bound_launch(const BoundArgs& a, int64_t max_chunks, cudaStream_t s) {
   if (a.n_total > 0 && max_chunks > 0) {

@@ -1,6 +1,6 @@
 // Internal interface of the escape-physics kernels (scf_escape.cu): the
 // boundedness test, the energy-based Lagrange radius with its coefficient-set
-// mask, and the tidal scales at the cluster centre (Sec. 2.3).  Not part of
+// mask, and the tidal scales at the cluster centre (Sec. 2.2).  Not part of
 // the public ABI.
 #pragma once
 
@@ -42,8 +42,8 @@ struct TidalArgs {
 
 // j-segments per progenitor for a block map of i_chunks blocks in total.
 int scf_bound_split(int64_t i_chunks, int n_sm);
-// i-particles per block of the pair kernel.
-int64_t scf_bound_chunk();
+// i-particles per block of the pair kernel (f32: single-precision particles).
+int64_t scf_bound_chunk(int f32);
 // max_chunks: i-blocks of the largest progenitor.
 cudaError_t scf_bound_launch(const BoundArgs& a, int64_t max_chunks, cudaStream_t s);
 cudaError_t scf_tidal_launch(const TidalArgs& a, cudaStream_t s);

@@ -126,7 +126,7 @@ class SCF:
         _lib.scf_energy(self._h, pos, vel, acc, com, out)
         return out
 
-    # -- escape physics (Sec. 2.3)
+    # -- escape physics (Sec. 2.2)
     def bound(self, pos, vel, kin: float = 0.5, frac: float = 0.999, energies: bool = False):
         """Boundedness by direct summation and the coefficient set r <= r_x.
         Returns ``(bound, mask, stats, E)``: uint8 ``(N,)`` flags, uint8 ``(N,)``

@@ -1,14 +1,14 @@
-"""Stream statistics of Sec. 4.3, measured on a snapshot (host-side analysis).
+"""Stream statistics of Sec. 3.3, measured on a snapshot (host-side analysis).
 
 This is post-processing of the particles a run leaves in device memory
 (positions, velocities, the bound flags of ``scf_bound``), not a step of the
 gravity solver: it copies them to the host and bins them with numpy.
 
-* Great-circle frame of an observer at the galactic centre (Fig. 3): the
+* Great-circle frame of an observer at the galactic centre (Figs. 1-2): the
   pole is the progenitor's orbital angular momentum R x V, the first axis
   points at the progenitor (phi_1 = phi_2 = 0 there) and phi_1 grows along
   its motion; phi_2 is the angle out of the instantaneous orbital plane.
-* Binning (Sec. 4.3): the unbound stars are binned in phi_1 from the
+* Binning (Sec. 3.3): the unbound stars are binned in phi_1 from the
   progenitor outwards, leading (phi_1 > 0) and trailing (phi_1 < 0) tails
   separately, each bin closed once it holds at least ``min_count`` stars and
   spans at least ``min_width`` degrees; a remainder too small to close a bin
@@ -70,7 +70,7 @@ def _tail_edges(a, min_count, min_width):
 
 
 def bin_edges(phi1, min_count=100, min_width=0.5):
-    """Edges (ascending, degrees) of the Sec. 4.3 binning of ``phi1``: from 0
+    """Edges (ascending, degrees) of the Sec. 3.3 binning of ``phi1``: from 0
     outwards in each tail, each bin >= min_count stars and >= min_width wide."""
     phi1 = np.asarray(phi1, dtype=np.float64)
     lead = np.sort(phi1[phi1 >= 0.0])
@@ -99,7 +99,7 @@ def stream_stats(X, Vh, R, V, unbound, edges=None, min_count=100, min_width=0.5)
 
     X, Vh: host-frame positions and velocities (n, 3); R, V: the progenitor's
     position and velocity; unbound: boolean (n,).  ``edges`` fixes the bins
-    (e.g. those of another run) instead of the Sec. 4.3 rule.
+    (e.g. those of another run) instead of the Sec. 3.3 rule.
     Returns a dict of arrays over bins: ``lo``, ``hi``, ``n``, ``rho``,
     ``track``, ``width``, ``sigma``, ``cos_mis``.
     """

@@ -14,7 +14,7 @@ against the oracle (oracle.boundedness, oracle.tidal_scales, oracle.evolve).
 * The stream comparison used once chaos has separated the trajectories:
   the stream-forming workload (N = 1e5, one radial period of the 5-20 kpc
   orbit, 8000 steps with the escape physics) run in double and in mixed
-  precision; the Sec. 4.3 statistics of the unbound stars (density, track,
+  precision; the Sec. 3.3 statistics of the unbound stars (density, track,
   width, velocity dispersion, misalignment) agree within 1% on bins of at
   least 500 stars, on the bins of the double-precision run.
 """

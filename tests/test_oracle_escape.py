@@ -1,20 +1,20 @@
 """Pins of the oracle's escape physics (oracle.boundedness, oracle.tidal_scales).
 
-* Boundedness (Sec. 2.3 footnote): the escape speed of a two-body pair, a
+* Boundedness (Sec. 2.2 footnote): the escape speed of a two-body pair, a
   distant test star against the point-mass escape speed of a Plummer sample,
   and the near-total boundedness of an equilibrium Plummer sample; the
   kinetic factor (1 as printed, 1/2 as the standard energy) moves the
   threshold by sqrt(2).
-* The energy-based Lagrange radius r_x (Sec. 2.3) against a brute-force scan
+* The energy-based Lagrange radius r_x (Sec. 2.2) against a brute-force scan
   of its definition (the smallest radius that encloses at least the fraction
   x of the bound particles), on small inputs, at x = 1 (the bound radius r_b)
   and with nothing bound.
 * Tidal scales: for a point-mass host the tidal tensor has eigenvalues
   GM/R^3 (2, -1, -1), so r_t is the Jacobi radius R (M_c / 3M)^(1/3) and
-  dt_int = sqrt(eta) sqrt(R^3 / GM) (Sec. 2.3, Sec. 4.1 footnote); the trace
+  dt_int = sqrt(eta) sqrt(R^3 / GM) (Sec. 2.2, Sec. 3.1 footnote); the trace
   of the tidal tensor is -4 pi G rho_host (Poisson's equation) for each host
   component.
-* The evolve schedule (Sec. 2.3): with every star bound and inside r_x it is
+* The evolve schedule (Sec. 2.2): with every star bound and inside r_x it is
   the plain leapfrog bit for bit; an unbound star beyond r_x leaves the
   cluster's evolution bit for bit unchanged (and changes it when left in the
   coefficient sum); on a circular orbit about a point mass, where dt_int is

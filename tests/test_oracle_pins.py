@@ -240,7 +240,7 @@ def test_mask_excludes_particles():
 
 
 def test_power_spectrum_spherical_and_origin():
-    # a particle at the origin is spherically symmetric: E_l = 0 for l > 0 (Sec. 5.2)
+    # a particle at the origin is spherically symmetric: E_l = 0 for l > 0 (Sec. 4.2)
     A = oracle.coeffs(np.array([[0, 0, 0, 1.0]]), 6, 4, 0.5)
     El = oracle.power_l(A, 6, 4, 0.5)
     assert El[0] > 0 and np.all(El[1:] == 0)
@@ -339,7 +339,7 @@ def test_expansion_of_offset_plummer_converges_to_exact_field():
 
 
 def test_scf_residual_against_direct_summation_small_n():
-    """Sec. 5.1 compares model accelerations with direct N-body summation.  For
+    """Sec. 4.1 compares model accelerations with direct N-body summation.  For
     a discrete sample (N <= 512, compact) the expansion of point masses
     converges only algebraically in nmax, so the check is a bounded residual
     that shrinks from (4,2) to (20,10) at points outside the sample."""

@@ -1,4 +1,4 @@
-"""Pins of the stream statistics (paper_2602_13385_gb300.streams, Sec. 4.3) on
+"""Pins of the stream statistics (paper_2602_13385_gb300.streams, Sec. 3.3) on
 synthetic streams whose answers are known in closed form:
 
 * the great-circle frame of a progenitor in the x-y plane moving along +y;
