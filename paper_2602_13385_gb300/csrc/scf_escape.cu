@@ -16,10 +16,9 @@
 //                  tiles and keeps four (float) or two (double) i-particles
 //                  per thread in registers.  Single precision sums blocks of
 //                  64 pair terms in float and adds them in double.  Double
-//                  precision is double throughout except 1/r: the single-
-//                  precision estimate refined by one Newton step in double
-//                  (relative error below 2e-13).  Each block writes one double
-//                  per particle and segment.
+//                  precision is double throughout; 1/r is the hardware
+//                  estimate refined by one Newton step.  Each block writes
+//                  one double per particle and segment.
 //   k_bound_finish one thread per particle: adds the segments in order, forms
 //                  E_i and the bound flag, and the radius key (bits of r^2).
 //   k_select       one block per progenitor: bound count and mass, radix
@@ -52,16 +51,27 @@ struct Elem<ScfD4> {
   static constexpr int I = 2;
 };
 
-// 1/sqrt(r2) of a pair; 0 for a pair that adds nothing (r2 zero, not finite,
-// or outside the normal single-precision range [1.18e-38, 3.40e38]).
-__device__ __forceinline__ float pair_inv_r(float r2) { return r2 > 0.f ? rsqrtf(r2) : 0.f; }
+// 1/sqrt(r2) of a pair; 0 for a pair that adds nothing: r2 zero, not finite,
+// or below the smallest normal number of the type (and in double precision
+// outside the normal single-precision range).
+//
+// Single precision: the hardware approximation (rsqrt.approx.ftz.f32, a few
+// ulp); r2 below FLT_MIN would be flushed to zero by it, so such pairs are left out.
+__device__ __forceinline__ float pair_inv_r(float r2) {
+  float y;
+  asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(r2));
+  return r2 >= 1.17549435e-38f ? y : 0.f;
+}
+// Double precision: the hardware estimate from the upper word of r2
+// (rsqrt.approx.ftz.f64, about 20 correct bits) and one Newton-Raphson step,
+// y <- y (3/2 - (r2/2) y^2), which turns a relative error e into -(3/2) e^2
+// (below 1e-12).  The normal range of r2 is tested on its upper word.
 __device__ __forceinline__ double pair_inv_r(double r2) {
-  // one Newton-Raphson step for y = r2^(-1/2), y <- y (3/2 - (r2/2) y^2), from the
-  // single-precision estimate: a relative error e becomes -(3/2) e^2
-  const float f = __double2float_rn(r2);
-  const double y = (double)rsqrtf(f);
+  double y;
+  asm("rsqrt.approx.ftz.f64 %0, %1;" : "=d"(y) : "d"(r2));
   const double yn = y * fma(-0.5 * r2, y * y, 1.5);
-  return (f >= 1.17549435e-38f && f <= 3.40282347e38f) ? yn : 0.0;
+  const unsigned hi = (unsigned)__double2hiint(r2);
+  return (hi - 0x00100000u) < (0x7FF00000u - 0x00100000u) ? yn : 0.0;
 }
 
 template <typename V4>

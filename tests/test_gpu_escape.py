@@ -80,6 +80,7 @@ def _compare(pos, vel, res, frac, tol, kin=0.5):
     v2 = vel[:, 0] ** 2 + vel[:, 1] ** 2 + vel[:, 2] ** 2
     scale = kin * v2 + np.abs(E_o - kin * v2)
     err = np.abs(E - E_o) / np.maximum(scale, 1e-300)
+    print(f"energy error vs oracle: max {err.max():.3g}, median {np.median(err):.3g}")
     assert err.max() < tol, err.max()
     decided = np.abs(E_o) > 4 * tol * scale
     assert np.array_equal(b[decided], b_o[decided])
