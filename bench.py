@@ -252,6 +252,43 @@ def workload_config(wl, precision, name):
 
 
 # --------------------------------------------------------------------- our arm
+# Pair terms of the boundedness sum: dx, dy, dz (3 adds), r^2 (1 multiply +
+# 2 FMAs) and m / r accumulated (1 FMA) = 7 operations of the FP32 or FP64
+# pipe per pair; 1/sqrt runs on the special-function unit.
+PAIR_OPS = 7
+
+
+def escape_timing(sim, p, v, offsets, precision, clocks, torch, reps=3):
+    """Time one scf_bound call (boundedness by direct summation, r_x and the
+    mask) with CUDA events on the handle's stream, after one untimed call."""
+    n = sim.n
+    bnd = torch.empty(n, dtype=torch.uint8, device=p.device)
+    msk = torch.empty_like(bnd)
+    st = torch.empty((sim.n_prog, 4), dtype=torch.float64, device=p.device)
+    from paper_2602_13385_gb300 import _lib
+    stream = sim.stream
+    with torch.cuda.stream(stream):
+        _lib.scf_bound(sim._h, p, v, 0.5, 0.999, None, bnd, msk, st)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(reps):
+            _lib.scf_bound(sim._h, p, v, 0.5, 0.999, None, bnd, msk, st)
+        e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / reps
+    pairs = float(sum((offsets[i + 1] - offsets[i]) ** 2 for i in range(len(offsets) - 1)))
+    clock = clocks.get("sm_max_mhz") or 2070.0
+    lanes = FP64_FMA_PER_SM_CLK if precision == "fp64" else FP32_FMA_PER_SM_CLK
+    ceiling = N_SM * lanes / PAIR_OPS * clock * 1e6
+    return {"kernel": "scf_bound (k_bound_pairs + k_bound_finish + k_select)", "ms": ms,
+            "pairs_per_s": pairs / (ms * 1e-3),
+            "roofline": {"bound": "alu", "achieved": pairs / (ms * 1e-3), "peak": ceiling, "unit": "pairs/s",
+                         "frac": pairs / (ms * 1e-3) / ceiling,
+                         "peak_basis": f"{'FP64' if precision == 'fp64' else 'FP32'} pipe: {N_SM} SMs x {lanes} "
+                                       f"lanes/clk / {PAIR_OPS} ops per pair x {clock:.0f} MHz"},
+            "n_bound": float(st[:, 0].sum().item())}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -266,6 +303,8 @@ def main():
                          "coefficient kernel, else 64/128/256 particles per tile; K3 = 64/128/256 threads)")
     ap.add_argument("--n", type=int, default=None,
                     help="particle count of a smaller case of the same workload (for profiling captures)")
+    ap.add_argument("--no-escape", action="store_true",
+                    help="skip the timing of the boundedness kernels (scf_bound) reported under 'escape'")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
@@ -403,6 +442,8 @@ def main():
                               candidates_ms=None if tuning is None else tuning["ms"]),
         "src_hash": src_hash(),
     }
+    if not args.no_escape:
+        line["escape"] = escape_timing(sim, p, v, offsets, precision, clocks, torch)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         base, ref = cpu_baseline(wl, precision) if wl.offsets is None else (None, None)
         if base is not None:
