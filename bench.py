@@ -252,10 +252,13 @@ def workload_config(wl, precision, name):
 
 
 # --------------------------------------------------------------------- our arm
-# Pair terms of the boundedness sum: dx, dy, dz (3 adds), r^2 (1 multiply +
-# 2 FMAs) and m / r accumulated (1 FMA) = 7 operations of the FP32 or FP64
-# pipe per pair; 1/sqrt runs on the special-function unit.
-PAIR_OPS = 7
+# Pair terms of the boundedness sum on the FP32 pipe.  Single precision:
+# dx, dy, dz (3 adds), r^2 (1 multiply + 2 FMAs) and m / r accumulated
+# (1 FMA) = 7 operations; 1/sqrt runs on the special-function unit.  Double
+# precision runs the same terms in float-float arithmetic: 86 single-precision
+# operations per pair (exact differences, squares with their rounding errors,
+# a Newton step for 1/r, a float-float accumulation).
+PAIR_OPS = {"mixed": 7, "fp64": 86}
 
 
 def escape_timing(sim, p, v, offsets, precision, clocks, torch, reps=3):
@@ -278,14 +281,15 @@ def escape_timing(sim, p, v, offsets, precision, clocks, torch, reps=3):
     ms = e0.elapsed_time(e1) / reps
     pairs = float(sum((offsets[i + 1] - offsets[i]) ** 2 for i in range(len(offsets) - 1)))
     clock = clocks.get("sm_max_mhz") or 2070.0
-    lanes = FP64_FMA_PER_SM_CLK if precision == "fp64" else FP32_FMA_PER_SM_CLK
-    ceiling = N_SM * lanes / PAIR_OPS * clock * 1e6
+    lanes = FP32_FMA_PER_SM_CLK
+    ops = PAIR_OPS[precision]
+    ceiling = N_SM * lanes / ops * clock * 1e6
     return {"kernel": "scf_bound (k_bound_pairs + k_bound_finish + k_select)", "ms": ms,
             "pairs_per_s": pairs / (ms * 1e-3),
             "roofline": {"bound": "alu", "achieved": pairs / (ms * 1e-3), "peak": ceiling, "unit": "pairs/s",
                          "frac": pairs / (ms * 1e-3) / ceiling,
-                         "peak_basis": f"{'FP64' if precision == 'fp64' else 'FP32'} pipe: {N_SM} SMs x {lanes} "
-                                       f"lanes/clk / {PAIR_OPS} ops per pair x {clock:.0f} MHz"},
+                         "peak_basis": f"FP32 pipe: {N_SM} SMs x {lanes} lanes/clk / {ops} ops per pair "
+                                       f"x {clock:.0f} MHz"},
             "n_bound": float(st[:, 0].sum().item())}
 
 

@@ -259,12 +259,13 @@ int scf_energy(scf_handle* h, const void* pos, const void* vel, const void* acc,
  * radius among p's bound particles, k = ceil(frac n_bound) (r_x = 0 when none
  * is bound); the coefficient set is r <= r_x (frac = 0.999 in the paper).
  * Radii are compared as r^2 = (x x + y y) + z z in double precision.
- * In double precision the pair sums are double and 1/r is the hardware
- * estimate refined by one Newton step (relative error < 1e-12); pairs whose
- * r^2 is not a normal double add nothing.  In mixed precision each pair
- * term and blocks of 64 of them are float (1/r the hardware approximation),
- * added in double; pairs whose r^2 is below the smallest normal float add
- * nothing.
+ * In double precision the pair terms are evaluated in float-float arithmetic
+ * (each coordinate and mass split into two floats, 48 bits; a term's
+ * relative error is about 1e-14 + 2^-48 |x| / r_ij) and blocks of 64 of them
+ * are added in double.  In mixed precision each pair term and blocks of 64
+ * of them are float (1/r the hardware approximation), added in double.  In
+ * both, pairs whose r^2 lies outside the normal float range
+ * [1.18e-38, 3.40e38] add nothing.
  *   pos, vel   device [N][4] in the handle's element type (16-byte aligned)
  *   kin        > 0 and finite;  frac in (0, 1]
  *   E_out      device [N] doubles (E_i), or NULL

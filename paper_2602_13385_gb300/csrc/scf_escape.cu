@@ -15,10 +15,11 @@
 //                  each block stages its j-segment through shared memory in
 //                  tiles and keeps four (float) or two (double) i-particles
 //                  per thread in registers.  Single precision sums blocks of
-//                  64 pair terms in float and adds them in double.  Double
-//                  precision is double throughout; 1/r is the hardware
-//                  estimate refined by one Newton step.  Each block writes
-//                  one double per particle and segment.
+//                  64 pair terms in float and adds them in double; double
+//                  precision evaluates the pair terms in float-float
+//                  arithmetic (k_bound_pairs_ff) and adds blocks of 64 of
+//                  them in double.  Each block writes one double per
+//                  particle and segment.
 //   k_bound_finish one thread per particle: adds the segments in order, forms
 //                  E_i and the bound flag, and the radius key (bits of r^2).
 //   k_select       one block per progenitor: bound count and mass, radix
@@ -51,29 +52,15 @@ struct Elem<ScfD4> {
   static constexpr int I = 2;
 };
 
-// 1/sqrt(r2) of a pair; 0 for a pair that adds nothing: r2 zero, not finite,
-// or below the smallest normal number of the type (and in double precision
-// outside the normal single-precision range).
-//
-// Single precision: the hardware approximation (rsqrt.approx.ftz.f32, a few
-// ulp); r2 below FLT_MIN would be flushed to zero by it, so such pairs are left out.
+// 1/sqrt(r2) of a single-precision pair by the hardware approximation
+// (rsqrt.approx.ftz.f32, a few ulp); 0 for a pair that adds nothing: r2 zero,
+// below the smallest normal float (which the approximation flushes to zero)
+// or not finite.
 __device__ __forceinline__ float pair_inv_r(float r2) {
   float y;
   asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(r2));
-  return r2 >= 1.17549435e-38f ? y : 0.f;
+  return r2 >= 1.17549435e-38f ? y : 0.f;  // r2 = inf gives y = 0
 }
-// Double precision: the hardware estimate from the upper word of r2
-// (rsqrt.approx.ftz.f64, about 20 correct bits) and one Newton-Raphson step,
-// y <- y (3/2 - (r2/2) y^2), which turns a relative error e into -(3/2) e^2
-// (below 1e-12).  The normal range of r2 is tested on its upper word.
-__device__ __forceinline__ double pair_inv_r(double r2) {
-  double y;
-  asm("rsqrt.approx.ftz.f64 %0, %1;" : "=d"(y) : "d"(r2));
-  const double yn = y * fma(-0.5 * r2, y * y, 1.5);
-  const unsigned hi = (unsigned)__double2hiint(r2);
-  return (hi - 0x00100000u) < (0x7FF00000u - 0x00100000u) ? yn : 0.0;
-}
-
 template <typename V4>
 __global__ void __launch_bounds__(kPairThreads) k_bound_pairs(BoundArgs a) {
   using T = typename Elem<V4>::T;
@@ -121,6 +108,127 @@ __global__ void __launch_bounds__(kPairThreads) k_bound_pairs(BoundArgs a) {
         }
 #pragma unroll
         for (int q = 0; q < kPairI; ++q) acc[q] += (double)part[q];
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < kPairI; ++q) {
+      const int64_t i = ib + threadIdx.x + q * kPairThreads;
+      if (i < o1) a.part[(size_t)blockIdx.z * (size_t)a.n_total + (size_t)i] = acc[q];
+    }
+  }
+}
+
+// Double-precision pair sums in float-float arithmetic ("double-single"):
+// GB300 retires 64 single-precision FMAs for each double one, and a pair term
+// carried as unevaluated sums of two floats (Dekker 1971; Knuth's TwoSum and
+// the FMA-based exact product) costs about 80 single-precision operations
+// against 11 double ones, so it runs several times faster at a relative error
+// near 1e-13.  Positions and masses are split once into hi + lo floats when
+// they are staged (48 of a double's 53 bits: a pair term's relative error
+// grows like 2^-48 |x| / r_ij for pairs far closer together than their
+// distance from the centre); separations are exact differences of the hi
+// parts plus the difference of the lo parts; r^2 keeps each square's
+// rounding error; 1/r is
+// the hardware estimate refined by one Newton step whose residual 1 - r^2 y^2
+// is formed in float-float; m / r is added to a float-float sum, folded into
+// a double every 64 pairs.
+struct FF {
+  float h, l;
+};
+
+// The error-free transformations are written with the _rn intrinsics, which
+// the compiler never contracts into FMAs (a contraction would break them).
+__device__ __forceinline__ FF two_sum(float a, float b) {
+  const float s = __fadd_rn(a, b);
+  const float bb = __fsub_rn(s, a);
+  return {s, __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb))};
+}
+
+__device__ __forceinline__ FF split_double(double x) {
+  const float h = __double2float_rn(x);
+  return {h, __double2float_rn(x - (double)h)};
+}
+
+__device__ __forceinline__ float rsqrt_approx(float x) {
+  float y;
+  asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+
+__global__ void __launch_bounds__(kPairThreads) k_bound_pairs_ff(BoundArgs a) {
+  constexpr int kPairI = Elem<ScfD4>::I;
+  __shared__ float4 s_hi[kPairThreads], s_lo[kPairThreads];
+  const ScfD4* pos = reinterpret_cast<const ScfD4*>(a.pos);
+  for (int p = blockIdx.y; p < a.n_prog; p += gridDim.y) {
+    const int64_t o0 = a.prog_off[p], o1 = a.prog_off[p + 1];
+    const int64_t ib = o0 + (int64_t)blockIdx.x * (kPairThreads * kPairI);
+    if (ib >= o1) continue;  // the same for every thread of the block
+    const int64_t seg = (o1 - o0 + a.split - 1) / a.split;
+    const int64_t j0 = min(o1, o0 + (int64_t)blockIdx.z * seg), j1 = min(o1, j0 + seg);
+    FF xi[kPairI], yi[kPairI], zi[kPairI];
+    double acc[kPairI];
+#pragma unroll
+    for (int q = 0; q < kPairI; ++q) {
+      const int64_t i = ib + threadIdx.x + q * kPairThreads;
+      const ScfD4 pi = i < o1 ? pos[i] : ScfD4{};
+      xi[q] = split_double(pi.x);
+      yi[q] = split_double(pi.y);
+      zi[q] = split_double(pi.z);
+      acc[q] = 0.0;
+    }
+    for (int64_t jb = j0; jb < j1; jb += kPairThreads) {
+      const int cnt = (int)min((int64_t)kPairThreads, j1 - jb);
+      __syncthreads();
+      if ((int)threadIdx.x < cnt) {
+        const ScfD4 pj = pos[jb + threadIdx.x];
+        const FF x = split_double(pj.x), y = split_double(pj.y), z = split_double(pj.z), m = split_double(pj.w);
+        s_hi[threadIdx.x] = make_float4(x.h, y.h, z.h, m.h);
+        s_lo[threadIdx.x] = make_float4(x.l, y.l, z.l, m.l);
+      }
+      __syncthreads();
+      for (int s = 0; s < cnt; s += kPairSub) {
+        const int e = min(cnt, s + kPairSub);
+        FF sum[kPairI];
+#pragma unroll
+        for (int q = 0; q < kPairI; ++q) sum[q] = {0.f, 0.f};
+#pragma unroll 2
+        for (int jj = s; jj < e; ++jj) {
+          const float4 hj = s_hi[jj], lj = s_lo[jj];
+#pragma unroll
+          for (int q = 0; q < kPairI; ++q) {
+            // separation: exact difference of the hi parts + difference of the lo parts
+            const FF dx = two_sum(hj.x, -xi[q].h), dy = two_sum(hj.y, -yi[q].h), dz = two_sum(hj.z, -zi[q].h);
+            const float lx = __fadd_rn(dx.l, __fsub_rn(lj.x, xi[q].l));
+            const float ly = __fadd_rn(dy.l, __fsub_rn(lj.y, yi[q].l));
+            const float lz = __fadd_rn(dz.l, __fsub_rn(lj.z, zi[q].l));
+            // r^2 = sum (h + l)^2 = sum h^2 + (2h + l) l, with the exact rounding
+            // error of each h^2, renormalised (all of r^2 may sit in the l parts)
+            const float px = __fmul_rn(dx.h, dx.h), py = __fmul_rn(dy.h, dy.h), pz = __fmul_rn(dz.h, dz.h);
+            const float cx = fmaf(__fadd_rn(__fadd_rn(dx.h, dx.h), lx), lx, fmaf(dx.h, dx.h, -px));
+            const float cy = fmaf(__fadd_rn(__fadd_rn(dy.h, dy.h), ly), ly, fmaf(dy.h, dy.h, -py));
+            const float cz = fmaf(__fadd_rn(__fadd_rn(dz.h, dz.h), lz), lz, fmaf(dz.h, dz.h, -pz));
+            const FF s1 = two_sum(px, py);
+            const FF s2 = two_sum(s1.h, pz);
+            const FF r2 = two_sum(s2.h, __fadd_rn(__fadd_rn(s1.l, s2.l), __fadd_rn(__fadd_rn(cx, cy), cz)));
+            const float r2h = r2.h, r2l = r2.l;
+            // 1/r: one Newton step y0 (1 + d/2), d = 1 - r^2 y0^2 in float-float
+            const float y0 = rsqrt_approx(r2h);
+            const float t = __fmul_rn(y0, y0), te = fmaf(y0, y0, -t);
+            const float u = __fmul_rn(r2h, t);
+            const float ue = fmaf(r2l, t, fmaf(r2h, te, fmaf(r2h, t, -u)));
+            const float d = __fsub_rn(__fsub_rn(1.f, u), ue);
+            const float corr = __fmul_rn(__fmul_rn(0.5f, y0), d);
+            const float yh = __fadd_rn(y0, corr), yl = __fsub_rn(corr, __fsub_rn(yh, y0));
+            // m / r into the float-float sum; pairs outside the normal range add nothing
+            const bool ok = r2h >= 1.17549435e-38f && r2h <= 3.40282347e38f;
+            const float ph = ok ? __fmul_rn(hj.w, yh) : 0.f;
+            const float pe = ok ? fmaf(hj.w, yl, fmaf(lj.w, yh, fmaf(hj.w, yh, -ph))) : 0.f;
+            const FF ns = two_sum(sum[q].h, ph);
+            sum[q] = {ns.h, __fadd_rn(sum[q].l, __fadd_rn(ns.l, pe))};
+          }
+        }
+#pragma unroll
+        for (int q = 0; q < kPairI; ++q) acc[q] += (double)sum[q].h + (double)sum[q].l;
       }
     }
 #pragma unroll
@@ -340,7 +448,7 @@ cudaError_t scf_bound_launch(const BoundArgs& a, int64_t max_chunks, cudaStream_
   if (a.n_total > 0 && max_chunks > 0) {
     const dim3 grid((unsigned)max_chunks, (unsigned)(a.n_prog < 65535 ? a.n_prog : 65535), (unsigned)a.split);
     if (a.f32) k_bound_pairs<float4><<<grid, kPairThreads, 0, s>>>(a);
-    else k_bound_pairs<ScfD4><<<grid, kPairThreads, 0, s>>>(a);
+    else k_bound_pairs_ff<<<grid, kPairThreads, 0, s>>>(a);
     const unsigned fb = (unsigned)((a.n_total + 255) / 256);
     if (a.f32) k_bound_finish<float4><<<fb, 256, 0, s>>>(a);
     else k_bound_finish<ScfD4><<<fb, 256, 0, s>>>(a);
