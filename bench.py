@@ -47,7 +47,12 @@ WORKLOADS = {
     "plummer_eccentric_fp64": ("plummer_eccentric", "fp64"),
     "batch10_mixed": ("progenitor_batch", "mixed"),
     "plummer_isolated_fp64": ("plummer_isolated", "fp64"),
+    # the paper's stream progenitors (King W0 = 5, 1e5 Msun, r_h = 10 pc, N = 2e5
+    # each) on its ten Table A3 orbits in MilkyWayPotential2022, (10, 5)
+    "paper_orbits_mixed": ("paper_orbits", "mixed"),
+    "paper_orbits_fp64": ("paper_orbits", "fp64"),
 }
+BUILDER_ARGS = {"paper_orbits": {"n_per": 200_000}}
 DEFAULT_WORKLOAD = "king_circular_fp64"
 
 
@@ -132,8 +137,13 @@ def build_workload(name, n_override=None):
     import workloads
     builder, precision = WORKLOADS[name]
     fn = getattr(workloads, builder)
-    wl = fn() if n_override is None else fn(n=n_override)
-    return wl, precision
+    kw = dict(BUILDER_ARGS.get(builder, {}))
+    if n_override is not None:
+        if "n_per" in kw:
+            kw["n_per"] = max(1, n_override // 10)
+        else:
+            kw["n"] = n_override
+    return fn(**kw), precision
 
 
 def traffic_for(kernel: str, workload: str):
@@ -247,7 +257,8 @@ def run_reference(args, rank, world):
 def workload_config(wl, precision, name):
     return {"workload": wl.name, "bench_name": name, "N": int(wl.n), "nmax": wl.nmax, "lmax": wl.lmax,
             "precision": precision, "n_progenitors": 1 if wl.offsets is None else len(wl.offsets) - 1,
-            "host": "NFW(Mvir=1e12,rs=20kpc)+MN(6.8e10,3,0.28kpc)+Hernquist(5e9,0.5kpc)" if wl.host else "none",
+            "host": ("MilkyWayPotential2022 (Table A2)" if wl.name.startswith("paper_orbits") else
+                     "NFW(Mvir=1e12,rs=20kpc)+MN(6.8e10,3,0.28kpc)+Hernquist(5e9,0.5kpc)") if wl.host else "none",
             "dt_henon": wl.dt, "l2": "flushed (256 MiB write) before every timed step"}
 
 

@@ -1,0 +1,113 @@
+"""The paper's ten orbits (Table A3) in MilkyWayPotential2022 (Table A2) as a
+batched GPU workload (`workloads.paper_orbits`).
+
+* The centre orbits the GPU integrates (kernel 2's double-precision leapfrog,
+  all ten progenitors in one launch) start on the energies and angular
+  momenta printed in Table 1 and keep them to the printed digits over
+  4000 steps; they agree with the oracle's integration of the same orbits.
+* Batching with the escape physics: with a schedule that every progenitor
+  shares (max_steps below every dt_int), one batched scf_evolve of the ten
+  clusters gives each cluster's state as the ten single-cluster runs do.
+"""
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+import workloads
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden", "mw2022_orbits.txt")
+
+
+@pytest.fixture(scope="module")
+def scf():
+    if not torch.cuda.is_available():
+        pytest.skip("needs a GPU")
+    import paper_2602_13385_gb300 as pkg
+    return pkg
+
+
+def dev(x, dtype=torch.float64):
+    return torch.tensor(np.ascontiguousarray(x), device="cuda", dtype=dtype)
+
+
+def _table1():
+    rows = [ln.split() for ln in open(GOLDEN) if ln.strip() and not ln.startswith("#")]
+    return np.array([[float(v) for v in r[1:]] for r in rows])
+
+
+def _E_Lz(wl, com):
+    """E in 1e5 (km/s)^2 and L_z in 1e3 kpc km/s of centre states (Henon units)."""
+    host = oracle.host_struct(wl.host)
+    u = wl.units
+    v_kms = u.V_pc_myr / workloads.KMS_TO_PC_MYR
+    out = []
+    for c in com:
+        _, psi = oracle.host_accel(host, c[:3])
+        E = (0.5 * np.dot(c[3:], c[3:]) + psi) * v_kms**2
+        Lz = (c[0] * c[4] - c[1] * c[3]) * u.rv_pc * 1e-3 * v_kms
+        out.append((E / 1e5, Lz / 1e3))
+    return np.array(out)
+
+
+def test_centre_orbits_keep_table1_integrals(scf):
+    wl = workloads.paper_orbits(n_per=300, nsteps=4000)
+    tab = _table1()
+    cfg = scf.Config(nmax=wl.nmax, lmax=wl.lmax, b=wl.b, dt=wl.dt, host=list(wl.host))
+    sim = scf.SCF(cfg, offsets=wl.offsets, b_per_prog=wl.b_per_prog)
+    p, v, c = dev(wl.pos), dev(wl.vel), dev(wl.com_per_prog)
+    a = sim.forces(p, sim.coeffs(p), com=c)
+    EL0 = _E_Lz(wl, wl.com_per_prog)
+    assert np.all(np.abs(EL0[:, 0] - tab[:, 7]) <= 0.005 + 1e-9), (EL0[:, 0], tab[:, 7])
+    assert np.all(np.abs(np.abs(EL0[:, 1]) - tab[:, 6]) <= 0.005 + 1e-9), (EL0[:, 1], tab[:, 6])
+    sim.step(p, v, a, com=c, nsteps=wl.nsteps)
+    com = c.cpu().numpy()
+    EL1 = _E_Lz(wl, com)
+    print("centre E drift", np.abs(EL1[:, 0] - EL0[:, 0]).max(), "L_z drift", np.abs(EL1[:, 1] - EL0[:, 1]).max())
+    assert np.all(np.abs(EL1[:, 0] - tab[:, 7]) <= 0.005 + 1e-9)
+    assert np.all(np.abs(np.abs(EL1[:, 1]) - tab[:, 6]) <= 0.005 + 1e-9)
+    assert np.abs(EL1[:, 1] - EL0[:, 1]).max() < 1e-9 * np.abs(EL0[:, 1]).max()   # axisymmetric host
+    # the oracle's leapfrog of the same centres (one massless particle at the centre)
+    host = oracle.host_struct(wl.host)
+    for i in (0, 5, 9):
+        pos = np.array([[0.0, 0.0, 0.0, 0.0]])
+        vel = np.zeros((1, 4))
+        acc = np.zeros((1, 4))
+        ref = oracle.step(pos, vel, acc, 0, 0, 1.0, wl.dt, wl.nsteps, com=wl.com_per_prog[i], host=host,
+                          A_frozen=np.zeros(2))[3]
+        assert np.max(np.abs(com[i] - ref)) < 1e-9 * np.max(np.abs(ref)), (i, com[i], ref)
+    assert sim.status() == (0, 0)
+
+
+def test_batched_evolve_matches_single_clusters(scf):
+    wl = workloads.paper_orbits(n_per=1500, nsteps=200)
+    host = oracle.host_struct(wl.host)
+    dt_int = oracle.tidal_scales(host, wl.com_per_prog[:, :3], np.ones(10))[:, 15]
+    max_steps = 40
+    assert np.all(np.floor(dt_int / wl.dt) > max_steps)     # one schedule for all
+    cfg = scf.Config(nmax=wl.nmax, lmax=wl.lmax, b=wl.b, dt=wl.dt, host=list(wl.host), precision="fp64")
+    sim = scf.SCF(cfg, offsets=wl.offsets, b_per_prog=wl.b_per_prog)
+    p, v, c = dev(wl.pos), dev(wl.vel), dev(wl.com_per_prog)
+    a = sim.forces(p, sim.coeffs(p), com=c)
+    b, m, st, n_int = sim.evolve(p, v, a, c, nsteps=wl.nsteps, max_steps=max_steps)
+    assert n_int == 5
+    P, V, B, ST = p.cpu().numpy(), v.cpu().numpy(), b.cpu().numpy(), st.cpu().numpy()
+    for i in (0, 3, 7):
+        s = slice(wl.offsets[i], wl.offsets[i + 1])
+        one = scf.SCF(scf.Config(nmax=wl.nmax, lmax=wl.lmax, b=float(wl.b_per_prog[i]), dt=wl.dt,
+                                 host=list(wl.host)), n=int(wl.offsets[i + 1] - wl.offsets[i]))
+        p1, v1, c1 = dev(wl.pos[s]), dev(wl.vel[s]), dev(wl.com_per_prog[i][None])
+        a1 = one.forces(p1, one.coeffs(p1), com=c1)
+        b1, m1, st1, n1 = one.evolve(p1, v1, a1, c1, nsteps=wl.nsteps, max_steps=max_steps)
+        assert n1 == n_int
+        assert np.array_equal(b1.cpu().numpy(), B[s]), i
+        assert st1[0, 0].item() == ST[i, 0] and abs(st1[0, 2].item() - ST[i, 2]) <= 1e-9 * ST[i, 2], i
+        scale = np.abs(P[s, :3]).max()
+        assert np.abs(p1.cpu().numpy() - P[s]).max() < 1e-9 * scale, i
+        assert np.abs(v1.cpu().numpy() - V[s]).max() < 1e-9 * np.abs(V[s, :3]).max(), i
+        assert np.array_equal(c1.cpu().numpy()[0], c.cpu().numpy()[i]), i
+    assert sim.status() == (0, 0)

@@ -420,6 +420,46 @@ def reference_track(R, V, n_points: int = 256, half_length: float = 50.0, sigma:
     return R[None] + s[:, None] * t[None] + off[:, :1] * e1[None] + off[:, 1:] * e2[None]
 
 
+# Table A3: initial positions (kpc) and velocities (km/s) of Orbits 0-9 in
+# the host frame of MilkyWayPotential2022.
+PAPER_ORBITS_A3 = [
+    (-8.26114834, 4.31927900, -6.25723160, -74.46836937, 14.72551502, -137.10220626),
+    (6.65417846, -6.77625060, -6.89249860, 131.88487388, -54.38017150, 4.34224828),
+    (7.90677816, 19.00502796, -7.29228303, -38.33588368, -66.85081211, 111.04181836),
+    (9.73591969, 8.80768907, 0.73284850, -59.71003689, 91.24008328, -39.80505238),
+    (-7.75511077, 6.32704860, 23.10803486, 1.54688377, -69.83998228, 18.65659155),
+    (-9.14496546, -2.86774379, 4.55846674, 25.93998870, -146.50950043, -246.21359733),
+    (-20.83691936, -15.77790335, -20.69545845, -13.04785291, -35.40337893, -181.82805977),
+    (-18.82672221, 27.56963834, 27.40177203, 25.20438668, -112.02637209, 29.55096514),
+    (22.45554180, 35.25629955, -2.75494642, -10.73021364, -7.94047313, -128.19547342),
+    (-23.95107022, 9.24097888, -14.06736155, 27.31176344, -167.54952847, -128.11428538),
+]
+
+
+def paper_orbits(n_per: int = 20_000, seed: int = 60, nsteps: int = 4000) -> Workload:
+    """The paper's stream progenitors on its ten orbits: King W0 = 5 clusters of
+    1e5 Msun and r_h = 10 pc (Sec. 3), one per orbit of Table A3, in
+    MilkyWayPotential2022 (Table A2); nmax = 10, lmax = 5 (the paper's
+    fiducial stream model), dt = 0.01.  The paper samples N = 5e4 or 2e5 stars
+    per cluster; ``n_per`` sets it here.  All clusters share one unit system."""
+    ref = king(20000, 5.0, seed)
+    units = Units(1e5, 10.0 / half_mass_radius(ref[0]))
+    host = host_in_units([(k, M, a * 1e3, b * 1e3) for (k, M, a, b) in mw2022_physical()], units)
+    pos_l, vel_l, bs, coms = [], [], [], []
+    for p, ic in enumerate(PAPER_ORBITS_A3):
+        pos, vel = king(int(n_per), 5.0, seed + 1 + p)
+        lam = (10.0 / units.rv_pc) / half_mass_radius(pos)     # exactly r_h = 10 pc
+        pos[:, :3] *= lam
+        vel[:, :3] /= math.sqrt(lam)
+        pos_l.append(pos)
+        vel_l.append(vel)
+        bs.append(basis_scale(half_mass_radius(pos)))
+        coms.append(_com_from_orbit({"R_kpc": ic[:3], "V_kms": ic[3:]}, units))
+    offsets = np.concatenate([[0], np.cumsum([len(q) for q in pos_l])]).astype(np.int64)
+    return Workload(f"paper_orbits10_king5_n{n_per}", np.concatenate(pos_l), np.concatenate(vel_l), 10, 5,
+                    float(bs[0]), 0.01, nsteps, host, coms[0], units, offsets, np.array(bs), np.array(coms))
+
+
 def progenitor_batch(n_prog: int = 10, seed: int = 40, n_range=(2e4, 5e5), nsteps: int = 2000,
                      scale: float = 1.0) -> Workload:
     """Batch of progenitors with N log-uniform in ``n_range`` (times ``scale``)
