@@ -63,6 +63,9 @@ struct scf_handle {
   int bound_split = 1;
   int64_t bound_chunks = 0;              // pair-kernel i-blocks of the largest progenitor
   const uint8_t* step_mask = nullptr;    // coefficient set of scf_step (scf_set_mask)
+  // kernel 2's second level: chunk sums and arrival counters
+  double* d_k2z = nullptr;               // [n_prog][kK2MaxChunks][2*NC]
+  unsigned* d_k2cnt = nullptr;           // [n_prog][groups], zero between launches
   ScfLaunchInfo k1d{}, k3d{};
   bool adj_ready = false;
   // launch timing (scf_profile)
@@ -183,6 +186,16 @@ K2Args k2_args(scf_handle* h, double* A_out, double* com, int mode) {
   a.com = com;
   a.host = h->host;
   a.sub = h->k1.variant == 1 ? h->k1.sub * h->k1.win : 0;
+  // split each column group's rows over z blocks when the groups alone would
+  // leave SMs idle (about three blocks per SM), at least 64 rows per chunk
+  const int groups = scf_k2_groups(h->nc);
+  const int64_t rows = (int64_t)h->k1_blocks * (a.sub > 0 ? a.sub : 1) / std::max(1, h->n_prog);
+  int z = (int)std::min<int64_t>(kK2MaxChunks, std::max<int64_t>(1, (3 * (int64_t)h->n_sm + (int64_t)groups * h->n_prog - 1) /
+                                                                        ((int64_t)groups * h->n_prog)));
+  z = (int)std::min<int64_t>(z, std::max<int64_t>(1, rows / 64));
+  a.z = z;
+  a.zpart = h->d_k2z;
+  a.counters = h->d_k2cnt;
   return a;
 }
 
@@ -461,6 +474,8 @@ int scf_init(const scf_config* cfg, int n_prog, const int64_t* offsets, const do
   const size_t o_bpart = take(sizeof(double) * (size_t)h->bound_split * (size_t)h->n_total);
   const size_t o_key = take(sizeof(unsigned long long) * (size_t)h->n_total);
   const size_t o_tid = take(sizeof(double) * 16 * (size_t)n_prog);
+  const size_t o_k2z = take(sizeof(double) * kK2MaxChunks * 2 * (size_t)h->nc * n_prog);
+  const size_t o_k2c = take(sizeof(unsigned) * (size_t)scf_k2_groups(h->nc) * n_prog);
   if (cudaMalloc(&h->d_base, off) != cudaSuccess) {
     cudaGetLastError();
     return fail(SCF_ERR_OUT_OF_MEMORY);
@@ -487,6 +502,8 @@ int scf_init(const scf_config* cfg, int n_prog, const int64_t* offsets, const do
   h->d_bpart = reinterpret_cast<double*>(base + o_bpart);
   h->d_key = reinterpret_cast<unsigned long long*>(base + o_key);
   h->d_tid = reinterpret_cast<double*>(base + o_tid);
+  h->d_k2z = reinterpret_cast<double*>(base + o_k2z);
+  h->d_k2cnt = reinterpret_cast<unsigned*>(base + o_k2c);
 
   std::vector<double> norm(2 * (size_t)h->nc), ksc(2 * (size_t)h->nc);
   scf_make_norm(cfg->nmax, cfg->lmax, norm.data());
@@ -497,6 +514,7 @@ int scf_init(const scf_config* cfg, int n_prog, const int64_t* offsets, const do
   bool ok = ksc_ok && put(h->d_norm, norm.data(), sizeof(double) * norm.size()) &&
             put(h->d_b, bs.data(), sizeof(double) * n_prog) &&
             put(h->d_off, h->offsets.data(), sizeof(int64_t) * (n_prog + 1)) &&
+            cudaMemset(h->d_k2cnt, 0, sizeof(unsigned) * (size_t)scf_k2_groups(h->nc) * n_prog) == cudaSuccess &&
             cudaMemset(h->d_status, 0, sizeof(unsigned) * 4) == cudaSuccess &&
             cudaMemset(h->d_A, 0, sizeof(double) * 2 * (size_t)h->nc * n_prog) == cudaSuccess;
   if (!ok) return fail(SCF_ERR_CUDA);

@@ -626,14 +626,19 @@ __device__ __forceinline__ void write_force_pair(void* F, int f32, size_t i, dou
 constexpr int K2_X = 16, K2_SLICES = 64;
 __global__ void __launch_bounds__(K2_X * K2_SLICES) k2_reduce(K2Args a) {
   __shared__ double s_c[K2_SLICES][K2_X], s_s[K2_SLICES][K2_X];
-  const int p = blockIdx.y;
+  __shared__ int s_last;
+  const int p = blockIdx.y, z = blockIdx.z, Z = gridDim.z;
   const int x = threadIdx.x, y = threadIdx.y;
   const int i = blockIdx.x * K2_X + x;
   const size_t stride = 2 * (size_t)a.nc;
   double sc = 0.0, ss = 0.0;
   if (i < a.nc) {
+    // this block's share of the progenitor's rows: chunk z of Z
+    const int mul = a.sub == 0 ? 1 : a.sub;
+    const int R0 = a.prog_blk_off[p] * mul, R1 = a.prog_blk_off[p + 1] * mul;
+    const int chunk = (R1 - R0 + Z - 1) / Z;
+    const int r0 = min(R1, R0 + z * chunk), r1 = min(R1, r0 + chunk);
     if (a.sub == 0) {  // double rows, one per block
-      const int r0 = a.prog_blk_off[p], r1 = a.prog_blk_off[p + 1];
 #pragma unroll 4
       for (int r = r0 + y; r < r1; r += K2_SLICES) {
         const double* src = a.partials + (size_t)r * stride + i;
@@ -648,7 +653,6 @@ __global__ void __launch_bounds__(K2_X * K2_SLICES) k2_reduce(K2Args a) {
       while ((l + 1) * (l + 2) / 2 <= lm) ++l;
       const bool has_t = lm != scf_lm(l, 0);
       const float* P = reinterpret_cast<const float*>(a.partials);
-      const int r0 = a.prog_blk_off[p] * a.sub, r1 = a.prog_blk_off[p + 1] * a.sub;
       float ch = 0.f, cl = 0.f, th = 0.f, tl = 0.f;
       auto two_sum = [](float& hi, float& lo, float v) {
         const float s = hi + v, bp = s - hi;
@@ -675,6 +679,33 @@ __global__ void __launch_bounds__(K2_X * K2_SLICES) k2_reduce(K2Args a) {
       sc += s_c[k][x];
       ss += s_s[k][x];
     }
+  }
+  if (Z > 1) {
+    // chunk sums to the scratch; the last of the Z blocks of this column
+    // group to arrive adds them in chunk order (the same order every run)
+    double* zp = a.zpart + (size_t)p * Z * stride;
+    if (y == 0 && i < a.nc) {
+      zp[(size_t)z * stride + i] = sc;
+      zp[(size_t)z * stride + a.nc + i] = ss;
+    }
+    __threadfence();
+    __syncthreads();
+    unsigned* cnt = a.counters + (size_t)p * gridDim.x + blockIdx.x;
+    if (x == 0 && y == 0) s_last = atomicAdd(cnt, 1u) == (unsigned)(Z - 1);
+    __syncthreads();
+    if (!s_last) return;
+    __threadfence();
+    if (y == 0 && i < a.nc) {
+      sc = __ldcg(zp + i);
+      ss = __ldcg(zp + a.nc + i);
+      for (int k = 1; k < Z; ++k) {
+        sc += __ldcg(zp + (size_t)k * stride + i);
+        ss += __ldcg(zp + (size_t)k * stride + a.nc + i);
+      }
+    }
+    if (x == 0 && y == 0) *cnt = 0u;  // ready for the next launch
+  }
+  if (y == 0 && i < a.nc) {
     const double S = sc * a.norm[i], T = ss * a.norm[a.nc + i];
     double* A = a.A_out + (size_t)p * stride;
     A[i] = S;
@@ -825,8 +856,11 @@ cudaError_t scf_k1_launch(int precision, const K1Args& a, int blocks, const ScfL
   return cudaGetLastError();
 }
 
+int scf_k2_groups(int nc) { return (nc + K2_X - 1) / K2_X; }
+
 cudaError_t scf_k2_launch(const K2Args& a, cudaStream_t s) {
-  dim3 grid((a.nc + K2_X - 1) / K2_X, a.n_prog);
+  const int Z = (a.zpart && a.counters && a.z > 1) ? a.z : 1;
+  dim3 grid((a.nc + K2_X - 1) / K2_X, a.n_prog, Z);
   k2_reduce<<<grid, dim3(K2_X, K2_SLICES), 0, s>>>(a);
   return cudaGetLastError();
 }

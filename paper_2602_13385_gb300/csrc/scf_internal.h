@@ -76,7 +76,16 @@ struct K2Args {
   // partials layout: sub == 0: [blocks][2*NC] doubles; sub > 0: [blocks][sub][2*NC]
   // floats without the T_nl0 entries (read as 0)
   int sub;
+  // optional second level: z > 1 blocks per column group each add a chunk of
+  // the rows into zpart ([n_prog][z][2*NC] doubles); the last to finish (per
+  // counters[n_prog][groups], zero between launches) adds the chunks in order
+  int z;
+  double* zpart;
+  unsigned* counters;
 };
+// Column groups of kernel 2 for NC coefficients (the counters per progenitor).
+int scf_k2_groups(int nc);
+constexpr int kK2MaxChunks = 16;
 
 // Force coefficients and a_host(R) from given coefficients (scf_forces).
 struct PrepArgs {
