@@ -187,12 +187,12 @@ K2Args k2_args(scf_handle* h, double* A_out, double* com, int mode) {
   a.host = h->host;
   a.sub = h->k1.variant == 1 ? h->k1.sub * h->k1.win : 0;
   // split each column group's rows over z blocks when the groups alone would
-  // leave SMs idle (about three blocks per SM), at least 64 rows per chunk
+  // leave SMs idle (about four blocks per SM), at least 32 rows per chunk
   const int groups = scf_k2_groups(h->nc);
   const int64_t rows = (int64_t)h->k1_blocks * (a.sub > 0 ? a.sub : 1) / std::max(1, h->n_prog);
-  int z = (int)std::min<int64_t>(kK2MaxChunks, std::max<int64_t>(1, (3 * (int64_t)h->n_sm + (int64_t)groups * h->n_prog - 1) /
-                                                                        ((int64_t)groups * h->n_prog)));
-  z = (int)std::min<int64_t>(z, std::max<int64_t>(1, rows / 64));
+  const int64_t gp = (int64_t)groups * h->n_prog;
+  int z = (int)std::min<int64_t>(kK2MaxChunks, std::max<int64_t>(1, (4 * (int64_t)h->n_sm + gp - 1) / gp));
+  z = (int)std::min<int64_t>(z, std::max<int64_t>(1, rows / 32));
   a.z = z;
   a.zpart = h->d_k2z;
   a.counters = h->d_k2cnt;

@@ -597,19 +597,41 @@ auto dispatch_tiled(int nmax, int lmax, F&& f) {
 // ---------------------------------------------------------------------------
 // kernel 2
 // ---------------------------------------------------------------------------
-__device__ void com_kdk(const ScfHostParams& hp, double* c, double dt) {
+// Host acceleration at (x, y, z) evaluated by one warp: lane c computes
+// component c and lane 0 adds them in component order, the same sum as
+// scf_host_accel (the dependent double-precision chains of the components
+// run side by side instead of one after another).  Result valid in lane 0.
+__device__ void host_accel_warp(const ScfHostParams& hp, double x, double y, double z, double& ax, double& ay,
+                                double& az) {
+  const int lane = threadIdx.x & 31;
+  double cx = 0.0, cy = 0.0, cz = 0.0;
+  if (lane < hp.n) scf_host_comp_accel<double>(hp.kind[lane], hp.GM[lane], hp.a[lane], hp.b[lane], x, y, z, cx, cy, cz);
+  ax = ay = az = 0.0;
+  for (int c = 0; c < hp.n; ++c) {
+    ax += __shfl_sync(0xffffffffu, cx, c);
+    ay += __shfl_sync(0xffffffffu, cy, c);
+    az += __shfl_sync(0xffffffffu, cz, c);
+  }
+}
+
+// Kick-drift-kick of the centre (R, V) in the host field by one warp (every
+// lane holds the same state); returns a_host at the new R in a_new.
+__device__ void com_kdk(const ScfHostParams& hp, double* c, double dt, double* a_new) {
   double ax, ay, az;
-  scf_host_accel(hp, c[0], c[1], c[2], ax, ay, az);
+  host_accel_warp(hp, c[0], c[1], c[2], ax, ay, az);
   c[3] += 0.5 * dt * ax;
   c[4] += 0.5 * dt * ay;
   c[5] += 0.5 * dt * az;
   c[0] += dt * c[3];
   c[1] += dt * c[4];
   c[2] += dt * c[5];
-  scf_host_accel(hp, c[0], c[1], c[2], ax, ay, az);
+  host_accel_warp(hp, c[0], c[1], c[2], ax, ay, az);
   c[3] += 0.5 * dt * ax;
   c[4] += 0.5 * dt * ay;
   c[5] += 0.5 * dt * az;
+  a_new[0] = ax;
+  a_new[1] = ay;
+  a_new[2] = az;
 }
 
 __device__ __forceinline__ void write_force_pair(void* F, int f32, size_t i, double c, double s) {
@@ -617,18 +639,39 @@ __device__ __forceinline__ void write_force_pair(void* F, int f32, size_t i, dou
   else reinterpret_cast<double2*>(F)[i] = make_double2(c, s);
 }
 
-// K2_X consecutive coefficient pairs per block (threadIdx.x) times K2_SLICES
-// row slices (threadIdx.y): slice y adds the rows y, y + K2_SLICES, ... of
-// the progenitor in order, reading K2_X consecutive entries of a row at a
-// time, and the slice sums are then added in the order of y, so the result
-// is the same on every run.  Many slices keep enough loads in flight to
-// stream the partials (a few rows per thread) with a one-progenitor grid.
-constexpr int K2_X = 16, K2_SLICES = 64;
+// Kernel 2.  Block (groups, p, 0) steps the centre of progenitor p and
+// evaluates a_host there (a chain of dependent double-precision operations
+// in one thread), concurrently with the reduction blocks.
+// Block (g < groups, p, z): coefficient pairs 32g .. 32g + 31 (threadIdx.x,
+// one 128-byte row segment per warp load) of progenitor p, over chunk z of
+// the progenitor's partial rows, in K2_SLICES row slices (threadIdx.y): slice
+// y adds rows y, y + K2_SLICES, ... of the chunk in order; the slices are
+// combined by a fixed binary tree.  With more than one chunk, each block
+// stores its chunk sums and the last block of the column group to finish
+// (an arrival counter, nobody waits) adds the chunks in chunk order.  Every
+// sum has a fixed order, so the result is the same on every run.
+constexpr int K2_X = 32, K2_SLICES = 8;
 __global__ void __launch_bounds__(K2_X * K2_SLICES) k2_reduce(K2Args a) {
   __shared__ double s_c[K2_SLICES][K2_X], s_s[K2_SLICES][K2_X];
   __shared__ int s_last;
   const int p = blockIdx.y, z = blockIdx.z, Z = gridDim.z;
   const int x = threadIdx.x, y = threadIdx.y;
+  const int groups = gridDim.x - 1;
+  if ((int)blockIdx.x == groups) {  // the centre block: its first warp
+    if (z == 0 && y == 0 && a.host.n > 0 && a.com != nullptr) {
+      double c[6], an[3];
+      for (int d = 0; d < 6; ++d) c[d] = a.com[6 * p + d];
+      if (a.mode == SCF_MODE_STEP) com_kdk(a.host, c, a.dt, an);
+      else host_accel_warp(a.host, c[0], c[1], c[2], an[0], an[1], an[2]);
+      if (x == 0) {
+        if (a.mode == SCF_MODE_STEP)
+          for (int d = 0; d < 6; ++d) a.com[6 * p + d] = c[d];
+        if (a.aR_out)
+          for (int d = 0; d < 3; ++d) a.aR_out[4 * p + d] = an[d];
+      }
+    }
+    return;
+  }
   const int i = blockIdx.x * K2_X + x;
   const size_t stride = 2 * (size_t)a.nc;
   double sc = 0.0, ss = 0.0;
@@ -671,18 +714,17 @@ __global__ void __launch_bounds__(K2_X * K2_SLICES) k2_reduce(K2Args a) {
   s_c[y][x] = sc;
   s_s[y][x] = ss;
   __syncthreads();
-  if (y == 0 && i < a.nc) {
-    sc = s_c[0][x];
-    ss = s_s[0][x];
 #pragma unroll
-    for (int k = 1; k < K2_SLICES; ++k) {
-      sc += s_c[k][x];
-      ss += s_s[k][x];
+  for (int h = K2_SLICES / 2; h >= 1; h >>= 1) {
+    if (y < h) {
+      s_c[y][x] += s_c[y + h][x];
+      s_s[y][x] += s_s[y + h][x];
     }
+    __syncthreads();
   }
+  sc = s_c[0][x];
+  ss = s_s[0][x];
   if (Z > 1) {
-    // chunk sums to the scratch; the last of the Z blocks of this column
-    // group to arrive adds them in chunk order (the same order every run)
     double* zp = a.zpart + (size_t)p * Z * stride;
     if (y == 0 && i < a.nc) {
       zp[(size_t)z * stride + i] = sc;
@@ -690,7 +732,7 @@ __global__ void __launch_bounds__(K2_X * K2_SLICES) k2_reduce(K2Args a) {
     }
     __threadfence();
     __syncthreads();
-    unsigned* cnt = a.counters + (size_t)p * gridDim.x + blockIdx.x;
+    unsigned* cnt = a.counters + (size_t)p * groups + blockIdx.x;
     if (x == 0 && y == 0) s_last = atomicAdd(cnt, 1u) == (unsigned)(Z - 1);
     __syncthreads();
     if (!s_last) return;
@@ -713,14 +755,6 @@ __global__ void __launch_bounds__(K2_X * K2_SLICES) k2_reduce(K2Args a) {
     if (a.F_out) {
       const double w = -a.G / a.b_prog[p] * c_tab.inv_nlm[i % a.nlm];
       write_force_pair(a.F_out, a.f32, (size_t)p * a.nc + i, w * S, w * T);
-    }
-  }
-  if (blockIdx.x == 0 && x == 0 && y == 0 && a.host.n > 0 && a.com != nullptr) {
-    double* c = a.com + 6 * p;
-    if (a.mode == SCF_MODE_STEP) com_kdk(a.host, c, a.dt);
-    if (a.aR_out) {
-      double* r = a.aR_out + 4 * p;
-      scf_host_accel(a.host, c[0], c[1], c[2], r[0], r[1], r[2]);
     }
   }
 }
@@ -860,7 +894,7 @@ int scf_k2_groups(int nc) { return (nc + K2_X - 1) / K2_X; }
 
 cudaError_t scf_k2_launch(const K2Args& a, cudaStream_t s) {
   const int Z = (a.zpart && a.counters && a.z > 1) ? a.z : 1;
-  dim3 grid((a.nc + K2_X - 1) / K2_X, a.n_prog, Z);
+  dim3 grid((a.nc + K2_X - 1) / K2_X + 1, a.n_prog, Z);  // + the centre block
   k2_reduce<<<grid, dim3(K2_X, K2_SLICES), 0, s>>>(a);
   return cudaGetLastError();
 }

@@ -16,6 +16,8 @@
   h^2 times the loss curvature; the largest disagreement measured on a GB300
   was 3.8e-7 (X_0), the bound is 1e-5.
 """
+import time
+
 import numpy as np
 import pytest
 
@@ -195,8 +197,12 @@ def test_differentiable_workload_full_size(pkg):
     sim.close()
     idx = pkg.adjoint.escaper_set(pot0, vel0)
     t64 = lambda v: torch.tensor(v, dtype=torch.float64, device="cuda")
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
     with torch.no_grad():
         pT, vT, cT = pkg.adjoint.run(pos0, vel0, com0, host_params(t64(Mvir0), t64(rs0)), spec)
+    torch.cuda.synchronize()
+    t_fwd = time.perf_counter() - t0
     track = cuda64(workloads.reference_track(cT[:3].cpu().numpy(), cT[3:].cpu().numpy(), seed=50))
     assign = pkg.adjoint.nearest_track_point(cT[:3] + pT[idx, :3], track)
 
@@ -207,8 +213,13 @@ def test_differentiable_workload_full_size(pkg):
     Mv = t64(Mvir0).requires_grad_()
     rs = t64(rs0).requires_grad_()
     c0 = com0.clone().requires_grad_()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
     L = loss(Mv, rs, c0)
     L.backward()
+    torch.cuda.synchronize()
+    t_grad = time.perf_counter() - t0
+    print(f"differentiable run: forward {t_fwd:.2f} s, forward + backward (checkpointed) {t_grad:.2f} s")
     L = L.detach()
     grads = [float(Mv.grad), float(rs.grad)] + c0.grad.cpu().tolist()
     fd = []
