@@ -75,6 +75,7 @@ class SCF:
             offsets = [0, int(n)]
         self.config = config
         self.offsets = [int(o) for o in offsets]
+        self.b_per_prog = None if b_per_prog is None else [float(x) for x in b_per_prog]
         self.n_prog = len(self.offsets) - 1
         self.n = self.offsets[-1]
         self.nc = n_coef(config.nmax, config.lmax)
