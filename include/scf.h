@@ -169,6 +169,15 @@ int scf_step(scf_handle* h, void* pos, void* vel, void* acc, double* com, int ns
  *                     (7 x 8 output tiles per thread over 64-particle
  *                     tiles; SCF_MIXED only, its default).  Reading
  *                     SCF_OPT_K1_TILE gives 0 while variant 1 is in use.
+ *   SCF_OPT_K3_VARIANT 0 = the field kernel in the handle's precision (the
+ *                     default); 1 = (SCF_FP64 only) the field kernel in
+ *                     float-float arithmetic on the single-precision pipe:
+ *                     the same results to about 1e-13 relative, the
+ *                     per-particle set-up, tidal difference and kick in
+ *                     double; 128-thread blocks only (other
+ *                     SCF_OPT_K3_BLOCK values return SCF_ERR_UNSUPPORTED
+ *                     while it is selected).  The adjoint always uses the
+ *                     double kernel.  The autotuner keeps the variant.
  * Setting a tile or block size synchronises the stream and rewrites the block
  * maps in the workspace (sized in scf_init for every allowed value).
  * Errors: SCF_ERR_NULL_POINTER, SCF_ERR_INVALID_ARG (unknown option or value),
@@ -177,6 +186,7 @@ int scf_step(scf_handle* h, void* pos, void* vel, void* acc, double* com, int ns
 #define SCF_OPT_K1_TILE 2
 #define SCF_OPT_K3_BLOCK 3
 #define SCF_OPT_K1_VARIANT 4
+#define SCF_OPT_K3_VARIANT 5
 int scf_set_option(scf_handle* h, int option, int value);
 int scf_get_option(const scf_handle* h, int option, int* value);
 

@@ -45,6 +45,7 @@ SCF_OPT_GRAPHS = 1
 SCF_OPT_K1_TILE = 2
 SCF_OPT_K3_BLOCK = 3
 SCF_OPT_K1_VARIANT = 4
+SCF_OPT_K3_VARIANT = 5
 
 
 class ScfError(RuntimeError):

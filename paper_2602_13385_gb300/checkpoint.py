@@ -66,7 +66,7 @@ def resume(path: str, device=None):
     offsets = ck["offsets"]
     sim = SCF(ck["config"], offsets=offsets, b_per_prog=ck["b_per_prog"], device=device)
     if ck["tiles"]:
-        sim.set_tiles(**{k: ck["tiles"][k] for k in ("k1_tile", "k3_block")})
+        sim.set_tiles(**{k: ck["tiles"][k] for k in ("k1_tile", "k3_block", "k3_variant") if k in ck["tiles"]})
     mask = ck["state"].get("mask")
     if mask is not None:
         sim.set_mask(mask)

@@ -30,8 +30,11 @@ struct scf_handle {
   int64_t* d_blk1_begin = nullptr;
   int64_t* d_blk1_end = nullptr;
   int* d_prog_blk_off = nullptr;
-  // kernel 3
+  // kernel 3 (k3: the kernel of the forward modes; k3_native: the native
+  // kernel of the same shape, used by the adjoint's ADJ_J mode)
   ScfLaunchInfo k3{};
+  ScfLaunchInfo k3_native{};
+  bool k3_ff = false;  // double-precision handles: float-float kernel 3
   int k3_blocks = 0;
   int* d_blk3_prog = nullptr;
   int64_t* d_blk3_begin = nullptr;
@@ -90,8 +93,9 @@ int upload_tables_once(int device) {
   cudaError_t e1 = scf_upload_const_coeffs(t);
   cudaError_t e2 = scf_upload_const_forces(t);
   cudaError_t e3 = scf_upload_const_adjoint(t);
+  cudaError_t e4 = scf_upload_const_forces_ff(t);
   delete t;
-  if (e1 != cudaSuccess || e2 != cudaSuccess || e3 != cudaSuccess) return SCF_ERR_CUDA;
+  if (e1 != cudaSuccess || e2 != cudaSuccess || e3 != cudaSuccess || e4 != cudaSuccess) return SCF_ERR_CUDA;
   g_const_ready[device] = true;
   return SCF_OK;
 }
@@ -257,7 +261,10 @@ int run_prep(scf_handle* h, const double* A, const double* com) {
 int run_forces(scf_handle* h, const void* pos, void* vel, void* acc, const double* com, int mode) {
   if (h->k3_blocks == 0) return SCF_OK;
   K3Args a = k3_args(h, pos, vel, acc, com, mode);
-  return cuda_fail(timed(h, 2, [&] { return scf_k3_launch(h->cfg.precision, a, h->k3_blocks, h->k3, h->stream); }));
+  if (h->k3.variant == 2 && mode != SCF_MODE_ADJ_J)
+    return cuda_fail(timed(h, 2, [&] { return scf_k3_ff_launch(a, h->k3_blocks, h->k3, h->stream); }));
+  return cuda_fail(
+      timed(h, 2, [&] { return scf_k3_launch(h->cfg.precision, a, h->k3_blocks, h->k3_native, h->stream); }));
 }
 
 // Kernel 1 block map: contiguous ranges of whole tiles, one progenitor per
@@ -354,9 +361,15 @@ int use_k1(scf_handle* h, int tp) {
 
 // Selects kernel 3's block size: launch info, block map, upload.
 int use_k3(scf_handle* h, int tb) {
-  ScfLaunchInfo info{};
+  ScfLaunchInfo native{}, info{};
   int bps = 0;
-  if (scf_k3_prepare(h->cfg.precision, h->cfg.lmax, h->cfg.nmax, tb, &info, &bps) != cudaSuccess || bps < 1) {
+  if (scf_k3_prepare(h->cfg.precision, h->cfg.lmax, h->cfg.nmax, tb, &native, &bps) != cudaSuccess || bps < 1) {
+    cudaGetLastError();
+    return SCF_ERR_UNSUPPORTED;
+  }
+  info = native;
+  if (h->k3_ff && (scf_k3_ff_prepare(h->cfg.lmax, h->cfg.nmax, tb, &info, &bps) != cudaSuccess || bps < 1 ||
+                   info.tile != native.tile)) {
     cudaGetLastError();
     return SCF_ERR_UNSUPPORTED;
   }
@@ -367,6 +380,7 @@ int use_k3(scf_handle* h, int tb) {
             put(h->d_blk3_end, m.end.data(), sizeof(int64_t) * m.end.size());
   if (!ok) return SCF_ERR_CUDA;
   h->k3 = info;
+  h->k3_native = native;
   h->k3_blocks = (int)m.prog.size();
   drop_graph(h);
   return SCF_OK;
@@ -620,6 +634,16 @@ int scf_set_option(scf_handle* h, int option, int value) {
     if (cudaStreamSynchronize(h->stream) != cudaSuccess) return SCF_ERR_CUDA;
     return option == SCF_OPT_K1_TILE ? use_k1(h, value) : use_k3(h, value);
   }
+  if (option == SCF_OPT_K3_VARIANT) {
+    if (value != 0 && value != 1) return SCF_ERR_INVALID_ARG;
+    if (value == 1 && h->cfg.precision != SCF_FP64) return SCF_ERR_UNSUPPORTED;
+    if (cudaStreamSynchronize(h->stream) != cudaSuccess) return SCF_ERR_CUDA;
+    const bool old = h->k3_ff;
+    h->k3_ff = value == 1;
+    const int rc = use_k3(h, h->k3.threads);
+    if (rc != SCF_OK) h->k3_ff = old;
+    return rc;
+  }
   if (option == SCF_OPT_K1_VARIANT) {
     if (value != 0 && value != 1) return SCF_ERR_INVALID_ARG;
     if (cudaStreamSynchronize(h->stream) != cudaSuccess) return SCF_ERR_CUDA;
@@ -634,6 +658,7 @@ int scf_get_option(const scf_handle* h, int option, int* value) {
   else if (option == SCF_OPT_K1_TILE) *value = h->k1.variant == 1 ? 0 : h->k1.tile;
   else if (option == SCF_OPT_K1_VARIANT) *value = h->k1.variant;
   else if (option == SCF_OPT_K3_BLOCK) *value = h->k3.threads;
+  else if (option == SCF_OPT_K3_VARIANT) *value = h->k3_ff ? 1 : 0;
   else return SCF_ERR_INVALID_ARG;
   return SCF_OK;
 }
@@ -764,7 +789,7 @@ int scf_adjoint_level(scf_handle* h, const void* pos, const double* com, double 
   if (h->k3_blocks > 0) {
     K3Args a = k3_args(h, pos, nullptr, nullptr, nullptr, SCF_MODE_ADJ_J);
     a.adj = adj;
-    if (scf_k3_launch(SCF_FP64, a, h->k3_blocks, h->k3, h->stream) != cudaSuccess) return SCF_ERR_CUDA;
+    if (scf_k3_launch(SCF_FP64, a, h->k3_blocks, h->k3_native, h->stream) != cudaSuccess) return SCF_ERR_CUDA;
   }
   return SCF_OK;
 }

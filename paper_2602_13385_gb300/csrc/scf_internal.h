@@ -193,6 +193,11 @@ cudaError_t scf_k1_tiled_prepare(int lmax, int nmax, ScfLaunchInfo* info, int* b
 // longest block has the given number of particles.
 int scf_k1_windows(int64_t max_particles_per_block, const ScfLaunchInfo& info);
 cudaError_t scf_k3_prepare(int precision, int lmax, int nmax, int tb, ScfLaunchInfo* info, int* blocks_per_sm);
+// Float-float kernel 3 for double-precision handles (info->variant = 2; the
+// same threads, tile and block map as the double kernel; modes COEFFS and STEP).
+cudaError_t scf_k3_ff_prepare(int lmax, int nmax, int tb, ScfLaunchInfo* info, int* blocks_per_sm);
+cudaError_t scf_k3_ff_launch(const K3Args& a, int blocks, const ScfLaunchInfo& info, cudaStream_t s);
+cudaError_t scf_upload_const_forces_ff(const ScfConst* t);
 
 cudaError_t scf_k1_launch(int precision, const K1Args& a, int blocks, const ScfLaunchInfo& info, cudaStream_t s);
 cudaError_t scf_k2_launch(const K2Args& a, cudaStream_t s);

@@ -186,12 +186,17 @@ class SCF:
         """Current kernel shapes: coefficient-kernel tile (0 = the register-tiled
         kernel of mixed precision) and field-kernel block."""
         return {"k1_tile": _lib.scf_get_option(self._h, _lib.SCF_OPT_K1_TILE),
-                "k3_block": _lib.scf_get_option(self._h, _lib.SCF_OPT_K3_BLOCK)}
+                "k3_block": _lib.scf_get_option(self._h, _lib.SCF_OPT_K3_BLOCK),
+                "k3_variant": _lib.scf_get_option(self._h, _lib.SCF_OPT_K3_VARIANT)}
 
-    def set_tiles(self, k1_tile: int | None = None, k3_block: int | None = None):
+    def set_tiles(self, k1_tile: int | None = None, k3_block: int | None = None, k3_variant: int | None = None):
         """``k1_tile``: 64, 128 or 256 particles per tile of the one-thread-per-
         output coefficient kernel, or 0 for the register-tiled kernel (mixed
-        precision only); ``k3_block``: 64, 128 or 256 threads per field block."""
+        precision only); ``k3_block``: 64, 128 or 256 threads per field block;
+        ``k3_variant``: 1 for the float-float field kernel of double-precision
+        handles, 0 for the native one."""
+        if k3_variant is not None:
+            _lib.scf_set_option(self._h, _lib.SCF_OPT_K3_VARIANT, int(k3_variant))
         if k1_tile is not None:
             if int(k1_tile) == 0:
                 _lib.scf_set_option(self._h, _lib.SCF_OPT_K1_VARIANT, 1)

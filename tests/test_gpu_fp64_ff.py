@@ -1,0 +1,106 @@
+"""The float-float field kernel of double-precision handles
+(SCF_OPT_K3_VARIANT = 1) against the FP64 oracle and the native kernel.
+
+* Forces (with the host's tidal term, particles at the origin, on the z axis
+  and far outside) from the oracle's coefficients: within the 1e-10 bar of
+  the FP64 path, and within 1e-12 of the native double kernel.
+* Ten leapfrog steps with a host: the same states as the oracle's (1e-10).
+* The adjoint (which always runs the native kernel) gives the same result
+  whichever variant the handle's forward kernel uses.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import workloads
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+TOL = 1e-10
+
+
+@pytest.fixture(scope="module")
+def scf():
+    if not torch.cuda.is_available():
+        pytest.skip("needs a GPU")
+    import paper_2602_13385_gb300 as pkg
+    return pkg
+
+
+def dev(x):
+    return torch.tensor(np.ascontiguousarray(x), device="cuda", dtype=torch.float64)
+
+
+def acc_err(a, b):
+    na = np.linalg.norm(b[:, :3], axis=1)
+    floor = max(1e-6 * np.median(na), 1e-300)
+    return np.linalg.norm(a[:, :3] - b[:, :3], axis=1) / np.maximum(na, floor)
+
+
+def handle(scf, wl_or_cfg, n, variant):
+    sim = scf.SCF(wl_or_cfg, n=n)
+    sim.set_tiles(k3_block=128, k3_variant=variant)
+    assert sim.tiles()["k3_variant"] == variant
+    return sim
+
+
+@pytest.mark.parametrize("nmax,lmax", [(20, 8), (10, 6), (6, 12)])
+def test_ff_forces_match_oracle_and_native(scf, nmax, lmax):
+    wl = workloads.king_circular(n=4000, seed=81, nsteps=1)
+    pos = wl.pos.copy()
+    pos[0, :3] = 0.0
+    pos[1, :3] = [0.0, 0.0, 0.3]
+    pos[2, :3] = [0.0, 0.0, -0.2]
+    pos[3, :3] = [40.0, -30.0, 10.0]
+    A = oracle.coeffs(wl.pos, nmax, lmax, wl.b)
+    host = oracle.host_struct(wl.host)
+    ref = oracle.forces(pos, A, nmax, lmax, wl.b, com=wl.com, host=host)
+    cfg = scf.Config(nmax=nmax, lmax=lmax, b=wl.b, host=list(wl.host))
+    out = {}
+    for variant in (0, 1):
+        sim = handle(scf, cfg, len(pos), variant)
+        out[variant] = sim.forces(dev(pos), dev(A[None]), com=dev(wl.com[None])).cpu().numpy()
+        assert sim.status() == (0, 0)
+    e_or, e_nat = acc_err(out[1], ref), acc_err(out[1], out[0])
+    print(f"({nmax},{lmax}) float-float kernel 3: vs oracle max {e_or.max():.2e} median {np.median(e_or):.2e}; "
+          f"vs native max {e_nat.max():.2e}")
+    assert e_or.max() < TOL and e_nat.max() < 1e-12
+    assert np.max(np.abs(out[1][:, 3] - ref[:, 3]) / np.abs(ref[:, 3])) < TOL
+
+
+def test_ff_leapfrog_matches_oracle(scf):
+    wl = workloads.king_circular(n=3000, seed=82, nsteps=10)
+    host = oracle.host_struct(wl.host)
+    A = oracle.coeffs(wl.pos, wl.nmax, wl.lmax, wl.b)
+    a0 = oracle.forces(wl.pos, A, wl.nmax, wl.lmax, wl.b, com=wl.com, host=host)
+    rp, rv, ra, rc, _ = oracle.step(wl.pos, wl.vel, a0, wl.nmax, wl.lmax, wl.b, wl.dt, wl.nsteps, com=wl.com,
+                                    host=host)
+    cfg = scf.Config(nmax=wl.nmax, lmax=wl.lmax, b=wl.b, dt=wl.dt, host=list(wl.host))
+    sim = handle(scf, cfg, wl.n, 1)
+    p, v, c = dev(wl.pos), dev(wl.vel), dev(wl.com[None])
+    a = dev(a0)
+    sim.step(p, v, a, com=c, nsteps=wl.nsteps)
+    P, V = p.cpu().numpy(), v.cpu().numpy()
+    ex = np.abs(P[:, :3] - rp[:, :3]).max() / np.abs(rp[:, :3]).max()
+    ev = np.abs(V[:, :3] - rv[:, :3]).max() / np.abs(rv[:, :3]).max()
+    print(f"float-float 10 steps: position {ex:.2e}, velocity {ev:.2e}")
+    assert ex < TOL and ev < TOL
+    assert sim.status() == (0, 0)
+
+
+def test_adjoint_unaffected_by_the_variant(scf):
+    wl = workloads.king_circular(n=2000, seed=83, nsteps=1)
+    cfg = scf.Config(nmax=10, lmax=6, b=wl.b, dt=wl.dt, host=list(wl.host))
+    res = []
+    for variant in (0, 1):
+        sim = handle(scf, cfg, wl.n, variant)
+        rng = np.random.default_rng(5)
+        xb = dev(np.c_[rng.normal(size=(wl.n, 3)), np.zeros(wl.n)])
+        vb = dev(np.c_[rng.normal(size=(wl.n, 3)), np.zeros(wl.n)])
+        cb = torch.zeros((1, 6), dtype=torch.float64, device="cuda")
+        th = torch.zeros((1, 2 * len(wl.host)), dtype=torch.float64, device="cuda")
+        from paper_2602_13385_gb300 import _lib
+        _lib.scf_adjoint_level(sim._h, dev(wl.pos), dev(wl.com[None]), 0.005, 1, xb, vb, cb, th)
+        res.append((xb.cpu().numpy(), vb.cpu().numpy(), cb.cpu().numpy(), th.cpu().numpy()))
+    for a, b in zip(*res):
+        assert np.array_equal(a, b)
