@@ -62,6 +62,8 @@ def test_diagnostics_snapshot(scf, tmp_path):
     wl = workloads.king_circular(n=4000, seed=72, nsteps=1)
     vel = wl.vel.copy()
     vel[::40, :3] *= 3.0
+    wl.pos[::97, :3] *= 30.0           # some stars far out and unbound: outside r_b
+    vel[::97, :3] *= 5.0
     cfg = scf.Config(nmax=8, lmax=4, b=wl.b, dt=wl.dt, host=list(wl.host))
     sim = scf.SCF(cfg, n=wl.n)
     p, v, c = dev(wl.pos), dev(vel), dev(wl.com[None])
