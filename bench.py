@@ -55,7 +55,7 @@ WORKLOADS = {
     "king_circular_fp64ff": ("king_circular", "fp64"),
     "plummer_eccentric_fp64ff": ("plummer_eccentric", "fp64"),
 }
-K3_VARIANT = {"king_circular_fp64ff": 1, "plummer_eccentric_fp64ff": 1}
+FF_WORKLOADS = {"king_circular_fp64ff", "plummer_eccentric_fp64ff"}
 BUILDER_ARGS = {"paper_orbits": {"n_per": 200_000}}
 DEFAULT_WORKLOAD = "king_circular_fp64"
 
@@ -357,8 +357,8 @@ def main():
     v = torch.tensor(wl.vel, device=dev, dtype=dtype)
     c = torch.tensor(coms, device=dev, dtype=torch.float64)
     use_com = c if wl.host else None
-    if K3_VARIANT.get(args.workload):
-        sim.set_tiles(k3_block=128, k3_variant=K3_VARIANT[args.workload])
+    if args.workload in FF_WORKLOADS:
+        sim.set_tiles(k3_block=128, k3_variant=1, k1_variant=2)
     a = sim.forces(p, sim.coeffs(p), com=use_com)
     tuning = None
     if args.tiles:
@@ -456,7 +456,7 @@ def main():
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None,
-        "dtype": ("f64 (field kernel in float-float)" if K3_VARIANT.get(args.workload) else "f64")
+        "dtype": ("f64 (kernels 1 and 3 in float-float)" if args.workload in FF_WORKLOADS else "f64")
                  if precision == "fp64" else "f32+f64",
         "data": "synthetic (seeded sample, see config.workload)",
         "config": workload_config(wl, precision, args.workload),

@@ -167,8 +167,12 @@ int scf_step(scf_handle* h, void* pos, void* vel, void* acc, double* com, int ns
  *                     and SCF_OPT_K1_TILE particles per tile (the double-
  *                     precision default); 1 = the register-tiled kernel
  *                     (7 x 8 output tiles per thread over 64-particle
- *                     tiles; SCF_MIXED only, its default).  Reading
- *                     SCF_OPT_K1_TILE gives 0 while variant 1 is in use.
+ *                     tiles; SCF_MIXED only, its default); 2 = (SCF_FP64
+ *                     only) the one-thread-per-output kernel in float-float
+ *                     arithmetic on the single-precision pipe (128-particle
+ *                     tiles only; partial sums within about 1e-13 of the
+ *                     double kernel's).  Reading SCF_OPT_K1_TILE gives 0
+ *                     while variant 1 is in use.
  *   SCF_OPT_K3_VARIANT 0 = the field kernel in the handle's precision (the
  *                     default); 1 = (SCF_FP64 only) the field kernel in
  *                     float-float arithmetic on the single-precision pipe:

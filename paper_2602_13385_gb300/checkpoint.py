@@ -66,7 +66,10 @@ def resume(path: str, device=None):
     offsets = ck["offsets"]
     sim = SCF(ck["config"], offsets=offsets, b_per_prog=ck["b_per_prog"], device=device)
     if ck["tiles"]:
-        sim.set_tiles(**{k: ck["tiles"][k] for k in ("k1_tile", "k3_block", "k3_variant") if k in ck["tiles"]})
+        t = ck["tiles"]
+        sim.set_tiles(k3_block=t["k3_block"], k3_variant=t.get("k3_variant"), k1_variant=t.get("k1_variant"))
+        if t.get("k1_variant", 0) != 2:
+            sim.set_tiles(k1_tile=t["k1_tile"])
     mask = ck["state"].get("mask")
     if mask is not None:
         sim.set_mask(mask)

@@ -25,6 +25,7 @@ struct scf_handle {
   size_t cap_rows = 0;                 // partial rows of 2*NC 8-byte entries (largest candidate)
   // kernel 1 / 2
   ScfLaunchInfo k1{};
+  bool k1_ff = false;  // double-precision handles: float-float kernel 1
   int k1_blocks = 0;
   int* d_blk1_prog = nullptr;
   int64_t* d_blk1_begin = nullptr;
@@ -94,8 +95,10 @@ int upload_tables_once(int device) {
   cudaError_t e2 = scf_upload_const_forces(t);
   cudaError_t e3 = scf_upload_const_adjoint(t);
   cudaError_t e4 = scf_upload_const_forces_ff(t);
+  cudaError_t e5 = scf_upload_const_coeffs_ff(t);
   delete t;
-  if (e1 != cudaSuccess || e2 != cudaSuccess || e3 != cudaSuccess || e4 != cudaSuccess) return SCF_ERR_CUDA;
+  if (e1 != cudaSuccess || e2 != cudaSuccess || e3 != cudaSuccess || e4 != cudaSuccess || e5 != cudaSuccess)
+    return SCF_ERR_CUDA;
   g_const_ready[device] = true;
   return SCF_OK;
 }
@@ -232,8 +235,10 @@ int run_coeffs(scf_handle* h, void* pos, void* vel, const void* acc, const uint8
                int mode) {
   if (h->k1_blocks > 0) {
     K1Args a = k1_args(h, pos, vel, acc, mask, mode);
-    if (timed(h, 0, [&] { return scf_k1_launch(h->cfg.precision, a, h->k1_blocks, h->k1, h->stream); }) !=
-        cudaSuccess)
+    if (timed(h, 0, [&] {
+          return h->k1.variant == 2 ? scf_k1_ff_launch(a, h->k1_blocks, h->k1, h->stream)
+                                    : scf_k1_launch(h->cfg.precision, a, h->k1_blocks, h->k1, h->stream);
+        }) != cudaSuccess)
       return SCF_ERR_CUDA;
   }
   K2Args b = k2_args(h, A_out, com, mode);
@@ -317,8 +322,9 @@ bool put(void* dst, const void* src, size_t bytes) {
 
 // Kernel 1 launch shape: the simple kernel with a particle tile of 64, 128
 // or 256 (tp), or the register-tiled single-precision kernel (tp = 0).
-int k1_shape(const scf_config& cfg, int tp, ScfLaunchInfo* info, int* bps) {
+int k1_shape(const scf_config& cfg, int tp, bool ff, ScfLaunchInfo* info, int* bps) {
   cudaError_t e = tp == 0 ? scf_k1_tiled_prepare(cfg.lmax, cfg.nmax, info, bps)
+                  : ff    ? scf_k1_ff_prepare(cfg.lmax, cfg.nmax, tp, info, bps)
                           : scf_k1_prepare(cfg.precision, cfg.lmax, cfg.nmax, tp, info, bps);
   if (e != cudaSuccess || *bps < 1) {
     cudaGetLastError();
@@ -344,7 +350,7 @@ int use_k1(scf_handle* h, int tp) {
   if (tp == 0 && h->cfg.precision != SCF_MIXED) return SCF_ERR_UNSUPPORTED;
   ScfLaunchInfo info{};
   int bps = 0;
-  if (k1_shape(h->cfg, tp, &info, &bps) != SCF_OK) return SCF_ERR_UNSUPPORTED;
+  if (k1_shape(h->cfg, tp, h->k1_ff && tp != 0, &info, &bps) != SCF_OK) return SCF_ERR_UNSUPPORTED;
   Map1 m = make_map1(h->offsets, h->n_prog, info.tile, (int64_t)h->n_sm * bps);
   if (info.variant == 1) info.win = scf_k1_windows(longest_block(m), info);
   if (m.prog.size() > h->cap_blk1 || k1_rows(info, m.prog.size()) > h->cap_rows) return SCF_ERR_UNSUPPORTED;
@@ -434,11 +440,14 @@ int scf_init(const scf_config* cfg, int n_prog, const int64_t* offsets, const do
   h->offsets.assign(offsets, offsets + n_prog + 1);
 
   // Capacity of the block maps and partial rows: the largest any candidate shape can need.
-  for (int tp : {64, 128, 256, 0}) {
+  for (int cand = 0; cand < 5; ++cand) {
+    const int tp = cand < 3 ? 64 << cand : cand == 3 ? 0 : 128;  // the last: float-float, 128
+    const bool ff = cand == 4;
     if (tp == 0 && cfg->precision != SCF_MIXED) continue;
+    if (ff && cfg->precision != SCF_FP64) continue;
     ScfLaunchInfo info{};
     int bps = 0;
-    if (k1_shape(*cfg, tp, &info, &bps) != SCF_OK) continue;
+    if (k1_shape(*cfg, tp, ff, &info, &bps) != SCF_OK) continue;
     const Map1 m = make_map1(h->offsets, n_prog, info.tile, (int64_t)h->n_sm * bps);
     const size_t blocks = m.prog.size();
     if (info.variant == 1) info.win = scf_k1_windows(longest_block(m), info);
@@ -645,9 +654,14 @@ int scf_set_option(scf_handle* h, int option, int value) {
     return rc;
   }
   if (option == SCF_OPT_K1_VARIANT) {
-    if (value != 0 && value != 1) return SCF_ERR_INVALID_ARG;
+    if (value < 0 || value > 2) return SCF_ERR_INVALID_ARG;
+    if (value == 2 && h->cfg.precision != SCF_FP64) return SCF_ERR_UNSUPPORTED;
     if (cudaStreamSynchronize(h->stream) != cudaSuccess) return SCF_ERR_CUDA;
-    return use_k1(h, value == 1 ? 0 : 128);
+    const bool old = h->k1_ff;
+    h->k1_ff = value == 2;
+    const int rc = use_k1(h, value == 1 ? 0 : 128);
+    if (rc != SCF_OK) h->k1_ff = old;
+    return rc;
   }
   return SCF_ERR_INVALID_ARG;
 }

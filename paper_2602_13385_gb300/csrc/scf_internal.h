@@ -198,6 +198,11 @@ cudaError_t scf_k3_prepare(int precision, int lmax, int nmax, int tb, ScfLaunchI
 cudaError_t scf_k3_ff_prepare(int lmax, int nmax, int tb, ScfLaunchInfo* info, int* blocks_per_sm);
 cudaError_t scf_k3_ff_launch(const K3Args& a, int blocks, const ScfLaunchInfo& info, cudaStream_t s);
 cudaError_t scf_upload_const_forces_ff(const ScfConst* t);
+// Float-float kernel 1 for double-precision handles (info->variant = 2; 128-
+// particle tiles; double partial rows as the native kernel).
+cudaError_t scf_k1_ff_prepare(int lmax, int nmax, int tp, ScfLaunchInfo* info, int* blocks_per_sm);
+cudaError_t scf_k1_ff_launch(const K1Args& a, int blocks, const ScfLaunchInfo& info, cudaStream_t s);
+cudaError_t scf_upload_const_coeffs_ff(const ScfConst* t);
 
 cudaError_t scf_k1_launch(int precision, const K1Args& a, int blocks, const ScfLaunchInfo& info, cudaStream_t s);
 cudaError_t scf_k2_launch(const K2Args& a, cudaStream_t s);

@@ -187,16 +187,23 @@ class SCF:
         kernel of mixed precision) and field-kernel block."""
         return {"k1_tile": _lib.scf_get_option(self._h, _lib.SCF_OPT_K1_TILE),
                 "k3_block": _lib.scf_get_option(self._h, _lib.SCF_OPT_K3_BLOCK),
+                "k1_variant": _lib.scf_get_option(self._h, _lib.SCF_OPT_K1_VARIANT),
                 "k3_variant": _lib.scf_get_option(self._h, _lib.SCF_OPT_K3_VARIANT)}
 
-    def set_tiles(self, k1_tile: int | None = None, k3_block: int | None = None, k3_variant: int | None = None):
+    def set_tiles(self, k1_tile: int | None = None, k3_block: int | None = None, k3_variant: int | None = None,
+                  k1_variant: int | None = None):
         """``k1_tile``: 64, 128 or 256 particles per tile of the one-thread-per-
         output coefficient kernel, or 0 for the register-tiled kernel (mixed
         precision only); ``k3_block``: 64, 128 or 256 threads per field block;
-        ``k3_variant``: 1 for the float-float field kernel of double-precision
-        handles, 0 for the native one."""
+        ``k1_variant`` 2 / ``k3_variant`` 1: the float-float coefficient /
+        field kernel of double-precision handles (128-wide only), 0 for the
+        native ones."""
         if k3_variant is not None:
             _lib.scf_set_option(self._h, _lib.SCF_OPT_K3_VARIANT, int(k3_variant))
+        if k1_variant is not None:
+            _lib.scf_set_option(self._h, _lib.SCF_OPT_K1_VARIANT, int(k1_variant))
+            if int(k1_variant) != 0:
+                k1_tile = None
         if k1_tile is not None:
             if int(k1_tile) == 0:
                 _lib.scf_set_option(self._h, _lib.SCF_OPT_K1_VARIANT, 1)

@@ -1,10 +1,15 @@
-"""The float-float field kernel of double-precision handles
-(SCF_OPT_K3_VARIANT = 1) against the FP64 oracle and the native kernel.
+"""The float-float kernels of double-precision handles (field kernel:
+SCF_OPT_K3_VARIANT = 1; coefficient kernel: SCF_OPT_K1_VARIANT = 2) against
+the FP64 oracle and the native kernels.
+
+* Coefficients (several shapes, a mask, particles at the origin and on the
+  axis): within the 1e-10 bar of the FP64 path and 1e-12 of the native kernel.
 
 * Forces (with the host's tidal term, particles at the origin, on the z axis
   and far outside) from the oracle's coefficients: within the 1e-10 bar of
   the FP64 path, and within 1e-12 of the native double kernel.
-* Ten leapfrog steps with a host: the same states as the oracle's (1e-10).
+* Ten leapfrog steps with a host, both kernels in float-float: the same
+  states as the oracle's (1e-10).
 * The adjoint (which always runs the native kernel) gives the same result
   whichever variant the handle's forward kernel uses.
 """
@@ -68,6 +73,30 @@ def test_ff_forces_match_oracle_and_native(scf, nmax, lmax):
     assert np.max(np.abs(out[1][:, 3] - ref[:, 3]) / np.abs(ref[:, 3])) < TOL
 
 
+@pytest.mark.parametrize("nmax,lmax", [(20, 8), (10, 6), (6, 12), (3, 1)])
+def test_ff_coefficients_match_oracle_and_native(scf, nmax, lmax):
+    pos, _ = workloads.plummer(2500, seed=84)
+    pos[0, :3] = 0.0
+    pos[1, :3] = [0.0, 0.0, 0.4]
+    pos[2, :3] = [30.0, 20.0, -10.0]
+    mask = (np.arange(len(pos)) % 7 != 3).astype(np.uint8)
+    b = 0.3
+    ref = oracle.coeffs(pos, nmax, lmax, b, mask=mask)
+    cfg = scf.Config(nmax=nmax, lmax=lmax, b=b)
+    out = {}
+    for variant in (0, 2):
+        sim = scf.SCF(cfg, n=len(pos))
+        sim.set_tiles(k1_tile=128)
+        sim.set_tiles(k1_variant=variant)
+        assert sim.tiles()["k1_variant"] == variant
+        out[variant] = sim.coeffs(dev(pos), mask=torch.tensor(mask, device="cuda")).cpu().numpy()[0]
+        assert sim.status() == (0, 0)
+    scale = np.abs(ref).max()
+    e_or, e_nat = np.abs(out[2] - ref).max() / scale, np.abs(out[2] - out[0]).max() / scale
+    print(f"({nmax},{lmax}) float-float kernel 1: vs oracle {e_or:.2e}, vs native {e_nat:.2e}")
+    assert e_or < TOL and e_nat < 1e-12
+
+
 def test_ff_leapfrog_matches_oracle(scf):
     wl = workloads.king_circular(n=3000, seed=82, nsteps=10)
     host = oracle.host_struct(wl.host)
@@ -77,6 +106,8 @@ def test_ff_leapfrog_matches_oracle(scf):
                                     host=host)
     cfg = scf.Config(nmax=wl.nmax, lmax=wl.lmax, b=wl.b, dt=wl.dt, host=list(wl.host))
     sim = handle(scf, cfg, wl.n, 1)
+    sim.set_tiles(k1_variant=2)
+    assert sim.tiles()["k1_variant"] == 2
     p, v, c = dev(wl.pos), dev(wl.vel), dev(wl.com[None])
     a = dev(a0)
     sim.step(p, v, a, com=c, nsteps=wl.nsteps)
