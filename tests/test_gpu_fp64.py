@@ -236,7 +236,8 @@ def test_every_tile_and_block_size_matches_oracle(scf, precision):
     tol_a = TOL if precision == "fp64" else 1e-5
     for size in (64, 128, 256):
         sim.set_tiles(k1_tile=size, k3_block=size)
-        assert sim.tiles() == {"k1_tile": size, "k3_block": size}
+        t = sim.tiles()
+        assert (t["k1_tile"], t["k3_block"]) == (size, size)
         A = sim.coeffs(p).cpu().numpy()[0]
         acc = sim.forces(p, dev(A_ref[None]), com=c).cpu().double().numpy()
         assert coef_err(A, A_ref) < tol_A
