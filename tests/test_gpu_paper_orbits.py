@@ -111,3 +111,45 @@ def test_batched_evolve_matches_single_clusters(scf):
         assert np.abs(v1.cpu().numpy() - V[s]).max() < 1e-9 * np.abs(V[s, :3]).max(), i
         assert np.array_equal(c1.cpu().numpy()[0], c.cpu().numpy()[i]), i
     assert sim.status() == (0, 0)
+
+
+def test_paper_orbit_streams_mixed_against_fp64(scf):
+    """400 Myr (20000 steps) of the ten progenitors (2e4 stars each) with the
+    escape physics, in mixed and in double precision: each stream's Sec. 3.3
+    statistics agree within 1% (R28) on the double run's bins of >= 500
+    stars, wherever a tail has that many."""
+    from paper_2602_13385_gb300 import streams
+    wl = workloads.paper_orbits(n_per=20_000, nsteps=20_000)
+    out = {}
+    for prec in ("fp64", "mixed"):
+        dtype = torch.float64 if prec == "fp64" else torch.float32
+        cfg = scf.Config(nmax=wl.nmax, lmax=wl.lmax, b=wl.b, dt=wl.dt, host=list(wl.host), precision=prec)
+        sim = scf.SCF(cfg, offsets=wl.offsets, b_per_prog=wl.b_per_prog)
+        if prec == "fp64":
+            sim.set_tiles(k3_block=128, k3_variant=1, k1_variant=2)
+        p, v, c = dev(wl.pos, dtype), dev(wl.vel, dtype), dev(wl.com_per_prog)
+        a = sim.forces(p, sim.coeffs(p), com=c)
+        _, _, _, n_int = sim.evolve(p, v, a, c, nsteps=wl.nsteps)
+        b, _, st, _ = sim.bound(p, v)
+        cc = c.cpu().numpy()
+        out[prec] = (p.double().cpu().numpy(), v.double().cpu().numpy(), cc, b.cpu().numpy() == 0, n_int)
+        assert sim.status() == (0, 0)
+    f, m = out["fp64"], out["mixed"]
+    assert f[4] == m[4] and np.array_equal(f[2], m[2])
+    compared = 0
+    for i in range(10):
+        s = slice(wl.offsets[i], wl.offsets[i + 1])
+        X = lambda o: o[0][s, :3] + o[2][i, :3]
+        V = lambda o: o[1][s, :3] + o[2][i, 3:]
+        uf, um = f[3][s], m[3][s]
+        line = f"orbit {i}: {uf.sum()} unbound (mixed {um.sum()})"
+        if uf.sum() >= 1000:
+            a = streams.stream_stats(X(f), V(f), f[2][i, :3], f[2][i, 3:], uf, min_count=500)
+            edges = np.concatenate([a["lo"], a["hi"][-1:]])
+            b = streams.stream_stats(X(m), V(m), m[2][i, :3], m[2][i, 3:], um, edges=edges)
+            d, ok = streams.compare(a, b, tol=0.01)
+            line += f", {len(edges) - 1} bins, max differences " + ", ".join(f"{k} {v:.1e}" for k, v in d.items())
+            assert ok, (i, d)
+            compared += 1
+        print(line)
+    assert compared >= 1
