@@ -370,18 +370,22 @@ def tidal_scales(host, R, M_c, eta=1.0 / 400.0, G=1.0):
 
 
 def evolve(pos, vel, acc, nmax, lmax, b, dt, nsteps, G=1.0, com=None, host=None, kin=0.5, frac=0.999,
-           eta=1.0 / 400.0, max_steps=1000):
+           eta=1.0 / 400.0, max_steps=1000, retune_every=0):
     """Leapfrog with the escape physics of Sec. 2.2.  At the start of every
     integration timestep: the boundedness test and the coefficient set
-    r <= r_x (:func:`boundedness`), the field of that set at the current
-    positions, and the length of the integration timestep, dt_int of
-    :func:`tidal_scales` at the current centre with the bound mass as M_c,
-    taken as ``clamp(floor(dt_int / dt), 1, max_steps)`` leapfrog steps
-    (``max_steps`` without a host; fewer at the end).
+    r <= r_x (:func:`boundedness`); at every ``retune_every``-th integration
+    timestep (the first included; 0 = never) a complete refresh, which with
+    alpha = 1 retunes the basis scale b to the Hernquist scale of the bound
+    stars' energy-based half-mass radius, b = r_50 / (1 + sqrt 2); the field
+    of the coefficient set at the current positions; and the length of the
+    integration timestep, dt_int of :func:`tidal_scales` at the current
+    centre with the bound mass as M_c, taken as
+    ``clamp(floor(dt_int / dt), 1, max_steps)`` leapfrog steps (``max_steps``
+    without a host; fewer at the end).
 
-    Returns ``(pos, vel, acc, com, bound, mask, stats, n_int)`` with ``bound``,
-    ``mask`` and ``stats = (n_bound, M_bound, r_x, set size)`` as of the start
-    of the last integration timestep."""
+    Returns ``(pos, vel, acc, com, bound, mask, stats, n_int, b)`` with
+    ``bound``, ``mask`` and ``stats = (n_bound, M_bound, r_x, set size)`` as
+    of the start of the last integration timestep and ``b`` the scale in use."""
     pos = _f64(pos).copy()
     vel = _f64(vel).copy()
     com = np.zeros(6) if com is None else _f64(com).copy()
@@ -389,9 +393,13 @@ def evolve(pos, vel, acc, nmax, lmax, b, dt, nsteps, G=1.0, com=None, host=None,
     done, n_int = 0, 0
     bound = mask = None
     stats = np.zeros(4)
+    b = float(b)
     while done < nsteps:
         E, bound, rx2, mask, Mb = boundedness(pos, vel, G, kin, frac)
         stats = np.array([bound.sum(), Mb, np.sqrt(rx2), mask.sum()], dtype=np.float64)
+        if retune_every > 0 and n_int % retune_every == 0 and bound.any():
+            r50 = np.sqrt(boundedness(pos, vel, G, kin, 0.5)[2])
+            b = r50 / (1.0 + np.sqrt(2.0))
         A = coeffs(pos, nmax, lmax, b, mask=mask)
         acc = forces(pos, A, nmax, lmax, b, G, com=com if has_host else None, host=host if has_host else None)
         k = max_steps
@@ -405,7 +413,7 @@ def evolve(pos, vel, acc, nmax, lmax, b, dt, nsteps, G=1.0, com=None, host=None,
                                      host=host if has_host else None, mask=mask)
         done += k
         n_int += 1
-    return pos, vel, acc, com, bound, mask, stats, n_int
+    return pos, vel, acc, com, bound, mask, stats, n_int, b
 
 
 def power_l(A, nmax, lmax, b):

@@ -14,6 +14,8 @@
   dt_int = sqrt(eta) sqrt(R^3 / GM) (Sec. 2.2, Sec. 3.1 footnote); the trace
   of the tidal tensor is -4 pi G rho_host (Poisson's equation) for each host
   component.
+* The complete refresh: on a Hernquist sphere of scale a the retuned basis
+  scale is a (r_50 = (1 + sqrt 2) a), and b changes only at refreshes.
 * The evolve schedule (Sec. 2.2): with every star bound and inside r_x it is
   the plain leapfrog bit for bit; an unbound star beyond r_x leaves the
   cluster's evolution bit for bit unchanged (and changes it when left in the
@@ -152,8 +154,8 @@ def test_evolve_without_escapers_is_the_plain_leapfrog():
     assert oracle.boundedness(pos, vel, frac=1.0)[3].all()
     acc = oracle.forces(pos, oracle.coeffs(pos, nmax, lmax, b), nmax, lmax, b)
     p1, v1, a1, _, _ = oracle.step(pos, vel, acc, nmax, lmax, b, dt, 7)
-    p2, v2, a2, _, bound, mask, stats, n_int = oracle.evolve(pos, vel, acc, nmax, lmax, b, dt, 7, frac=1.0,
-                                                             max_steps=3)
+    p2, v2, a2, _, bound, mask, stats, n_int, _ = oracle.evolve(pos, vel, acc, nmax, lmax, b, dt, 7, frac=1.0,
+                                                                max_steps=3)
     assert n_int == 3 and mask.all() and stats[3] == 256
     assert np.array_equal(p1, p2) and np.array_equal(v1, v2) and np.array_equal(a1, a2)
 
@@ -195,3 +197,19 @@ def test_integration_timestep_count_on_a_circular_orbit():
     assert out[7] == 5
     ts = oracle.tidal_scales(host, out[3][:3], np.array([1.0]), eta)[0]
     assert 7.0 < ts[15] / dt < 8.0
+
+
+def test_complete_refresh_retunes_b_to_the_hernquist_scale():
+    # a Hernquist sphere of scale a has r_50 = (1 + sqrt 2) a, so the retuned
+    # b is the sample's scale (to sampling noise); with no retuning b stays
+    a = 0.7
+    pos = workloads.hernquist_positions(20000, a, seed=18, rmax_over_b=200.0)
+    vel = np.zeros_like(pos)                       # every star bound
+    acc = np.zeros_like(pos)
+    out = oracle.evolve(pos, vel, acc, 2, 1, 0.3, 1e-4, 1, max_steps=1, retune_every=5)
+    assert abs(out[8] - a) < 0.03 * a, out[8]
+    assert oracle.evolve(pos, vel, acc, 2, 1, 0.3, 1e-4, 1, max_steps=1)[8] == 0.3
+    # a step of 1e-4 barely moves the stars, so retuning at integration
+    # timesteps 0 and 2 of 3 gives the same scale as retuning once
+    out3 = oracle.evolve(pos, vel, acc, 2, 1, 0.3, 1e-4, 3, max_steps=1, retune_every=2)
+    assert out3[7] == 3 and abs(out3[8] - out[8]) < 1e-6 * a
