@@ -315,17 +315,22 @@ int scf_tidal(scf_handle* h, const double* com, const double* M_c, double eta, d
 int scf_set_mask(scf_handle* h, const uint8_t* mask);
 
 typedef struct scf_escape_params {
-  double kin;     /* kinetic factor of the boundedness test (0.5, or 1 as printed) */
-  double frac;    /* the coefficient set is r <= r_x of this fraction (0.999) */
-  double eta;     /* integration-timestep parameter (1/400) */
-  int max_steps;  /* most leapfrog steps per integration timestep (>= 1) */
+  double kin;        /* kinetic factor of the boundedness test (0.5, or 1 as printed) */
+  double frac;       /* the coefficient set is r <= r_x of this fraction (0.999) */
+  double eta;        /* integration-timestep parameter (1/400) */
+  int max_steps;     /* most leapfrog steps per integration timestep (>= 1) */
+  int retune_every;  /* complete refresh every this many integration timesteps, the
+                        first included (the paper: 5); 0 = never.  With alpha = 1 it
+                        sets each progenitor's b to r_50 / (1 + sqrt 2), r_50 the
+                        energy-based Lagrange radius of half the bound stars */
 } scf_escape_params;
 
 /* nsteps leapfrog steps with the escape physics of Sec. 2.2.  At the start of
  * every integration timestep: scf_bound (bound flags, the mask r <= r_x and
  * stats, into the caller's buffers), the mask becomes the step's coefficient
- * set (scf_set_mask), acc is recomputed at the current positions from that
- * set, and the next integration timestep is the smallest dt_int of scf_tidal
+ * set (scf_set_mask), at a complete refresh (retune_every) each progenitor's
+ * b is retuned (scf_get_scales reads it), acc is recomputed at the current
+ * positions from that set, and the next integration timestep is the smallest dt_int of scf_tidal
  * at the current centres with M_c = the bound mass; it runs
  * clamp(floor(dt_int / dt), 1, max_steps) steps of scf_step (fewer at the
  * end; max_steps without host components).  Reads dt_int back once per
@@ -337,6 +342,12 @@ typedef struct scf_escape_params {
  * parameter or dt <= 0. */
 int scf_evolve(scf_handle* h, void* pos, void* vel, void* acc, double* com, int nsteps, const scf_escape_params* ep,
                uint8_t* bound, uint8_t* mask, double* stats, int* n_refresh);
+
+/* Copies the basis scale b of every progenitor (device [n_prog] doubles, on
+ * the handle's stream) into b_out: the value given to scf_init, or the last
+ * one a complete refresh of scf_evolve set.
+ * Errors: SCF_ERR_NULL_POINTER, SCF_ERR_CUDA. */
+int scf_get_scales(scf_handle* h, double* b_out);
 
 /* Copies (device to device, on the handle's stream) the coefficients used by
  * the last force evaluation of scf_step into A_out ([n_prog][2*NC] doubles). */

@@ -33,7 +33,7 @@ def save(path: str, sim, state: dict, step: int = 0, extra: dict | None = None) 
         "config": dataclasses.asdict(sim.config),
         "step": int(step),
         "offsets": list(sim.offsets),
-        "b_per_prog": sim.b_per_prog,
+        "b_per_prog": [float(x) for x in sim.scales().cpu()],  # as retuned by complete refreshes
         "tiles": sim.tiles(),
         "state": {k: v.detach().cpu() for k, v in state.items() if v is not None},
         "extra": extra or {},

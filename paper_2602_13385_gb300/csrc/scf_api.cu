@@ -64,6 +64,7 @@ struct scf_handle {
   double* d_bpart = nullptr;             // [bound_split][n_total]
   unsigned long long* d_key = nullptr;   // [n_total]
   double* d_tid = nullptr;               // [n_prog][16]
+  double* d_half = nullptr;              // [n_prog][4] selection at frac 1/2 (complete refresh)
   int bound_split = 1;
   int64_t bound_chunks = 0;              // pair-kernel i-blocks of the largest progenitor
   const uint8_t* step_mask = nullptr;    // coefficient set of scf_step (scf_set_mask)
@@ -497,6 +498,7 @@ int scf_init(const scf_config* cfg, int n_prog, const int64_t* offsets, const do
   const size_t o_bpart = take(sizeof(double) * (size_t)h->bound_split * (size_t)h->n_total);
   const size_t o_key = take(sizeof(unsigned long long) * (size_t)h->n_total);
   const size_t o_tid = take(sizeof(double) * 16 * (size_t)n_prog);
+  const size_t o_half = take(sizeof(double) * 4 * (size_t)n_prog);
   const size_t o_k2z = take(sizeof(double) * kK2MaxChunks * 2 * (size_t)h->nc * n_prog);
   const size_t o_k2c = take(sizeof(unsigned) * (size_t)scf_k2_groups(h->nc) * n_prog);
   if (cudaMalloc(&h->d_base, off) != cudaSuccess) {
@@ -525,6 +527,7 @@ int scf_init(const scf_config* cfg, int n_prog, const int64_t* offsets, const do
   h->d_bpart = reinterpret_cast<double*>(base + o_bpart);
   h->d_key = reinterpret_cast<unsigned long long*>(base + o_key);
   h->d_tid = reinterpret_cast<double*>(base + o_tid);
+  h->d_half = reinterpret_cast<double*>(base + o_half);
   h->d_k2z = reinterpret_cast<double*>(base + o_k2z);
   h->d_k2cnt = reinterpret_cast<unsigned*>(base + o_k2c);
 
@@ -899,7 +902,8 @@ int scf_evolve(scf_handle* h, void* pos, void* vel, void* acc, double* com, int 
   if (!aligned16(pos) || !aligned16(vel) || !aligned16(acc)) return SCF_ERR_MISALIGNED;
   if (nsteps < 0 || ep->max_steps < 1 || !(ep->eta > 0.0) || !std::isfinite(ep->eta) || !(h->cfg.dt > 0.0))
     return SCF_ERR_INVALID_ARG;
-  if (!(ep->kin > 0.0) || !std::isfinite(ep->kin) || !(ep->frac > 0.0 && ep->frac <= 1.0)) return SCF_ERR_INVALID_ARG;
+  if (!(ep->kin > 0.0) || !std::isfinite(ep->kin) || !(ep->frac > 0.0 && ep->frac <= 1.0) || ep->retune_every < 0)
+    return SCF_ERR_INVALID_ARG;
   int rc = scf_set_mask(h, mask);
   if (rc != SCF_OK) return rc;
   std::vector<double> tid(16 * (size_t)h->n_prog);
@@ -908,6 +912,23 @@ int scf_evolve(scf_handle* h, void* pos, void* vel, void* acc, double* com, int 
     // boundedness and the coefficient set r <= r_x
     rc = scf_bound(h, pos, vel, ep->kin, ep->frac, nullptr, bound, mask, stats);
     if (rc != SCF_OK) return rc;
+    if (ep->retune_every > 0 && refreshes % ep->retune_every == 0) {
+      // complete refresh (alpha = 1): b from the bound stars' half-mass radius
+      BoundArgs a{};
+      a.pos = pos;
+      a.prog_off = h->d_off;
+      a.n_prog = h->n_prog;
+      a.n_total = h->n_total;
+      a.f32 = h->cfg.precision == SCF_MIXED;
+      a.frac = 0.5;
+      a.key = h->d_key;
+      a.bound = bound;
+      a.mask = nullptr;
+      a.stats = h->d_half;
+      if (cuda_fail(scf_select_launch(a, h->stream)) != SCF_OK ||
+          cuda_fail(scf_retune_b_launch(h->d_half, h->d_b, h->n_prog, h->stream)) != SCF_OK)
+        return SCF_ERR_CUDA;
+    }
     // the field of the new set at the current positions (the next opening kick uses it)
     rc = run_coeffs(h, pos, nullptr, nullptr, mask, h->d_A, nullptr, SCF_MODE_COEFFS);
     if (rc == SCF_OK) rc = run_prep(h, h->d_A, com);
@@ -935,6 +956,12 @@ int scf_evolve(scf_handle* h, void* pos, void* vel, void* acc, double* com, int 
   }
   if (n_refresh) *n_refresh = refreshes;
   return SCF_OK;
+}
+
+int scf_get_scales(scf_handle* h, double* b_out) {
+  if (!h || !b_out) return SCF_ERR_NULL_POINTER;
+  return cuda_fail(
+      cudaMemcpyAsync(b_out, h->d_b, sizeof(double) * h->n_prog, cudaMemcpyDeviceToDevice, h->stream));
 }
 
 int scf_last_coeffs(scf_handle* h, double* A_out) {

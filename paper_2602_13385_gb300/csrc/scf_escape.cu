@@ -458,6 +458,29 @@ cudaError_t scf_bound_launch(const BoundArgs& a, int64_t max_chunks, cudaStream_
   return cudaGetLastError();
 }
 
+cudaError_t scf_select_launch(const BoundArgs& a, cudaStream_t s) {
+  if (a.f32) k_select<float4><<<a.n_prog, kSelectThreads, 0, s>>>(a);
+  else k_select<ScfD4><<<a.n_prog, kSelectThreads, 0, s>>>(a);
+  return cudaGetLastError();
+}
+
+namespace {
+// Complete refresh with alpha = 1: b = r_50 / (1 + sqrt 2), the Hernquist
+// scale of the bound stars' energy-based half-mass radius (stats from a
+// selection at frac = 0.5); unchanged for a progenitor with nothing bound.
+__global__ void k_retune_b(const double* stats, double* b_prog, int n_prog) {
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= n_prog) return;
+  const double* st = stats + 4 * (size_t)p;
+  if (st[0] > 0.0 && st[2] > 0.0) b_prog[p] = st[2] / (1.0 + 1.4142135623730950488);
+}
+}  // namespace
+
+cudaError_t scf_retune_b_launch(const double* stats, double* b_prog, int n_prog, cudaStream_t s) {
+  k_retune_b<<<(n_prog + 127) / 128, 128, 0, s>>>(stats, b_prog, n_prog);
+  return cudaGetLastError();
+}
+
 cudaError_t scf_tidal_launch(const TidalArgs& a, cudaStream_t s) {
   k_tidal<<<(a.n_prog + 127) / 128, 128, 0, s>>>(a);
   return cudaGetLastError();

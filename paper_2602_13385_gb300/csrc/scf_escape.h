@@ -47,3 +47,8 @@ int64_t scf_bound_chunk(int f32);
 // max_chunks: i-blocks of the largest progenitor.
 cudaError_t scf_bound_launch(const BoundArgs& a, int64_t max_chunks, cudaStream_t s);
 cudaError_t scf_tidal_launch(const TidalArgs& a, cudaStream_t s);
+// The selection alone (bound flags and radius keys from a previous
+// scf_bound_launch; mask may be null).
+cudaError_t scf_select_launch(const BoundArgs& a, cudaStream_t s);
+// b_prog[p] = r_x / (1 + sqrt 2) from the stats of a selection at frac = 0.5.
+cudaError_t scf_retune_b_launch(const double* stats, double* b_prog, int n_prog, cudaStream_t s);

@@ -156,9 +156,10 @@ class SCF:
         _lib.scf_set_mask(self._h, mask)
 
     def evolve(self, pos, vel, acc, com=None, nsteps: int = 1, kin: float = 0.5, frac: float = 0.999,
-               eta: float = 1.0 / 400.0, max_steps: int = 1000):
+               eta: float = 1.0 / 400.0, max_steps: int = 1000, retune_every: int = 0):
         """``nsteps`` leapfrog steps with boundedness, the r <= r_x coefficient
-        set and the tidal integration timestep (scf_evolve).  Returns
+        set, the tidal integration timestep and, every ``retune_every``
+        integration timesteps, a complete refresh of b (scf_evolve).  Returns
         ``(bound, mask, stats, n_int)`` as of the last integration timestep."""
         for t, nm in ((pos, "pos"), (vel, "vel"), (acc, "acc")):
             self._check_particles(t, nm)
@@ -168,8 +169,15 @@ class SCF:
                                  torch.empty((self.n_prog, 4), dtype=torch.float64, device=self.device))
         b, m, st = self._evolve_bufs
         self._mask_ref = m
-        n_int = _lib.scf_evolve(self._h, pos, vel, acc, com, nsteps, kin, frac, eta, max_steps, b, m, st)
+        n_int = _lib.scf_evolve(self._h, pos, vel, acc, com, nsteps, kin, frac, eta, max_steps, b, m, st,
+                                retune_every)
         return b, m, st, n_int
+
+    def scales(self):
+        """(n_prog,) float64: the basis scale b of every progenitor."""
+        out = torch.empty(self.n_prog, dtype=torch.float64, device=self.device)
+        _lib.scf_get_scales(self._h, out)
+        return out
 
     def last_coeffs(self, out: torch.Tensor | None = None):
         out = self.new_coeffs() if out is None else out

@@ -94,5 +94,6 @@ def test_null_handle_is_rejected(lib):
     assert lib.scf_bound(None, None, None, 0.5, 0.999, None, None, None, None) == -2
     assert lib.scf_tidal(None, None, None, 0.0025, None) == -2
     assert lib.scf_set_mask(None, None) == -2
+    assert lib.scf_get_scales(None, None) == -2
     assert lib.scf_evolve(None, None, None, None, None, 1, None, None, None, None, None) == -2
     assert lib.scf_free(None) == 0

@@ -322,3 +322,27 @@ def test_stream_statistics_mixed_against_fp64(stream_runs):
     n_bins, d, ok = results[500]
     assert n_bins >= 8 and ok, d
     assert results[100][0] >= 15
+
+
+def test_evolve_with_complete_refresh_matches_oracle(scf):
+    """Complete refreshes (retune_every = 2): b retuned to r_50 / (1 + sqrt 2)
+    at integration timesteps 0, 2, 4 as the oracle's schedule does."""
+    dtype, pos, vel, b, nmax, lmax, dt, eta, comps, com, nsteps, max_steps, n_int = _evolve_case(scf, "fp64",
+                                                                                               "galaxy")
+    host = oracle.host_struct(comps)
+    acc0 = oracle.forces(pos, oracle.coeffs(pos, nmax, lmax, b), nmax, lmax, b, com=com, host=host)
+    ref = oracle.evolve(pos, vel, acc0, nmax, lmax, b, dt, nsteps, com=com, host=host, eta=eta, max_steps=max_steps,
+                        retune_every=2)
+    assert ref[7] == n_int and ref[8] != b
+    sim = scf.SCF(scf.Config(nmax=nmax, lmax=lmax, b=b, dt=dt, host=comps), n=pos.shape[0])
+    p, v, a, c = dev(pos), dev(vel), dev(acc0), dev(com[None])
+    bnd, m, st, n = sim.evolve(p, v, a, c, nsteps=nsteps, eta=eta, max_steps=max_steps, retune_every=2)
+    assert n == n_int
+    b_gpu = sim.scales().cpu().numpy()[0]
+    print(f"retuned b: GPU {b_gpu:.15g}, oracle {ref[8]:.15g} (initial {b:.6g})")
+    assert abs(b_gpu - ref[8]) <= 1e-14 * ref[8]
+    assert np.array_equal(bnd.cpu().numpy().astype(bool), ref[4])
+    scale = np.max(np.abs(ref[0][:, :3]))
+    assert np.max(np.abs(p.cpu().numpy() - ref[0])) < 1e-10 * scale
+    assert np.max(np.abs(v.cpu().numpy() - ref[1])) < 1e-10 * np.max(np.abs(ref[1][:, :3]))
+    assert sim.status() == (0, 0)
