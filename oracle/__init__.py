@@ -5,7 +5,8 @@ Only the test suite, ``__graft_entry__.smoke()`` and the CPU-baseline leg of
 definition of what the CUDA path computes, written from the paper:
 
 * Eq. 1-3 (basis expansion, coefficients as a mass-weighted particle sum),
-* Eq. 4 with alpha = 1 (Hernquist-Ostriker Gegenbauer radial basis),
+* Eq. 4, the Zhao (1996) radial family of exponent ``alpha`` (every basis
+  function takes it; the default 1 is the Hernquist-Ostriker Gegenbauer basis),
 * Sec. 2.1 (accelerating, non-rotating cluster frame; COM test particle),
 * App. A (Hernquist, NFW, Miyamoto-Nagai host components).
 
@@ -72,24 +73,24 @@ def _load():
         "or_dplm_dtheta": (d, [i, i, d]),
         "or_mplm_over_sin": (d, [i, i, d]),
         "or_nlm2": (d, [i, i]),
-        "or_knl": (d, [i, i]),
-        "or_inl": (d, [i, i, d]),
-        "or_phi_nl": (d, [i, i, d, d]),
-        "or_phi_nl_over_r": (d, [i, i, d, d]),
-        "or_dphi_nl_dr": (d, [i, i, d, d]),
-        "or_rho_nl": (d, [i, i, d, d]),
-        "or_coeffs": (None, [i64, p, p, i, i, d, p]),
-        "or_field": (None, [i64, p, p, i, i, d, d, p]),
+        "or_knl": (d, [i, i, d]),
+        "or_inl": (d, [i, i, d, d]),
+        "or_phi_nl": (d, [i, i, d, d, d]),
+        "or_phi_nl_over_r": (d, [i, i, d, d, d]),
+        "or_dphi_nl_dr": (d, [i, i, d, d, d]),
+        "or_rho_nl": (d, [i, i, d, d, d]),
+        "or_coeffs": (None, [i64, p, p, i, i, d, d, p]),
+        "or_field": (None, [i64, p, p, i, i, d, d, d, p]),
         "or_host_accel": (None, [p, p, p, p]),
         "or_tidal": (None, [p, p, p, p]),
         "or_tidal_tensor": (None, [p, i64, p, p]),
         "or_host_accel_many": (None, [p, i64, p, p]),
         "or_tidal_many": (None, [p, p, i64, p, p]),
-        "or_forces": (None, [i64, p, p, p, p, i, i, d, d, p]),
-        "or_energy": (None, [i64, p, p, p, p, p, i, i, d, d, p]),
-        "or_step": (None, [i64, p, p, p, p, p, i, i, d, d, d, i, p, p, p]),
+        "or_forces": (None, [i64, p, p, p, p, i, i, d, d, d, p]),
+        "or_energy": (None, [i64, p, p, p, p, p, i, i, d, d, d, p]),
+        "or_step": (None, [i64, p, p, p, p, p, i, i, d, d, d, d, i, p, p, p]),
         "or_direct": (None, [i64, p, i64, p, d, p]),
-        "or_power_l": (None, [p, i, i, d, p]),
+        "or_power_l": (None, [p, i, i, d, d, p]),
         "or_num_threads": (i, []),
     }
     for name, (res, args) in sig.items():
@@ -158,47 +159,50 @@ def nlm2(l, m):
     return _load().or_nlm2(int(l), int(m))
 
 
-def knl(n, l):
-    return _load().or_knl(int(n), int(l))
+# ``alpha``: the exponent of the Zhao (1996) radial family (Eq. 4); 1 is the
+# Hernquist-Ostriker basis, 1/2 the Clutton-Brock one.
+def knl(n, l, alpha=1.0):
+    return _load().or_knl(int(n), int(l), float(alpha))
 
 
-def inl(n, l, b):
-    return _load().or_inl(int(n), int(l), float(b))
+def inl(n, l, b, alpha=1.0):
+    return _load().or_inl(int(n), int(l), float(b), float(alpha))
 
 
-def phi_nl(n, l, b, r):
-    return _load().or_phi_nl(int(n), int(l), float(b), float(r))
+def phi_nl(n, l, b, r, alpha=1.0):
+    return _load().or_phi_nl(int(n), int(l), float(b), float(alpha), float(r))
 
 
-def phi_nl_over_r(n, l, b, r):
-    return _load().or_phi_nl_over_r(int(n), int(l), float(b), float(r))
+def phi_nl_over_r(n, l, b, r, alpha=1.0):
+    return _load().or_phi_nl_over_r(int(n), int(l), float(b), float(alpha), float(r))
 
 
-def dphi_nl_dr(n, l, b, r):
-    return _load().or_dphi_nl_dr(int(n), int(l), float(b), float(r))
+def dphi_nl_dr(n, l, b, r, alpha=1.0):
+    return _load().or_dphi_nl_dr(int(n), int(l), float(b), float(alpha), float(r))
 
 
-def rho_nl(n, l, b, r):
-    return _load().or_rho_nl(int(n), int(l), float(b), float(r))
+def rho_nl(n, l, b, r, alpha=1.0):
+    return _load().or_rho_nl(int(n), int(l), float(b), float(alpha), float(r))
 
 
 # ---------------------------------------------------------------- arrays
-def coeffs(pos, nmax, lmax, b, mask=None):
+def coeffs(pos, nmax, lmax, b, mask=None, alpha=1.0):
     """Real-form coefficients ``[S | T]`` of Eq. 3b for ``pos`` (N, 4)."""
     pos = _f64(pos)
     n = pos.shape[0]
     m = None if mask is None else np.ascontiguousarray(mask, dtype=np.uint8)
     A = np.zeros(2 * n_coef(nmax, lmax))
-    _load().or_coeffs(n, _ptr(pos), _ptr(m), int(nmax), int(lmax), float(b), _ptr(A))
+    _load().or_coeffs(n, _ptr(pos), _ptr(m), int(nmax), int(lmax), float(b), float(alpha), _ptr(A))
     return A
 
 
-def field(pos, A, nmax, lmax, b, G=1.0):
+def field(pos, A, nmax, lmax, b, G=1.0, alpha=1.0):
     """(N, 4) = (ax, ay, az, potential) of the expansion at ``pos[:, :3]``."""
     pos = _f64(pos)
     A = _f64(A)
     out = np.zeros((pos.shape[0], 4))
-    _load().or_field(pos.shape[0], _ptr(pos), _ptr(A), int(nmax), int(lmax), float(b), float(G), _ptr(out))
+    _load().or_field(pos.shape[0], _ptr(pos), _ptr(A), int(nmax), int(lmax), float(b), float(alpha), float(G),
+                     _ptr(out))
     return out
 
 
@@ -243,18 +247,18 @@ def tidal_many(host, R, pos):
     return a
 
 
-def forces(pos, A, nmax, lmax, b, G=1.0, com=None, host=None):
+def forces(pos, A, nmax, lmax, b, G=1.0, com=None, host=None, alpha=1.0):
     pos = _f64(pos)
     A = _f64(A)
     out = np.zeros((pos.shape[0], 4))
     c = None if com is None else _f64(com)
     hp = None if host is None else ctypes.byref(host)
-    _load().or_forces(pos.shape[0], _ptr(pos), _ptr(A), _ptr(c), hp, int(nmax), int(lmax), float(b), float(G),
-                      _ptr(out))
+    _load().or_forces(pos.shape[0], _ptr(pos), _ptr(A), _ptr(c), hp, int(nmax), int(lmax), float(b), float(alpha),
+                      float(G), _ptr(out))
     return out
 
 
-def energy(pos, vel, A, nmax, lmax, b, G=1.0, com=None, host=None):
+def energy(pos, vel, A, nmax, lmax, b, G=1.0, com=None, host=None, alpha=1.0):
     """(K, W, U, K + W + U): kinetic, self (1/2 sum m psi_SCF) and tidal
     energy of the particles in the cluster frame (see or_energy)."""
     pos = _f64(pos)
@@ -264,11 +268,12 @@ def energy(pos, vel, A, nmax, lmax, b, G=1.0, com=None, host=None):
     c = None if com is None else _f64(com)
     hp = None if host is None else ctypes.byref(host)
     _load().or_energy(pos.shape[0], _ptr(pos), _ptr(vel), _ptr(A), _ptr(c), hp, int(nmax), int(lmax), float(b),
-                      float(G), _ptr(out))
+                      float(alpha), float(G), _ptr(out))
     return out
 
 
-def step(pos, vel, acc, nmax, lmax, b, dt, nsteps, G=1.0, com=None, host=None, A_frozen=None, mask=None):
+def step(pos, vel, acc, nmax, lmax, b, dt, nsteps, G=1.0, com=None, host=None, A_frozen=None, mask=None,
+         alpha=1.0):
     """Kick-drift-kick leapfrog; returns new ``(pos, vel, acc, com, A_last)``.
 
     ``acc`` must hold the acceleration at ``pos`` (from :func:`forces`);
@@ -282,7 +287,7 @@ def step(pos, vel, acc, nmax, lmax, b, dt, nsteps, G=1.0, com=None, host=None, A
     Af = None if A_frozen is None else _f64(A_frozen)
     mk = None if mask is None else np.ascontiguousarray(mask, dtype=np.uint8)
     _load().or_step(pos.shape[0], _ptr(pos), _ptr(vel), _ptr(acc), _ptr(com), hp, int(nmax), int(lmax), float(b),
-                    float(G), float(dt), int(nsteps), _ptr(Af), _ptr(mk), _ptr(A_out))
+                    float(alpha), float(G), float(dt), int(nsteps), _ptr(Af), _ptr(mk), _ptr(A_out))
     return pos, vel, acc, com, A_out
 
 
@@ -369,14 +374,25 @@ def tidal_scales(host, R, M_c, eta=1.0 / 400.0, G=1.0):
     return out
 
 
+def zhao_half_mass_scale(r50, alpha=1.0):
+    """Scale b of the lowest-order density of the Zhao family (Eq. 4) whose
+    half-mass radius is ``r50``.  The enclosed mass of rho_00, from
+    M(r) = r^2 dU_00/dr, is (t / (1 + t))^(alpha + 1) with t = (r/b)^(1/alpha),
+    so M = 1/2 at t = 1 / (2^(1/(alpha+1)) - 1) and
+    ``b = r50 (2^(1/(alpha+1)) - 1)^alpha`` (alpha = 1: r50 / (1 + sqrt 2),
+    the Hernquist scale; alpha = 1/2: r50 sqrt(2^(2/3) - 1), the Plummer one)."""
+    return float(r50) * (2.0 ** (1.0 / (alpha + 1.0)) - 1.0) ** alpha
+
+
 def evolve(pos, vel, acc, nmax, lmax, b, dt, nsteps, G=1.0, com=None, host=None, kin=0.5, frac=0.999,
-           eta=1.0 / 400.0, max_steps=1000, retune_every=0):
+           eta=1.0 / 400.0, max_steps=1000, retune_every=0, alpha=1.0):
     """Leapfrog with the escape physics of Sec. 2.2.  At the start of every
     integration timestep: the boundedness test and the coefficient set
     r <= r_x (:func:`boundedness`); at every ``retune_every``-th integration
-    timestep (the first included; 0 = never) a complete refresh, which with
-    alpha = 1 retunes the basis scale b to the Hernquist scale of the bound
-    stars' energy-based half-mass radius, b = r_50 / (1 + sqrt 2); the field
+    timestep (the first included; 0 = never) a complete refresh, which
+    retunes the basis scale b (alpha fixed) to the scale of the lowest-order
+    density whose half-mass radius is the bound stars' energy-based one,
+    :func:`zhao_half_mass_scale` (alpha = 1: b = r_50 / (1 + sqrt 2)); the field
     of the coefficient set at the current positions; and the length of the
     integration timestep, dt_int of :func:`tidal_scales` at the current
     centre with the bound mass as M_c, taken as
@@ -399,9 +415,10 @@ def evolve(pos, vel, acc, nmax, lmax, b, dt, nsteps, G=1.0, com=None, host=None,
         stats = np.array([bound.sum(), Mb, np.sqrt(rx2), mask.sum()], dtype=np.float64)
         if retune_every > 0 and n_int % retune_every == 0 and bound.any():
             r50 = np.sqrt(boundedness(pos, vel, G, kin, 0.5)[2])
-            b = r50 / (1.0 + np.sqrt(2.0))
-        A = coeffs(pos, nmax, lmax, b, mask=mask)
-        acc = forces(pos, A, nmax, lmax, b, G, com=com if has_host else None, host=host if has_host else None)
+            b = zhao_half_mass_scale(r50, alpha)
+        A = coeffs(pos, nmax, lmax, b, mask=mask, alpha=alpha)
+        acc = forces(pos, A, nmax, lmax, b, G, com=com if has_host else None, host=host if has_host else None,
+                     alpha=alpha)
         k = max_steps
         if has_host:
             dt_int = tidal_scales(host, com[:3], np.array([Mb]), eta, G)[0, 15]
@@ -410,17 +427,17 @@ def evolve(pos, vel, acc, nmax, lmax, b, dt, nsteps, G=1.0, com=None, host=None,
                 k = 1 if ks < 1 else int(ks)
         k = min(k, nsteps - done)
         pos, vel, acc, com, _ = step(pos, vel, acc, nmax, lmax, b, dt, k, G, com=com if has_host else None,
-                                     host=host if has_host else None, mask=mask)
+                                     host=host if has_host else None, mask=mask, alpha=alpha)
         done += k
         n_int += 1
     return pos, vel, acc, com, bound, mask, stats, n_int, b
 
 
-def power_l(A, nmax, lmax, b):
+def power_l(A, nmax, lmax, b, alpha=1.0):
     """E_l = sum_{n,m} |a_nlm|^2 in the bi-orthonormal normalisation of Eq. 3a."""
     A = _f64(A)
     El = np.zeros(lmax + 1)
-    _load().or_power_l(_ptr(A), int(nmax), int(lmax), float(b), _ptr(El))
+    _load().or_power_l(_ptr(A), int(nmax), int(lmax), float(b), float(alpha), _ptr(El))
     return El
 
 

@@ -12,8 +12,9 @@
  *   - Eq. 2:     separable basis psi_nlm = U_n^l(r) Y_l^m(theta, phi).
  *   - Eq. 3a/3b: coefficients from a mass-weighted particle sum,
  *                a_nlm = -sum_k m_k psi*_nlm(r_k).
- *   - Eq. 4:     Zhao (1996) radial family; alpha = 1 is the Hernquist-Ostriker
- *                (1992) Gegenbauer basis used here.
+ *   - Eq. 4:     Zhao (1996) radial family of exponent alpha; alpha = 1 is the
+ *                Hernquist-Ostriker (1992) Gegenbauer basis, alpha = 1/2 the
+ *                Clutton-Brock (1973) one.
  *   - Sec. 2 ("N individual, embarrassingly parallel integrations"): every
  *                particle is moved in -grad psi_SCF.
  *   - Sec. 2.1:  accelerating, non-rotating cluster frame whose origin follows
@@ -22,12 +23,16 @@
  *
  * Conventions (the paper's normalisation is a bi-orthonormal basis with a
  * leading minus in Eq. 3a; the reading below is the same expansion written
- * with the Hernquist-Ostriker normalisation I_nl):
- *   s = r/b, xi = (s-1)/(s+1), alpha_l = 2l + 3/2
- *   Phi_nl(r) = -(1/b) s^l (1+s)^-(2l+1) C_n^(alpha_l)(xi)          (G = 1)
- *   rho_nl(r) = K_nl/(2 pi b^3) s^(l-1) (1+s)^-(2l+3) C_n^(alpha_l)(xi)
- *   K_nl      = n(n+4l+3)/2 + (l+1)(2l+1)
+ * with the normalisation I_nl of each potential-density pair):
+ *   s = r/b, t = s^(1/alpha), xi = (t-1)/(t+1), a_l = (2l+1) alpha,
+ *   lambda_l = a_l + 1/2 (Gegenbauer index; 2l + 3/2 at alpha = 1)
+ *   Phi_nl(r) = -(1/b) s^l (1+t)^-a_l C_n^(lambda_l)(xi)            (G = 1)
+ *   rho_nl(r) = K_nl/(4 pi b^3) s^(l-2+1/alpha) (1+t)^-(a_l+2) C_n^(lambda_l)(xi)
+ *   K_nl      = (n + a_l)(n + a_l + 1) / alpha^2
+ *               (at alpha = 1: twice n(n+4l+3)/2 + (l+1)(2l+1), the
+ *               Hernquist-Ostriker constant with its 1/(2 pi) prefactor)
  *   I_nl      = int r^2 rho_nl Phi_nl dr
+ * U_00 = -(1/b)(1 + s^(1/alpha))^-alpha is the form Eq. 4 prints.
  *   Real form of the coefficients (S = cosine part, T = sine part):
  *   S_nlm = (2-delta_m0)/I_nl N_lm^2 sum_k w_k m_k Phi_nl(r_k) P_l^m(cos th_k) cos(m ph_k)
  *   T_nlm = (2-delta_m0)/I_nl N_lm^2 sum_k w_k m_k Phi_nl(r_k) P_l^m(cos th_k) sin(m ph_k)
@@ -123,47 +128,78 @@ double or_nlm2(int l, int m) {
 }
 
 /* ------------------------------------------------------------------------ */
-/* Hernquist-Ostriker radial basis (Eq. 4 with alpha = 1)                   */
+/* Zhao (1996) radial basis (Eq. 4), exponent alpha > 0                     */
 /* ------------------------------------------------------------------------ */
 
-double or_knl(int n, int l) { return 0.5 * n * (n + 4.0 * l + 3.0) + (l + 1.0) * (2.0 * l + 1.0); }
-
-/* Closed form of I_nl = int_0^inf r^2 rho_nl Phi_nl dr:
- *   I_nl = -K_nl Gamma(n+4l+3) / (2^(8l+6) n! (n+2l+3/2) Gamma(2l+3/2)^2) / b. */
-double or_inl(int n, int l, double b) {
-  double lg = lgamma(n + 4.0 * l + 3.0) - (8.0 * l + 6.0) * log(2.0) - lgamma(n + 1.0) -
-              log(n + 2.0 * l + 1.5) - 2.0 * lgamma(2.0 * l + 1.5);
-  return -or_knl(n, l) * exp(lg) / b;
+double or_knl(int n, int l, double alpha) {
+  const double a = (2.0 * l + 1.0) * alpha;
+  return (n + a) * (n + a + 1.0) / (alpha * alpha);
 }
 
-double or_phi_nl(int n, int l, double b, double r) {
-  double s = r / b, xi = (s - 1.0) / (s + 1.0);
-  return -(1.0 / b) * pow(s, l) * pow(1.0 + s, -(2.0 * l + 1.0)) * or_gegenbauer(n, 2.0 * l + 1.5, xi);
+/* Closed form of I_nl = int_0^inf r^2 rho_nl Phi_nl dr.  With t = s^(1/alpha)
+ * the integrand becomes -(K_nl alpha / 4 pi b) t^a (1+t)^-(2a+2) C_n^2 dt, and
+ * xi = (t-1)/(t+1) turns it into the Gegenbauer weight (1 - xi^2)^(lambda-1/2)
+ * / 2^(2a+1) dxi, whose integral of C_n^2 is
+ * pi 2^(1-2 lambda) Gamma(n+2 lambda) / (n! (n+lambda) Gamma(lambda)^2):
+ *   I_nl = -K_nl alpha Gamma(n+2 lambda) / (2^(4a+3) n! (n+lambda) Gamma(lambda)^2) / b
+ * (alpha = 1: -K_nl Gamma(n+4l+3) / (2^(8l+7) n! (n+2l+3/2) Gamma(2l+3/2)^2) / b). */
+double or_inl(int n, int l, double b, double alpha) {
+  const double a = (2.0 * l + 1.0) * alpha, lam = a + 0.5;
+  double lg = lgamma(n + 2.0 * lam) - (4.0 * a + 3.0) * log(2.0) - lgamma(n + 1.0) - log(n + lam) -
+              2.0 * lgamma(lam);
+  return -or_knl(n, l, alpha) * alpha * exp(lg) / b;
+}
+
+/* s, t = s^(1/alpha) and xi = (t-1)/(t+1) of a radius. */
+static void zhao_coords(double r, double b, double alpha, double* s, double* t, double* xi) {
+  *s = r / b;
+  *t = (alpha == 1.0) ? *s : pow(*s, 1.0 / alpha);
+  *xi = (*t - 1.0) / (*t + 1.0);
+}
+
+double or_phi_nl(int n, int l, double b, double alpha, double r) {
+  double s, t, xi;
+  zhao_coords(r, b, alpha, &s, &t, &xi);
+  const double a = (2.0 * l + 1.0) * alpha;
+  return -(1.0 / b) * pow(s, l) * pow(1.0 + t, -a) * or_gegenbauer(n, a + 0.5, xi);
 }
 
 /* Phi_nl(r) / r for l >= 1 (finite at r = 0). */
-double or_phi_nl_over_r(int n, int l, double b, double r) {
-  double s = r / b, xi = (s - 1.0) / (s + 1.0);
-  return -(1.0 / (b * b)) * pow(s, l - 1) * pow(1.0 + s, -(2.0 * l + 1.0)) * or_gegenbauer(n, 2.0 * l + 1.5, xi);
+double or_phi_nl_over_r(int n, int l, double b, double alpha, double r) {
+  double s, t, xi;
+  zhao_coords(r, b, alpha, &s, &t, &xi);
+  const double a = (2.0 * l + 1.0) * alpha;
+  return -(1.0 / (b * b)) * pow(s, l - 1) * pow(1.0 + t, -a) * or_gegenbauer(n, a + 0.5, xi);
 }
 
-/* dPhi_nl/dr using dC_n^a/dxi = 2a C_{n-1}^{a+1} and dxi/ds = 2/(1+s)^2. */
-double or_dphi_nl_dr(int n, int l, double b, double r) {
-  double s = r / b, xi = (s - 1.0) / (s + 1.0), alpha = 2.0 * l + 1.5;
-  double cn = or_gegenbauer(n, alpha, xi);
-  double dcn = 2.0 * alpha * or_gegenbauer(n - 1, alpha + 1.0, xi);
-  double q = 1.0 / (1.0 + s);
-  double sl = pow(s, l), qpow = pow(q, 2.0 * l + 1.0);
+/* dPhi_nl/dr.  With q = 1/(1+t) and dt/ds = t/(alpha s):
+ *   d/ds [s^l q^a] = s^(l-1) q^a l - (2l+1) s^l q^a w,    w = q t / s,
+ *   dC_n^lam/dxi = 2 lam C_{n-1}^(lam+1),  dxi/ds = 2 q w / alpha
+ * (alpha = 1: w = q, dxi/ds = 2 q^2).  w = q s^(1/alpha - 1) is 0 at s = 0 for
+ * alpha < 1 and unbounded for alpha > 1; there it is set to 0: the terms it
+ * multiplies carry s^l, and the l = 0 radial term at r = 0, which has no
+ * direction, is dropped by the caller. */
+double or_dphi_nl_dr(int n, int l, double b, double alpha, double r) {
+  double s, t, xi;
+  zhao_coords(r, b, alpha, &s, &t, &xi);
+  const double a = (2.0 * l + 1.0) * alpha, lam = a + 0.5;
+  double cn = or_gegenbauer(n, lam, xi);
+  double dcn = 2.0 * lam * or_gegenbauer(n - 1, lam + 1.0, xi);
+  double q = 1.0 / (1.0 + t);
+  double w = (alpha == 1.0) ? q : (s > 0.0 ? q * pow(s, 1.0 / alpha - 1.0) : 0.0);
+  double sl = pow(s, l), qpow = pow(q, a);
   double t1 = (l > 0) ? l * pow(s, l - 1) * qpow * cn : 0.0;
-  double t2 = -(2.0 * l + 1.0) * sl * qpow * q * cn;
-  double t3 = sl * qpow * dcn * 2.0 * q * q;
+  double t2 = -(2.0 * l + 1.0) * sl * qpow * w * cn;
+  double t3 = sl * qpow * dcn * 2.0 * q * w / alpha;
   return -(1.0 / (b * b)) * (t1 + t2 + t3);
 }
 
-double or_rho_nl(int n, int l, double b, double r) {
-  double s = r / b, xi = (s - 1.0) / (s + 1.0);
-  return or_knl(n, l) / (2.0 * OR_PI * b * b * b) * pow(s, l - 1.0) * pow(1.0 + s, -(2.0 * l + 3.0)) *
-         or_gegenbauer(n, 2.0 * l + 1.5, xi);
+double or_rho_nl(int n, int l, double b, double alpha, double r) {
+  double s, t, xi;
+  zhao_coords(r, b, alpha, &s, &t, &xi);
+  const double a = (2.0 * l + 1.0) * alpha;
+  return or_knl(n, l, alpha) / (4.0 * OR_PI * b * b * b) * pow(s, l - 2.0 + 1.0 / alpha) * pow(1.0 + t, -(a + 2.0)) *
+         or_gegenbauer(n, a + 0.5, xi);
 }
 
 /* ------------------------------------------------------------------------ */
@@ -197,7 +233,8 @@ static void sph(double x, double y, double z, double* r, double* costh, double* 
 #define OR_CHUNKS 64
 
 /* A = [S | T] for the particles with mask[k] != 0 (mask NULL: all). */
-void or_coeffs(int64_t n_part, const double* pos, const uint8_t* mask, int nmax, int lmax, double b, double* A) {
+void or_coeffs(int64_t n_part, const double* pos, const uint8_t* mask, int nmax, int lmax, double b, double alpha,
+               double* A) {
   const int nn = nmax + 1, nlm = nlm_count(lmax), nc = nn * nlm;
   /* Fixed particle chunks summed in chunk order: the result does not depend
    * on the number of threads. */
@@ -217,7 +254,7 @@ void or_coeffs(int64_t n_part, const double* pos, const uint8_t* mask, int nmax,
       double r, costh, sinth, phi;
       sph(p[0], p[1], p[2], &r, &costh, &sinth, &phi);
       for (int n = 0; n <= nmax; ++n)
-        for (int l = 0; l <= lmax; ++l) phinl[n * (lmax + 1) + l] = or_phi_nl(n, l, b, r);
+        for (int l = 0; l <= lmax; ++l) phinl[n * (lmax + 1) + l] = or_phi_nl(n, l, b, alpha, r);
       for (int l = 0; l <= lmax; ++l)
         for (int m = 0; m <= l; ++m) plm[lm_index(l, m)] = plm_cs(l, m, costh, sinth);
       for (int n = 0; n <= nmax; ++n)
@@ -245,7 +282,7 @@ void or_coeffs(int64_t n_part, const double* pos, const uint8_t* mask, int nmax,
   free(part);
   for (int n = 0; n <= nmax; ++n)
     for (int l = 0; l <= lmax; ++l) {
-      double inl = or_inl(n, l, b);
+      double inl = or_inl(n, l, b, alpha);
       for (int m = 0; m <= l; ++m) {
         double f = (m == 0 ? 1.0 : 2.0) / inl * or_nlm2(l, m);
         int i = n * nlm + lm_index(l, m);
@@ -267,16 +304,17 @@ void or_coeffs(int64_t n_part, const double* pos, const uint8_t* mask, int nmax,
  * above are finite).  At r = 0 the l = 0 radial term has no direction and is
  * dropped (its limit depends on the direction of approach); the l = 1 terms
  * give the finite gradient there and l >= 2 terms vanish. */
-static void field_one(const double* x3, const double* A, int nmax, int lmax, double b, double G, double* out4) {
+static void field_one(const double* x3, const double* A, int nmax, int lmax, double b, double alpha, double G,
+                      double* out4) {
   const int nlm = nlm_count(lmax), nc = (nmax + 1) * nlm;
   double r, costh, sinth, phi;
   sph(x3[0], x3[1], x3[2], &r, &costh, &sinth, &phi);
   double pot = 0.0, ar = 0.0, ath = 0.0, aph = 0.0;
   for (int l = 0; l <= lmax; ++l) {
     for (int n = 0; n <= nmax; ++n) {
-      double phi_nl = or_phi_nl(n, l, b, r);
-      double dphi = or_dphi_nl_dr(n, l, b, r);
-      double phi_r = (l >= 1) ? or_phi_nl_over_r(n, l, b, r) : 0.0;
+      double phi_nl = or_phi_nl(n, l, b, alpha, r);
+      double dphi = (r == 0.0 && l == 0) ? 0.0 : or_dphi_nl_dr(n, l, b, alpha, r);
+      double phi_r = (l >= 1) ? or_phi_nl_over_r(n, l, b, alpha, r) : 0.0;
       for (int m = 0; m <= l; ++m) {
         int i = n * nlm + lm_index(l, m);
         double S = A[i], T = A[nc + i];
@@ -299,9 +337,10 @@ static void field_one(const double* x3, const double* A, int nmax, int lmax, dou
   out4[3] = G * pot;
 }
 
-void or_field(int64_t n_part, const double* pos, const double* A, int nmax, int lmax, double b, double G, double* acc) {
+void or_field(int64_t n_part, const double* pos, const double* A, int nmax, int lmax, double b, double alpha, double G,
+              double* acc) {
 #pragma omp parallel for schedule(static)
-  for (int64_t k = 0; k < n_part; ++k) field_one(pos + 4 * k, A, nmax, lmax, b, G, acc + 4 * k);
+  for (int64_t k = 0; k < n_part; ++k) field_one(pos + 4 * k, A, nmax, lmax, b, alpha, G, acc + 4 * k);
 }
 
 /* ------------------------------------------------------------------------ */
@@ -497,9 +536,9 @@ void or_tidal_many(const or_host* h, const double* R, int64_t n, const double* p
  *   out[3] = K + W + U.
  * Sums run in particle order in long double. */
 void or_energy(int64_t n_part, const double* pos, const double* vel, const double* A, const double* com,
-               const or_host* host, int nmax, int lmax, double b, double G, double* out) {
+               const or_host* host, int nmax, int lmax, double b, double alpha, double G, double* out) {
   double* f = (double*)malloc(sizeof(double) * 4 * (n_part > 0 ? n_part : 1));
-  or_field(n_part, pos, A, nmax, lmax, b, G, f);
+  or_field(n_part, pos, A, nmax, lmax, b, alpha, G, f);
   const int has_host = host && host->n > 0 && com;
   long double aR[3] = {0, 0, 0}, pR = 0;
   if (has_host) {
@@ -529,8 +568,8 @@ void or_energy(int64_t n_part, const double* pos, const double* vel, const doubl
 
 /* acc = -grad psi_SCF (coefficients A) + tidal term (host may be NULL). */
 void or_forces(int64_t n_part, const double* pos, const double* A, const double* com, const or_host* host, int nmax,
-               int lmax, double b, double G, double* acc) {
-  or_field(n_part, pos, A, nmax, lmax, b, G, acc);
+               int lmax, double b, double alpha, double G, double* acc) {
+  or_field(n_part, pos, A, nmax, lmax, b, alpha, G, acc);
   if (host && host->n > 0) {
 #pragma omp parallel for schedule(static)
     for (int64_t k = 0; k < n_part; ++k) {
@@ -557,7 +596,8 @@ void or_forces(int64_t n_part, const double* pos, const double* A, const double*
  * particle moves in the field (Sec. 2.2).  A_out (nullable) receives the last
  * coefficients used. */
 void or_step(int64_t n_part, double* pos, double* vel, double* acc, double* com, const or_host* host, int nmax,
-             int lmax, double b, double G, double dt, int nsteps, const double* A_frozen, const uint8_t* mask,
+             int lmax, double b, double alpha, double G, double dt, int nsteps, const double* A_frozen,
+             const uint8_t* mask,
              double* A_out) {
   const int nc = (nmax + 1) * nlm_count(lmax);
   double* A = (double*)malloc(sizeof(double) * 2 * nc);
@@ -581,8 +621,8 @@ void or_step(int64_t n_part, double* pos, double* vel, double* acc, double* com,
       }
     }
     if (A_frozen) memcpy(A, A_frozen, sizeof(double) * 2 * nc);
-    else or_coeffs(n_part, pos, mask, nmax, lmax, b, A);
-    or_forces(n_part, pos, A, com, host, nmax, lmax, b, G, acc);
+    else or_coeffs(n_part, pos, mask, nmax, lmax, b, alpha, A);
+    or_forces(n_part, pos, A, com, host, nmax, lmax, b, alpha, G, acc);
     if (has_host) {
       or_host_accel(host, com, aR, NULL);
       for (int d = 0; d < 3; ++d) com[3 + d] += 0.5 * dt * aR[d];
@@ -625,12 +665,12 @@ void or_direct(int64_t n_src, const double* src, int64_t n_tgt, const double* tg
  * the real form: the orthonormal-harmonic coefficient is A_nl0 = S_nl0/N_l0
  * and, for m > 0, |A_nlm|^2 = |A_nl,-m|^2 = (S^2 + T^2)/(4 N_lm^2); the
  * bi-orthonormal basis rescales each by sqrt(|I_nl|). */
-void or_power_l(const double* A, int nmax, int lmax, double b, double* El) {
+void or_power_l(const double* A, int nmax, int lmax, double b, double alpha, double* El) {
   const int nlm = nlm_count(lmax), nc = (nmax + 1) * nlm;
   for (int l = 0; l <= lmax; ++l) {
     double e = 0.0;
     for (int n = 0; n <= nmax; ++n) {
-      double inl = fabs(or_inl(n, l, b));
+      double inl = fabs(or_inl(n, l, b, alpha));
       for (int m = 0; m <= l; ++m) {
         int i = n * nlm + lm_index(l, m);
         double n2 = or_nlm2(l, m);
