@@ -54,9 +54,14 @@ WORKLOADS = {
     # double-precision particles with the float-float field kernel (SCF_OPT_K3_VARIANT = 1)
     "king_circular_fp64ff": ("king_circular", "fp64"),
     "plummer_eccentric_fp64ff": ("plummer_eccentric", "fp64"),
+    # the Plummer cluster in the alpha = 1/2 (Clutton-Brock) member of the radial family
+    "plummer_eccentric_cb_mixed": ("plummer_eccentric_cb", "mixed"),
+    "plummer_eccentric_cb_fp64": ("plummer_eccentric_cb", "fp64"),
 }
 FF_WORKLOADS = {"king_circular_fp64ff", "plummer_eccentric_fp64ff"}
 BUILDER_ARGS = {"paper_orbits": {"n_per": 200_000}}
+# per workload (not builder): the double-precision Clutton-Brock line runs N = 1e5
+WORKLOAD_ARGS = {"plummer_eccentric_cb_fp64": {"n": 100_000}}
 DEFAULT_WORKLOAD = "king_circular_fp64"
 
 
@@ -142,6 +147,7 @@ def build_workload(name, n_override=None):
     builder, precision = WORKLOADS[name]
     fn = getattr(workloads, builder)
     kw = dict(BUILDER_ARGS.get(builder, {}))
+    kw.update(WORKLOAD_ARGS.get(name, {}))
     if n_override is not None:
         if "n_per" in kw:
             kw["n_per"] = max(1, n_override // 10)
@@ -174,16 +180,17 @@ def cpu_baseline(wl, precision, steps=2):
     host = oracle.host_struct(wl.host) if wl.host else None
     com = wl.com if wl.host else np.zeros(6)
     t0 = time.perf_counter()
-    A0 = oracle.coeffs(wl.pos, wl.nmax, wl.lmax, wl.b)
-    acc0 = oracle.forces(wl.pos, A0, wl.nmax, wl.lmax, wl.b, com=com, host=host)
+    A0 = oracle.coeffs(wl.pos, wl.nmax, wl.lmax, wl.b, alpha=wl.alpha)
+    acc0 = oracle.forces(wl.pos, A0, wl.nmax, wl.lmax, wl.b, com=com, host=host, alpha=wl.alpha)
     t_init = time.perf_counter() - t0
     t0 = time.perf_counter()
-    p1, v1, a1, c1, A1 = oracle.step(wl.pos, wl.vel, acc0, wl.nmax, wl.lmax, wl.b, wl.dt, 1, com=com, host=host)
+    p1, v1, a1, c1, A1 = oracle.step(wl.pos, wl.vel, acc0, wl.nmax, wl.lmax, wl.b, wl.dt, 1, com=com, host=host,
+                                     alpha=wl.alpha)
     t1 = time.perf_counter() - t0
     t_rest = 0.0
     if steps > 1:
         t0 = time.perf_counter()
-        oracle.step(p1, v1, a1, wl.nmax, wl.lmax, wl.b, wl.dt, steps - 1, com=c1, host=host)
+        oracle.step(p1, v1, a1, wl.nmax, wl.lmax, wl.b, wl.dt, steps - 1, com=c1, host=host, alpha=wl.alpha)
         t_rest = time.perf_counter() - t0
     secs = t1 + t_rest
     return {
@@ -227,8 +234,8 @@ def run_reference(args, rank, world):
     com = wl.com if wl.host else np.zeros(6)
     # bounded sample: keep a step near <= 3 s of host time
     t0 = time.perf_counter()
-    A0 = oracle.coeffs(wl.pos, wl.nmax, wl.lmax, wl.b)
-    acc = oracle.forces(wl.pos, A0, wl.nmax, wl.lmax, wl.b, com=com, host=host)
+    A0 = oracle.coeffs(wl.pos, wl.nmax, wl.lmax, wl.b, alpha=wl.alpha)
+    acc = oracle.forces(wl.pos, A0, wl.nmax, wl.lmax, wl.b, com=com, host=host, alpha=wl.alpha)
     t_full = time.perf_counter() - t0
     n = wl.n
     if t_full > 3.0:
@@ -237,10 +244,12 @@ def run_reference(args, rank, world):
     pos[:, 3] *= wl.n / n
     c = com.copy()
     for _ in range(args.warmup):
-        pos, vel, acc, c, _ = oracle.step(pos, vel, acc, wl.nmax, wl.lmax, wl.b, wl.dt, 1, com=c, host=host)
+        pos, vel, acc, c, _ = oracle.step(pos, vel, acc, wl.nmax, wl.lmax, wl.b, wl.dt, 1, com=c, host=host,
+                                          alpha=wl.alpha)
     t0 = time.perf_counter()
     for _ in range(args.steps):
-        pos, vel, acc, c, _ = oracle.step(pos, vel, acc, wl.nmax, wl.lmax, wl.b, wl.dt, 1, com=c, host=host)
+        pos, vel, acc, c, _ = oracle.step(pos, vel, acc, wl.nmax, wl.lmax, wl.b, wl.dt, 1, com=c, host=host,
+                                          alpha=wl.alpha)
     secs = time.perf_counter() - t0
     value = n * args.steps / secs
     sample = (f"{n} of the workload's {wl.n} particles (mass rescaled), {args.steps} leapfrog steps by the FP64 "
@@ -348,7 +357,8 @@ def main():
     from paper_2602_13385_gb300 import SCF, Config
     wl, precision = build_workload(args.workload, args.n)
     dtype = torch.float64 if precision == "fp64" else torch.float32
-    cfg = Config(nmax=wl.nmax, lmax=wl.lmax, b=wl.b, dt=wl.dt, precision=precision, host=list(wl.host))
+    cfg = Config(nmax=wl.nmax, lmax=wl.lmax, b=wl.b, dt=wl.dt, precision=precision, host=list(wl.host),
+                 alpha=wl.alpha)
     offsets = [0, wl.n] if wl.offsets is None else list(wl.offsets)
     sim = SCF(cfg, offsets=offsets, b_per_prog=wl.b_per_prog)
     dev = sim.device

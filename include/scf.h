@@ -6,8 +6,9 @@
  * bi-orthogonal basis (Eq. 1a-2), the expansion coefficients are a
  * mass-weighted sum over particles (Eq. 3b), every particle moves in the
  * expansion's field plus the tidal field of an analytic host galaxy (Sec. 2.1,
- * App. A), and the radial basis is the Zhao family of Eq. 4 at alpha = 1
- * (Hernquist-Ostriker Gegenbauer basis), in units with G given by the caller
+ * App. A), and the radial basis is the Zhao family of Eq. 4 (alpha = 1, the
+ * Hernquist-Ostriker Gegenbauer basis, by default; any alpha in
+ * SCF_ALPHA_MIN..SCF_ALPHA_MAX), in units with G given by the caller
  * (Henon units: G = 1).
  *
  * All compute runs in CUDA kernels on one GPU (sm_103a).  The library does not
@@ -65,7 +66,7 @@ extern "C" {
 #define SCF_ERR_INVALID_ARG (-1)   /* a size, count, offset or option is out of range */
 #define SCF_ERR_NULL_POINTER (-2)  /* a required pointer is NULL */
 #define SCF_ERR_MISALIGNED (-3)    /* a particle pointer is not 16-byte aligned */
-#define SCF_ERR_UNSUPPORTED (-4)   /* alpha != 1, lmax/nmax beyond the compiled limits */
+#define SCF_ERR_UNSUPPORTED (-4)   /* lmax/nmax beyond the compiled limits, alpha out of range, a variant with alpha != 1 */
 #define SCF_ERR_CUDA (-5)          /* a CUDA runtime call or kernel launch failed */
 #define SCF_ERR_OUT_OF_MEMORY (-6) /* workspace allocation failed in scf_init */
 #define SCF_ERR_DEVICE_STATUS (-7) /* scf_status found device-side problems */
@@ -80,6 +81,8 @@ extern "C" {
 #define SCF_MAX_LMAX 12
 #define SCF_MAX_NMAX 40
 #define SCF_MAX_HOST_COMPONENTS 8
+#define SCF_ALPHA_MIN 0.1 /* range of the Zhao exponent alpha (Eq. 4) */
+#define SCF_ALPHA_MAX 4.0
 
 /* ---- precision (Sec. 2 leaves it open) ---- */
 #define SCF_FP64 0  /* every step in double precision */
@@ -98,7 +101,8 @@ typedef struct scf_host_component {
 typedef struct scf_config {
   int nmax;          /* radial truncation, 0 <= nmax <= SCF_MAX_NMAX */
   int lmax;          /* angular truncation, 0 <= lmax <= SCF_MAX_LMAX */
-  double alpha;      /* Zhao exponent of Eq. 4; must be 1 (Hernquist-Ostriker basis) */
+  double alpha;      /* Zhao exponent of Eq. 4, SCF_ALPHA_MIN..SCF_ALPHA_MAX: 1 = Hernquist-Ostriker
+                      * basis (all kernels), 1/2 = Clutton-Brock; see "Radial family" below */
   double b;          /* basis scale length b of Eq. 4 (> 0); per-progenitor values may override */
   double G;          /* gravitational constant (1 in Henon units) */
   double dt;         /* leapfrog step for scf_step */
@@ -108,6 +112,20 @@ typedef struct scf_config {
 } scf_config;
 
 typedef struct scf_handle scf_handle;
+
+/* Radial family (Eq. 4; Zhao 1996).  With s = r/b, t = s^(1/alpha),
+ * xi = (t-1)/(t+1), a_l = (2l+1) alpha and lambda_l = a_l + 1/2, the radial
+ * functions are  U_nl(r) = -(1/b) s^l (1+t)^(-a_l) C_n^(lambda_l)(xi),  the
+ * lowest one the U_00 ~ (1 + (r/b)^(1/alpha))^(-alpha) that Eq. 4 prints.
+ * alpha = 1 runs every kernel and option.  Any other alpha runs the general
+ * coefficient and field kernels (recurrence tables of the handle's alpha in
+ * its workspace): SCF_OPT_K1_TILE and SCF_OPT_K3_BLOCK accept only 128, the
+ * float-float variants and the adjoint return SCF_ERR_UNSUPPORTED, and
+ * scf_coeffs_noalloc takes alpha = 1 only.  An alpha whose tables overflow
+ * single precision at the handle's (nmax, lmax) returns SCF_ERR_UNSUPPORTED
+ * from scf_init; alpha <= 0 or non-finite returns SCF_ERR_INVALID_ARG.  At
+ * r = 0 the l = 0 radial force has no direction (for alpha > 1 it grows
+ * without bound towards the centre) and is left out there. */
 
 /* Creates a handle for n_prog progenitors (independent clusters sharing the
  * configuration) whose particles occupy [offsets[p], offsets[p+1]) of every
@@ -320,9 +338,12 @@ typedef struct scf_escape_params {
   double eta;        /* integration-timestep parameter (1/400) */
   int max_steps;     /* most leapfrog steps per integration timestep (>= 1) */
   int retune_every;  /* complete refresh every this many integration timesteps, the
-                        first included (the paper: 5); 0 = never.  With alpha = 1 it
-                        sets each progenitor's b to r_50 / (1 + sqrt 2), r_50 the
-                        energy-based Lagrange radius of half the bound stars */
+                        first included (the paper: 5); 0 = never.  It sets each
+                        progenitor's b (alpha fixed) so that the lowest-order density
+                        of the family, whose enclosed mass is (t/(1+t))^(alpha+1),
+                        has half its mass inside r_50, the energy-based Lagrange
+                        radius of half the bound stars: b = r_50 (2^(1/(alpha+1)) - 1)^alpha
+                        (r_50 / (1 + sqrt 2) at alpha = 1) */
 } scf_escape_params;
 
 /* nsteps leapfrog steps with the escape physics of Sec. 2.2.  At the start of

@@ -381,6 +381,8 @@ def zhao_half_mass_scale(r50, alpha=1.0):
     so M = 1/2 at t = 1 / (2^(1/(alpha+1)) - 1) and
     ``b = r50 (2^(1/(alpha+1)) - 1)^alpha`` (alpha = 1: r50 / (1 + sqrt 2),
     the Hernquist scale; alpha = 1/2: r50 sqrt(2^(2/3) - 1), the Plummer one)."""
+    if alpha == 1.0:
+        return float(r50) / (1.0 + np.sqrt(2.0))
     return float(r50) * (2.0 ** (1.0 / (alpha + 1.0)) - 1.0) ** alpha
 
 

@@ -3,6 +3,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <memory>
 #include <mutex>
 #include <new>
 #include <vector>
@@ -26,6 +27,8 @@ struct scf_handle {
   // kernel 1 / 2
   ScfLaunchInfo k1{};
   bool k1_ff = false;  // double-precision handles: float-float kernel 1
+  bool gen = false;    // radial family of exponent alpha != 1: the general kernels 1 and 3
+  ScfConst* d_tab = nullptr;  // their recurrence tables (device memory; gen handles only)
   int k1_blocks = 0;
   int* d_blk1_prog = nullptr;
   int64_t* d_blk1_begin = nullptr;
@@ -106,6 +109,23 @@ int upload_tables_once(int device) {
 
 bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
 
+// The general kernels read these entries for l <= lmax, n <= nmax; in single
+// precision (f32) the scales and ratios must also stay finite and non-zero.
+bool tables_finite(const ScfConst& t, int lmax, int nmax, bool f32) {
+  for (int l = 0; l <= lmax; ++l)
+    for (int n = 0; n <= nmax; ++n) {
+      const double d[4] = {t.gbeta[l][n], t.hbeta[l][n], t.gscale[l][n], t.hscale[l][n]};
+      const float f[5] = {t.gbetaf[l][n], t.hbetaf[l][n], t.gscalef[l][n], t.hscalef[l][n], t.hratiof[l][n]};
+      for (double x : d)
+        if (!std::isfinite(x)) return false;
+      if (!f32) continue;
+      for (float x : f)
+        if (!std::isfinite(x)) return false;
+      if (t.gscalef[l][n] == 0.f || t.hscalef[l][n] == 0.f) return false;
+    }
+  return true;
+}
+
 void drop_graph(scf_handle* h) {
   if (h->step_exec) cudaGraphExecDestroy(h->step_exec);
   h->step_exec = nullptr;
@@ -117,7 +137,8 @@ size_t round_up(size_t x) { return (x + 255) & ~size_t(255); }
 int check_config(const scf_config* c) {
   if (c->nmax < 0 || c->lmax < 0 || c->n_host < 0 || c->n_host > SCF_MAX_HOST_COMPONENTS) return SCF_ERR_INVALID_ARG;
   if (c->nmax > SCF_MAX_NMAX || c->lmax > SCF_MAX_LMAX) return SCF_ERR_UNSUPPORTED;
-  if (c->alpha != 1.0) return SCF_ERR_UNSUPPORTED;
+  if (!(c->alpha > 0.0) || !std::isfinite(c->alpha)) return SCF_ERR_INVALID_ARG;
+  if (c->alpha < SCF_ALPHA_MIN || c->alpha > SCF_ALPHA_MAX) return SCF_ERR_UNSUPPORTED;
   if (c->precision != SCF_FP64 && c->precision != SCF_MIXED) return SCF_ERR_INVALID_ARG;
   if (!std::isfinite(c->G) || !std::isfinite(c->dt) || !std::isfinite(c->b)) return SCF_ERR_INVALID_ARG;
   for (int i = 0; i < c->n_host; ++i) {
@@ -172,6 +193,9 @@ K1Args k1_args(scf_handle* h, void* pos, void* vel, const void* acc, const uint8
   a.mode = mode;
   a.dt = h->cfg.dt;
   a.status = h->d_status;
+  a.tab = h->d_tab;
+  a.alpha = h->cfg.alpha;
+  a.inv_alpha = 1.0 / h->cfg.alpha;
   return a;
 }
 
@@ -229,6 +253,9 @@ K3Args k3_args(scf_handle* h, const void* pos, void* vel, void* acc, const doubl
   a.dt = h->cfg.dt;
   a.host = h->host;
   a.status = h->d_status;
+  a.tab = h->d_tab;
+  a.alpha = h->cfg.alpha;
+  a.inv_alpha = 1.0 / h->cfg.alpha;
   return a;
 }
 
@@ -322,8 +349,18 @@ bool put(void* dst, const void* src, size_t bytes) {
 }
 
 // Kernel 1 launch shape: the simple kernel with a particle tile of 64, 128
-// or 256 (tp), or the register-tiled single-precision kernel (tp = 0).
+// or 256 (tp), or the register-tiled single-precision kernel (tp = 0).  For a
+// radial family of exponent alpha != 1 only the general simple kernel with
+// 128-particle tiles.
 int k1_shape(const scf_config& cfg, int tp, bool ff, ScfLaunchInfo* info, int* bps) {
+  if (cfg.alpha != 1.0) {
+    if (tp != 128 || ff) return SCF_ERR_UNSUPPORTED;
+    if (scf_k1_gen_prepare(cfg.precision, cfg.lmax, cfg.nmax, info, bps) != cudaSuccess || *bps < 1) {
+      cudaGetLastError();
+      return SCF_ERR_UNSUPPORTED;
+    }
+    return SCF_OK;
+  }
   cudaError_t e = tp == 0 ? scf_k1_tiled_prepare(cfg.lmax, cfg.nmax, info, bps)
                   : ff    ? scf_k1_ff_prepare(cfg.lmax, cfg.nmax, tp, info, bps)
                           : scf_k1_prepare(cfg.precision, cfg.lmax, cfg.nmax, tp, info, bps);
@@ -370,7 +407,10 @@ int use_k1(scf_handle* h, int tp) {
 int use_k3(scf_handle* h, int tb) {
   ScfLaunchInfo native{}, info{};
   int bps = 0;
-  if (scf_k3_prepare(h->cfg.precision, h->cfg.lmax, h->cfg.nmax, tb, &native, &bps) != cudaSuccess || bps < 1) {
+  if (h->gen && (tb != 128 || h->k3_ff)) return SCF_ERR_UNSUPPORTED;  // general kernel: 128 threads
+  if ((h->gen ? scf_k3_gen_prepare(h->cfg.precision, h->cfg.lmax, h->cfg.nmax, &native, &bps)
+              : scf_k3_prepare(h->cfg.precision, h->cfg.lmax, h->cfg.nmax, tb, &native, &bps)) != cudaSuccess ||
+      bps < 1) {
     cudaGetLastError();
     return SCF_ERR_UNSUPPORTED;
   }
@@ -433,6 +473,7 @@ int scf_init(const scf_config* cfg, int n_prog, const int64_t* offsets, const do
     delete h;
     return code;
   };
+  h->gen = cfg->alpha != 1.0;
   if (cudaGetDevice(&h->device) != cudaSuccess) return fail(SCF_ERR_CUDA);
   rc = upload_tables_once(h->device);
   if (rc != SCF_OK) return fail(rc);
@@ -501,6 +542,7 @@ int scf_init(const scf_config* cfg, int n_prog, const int64_t* offsets, const do
   const size_t o_half = take(sizeof(double) * 4 * (size_t)n_prog);
   const size_t o_k2z = take(sizeof(double) * kK2MaxChunks * 2 * (size_t)h->nc * n_prog);
   const size_t o_k2c = take(sizeof(unsigned) * (size_t)scf_k2_groups(h->nc) * n_prog);
+  const size_t o_tab = h->gen ? take(sizeof(ScfConst)) : off;
   if (cudaMalloc(&h->d_base, off) != cudaSuccess) {
     cudaGetLastError();
     return fail(SCF_ERR_OUT_OF_MEMORY);
@@ -531,9 +573,19 @@ int scf_init(const scf_config* cfg, int n_prog, const int64_t* offsets, const do
   h->d_k2z = reinterpret_cast<double*>(base + o_k2z);
   h->d_k2cnt = reinterpret_cast<unsigned*>(base + o_k2c);
 
+  if (h->gen) {  // recurrence tables of the handle's radial family
+    h->d_tab = reinterpret_cast<ScfConst*>(base + o_tab);
+    std::unique_ptr<ScfConst> t(new (std::nothrow) ScfConst);
+    if (!t) return fail(SCF_ERR_OUT_OF_MEMORY);
+    scf_make_const(t.get(), cfg->alpha);
+    if (!tables_finite(*t, cfg->lmax, cfg->nmax, cfg->precision == SCF_MIXED)) return fail(SCF_ERR_UNSUPPORTED);
+    if (!put(h->d_tab, t.get(), sizeof(ScfConst))) return fail(SCF_ERR_CUDA);
+  }
   std::vector<double> norm(2 * (size_t)h->nc), ksc(2 * (size_t)h->nc);
-  scf_make_norm(cfg->nmax, cfg->lmax, norm.data());
-  scf_make_kscale(cfg->nmax, cfg->lmax, ksc.data());
+  scf_make_norm(cfg->nmax, cfg->lmax, norm.data(), cfg->alpha);
+  scf_make_kscale(cfg->nmax, cfg->lmax, ksc.data(), cfg->alpha);
+  for (double x : norm)
+    if (!std::isfinite(x)) return fail(SCF_ERR_UNSUPPORTED);
   std::vector<float> ksc_f(ksc.begin(), ksc.end());
   const bool ksc_ok = cfg->precision == SCF_MIXED ? put(h->d_kscale, ksc_f.data(), sizeof(float) * ksc_f.size())
                                                   : put(h->d_kscale, ksc.data(), sizeof(double) * ksc.size());
@@ -746,6 +798,7 @@ int scf_adjoint_level(scf_handle* h, const void* pos, const double* com, double 
                       void* vbar, double* combar, double* thetabar) {
   if (!h) return SCF_ERR_NULL_POINTER;
   if (h->cfg.precision != SCF_FP64) return SCF_ERR_ADJOINT_FP64;
+  if (h->gen) return SCF_ERR_UNSUPPORTED;  // the adjoint kernels are written for alpha = 1
   if ((!pos || !xbar || !vbar) && h->n_total > 0) return SCF_ERR_NULL_POINTER;
   if (h->host.n > 0 && (!com || !combar || !thetabar)) return SCF_ERR_NULL_POINTER;
   if (!aligned16(pos) || !aligned16(xbar) || !aligned16(vbar)) return SCF_ERR_MISALIGNED;
@@ -913,7 +966,7 @@ int scf_evolve(scf_handle* h, void* pos, void* vel, void* acc, double* com, int 
     rc = scf_bound(h, pos, vel, ep->kin, ep->frac, nullptr, bound, mask, stats);
     if (rc != SCF_OK) return rc;
     if (ep->retune_every > 0 && refreshes % ep->retune_every == 0) {
-      // complete refresh (alpha = 1): b from the bound stars' half-mass radius
+      // complete refresh: b from the bound stars' half-mass radius (alpha fixed)
       BoundArgs a{};
       a.pos = pos;
       a.prog_off = h->d_off;
@@ -926,7 +979,7 @@ int scf_evolve(scf_handle* h, void* pos, void* vel, void* acc, double* com, int 
       a.mask = nullptr;
       a.stats = h->d_half;
       if (cuda_fail(scf_select_launch(a, h->stream)) != SCF_OK ||
-          cuda_fail(scf_retune_b_launch(h->d_half, h->d_b, h->n_prog, h->stream)) != SCF_OK)
+          cuda_fail(scf_retune_b_launch(h->d_half, h->d_b, h->n_prog, h->cfg.alpha, h->stream)) != SCF_OK)
         return SCF_ERR_CUDA;
     }
     // the field of the new set at the current positions (the next opening kick uses it)
@@ -1047,7 +1100,9 @@ const char* scf_strerror(int code) {
     case SCF_ERR_INVALID_ARG: return "invalid argument (size, count, offset or option out of range)";
     case SCF_ERR_NULL_POINTER: return "required pointer is NULL";
     case SCF_ERR_MISALIGNED: return "particle pointer is not 16-byte aligned";
-    case SCF_ERR_UNSUPPORTED: return "unsupported configuration (alpha != 1 or nmax/lmax above the compiled limits)";
+    case SCF_ERR_UNSUPPORTED:
+      return "unsupported configuration (nmax/lmax above the compiled limits, alpha outside its range, or a kernel "
+             "variant or the adjoint with alpha != 1)";
     case SCF_ERR_CUDA: return "CUDA runtime error";
     case SCF_ERR_OUT_OF_MEMORY: return "workspace allocation failed";
     case SCF_ERR_DEVICE_STATUS: return "device reported non-finite particle data";

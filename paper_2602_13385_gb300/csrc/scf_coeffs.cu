@@ -60,7 +60,18 @@ template <> struct BlockAcc<float> {
   __device__ static double value(const float2* a, int i) { return (double)a[i].x + (double)a[i].y; }
 };
 
-template <typename T, int LMAX, int TP>
+// Radial family of exponent alpha != 1 (GEN): the recurrence steps and scales
+// come from the handle's tables in device memory instead of the constant bank.
+template <typename T, bool GEN>
+__device__ __forceinline__ T k1_gbeta(const K1Args& a, int l, int n) {
+  if constexpr (GEN) return sizeof(T) == 8 ? (T)__ldg(&a.tab->gbeta[l][n]) : (T)__ldg(&a.tab->gbetaf[l][n]);
+  else return tab_gbeta<T>(l, n);
+}
+
+__device__ __forceinline__ double scf_pow(double x, double y) { return pow(x, y); }
+__device__ __forceinline__ float scf_pow(float x, float y) { return powf(x, y); }
+
+template <typename T, int LMAX, int TP, bool GEN = false>
 __global__ void __launch_bounds__(TP) k1_partials(K1Args a) {
   constexpr int YS = 2 * LMAX + 1;
   using V4 = typename Vec4<T>::type;
@@ -114,9 +125,12 @@ __global__ void __launch_bounds__(TP) k1_partials(K1Args a) {
     const T rinv = r > (T)0 ? (T)1 / r : (T)0;
     const T u = x * rinv, v = y * rinv, c = z * rinv;
     const T s = r * binv;
-    const T q = (T)1 / ((T)1 + s);
+    // alpha = 1: q = 1/(1+s), prefactor s^l q^(2l+1); alpha != 1: t = s^(1/alpha)
+    // replaces s in q and xi, and q^alpha carries the prefactor s^l q^((2l+1) alpha)
+    const T q = (T)1 / ((T)1 + (GEN ? scf_pow(s, (T)a.inv_alpha) : s));
     const T xi = (T)1 - (T)2 * q;
-    const T sq2 = s * q * q;
+    const T qa = GEN ? scf_pow(q, (T)a.alpha) : q;
+    const T sq2 = s * qa * qa;
     T Wc[LMAX + 1], Ws[LMAX + 1];
     Wc[0] = 1;
     Ws[0] = 0;
@@ -126,7 +140,7 @@ __global__ void __launch_bounds__(TP) k1_partials(K1Args a) {
       Ws[m] = Wc[m - 1] * v + Ws[m - 1] * u;
     }
     T P[LMAX + 1], P1[LMAX + 1], P2[LMAX + 1];
-    T pre = mass * q;  // m_k s^l q^(2l+1) at l = 0
+    T pre = mass * qa;  // m_k s^l q^((2l+1) alpha) at l = 0
 
 #pragma unroll
     for (int l = 0; l <= LMAX; ++l) {
@@ -143,7 +157,7 @@ __global__ void __launch_bounds__(TP) k1_partials(K1Args a) {
         T* Rt = R + tid * NN;
         Rt[0] = 1;
         for (int n = 1; n < NN; ++n) {
-          const T cn = xi * c0 - tab_gbeta<T>(l, n) * cm1;
+          const T cn = xi * c0 - k1_gbeta<T, GEN>(a, l, n) * cm1;
           cm1 = c0;
           c0 = cn;
           Rt[n] = cn;
@@ -184,7 +198,8 @@ __global__ void __launch_bounds__(TP) k1_partials(K1Args a) {
     const int n = ii / a.nlm, lm = ii - n * a.nlm;
     int l = 0;
     while ((l + 1) * (l + 2) / 2 <= lm) ++l;
-    out[i] = Acc::value(acc, i) * c_tab.gscale[l][n];  // undo the scaling of the staged C_n
+    const double gs = GEN ? a.tab->gscale[l][n] : c_tab.gscale[l][n];
+    out[i] = Acc::value(acc, i) * gs;  // undo the scaling of the staged C_n
   }
 }
 
@@ -774,12 +789,12 @@ __global__ void k_prep(PrepArgs a) {
   }
 }
 
-template <typename T, int TP, int LMAX>
+template <typename T, int TP, int LMAX, bool GEN = false>
 struct K1At {
-  static void* fn() { return (void*)k1_partials<T, LMAX, TP>; }
+  static void* fn() { return (void*)k1_partials<T, LMAX, TP, GEN>; }
   static size_t smem(int nmax, int nc) { return k1_smem<T, LMAX, TP>(nmax, nc); }
   static void launch(const K1Args& a, int blocks, size_t smem, cudaStream_t s) {
-    k1_partials<T, LMAX, TP><<<blocks, TP, smem, s>>>(a);
+    k1_partials<T, LMAX, TP, GEN><<<blocks, TP, smem, s>>>(a);
   }
 };
 
@@ -792,15 +807,15 @@ int lmax_bucket(int lmax) {
   return 12;
 }
 
-template <typename T, int TP, typename F>
+template <typename T, int TP, typename F, bool GEN = false>
 auto dispatch_lmax(int lmax, F&& f) {
   switch (lmax_bucket(lmax)) {
-    case 2: return f(K1At<T, TP, 2>());
-    case 4: return f(K1At<T, TP, 4>());
-    case 6: return f(K1At<T, TP, 6>());
-    case 8: return f(K1At<T, TP, 8>());
-    case 10: return f(K1At<T, TP, 10>());
-    default: return f(K1At<T, TP, 12>());
+    case 2: return f(K1At<T, TP, 2, GEN>());
+    case 4: return f(K1At<T, TP, 4, GEN>());
+    case 6: return f(K1At<T, TP, 6, GEN>());
+    case 8: return f(K1At<T, TP, 8, GEN>());
+    case 10: return f(K1At<T, TP, 10, GEN>());
+    default: return f(K1At<T, TP, 12, GEN>());
   }
 }
 
@@ -816,26 +831,34 @@ auto dispatch_k1(int tp, int lmax, F&& f) {
 
 }  // namespace
 
-template <typename T>
+template <typename T, bool GEN = false>
 static cudaError_t k1_prepare_t(int lmax, int nmax, int tp, ScfLaunchInfo* info, int* blocks_per_sm) {
   const int nlm = (lmax + 1) * (lmax + 2) / 2, nc = (nmax + 1) * nlm;
   if (tp != 64 && tp != 128 && tp != 256) return cudaErrorInvalidValue;
-  return dispatch_k1<T>(tp, lmax, [&](auto k) -> cudaError_t {
+  if (GEN && tp != 128) return cudaErrorInvalidValue;
+  auto body = [&](auto k) -> cudaError_t {
     using KK = decltype(k);
     info->threads = tp;
     info->tile = tp;
-    info->variant = 0;
+    info->variant = GEN ? 3 : 0;
     info->smem = KK::smem(nmax, nc);
     if (info->smem > 227 * 1024) return cudaErrorInvalidConfiguration;
     cudaError_t e = cudaFuncSetAttribute(KK::fn(), cudaFuncAttributeMaxDynamicSharedMemorySize, (int)info->smem);
     if (e != cudaSuccess) return e;
     return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, KK::fn(), info->threads, info->smem);
-  });
+  };
+  if constexpr (GEN) return dispatch_lmax<T, 128, decltype(body)&, true>(lmax, body);
+  else return dispatch_k1<T>(tp, lmax, body);
 }
 
 cudaError_t scf_k1_prepare(int precision, int lmax, int nmax, int tp, ScfLaunchInfo* info, int* blocks_per_sm) {
   if (precision == 1) return k1_prepare_t<float>(lmax, nmax, tp, info, blocks_per_sm);
   return k1_prepare_t<double>(lmax, nmax, tp, info, blocks_per_sm);
+}
+
+cudaError_t scf_k1_gen_prepare(int precision, int lmax, int nmax, ScfLaunchInfo* info, int* blocks_per_sm) {
+  if (precision == 1) return k1_prepare_t<float, true>(lmax, nmax, 128, info, blocks_per_sm);
+  return k1_prepare_t<double, true>(lmax, nmax, 128, info, blocks_per_sm);
 }
 
 cudaError_t scf_k1_tiled_prepare(int lmax, int nmax, ScfLaunchInfo* info, int* blocks_per_sm) {
@@ -885,8 +908,14 @@ cudaError_t scf_k1_launch(int precision, const K1Args& a, int blocks, const ScfL
     decltype(k)::launch(a, blocks, info.smem, s);
     return 0;
   };
-  if (precision == 1) dispatch_k1<float>(info.tile, a.lmax, go);
-  else dispatch_k1<double>(info.tile, a.lmax, go);
+  if (info.variant == 3) {  // radial family of exponent alpha != 1, 128-particle tiles
+    if (precision == 1) dispatch_lmax<float, 128, decltype(go)&, true>(a.lmax, go);
+    else dispatch_lmax<double, 128, decltype(go)&, true>(a.lmax, go);
+  } else if (precision == 1) {
+    dispatch_k1<float>(info.tile, a.lmax, go);
+  } else {
+    dispatch_k1<double>(info.tile, a.lmax, go);
+  }
   return cudaGetLastError();
 }
 

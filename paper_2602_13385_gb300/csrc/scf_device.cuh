@@ -7,7 +7,9 @@
 //   Pb_lm(c) = N_lm P_l^m(c) / sin^m(th): the normalised associated Legendre
 //              function without its sin^m factor (a polynomial in c),
 //   s = r/b, q = 1/(1+s), xi = (s-1)/(s+1) = 1 - 2q,
-//   radial factor of degree l: s^l q^(2l+1) C_n^(2l+3/2)(xi)  (Eq. 4, alpha = 1).
+//   radial factor of degree l: s^l q^(2l+1) C_n^(2l+3/2)(xi)  (Eq. 4, alpha = 1);
+//   for the Zhao family of exponent alpha, t = s^(1/alpha) replaces s in q and
+//   xi, q^((2l+1) alpha) replaces q^(2l+1), and the index is (2l+1) alpha + 1/2.
 // Coefficient pass (Eq. 3b):  Sh_nlm = sum_k m_k s^l q^(2l+1) C_n Pb_lm C_m(k), Th: S_m.
 // Field (Eq. 1a):  psi = sum_lm Pb_lm [Gc_lm C_m + Gs_lm S_m],
 //   G_lm(r) = s^l q^(2l+1) sum_n F_nlm C_n,  F = -G {S,T}_nlm / (b N_lm),
@@ -60,8 +62,9 @@ struct ScfConst {
   float hratiof[SCF_LMAX_CAP + 1][SCF_NMAX_CAP + 1];
 };
 
-// Host-side generation of the tables (scf_tables.cu).
-void scf_make_const(ScfConst* t);
+// Host-side generation of the tables (scf_tables.cu) for the radial family of
+// exponent alpha (1: Hernquist-Ostriker, the tables of the constant banks).
+void scf_make_const(ScfConst* t, double alpha = 1.0);
 
 // Host potential parameters passed by value to the kernels.
 struct ScfHostParams {

@@ -27,10 +27,12 @@
 //                  shared-memory histograms of integer counts), the mask.
 //   k_tidal        one thread per progenitor.
 // Every sum has a fixed order, so results are bitwise reproducible.
+#include <cmath>
 #include <cstdint>
 #include <math_constants.h>
 
 #include "scf_device.cuh"
+
 #include "scf_escape.h"
 
 namespace {
@@ -465,19 +467,26 @@ cudaError_t scf_select_launch(const BoundArgs& a, cudaStream_t s) {
 }
 
 namespace {
-// Complete refresh with alpha = 1: b = r_50 / (1 + sqrt 2), the Hernquist
-// scale of the bound stars' energy-based half-mass radius (stats from a
-// selection at frac = 0.5); unchanged for a progenitor with nothing bound.
-__global__ void k_retune_b(const double* stats, double* b_prog, int n_prog) {
+// Complete refresh: b = r_50 / div, the scale of the lowest-order density of
+// the radial family whose half-mass radius is the bound stars' energy-based
+// one (stats from a selection at frac = 0.5); unchanged for a progenitor with
+// nothing bound.
+__global__ void k_retune_b(const double* stats, double* b_prog, int n_prog, double div) {
   const int p = blockIdx.x * blockDim.x + threadIdx.x;
   if (p >= n_prog) return;
   const double* st = stats + 4 * (size_t)p;
-  if (st[0] > 0.0 && st[2] > 0.0) b_prog[p] = st[2] / (1.0 + 1.4142135623730950488);
+  if (st[0] > 0.0 && st[2] > 0.0) b_prog[p] = st[2] / div;
 }
 }  // namespace
 
-cudaError_t scf_retune_b_launch(const double* stats, double* b_prog, int n_prog, cudaStream_t s) {
-  k_retune_b<<<(n_prog + 127) / 128, 128, 0, s>>>(stats, b_prog, n_prog);
+double scf_half_mass_divisor(double alpha) {
+  // enclosed mass of the lowest-order density: (t/(1+t))^(alpha+1), t = (r/b)^(1/alpha)
+  if (alpha == 1.0) return 1.0 + 1.4142135623730950488;  // Hernquist
+  return std::pow(std::pow(2.0, 1.0 / (alpha + 1.0)) - 1.0, -alpha);
+}
+
+cudaError_t scf_retune_b_launch(const double* stats, double* b_prog, int n_prog, double alpha, cudaStream_t s) {
+  k_retune_b<<<(n_prog + 127) / 128, 128, 0, s>>>(stats, b_prog, n_prog, scf_half_mass_divisor(alpha));
   return cudaGetLastError();
 }
 

@@ -50,5 +50,7 @@ cudaError_t scf_tidal_launch(const TidalArgs& a, cudaStream_t s);
 // The selection alone (bound flags and radius keys from a previous
 // scf_bound_launch; mask may be null).
 cudaError_t scf_select_launch(const BoundArgs& a, cudaStream_t s);
-// b_prog[p] = r_x / (1 + sqrt 2) from the stats of a selection at frac = 0.5.
-cudaError_t scf_retune_b_launch(const double* stats, double* b_prog, int n_prog, cudaStream_t s);
+// b_prog[p] = r_x / scf_half_mass_divisor(alpha) from the stats of a selection at
+// frac = 0.5: r_x / (1 + sqrt 2) at alpha = 1, r_x (2^(1/(alpha+1)) - 1)^alpha otherwise.
+double scf_half_mass_divisor(double alpha);
+cudaError_t scf_retune_b_launch(const double* stats, double* b_prog, int n_prog, double alpha, cudaStream_t s);

@@ -43,7 +43,27 @@ template <typename T> __device__ __forceinline__ T tldiag(int l) { return sizeof
 template <typename T> __device__ __forceinline__ T tgbeta(int l, int n) { return sizeof(T) == 8 ? (T)c_tab.gbeta[l][n] : (T)c_tab.gbetaf[l][n]; }
 template <typename T> __device__ __forceinline__ T thbeta(int l, int n) { return sizeof(T) == 8 ? (T)c_tab.hbeta[l][n] : (T)c_tab.hbetaf[l][n]; }
 
-template <typename T, int LMAX, int K3_TB>
+// Radial family of exponent alpha != 1 (GEN): recurrence steps from the
+// handle's tables in device memory instead of the constant bank.
+template <typename T, bool GEN>
+__device__ __forceinline__ T k3_gbeta(const K3Args& a, int l, int n) {
+  if constexpr (GEN) return sizeof(T) == 8 ? (T)__ldg(&a.tab->gbeta[l][n]) : (T)__ldg(&a.tab->gbetaf[l][n]);
+  else return tgbeta<T>(l, n);
+}
+template <typename T, bool GEN>
+__device__ __forceinline__ T k3_hbeta(const K3Args& a, int l, int n) {
+  if constexpr (GEN) return sizeof(T) == 8 ? (T)__ldg(&a.tab->hbeta[l][n]) : (T)__ldg(&a.tab->hbetaf[l][n]);
+  else return thbeta<T>(l, n);
+}
+template <bool GEN>
+__device__ __forceinline__ float k3_hratio(const K3Args& a, int l, int n) {
+  if constexpr (GEN) return __ldg(&a.tab->hratiof[l][n]);
+  else return c_tab.hratiof[l][n];
+}
+__device__ __forceinline__ double k3_pow(double x, double y) { return pow(x, y); }
+__device__ __forceinline__ float k3_pow(float x, float y) { return powf(x, y); }
+
+template <typename T, int LMAX, int K3_TB, bool GEN = false>
 __global__ void __launch_bounds__(K3_TB) k3_forces(K3Args a) {
   using V4 = typename Vec4<T>::type;
   using V2 = typename Vec2<T>::type;
@@ -125,9 +145,16 @@ __global__ void __launch_bounds__(K3_TB) k3_forces(K3Args a) {
   const T rinv = r > (T)0 ? (T)1 / r : (T)0;
   const T u = x * rinv, v = y * rinv, c = z * rinv;
   const T s = r * binv;
-  const T q = (T)1 / ((T)1 + s);
+  // alpha = 1: q = 1/(1+s), prefactor s^l q^(2l+1).  alpha != 1: with
+  // t = s^(1/alpha), q = 1/(1+t), the prefactor is s^l q^((2l+1) alpha) and
+  // the radial derivative carries w = q t / s (= q at alpha = 1), set to 0 at
+  // s = 0 where the terms it multiplies vanish (l >= 1) or have no direction
+  const T t = GEN ? k3_pow(s, (T)a.inv_alpha) : s;
+  const T q = (T)1 / ((T)1 + t);
   const T xi = (T)1 - (T)2 * q;
-  const T sq2 = s * q * q;
+  const T qa = GEN ? k3_pow(q, (T)a.alpha) : q;
+  const T w = GEN ? (s > (T)0 ? q * k3_pow(s, (T)(a.inv_alpha - 1.0)) : (T)0) : q;
+  const T sq2 = s * qa * qa;
 
   T Wc[LMAX + 1], Ws[LMAX + 1];
   Wc[0] = 1;
@@ -139,8 +166,8 @@ __global__ void __launch_bounds__(K3_TB) k3_forces(K3Args a) {
   }
   T P[LMAX + 1], P1[LMAX + 1], P2[LMAX + 1];
   T An = 0, Ax = 0, Ay = 0, Az = 0, pot = 0;
-  T slq = q;        // s^l q^(2l+1)
-  T sl1q = q * q * q;  // s^(l-1) q^(2l+1) for l >= 1 (set at l = 1)
+  T slq = qa;              // s^l q^((2l+1) alpha)
+  T sl1q = qa * qa * qa;    // s^(l-1) q^((2l+1) alpha) for l >= 1 (set at l = 1)
   const int NN = a.nmax + 1;
 
 #pragma unroll
@@ -173,10 +200,10 @@ __global__ void __launch_bounds__(K3_TB) k3_forces(K3Args a) {
       T cm1 = 0, c0 = 1;  // Ch_{n-2}, Ch_{n-1}
       T dm1 = 0, d0 = 1;  // Dh_{n-2}, Dh_{n-1}
       for (int n = 1; n < NN; ++n) {
-        const T cn = xi * c0 - tgbeta<T>(l, n) * cm1;
+        const T cn = xi * c0 - k3_gbeta<T, GEN>(a, l, n) * cm1;
         const int o = n * a.nlm + lm0;
         if constexpr (kF2) {
-          const T dd = d0 * c_tab.hratiof[l][n];
+          const T dd = d0 * k3_hratio<GEN>(a, l, n);
 #pragma unroll
           for (int m = 0; m <= l; ++m) {
             const V2 fv = F2[o + m];
@@ -195,18 +222,18 @@ __global__ void __launch_bounds__(K3_TB) k3_forces(K3Args a) {
             Z1s[m] += fv.w * d0;
           }
         }
-        const T dn = xi * d0 - thbeta<T>(l, n) * dm1;
+        const T dn = xi * d0 - k3_hbeta<T, GEN>(a, l, n) * dm1;
         cm1 = c0;
         c0 = cn;
         dm1 = d0;
         d0 = dn;
       }
     }
-    // radial prefactors
-    const T al4 = (T)(4.0 * (2.0 * l + 1.5));
+    // radial prefactors; al4 = 4 lambda_l / alpha (4 (2l + 3/2) at alpha = 1)
+    const T al4 = GEN ? (T)(4.0 * (2 * l + 1) + 2.0 * a.inv_alpha) : (T)(4.0 * (2.0 * l + 1.5));
     const T k1 = (l >= 1) ? binv * sl1q : (T)0;                                  // G/r per Z0
-    const T k2a = binv * ((l >= 1 ? (T)l * sl1q : (T)0) - (T)(2 * l + 1) * slq * q);  // G' per Z0
-    const T k2b = binv * al4 * slq * q * q;                                       // G' per Z1
+    const T k2a = binv * ((l >= 1 ? (T)l * sl1q : (T)0) - (T)(2 * l + 1) * slq * w);  // G' per Z0
+    const T k2b = binv * al4 * slq * q * w;                                       // G' per Z1
 #pragma unroll
     for (int m = 0; m <= l; ++m) {
       const T g0c = slq * Z0c[m], g0s = slq * Z0s[m];
@@ -314,11 +341,11 @@ __global__ void __launch_bounds__(K3_TB) k3_forces(K3Args a) {
   }
 }
 
-template <typename T, int TB, int LMAX>
+template <typename T, int TB, int LMAX, bool GEN = false>
 struct K3At {
-  static void* fn() { return (void*)k3_forces<T, LMAX, TB>; }
+  static void* fn() { return (void*)k3_forces<T, LMAX, TB, GEN>; }
   static void launch(const K3Args& a, int blocks, size_t smem, cudaStream_t s) {
-    k3_forces<T, LMAX, TB><<<blocks, TB, smem, s>>>(a);
+    k3_forces<T, LMAX, TB, GEN><<<blocks, TB, smem, s>>>(a);
   }
 };
 
@@ -331,15 +358,15 @@ int lmax_bucket(int lmax) {
   return 12;
 }
 
-template <typename T, int TB, typename Fn>
+template <typename T, int TB, typename Fn, bool GEN = false>
 auto dispatch_lmax(int lmax, Fn&& f) {
   switch (lmax_bucket(lmax)) {
-    case 2: return f(K3At<T, TB, 2>());
-    case 4: return f(K3At<T, TB, 4>());
-    case 6: return f(K3At<T, TB, 6>());
-    case 8: return f(K3At<T, TB, 8>());
-    case 10: return f(K3At<T, TB, 10>());
-    default: return f(K3At<T, TB, 12>());
+    case 2: return f(K3At<T, TB, 2, GEN>());
+    case 4: return f(K3At<T, TB, 4, GEN>());
+    case 6: return f(K3At<T, TB, 6, GEN>());
+    case 8: return f(K3At<T, TB, 8, GEN>());
+    case 10: return f(K3At<T, TB, 10, GEN>());
+    default: return f(K3At<T, TB, 12, GEN>());
   }
 }
 
@@ -353,21 +380,24 @@ auto dispatch_k3(int tb, int lmax, Fn&& f) {
   }
 }
 
-template <typename T>
+template <typename T, bool GEN = false>
 cudaError_t prepare_t(int lmax, int nmax, int tb, ScfLaunchInfo* info, int* blocks_per_sm) {
   const int nlm = (lmax + 1) * (lmax + 2) / 2, nc = (nmax + 1) * nlm;
   if (tb != 64 && tb != 128 && tb != 256) return cudaErrorInvalidValue;
-  return dispatch_k3<T>(tb, lmax, [&](auto k) -> cudaError_t {
+  if (GEN && tb != 128) return cudaErrorInvalidValue;
+  auto body = [&](auto k) -> cudaError_t {
     using KK = decltype(k);
     info->threads = tb;
     info->tile = sizeof(T) == 8 ? tb / 2 : tb;  // double: two warps share a particle (split degrees)
-    info->variant = 0;
+    info->variant = GEN ? 3 : 0;
     // scaled (cosine, sine) per coefficient; double also the alpha + 1 family's
     info->smem = sizeof(T) * (sizeof(T) == 4 ? 2 : 4) * (size_t)nc;
     cudaError_t e = cudaFuncSetAttribute(KK::fn(), cudaFuncAttributeMaxDynamicSharedMemorySize, (int)info->smem);
     if (e != cudaSuccess) return e;
     return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, KK::fn(), info->threads, info->smem);
-  });
+  };
+  if constexpr (GEN) return dispatch_lmax<T, 128, decltype(body)&, true>(lmax, body);
+  else return dispatch_k3<T>(tb, lmax, body);
 }
 
 }  // namespace
@@ -377,12 +407,23 @@ cudaError_t scf_k3_prepare(int precision, int lmax, int nmax, int tb, ScfLaunchI
   return prepare_t<double>(lmax, nmax, tb, info, blocks_per_sm);
 }
 
+cudaError_t scf_k3_gen_prepare(int precision, int lmax, int nmax, ScfLaunchInfo* info, int* blocks_per_sm) {
+  if (precision == 1) return prepare_t<float, true>(lmax, nmax, 128, info, blocks_per_sm);
+  return prepare_t<double, true>(lmax, nmax, 128, info, blocks_per_sm);
+}
+
 cudaError_t scf_k3_launch(int precision, const K3Args& a, int blocks, const ScfLaunchInfo& info, cudaStream_t s) {
   auto go = [&](auto k) -> int {
     decltype(k)::launch(a, blocks, info.smem, s);
     return 0;
   };
-  if (precision == 1) dispatch_k3<float>(info.threads, a.lmax, go);
-  else dispatch_k3<double>(info.threads, a.lmax, go);
+  if (info.variant == 3) {  // radial family of exponent alpha != 1, 128-thread blocks
+    if (precision == 1) dispatch_lmax<float, 128, decltype(go)&, true>(a.lmax, go);
+    else dispatch_lmax<double, 128, decltype(go)&, true>(a.lmax, go);
+  } else if (precision == 1) {
+    dispatch_k3<float>(info.threads, a.lmax, go);
+  } else {
+    dispatch_k3<double>(info.threads, a.lmax, go);
+  }
   return cudaGetLastError();
 }

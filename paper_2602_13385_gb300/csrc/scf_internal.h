@@ -52,6 +52,10 @@ struct K1Args {
   // sub-groups per block, windows per block and tiles per window (partials
   // are then float rows, sub * win per block)
   int items, sub, win, win_tiles;
+  // radial family of exponent alpha != 1 (the general kernels): the handle's
+  // tables in device memory, alpha and 1/alpha
+  const ScfConst* tab;
+  double alpha, inv_alpha;
 };
 
 // Kernel 2: fixed-order reduction of the partials, normalisation, and the
@@ -119,6 +123,8 @@ struct K3Args {
   ScfHostParams host;
   unsigned* status;
   AdjArgs adj;
+  const ScfConst* tab;  // radial family of exponent alpha != 1, as in K1Args
+  double alpha, inv_alpha;
 };
 
 // Adjoint of the tidal term and of the centre orbit at one level of the reverse sweep.
@@ -164,10 +170,10 @@ struct ScfLaunchInfo {
   int win_tiles; // variant 1: tiles per window
 };
 
-void scf_make_norm(int nmax, int lmax, double* norm);
+void scf_make_norm(int nmax, int lmax, double* norm, double alpha = 1.0);
 // Per-coefficient scale pairs (gscale[l][n], hscale[l][n-1]; 0 at n = 0) of the
 // field kernel's scaled recurrences, as doubles ([NC][2]).
-void scf_make_kscale(int nmax, int lmax, double* kscale);
+void scf_make_kscale(int nmax, int lmax, double* kscale, double alpha = 1.0);
 
 cudaError_t scf_com_adj_launch(const ComAdjArgs& a, cudaStream_t s);
 // Dual-number kernels of the adjoint (double precision).  Both loop over their
@@ -187,12 +193,18 @@ cudaError_t scf_upload_const_adjoint(const ScfConst* t);
 // the given sizes; sets the shared-memory attribute of the instantiation.
 // tp: kernel 1 particle tile (64, 128, 256); tb: kernel 3 block size (64, 128, 256).
 cudaError_t scf_k1_prepare(int precision, int lmax, int nmax, int tp, ScfLaunchInfo* info, int* blocks_per_sm);
+// Kernel 1 for the radial family of exponent alpha != 1 (K1Args::tab), 128-particle
+// tiles; info->variant = 3.
+cudaError_t scf_k1_gen_prepare(int precision, int lmax, int nmax, ScfLaunchInfo* info, int* blocks_per_sm);
 // Register-tiled single-precision kernel 1 (info->variant = 1).
 cudaError_t scf_k1_tiled_prepare(int lmax, int nmax, ScfLaunchInfo* info, int* blocks_per_sm);
 // Windows per block of the register-tiled kernel for a block map whose
 // longest block has the given number of particles.
 int scf_k1_windows(int64_t max_particles_per_block, const ScfLaunchInfo& info);
 cudaError_t scf_k3_prepare(int precision, int lmax, int nmax, int tb, ScfLaunchInfo* info, int* blocks_per_sm);
+// Kernel 3 for the radial family of exponent alpha != 1 (K3Args::tab), 128-thread
+// blocks; info->variant = 3.
+cudaError_t scf_k3_gen_prepare(int precision, int lmax, int nmax, ScfLaunchInfo* info, int* blocks_per_sm);
 // Float-float kernel 3 for double-precision handles (info->variant = 2; the
 // same threads, tile and block map as the double kernel; modes COEFFS and STEP).
 cudaError_t scf_k3_ff_prepare(int lmax, int nmax, int tb, ScfLaunchInfo* info, int* blocks_per_sm);

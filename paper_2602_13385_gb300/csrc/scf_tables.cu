@@ -8,12 +8,16 @@
 
 static const double kPi = 3.14159265358979323846;
 
-void scf_make_const(ScfConst* t) {
+// Gegenbauer index of degree l in the Zhao (1996) family of exponent alpha
+// (Eq. 4): lambda_l = (2l + 1) alpha + 1/2 (2l + 3/2 for Hernquist-Ostriker).
+static double zhao_lambda(int l, double alpha) { return (2.0 * l + 1.0) * alpha + 0.5; }
+
+void scf_make_const(ScfConst* t, double alpha) {
   std::memset(t, 0, sizeof(*t));
   for (int l = 0; l <= SCF_LMAX_CAP; ++l) {
-    const double al = 2.0 * l + 1.5;
+    const double al = zhao_lambda(l, alpha);
     for (int fam = 0; fam < 2; ++fam) {
-      const double a = al + fam;  // alpha_l (values) and alpha_l + 1 (derivative family)
+      const double a = al + fam;  // lambda_l (values) and lambda_l + 1 (derivative family)
       double* A = fam ? t->hA[l] : t->gA[l];
       double* B = fam ? t->hB[l] : t->gB[l];
       A[1] = 2.0 * a;
@@ -73,16 +77,21 @@ void scf_make_const(ScfConst* t) {
 }
 
 // S = -(2 - delta_m0) N_lm / I_nl(b) * (1/b) * Sh, and b I_nl(b) = I_nl(1), so
-// the factor is independent of b:  -(2 - delta_m0) N_lm / I_nl(1), with
-// I_nl(1) = -K_nl Gamma(n+4l+3) / (2^(8l+6) n! (n+2l+3/2) Gamma(2l+3/2)^2).
-void scf_make_norm(int nmax, int lmax, double* norm /* 2*NC */) {
+// the factor is independent of b:  -(2 - delta_m0) N_lm / I_nl(1).  The radial
+// self-energy of pair (n, l) of the Zhao family, with a = (2l+1) alpha and
+// lambda = a + 1/2, follows from the Gegenbauer norm after t = s^(1/alpha),
+// xi = (t-1)/(t+1):
+//   I_nl(1) = -(n+a)(n+a+1)/alpha Gamma(n+2 lambda) / (2^(4a+3) n! (n+lambda) Gamma(lambda)^2)
+// (alpha = 1: -K_nl Gamma(n+4l+3) / (2^(8l+6) n! (n+2l+3/2) Gamma(2l+3/2)^2),
+// K_nl = n(n+4l+3)/2 + (l+1)(2l+1)).
+void scf_make_norm(int nmax, int lmax, double* norm /* 2*NC */, double alpha) {
   const int nlm = (lmax + 1) * (lmax + 2) / 2, nc = (nmax + 1) * nlm;
   for (int n = 0; n <= nmax; ++n)
     for (int l = 0; l <= lmax; ++l) {
-      const double knl = 0.5 * n * (n + 4.0 * l + 3.0) + (l + 1.0) * (2.0 * l + 1.0);
-      const double lg = std::lgamma(n + 4.0 * l + 3.0) - (8.0 * l + 6.0) * std::log(2.0) - std::lgamma(n + 1.0) -
-                        std::log(n + 2.0 * l + 1.5) - 2.0 * std::lgamma(2.0 * l + 1.5);
-      const double inl = -knl * std::exp(lg);
+      const double a = (2.0 * l + 1.0) * alpha, lam = zhao_lambda(l, alpha);
+      const double lg = std::lgamma(n + 2.0 * lam) - (4.0 * a + 3.0) * std::log(2.0) - std::lgamma(n + 1.0) -
+                        std::log(n + lam) - 2.0 * std::lgamma(lam);
+      const double inl = -(n + a) * (n + a + 1.0) / alpha * std::exp(lg);
       for (int m = 0; m <= l; ++m) {
         double ratio = 1.0;
         for (int k = l - m + 1; k <= l + m; ++k) ratio /= (double)k;
@@ -95,9 +104,9 @@ void scf_make_norm(int nmax, int lmax, double* norm /* 2*NC */) {
     }
 }
 
-void scf_make_kscale(int nmax, int lmax, double* kscale) {
+void scf_make_kscale(int nmax, int lmax, double* kscale, double alpha) {
   ScfConst* t = new ScfConst;
-  scf_make_const(t);
+  scf_make_const(t, alpha);
   const int nlm = (lmax + 1) * (lmax + 2) / 2;
   for (int n = 0; n <= nmax; ++n)
     for (int l = 0; l <= lmax; ++l)

@@ -224,7 +224,7 @@ class SCF:
         n = max(self.n, 1)
         n2 = float(f"{n:.2g}")          # shapes are chosen per problem-size bucket
         return "|".join(str(x) for x in (torch.cuda.get_device_name(self.device), self.config.precision,
-                                         self.config.nmax, self.config.lmax, n2, self.n_prog))
+                                         self.config.nmax, self.config.lmax, n2, self.n_prog, self.config.alpha))
 
     def autotune(self, pos, com=None, acc=None, reps: int = 5, cache: bool = True) -> dict:
         """Chooses the kernel shapes by timing every allowed size on ``pos``

@@ -69,7 +69,10 @@ def _init(lib, cfg, offsets=(0, 10), b=None):
 
 def test_init_rejects_bad_arguments_before_device_work(lib):
     assert lib.scf_init(None, 1, None, None, None, None) == -2
-    assert _init(lib, _cfg(alpha=0.5)) == -4          # only the alpha = 1 basis is built
+    assert _init(lib, _cfg(alpha=0.0)) == -1          # the radial family needs alpha > 0
+    assert _init(lib, _cfg(alpha=float("nan"))) == -1
+    assert _init(lib, _cfg(alpha=0.05)) == -4         # outside SCF_ALPHA_MIN..SCF_ALPHA_MAX
+    assert _init(lib, _cfg(alpha=5.0)) == -4
     assert _init(lib, _cfg(lmax=13)) == -4
     assert _init(lib, _cfg(nmax=41)) == -4
     assert _init(lib, _cfg(nmax=-1)) == -1

@@ -207,11 +207,15 @@ def half_mass_radius(pos4) -> float:
     return float(r[order][np.searchsorted(cm, 0.5 * cm[-1])])
 
 
-def basis_scale(r_half: float) -> float:
-    """Basis scale b of a Hernquist sphere with the same half-mass radius
-    (r_h = (1 + sqrt 2) b); the paper retunes b at each complete refresh
-    (Sec. 2), the hot path keeps it fixed per run."""
-    return r_half / (1.0 + math.sqrt(2.0))
+def basis_scale(r_half: float, alpha: float = 1.0) -> float:
+    """Basis scale b of the lowest-order density of the radial family (Eq. 4)
+    with the same half-mass radius: its enclosed mass is (t/(1+t))^(alpha+1),
+    t = (r/b)^(1/alpha), so b = r_h (2^(1/(alpha+1)) - 1)^alpha -- a Hernquist
+    sphere's r_h = (1 + sqrt 2) b at alpha = 1, a Plummer sphere's scale at
+    alpha = 1/2.  The paper retunes b at each complete refresh (Sec. 2)."""
+    if alpha == 1.0:
+        return r_half / (1.0 + math.sqrt(2.0))
+    return r_half * (2.0 ** (1.0 / (alpha + 1.0)) - 1.0) ** alpha
 
 
 # --------------------------------------------------------------------------
@@ -330,6 +334,7 @@ class Workload:
     offsets: np.ndarray | None = None          # progenitor boundaries (batched workloads)
     b_per_prog: np.ndarray | None = None
     com_per_prog: np.ndarray | None = None
+    alpha: float = 1.0                         # exponent of the radial family (Eq. 4)
 
     @property
     def n(self) -> int:
@@ -374,6 +379,18 @@ def plummer_eccentric(n: int = 1_000_000, seed: int = 3, nsteps: int = 2000) -> 
     host = host_in_units(galaxy_host_physical(), units)
     com = _com_from_orbit(_orbit_ics()["eccentric_5_20kpc"], units)
     return Workload(f"plummer_n{n}_eccentric", pos, vel, 20, 10, basis_scale(rh), 0.01, nsteps, host, com, units)
+
+
+def plummer_eccentric_cb(n: int = 1_000_000, seed: int = 3, nsteps: int = 2000) -> Workload:
+    """The same Plummer cluster and orbit expanded in the alpha = 1/2 member of
+    the radial family (Eq. 4; the Clutton-Brock basis, whose lowest-order pair
+    is the Plummer sphere), b = the sample's Plummer scale; nmax = 20, lmax = 10."""
+    wl = plummer_eccentric(n, seed, nsteps)
+    rh = half_mass_radius(wl.pos)
+    wl.name = f"plummer_n{n}_eccentric_alpha0.5"
+    wl.alpha = 0.5
+    wl.b = basis_scale(rh, 0.5)
+    return wl
 
 
 def plummer_stream(n: int = 100_000, seed: int = 6, nsteps: int = 6000) -> Workload:
