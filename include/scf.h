@@ -119,7 +119,8 @@ typedef struct scf_handle scf_handle;
  * lowest one the U_00 ~ (1 + (r/b)^(1/alpha))^(-alpha) that Eq. 4 prints.
  * alpha = 1 runs every kernel and option.  Any other alpha runs the general
  * coefficient and field kernels (recurrence tables of the handle's alpha in
- * its workspace): SCF_OPT_K1_TILE and SCF_OPT_K3_BLOCK accept only 128, the
+ * its workspace): SCF_OPT_K1_TILE accepts 128 and (SCF_MIXED, the default
+ * there) 0, SCF_OPT_K3_BLOCK only 128, the
  * float-float variants and the adjoint return SCF_ERR_UNSUPPORTED, and
  * scf_coeffs_noalloc takes alpha = 1 only.  An alpha whose tables overflow
  * single precision at the handle's (nmax, lmax) returns SCF_ERR_UNSUPPORTED

@@ -350,12 +350,15 @@ bool put(void* dst, const void* src, size_t bytes) {
 
 // Kernel 1 launch shape: the simple kernel with a particle tile of 64, 128
 // or 256 (tp), or the register-tiled single-precision kernel (tp = 0).  For a
-// radial family of exponent alpha != 1 only the general simple kernel with
-// 128-particle tiles.
+// radial family of exponent alpha != 1: the general simple kernel with
+// 128-particle tiles, or (mixed precision) the register-tiled kernel's
+// runtime-indexed basis.
 int k1_shape(const scf_config& cfg, int tp, bool ff, ScfLaunchInfo* info, int* bps) {
   if (cfg.alpha != 1.0) {
-    if (tp != 128 || ff) return SCF_ERR_UNSUPPORTED;
-    if (scf_k1_gen_prepare(cfg.precision, cfg.lmax, cfg.nmax, info, bps) != cudaSuccess || *bps < 1) {
+    if ((tp != 128 && tp != 0) || ff) return SCF_ERR_UNSUPPORTED;
+    const cudaError_t e = tp == 0 ? scf_k1_tiled_prepare(cfg.lmax, cfg.nmax, info, bps, true)
+                                  : scf_k1_gen_prepare(cfg.precision, cfg.lmax, cfg.nmax, info, bps);
+    if (e != cudaSuccess || *bps < 1) {
       cudaGetLastError();
       return SCF_ERR_UNSUPPORTED;
     }

@@ -267,15 +267,17 @@ __host__ __device__ constexpr int chunk_base(int l) {  // chunks of the degrees 
   return k;
 }
 __host__ __device__ constexpr int y_row(int l, int mm) { return YCH * (chunk_base(l) + mm / TM) + mm % TM; }
-inline size_t smem_bytes(int nmax, int lmax) {
+inline size_t smem_bytes(int nmax, int lmax, bool gen = false) {
   const size_t rows = (size_t)(lmax + 1) * (nmax + 1) + (TN - 1) + (size_t)YCH * chunk_base(lmax + 1);
-  return sizeof(float) * TPP * rows;
+  // gen: then the Gegenbauer steps gbeta[l][n] of the handle's radial family
+  return sizeof(float) * (TPP * rows + (gen ? (size_t)(lmax + 1) * (nmax + 1) : 0));
 }
 
 // Stores a worker's register sums (times the constant gscale of the staged
-// C_n) into its window slot and clears them; zero = true stores zeros.
+// C_n) into its window slot and clears them; zero = true stores zeros.  tab:
+// the tables of a radial family with alpha != 1 (null: the constant bank's).
 __device__ __forceinline__ void store_tile(float (&acc)[TN][TM], float* __restrict__ out, bool zero, int l, int n0,
-                                           int mm0, int nn, int nlm, int nc) {
+                                           int mm0, int nn, int nlm, int nc, const ScfConst* tab) {
 #pragma unroll
   for (int j = 0; j < TM; ++j) {
     const int mm = mm0 + j;
@@ -283,7 +285,10 @@ __device__ __forceinline__ void store_tile(float (&acc)[TN][TM], float* __restri
     const bool jok = mm <= 2 * l;
 #pragma unroll
     for (int i = 0; i < TN; ++i) {
-      if (jok && n0 + i < nn) out[(n0 + i) * nlm + col] = zero ? 0.f : acc[i][j] * c_tab.gscalef[l][n0 + i];
+      if (jok && n0 + i < nn) {
+        const float gs = tab ? __ldg(&tab->gscalef[l][n0 + i]) : c_tab.gscalef[l][n0 + i];
+        out[(n0 + i) * nlm + col] = zero ? 0.f : acc[i][j] * gs;
+      }
       acc[i][j] = 0.f;
     }
   }
@@ -291,10 +296,14 @@ __device__ __forceinline__ void store_tile(float (&acc)[TN][TM], float* __restri
 
 // Basis of one particle for thread set q (runtime degrees and orders): the
 // chains l = q + 4j (radial rows) and m = q + 4j (Legendre columns, angular rows).
-template <int NCH>
+// GEN: a radial family with alpha != 1, its Gegenbauer steps from sg (shared
+// memory, [l][n] rows of NN); qv is then q^alpha and sq2 = s q^(2 alpha) (the
+// factors of the prefactor).
+template <int NCH, bool GEN = false>
 struct BasisGeneric {
+  static constexpr bool kGen = GEN;
   static __device__ __forceinline__ void run(int q, float* Rs, float* Ys, int t, int NN, int L, float mass, float u,
-                                             float v, float c, float qv, float xi, float sq2) {
+                                             float v, float c, float qv, float xi, float sq2, const float* sg) {
       // radial chains of the degrees l = q + 4j: R[l][n] = Ch_n(xi)
     {
       float c0[NCH], cm1[NCH];
@@ -310,7 +319,8 @@ struct BasisGeneric {
         for (int j = 0; j < NCH; ++j) {
           const int l = q + 4 * j;
           if (l <= L) {
-            const float cn = fmaf(-c_tab.gbetaf[l][n], cm1[j], xi * c0[j]);
+            const float gb = GEN ? sg[l * NN + n] : c_tab.gbetaf[l][n];
+            const float cn = fmaf(-gb, cm1[j], xi * c0[j]);
             cm1[j] = c0[j];
             c0[j] = cn;
             Rs[(l * NN + n) * TPP + t] = cn;
@@ -368,9 +378,9 @@ struct BasisGeneric {
 
 // The same with the shape fixed at compile time: every recurrence constant is
 // an immediate constant-bank operand and every staged row an immediate offset.
-template <int Q, int NN, int L>
+template <int Q, int NN, int L, bool GEN>
 __device__ __forceinline__ void basis_fixed(float* Rs, float* Ys, int t, float mass, float u, float v, float c,
-                                            float qv, float xi, float sq2) {
+                                            float qv, float xi, float sq2, const float* sg) {
   constexpr int NJ = Q <= L ? (L - Q) / 4 + 1 : 0;
   if constexpr (NJ > 0) {
     // radial rows Ch_n(xi) of the degrees l = Q + 4j
@@ -386,7 +396,8 @@ __device__ __forceinline__ void basis_fixed(float* Rs, float* Ys, int t, float m
 #pragma unroll
       for (int j = 0; j < NJ; ++j) {
         const int l = Q + 4 * j;
-        const float cn = fmaf(-c_tab.gbetaf[l][n], cm1[j], xi * c0[j]);
+        const float gb = GEN ? sg[l * NN + n] : c_tab.gbetaf[l][n];  // GEN: an immediate shared offset
+        const float cn = fmaf(-gb, cm1[j], xi * c0[j]);
         cm1[j] = c0[j];
         c0[j] = cn;
         Rs[(l * NN + n) * TPP + t] = cn;
@@ -439,15 +450,16 @@ __device__ __forceinline__ void basis_fixed(float* Rs, float* Ys, int t, float m
   }
 }
 
-template <int NN_, int L_>
+template <int NN_, int L_, bool GEN = false>
 struct BasisFixed {
+  static constexpr bool kGen = GEN;
   static __device__ __forceinline__ void run(int q, float* Rs, float* Ys, int t, int, int, float mass, float u,
-                                             float v, float c, float qv, float xi, float sq2) {
+                                             float v, float c, float qv, float xi, float sq2, const float* sg) {
     switch (q) {  // warp-uniform
-      case 0: basis_fixed<0, NN_, L_>(Rs, Ys, t, mass, u, v, c, qv, xi, sq2); break;
-      case 1: basis_fixed<1, NN_, L_>(Rs, Ys, t, mass, u, v, c, qv, xi, sq2); break;
-      case 2: basis_fixed<2, NN_, L_>(Rs, Ys, t, mass, u, v, c, qv, xi, sq2); break;
-      default: basis_fixed<3, NN_, L_>(Rs, Ys, t, mass, u, v, c, qv, xi, sq2); break;
+      case 0: basis_fixed<0, NN_, L_, GEN>(Rs, Ys, t, mass, u, v, c, qv, xi, sq2, sg); break;
+      case 1: basis_fixed<1, NN_, L_, GEN>(Rs, Ys, t, mass, u, v, c, qv, xi, sq2, sg); break;
+      case 2: basis_fixed<2, NN_, L_, GEN>(Rs, Ys, t, mass, u, v, c, qv, xi, sq2, sg); break;
+      default: basis_fixed<3, NN_, L_, GEN>(Rs, Ys, t, mass, u, v, c, qv, xi, sq2, sg); break;
     }
   }
 };
@@ -466,6 +478,9 @@ __global__ void __maxnreg__(128) k1_tiled(K1Args a) {
   // padding rows and the angular rows past 2l of each degree's last chunk are never written by the basis
   for (int i = tid; i < (TN - 1) * TPP; i += blockDim.x) Rs[rR * TPP + i] = 0.f;
   for (int i = tid; i < YCH * chunk_base(L + 1) * TPP; i += blockDim.x) Ys[i] = 0.f;
+  float* SG = Ys + YCH * chunk_base(L + 1) * TPP;  // [L + 1][NN] Gegenbauer steps (radial family alpha != 1)
+  if constexpr (B::kGen)
+    for (int i = tid; i < rR; i += blockDim.x) SG[i] = a.tab->gbetaf[i / NN][i % NN];
   __syncthreads();
 
   // contraction role: item (l, c, d) = output tile, sgrp = particle sub-group
@@ -541,10 +556,12 @@ __global__ void __maxnreg__(128) k1_tiled(K1Args a) {
       const float rinv = r > 0.f ? 1.f / r : 0.f;
       const float u = x * rinv, v = y * rinv, c = z * rinv;
       const float s = r * binv;
-      const float qv = 1.f / (1.f + s);
-      const float xi = 1.f - 2.f * qv;
+      // alpha != 1: t = s^(1/alpha) in q and xi, q^alpha in the prefactor
+      const float qq = 1.f / (1.f + (B::kGen ? powf(s, (float)a.inv_alpha) : s));
+      const float xi = 1.f - 2.f * qq;
+      const float qv = B::kGen ? powf(qq, (float)a.alpha) : qq;
       const float sq2 = s * qv * qv;
-      B::run(q, Rs, Ys, t, NN, L, mass, u, v, c, qv, xi, sq2);
+      B::run(q, Rs, Ys, t, NN, L, mass, u, v, c, qv, xi, sq2, SG);
     }
     __syncthreads();
     if (step && warp < 2 && lane < TP / 2) {  // chain set 0 writes the kicked and drifted state back
@@ -574,7 +591,7 @@ __global__ void __maxnreg__(128) k1_tiled(K1Args a) {
         }
       }
       if (++tiles == a.win_tiles || last) {
-        store_tile(acc, out + (size_t)win * 2 * a.nc, false, il, n0, mm0, NN, a.nlm, a.nc);
+        store_tile(acc, out + (size_t)win * 2 * a.nc, false, il, n0, mm0, NN, a.nlm, a.nc, B::kGen ? a.tab : nullptr);
         ++win;
         tiles = 0;
       }
@@ -582,7 +599,8 @@ __global__ void __maxnreg__(128) k1_tiled(K1Args a) {
     __syncthreads();
   }
   if (worker)  // windows this block did not fill (fewer tiles than the longest block)
-    for (; win < a.win; ++win) store_tile(acc, out + (size_t)win * 2 * a.nc, true, il, n0, mm0, NN, a.nlm, a.nc);
+    for (; win < a.win; ++win)
+      store_tile(acc, out + (size_t)win * 2 * a.nc, true, il, n0, mm0, NN, a.nlm, a.nc, B::kGen ? a.tab : nullptr);
 }
 
 template <class B>
@@ -594,9 +612,21 @@ struct K1Tiled {
 };
 
 // Shapes with a compile-time basis: (nmax, lmax) = (20, 10), (20, 8), (10, 6);
-// every other shape runs the runtime-indexed basis.
+// every other shape runs the runtime-indexed basis, and so does a radial
+// family with alpha != 1 (gen), whose steps come from the handle's tables.
 template <typename F>
-auto dispatch_tiled(int nmax, int lmax, F&& f) {
+auto dispatch_tiled(int nmax, int lmax, F&& f, bool gen = false) {
+  if (gen) {
+    if (nmax == 20 && lmax == 10) return f(K1Tiled<BasisFixed<21, 10, true>>());
+    if (nmax == 20 && lmax == 8) return f(K1Tiled<BasisFixed<21, 8, true>>());
+    if (nmax == 10 && lmax == 6) return f(K1Tiled<BasisFixed<11, 6, true>>());
+    switch ((lmax + 4) / 4) {
+      case 1: return f(K1Tiled<BasisGeneric<1, true>>());
+      case 2: return f(K1Tiled<BasisGeneric<2, true>>());
+      case 3: return f(K1Tiled<BasisGeneric<3, true>>());
+      default: return f(K1Tiled<BasisGeneric<4, true>>());
+    }
+  }
   if (nmax == 20 && lmax == 10) return f(K1Tiled<BasisFixed<21, 10>>());
   if (nmax == 20 && lmax == 8) return f(K1Tiled<BasisFixed<21, 8>>());
   if (nmax == 10 && lmax == 6) return f(K1Tiled<BasisFixed<11, 6>>());
@@ -861,7 +891,7 @@ cudaError_t scf_k1_gen_prepare(int precision, int lmax, int nmax, ScfLaunchInfo*
   return k1_prepare_t<double, true>(lmax, nmax, 128, info, blocks_per_sm);
 }
 
-cudaError_t scf_k1_tiled_prepare(int lmax, int nmax, ScfLaunchInfo* info, int* blocks_per_sm) {
+cudaError_t scf_k1_tiled_prepare(int lmax, int nmax, ScfLaunchInfo* info, int* blocks_per_sm, bool gen) {
   using namespace tiled;
   const int items = n_items(nmax, lmax);
   if (items > MAX_THREADS) return cudaErrorInvalidConfiguration;
@@ -873,7 +903,7 @@ cudaError_t scf_k1_tiled_prepare(int lmax, int nmax, ScfLaunchInfo* info, int* b
   info->variant = 1;
   info->win = 1;  // set from the block map by the caller (scf_k1_windows)
   info->win_tiles = WINDOW_TILES;
-  info->smem = smem_bytes(nmax, lmax);
+  info->smem = smem_bytes(nmax, lmax, gen);
   if (info->smem > 227 * 1024) return cudaErrorInvalidConfiguration;
   return dispatch_tiled(nmax, lmax, [&](auto k) -> cudaError_t {
     using KK = decltype(k);
@@ -883,7 +913,7 @@ cudaError_t scf_k1_tiled_prepare(int lmax, int nmax, ScfLaunchInfo* info, int* b
     e = cudaFuncSetAttribute(KK::fn(), cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared);
     if (e != cudaSuccess) return e;
     return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, KK::fn(), info->threads, info->smem);
-  });
+  }, gen);
 }
 
 int scf_k1_windows(int64_t max_particles_per_block, const ScfLaunchInfo& info) {
@@ -901,7 +931,7 @@ cudaError_t scf_k1_launch(int precision, const K1Args& a, int blocks, const ScfL
     tiled::dispatch_tiled(a.nmax, a.lmax, [&](auto k) -> int {
       decltype(k)::launch(b, blocks, info.threads, info.smem, s);
       return 0;
-    });
+    }, a.tab != nullptr);
     return cudaGetLastError();
   }
   auto go = [&](auto k) -> int {

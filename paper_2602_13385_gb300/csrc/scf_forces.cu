@@ -44,7 +44,9 @@ template <typename T> __device__ __forceinline__ T tgbeta(int l, int n) { return
 template <typename T> __device__ __forceinline__ T thbeta(int l, int n) { return sizeof(T) == 8 ? (T)c_tab.hbeta[l][n] : (T)c_tab.hbetaf[l][n]; }
 
 // Radial family of exponent alpha != 1 (GEN): recurrence steps from the
-// handle's tables in device memory instead of the constant bank.
+// handle's tables in device memory (read-only cache; warp-uniform addresses)
+// instead of the constant bank.  (Staging them in shared memory per block
+// measured slower: more registers, one block fewer per SM.)
 template <typename T, bool GEN>
 __device__ __forceinline__ T k3_gbeta(const K3Args& a, int l, int n) {
   if constexpr (GEN) return sizeof(T) == 8 ? (T)__ldg(&a.tab->gbeta[l][n]) : (T)__ldg(&a.tab->gbetaf[l][n]);

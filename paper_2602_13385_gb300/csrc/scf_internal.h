@@ -197,7 +197,9 @@ cudaError_t scf_k1_prepare(int precision, int lmax, int nmax, int tp, ScfLaunchI
 // tiles; info->variant = 3.
 cudaError_t scf_k1_gen_prepare(int precision, int lmax, int nmax, ScfLaunchInfo* info, int* blocks_per_sm);
 // Register-tiled single-precision kernel 1 (info->variant = 1).
-cudaError_t scf_k1_tiled_prepare(int lmax, int nmax, ScfLaunchInfo* info, int* blocks_per_sm);
+// gen: the radial family of exponent alpha != 1 (runtime steps from K1Args::tab,
+// which the launch then requires).
+cudaError_t scf_k1_tiled_prepare(int lmax, int nmax, ScfLaunchInfo* info, int* blocks_per_sm, bool gen = false);
 // Windows per block of the register-tiled kernel for a block map whose
 // longest block has the given number of particles.
 int scf_k1_windows(int64_t max_particles_per_block, const ScfLaunchInfo& info);

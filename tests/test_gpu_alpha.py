@@ -151,9 +151,14 @@ def test_mixed_matches_oracle(scf, alpha, nmax, lmax, n):
     b = workloads.basis_scale(workloads.half_mass_radius(wl.pos), alpha)
     host = oracle.host_struct(wl.host)
     sim = make(scf, nmax, lmax, b, alpha, n=n, host=wl.host, precision="mixed")
+    assert sim.tiles()["k1_tile"] == 0            # the register-tiled kernel by default
     A = sim.coeffs(dev(wl.pos, torch.float32)).cpu().numpy()[0]
     A_ref = oracle.coeffs(p32, nmax, lmax, b, alpha=alpha)
     eA = biorth_err(A, A_ref, nmax, lmax, alpha)
+    sim.set_tiles(k1_tile=128)                     # and the one-thread-per-output kernel
+    A_simple = sim.coeffs(dev(wl.pos, torch.float32)).cpu().numpy()[0]
+    assert biorth_err(A_simple, A_ref, nmax, lmax, alpha) < 1e-6
+    sim.set_tiles(k1_tile=0)
     acc = sim.forces(dev(wl.pos, torch.float32), dev(A_ref[None]), com=dev(wl.com[None])).cpu().double().numpy()
     ref = oracle.forces(p32, A_ref, nmax, lmax, b, com=wl.com, host=host, alpha=alpha)
     e = acc_err(acc, ref)
@@ -186,6 +191,7 @@ def test_alpha_options_and_limits(scf):
     from paper_2602_13385_gb300 import _lib
     sim = make(scf, 10, 6, 0.3, 0.5, n=1000)
     for kw in ({"k1_tile": 64}, {"k1_tile": 0}, {"k3_block": 256}, {"k3_variant": 1}, {"k1_variant": 2}):
+        # (k1_tile 0, the register-tiled kernel, is single precision only)
         with pytest.raises(_lib.ScfError):
             sim.set_tiles(**kw)
     assert sim.tiles()["k1_tile"] == 128 and sim.tiles()["k3_block"] == 128
