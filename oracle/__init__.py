@@ -81,6 +81,7 @@ def _load():
         "or_rho_nl": (d, [i, i, d, d, d]),
         "or_coeffs": (None, [i64, p, p, i, i, d, d, p]),
         "or_field": (None, [i64, p, p, i, i, d, d, d, p]),
+        "or_density": (None, [i64, p, p, i, i, d, d, p]),
         "or_host_accel": (None, [p, p, p, p]),
         "or_tidal": (None, [p, p, p, p]),
         "or_tidal_tensor": (None, [p, i64, p, p]),
@@ -203,6 +204,15 @@ def field(pos, A, nmax, lmax, b, G=1.0, alpha=1.0):
     out = np.zeros((pos.shape[0], 4))
     _load().or_field(pos.shape[0], _ptr(pos), _ptr(A), int(nmax), int(lmax), float(b), float(alpha), float(G),
                      _ptr(out))
+    return out
+
+
+def density(pos, A, nmax, lmax, b, alpha=1.0):
+    """Mass density of the expansion (Eq. 1b) at ``pos[:, :3]`` -> (N,)."""
+    pos = _f64(pos)
+    A = _f64(A)
+    out = np.zeros(pos.shape[0])
+    _load().or_density(pos.shape[0], _ptr(pos), _ptr(A), int(nmax), int(lmax), float(b), float(alpha), _ptr(out))
     return out
 
 
@@ -433,6 +443,86 @@ def evolve(pos, vel, acc, nmax, lmax, b, dt, nsteps, G=1.0, com=None, host=None,
         done += k
         n_int += 1
     return pos, vel, acc, com, bound, mask, stats, n_int, b
+
+
+# ---------------------------------------------------------------- re-centring (Sec. 2.1)
+def a000_profile(s, alpha=1.0):
+    """g(s) = (1 + s^(1/alpha))^-alpha = -b U_00(r): the radial profile of the
+    lowest-order potential (Eq. 4), s = r/b."""
+    s = np.asarray(s, dtype=np.float64)
+    return (1.0 + s ** (1.0 / alpha)) ** -alpha
+
+
+def expansion_centre(pos, b, alpha=1.0, mask=None, tol=1e-12, max_iter=100):
+    """The point x_c at which a_000 of the particles' expansion is largest
+    (Sec. 2.1: the SCF centre), the expansion taken about x_c with alpha and b
+    fixed, over the coefficient set (``mask``; all particles if None).
+
+    a_000 is a positive multiple of F(x_c) = sum_k m_k g(|x_k - x_c| / b) (the
+    lowest basis function is -g/b times a constant, its normalisation I_00 < 0),
+    so x_c solves grad F = 0, i.e. sum_k m_k w_k (x_k - x_c) = 0 with
+    w_k = -g'(s_k)/s_k = t_k (1 + t_k)^(-alpha-1) / s_k^2, t = s^(1/alpha).  The
+    iteration x_c <- sum m w x / sum m w from x_c = 0 (the current centre)
+    climbs F (a mean-shift step); it stops when the step is below tol * b or
+    after max_iter steps.  s_k^2 is floored at 1e-300 (a particle on x_c: the
+    iteration has arrived there).  Returns (x_c, iterations)."""
+    pos = _f64(pos)
+    sel = np.ones(pos.shape[0], bool) if mask is None else np.asarray(mask, bool)
+    x, m = pos[sel, :3], pos[sel, 3]
+    xc = np.zeros(3)
+    it = 0
+    for it in range(1, max_iter + 1):
+        d = x - xc
+        s2 = np.maximum((d[:, 0] * d[:, 0] + d[:, 1] * d[:, 1] + d[:, 2] * d[:, 2]) / (b * b), 1e-300)
+        s = np.sqrt(s2)
+        t = s ** (1.0 / alpha)
+        w = m * t * (1.0 + t) ** (-alpha - 1.0) / s2
+        new = (w[:, None] * x).sum(axis=0) / w.sum()
+        step = np.sqrt(np.sum((new - xc) ** 2))
+        xc = new
+        if step <= tol * b:
+            break
+    return xc, it
+
+
+def core_frame(pos, vel, A, nmax, lmax, b, alpha=1.0):
+    """Core radius and core velocity about the current centre (Sec. 2.1):
+    r_core^2 = sum_i rho_i^2 r_i^2 / sum_i rho_i^2 with rho_i the expansion's
+    density at each particle (:func:`density`; particles at r = 0, where a
+    cusped rho is infinite, are left out of both sums), and the frame velocity
+    = the mass-weighted mean velocity of the particles with r < r_core.
+    Returns (r_core, V_core)."""
+    pos = _f64(pos)
+    vel = _f64(vel)
+    rho = density(pos, A, nmax, lmax, b, alpha)
+    r2 = pos[:, 0] * pos[:, 0] + pos[:, 1] * pos[:, 1] + pos[:, 2] * pos[:, 2]
+    ok = r2 > 0.0
+    w = rho[ok] * rho[ok]
+    rc2 = float((w * r2[ok]).sum() / w.sum()) if w.sum() > 0 else 0.0
+    core = r2 < rc2
+    mc = pos[core, 3]
+    V = (mc[:, None] * vel[core, :3]).sum(axis=0) / mc.sum() if mc.sum() > 0 else np.zeros(3)
+    return float(np.sqrt(rc2)), V
+
+
+def recentre(pos, vel, com, nmax, lmax, b, alpha=1.0, mask=None, tol=1e-12, max_iter=100):
+    """Moves the cluster frame to the SCF centre with the core velocity
+    (Sec. 2.1): x_c of :func:`expansion_centre`, then the coefficients of the
+    set about x_c, then :func:`core_frame` about x_c; particles are shifted by
+    (-x_c, -V_core) and the centre by (+x_c, +V_core), so host-frame positions
+    and velocities are unchanged.  Returns (pos, vel, com, x_c, V_core, r_core,
+    iterations)."""
+    pos = _f64(pos).copy()
+    vel = _f64(vel).copy()
+    com = np.zeros(6) if com is None else _f64(com).copy()
+    xc, it = expansion_centre(pos, b, alpha, mask, tol, max_iter)
+    pos[:, :3] -= xc
+    com[:3] += xc
+    A = coeffs(pos, nmax, lmax, b, mask=mask, alpha=alpha)
+    rc, V = core_frame(pos, vel, A, nmax, lmax, b, alpha)
+    vel[:, :3] -= V
+    com[3:] += V
+    return pos, vel, com, xc, V, rc, it
 
 
 def power_l(A, nmax, lmax, b, alpha=1.0):

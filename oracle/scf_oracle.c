@@ -343,6 +343,29 @@ void or_field(int64_t n_part, const double* pos, const double* A, int nmax, int 
   for (int64_t k = 0; k < n_part; ++k) field_one(pos + 4 * k, A, nmax, lmax, b, alpha, G, acc + 4 * k);
 }
 
+/* Density of the expansion (Eq. 1b) at each point:
+ *   rho(x) = sum_nl rho_nl(r) sum_m P_l^m(cos th) [S_nlm cos(m ph) + T_nlm sin(m ph)]
+ * (mass density: no G).  Infinite at r = 0 where rho_00 has a cusp (alpha > 1/2). */
+void or_density(int64_t n_part, const double* pos, const double* A, int nmax, int lmax, double b, double alpha,
+                double* rho) {
+  const int nlm = nlm_count(lmax), nc = (nmax + 1) * nlm;
+#pragma omp parallel for schedule(static)
+  for (int64_t k = 0; k < n_part; ++k) {
+    double r, costh, sinth, phi;
+    sph(pos[4 * k], pos[4 * k + 1], pos[4 * k + 2], &r, &costh, &sinth, &phi);
+    double sum = 0.0;
+    for (int l = 0; l <= lmax; ++l)
+      for (int n = 0; n <= nmax; ++n) {
+        const double rnl = or_rho_nl(n, l, b, alpha, r);
+        for (int m = 0; m <= l; ++m) {
+          const int i = n * nlm + lm_index(l, m);
+          sum += rnl * plm_cs(l, m, costh, sinth) * (A[i] * cos(m * phi) + A[nc + i] * sin(m * phi));
+        }
+      }
+    rho[k] = sum;
+  }
+}
+
 /* ------------------------------------------------------------------------ */
 /* Host potential (App. A): Hernquist, NFW, Miyamoto-Nagai                  */
 /* ------------------------------------------------------------------------ */

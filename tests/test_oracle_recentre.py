@@ -1,0 +1,143 @@
+"""Pins of the oracle's re-centring (Sec. 2.1): the SCF centre at the maximum
+of a_000, the expansion's density, the core radius and the core velocity.
+
+* a sample symmetric under the eight reflections about a point c has its
+  centre exactly at c, and its core velocity is the bulk velocity added to
+  velocities reflected with the positions;
+* the centre is a stationary point and a local maximum of a_000, which is
+  computed here directly from the coefficient pass (S_000 of the particles
+  shifted by -x_c), not from the iteration's profile;
+* the expansion's density is the Zhao lowest-order density for the projected
+  lowest-order sphere (Plummer at alpha = 1/2, Hernquist at alpha = 1) and
+  equals the Laplacian of the potential over 4 pi (Eq. 1b against Eq. 1a) for
+  a general expansion, by finite differences;
+* the core radius of a Plummer sample in its own basis (alpha = 1/2, b = a)
+  is that of the Plummer density, r_core^2 = int rho^3 r^4 dr / int rho^3 r^2 dr
+  = 0.3 a^2, within sampling noise;
+* re-centring leaves host-frame positions and velocities unchanged.
+"""
+import math
+
+import numpy as np
+import pytest
+from scipy import special
+
+import oracle
+import workloads
+
+
+def _a000(pos, xc, b, alpha, mask=None):
+    p = pos.copy()
+    p[:, :3] -= xc
+    return oracle.coeffs(p, 0, 0, b, mask=mask, alpha=alpha)[0]
+
+
+def _symmetric(n, seed, c, V0):
+    pos, vel = workloads.plummer(n, seed=seed)
+    P, V = [], []
+    for sx in (1, -1):
+        for sy in (1, -1):
+            for sz in (1, -1):
+                sgn = np.array([sx, sy, sz])
+                q, u = pos.copy(), vel.copy()
+                q[:, :3] *= sgn
+                u[:, :3] *= sgn
+                q[:, 3] /= 8
+                P.append(q)
+                V.append(u)
+    P, V = np.concatenate(P), np.concatenate(V)
+    P[:, :3] += c
+    V[:, :3] += V0
+    return P, V
+
+
+@pytest.mark.parametrize("alpha", [0.5, 1.0, 1.5])
+def test_symmetric_sample_centre_and_core_velocity(alpha):
+    c, V0 = np.array([0.11, -0.05, 0.023]), np.array([0.3, -0.2, 0.1])
+    pos, vel = _symmetric(3000, 21, c, V0)
+    xc, it = oracle.expansion_centre(pos, 0.3, alpha)
+    assert np.allclose(xc, c, rtol=0, atol=1e-12)
+    p2, v2, com, xc2, V, rc, _ = oracle.recentre(pos, vel, np.zeros(6), 6, 4, 0.3, alpha)
+    assert np.allclose(V, V0, rtol=0, atol=1e-12)
+    assert 0.0 < rc < 1.0
+
+
+@pytest.mark.parametrize("alpha", [0.5, 1.0])
+def test_centre_is_the_maximum_of_a000(alpha):
+    pos, _ = workloads.plummer(5000, seed=22)
+    pos[:, :3] += np.array([0.05, 0.02, -0.04])
+    b = 0.3
+    mask = np.arange(pos.shape[0]) % 7 != 3
+    xc, it = oracle.expansion_centre(pos, b, alpha, mask=mask)
+    assert it < 100
+    a0 = _a000(pos, xc, b, alpha, mask)
+    rng = np.random.default_rng(3)
+    for _ in range(12):
+        d = rng.normal(size=3)
+        d *= 1e-3 * b / np.linalg.norm(d)
+        assert _a000(pos, xc + d, b, alpha, mask) < a0
+    if alpha != 1.0:   # smooth profile: the gradient vanishes (central differences)
+        h = 1e-5 * b
+        g = [(_a000(pos, xc + h * e, b, alpha, mask) - _a000(pos, xc - h * e, b, alpha, mask)) / (2 * h)
+             for e in np.eye(3)]
+        assert np.max(np.abs(g)) < 1e-7 * a0 / b
+
+
+def _zhao_sphere(b, alpha, nodes=80):
+    x, w = special.roots_jacobi(nodes, alpha, alpha)
+    p = 0.5 * (x + 1)
+    pos = np.zeros((nodes, 4))
+    pos[:, 0] = b * (p / (1 - p)) ** alpha
+    pos[:, 3] = (alpha + 1) * 2.0 ** (-2 * alpha - 1) * w / (1 - p) ** alpha
+    return pos
+
+
+def test_density_of_the_lowest_order_spheres():
+    pts = np.random.default_rng(4).normal(size=(10, 4))
+    r = np.linalg.norm(pts[:, :3], axis=1)
+    b = 0.45
+    A = oracle.coeffs(_zhao_sphere(b, 0.5), 6, 0, b, alpha=0.5)          # Plummer
+    assert np.allclose(oracle.density(pts, A, 6, 0, b, 0.5), 3 / (4 * math.pi * b ** 3) * (1 + (r / b) ** 2) ** -2.5,
+                       rtol=1e-10)
+    A = oracle.coeffs(_zhao_sphere(b, 1.0), 6, 0, b, alpha=1.0)          # Hernquist
+    assert np.allclose(oracle.density(pts, A, 6, 0, b, 1.0), b / (2 * math.pi * r * (r + b) ** 3), rtol=1e-10)
+
+
+@pytest.mark.parametrize("alpha", [0.5, 1.0, 1.7])
+def test_density_is_laplacian_of_potential(alpha):
+    nmax, lmax, b = 5, 4, 0.4
+    pos, _ = workloads.plummer(400, seed=23)
+    A = oracle.coeffs(pos, nmax, lmax, b, alpha=alpha)
+    pts = np.array([[0.3, -0.2, 0.5, 0], [0.7, 0.1, -0.2, 0], [-0.1, 0.45, 0.3, 0]])
+    rho = oracle.density(pts, A, nmax, lmax, b, alpha)
+    h = 2e-3
+    for k in range(len(pts)):
+        lap = 0.0
+        for d in range(3):
+            def pot(dx):
+                p = pts[k:k + 1].copy()
+                p[0, d] += dx
+                return oracle.field(p, A, nmax, lmax, b, alpha=alpha)[0, 3]
+            lap += (-pot(2 * h) + 16 * pot(h) - 30 * pot(0) + 16 * pot(-h) - pot(-2 * h)) / (12 * h * h)
+        assert lap == pytest.approx(4 * math.pi * rho[k], rel=1e-6)
+
+
+def test_plummer_core_radius():
+    n, a = 200000, 3 * math.pi / 16     # Henon-unit Plummer scale
+    pos, vel = workloads.plummer(n, seed=24)
+    A = oracle.coeffs(pos, 6, 0, a, alpha=0.5)
+    rc, V = oracle.core_frame(pos, vel, A, 6, 0, a, 0.5)
+    print(f"Plummer r_core / a = {rc / a:.4f} (density of the Plummer sphere: sqrt(0.3) = {math.sqrt(0.3):.4f})")
+    assert rc / a == pytest.approx(math.sqrt(0.3), rel=0.02)
+    assert np.linalg.norm(V) < 0.05       # an isotropic sample at rest
+
+
+def test_recentre_keeps_host_frame_state():
+    pos, vel = workloads.plummer(3000, seed=25)
+    pos[:, :3] += 0.07
+    vel[:, :3] += 0.02
+    com = np.array([10.0, -3.0, 1.0, 0.1, 0.2, -0.3])
+    p2, v2, c2, xc, V, rc, it = oracle.recentre(pos, vel, com, 8, 4, 0.3, 1.0)
+    assert np.allclose(p2[:, :3] + c2[:3], pos[:, :3] + com[:3], rtol=0, atol=1e-13)
+    assert np.allclose(v2[:, :3] + c2[3:], vel[:, :3] + com[3:], rtol=0, atol=1e-14)
+    assert np.linalg.norm(xc - 0.07) < 0.1 and np.linalg.norm(V - 0.02) < 0.2   # sampling noise of the core
