@@ -345,7 +345,39 @@ typedef struct scf_escape_params {
                         has half its mass inside r_50, the energy-based Lagrange
                         radius of half the bound stars: b = r_50 (2^(1/(alpha+1)) - 1)^alpha
                         (r_50 / (1 + sqrt 2) at alpha = 1) */
+  int recentre;      /* 1: at each complete refresh, first scf_recentre (the SCF centre
+                        and core velocity, 100 iterations at most, step tolerance
+                        1e-12 b) with the current coefficient set, then scf_bound again
+                        in the new frame; 0: the frame stays on the centre orbit */
 } scf_escape_params;
+
+/* Re-centring of the cluster frame (Sec. 2.1).  For every progenitor:
+ * 1. the SCF centre x_c, where a_000 of the expansion about x_c (alpha, b fixed)
+ *    is largest: a_000 is a positive multiple of sum_k m_k g(|x_k - x_c|/b),
+ *    g(s) = (1 + s^(1/alpha))^-alpha, summed over the coefficient set (mask;
+ *    NULL = all particles), and x_c is reached by the fixed-point (mean-shift)
+ *    iteration x_c += sum m w (x_k - x_c) / sum m w, w = t (1+t)^(-alpha-1) / s^2,
+ *    t = s^(1/alpha), from x_c = 0, until the step is <= tol * b or after
+ *    max_iter steps; every particle is then shifted by -x_c;
+ * 2. the core radius r_core^2 = sum_i rho_i^2 r_i^2 / sum_i rho_i^2 over all
+ *    particles (rho_i the density of the set's expansion about x_c, Eq. 1b;
+ *    particles at r = 0 left out) and the core velocity V_core = the
+ *    mass-weighted mean velocity of the particles with r < r_core; every
+ *    velocity is then shifted by -V_core;
+ * 3. com (nullable) += (x_c, V_core), so host-frame positions and velocities
+ *    are unchanged and the centre orbit continues from the new centre.
+ *   pos, vel  device particles, shifted in place;  acc  device [N][4], used as
+ *             scratch (overwritten; recompute the field before the next step);
+ *   mask      device, one byte per particle, or NULL;
+ *   max_iter  1..1000;  tol >= 0 (relative to b);
+ *   out       host [n_prog][8] = (x_c, V_core, r_core, iterations), or NULL
+ *             (then nothing is synchronised).
+ * Sums in double precision in a fixed order (weights in the handle's
+ * precision): reproducible bit for bit.  The handle's coefficients (scf_last_coeffs)
+ * are those of the set about the new centre.
+ * Errors: SCF_ERR_NULL_POINTER, SCF_ERR_MISALIGNED, SCF_ERR_INVALID_ARG, SCF_ERR_CUDA. */
+int scf_recentre(scf_handle* h, void* pos, void* vel, void* acc, double* com, const uint8_t* mask, int max_iter,
+                 double tol, double* out);
 
 /* nsteps leapfrog steps with the escape physics of Sec. 2.2.  At the start of
  * every integration timestep: scf_bound (bound flags, the mask r <= r_x and

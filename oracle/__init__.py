@@ -397,11 +397,14 @@ def zhao_half_mass_scale(r50, alpha=1.0):
 
 
 def evolve(pos, vel, acc, nmax, lmax, b, dt, nsteps, G=1.0, com=None, host=None, kin=0.5, frac=0.999,
-           eta=1.0 / 400.0, max_steps=1000, retune_every=0, alpha=1.0):
+           eta=1.0 / 400.0, max_steps=1000, retune_every=0, alpha=1.0, recentre=False):
     """Leapfrog with the escape physics of Sec. 2.2.  At the start of every
     integration timestep: the boundedness test and the coefficient set
     r <= r_x (:func:`boundedness`); at every ``retune_every``-th integration
-    timestep (the first included; 0 = never) a complete refresh, which
+    timestep (the first included; 0 = never) a complete refresh, which (with
+    ``recentre``) first moves the frame to the SCF centre and core velocity
+    (:func:`recentre`, over the coefficient set) and takes the boundedness
+    again in it, then
     retunes the basis scale b (alpha fixed) to the scale of the lowest-order
     density whose half-mass radius is the bound stars' energy-based one,
     :func:`zhao_half_mass_scale` (alpha = 1: b = r_50 / (1 + sqrt 2)); the field
@@ -425,9 +428,14 @@ def evolve(pos, vel, acc, nmax, lmax, b, dt, nsteps, G=1.0, com=None, host=None,
     while done < nsteps:
         E, bound, rx2, mask, Mb = boundedness(pos, vel, G, kin, frac)
         stats = np.array([bound.sum(), Mb, np.sqrt(rx2), mask.sum()], dtype=np.float64)
-        if retune_every > 0 and n_int % retune_every == 0 and bound.any():
-            r50 = np.sqrt(boundedness(pos, vel, G, kin, 0.5)[2])
-            b = zhao_half_mass_scale(r50, alpha)
+        if retune_every > 0 and n_int % retune_every == 0:
+            if recentre:   # the frame to the SCF centre and core velocity, boundedness again in it
+                pos, vel, com, _, _, _, _ = _recentre_frame(pos, vel, com, nmax, lmax, b, alpha, mask=mask)
+                E, bound, rx2, mask, Mb = boundedness(pos, vel, G, kin, frac)
+                stats = np.array([bound.sum(), Mb, np.sqrt(rx2), mask.sum()], dtype=np.float64)
+            if bound.any():
+                r50 = np.sqrt(boundedness(pos, vel, G, kin, 0.5)[2])
+                b = zhao_half_mass_scale(r50, alpha)
         A = coeffs(pos, nmax, lmax, b, mask=mask, alpha=alpha)
         acc = forces(pos, A, nmax, lmax, b, G, com=com if has_host else None, host=host if has_host else None,
                      alpha=alpha)
@@ -438,8 +446,10 @@ def evolve(pos, vel, acc, nmax, lmax, b, dt, nsteps, G=1.0, com=None, host=None,
             if ks < k:
                 k = 1 if ks < 1 else int(ks)
         k = min(k, nsteps - done)
-        pos, vel, acc, com, _ = step(pos, vel, acc, nmax, lmax, b, dt, k, G, com=com if has_host else None,
-                                     host=host if has_host else None, mask=mask, alpha=alpha)
+        pos, vel, acc, c2, _ = step(pos, vel, acc, nmax, lmax, b, dt, k, G, com=com if has_host else None,
+                                    host=host if has_host else None, mask=mask, alpha=alpha)
+        if has_host:    # without a host the centre is not integrated (it keeps the re-centring offsets)
+            com = c2
         done += k
         n_int += 1
     return pos, vel, acc, com, bound, mask, stats, n_int, b
@@ -523,6 +533,9 @@ def recentre(pos, vel, com, nmax, lmax, b, alpha=1.0, mask=None, tol=1e-12, max_
     vel[:, :3] -= V
     com[3:] += V
     return pos, vel, com, xc, V, rc, it
+
+
+_recentre_frame = recentre   # (evolve's keyword of the same name shadows it there)
 
 
 def power_l(A, nmax, lmax, b, alpha=1.0):

@@ -29,6 +29,7 @@ struct scf_handle {
   bool k1_ff = false;  // double-precision handles: float-float kernel 1
   bool gen = false;    // radial family of exponent alpha != 1: the general kernels 1 and 3
   ScfConst* d_tab = nullptr;  // their recurrence tables (device memory; gen handles only)
+  double* d_rc = nullptr;     // [n_prog][16] re-centring state (scf_recentre)
   int k1_blocks = 0;
   int* d_blk1_prog = nullptr;
   int64_t* d_blk1_begin = nullptr;
@@ -108,6 +109,10 @@ int upload_tables_once(int device) {
 }
 
 bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
+
+// Re-centring at complete refreshes (scf_evolve): iteration cap and step tolerance.
+constexpr int kRecentreIters = 100;
+constexpr double kRecentreTol = 1e-12;
 
 // The general kernels read these entries for l <= lmax, n <= nmax; in single
 // precision (f32) the scales and ratios must also stay finite and non-zero.
@@ -546,6 +551,7 @@ int scf_init(const scf_config* cfg, int n_prog, const int64_t* offsets, const do
   const size_t o_k2z = take(sizeof(double) * kK2MaxChunks * 2 * (size_t)h->nc * n_prog);
   const size_t o_k2c = take(sizeof(unsigned) * (size_t)scf_k2_groups(h->nc) * n_prog);
   const size_t o_tab = h->gen ? take(sizeof(ScfConst)) : off;
+  const size_t o_rc = take(sizeof(double) * 16 * (size_t)n_prog);
   if (cudaMalloc(&h->d_base, off) != cudaSuccess) {
     cudaGetLastError();
     return fail(SCF_ERR_OUT_OF_MEMORY);
@@ -575,6 +581,7 @@ int scf_init(const scf_config* cfg, int n_prog, const int64_t* offsets, const do
   h->d_half = reinterpret_cast<double*>(base + o_half);
   h->d_k2z = reinterpret_cast<double*>(base + o_k2z);
   h->d_k2cnt = reinterpret_cast<unsigned*>(base + o_k2c);
+  h->d_rc = reinterpret_cast<double*>(base + o_rc);
 
   if (h->gen) {  // recurrence tables of the handle's radial family
     h->d_tab = reinterpret_cast<ScfConst*>(base + o_tab);
@@ -958,7 +965,8 @@ int scf_evolve(scf_handle* h, void* pos, void* vel, void* acc, double* com, int 
   if (!aligned16(pos) || !aligned16(vel) || !aligned16(acc)) return SCF_ERR_MISALIGNED;
   if (nsteps < 0 || ep->max_steps < 1 || !(ep->eta > 0.0) || !std::isfinite(ep->eta) || !(h->cfg.dt > 0.0))
     return SCF_ERR_INVALID_ARG;
-  if (!(ep->kin > 0.0) || !std::isfinite(ep->kin) || !(ep->frac > 0.0 && ep->frac <= 1.0) || ep->retune_every < 0)
+  if (!(ep->kin > 0.0) || !std::isfinite(ep->kin) || !(ep->frac > 0.0 && ep->frac <= 1.0) || ep->retune_every < 0 ||
+      (ep->recentre != 0 && ep->recentre != 1))
     return SCF_ERR_INVALID_ARG;
   int rc = scf_set_mask(h, mask);
   if (rc != SCF_OK) return rc;
@@ -969,7 +977,14 @@ int scf_evolve(scf_handle* h, void* pos, void* vel, void* acc, double* com, int 
     rc = scf_bound(h, pos, vel, ep->kin, ep->frac, nullptr, bound, mask, stats);
     if (rc != SCF_OK) return rc;
     if (ep->retune_every > 0 && refreshes % ep->retune_every == 0) {
-      // complete refresh: b from the bound stars' half-mass radius (alpha fixed)
+      // complete refresh: the frame moved to the SCF centre and core velocity
+      // (boundedness again in the new frame), then b from the bound stars'
+      // half-mass radius (alpha fixed)
+      if (ep->recentre) {
+        rc = scf_recentre(h, pos, vel, acc, com, mask, kRecentreIters, kRecentreTol, nullptr);
+        if (rc == SCF_OK) rc = scf_bound(h, pos, vel, ep->kin, ep->frac, nullptr, bound, mask, stats);
+        if (rc != SCF_OK) return rc;
+      }
       BoundArgs a{};
       a.pos = pos;
       a.prog_off = h->d_off;
@@ -1011,6 +1026,64 @@ int scf_evolve(scf_handle* h, void* pos, void* vel, void* acc, double* com, int 
     ++refreshes;
   }
   if (n_refresh) *n_refresh = refreshes;
+  return SCF_OK;
+}
+
+int scf_recentre(scf_handle* h, void* pos, void* vel, void* acc, double* com, const uint8_t* mask, int max_iter,
+                 double tol, double* out) {
+  if (!h) return SCF_ERR_NULL_POINTER;
+  if ((!pos || !vel || !acc) && h->n_total > 0) return SCF_ERR_NULL_POINTER;
+  if (!aligned16(pos) || !aligned16(vel) || !aligned16(acc)) return SCF_ERR_MISALIGNED;
+  if (max_iter < 1 || max_iter > 1000 || !(tol >= 0.0) || !std::isfinite(tol)) return SCF_ERR_INVALID_ARG;
+  RecentreArgs a{};
+  a.pos = pos;
+  a.vel = vel;
+  a.acc = acc;
+  a.mask = mask;
+  a.blk_prog = h->d_blk3_prog;
+  a.blk_begin = h->d_blk3_begin;
+  a.blk_end = h->d_blk3_end;
+  a.n_blocks = h->k3_blocks;
+  a.n_prog = h->n_prog;
+  a.f32 = h->cfg.precision == SCF_MIXED;
+  a.b_prog = h->d_b;
+  a.alpha = h->cfg.alpha;
+  a.inv_alpha = 1.0 / h->cfg.alpha;
+  a.tol = tol;
+  a.part = h->d_en_part;
+  a.state = h->d_rc;
+  a.com = com;
+  // 1. the centre, particles shifted to it
+  if (cuda_fail(scf_centre_launch(a, max_iter, h->stream)) != SCF_OK) return SCF_ERR_CUDA;
+  // 2. the set's coefficients about it; the density's potential (K_nl A) in acc.w
+  int rc = run_coeffs(h, pos, nullptr, nullptr, mask, h->d_A, nullptr, SCF_MODE_COEFFS);
+  if (rc != SCF_OK) return rc;
+  if (cuda_fail(scf_scale_k_launch(h->d_A, h->d_k2z, h->cfg.nmax, h->cfg.lmax, h->n_prog, h->cfg.alpha,
+                                   h->stream)) != SCF_OK)
+    return SCF_ERR_CUDA;
+  rc = run_prep(h, h->d_k2z, nullptr);
+  if (rc == SCF_OK) rc = run_forces(h, pos, nullptr, acc, nullptr, SCF_MODE_COEFFS);
+  if (rc != SCF_OK) return rc;
+  // 3. core radius and velocity, the frame moved to (x_c, V_core)
+  if (cuda_fail(scf_core_launch(a, h->stream)) != SCF_OK) return SCF_ERR_CUDA;
+  if (!out) return SCF_OK;
+  std::vector<double> st(16 * (size_t)h->n_prog);
+  if (cudaMemcpyAsync(st.data(), h->d_rc, sizeof(double) * st.size(), cudaMemcpyDeviceToHost, h->stream) !=
+          cudaSuccess ||
+      cudaStreamSynchronize(h->stream) != cudaSuccess)
+    return SCF_ERR_CUDA;
+  for (int p = 0; p < h->n_prog; ++p) {
+    const double* s = st.data() + 16 * (size_t)p;
+    double* o = out + 8 * (size_t)p;
+    o[0] = s[0];
+    o[1] = s[1];
+    o[2] = s[2];
+    o[3] = s[6];
+    o[4] = s[7];
+    o[5] = s[8];
+    o[6] = std::sqrt(s[5]);
+    o[7] = s[3];
+  }
   return SCF_OK;
 }
 

@@ -159,6 +159,32 @@ struct EnergyArgs {
 };
 cudaError_t scf_energy_launch(const EnergyArgs& a, cudaStream_t s);
 
+// Re-centring (scf_recentre.cu): the SCF centre at the maximum of a_000 and the
+// core frame velocity, per kernel-3 block range with fixed-order sums.
+struct RecentreArgs {
+  void* pos;                 // [N][4], shifted in place by -x_c
+  void* vel;                 // [N][4], shifted in place by -V_core
+  const void* acc;           // acc.w = potential of the K_nl-scaled coefficients (core pass)
+  const uint8_t* mask;       // coefficient set of the centre iteration, or null
+  const int* blk_prog;
+  const int64_t* blk_begin;
+  const int64_t* blk_end;
+  int n_blocks, n_prog;
+  int f32;                   // float4 (mixed) or double4 particles
+  const double* b_prog;
+  double alpha, inv_alpha, tol;
+  double* part;              // [n_blocks][4] scratch
+  double* state;             // [n_prog][16]: x_c(3), iterations, converged, r_core^2, V_core(3)
+  double* com;               // [n_prog][6] or null: += (x_c, V_core)
+};
+// max_iter mean-shift iterations (converged progenitors skip), then x -= x_c.
+cudaError_t scf_centre_launch(const RecentreArgs& a, int max_iter, cudaStream_t s);
+// KA = K_nl A (every progenitor's [2 NC] row).
+cudaError_t scf_scale_k_launch(const double* A, double* KA, int nmax, int lmax, int n_prog, double alpha,
+                               cudaStream_t s);
+// r_core and V_core from acc.w, com += (x_c, V_core), v -= V_core.
+cudaError_t scf_core_launch(const RecentreArgs& a, cudaStream_t s);
+
 struct ScfLaunchInfo {
   int threads;   // threads per block
   int tile;      // particles per tile (block ranges are whole tiles)

@@ -1,0 +1,285 @@
+// Re-centring of the cluster frame (Sec. 2.1): the expansion centre is put
+// where a_000 is largest, and the frame velocity is the mass-weighted mean
+// velocity of the particles inside the core radius
+//   r_core^2 = sum_i rho_i^2 r_i^2 / sum_i rho_i^2,
+// rho_i the expansion's density at particle i.
+//
+// Centre.  a_000 of the particles' expansion about x_c (alpha, b fixed) is a
+// positive multiple of F(x_c) = sum_k m_k g(s_k), g(s) = (1 + s^(1/alpha))^-alpha,
+// s_k = |x_k - x_c| / b, so grad F = 0 reads sum_k m_k w_k (x_k - x_c) = 0 with
+// w_k = t_k (1 + t_k)^(-alpha-1) / s_k^2, t = s^(1/alpha).  Each iteration
+// (k_centre_blocks + k_centre_sum, launched max_iter times) moves x_c by
+// sum m w (x_k - x_c) / sum m w; a progenitor whose step fell below tol * b
+// stops (its later launches return at once).  Weights in the handle's
+// precision, sums in double.
+//
+// Core.  The density of degree-l, order-n radial pair is
+//   rho_nl = -Phi_nl K_nl s^(1/alpha - 2) q^2 / (4 pi b^2),   q = 1/(1 + t),
+// K_nl = (n + a_l)(n + a_l + 1)/alpha^2, a_l = (2l+1) alpha, so the density at a
+// particle is that per-particle factor times the potential of the coefficients
+// K_nl A_nlm, which kernel 3 evaluates (acc.w).  Only ratios of rho^2 enter
+// r_core, so the constant factor is dropped.  Particles at r = 0 (where a
+// cusped density is infinite) are left out of both sums.
+//
+// Every sum is a per-block row (kernel-3 block map, fixed shuffle tree) added
+// per progenitor in block order by one warp: deterministic.
+#include <cmath>
+
+#include "scf_device.cuh"
+#include "scf_internal.h"
+
+namespace {
+
+constexpr int kRcThreads = 128;
+constexpr int kRcWarps = kRcThreads / 32;
+
+// Fixed-order block sum of NV values per thread into part[blockIdx.x][0..NV).
+template <int NV>
+__device__ __forceinline__ void block_row(double (&v)[NV], double* part) {
+  __shared__ double s_w[kRcWarps][NV];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int i = 0; i < NV; ++i) {
+    double x = v[i];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+    if (lane == 0) s_w[warp][i] = x;
+  }
+  __syncthreads();
+  if (threadIdx.x < NV) {
+    double x = 0.0;
+#pragma unroll
+    for (int w = 0; w < kRcWarps; ++w) x += s_w[w][threadIdx.x];
+    part[(size_t)blockIdx.x * 4 + threadIdx.x] = x;
+  }
+}
+
+// One warp: the rows of progenitor p's blocks in block order (lane-strided,
+// then a fixed shuffle tree); every lane returns the totals.
+template <int NV>
+__device__ __forceinline__ void prog_sum(const RecentreArgs& a, int p, double (&v)[NV]) {
+  const int lane = threadIdx.x;
+#pragma unroll
+  for (int i = 0; i < NV; ++i) v[i] = 0.0;
+  for (int b = lane; b < a.n_blocks; b += 32) {
+    if (a.blk_prog[b] != p) continue;
+#pragma unroll
+    for (int i = 0; i < NV; ++i) v[i] += a.part[(size_t)b * 4 + i];
+  }
+#pragma unroll
+  for (int i = 0; i < NV; ++i)
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v[i] += __shfl_xor_sync(0xffffffffu, v[i], o);
+}
+
+// Mean-shift weight t (1+t)^(-alpha-1) / s^2 of a squared distance s2 = s^2.
+template <typename T>
+__device__ __forceinline__ T centre_weight(T s2, double alpha, double inv_alpha) {
+  if (sizeof(T) == 4) s2 = fmax(s2, (T)1e-30f);  // the double floor (1e-300) underflows in float
+  if (alpha == 1.0) {
+    const T s = sqrt(s2), q = (T)1 / ((T)1 + s);
+    return q * q / s;  // t = s: s / (1+s)^2 / s^2
+  }
+  const T s = sqrt(s2), t = pow(s, (T)inv_alpha);
+  return t * pow((T)1 + t, (T)(-alpha - 1.0)) / s2;
+}
+
+template <typename V4, typename T>
+__global__ void __launch_bounds__(kRcThreads) k_centre_blocks(RecentreArgs a) {
+  const int p = a.blk_prog[blockIdx.x];
+  const double* st = a.state + 16 * (size_t)p;
+  if (st[4] != 0.0) return;  // converged (the sum kernel skips it too)
+  const double xc = st[0], yc = st[1], zc = st[2];
+  const double b = a.b_prog[p], ib2 = 1.0 / (b * b);
+  const V4* pos = reinterpret_cast<const V4*>(a.pos);
+  double v[4] = {0.0, 0.0, 0.0, 0.0};
+  const int64_t end = a.blk_end[blockIdx.x];
+  for (int64_t k = a.blk_begin[blockIdx.x] + threadIdx.x; k < end; k += kRcThreads) {
+    if (a.mask && !a.mask[k]) continue;
+    const V4 q = pos[k];
+    const double dx = (double)q.x - xc, dy = (double)q.y - yc, dz = (double)q.z - zc;
+    const double s2 = fmax((dx * dx + dy * dy + dz * dz) * ib2, 1e-300);
+    const double w = (double)q.w * (double)centre_weight<T>((T)s2, a.alpha, a.inv_alpha);
+    v[0] += w * dx;
+    v[1] += w * dy;
+    v[2] += w * dz;
+    v[3] += w;
+  }
+  block_row<4>(v, a.part);
+}
+
+__global__ void k_centre_sum(RecentreArgs a) {
+  const int p = blockIdx.x;
+  double* st = a.state + 16 * (size_t)p;
+  if (st[4] != 0.0) return;
+  double v[4];
+  prog_sum<4>(a, p, v);
+  if (threadIdx.x != 0) return;
+  if (!(v[3] > 0.0) || !isfinite(v[3])) {  // empty set: stay
+    st[4] = 1.0;
+    return;
+  }
+  const double sx = v[0] / v[3], sy = v[1] / v[3], sz = v[2] / v[3];
+  st[0] += sx;
+  st[1] += sy;
+  st[2] += sz;
+  st[3] += 1.0;
+  if (sqrt(sx * sx + sy * sy + sz * sz) <= a.tol * a.b_prog[p]) st[4] = 1.0;
+}
+
+// x_k -= x_c of the particle's progenitor (every particle, in the set or not).
+template <typename V4>
+__global__ void __launch_bounds__(kRcThreads) k_shift_pos(RecentreArgs a) {
+  const int p = a.blk_prog[blockIdx.x];
+  const double* st = a.state + 16 * (size_t)p;
+  V4* pos = reinterpret_cast<V4*>(a.pos);
+  const int64_t end = a.blk_end[blockIdx.x];
+  for (int64_t k = a.blk_begin[blockIdx.x] + threadIdx.x; k < end; k += kRcThreads) {
+    V4 q = pos[k];
+    q.x = (decltype(q.x))((double)q.x - st[0]);
+    q.y = (decltype(q.y))((double)q.y - st[1]);
+    q.z = (decltype(q.z))((double)q.z - st[2]);
+    pos[k] = q;
+  }
+}
+
+// K_nl A_nlm into KA (the coefficients whose potential gives the density).
+__global__ void k_scale_k(const double* A, double* KA, int nmax, int lmax, int n_prog, double alpha) {
+  const int nlm = (lmax + 1) * (lmax + 2) / 2, nc = (nmax + 1) * nlm;
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= (int64_t)2 * nc * n_prog) return;
+  const int j = (int)(i % (2 * nc)), ii = j < nc ? j : j - nc;
+  const int n = ii / nlm, lm = ii - n * nlm;
+  int l = 0;
+  while ((l + 1) * (l + 2) / 2 <= lm) ++l;
+  const double al = (2.0 * l + 1.0) * alpha;
+  KA[i] = (n + al) * (n + al + 1.0) / (alpha * alpha) * A[i];
+}
+
+template <typename V4>
+__global__ void __launch_bounds__(kRcThreads) k_core_blocks1(RecentreArgs a) {
+  const int p = a.blk_prog[blockIdx.x];
+  const double ib = 1.0 / a.b_prog[p];
+  const V4* pos = reinterpret_cast<const V4*>(a.pos);
+  const V4* acc = reinterpret_cast<const V4*>(a.acc);
+  double v[2] = {0.0, 0.0};
+  const int64_t end = a.blk_end[blockIdx.x];
+  for (int64_t k = a.blk_begin[blockIdx.x] + threadIdx.x; k < end; k += kRcThreads) {
+    const V4 q = pos[k];
+    const double r2 = ((double)q.x * q.x + (double)q.y * q.y) + (double)q.z * q.z;
+    if (!(r2 > 0.0)) continue;
+    const double s = sqrt(r2) * ib;
+    const double t = a.alpha == 1.0 ? s : pow(s, a.inv_alpha);
+    const double qq = 1.0 / (1.0 + t);
+    const double fac = (a.alpha == 1.0 ? 1.0 / s : pow(s, a.inv_alpha - 2.0)) * qq * qq;
+    const double rho = fac * (double)acc[k].w;  // density up to a constant factor
+    v[0] += rho * rho * r2;
+    v[1] += rho * rho;
+  }
+  double w4[4] = {v[0], v[1], 0.0, 0.0};
+  block_row<4>(w4, a.part);
+}
+
+__global__ void k_core_sum1(RecentreArgs a) {
+  const int p = blockIdx.x;
+  double v[2];
+  prog_sum<2>(a, p, v);
+  if (threadIdx.x == 0) a.state[16 * (size_t)p + 5] = v[1] > 0.0 ? v[0] / v[1] : 0.0;  // r_core^2
+}
+
+template <typename V4>
+__global__ void __launch_bounds__(kRcThreads) k_core_blocks2(RecentreArgs a) {
+  const int p = a.blk_prog[blockIdx.x];
+  const double rc2 = a.state[16 * (size_t)p + 5];
+  const V4* pos = reinterpret_cast<const V4*>(a.pos);
+  const V4* vel = reinterpret_cast<const V4*>(a.vel);
+  double v[4] = {0.0, 0.0, 0.0, 0.0};
+  const int64_t end = a.blk_end[blockIdx.x];
+  for (int64_t k = a.blk_begin[blockIdx.x] + threadIdx.x; k < end; k += kRcThreads) {
+    const V4 q = pos[k];
+    const double r2 = ((double)q.x * q.x + (double)q.y * q.y) + (double)q.z * q.z;
+    if (!(r2 < rc2)) continue;
+    const V4 u = vel[k];
+    const double m = q.w;
+    v[0] += m * u.x;
+    v[1] += m * u.y;
+    v[2] += m * u.z;
+    v[3] += m;
+  }
+  block_row<4>(v, a.part);
+}
+
+__global__ void k_core_sum2(RecentreArgs a) {
+  const int p = blockIdx.x;
+  double v[4];
+  prog_sum<4>(a, p, v);
+  if (threadIdx.x != 0) return;
+  double* st = a.state + 16 * (size_t)p;
+  for (int i = 0; i < 3; ++i) st[6 + i] = v[3] > 0.0 ? v[i] / v[3] : 0.0;
+  if (a.com) {
+    double* c = a.com + 6 * (size_t)p;
+    for (int i = 0; i < 3; ++i) {
+      c[i] += st[i];
+      c[3 + i] += st[6 + i];
+    }
+  }
+}
+
+template <typename V4>
+__global__ void __launch_bounds__(kRcThreads) k_shift_vel(RecentreArgs a) {
+  const int p = a.blk_prog[blockIdx.x];
+  const double* st = a.state + 16 * (size_t)p;
+  V4* vel = reinterpret_cast<V4*>(a.vel);
+  const int64_t end = a.blk_end[blockIdx.x];
+  for (int64_t k = a.blk_begin[blockIdx.x] + threadIdx.x; k < end; k += kRcThreads) {
+    V4 u = vel[k];
+    u.x = (decltype(u.x))((double)u.x - st[6]);
+    u.y = (decltype(u.y))((double)u.y - st[7]);
+    u.z = (decltype(u.z))((double)u.z - st[8]);
+    vel[k] = u;
+  }
+}
+
+}  // namespace
+
+cudaError_t scf_centre_launch(const RecentreArgs& a, int max_iter, cudaStream_t s) {
+  if (cudaMemsetAsync(a.state, 0, sizeof(double) * 16 * (size_t)a.n_prog, s) != cudaSuccess)
+    return cudaGetLastError();
+  for (int it = 0; it < max_iter; ++it) {
+    if (a.n_blocks > 0) {
+      if (a.f32) k_centre_blocks<float4, float><<<a.n_blocks, kRcThreads, 0, s>>>(a);
+      else k_centre_blocks<ScfD4, double><<<a.n_blocks, kRcThreads, 0, s>>>(a);
+    }
+    k_centre_sum<<<a.n_prog, 32, 0, s>>>(a);
+  }
+  if (a.n_blocks > 0) {
+    if (a.f32) k_shift_pos<float4><<<a.n_blocks, kRcThreads, 0, s>>>(a);
+    else k_shift_pos<ScfD4><<<a.n_blocks, kRcThreads, 0, s>>>(a);
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t scf_scale_k_launch(const double* A, double* KA, int nmax, int lmax, int n_prog, double alpha,
+                               cudaStream_t s) {
+  const int64_t n = (int64_t)2 * (nmax + 1) * ((lmax + 1) * (lmax + 2) / 2) * n_prog;
+  k_scale_k<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(A, KA, nmax, lmax, n_prog, alpha);
+  return cudaGetLastError();
+}
+
+cudaError_t scf_core_launch(const RecentreArgs& a, cudaStream_t s) {
+  if (a.n_blocks > 0) {
+    if (a.f32) k_core_blocks1<float4><<<a.n_blocks, kRcThreads, 0, s>>>(a);
+    else k_core_blocks1<ScfD4><<<a.n_blocks, kRcThreads, 0, s>>>(a);
+  }
+  k_core_sum1<<<a.n_prog, 32, 0, s>>>(a);
+  if (a.n_blocks > 0) {
+    if (a.f32) k_core_blocks2<float4><<<a.n_blocks, kRcThreads, 0, s>>>(a);
+    else k_core_blocks2<ScfD4><<<a.n_blocks, kRcThreads, 0, s>>>(a);
+  }
+  k_core_sum2<<<a.n_prog, 32, 0, s>>>(a);
+  if (a.n_blocks > 0) {
+    if (a.f32) k_shift_vel<float4><<<a.n_blocks, kRcThreads, 0, s>>>(a);
+    else k_shift_vel<ScfD4><<<a.n_blocks, kRcThreads, 0, s>>>(a);
+  }
+  return cudaGetLastError();
+}

@@ -156,10 +156,11 @@ class SCF:
         _lib.scf_set_mask(self._h, mask)
 
     def evolve(self, pos, vel, acc, com=None, nsteps: int = 1, kin: float = 0.5, frac: float = 0.999,
-               eta: float = 1.0 / 400.0, max_steps: int = 1000, retune_every: int = 0):
+               eta: float = 1.0 / 400.0, max_steps: int = 1000, retune_every: int = 0, recentre: bool = False):
         """``nsteps`` leapfrog steps with boundedness, the r <= r_x coefficient
         set, the tidal integration timestep and, every ``retune_every``
-        integration timesteps, a complete refresh of b (scf_evolve).  Returns
+        integration timesteps, a complete refresh of b, preceded with
+        ``recentre`` by :meth:`recentre` (scf_evolve).  Returns
         ``(bound, mask, stats, n_int)`` as of the last integration timestep."""
         for t, nm in ((pos, "pos"), (vel, "vel"), (acc, "acc")):
             self._check_particles(t, nm)
@@ -170,8 +171,17 @@ class SCF:
         b, m, st = self._evolve_bufs
         self._mask_ref = m
         n_int = _lib.scf_evolve(self._h, pos, vel, acc, com, nsteps, kin, frac, eta, max_steps, b, m, st,
-                                retune_every)
+                                retune_every, recentre)
         return b, m, st, n_int
+
+    def recentre(self, pos, vel, acc, com=None, mask=None, max_iter: int = 100, tol: float = 1e-12):
+        """Moves each progenitor's frame to its SCF centre (the maximum of a_000)
+        and core velocity (Sec. 2.1; scf_recentre): particles shifted in place,
+        ``com`` += (x_c, V_core); ``acc`` is used as scratch.  Returns a numpy
+        array (n_prog, 8) = (x_c, V_core, r_core, iterations)."""
+        for t, nm in ((pos, "pos"), (vel, "vel"), (acc, "acc")):
+            self._check_particles(t, nm)
+        return _lib.scf_recentre(self._h, self.n_prog, pos, vel, acc, com, mask, max_iter, tol)
 
     def scales(self):
         """(n_prog,) float64: the basis scale b of every progenitor."""

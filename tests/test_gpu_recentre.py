@@ -1,0 +1,161 @@
+"""Re-centring on the GPU (scf_recentre, Sec. 2.1) against the oracle's.
+
+Double precision: the centre within 1e-10 b, the core radius and velocity
+within 1e-10 relative, the same iteration count, particles and centre
+shifted consistently; mixed precision within 1e-5 b (centre) and 1e-4
+(core).  Symmetric samples give the exact centre and core velocity.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import workloads
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def scf():
+    if not torch.cuda.is_available():
+        pytest.skip("needs a GPU")
+    import paper_2602_13385_gb300 as pkg
+    return pkg
+
+
+def dev(x, dtype=torch.float64):
+    return torch.tensor(np.ascontiguousarray(x), device="cuda", dtype=dtype)
+
+
+def symmetric(n, seed, c, V0):
+    pos, vel = workloads.plummer(n, seed=seed)
+    P, V = [], []
+    for sx in (1, -1):
+        for sy in (1, -1):
+            for sz in (1, -1):
+                sgn = np.array([sx, sy, sz])
+                q, u = pos.copy(), vel.copy()
+                q[:, :3] *= sgn
+                u[:, :3] *= sgn
+                q[:, 3] /= 8
+                P.append(q)
+                V.append(u)
+    P, V = np.concatenate(P), np.concatenate(V)
+    P[:, :3] += c
+    V[:, :3] += V0
+    return P, V
+
+
+@pytest.mark.parametrize("alpha", [0.5, 1.0])
+def test_symmetric_sample(scf, alpha):
+    c, V0 = np.array([0.11, -0.05, 0.023]), np.array([0.3, -0.2, 0.1])
+    pos, vel = symmetric(2000, 31, c, V0)
+    n = pos.shape[0]
+    sim = scf.SCF(scf.Config(nmax=8, lmax=4, b=0.3, alpha=alpha), n=n)
+    p, v, a, com = dev(pos), dev(vel), torch.zeros(n, 4, dtype=torch.float64, device="cuda"), dev(np.zeros((1, 6)))
+    out = sim.recentre(p, v, a, com)
+    assert np.allclose(out[0, :3], c, rtol=0, atol=1e-12)
+    assert np.allclose(out[0, 3:6], V0, rtol=0, atol=1e-12)
+    assert np.allclose(com.cpu().numpy()[0], np.concatenate([c, V0]), rtol=0, atol=1e-12)
+    assert np.allclose(p.cpu().numpy()[:, :3], pos[:, :3] - c, rtol=0, atol=2e-12)    # x_c to 1e-12
+    assert np.allclose(v.cpu().numpy()[:, :3], vel[:, :3] - V0, rtol=0, atol=2e-12)
+
+
+@pytest.mark.parametrize("alpha,masked", [(0.5, False), (1.0, True), (1.5, False)])
+def test_fp64_matches_oracle(scf, alpha, masked):
+    pos, vel = workloads.plummer(6000, seed=32)
+    pos[:, :3] += np.array([0.06, -0.03, 0.02])
+    vel[:, :3] += np.array([0.01, 0.02, -0.03])
+    n, nmax, lmax, b = pos.shape[0], 10, 6, 0.3
+    mask = (np.arange(n) % 5 != 2).astype(np.uint8) if masked else None
+    com0 = np.array([5.0, 1.0, -2.0, 0.1, 0.0, 0.2])
+    rp, rv, rc, rxc, rV, rrc, rit = oracle.recentre(pos, vel, com0, nmax, lmax, b, alpha, mask=mask)
+    sim = scf.SCF(scf.Config(nmax=nmax, lmax=lmax, b=b, alpha=alpha), n=n)
+    p, v, a, com = dev(pos), dev(vel), torch.zeros(n, 4, dtype=torch.float64, device="cuda"), dev(com0[None])
+    m = None if mask is None else torch.tensor(mask, device="cuda")
+    out = sim.recentre(p, v, a, com, mask=m)
+    print(f"alpha {alpha}: x_c {out[0, :3]} (oracle {rxc}), iterations {out[0, 7]:.0f} ({rit}), "
+          f"r_core {out[0, 6]:.12g} ({rrc:.12g})")
+    assert out[0, 7] == rit
+    assert np.max(np.abs(out[0, :3] - rxc)) < 1e-10 * b
+    assert abs(out[0, 6] - rrc) < 1e-10 * rrc
+    assert np.max(np.abs(out[0, 3:6] - rV)) < 1e-10 * np.max(np.abs(rV))
+    assert np.max(np.abs(p.cpu().numpy()[:, :3] - rp[:, :3])) < 1e-12
+    assert np.max(np.abs(v.cpu().numpy()[:, :3] - rv[:, :3])) < 1e-12
+    assert np.max(np.abs(com.cpu().numpy()[0] - rc)) < 1e-12 * np.max(np.abs(rc))
+
+
+def test_mixed_matches_oracle(scf):
+    pos, vel = workloads.plummer(20000, seed=33)
+    pos[:, :3] += np.array([0.04, 0.01, -0.02])
+    p32 = pos.astype(np.float32).astype(np.float64)
+    v32 = vel.astype(np.float32).astype(np.float64)
+    n, nmax, lmax, b = pos.shape[0], 12, 6, 0.3
+    _, _, _, rxc, rV, rrc, rit = oracle.recentre(p32, v32, np.zeros(6), nmax, lmax, b, 1.0)
+    sim = scf.SCF(scf.Config(nmax=nmax, lmax=lmax, b=b, precision="mixed"), n=n)
+    p, v = dev(pos, torch.float32), dev(vel, torch.float32)
+    a = torch.zeros(n, 4, dtype=torch.float32, device="cuda")
+    out = sim.recentre(p, v, a, None)
+    print(f"mixed: x_c {out[0, :3]} (oracle {rxc}), r_core {out[0, 6]:.8g} ({rrc:.8g}), V {out[0, 3:6]} ({rV})")
+    assert np.max(np.abs(out[0, :3] - rxc)) < 1e-5 * b
+    assert abs(out[0, 6] - rrc) < 1e-4 * rrc
+    assert np.max(np.abs(out[0, 3:6] - rV)) < 1e-3 * np.std(vel[:, :3])
+
+
+def test_batched_progenitors(scf):
+    sizes = [3000, 0, 1500]
+    shifts = [np.array([0.05, 0.0, -0.02]), np.zeros(3), np.array([-0.03, 0.04, 0.01])]
+    pos_l, vel_l = [], []
+    for i, n in enumerate(sizes):
+        p, v = workloads.plummer(max(n, 1), seed=40 + i)
+        p[:, :3] += shifts[i]
+        pos_l.append(p[:n])
+        vel_l.append(v[:n])
+    offsets = np.concatenate([[0], np.cumsum(sizes)])
+    pos, vel = np.concatenate(pos_l), np.concatenate(vel_l)
+    b_l = [0.3, 0.3, 0.25]
+    sim = scf.SCF(scf.Config(nmax=8, lmax=4, b=0.3), offsets=offsets, b_per_prog=b_l)
+    p, v, a = dev(pos), dev(vel), torch.zeros(pos.shape[0], 4, dtype=torch.float64, device="cuda")
+    com = dev(np.zeros((3, 6)))
+    out = sim.recentre(p, v, a, com)
+    for i, n in enumerate(sizes):
+        if n == 0:
+            assert np.all(out[i, :7] == 0)
+            continue
+        _, _, _, rxc, rV, rrc, rit = oracle.recentre(pos_l[i], vel_l[i], np.zeros(6), 8, 4, b_l[i])
+        assert np.max(np.abs(out[i, :3] - rxc)) < 1e-10 * b_l[i]
+        assert abs(out[i, 6] - rrc) < 1e-10 * rrc
+
+
+def test_evolve_with_recentring(scf):
+    """Escape-physics run with a host and a complete refresh (re-centring,
+    boundedness in the new frame, b retuned) every second integration
+    timestep, against the oracle's."""
+    wl = workloads.plummer_eccentric(n=3000, seed=34, nsteps=1)
+    nmax, lmax, alpha = 8, 4, 1.0
+    host = oracle.host_struct(wl.host)
+    a0 = oracle.forces(wl.pos, oracle.coeffs(wl.pos, nmax, lmax, wl.b), nmax, lmax, wl.b, com=wl.com, host=host)
+    ref = oracle.evolve(wl.pos, wl.vel, a0, nmax, lmax, wl.b, wl.dt, 12, com=wl.com, host=host, max_steps=3,
+                        retune_every=2, recentre=True)
+    sim = scf.SCF(scf.Config(nmax=nmax, lmax=lmax, b=wl.b, dt=wl.dt, host=list(wl.host)), n=wl.n)
+    p, v, a, c = dev(wl.pos), dev(wl.vel), dev(a0), dev(wl.com[None])
+    _, _, _, n_int = sim.evolve(p, v, a, c, nsteps=12, max_steps=3, retune_every=2, recentre=True)
+    assert n_int == ref[7]
+    b_gpu = float(sim.scales().cpu().numpy()[0])
+    ex = np.max(np.abs(p.cpu().numpy()[:, :3] - ref[0][:, :3]))
+    ec = np.max(np.abs(c.cpu().numpy()[0] - ref[3]))
+    print(f"evolve with re-centring: b {b_gpu:.15g} ({ref[8]:.15g}), positions {ex:.1e}, centre {ec:.1e}")
+    assert abs(b_gpu - ref[8]) < 1e-12 * ref[8]
+    assert ex < 1e-10 * np.max(np.abs(ref[0][:, :3]))
+    assert ec < 1e-10 * np.max(np.abs(ref[3]))
+    assert sim.status() == (0, 0)
+
+
+def test_invalid_arguments(scf):
+    from paper_2602_13385_gb300 import _lib
+    pos, vel = workloads.plummer(100, seed=35)
+    sim = scf.SCF(scf.Config(nmax=4, lmax=2, b=0.3), n=100)
+    p, v, a = dev(pos), dev(vel), torch.zeros(100, 4, dtype=torch.float64, device="cuda")
+    for kw in ({"max_iter": 0}, {"max_iter": 5000}, {"tol": -1.0}, {"tol": float("nan")}):
+        with pytest.raises(_lib.ScfError, match="INVALID_ARG"):
+            sim.recentre(p, v, a, None, **kw)
