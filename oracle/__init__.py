@@ -397,7 +397,7 @@ def zhao_half_mass_scale(r50, alpha=1.0):
 
 
 def evolve(pos, vel, acc, nmax, lmax, b, dt, nsteps, G=1.0, com=None, host=None, kin=0.5, frac=0.999,
-           eta=1.0 / 400.0, max_steps=1000, retune_every=0, alpha=1.0, recentre=False):
+           eta=1.0 / 400.0, max_steps=1000, retune_every=0, alpha=1.0, recentre=False, retune_rule="half_mass"):
     """Leapfrog with the escape physics of Sec. 2.2.  At the start of every
     integration timestep: the boundedness test and the coefficient set
     r <= r_x (:func:`boundedness`); at every ``retune_every``-th integration
@@ -405,7 +405,9 @@ def evolve(pos, vel, acc, nmax, lmax, b, dt, nsteps, G=1.0, com=None, host=None,
     ``recentre``) first moves the frame to the SCF centre and core velocity
     (:func:`recentre`, over the coefficient set) and takes the boundedness
     again in it, then
-    retunes the basis scale b (alpha fixed) to the scale of the lowest-order
+    retunes the basis scale b (alpha fixed): with ``retune_rule="a000"`` to
+    the maximum of a_000 (:func:`a000_scale`, over the coefficient set), else
+    to the scale of the lowest-order
     density whose half-mass radius is the bound stars' energy-based one,
     :func:`zhao_half_mass_scale` (alpha = 1: b = r_50 / (1 + sqrt 2)); the field
     of the coefficient set at the current positions; and the length of the
@@ -433,7 +435,9 @@ def evolve(pos, vel, acc, nmax, lmax, b, dt, nsteps, G=1.0, com=None, host=None,
                 pos, vel, com, _, _, _, _ = _recentre_frame(pos, vel, com, nmax, lmax, b, alpha, mask=mask)
                 E, bound, rx2, mask, Mb = boundedness(pos, vel, G, kin, frac)
                 stats = np.array([bound.sum(), Mb, np.sqrt(rx2), mask.sum()], dtype=np.float64)
-            if bound.any():
+            if retune_rule == "a000":   # b maximising a_000 of the coefficient set
+                b = a000_scale(pos, b, alpha, mask=mask)
+            elif bound.any():
                 r50 = np.sqrt(boundedness(pos, vel, G, kin, 0.5)[2])
                 b = zhao_half_mass_scale(r50, alpha)
         A = coeffs(pos, nmax, lmax, b, mask=mask, alpha=alpha)
@@ -536,6 +540,55 @@ def recentre(pos, vel, com, nmax, lmax, b, alpha=1.0, mask=None, tol=1e-12, max_
 
 
 _recentre_frame = recentre   # (evolve's keyword of the same name shadows it there)
+
+
+def a000_biorth(pos, b, alpha=1.0, mask=None):
+    """a_000 of the particles about the origin in the bi-orthonormal
+    normalisation of Eq. 3a (the lowest pair scaled to unit self-energy,
+    psi_000 = U_00 Y_00 / sqrt|I_00(b)|), as a function of b (alpha fixed):
+    a_000 = Y_00 / sqrt(|I_00(1)| b) sum_k m_k g(r_k / b)."""
+    pos = _f64(pos)
+    sel = np.ones(pos.shape[0], bool) if mask is None else np.asarray(mask, bool)
+    r = np.sqrt(np.sum(pos[sel, :3] ** 2, axis=1))
+    y00 = 1.0 / np.sqrt(4.0 * np.pi)
+    return y00 / np.sqrt(abs(inl(0, 0, 1.0, alpha)) * b) * float(np.sum(pos[sel, 3] * a000_profile(r / b, alpha)))
+
+
+def a000_scale(pos, b0, alpha=1.0, mask=None, span=8.0, points=33, rounds=3):
+    """The basis scale that maximises :func:`a000_biorth` (Sec. 2: b tuned so
+    that the lowest mode approximates the cluster; the same criterion as the
+    centre, Sec. 2.1), searched in ln b: ``rounds`` grids of ``points`` values,
+    the first over [b0/span, b0 span], each next over one step either side of
+    the previous best; the best point of the last grid is moved to the vertex
+    of the parabola through it and its two neighbours (none at an edge).
+    Only the b-dependent factor b^(-1/2) sum m g(r/b) is compared.  An empty
+    set keeps b0."""
+    pos = _f64(pos)
+    sel = np.ones(pos.shape[0], bool) if mask is None else np.asarray(mask, bool)
+    if not sel.any():
+        return float(b0)
+    r = np.sqrt(np.sum(pos[sel, :3] ** 2, axis=1))
+    m = pos[sel, 3]
+
+    def h(lnb):
+        bb = np.exp(lnb)
+        return bb ** -0.5 * float(np.sum(m * a000_profile(r / bb, alpha)))
+
+    lo = np.log(b0) - np.log(span)
+    step = 2.0 * np.log(span) / (points - 1)
+    for rnd in range(rounds):
+        hs = [h(lo + j * step) for j in range(points)]
+        j = int(np.argmax(hs))
+        if rnd + 1 < rounds:
+            lo = lo + (j - 1) * step
+            step = 2.0 * step / (points - 1)
+    x = lo + j * step
+    if 0 < j < points - 1:
+        hm, h0, hp = hs[j - 1], hs[j], hs[j + 1]
+        den = hm - 2.0 * h0 + hp
+        if den < 0.0:
+            x += 0.5 * step * (hm - hp) / den
+    return float(np.exp(x))
 
 
 def power_l(A, nmax, lmax, b, alpha=1.0):

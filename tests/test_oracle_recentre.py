@@ -141,3 +141,38 @@ def test_recentre_keeps_host_frame_state():
     assert np.allclose(p2[:, :3] + c2[:3], pos[:, :3] + com[:3], rtol=0, atol=1e-13)
     assert np.allclose(v2[:, :3] + c2[3:], vel[:, :3] + com[3:], rtol=0, atol=1e-14)
     assert np.linalg.norm(xc - 0.07) < 0.1 and np.linalg.norm(V - 0.02) < 0.2   # sampling noise of the core
+
+
+# --------------------------------------------------------------- b at the maximum of a_000
+@pytest.mark.parametrize("alpha", [0.5, 1.0, 1.5])
+def test_a000_scale_of_the_lowest_order_sphere_is_its_own(alpha):
+    """The projection of a density onto the unit-energy lowest pair is largest
+    when the pair's density is the density itself (Cauchy-Schwarz in the
+    energy inner product): the search returns the sphere's own scale."""
+    b_true = 0.37
+    pos = _zhao_sphere(b_true, alpha, nodes=120)
+    for b0 in (0.2, 0.37, 0.9):
+        b = oracle.a000_scale(pos, b0, alpha)
+        assert b == pytest.approx(b_true, rel=1e-7)
+
+
+def test_a000_scale_of_samples():
+    a = 3 * math.pi / 16
+    pos, _ = workloads.plummer(200000, seed=26)
+    assert oracle.a000_scale(pos, 0.3, 0.5) / a == pytest.approx(1.0, abs=0.01)      # Plummer in its own basis
+    hp = workloads.hernquist_positions(200000, 0.4, seed=27)
+    assert oracle.a000_scale(hp, 0.3, 1.0) / 0.4 == pytest.approx(1.0, abs=0.01)     # Hernquist in its own
+
+
+def test_a000_scale_is_a_maximum_of_a000():
+    pos, _ = workloads.plummer(5000, seed=28)
+    mask = np.arange(5000) % 4 != 1
+    for alpha in (0.5, 1.0):
+        b = oracle.a000_scale(pos, 0.3, alpha, mask=mask)
+        a0 = oracle.a000_biorth(pos, b, alpha, mask=mask)
+        # a_000 from the coefficient pass (S_000 sqrt|I_00| / N_00) agrees with the closed form
+        S = oracle.coeffs(pos, 0, 0, b, mask=mask, alpha=alpha)[0]
+        assert S * math.sqrt(abs(oracle.inl(0, 0, b, alpha))) * math.sqrt(4 * math.pi) == pytest.approx(a0, rel=1e-12)
+        for f in (1 - 1e-3, 1 + 1e-3):
+            assert oracle.a000_biorth(pos, b * f, alpha, mask=mask) < a0
+    assert oracle.a000_scale(pos, 0.3, 1.0, mask=np.zeros(5000, bool)) == 0.3     # empty set keeps b
