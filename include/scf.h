@@ -349,7 +349,23 @@ typedef struct scf_escape_params {
                         and core velocity, 100 iterations at most, step tolerance
                         1e-12 b) with the current coefficient set, then scf_bound again
                         in the new frame; 0: the frame stays on the centre orbit */
+  int retune_rule;   /* b at a complete refresh: 0 = the half-mass rule above,
+                        1 = scf_retune_a000 (the maximum of a_000) over the coefficient set */
 } scf_escape_params;
+
+/* Basis scale of each progenitor at the maximum of a_000 in the bi-orthonormal
+ * normalisation of Eq. 3a (Sec. 2: b tuned so that the lowest mode
+ * approximates the cluster; alpha and the centre fixed).  With the lowest pair
+ * scaled to unit self-energy, a_000(b) = Y_00 / sqrt(|I_00(1)| b) *
+ * sum_k m_k g(r_k / b) over the coefficient set (mask; NULL = all),
+ * g(s) = (1 + s^(1/alpha))^-alpha.  Search in ln b: 3 grids of 33 values, the
+ * first over [b/8, 8b], each next over one step either side of the previous
+ * best (the first best in grid order), the last best moved to the vertex of
+ * the parabola through it and its neighbours.  An empty set keeps b.  Updates
+ * the handle's scales (scf_get_scales) on its stream; double-precision sums in
+ * a fixed order.
+ * Errors: SCF_ERR_NULL_POINTER, SCF_ERR_MISALIGNED, SCF_ERR_CUDA. */
+int scf_retune_a000(scf_handle* h, const void* pos, const uint8_t* mask);
 
 /* Re-centring of the cluster frame (Sec. 2.1).  For every progenitor:
  * 1. the SCF centre x_c, where a_000 of the expansion about x_c (alpha, b fixed)

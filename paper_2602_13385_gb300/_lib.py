@@ -40,7 +40,7 @@ ERRORS = {
 EXPORTS = ["scf_init", "scf_coeffs", "scf_forces", "scf_step", "scf_last_coeffs", "scf_status",
            "scf_launches_per_call", "scf_profile", "scf_profile_read", "scf_coeffs_noalloc", "scf_set_option",
            "scf_get_option", "scf_autotune", "scf_adjoint_level", "scf_energy", "scf_bound", "scf_tidal",
-           "scf_set_mask", "scf_evolve", "scf_get_scales", "scf_recentre", "scf_free", "scf_strerror"]
+           "scf_set_mask", "scf_evolve", "scf_get_scales", "scf_recentre", "scf_retune_a000", "scf_free", "scf_strerror"]
 SCF_OPT_GRAPHS = 1
 SCF_OPT_K1_TILE = 2
 SCF_OPT_K3_BLOCK = 3
@@ -60,7 +60,8 @@ class scf_host_component(ctypes.Structure):
 
 class scf_escape_params(ctypes.Structure):
     _fields_ = [("kin", ctypes.c_double), ("frac", ctypes.c_double), ("eta", ctypes.c_double),
-                ("max_steps", ctypes.c_int), ("retune_every", ctypes.c_int), ("recentre", ctypes.c_int)]
+                ("max_steps", ctypes.c_int), ("retune_every", ctypes.c_int), ("recentre", ctypes.c_int),
+                ("retune_rule", ctypes.c_int)]
 
 
 class scf_config(ctypes.Structure):
@@ -108,6 +109,7 @@ def load(build: bool = True) -> ctypes.CDLL:
     lib.scf_set_mask.argtypes = [vp, vp]
     lib.scf_get_scales.argtypes = [vp, vp]
     lib.scf_recentre.argtypes = [vp, vp, vp, vp, vp, vp, i, d, dp]
+    lib.scf_retune_a000.argtypes = [vp, vp, vp]
     lib.scf_evolve.argtypes = [vp, vp, vp, vp, vp, i, ctypes.POINTER(scf_escape_params), vp, vp, vp,
                                ctypes.POINTER(i)]
     lib.scf_free.argtypes = [vp]
@@ -266,11 +268,11 @@ def scf_set_mask(h, mask):
 
 
 def scf_evolve(h, pos, vel, acc, com, nsteps: int, kin: float, frac: float, eta: float, max_steps: int,
-               bound, mask, stats, retune_every: int = 0, recentre: bool = False) -> int:
+               bound, mask, stats, retune_every: int = 0, recentre: bool = False, retune_rule: int = 0) -> int:
     """Returns the number of integration timesteps."""
     import torch
     ep = scf_escape_params(float(kin), float(frac), float(eta), int(max_steps), int(retune_every),
-                           1 if recentre else 0)
+                           1 if recentre else 0, int(retune_rule))
     n = ctypes.c_int(0)
     _check(load().scf_evolve(h, _ptr(pos), _ptr(vel), _ptr(acc), _ptr(com, torch.float64), int(nsteps),
                              ctypes.byref(ep), _ptr(bound, torch.uint8), _ptr(mask, torch.uint8),
@@ -287,6 +289,11 @@ def scf_recentre(h, n_prog: int, pos, vel, acc, com, mask, max_iter: int, tol: f
                                _ptr(mask, torch.uint8), int(max_iter), float(tol),
                                out.ctypes.data_as(ctypes.POINTER(ctypes.c_double))), "scf_recentre")
     return out
+
+
+def scf_retune_a000(h, pos, mask):
+    import torch
+    _check(load().scf_retune_a000(h, _ptr(pos), _ptr(mask, torch.uint8)), "scf_retune_a000")
 
 
 def scf_get_scales(h, b_out):

@@ -30,6 +30,7 @@ struct scf_handle {
   bool gen = false;    // radial family of exponent alpha != 1: the general kernels 1 and 3
   ScfConst* d_tab = nullptr;  // their recurrence tables (device memory; gen handles only)
   double* d_rc = nullptr;     // [n_prog][16] re-centring state (scf_recentre)
+  double* d_sp = nullptr;     // [k3 blocks][kScalePoints + 1] partial sums of the b search
   int k1_blocks = 0;
   int* d_blk1_prog = nullptr;
   int64_t* d_blk1_begin = nullptr;
@@ -552,6 +553,7 @@ int scf_init(const scf_config* cfg, int n_prog, const int64_t* offsets, const do
   const size_t o_k2c = take(sizeof(unsigned) * (size_t)scf_k2_groups(h->nc) * n_prog);
   const size_t o_tab = h->gen ? take(sizeof(ScfConst)) : off;
   const size_t o_rc = take(sizeof(double) * 16 * (size_t)n_prog);
+  const size_t o_sp = take(sizeof(double) * (kScalePoints + 1) * nb3);
   if (cudaMalloc(&h->d_base, off) != cudaSuccess) {
     cudaGetLastError();
     return fail(SCF_ERR_OUT_OF_MEMORY);
@@ -582,6 +584,7 @@ int scf_init(const scf_config* cfg, int n_prog, const int64_t* offsets, const do
   h->d_k2z = reinterpret_cast<double*>(base + o_k2z);
   h->d_k2cnt = reinterpret_cast<unsigned*>(base + o_k2c);
   h->d_rc = reinterpret_cast<double*>(base + o_rc);
+  h->d_sp = reinterpret_cast<double*>(base + o_sp);
 
   if (h->gen) {  // recurrence tables of the handle's radial family
     h->d_tab = reinterpret_cast<ScfConst*>(base + o_tab);
@@ -966,7 +969,7 @@ int scf_evolve(scf_handle* h, void* pos, void* vel, void* acc, double* com, int 
   if (nsteps < 0 || ep->max_steps < 1 || !(ep->eta > 0.0) || !std::isfinite(ep->eta) || !(h->cfg.dt > 0.0))
     return SCF_ERR_INVALID_ARG;
   if (!(ep->kin > 0.0) || !std::isfinite(ep->kin) || !(ep->frac > 0.0 && ep->frac <= 1.0) || ep->retune_every < 0 ||
-      (ep->recentre != 0 && ep->recentre != 1))
+      (ep->recentre != 0 && ep->recentre != 1) || (ep->retune_rule != 0 && ep->retune_rule != 1))
     return SCF_ERR_INVALID_ARG;
   int rc = scf_set_mask(h, mask);
   if (rc != SCF_OK) return rc;
@@ -985,20 +988,25 @@ int scf_evolve(scf_handle* h, void* pos, void* vel, void* acc, double* com, int 
         if (rc == SCF_OK) rc = scf_bound(h, pos, vel, ep->kin, ep->frac, nullptr, bound, mask, stats);
         if (rc != SCF_OK) return rc;
       }
-      BoundArgs a{};
-      a.pos = pos;
-      a.prog_off = h->d_off;
-      a.n_prog = h->n_prog;
-      a.n_total = h->n_total;
-      a.f32 = h->cfg.precision == SCF_MIXED;
-      a.frac = 0.5;
-      a.key = h->d_key;
-      a.bound = bound;
-      a.mask = nullptr;
-      a.stats = h->d_half;
-      if (cuda_fail(scf_select_launch(a, h->stream)) != SCF_OK ||
-          cuda_fail(scf_retune_b_launch(h->d_half, h->d_b, h->n_prog, h->cfg.alpha, h->stream)) != SCF_OK)
-        return SCF_ERR_CUDA;
+      if (ep->retune_rule == 1) {  // b at the maximum of a_000 of the coefficient set
+        rc = scf_retune_a000(h, pos, mask);
+        if (rc != SCF_OK) return rc;
+      } else {
+        BoundArgs a{};
+        a.pos = pos;
+        a.prog_off = h->d_off;
+        a.n_prog = h->n_prog;
+        a.n_total = h->n_total;
+        a.f32 = h->cfg.precision == SCF_MIXED;
+        a.frac = 0.5;
+        a.key = h->d_key;
+        a.bound = bound;
+        a.mask = nullptr;
+        a.stats = h->d_half;
+        if (cuda_fail(scf_select_launch(a, h->stream)) != SCF_OK ||
+            cuda_fail(scf_retune_b_launch(h->d_half, h->d_b, h->n_prog, h->cfg.alpha, h->stream)) != SCF_OK)
+          return SCF_ERR_CUDA;
+      }
     }
     // the field of the new set at the current positions (the next opening kick uses it)
     rc = run_coeffs(h, pos, nullptr, nullptr, mask, h->d_A, nullptr, SCF_MODE_COEFFS);
@@ -1085,6 +1093,28 @@ int scf_recentre(scf_handle* h, void* pos, void* vel, void* acc, double* com, co
     o[7] = s[3];
   }
   return SCF_OK;
+}
+
+int scf_retune_a000(scf_handle* h, const void* pos, const uint8_t* mask) {
+  if (!h) return SCF_ERR_NULL_POINTER;
+  if (!pos && h->n_total > 0) return SCF_ERR_NULL_POINTER;
+  if (!aligned16(pos)) return SCF_ERR_MISALIGNED;
+  ScaleArgs a{};
+  a.pos = pos;
+  a.mask = mask;
+  a.blk_prog = h->d_blk3_prog;
+  a.blk_begin = h->d_blk3_begin;
+  a.blk_end = h->d_blk3_end;
+  a.n_blocks = h->k3_blocks;
+  a.n_prog = h->n_prog;
+  a.f32 = h->cfg.precision == SCF_MIXED;
+  a.b_prog = h->d_b;
+  a.alpha = h->cfg.alpha;
+  a.inv_alpha = 1.0 / h->cfg.alpha;
+  a.span = 8.0;
+  a.part = h->d_sp;
+  a.state = h->d_rc;
+  return cuda_fail(scf_scale_a000_launch(a, h->stream));
 }
 
 int scf_get_scales(scf_handle* h, double* b_out) {

@@ -185,6 +185,25 @@ cudaError_t scf_scale_k_launch(const double* A, double* KA, int nmax, int lmax, 
 // r_core and V_core from acc.w, com += (x_c, V_core), v -= V_core.
 cudaError_t scf_core_launch(const RecentreArgs& a, cudaStream_t s);
 
+// Basis scale at the maximum of the bi-orthonormal a_000 (scf_recentre.cu):
+// kScaleRounds grids of kScalePoints values of ln b, b_prog updated in place.
+constexpr int kScalePoints = 33;
+constexpr int kScaleRounds = 3;
+struct ScaleArgs {
+  const void* pos;
+  const uint8_t* mask;       // coefficient set, or null
+  const int* blk_prog;
+  const int64_t* blk_begin;
+  const int64_t* blk_end;
+  int n_blocks, n_prog;
+  int f32;
+  double* b_prog;            // [n_prog], read and updated
+  double alpha, inv_alpha, span;
+  double* part;              // [n_blocks][kScalePoints + 1] scratch
+  double* state;             // [n_prog][4] scratch
+};
+cudaError_t scf_scale_a000_launch(const ScaleArgs& a, cudaStream_t s);
+
 struct ScfLaunchInfo {
   int threads;   // threads per block
   int tile;      // particles per tile (block ranges are whole tiles)

@@ -283,3 +283,124 @@ cudaError_t scf_core_launch(const RecentreArgs& a, cudaStream_t s) {
   }
   return cudaGetLastError();
 }
+
+// ---------------------------------------------------------------------------
+// Basis scale at the maximum of a_000 (Sec. 2; alpha and the centre fixed).
+// In the bi-orthonormal normalisation of Eq. 3a, a_000(b) is a constant times
+// h(b) = b^(-1/2) sum_k m_k g(r_k / b) over the coefficient set.  Search in
+// ln b: kScaleRounds grids of kScalePoints values, the first over
+// [b/span, b span], each next over one step either side of the previous best
+// (the first best in grid order); the last best moves to the vertex of the
+// parabola through it and its neighbours.  An empty set keeps b.
+// state[p]: [0] ln b of the grid's first point, [1] the step, [2] best index.
+namespace {
+
+template <typename V4>
+__global__ void __launch_bounds__(kRcThreads) k_scale_blocks(ScaleArgs a) {
+  constexpr int NP = kScalePoints;
+  __shared__ double s_ib[NP];
+  __shared__ double s_w[kRcWarps][NP + 1];
+  const int p = a.blk_prog[blockIdx.x];
+  const double* st = a.state + 4 * (size_t)p;
+  if (threadIdx.x < NP) s_ib[threadIdx.x] = exp(-(st[0] + threadIdx.x * st[1]));  // 1 / b_j
+  __syncthreads();
+  double v[NP + 1];
+#pragma unroll
+  for (int j = 0; j <= NP; ++j) v[j] = 0.0;
+  const V4* pos = reinterpret_cast<const V4*>(a.pos);
+  const int64_t end = a.blk_end[blockIdx.x];
+  for (int64_t k = a.blk_begin[blockIdx.x] + threadIdx.x; k < end; k += kRcThreads) {
+    if (a.mask && !a.mask[k]) continue;
+    const V4 q = pos[k];
+    const double r = sqrt(((double)q.x * q.x + (double)q.y * q.y) + (double)q.z * q.z);
+    const double m = q.w;
+#pragma unroll
+    for (int j = 0; j < NP; ++j) {
+      const double s = r * s_ib[j];
+      v[j] += m * (a.alpha == 1.0 ? 1.0 / (1.0 + s) : pow(1.0 + pow(s, a.inv_alpha), -a.alpha));
+    }
+    v[NP] += m;
+  }
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int j = 0; j <= NP; ++j) {
+    double x = v[j];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+    if (lane == 0) s_w[warp][j] = x;
+  }
+  __syncthreads();
+  if (threadIdx.x <= NP) {
+    double x = 0.0;
+#pragma unroll
+    for (int w = 0; w < kRcWarps; ++w) x += s_w[w][threadIdx.x];
+    a.part[(size_t)blockIdx.x * (NP + 1) + threadIdx.x] = x;
+  }
+}
+
+__global__ void k_scale_init(ScaleArgs a) {
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= a.n_prog) return;
+  double* st = a.state + 4 * (size_t)p;
+  st[0] = log(a.b_prog[p]) - log(a.span);
+  st[1] = 2.0 * log(a.span) / (kScalePoints - 1);
+  st[2] = 0.0;
+}
+
+// One warp per progenitor: the grid's sums in block order, the best point,
+// the next grid (or, after the last round, the new b).
+__global__ void k_scale_sum(ScaleArgs a, int round) {
+  constexpr int NP = kScalePoints;
+  const int p = blockIdx.x, lane = threadIdx.x;
+  __shared__ double s_h[NP + 1];
+  double v[NP + 1];
+#pragma unroll
+  for (int j = 0; j <= NP; ++j) v[j] = 0.0;
+  for (int b = lane; b < a.n_blocks; b += 32) {
+    if (a.blk_prog[b] != p) continue;
+#pragma unroll
+    for (int j = 0; j <= NP; ++j) v[j] += a.part[(size_t)b * (NP + 1) + j];
+  }
+#pragma unroll
+  for (int j = 0; j <= NP; ++j)
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v[j] += __shfl_xor_sync(0xffffffffu, v[j], o);
+  if (lane != 0) return;
+  double* st = a.state + 4 * (size_t)p;
+  if (!(v[NP] > 0.0)) return;  // empty set: b unchanged
+  int best = 0;
+  double hb = -1.0;
+  for (int j = 0; j < NP; ++j) {
+    s_h[j] = exp(-0.5 * (st[0] + j * st[1])) * v[j];
+    if (s_h[j] > hb) {
+      hb = s_h[j];
+      best = j;
+    }
+  }
+  if (round + 1 < kScaleRounds) {
+    st[0] += (best - 1) * st[1];
+    st[1] = 2.0 * st[1] / (NP - 1);
+    return;
+  }
+  double x = st[0] + best * st[1];
+  if (best > 0 && best < NP - 1) {
+    const double hm = s_h[best - 1], h0 = s_h[best], hp = s_h[best + 1];
+    const double den = hm - 2.0 * h0 + hp;
+    if (den < 0.0) x += 0.5 * st[1] * (hm - hp) / den;
+  }
+  a.b_prog[p] = exp(x);
+}
+
+}  // namespace
+
+cudaError_t scf_scale_a000_launch(const ScaleArgs& a, cudaStream_t s) {
+  k_scale_init<<<(a.n_prog + 127) / 128, 128, 0, s>>>(a);
+  for (int r = 0; r < kScaleRounds; ++r) {
+    if (a.n_blocks > 0) {
+      if (a.f32) k_scale_blocks<float4><<<a.n_blocks, kRcThreads, 0, s>>>(a);
+      else k_scale_blocks<ScfD4><<<a.n_blocks, kRcThreads, 0, s>>>(a);
+    }
+    k_scale_sum<<<a.n_prog, 32, 0, s>>>(a, r);
+  }
+  return cudaGetLastError();
+}

@@ -156,10 +156,12 @@ class SCF:
         _lib.scf_set_mask(self._h, mask)
 
     def evolve(self, pos, vel, acc, com=None, nsteps: int = 1, kin: float = 0.5, frac: float = 0.999,
-               eta: float = 1.0 / 400.0, max_steps: int = 1000, retune_every: int = 0, recentre: bool = False):
+               eta: float = 1.0 / 400.0, max_steps: int = 1000, retune_every: int = 0, recentre: bool = False,
+               retune_rule: str = "half_mass"):
         """``nsteps`` leapfrog steps with boundedness, the r <= r_x coefficient
         set, the tidal integration timestep and, every ``retune_every``
-        integration timesteps, a complete refresh of b, preceded with
+        integration timesteps, a complete refresh of b (``retune_rule``
+        "half_mass" or "a000", :meth:`retune_a000`), preceded with
         ``recentre`` by :meth:`recentre` (scf_evolve).  Returns
         ``(bound, mask, stats, n_int)`` as of the last integration timestep."""
         for t, nm in ((pos, "pos"), (vel, "vel"), (acc, "acc")):
@@ -171,8 +173,14 @@ class SCF:
         b, m, st = self._evolve_bufs
         self._mask_ref = m
         n_int = _lib.scf_evolve(self._h, pos, vel, acc, com, nsteps, kin, frac, eta, max_steps, b, m, st,
-                                retune_every, recentre)
+                                retune_every, recentre, {"half_mass": 0, "a000": 1}[retune_rule])
         return b, m, st, n_int
+
+    def retune_a000(self, pos, mask=None):
+        """Sets each progenitor's b to the maximum of a_000 of the coefficient
+        set (scf_retune_a000); :meth:`scales` reads it."""
+        self._check_particles(pos, "pos")
+        _lib.scf_retune_a000(self._h, pos, mask)
 
     def recentre(self, pos, vel, acc, com=None, mask=None, max_iter: int = 100, tol: float = 1e-12):
         """Moves each progenitor's frame to its SCF centre (the maximum of a_000)

@@ -159,3 +159,58 @@ def test_invalid_arguments(scf):
     for kw in ({"max_iter": 0}, {"max_iter": 5000}, {"tol": -1.0}, {"tol": float("nan")}):
         with pytest.raises(_lib.ScfError, match="INVALID_ARG"):
             sim.recentre(p, v, a, None, **kw)
+
+
+# --------------------------------------------------------------- b at the maximum of a_000
+@pytest.mark.parametrize("alpha,masked,precision", [(0.5, False, "fp64"), (1.0, True, "fp64"), (1.5, False, "fp64"),
+                                                    (1.0, False, "mixed")])
+def test_retune_a000_matches_oracle(scf, alpha, masked, precision):
+    pos, _ = workloads.plummer(20000, seed=36)
+    n = pos.shape[0]
+    mask = (np.arange(n) % 3 != 1).astype(np.uint8) if masked else None
+    dt = torch.float64 if precision == "fp64" else torch.float32
+    p_ref = pos if precision == "fp64" else pos.astype(np.float32).astype(np.float64)
+    b_ref = oracle.a000_scale(p_ref, 0.3, alpha, mask=mask)
+    sim = scf.SCF(scf.Config(nmax=6, lmax=2, b=0.3, alpha=alpha, precision=precision), n=n)
+    sim.retune_a000(dev(pos, dt), None if mask is None else torch.tensor(mask, device="cuda"))
+    b = float(sim.scales().cpu().numpy()[0])
+    print(f"a_000 scale ({precision}, alpha {alpha}): GPU {b:.15g}, oracle {b_ref:.15g}")
+    # the parabola's vertex divides by a second difference of ~1e-7 h: rounding of h
+    # at 1e-16 moves it by ~1e-12 relative
+    assert abs(b - b_ref) < 1e-10 * b_ref
+
+
+def test_retune_a000_batched(scf):
+    sizes = [4000, 0, 2500]
+    scales = [1.0, 1.0, 0.6]
+    pos_l = []
+    for i, n in enumerate(sizes):
+        p, _ = workloads.plummer(max(n, 1), seed=50 + i)
+        p[:, :3] *= scales[i]
+        pos_l.append(p[:n])
+    offsets = np.concatenate([[0], np.cumsum(sizes)])
+    b0 = [0.3, 0.3, 0.2]
+    sim = scf.SCF(scf.Config(nmax=4, lmax=2, b=0.3, alpha=0.5), offsets=offsets, b_per_prog=b0)
+    sim.retune_a000(dev(np.concatenate(pos_l)))
+    b = sim.scales().cpu().numpy()
+    assert b[1] == b0[1]                                      # empty progenitor keeps its b
+    for i in (0, 2):
+        ref = oracle.a000_scale(pos_l[i], b0[i], 0.5)
+        assert abs(b[i] - ref) < 1e-10 * ref
+
+
+def test_evolve_with_a000_refresh(scf):
+    wl = workloads.plummer_eccentric(n=3000, seed=37, nsteps=1)
+    nmax, lmax = 8, 4
+    host = oracle.host_struct(wl.host)
+    a0 = oracle.forces(wl.pos, oracle.coeffs(wl.pos, nmax, lmax, wl.b), nmax, lmax, wl.b, com=wl.com, host=host)
+    ref = oracle.evolve(wl.pos, wl.vel, a0, nmax, lmax, wl.b, wl.dt, 12, com=wl.com, host=host, max_steps=3,
+                        retune_every=2, recentre=True, retune_rule="a000")
+    sim = scf.SCF(scf.Config(nmax=nmax, lmax=lmax, b=wl.b, dt=wl.dt, host=list(wl.host)), n=wl.n)
+    p, v, a, c = dev(wl.pos), dev(wl.vel), dev(a0), dev(wl.com[None])
+    sim.evolve(p, v, a, c, nsteps=12, max_steps=3, retune_every=2, recentre=True, retune_rule="a000")
+    b_gpu = float(sim.scales().cpu().numpy()[0])
+    ex = np.max(np.abs(p.cpu().numpy()[:, :3] - ref[0][:, :3]))
+    print(f"evolve with the a_000 refresh: b {b_gpu:.15g} ({ref[8]:.15g}), positions {ex:.1e}")
+    assert abs(b_gpu - ref[8]) < 1e-10 * ref[8]
+    assert ex < 1e-9 * np.max(np.abs(ref[0][:, :3]))
