@@ -83,7 +83,9 @@ def per_particle_bytes(elem):
 
 
 # sources that decide the code and launch shapes of the three step kernels
-STEP_SOURCES = ["scf_api.cu", "scf_coeffs.cu", "scf_device.cuh", "scf_forces.cu", "scf_internal.h", "scf_tables.cu"]
+# the sources of the step kernels' code (kernels 1-3, their device helpers and
+# tables); the launch shapes are fixed by --tiles in the capture command
+STEP_SOURCES = ["scf_coeffs.cu", "scf_device.cuh", "scf_forces.cu", "scf_tables.cu"]
 
 
 def src_hash():
