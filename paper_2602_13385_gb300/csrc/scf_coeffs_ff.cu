@@ -54,6 +54,7 @@ __global__ void __launch_bounds__(kFFTile) k1_partials_ff(K1Args a) {
     LS[i] = ff_from(c_tab.lsub[i]);
     LD[i] = ff_from(c_tab.ldiag[i]);
   }
+  __syncthreads();  // the tables above are read by every thread's basis
 
   const int prog = a.blk_prog[blockIdx.x];
   const double binv = 1.0 / a.b_prog[prog];

@@ -135,3 +135,27 @@ def test_adjoint_unaffected_by_the_variant(scf):
         res.append((xb.cpu().numpy(), vb.cpu().numpy(), cb.cpu().numpy(), th.cpu().numpy()))
     for a, b in zip(*res):
         assert np.array_equal(a, b)
+
+
+def test_ff_coefficients_after_other_kernels(scf):
+    """Kernel 1 in float-float stages its recurrence tables in shared memory;
+    it must not depend on what earlier kernels left there (a missing barrier
+    once let warps read tables another warp had not yet written).  Other
+    kernels that fill shared memory run in between, and every result is
+    checked against the oracle."""
+    pos, vel = workloads.plummer(2500, seed=85)
+    b = 0.3
+    ref = oracle.coeffs(pos, 20, 8, b)
+    scale = np.abs(ref).max()
+    cfg = scf.Config(nmax=20, lmax=8, b=b)
+    sim = scf.SCF(cfg, n=len(pos))
+    sim.set_tiles(k1_tile=128)
+    sim.set_tiles(k1_variant=2)
+    other = scf.SCF(scf.Config(nmax=20, lmax=8, b=b), n=len(pos))
+    p, v = dev(pos), dev(vel)
+    for _ in range(3):
+        other.bound(p, v)                                  # shared-memory j tiles and histograms
+        other.coeffs(p)                                    # the native kernel's staged rows
+        A = sim.coeffs(p).cpu().numpy()[0]
+        assert np.abs(A - ref).max() / scale < TOL
+    assert sim.status() == (0, 0)
