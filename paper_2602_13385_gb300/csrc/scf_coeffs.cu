@@ -91,8 +91,6 @@ __global__ void __launch_bounds__(TP) k1_partials(K1Args a) {
   const int64_t k_begin = a.blk_begin[blockIdx.x], k_end = a.blk_end[blockIdx.x];
   V4* pos4 = reinterpret_cast<V4*>(a.pos);
 
-  const T h = (T)(0.5 * a.dt), dt = (T)a.dt;                  // kick and drift
-  const T inv_al = (T)a.inv_alpha, al = (T)a.alpha;           // radial family (GEN)
   for (int64_t base = k_begin; base < k_end; base += TP) {
     const int64_t k = base + tid;
     T x = 0, y = 0, z = 0, mass = 0;
@@ -103,6 +101,7 @@ __global__ void __launch_bounds__(TP) k1_partials(K1Args a) {
         const V4* acc4 = reinterpret_cast<const V4*>(a.acc);
         V4 v = vel4[k];
         const V4 g = acc4[k];
+        const T h = (T)(0.5 * a.dt), dt = (T)a.dt;
         v.x += h * g.x;
         v.y += h * g.y;
         v.z += h * g.z;
@@ -128,9 +127,9 @@ __global__ void __launch_bounds__(TP) k1_partials(K1Args a) {
     const T s = r * binv;
     // alpha = 1: q = 1/(1+s), prefactor s^l q^(2l+1); alpha != 1: t = s^(1/alpha)
     // replaces s in q and xi, and q^alpha carries the prefactor s^l q^((2l+1) alpha)
-    const T q = (T)1 / ((T)1 + (GEN ? scf_pow(s, inv_al) : s));
+    const T q = (T)1 / ((T)1 + (GEN ? scf_pow(s, (T)a.inv_alpha) : s));
     const T xi = (T)1 - (T)2 * q;
-    const T qa = GEN ? scf_pow(q, al) : q;
+    const T qa = GEN ? scf_pow(q, (T)a.alpha) : q;
     const T sq2 = s * qa * qa;
     T Wc[LMAX + 1], Ws[LMAX + 1];
     Wc[0] = 1;
@@ -519,8 +518,6 @@ __global__ void __maxnreg__(128) k1_tiled(K1Args a) {
   const int64_t k_begin = a.blk_begin[blockIdx.x], k_end = a.blk_end[blockIdx.x];
   float4* pos4 = reinterpret_cast<float4*>(a.pos);
   const bool step = a.mode == SCF_MODE_STEP;
-  const float hk = (float)(0.5 * a.dt), dtk = (float)a.dt;           // kick and drift
-  const float inv_al = (float)a.inv_alpha, al = (float)a.alpha;      // radial family (GEN)
   int tiles = 0;
   for (int64_t base = k_begin; base < k_end; base += TP) {
     const bool last = base + TP >= k_end;
@@ -536,12 +533,13 @@ __global__ void __maxnreg__(128) k1_tiled(K1Args a) {
         if (step) {
           float4 v = reinterpret_cast<float4*>(a.vel)[k];
           const float4 g = reinterpret_cast<const float4*>(a.acc)[k];
-          v.x += hk * g.x;
-          v.y += hk * g.y;
-          v.z += hk * g.z;
-          p.x += dtk * v.x;
-          p.y += dtk * v.y;
-          p.z += dtk * v.z;
+          const float h = (float)(0.5 * a.dt), dt = (float)a.dt;
+          v.x += h * g.x;
+          v.y += h * g.y;
+          v.z += h * g.z;
+          p.x += dt * v.x;
+          p.y += dt * v.y;
+          p.z += dt * v.z;
           p_new = p;
           v_new = v;
         }
@@ -559,9 +557,9 @@ __global__ void __maxnreg__(128) k1_tiled(K1Args a) {
       const float u = x * rinv, v = y * rinv, c = z * rinv;
       const float s = r * binv;
       // alpha != 1: t = s^(1/alpha) in q and xi, q^alpha in the prefactor
-      const float qq = 1.f / (1.f + (B::kGen ? powf(s, inv_al) : s));
+      const float qq = 1.f / (1.f + (B::kGen ? powf(s, (float)a.inv_alpha) : s));
       const float xi = 1.f - 2.f * qq;
-      const float qv = B::kGen ? powf(qq, al) : qq;
+      const float qv = B::kGen ? powf(qq, (float)a.alpha) : qq;
       const float sq2 = s * qv * qv;
       B::run(q, Rs, Ys, t, NN, L, mass, u, v, c, qv, xi, sq2, SG);
     }

@@ -151,13 +151,11 @@ __global__ void __launch_bounds__(K3_TB) k3_forces(K3Args a) {
   // t = s^(1/alpha), q = 1/(1+t), the prefactor is s^l q^((2l+1) alpha) and
   // the radial derivative carries w = q t / s (= q at alpha = 1), set to 0 at
   // s = 0 where the terms it multiplies vanish (l >= 1) or have no direction
-  const T inv_al = (T)a.inv_alpha, al = (T)a.alpha, inv_al1 = (T)(a.inv_alpha - 1.0);
-  const T t = GEN ? k3_pow(s, inv_al) : s;
+  const T t = GEN ? k3_pow(s, (T)a.inv_alpha) : s;
   const T q = (T)1 / ((T)1 + t);
   const T xi = (T)1 - (T)2 * q;
-  const T qa = GEN ? k3_pow(q, al) : q;
-  const T w = GEN ? (s > (T)0 ? q * k3_pow(s, inv_al1) : (T)0) : q;
-  const T ial2 = (T)(2.0 * a.inv_alpha);  // 2 / alpha, for 4 lambda_l / alpha below
+  const T qa = GEN ? k3_pow(q, (T)a.alpha) : q;
+  const T w = GEN ? (s > (T)0 ? q * k3_pow(s, (T)(a.inv_alpha - 1.0)) : (T)0) : q;
   const T sq2 = s * qa * qa;
 
   T Wc[LMAX + 1], Ws[LMAX + 1];
@@ -234,7 +232,7 @@ __global__ void __launch_bounds__(K3_TB) k3_forces(K3Args a) {
       }
     }
     // radial prefactors; al4 = 4 lambda_l / alpha (4 (2l + 3/2) at alpha = 1)
-    const T al4 = GEN ? (T)(4 * (2 * l + 1)) + ial2 : (T)(4.0 * (2.0 * l + 1.5));
+    const T al4 = GEN ? (T)(4.0 * (2 * l + 1) + 2.0 * a.inv_alpha) : (T)(4.0 * (2.0 * l + 1.5));
     const T k1 = (l >= 1) ? binv * sl1q : (T)0;                                  // G/r per Z0
     const T k2a = binv * ((l >= 1 ? (T)l * sl1q : (T)0) - (T)(2 * l + 1) * slq * w);  // G' per Z0
     const T k2b = binv * al4 * slq * q * w;                                       // G' per Z1
