@@ -319,6 +319,39 @@ def escape_timing(sim, p, v, offsets, precision, clocks, torch, reps=3):
             "n_bound": float(st[:, 0].sum().item())}
 
 
+def refresh_timing(sim, p, v, torch, reps=3):
+    """Time the complete-refresh operations on the bench state (copies of the
+    particles, after one untimed call each): scf_recentre (the SCF centre,
+    density, core frame; 100 iterations at most) and scf_retune_a000 (b at the
+    maximum of a_000).  The latter changes the handle's scales, so this runs
+    last."""
+    from paper_2602_13385_gb300 import _lib
+    stream = sim.stream
+    pc, vc = p.clone(), v.clone()
+    ac = torch.empty_like(p)
+    out = {}
+    with torch.cuda.stream(stream):
+        res = _lib.scf_recentre(sim._h, sim.n_prog, pc, vc, ac, None, None, 100, 1e-12)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(reps):
+            _lib.scf_recentre(sim._h, sim.n_prog, pc, vc, ac, None, None, 100, 1e-12)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        out["recentre_ms"] = e0.elapsed_time(e1) / reps
+        out["recentre_iterations"] = float(res[:, 7].max())
+        _lib.scf_retune_a000(sim._h, p, None)
+        e0.record(stream)
+        for _ in range(reps):
+            _lib.scf_retune_a000(sim._h, p, None)
+        e1.record(stream)
+    torch.cuda.synchronize()
+    out["retune_a000_ms"] = e0.elapsed_time(e1) / reps
+    out["what"] = ("complete-refresh operations (Sec. 2, 2.1), per call on the bench state: re-centring "
+                   "(including its host read-back) and the a_000 scale search")
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -484,6 +517,8 @@ def main():
         if base is not None:
             line["cpu_baseline"] = base
             line["error_vs_oracle"] = oracle_error(sim, wl, ref, dtype, torch)
+    if not args.no_escape:
+        line["refresh"] = refresh_timing(sim, p, v, torch)
     sim.close()
     if rank == 0:
         print(json.dumps(line), flush=True)
