@@ -485,6 +485,8 @@ def expansion_centre(pos, b, alpha=1.0, mask=None, tol=1e-12, max_iter=100):
     x, m = pos[sel, :3], pos[sel, 3]
     xc = np.zeros(3)
     it = 0
+    if not (m.sum() > 0.0):     # an empty set (or no mass): the centre stays
+        return xc, 0
     for it in range(1, max_iter + 1):
         d = x - xc
         s2 = np.maximum((d[:, 0] * d[:, 0] + d[:, 1] * d[:, 1] + d[:, 2] * d[:, 2]) / (b * b), 1e-300)

@@ -214,3 +214,24 @@ def test_evolve_with_a000_refresh(scf):
     print(f"evolve with the a_000 refresh: b {b_gpu:.15g} ({ref[8]:.15g}), positions {ex:.1e}")
     assert abs(b_gpu - ref[8]) < 1e-10 * ref[8]
     assert ex < 1e-9 * np.max(np.abs(ref[0][:, :3]))
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_degenerate_sets(scf, precision):
+    dt = torch.float64 if precision == "fp64" else torch.float32
+    pos, vel = workloads.plummer(200, seed=38)
+    # nothing in the set: the frame stays, no core, particles untouched
+    sim = scf.SCF(scf.Config(nmax=4, lmax=2, b=0.3, precision=precision), n=200)
+    p, v, a = dev(pos, dt), dev(vel, dt), torch.zeros(200, 4, dtype=dt, device="cuda")
+    p0, v0 = p.clone(), v.clone()
+    out = sim.recentre(p, v, a, None, mask=torch.zeros(200, dtype=torch.uint8, device="cuda"))
+    assert np.all(out[0] == 0)
+    assert torch.equal(p, p0) and torch.equal(v, v0)
+    # one particle: the centre moves onto it; at r = 0 it has no core
+    sim1 = scf.SCF(scf.Config(nmax=4, lmax=2, b=0.3, precision=precision), n=1)
+    p1, v1 = dev(pos[:1], dt), dev(vel[:1], dt)
+    out = sim1.recentre(p1, v1, torch.zeros(1, 4, dtype=dt, device="cuda"), None)
+    tol = 1e-15 if precision == "fp64" else 1e-7
+    assert np.allclose(out[0, :3], p1.new_tensor(pos[:1, :3]).cpu().double().numpy()[0], rtol=0, atol=tol)
+    assert out[0, 6] == 0.0 and np.all(out[0, 3:6] == 0.0)
+    assert float(p1[0, :3].abs().max()) <= tol

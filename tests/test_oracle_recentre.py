@@ -176,3 +176,15 @@ def test_a000_scale_is_a_maximum_of_a000():
         for f in (1 - 1e-3, 1 + 1e-3):
             assert oracle.a000_biorth(pos, b * f, alpha, mask=mask) < a0
     assert oracle.a000_scale(pos, 0.3, 1.0, mask=np.zeros(5000, bool)) == 0.3     # empty set keeps b
+
+
+def test_recentre_degenerate_sets():
+    pos, vel = workloads.plummer(200, seed=29)
+    # nothing in the set: the frame stays, no core
+    p2, v2, c2, xc, V, rc, it = oracle.recentre(pos, vel, np.zeros(6), 4, 2, 0.3, 1.0, mask=np.zeros(200, bool))
+    assert it == 0 and np.all(xc == 0) and np.all(V == 0) and rc == 0.0
+    assert np.array_equal(p2, pos) and np.array_equal(v2, vel)
+    # one particle: the centre moves onto it; at r = 0 it has no core
+    one, v1 = pos[:1].copy(), vel[:1].copy()
+    p2, v2, c2, xc, V, rc, it = oracle.recentre(one, v1, np.zeros(6), 4, 2, 0.3, 1.0)
+    assert np.allclose(xc, one[0, :3], rtol=0, atol=1e-15) and rc == 0.0 and np.all(V == 0)
