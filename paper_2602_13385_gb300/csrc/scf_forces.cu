@@ -201,7 +201,11 @@ __global__ void __launch_bounds__(K3_TB) k3_forces(K3Args a) {
     {
       T cm1 = 0, c0 = 1;  // Ch_{n-2}, Ch_{n-1}
       T dm1 = 0, d0 = 1;  // Dh_{n-2}, Dh_{n-1}
-      for (int n = 1; n < NN; ++n) {
+      // The single-precision alpha = 1 kernel of the (20,10)-class degree bucket
+      // runs the radial loop unrolled by two (measured 3% faster there); every
+      // other instantiation keeps the compiler's choice (unrolling measured
+      // slower at lmax 8 and for alpha != 1).
+      auto radial_step = [&](int n) {
         const T cn = xi * c0 - k3_gbeta<T, GEN>(a, l, n) * cm1;
         const int o = n * a.nlm + lm0;
         if constexpr (kF2) {
@@ -229,6 +233,12 @@ __global__ void __launch_bounds__(K3_TB) k3_forces(K3Args a) {
         c0 = cn;
         dm1 = d0;
         d0 = dn;
+      };
+      if constexpr (kF2 && !GEN && LMAX == 10) {
+#pragma unroll 2
+        for (int n = 1; n < NN; ++n) radial_step(n);
+      } else {
+        for (int n = 1; n < NN; ++n) radial_step(n);
       }
     }
     // radial prefactors; al4 = 4 lambda_l / alpha (4 (2l + 3/2) at alpha = 1)
