@@ -319,6 +319,24 @@ def escape_timing(sim, p, v, offsets, precision, clocks, torch, reps=3):
             "n_bound": float(st[:, 0].sum().item())}
 
 
+def max_over_ranks(ms: float, device=None) -> float:
+    """The slowest rank's time, on every rank (the local time without a
+    process group, or with one rank)."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(ms)
+    t = torch.tensor([float(ms)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(units_per_rank: int, steps: int, world: int, ms_max: float) -> float:
+    """Units all ranks processed (independent replicas, weak scaling) per second
+    of the slowest rank."""
+    return units_per_rank * steps * world / (ms_max * 1e-3)
+
+
 def refresh_timing(sim, p, v, torch, reps=3):
     """Time the complete-refresh operations on the bench state (copies of the
     particles, after one untimed call each): scf_recentre (the SCF centre,
@@ -442,12 +460,8 @@ def main():
     if rc != 0:
         raise RuntimeError(f"device status {st} after the timed steps")
 
-    ms_max = ms_total
-    if dist is not None:
-        t = torch.tensor([ms_total], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_max = float(t.item())
-    value = wl.n * args.steps * world / (ms_max * 1e-3)
+    ms_max = max_over_ranks(ms_total, dev)
+    value = whole_job_rate(wl.n, args.steps, world, ms_max)
 
     # end to end through the public API with host buffers (pinned)
     h_in = [t.cpu().pin_memory() for t in (p, v, a, c)]
