@@ -271,6 +271,7 @@ def run_reference(args, rank, world):
 
 def workload_config(wl, precision, name):
     return {"workload": wl.name, "bench_name": name, "N": int(wl.n), "nmax": wl.nmax, "lmax": wl.lmax,
+            "alpha": wl.alpha,
             "precision": precision, "n_progenitors": 1 if wl.offsets is None else len(wl.offsets) - 1,
             "host": ("MilkyWayPotential2022 (Table A2)" if wl.name.startswith("paper_orbits") else
                      "NFW(Mvir=1e12,rs=20kpc)+MN(6.8e10,3,0.28kpc)+Hernquist(5e9,0.5kpc)") if wl.host else "none",
