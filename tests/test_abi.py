@@ -99,4 +99,6 @@ def test_null_handle_is_rejected(lib):
     assert lib.scf_set_mask(None, None) == -2
     assert lib.scf_get_scales(None, None) == -2
     assert lib.scf_evolve(None, None, None, None, None, 1, None, None, None, None, None) == -2
+    assert lib.scf_recentre(None, None, None, None, None, None, 100, 1e-12, None) == -2
+    assert lib.scf_retune_a000(None, None, None) == -2
     assert lib.scf_free(None) == 0
