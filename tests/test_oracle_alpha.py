@@ -233,3 +233,36 @@ def test_alpha_one_is_unchanged():
     assert oracle.knl(3, 2) == pytest.approx(2 * (0.5 * 3 * (3 + 8 + 3) + 3 * 5), rel=1e-15)
     pos, _ = workloads.plummer(50, seed=15)
     assert np.array_equal(oracle.coeffs(pos, 4, 3, b), oracle.coeffs(pos, 4, 3, b, alpha=1.0))
+
+
+def _random_rotation(seed):
+    q, r = np.linalg.qr(np.random.default_rng(seed).normal(size=(3, 3)))
+    q *= np.sign(np.diag(r))
+    if np.linalg.det(q) < 0:
+        q[:, 0] = -q[:, 0]
+    return q
+
+
+@pytest.mark.parametrize("alpha", [0.5, 1.0, 1.5])
+def test_rotation_invariance(alpha):
+    """A rotation of the sample leaves each degree's power E_l unchanged and
+    rotates the field: psi(R x; R sample) = psi(x; sample), a(R x) = R a(x).
+    This ties the relative normalisation of every order m (the (2 - delta_m0)
+    factor, N_lm, the sine terms) to geometry rather than to a formula."""
+    nmax, lmax, b = 6, 5, 0.35
+    pos, _ = workloads.plummer(600, seed=90)
+    pos[:, :3] += np.array([0.07, -0.04, 0.05])      # not centred: every m is present
+    Rm = _random_rotation(91)
+    rot = pos.copy()
+    rot[:, :3] = pos[:, :3] @ Rm.T
+    A = oracle.coeffs(pos, nmax, lmax, b, alpha=alpha)
+    Ar = oracle.coeffs(rot, nmax, lmax, b, alpha=alpha)
+    E, Er = oracle.power_l(A, nmax, lmax, b, alpha), oracle.power_l(Ar, nmax, lmax, b, alpha)
+    assert np.allclose(E, Er, rtol=1e-11, atol=0)
+    pts = np.random.default_rng(92).normal(size=(8, 4)) * 0.5
+    f = oracle.field(pts, A, nmax, lmax, b, alpha=alpha)
+    pr = pts.copy()
+    pr[:, :3] = pts[:, :3] @ Rm.T
+    fr = oracle.field(pr, Ar, nmax, lmax, b, alpha=alpha)
+    assert np.allclose(fr[:, 3], f[:, 3], rtol=1e-11)
+    assert np.allclose(fr[:, :3], f[:, :3] @ Rm.T, rtol=1e-10, atol=1e-12 * np.abs(f[:, :3]).max())
