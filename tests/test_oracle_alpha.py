@@ -266,3 +266,26 @@ def test_rotation_invariance(alpha):
     fr = oracle.field(pr, Ar, nmax, lmax, b, alpha=alpha)
     assert np.allclose(fr[:, 3], f[:, 3], rtol=1e-11)
     assert np.allclose(fr[:, :3], f[:, :3] @ Rm.T, rtol=1e-10, atol=1e-12 * np.abs(f[:, :3]).max())
+
+
+@pytest.mark.parametrize("alpha", [0.5, 1.0, 2.0])
+def test_joint_scaling_of_positions_and_b(alpha):
+    """Positions and b scaled together by lam: U_nl -> U_nl / lam and
+    I_nl -> I_nl / lam, so the coefficients are unchanged, the potential
+    scales as 1/lam and the acceleration as 1/lam^2 (every power of b in the
+    normalisation and the field is tied down)."""
+    nmax, lmax, b, lam = 6, 4, 0.3, 3.7
+    pos, _ = workloads.plummer(400, seed=93)
+    pos[:, :3] += np.array([0.03, 0.02, -0.05])
+    big = pos.copy()
+    big[:, :3] *= lam
+    A = oracle.coeffs(pos, nmax, lmax, b, alpha=alpha)
+    Ab = oracle.coeffs(big, nmax, lmax, lam * b, alpha=alpha)
+    assert np.allclose(Ab, A, rtol=1e-11, atol=1e-13 * np.abs(A).max())
+    pts = np.random.default_rng(94).normal(size=(6, 4)) * 0.4
+    f = oracle.field(pts, A, nmax, lmax, b, alpha=alpha)
+    ptsb = pts.copy()
+    ptsb[:, :3] *= lam
+    fb = oracle.field(ptsb, Ab, nmax, lmax, lam * b, alpha=alpha)
+    assert np.allclose(fb[:, 3], f[:, 3] / lam, rtol=1e-11)
+    assert np.allclose(fb[:, :3], f[:, :3] / lam ** 2, rtol=1e-10, atol=1e-12 * np.abs(f[:, :3]).max())
