@@ -556,15 +556,27 @@ def a000_biorth(pos, b, alpha=1.0, mask=None):
     return y00 / np.sqrt(abs(inl(0, 0, 1.0, alpha)) * b) * float(np.sum(pos[sel, 3] * a000_profile(r / b, alpha)))
 
 
-def a000_scale(pos, b0, alpha=1.0, mask=None, span=8.0, points=33, rounds=3):
+def a000_scale_slope(pos, lnb, alpha=1.0, mask=None):
+    """d ln a_000 / d ln b at b = exp(lnb) (alpha and the centre fixed).
+    With t_k = (r_k / b)^(1/alpha), g = (1 + t)^-alpha and -s g'(s) = t (1 + t)^(-alpha-1):
+    d ln h / d ln b = -1/2 + sum m t (1+t)^(-alpha-1) / sum m (1+t)^-alpha,
+    h(b) = b^(-1/2) sum m g(r/b) the b-dependent factor of a_000."""
+    pos = _f64(pos)
+    sel = np.ones(pos.shape[0], bool) if mask is None else np.asarray(mask, bool)
+    r = np.sqrt(np.sum(pos[sel, :3] ** 2, axis=1))
+    m = pos[sel, 3]
+    t = (r / np.exp(lnb)) ** (1.0 / alpha)
+    return -0.5 + float(np.sum(m * t * (1.0 + t) ** (-alpha - 1.0))) / float(np.sum(m * (1.0 + t) ** -alpha))
+
+
+def a000_scale(pos, b0, alpha=1.0, mask=None, span=8.0, points=257):
     """The basis scale that maximises :func:`a000_biorth` (Sec. 2: b tuned so
-    that the lowest mode approximates the cluster; the same criterion as the
-    centre, Sec. 2.1), searched in ln b: ``rounds`` grids of ``points`` values,
-    the first over [b0/span, b0 span], each next over one step either side of
-    the previous best; the best point of the last grid is moved to the vertex
-    of the parabola through it and its two neighbours (none at an edge).
-    Only the b-dependent factor b^(-1/2) sum m g(r/b) is compared.  An empty
-    set keeps b0."""
+    that the lowest mode approximates the cluster; Sec. 2.1: the same
+    criterion as the centre), over b in [b0/span, b0 span].  The largest of
+    the b-dependent factor h(b) = b^(-1/2) sum m g(r/b) on ``points`` values
+    of ln b brackets the maximum; inside the bracket the maximum is the root of
+    :func:`a000_scale_slope`, found by bisection to the last bit of ln b.  A
+    maximum at an end of the range returns that end; an empty set keeps b0."""
     pos = _f64(pos)
     sel = np.ones(pos.shape[0], bool) if mask is None else np.asarray(mask, bool)
     if not sel.any():
@@ -576,21 +588,23 @@ def a000_scale(pos, b0, alpha=1.0, mask=None, span=8.0, points=33, rounds=3):
         bb = np.exp(lnb)
         return bb ** -0.5 * float(np.sum(m * a000_profile(r / bb, alpha)))
 
-    lo = np.log(b0) - np.log(span)
-    step = 2.0 * np.log(span) / (points - 1)
-    for rnd in range(rounds):
-        hs = [h(lo + j * step) for j in range(points)]
-        j = int(np.argmax(hs))
-        if rnd + 1 < rounds:
-            lo = lo + (j - 1) * step
-            step = 2.0 * step / (points - 1)
-    x = lo + j * step
-    if 0 < j < points - 1:
-        hm, h0, hp = hs[j - 1], hs[j], hs[j + 1]
-        den = hm - 2.0 * h0 + hp
-        if den < 0.0:
-            x += 0.5 * step * (hm - hp) / den
-    return float(np.exp(x))
+    xs = np.linspace(np.log(b0) - np.log(span), np.log(b0) + np.log(span), points)
+    j = int(np.argmax([h(x) for x in xs]))
+    if j == 0 or j == points - 1:
+        return float(np.exp(xs[j]))
+    lo, hi = xs[j - 1], xs[j + 1]
+    slope = lambda x: a000_scale_slope(pos, x, alpha, mask)
+    if not (slope(lo) > 0.0 > slope(hi)):
+        return float(np.exp(xs[j]))
+    while True:
+        mid = 0.5 * (lo + hi)
+        if mid <= lo or mid >= hi:
+            break
+        if slope(mid) > 0.0:
+            lo = mid
+        else:
+            hi = mid
+    return float(np.exp(0.5 * (lo + hi)))
 
 
 def power_l(A, nmax, lmax, b, alpha=1.0):

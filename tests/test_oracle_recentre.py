@@ -153,7 +153,20 @@ def test_a000_scale_of_the_lowest_order_sphere_is_its_own(alpha):
     pos = _zhao_sphere(b_true, alpha, nodes=120)
     for b0 in (0.2, 0.37, 0.9):
         b = oracle.a000_scale(pos, b0, alpha)
-        assert b == pytest.approx(b_true, rel=1e-7)
+        assert b == pytest.approx(b_true, rel=1e-12)
+
+
+@pytest.mark.parametrize("alpha", [0.5, 1.0, 1.5])
+def test_a000_scale_slope_is_the_derivative_of_ln_a000(alpha):
+    """The stationarity condition the maximiser solves is d ln a_000 / d ln b,
+    by 4th-order central differences of the closed form a_000(b)."""
+    pos, _ = workloads.plummer(3000, seed=30)
+    mask = np.arange(3000) % 5 != 4
+    for b in (0.15, 0.3, 0.8):
+        x, h = math.log(b), 1e-3
+        f = lambda y: math.log(oracle.a000_biorth(pos, math.exp(y), alpha, mask=mask))
+        fd = (-f(x + 2 * h) + 8 * f(x + h) - 8 * f(x - h) + f(x - 2 * h)) / (12 * h)
+        assert oracle.a000_scale_slope(pos, x, alpha, mask=mask) == pytest.approx(fd, abs=1e-10)
 
 
 def test_a000_scale_of_samples():
@@ -173,8 +186,9 @@ def test_a000_scale_is_a_maximum_of_a000():
         # a_000 from the coefficient pass (S_000 sqrt|I_00| / N_00) agrees with the closed form
         S = oracle.coeffs(pos, 0, 0, b, mask=mask, alpha=alpha)[0]
         assert S * math.sqrt(abs(oracle.inl(0, 0, b, alpha))) * math.sqrt(4 * math.pi) == pytest.approx(a0, rel=1e-12)
-        for f in (1 - 1e-3, 1 + 1e-3):
+        for f in (1 - 1e-3, 1 + 1e-3, 1 - 1e-6, 1 + 1e-6):
             assert oracle.a000_biorth(pos, b * f, alpha, mask=mask) < a0
+        assert abs(oracle.a000_scale_slope(pos, math.log(b), alpha, mask=mask)) < 1e-14
     assert oracle.a000_scale(pos, 0.3, 1.0, mask=np.zeros(5000, bool)) == 0.3     # empty set keeps b
 
 
