@@ -93,6 +93,7 @@ def _load():
         "or_direct": (None, [i64, p, i64, p, d, p]),
         "or_power_l": (None, [p, i, i, d, d, p]),
         "or_num_threads": (i, []),
+        "or_lower_gamma": (d, [d, d]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -214,6 +215,12 @@ def density(pos, A, nmax, lmax, b, alpha=1.0):
     out = np.zeros(pos.shape[0])
     _load().or_density(pos.shape[0], _ptr(pos), _ptr(A), int(nmax), int(lmax), float(b), float(alpha), _ptr(out))
     return out
+
+
+def lower_gamma(a, x):
+    """Lower incomplete gamma function gamma(a, x) (unregularised), long double
+    series / continued fraction of the oracle (App. A bulge)."""
+    return _load().or_lower_gamma(float(a), float(x))
 
 
 def host_accel(host, x):

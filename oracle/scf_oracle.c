@@ -19,7 +19,9 @@
  *                particle is moved in -grad psi_SCF.
  *   - Sec. 2.1:  accelerating, non-rotating cluster frame whose origin follows
  *                a centre-of-mass test particle in the host potential.
- *   - App. A:    Hernquist, NFW and Miyamoto-Nagai host components.
+ *   - App. A:    Hernquist, NFW and Miyamoto-Nagai host components, and the
+ *                power-law bulge with an exponential cut-off of
+ *                MWPotential2014 (lower incomplete gamma function).
  *
  * Conventions (the paper's normalisation is a bi-orthonormal basis with a
  * leading minus in Eq. 3a; the reading below is the same expansion written
@@ -44,6 +46,7 @@
  * Particle storage: 4 doubles per particle, (x, y, z, m) for positions,
  * (vx, vy, vz, unused) for velocities, (ax, ay, az, potential) for accelerations.
  */
+#include <float.h>
 #include <math.h>
 #include <stdint.h>
 #include <stdlib.h>
@@ -367,17 +370,76 @@ void or_density(int64_t n_part, const double* pos, const double* A, int nmax, in
 }
 
 /* ------------------------------------------------------------------------ */
-/* Host potential (App. A): Hernquist, NFW, Miyamoto-Nagai                  */
+/* Host potential (App. A): Hernquist, NFW, Miyamoto-Nagai, cut-off bulge    */
 /* ------------------------------------------------------------------------ */
 
-enum { OR_HOST_HERNQUIST = 1, OR_HOST_NFW = 2, OR_HOST_MN = 3 };
+enum { OR_HOST_HERNQUIST = 1, OR_HOST_NFW = 2, OR_HOST_MN = 3, OR_HOST_POWCUT = 4 };
 
 typedef struct {
   int kind;
-  double M; /* Hernquist: total mass; NFW: scale mass M_NFW; MN: disk mass */
-  double a; /* Hernquist: scale radius; NFW: r_s; MN: scale length a */
-  double b; /* MN: scale height b; unused otherwise */
+  double M; /* Hernquist: total mass; NFW: scale mass M_NFW; MN: disk mass; bulge: total mass M_b */
+  double a; /* Hernquist: scale radius; NFW: r_s; MN: scale length a; bulge: cut-off radius r_c */
+  double b; /* MN: scale height b; bulge: power-law index alpha (rho ~ r^-alpha); unused otherwise */
 } or_host_comp;
+
+/* Lower incomplete gamma function gamma(a, x) = int_0^x t^(a-1) e^-t dt,
+ * a > 0, x >= 0, in long double.  For x < a + 1 the power series
+ *   gamma(a, x) = x^a e^-x sum_{n>=0} x^n / (a (a+1) ... (a+n))
+ * (Abramowitz & Stegun 6.5.4 with 6.5.29); otherwise gamma = Gamma(a) - Gamma(a, x)
+ * with the upper function from Legendre's continued fraction
+ *   Gamma(a, x) = x^a e^-x / (x + 1 - a - 1(1-a)/(x + 3 - a - 2(2-a)/(x + 5 - a - ...)))
+ * (A&S 6.5.31), evaluated forwards by the modified Lentz method. */
+static long double lower_gamma_l(long double a, long double x) {
+  if (!(x > 0)) return 0;
+  const long double eps = 4 * LDBL_EPSILON, tiny = 1e-300L;
+  const long double pref = expl(a * logl(x) - x);
+  if (x < a + 1) {
+    long double term = 1 / a, sum = term, ap = a;
+    for (int n = 1; n < 10000; ++n) {
+      ap += 1;
+      term *= x / ap;
+      sum += term;
+      if (fabsl(term) < fabsl(sum) * eps) break;
+    }
+    return pref * sum;
+  }
+  /* b_k = x + 2k + 1 - a, a_k = -k (k - a); f = b_0 + a_1/(b_1 + a_2/(b_2 + ...)) */
+  long double b = x + 1 - a, c = 1 / tiny, d = 1 / b, f = d;
+  for (int k = 1; k < 10000; ++k) {
+    const long double an = -k * (k - a);
+    b += 2;
+    d = an * d + b;
+    if (fabsl(d) < tiny) d = tiny;
+    c = b + an / c;
+    if (fabsl(c) < tiny) c = tiny;
+    d = 1 / d;
+    const long double delta = d * c;
+    f *= delta;
+    if (fabsl(delta - 1) < eps) break;
+  }
+  return tgammal(a) - pref * f;
+}
+
+double or_lower_gamma(double a, double x) { return (double)lower_gamma_l(a, x); }
+
+/* Power-law bulge with an exponential cut-off (App. A, MWPotential2014):
+ *   rho = rho0 (r_c/r)^alpha exp(-(r/r_c)^2),  s = (3 - alpha)/2,  x = (r/r_c)^2,
+ *   M_enc = M_b gamma(s, x)/Gamma(s),  f_r = -G M_enc/r^2,
+ *   psi = G M_b/Gamma(s) (gamma(1 - alpha/2, x)/r_c - gamma(s, x)/r),
+ *   d f_r/dr = 2 G M_b (gamma(s, x) - x^s e^-x)/(Gamma(s) r^3). */
+static void powcut_eval_l(long double GM, long double rc, long double alpha, long double r, long double* fr,
+                          long double* dfr, long double* psi) {
+  const long double s = 0.5L * (3 - alpha), x = (r / rc) * (r / rc), gs = tgammal(s);
+  const long double lg = lower_gamma_l(s, x);
+  if (psi) *psi = GM / gs * (lower_gamma_l(1 - 0.5L * alpha, x) / rc - (r > 0 ? lg / r : 0));
+  if (r > 0) {
+    if (fr) *fr = -GM * lg / (gs * r * r);
+    if (dfr) *dfr = 2 * GM * (lg - expl(s * logl(x) - x)) / (gs * r * r * r);
+  } else {
+    if (fr) *fr = 0;
+    if (dfr) *dfr = 0;
+  }
+}
 
 typedef struct {
   int n;
@@ -425,6 +487,13 @@ static void host_eval_l(const or_host* h, const long double* x, long double* a, 
       ax += -GM * x[0] / D3;
       ay += -GM * x[1] / D3;
       az += -GM * x[2] * zab / (zb * D3);
+    } else if (c->kind == OR_HOST_POWCUT) {
+      long double fr, p;
+      powcut_eval_l(GM, c->a, c->b, r, &fr, NULL, &p);
+      ps += p;
+      if (r > 0) {
+        ax += fr * x[0] / r; ay += fr * x[1] / r; az += fr * x[2] / r;
+      }
     }
   }
   a[0] = ax; a[1] = ay; a[2] = az;
@@ -456,7 +525,8 @@ void or_tidal(const or_host* h, const double* R, const double* x, double* a) {
  * with, from App. A,
  *   Hernquist: f_r = -GM/(r+a)^2,            d f_r/dr = 2GM/(r+a)^3
  *              (the printed 2GM (r/a)^3 / (r^3 (1+r/a)^3) is the same),
- *   NFW:       f_r = -GM g(u)/r^2, u = r/r_s, d f_r/dr = (2GM g/r^3) (1 - u^2 / (2 g (1+u)^2)).
+ *   NFW:       f_r = -GM g(u)/r^2, u = r/r_s, d f_r/dr = (2GM g/r^3) (1 - u^2 / (2 g (1+u)^2)),
+ *   bulge:     f_r = -G M_enc/r^2, d f_r/dr as printed in App. A (powcut_eval_l).
  * Miyamoto-Nagai (cylindrical R, z; z_ab = sqrt(z^2+b^2) + a, D^2 = R^2 + z_ab^2):
  *   f_R = -GM R/D^3,  f_z = -GM z z_ab/(sqrt(z^2+b^2) D^3),
  *   d f_R/dR = 3GM R^2/D^5 - GM/D^3,
@@ -474,13 +544,15 @@ static void tidal_tensor_l(const or_host* h, const long double* x, long double* 
   for (int i = 0; i < h->n; ++i) {
     const or_host_comp* c = &h->c[i];
     const long double GM = (long double)h->G * c->M;
-    if (c->kind == OR_HOST_HERNQUIST || c->kind == OR_HOST_NFW) {
+    if (c->kind == OR_HOST_HERNQUIST || c->kind == OR_HOST_NFW || c->kind == OR_HOST_POWCUT) {
       if (!(r > 0)) continue;
       long double fr, dfr;
       if (c->kind == OR_HOST_HERNQUIST) {
         const long double ra = r + c->a;
         fr = -GM / (ra * ra);
         dfr = 2 * GM / (ra * ra * ra);
+      } else if (c->kind == OR_HOST_POWCUT) {
+        powcut_eval_l(GM, c->a, c->b, r, &fr, &dfr, NULL);
       } else {
         const long double u = r / c->a;
         const long double g = log1pl(u) - u / (1 + u);

@@ -34,6 +34,7 @@ H0_KMS_MPC = 70.0
 HOST_HERNQUIST = 1
 HOST_NFW = 2
 HOST_MN = 3
+HOST_POWCUT = 4      # power-law bulge with an exponential cut-off (b holds the index alpha)
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 
@@ -311,8 +312,38 @@ def mw2022_physical():
     ]
 
 
+# MWPotential2014 (App. A "MWPotential2014" subsection and its table): the
+# components contribute f_b, f_d, f_h of the centripetal acceleration
+# f_cent = G M_s / r0^2 of a circular disk orbit at r0 = 8 kpc.
+MW2014_R0_KPC = 8.0
+MW2014_MS = 9.00273072e10         # scale mass M_s, Msun
+MW2014_F_CENT_PC_MYR2 = 6.32793804994
+
+
+def mw2014_physical():
+    """MWPotential2014 recast as in App. A (kind, M_msun, a_kpc, b): the
+    exponentially cut-off power-law bulge (alpha = 1.8, r_c = 1.9 kpc; b holds
+    alpha), the Miyamoto-Nagai disk (a = 3 kpc, b = 0.28 kpc) and the NFW halo
+    (R_s = 16 kpc, scale mass), with the masses that give each component its
+    fraction (0.05, 0.6, 0.35) of f_cent at r0 = 8 kpc:
+    M_b = f_b M_s Gamma(s)/gamma(s, (r0/r_c)^2), s = (3 - alpha)/2;
+    M_d = f_d M_s (r0^2 + (a + b)^2)^(3/2) / r0^3;  M_h = f_h M_s / g(r0/R_s),
+    g(u) = ln(1 + u) - u/(1 + u).  Lengths in kpc for G in kpc (km/s)^2/Msun."""
+    from scipy.special import gammainc      # regularised lower incomplete gamma
+    r0, alpha, rc, a, b, Rs = MW2014_R0_KPC, 1.8, 1.9, 3.0, 0.28, 16.0
+    s = 0.5 * (3.0 - alpha)
+    Mb = 0.05 * MW2014_MS / gammainc(s, (r0 / rc) ** 2)
+    Md = 0.6 * MW2014_MS * (r0 * r0 + (a + b) ** 2) ** 1.5 / r0 ** 3
+    u = r0 / Rs
+    Mh = 0.35 * MW2014_MS / (math.log1p(u) - u / (1.0 + u))
+    return [(HOST_POWCUT, Mb, rc, alpha), (HOST_MN, Md, a, b), (HOST_NFW, Mh, Rs, 0.0)]
+
+
 def host_in_units(components_phys, units: Units):
-    return [(k, units.mass(M), units.length(a), units.length(b)) for (k, M, a, b) in components_phys]
+    """Host components in the cluster's Henon units (b is a length except for
+    the cut-off bulge, whose b is its dimensionless power-law index)."""
+    return [(k, units.mass(M), units.length(a), b if k == HOST_POWCUT else units.length(b))
+            for (k, M, a, b) in components_phys]
 
 
 # --------------------------------------------------------------------------
