@@ -404,7 +404,8 @@ def zhao_half_mass_scale(r50, alpha=1.0):
 
 
 def evolve(pos, vel, acc, nmax, lmax, b, dt, nsteps, G=1.0, com=None, host=None, kin=0.5, frac=0.999,
-           eta=1.0 / 400.0, max_steps=1000, retune_every=0, alpha=1.0, recentre=False, retune_rule="half_mass"):
+           eta=1.0 / 400.0, max_steps=1000, retune_every=0, alpha=1.0, recentre=False, retune_rule="half_mass",
+           alpha_range=(0.25, 2.0), return_alpha=False):
     """Leapfrog with the escape physics of Sec. 2.2.  At the start of every
     integration timestep: the boundedness test and the coefficient set
     r <= r_x (:func:`boundedness`); at every ``retune_every``-th integration
@@ -413,7 +414,9 @@ def evolve(pos, vel, acc, nmax, lmax, b, dt, nsteps, G=1.0, com=None, host=None,
     (:func:`recentre`, over the coefficient set) and takes the boundedness
     again in it, then
     retunes the basis scale b (alpha fixed): with ``retune_rule="a000"`` to
-    the maximum of a_000 (:func:`a000_scale`, over the coefficient set), else
+    the maximum of a_000 (:func:`a000_scale`, over the coefficient set); with
+    ``"alpha_a000"`` alpha and b together at the joint maximum of a_000
+    (:func:`a000_alpha_scale`, alpha in ``alpha_range``); else
     to the scale of the lowest-order
     density whose half-mass radius is the bound stars' energy-based one,
     :func:`zhao_half_mass_scale` (alpha = 1: b = r_50 / (1 + sqrt 2)); the field
@@ -425,7 +428,8 @@ def evolve(pos, vel, acc, nmax, lmax, b, dt, nsteps, G=1.0, com=None, host=None,
 
     Returns ``(pos, vel, acc, com, bound, mask, stats, n_int, b)`` with
     ``bound``, ``mask`` and ``stats = (n_bound, M_bound, r_x, set size)`` as
-    of the start of the last integration timestep and ``b`` the scale in use."""
+    of the start of the last integration timestep and ``b`` the scale in use
+    (``return_alpha``: and then the exponent in use)."""
     pos = _f64(pos).copy()
     vel = _f64(vel).copy()
     com = np.zeros(6) if com is None else _f64(com).copy()
@@ -444,6 +448,9 @@ def evolve(pos, vel, acc, nmax, lmax, b, dt, nsteps, G=1.0, com=None, host=None,
                 stats = np.array([bound.sum(), Mb, np.sqrt(rx2), mask.sum()], dtype=np.float64)
             if retune_rule == "a000":   # b maximising a_000 of the coefficient set
                 b = a000_scale(pos, b, alpha, mask=mask)
+            elif retune_rule == "alpha_a000":   # alpha and b at the joint maximum
+                alpha, bs = a000_alpha_scale(pos, alpha, b, mask=mask, alpha_range=alpha_range)
+                b = float(bs[0])
             elif bound.any():
                 r50 = np.sqrt(boundedness(pos, vel, G, kin, 0.5)[2])
                 b = zhao_half_mass_scale(r50, alpha)
@@ -463,6 +470,8 @@ def evolve(pos, vel, acc, nmax, lmax, b, dt, nsteps, G=1.0, com=None, host=None,
             com = c2
         done += k
         n_int += 1
+    if return_alpha:
+        return pos, vel, acc, com, bound, mask, stats, n_int, b, alpha
     return pos, vel, acc, com, bound, mask, stats, n_int, b
 
 
@@ -612,6 +621,93 @@ def a000_scale(pos, b0, alpha=1.0, mask=None, span=8.0, points=257):
         else:
             hi = mid
     return float(np.exp(0.5 * (lo + hi)))
+
+
+def dln_i00_dalpha(alpha):
+    """d ln|I_00| / d alpha of the lowest pair's normalisation (at b = 1),
+    I_00 = -(alpha + 1) Gamma(2 alpha + 1) / (2^(4 alpha + 3) (alpha + 1/2) Gamma(alpha + 1/2)^2)
+    (the n = l = 0 case of the closed form in the Zhao family):
+    1/(alpha+1) + 2 psi(2 alpha + 1) - 4 ln 2 - 1/(alpha + 1/2) - 2 psi(alpha + 1/2)."""
+    from scipy.special import digamma
+    a = float(alpha)
+    return 1.0 / (a + 1.0) + 2.0 * digamma(2.0 * a + 1.0) - 4.0 * np.log(2.0) - 1.0 / (a + 0.5) - 2.0 * digamma(a + 0.5)
+
+
+def a000_alpha_slope(pos, alpha, b, mask=None):
+    """d ln a_000 / d alpha at fixed b and centre (bi-orthonormal normalisation):
+    -1/2 d ln|I_00|/d alpha + sum m g d ln g/d alpha / sum m g, with g = (1 + t)^-alpha,
+    t = (r/b)^(1/alpha) and d ln g / d alpha = -ln(1 + t) + t ln(r/b) / (alpha (1 + t))."""
+    pos = _f64(pos)
+    sel = np.ones(pos.shape[0], bool) if mask is None else np.asarray(mask, bool)
+    r = np.sqrt(np.sum(pos[sel, :3] ** 2, axis=1))
+    m = pos[sel, 3]
+    s = r / b
+    t = s ** (1.0 / alpha)
+    g = (1.0 + t) ** -alpha
+    with np.errstate(divide="ignore", invalid="ignore"):
+        tls = np.where(s > 0.0, t * np.log(np.where(s > 0.0, s, 1.0)), 0.0)
+    dlng = -np.log1p(t) + tls / (alpha * (1.0 + t))
+    return -0.5 * dln_i00_dalpha(alpha) + float(np.sum(m * g * dlng)) / float(np.sum(m * g))
+
+
+def a000_alpha_scale(pos, alpha0, b0, offsets=None, mask=None, alpha_range=(0.25, 2.0), points=33, span=8.0):
+    """The exponent alpha of the radial family (Eq. 4) and the scales b_p that
+    maximise a_000 (the same criterion as b alone; Secs. 2 and 2.2: a complete
+    refresh retunes alpha and b).  One alpha is shared by the progenitors
+    (``offsets``, as in a batched handle): it maximises the product of their
+    a_000, each at its own maximising b_p(alpha) (:func:`a000_scale`).  By the
+    envelope theorem d/d alpha of sum_p ln a_000,p(alpha, b_p(alpha)) is the sum
+    of :func:`a000_alpha_slope` at b_p(alpha).  ``points`` values of ln alpha over
+    ``alpha_range`` bracket the maximum of that sum; bisection on its slope
+    finds it to the last bit (an end of the range returns that end).
+    Progenitors with an empty set keep b0 and take no part.  Returns
+    ``(alpha, b)`` with b an array of the progenitors' scales."""
+    pos = _f64(pos)
+    offsets = [0, pos.shape[0]] if offsets is None else [int(o) for o in offsets]
+    b0 = np.broadcast_to(np.asarray(b0, dtype=np.float64), (len(offsets) - 1,)).copy()
+    sel = np.ones(pos.shape[0], bool) if mask is None else np.asarray(mask, bool)
+    live = [p for p in range(len(offsets) - 1) if sel[offsets[p]:offsets[p + 1]].any()]
+    if not live:
+        return float(alpha0), b0
+
+    def parts(p):
+        lo, hi = offsets[p], offsets[p + 1]
+        return pos[lo:hi], sel[lo:hi]
+
+    def scales(al):
+        b = b0.copy()
+        for p in live:
+            q, m = parts(p)
+            b[p] = a000_scale(q, b0[p], al, mask=m, span=span)
+        return b
+
+    def H(al):
+        b = scales(al)
+        return sum(np.log(a000_biorth(*parts(p)[:1], b[p], al, mask=parts(p)[1])) for p in live)
+
+    def dH(al):
+        b = scales(al)
+        return sum(a000_alpha_slope(parts(p)[0], al, b[p], mask=parts(p)[1]) for p in live)
+
+    xs = np.linspace(np.log(alpha_range[0]), np.log(alpha_range[1]), points)
+    j = int(np.argmax([H(np.exp(x)) for x in xs]))
+    if j == 0 or j == points - 1:
+        al = float(np.exp(xs[j]))
+        return al, scales(al)
+    lo, hi = xs[j - 1], xs[j + 1]
+    if not (dH(np.exp(lo)) > 0.0 > dH(np.exp(hi))):
+        al = float(np.exp(xs[j]))
+        return al, scales(al)
+    while True:
+        mid = 0.5 * (lo + hi)
+        if mid <= lo or mid >= hi:
+            break
+        if dH(np.exp(mid)) > 0.0:
+            lo = mid
+        else:
+            hi = mid
+    al = float(np.exp(0.5 * (lo + hi)))
+    return al, scales(al)
 
 
 def power_l(A, nmax, lmax, b, alpha=1.0):

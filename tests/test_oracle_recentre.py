@@ -202,3 +202,62 @@ def test_recentre_degenerate_sets():
     one, v1 = pos[:1].copy(), vel[:1].copy()
     p2, v2, c2, xc, V, rc, it = oracle.recentre(one, v1, np.zeros(6), 4, 2, 0.3, 1.0)
     assert np.allclose(xc, one[0, :3], rtol=0, atol=1e-15) and rc == 0.0 and np.all(V == 0)
+
+
+# --------------------------------------------------------------- alpha and b at the maximum of a_000
+def test_lowest_pair_normalisation_derivative():
+    """d ln|I_00|/d alpha (digamma form) against central differences of the
+    oracle's own closed-form I_00(alpha)."""
+    for al in (0.3, 0.7, 1.0, 1.9, 3.0):
+        h = 1e-5
+        fd = (math.log(abs(oracle.inl(0, 0, 1.0, al + h))) - math.log(abs(oracle.inl(0, 0, 1.0, al - h)))) / (2 * h)
+        assert oracle.dln_i00_dalpha(al) == pytest.approx(fd, rel=1e-8)
+
+
+@pytest.mark.parametrize("alpha", [0.5, 1.0, 1.5])
+def test_a000_alpha_slope_is_the_derivative_of_ln_a000(alpha):
+    pos, _ = workloads.plummer(3000, seed=31)
+    mask = np.arange(3000) % 7 != 2
+    for b in (0.2, 0.45):
+        h = 1e-4
+        f = lambda al: math.log(oracle.a000_biorth(pos, b, al, mask=mask))
+        fd = (-f(alpha + 2 * h) + 8 * f(alpha + h) - 8 * f(alpha - h) + f(alpha - 2 * h)) / (12 * h)
+        assert oracle.a000_alpha_slope(pos, alpha, b, mask=mask) == pytest.approx(fd, abs=1e-9)
+
+
+@pytest.mark.parametrize("alpha0", [0.5, 0.7, 1.0, 1.5])
+def test_alpha_and_b_of_the_lowest_order_sphere_are_its_own(alpha0):
+    """Cauchy-Schwarz in the energy inner product over the whole family: the
+    unit-energy lowest pair of (alpha, b) projects a density most strongly
+    when its density is that density, so the joint maximum of a_000 over
+    (alpha, b) returns the projected sphere's own exponent and scale."""
+    pos = _zhao_sphere(0.37, alpha0, nodes=160)
+    al, b = oracle.a000_alpha_scale(pos, 1.0, 0.3)
+    assert al == pytest.approx(alpha0, rel=1e-8)
+    assert b[0] == pytest.approx(0.37, rel=1e-10)
+
+
+def test_alpha_and_b_of_samples_and_of_a_batch():
+    a = 3 * math.pi / 16
+    pos, _ = workloads.plummer(10000, seed=26)                # the alpha = 1/2 lowest-order sphere
+    al, b = oracle.a000_alpha_scale(pos, 1.0, 0.3)
+    assert al == pytest.approx(0.5, rel=0.02) and b[0] == pytest.approx(a, rel=0.02)
+    hp = workloads.hernquist_positions(10000, 0.4, seed=28)   # the alpha = 1 one
+    al, b = oracle.a000_alpha_scale(hp, 0.7, 0.3)
+    assert al == pytest.approx(1.0, rel=0.03) and b[0] == pytest.approx(0.4, rel=0.03)
+    # a joint maximum: a_000 falls when alpha moves with b re-maximised
+    def H(x):
+        return math.log(oracle.a000_biorth(hp, oracle.a000_scale(hp, 0.4, x), x))
+    for f in (1 - 1e-3, 1 + 1e-3):
+        assert H(al * f) < H(al)
+    # a batch shares alpha; each progenitor keeps its own b; an empty one keeps b0
+    p1, _ = workloads.plummer(5000, seed=1)
+    p2, _ = workloads.plummer(6000, seed=2)
+    p2[:, :3] *= 0.6
+    P = np.concatenate([p1, p2])
+    mask = np.ones(11000, bool)
+    al, b = oracle.a000_alpha_scale(np.concatenate([P, P[:10]]), 1.0, [0.3, 0.2, 0.25],
+                                    offsets=[0, 5000, 11000, 11010],
+                                    mask=np.concatenate([mask, np.zeros(10, bool)]))
+    assert al == pytest.approx(0.5, rel=0.03)
+    assert b[0] == pytest.approx(a, rel=0.03) and b[1] == pytest.approx(0.6 * a, rel=0.03) and b[2] == 0.25
