@@ -6,15 +6,23 @@ A step is one pass of the whole hot path (scf_step with nsteps = 1): half kick
 step (kernel 2), field + tidal term + half kick (kernel 3).  One step
 evaluates one force per particle, so value = particles x steps / device time.
 
-Default workload: King W0 = 6 cluster, N = 1e5 (1e5 Msun, r_h = 3 pc) on a
-circular orbit at R = 8 kpc in the NFW + Miyamoto-Nagai + Hernquist host,
-nmax = 20, lmax = 8, double precision.  Inputs are seeded and synthetic.
+Default (the headline line): a Plummer cluster of N = 1e6 (2e5 Msun, r_h =
+4 pc) on the 5-20 kpc eccentric orbit in the NFW + Miyamoto-Nagai +
+Hernquist host, nmax = 20, lmax = 10, double precision: the largest
+single-cluster workload, in the paper's precision.  The same run adds, as the
+keys "mixed" and "batch", the same cluster in mixed precision (FP32 basis and
+field, FP64 sums and centre) and the batch of ten King progenitors of uneven
+N (1.91e6 in all) on their own orbits in mixed precision, each with its own
+timing, roofline, end-to-end rate, clocks, CPU baseline and error against the
+FP64 oracle.  Inputs are seeded and synthetic; samples are rounded to float32
+values so that both precisions start from the same state.
 
   python bench.py [--steps K] [--warmup W] [--gpus N] [--workload NAME] [--impl ours|reference]
 
-With torchrun (N > 1) every rank runs an independent replica of the workload
-(the step has no cross-GPU exchange in this build); value = all ranks'
-evaluations / max rank time.  Prints one JSON line on rank 0.
+With --workload only that line is run.  With torchrun (N > 1) every rank runs
+an independent replica of the workload (the step has no cross-GPU exchange in
+this build); value = all ranks' evaluations / max rank time.  Prints one JSON
+line on rank 0.
 """
 from __future__ import annotations
 
@@ -35,7 +43,11 @@ sys.path.insert(0, ROOT)
 METRIC = "SCF particle-force evals/s on 1 GB300 at stated err vs FP64 oracle; % FP roofline"
 UNIT = "particle-force evals/s"
 L2_FLUSH_BYTES = 256 << 20           # > 129 MB L2
-FP64_FMA_PER_SM_CLK = 2              # measured: 1.20 TFLOP/s FP64 FMA chains at 1995 MHz on 152 SMs
+# Nominal non-tensor FMA units per SM and clock on GB300 (sm_103): 128 FP32
+# lanes; FP64 at 1/64 of that rate.  The roofline peak is these unit counts x
+# 152 SMs x 2 flops x the maximum SM clock; the FMA-chain kernel scf_fma_peak
+# measures the achievable rate beside it ("peak_measured").
+FP64_FMA_PER_SM_CLK = 2
 FP32_FMA_PER_SM_CLK = 128
 N_SM = 152
 
@@ -62,7 +74,10 @@ FF_WORKLOADS = {"king_circular_fp64ff", "plummer_eccentric_fp64ff"}
 BUILDER_ARGS = {"paper_orbits": {"n_per": 200_000}}
 # per workload (not builder): the double-precision Clutton-Brock line runs N = 1e5
 WORKLOAD_ARGS = {"plummer_eccentric_cb_fp64": {"n": 100_000}}
-DEFAULT_WORKLOAD = "king_circular_fp64"
+DEFAULT_WORKLOAD = "plummer_eccentric_fp64"
+# lines of the default run: (JSON key, workload); the first is the headline
+DEFAULT_LINES = [("headline", "plummer_eccentric_fp64"), ("mixed", "plummer_eccentric_mixed"),
+                 ("batch", "batch10_mixed")]
 
 
 def per_particle_flops(nmax, lmax):
@@ -153,9 +168,14 @@ def build_workload(name, n_override=None):
     if n_override is not None:
         if "n_per" in kw:
             kw["n_per"] = max(1, n_override // 10)
+        elif builder == "progenitor_batch":
+            kw["scale"] = n_override / 1.91e6
         else:
             kw["n"] = n_override
-    return fn(**kw), precision
+    wl = fn(**kw)
+    wl.pos = _f32_exact(wl.pos)
+    wl.vel = _f32_exact(wl.vel)
+    return wl, precision
 
 
 def traffic_for(kernel: str, workload: str):
@@ -174,55 +194,95 @@ def traffic_for(kernel: str, workload: str):
     return None
 
 
-def cpu_baseline(wl, precision, steps=2):
-    """The FP64 oracle timed on the host cores on the same workload (full N,
-    `steps` leapfrog steps), plus the GPU-vs-oracle error on that first step."""
+def _f32_exact(a):
+    """float64 array holding float32-representable values (the mixed-precision
+    state then equals the double-precision one exactly)."""
+    import numpy as np
+    return np.asarray(a, dtype=np.float32).astype(np.float64)
+
+
+def oracle_sample(wl):
+    """Progenitors the oracle checks: all of a single cluster; for a batch the
+    three smallest (a bounded, stated sample of the same launch)."""
+    if wl.offsets is None:
+        return [0]
+    sizes = [int(wl.offsets[i + 1] - wl.offsets[i]) for i in range(len(wl.offsets) - 1)]
+    return sorted(sorted(range(len(sizes)), key=lambda i: sizes[i])[:3])
+
+
+def oracle_reference(wl):
+    """The FP64 oracle on the sampled progenitors: the initial acceleration
+    (untimed) and one leapfrog step from it (timed: the CPU baseline)."""
     import numpy as np
     import oracle
     host = oracle.host_struct(wl.host) if wl.host else None
-    com = wl.com if wl.host else np.zeros(6)
-    t0 = time.perf_counter()
-    A0 = oracle.coeffs(wl.pos, wl.nmax, wl.lmax, wl.b, alpha=wl.alpha)
-    acc0 = oracle.forces(wl.pos, A0, wl.nmax, wl.lmax, wl.b, com=com, host=host, alpha=wl.alpha)
-    t_init = time.perf_counter() - t0
-    t0 = time.perf_counter()
-    p1, v1, a1, c1, A1 = oracle.step(wl.pos, wl.vel, acc0, wl.nmax, wl.lmax, wl.b, wl.dt, 1, com=com, host=host,
-                                     alpha=wl.alpha)
-    t1 = time.perf_counter() - t0
-    t_rest = 0.0
-    if steps > 1:
+    refs, n_done, secs, t_init = [], 0, 0.0, 0.0
+    for p in oracle_sample(wl):
+        if wl.offsets is None:
+            lo, hi, b, com = 0, wl.n, wl.b, (wl.com if wl.host else np.zeros(6))
+        else:
+            lo, hi = int(wl.offsets[p]), int(wl.offsets[p + 1])
+            b, com = float(wl.b_per_prog[p]), np.array(wl.com_per_prog[p])
+        pos, vel = wl.pos[lo:hi], wl.vel[lo:hi]
         t0 = time.perf_counter()
-        oracle.step(p1, v1, a1, wl.nmax, wl.lmax, wl.b, wl.dt, steps - 1, com=c1, host=host, alpha=wl.alpha)
-        t_rest = time.perf_counter() - t0
-    secs = t1 + t_rest
-    return {
-        "value": wl.n * steps / secs, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
-        "sample": f"{steps} full leapfrog steps of the same workload (N={wl.n}) by the FP64 C oracle "
-                  f"(OpenMP, {oracle.num_threads()} threads); initial force evaluation {t_init:.2f} s not counted",
-        "seconds": secs,
-    }, (wl.pos, wl.vel, acc0, com, p1, v1, a1, A1)
+        A0 = oracle.coeffs(pos, wl.nmax, wl.lmax, b, alpha=wl.alpha)
+        acc0 = oracle.forces(pos, A0, wl.nmax, wl.lmax, b, com=com, host=host, alpha=wl.alpha)
+        t1 = time.perf_counter()
+        p1, v1, a1, c1, A1 = oracle.step(pos, vel, acc0, wl.nmax, wl.lmax, b, wl.dt, 1, com=com, host=host,
+                                         alpha=wl.alpha)
+        t2 = time.perf_counter()
+        t_init += t1 - t0
+        secs += t2 - t1
+        n_done += hi - lo
+        refs.append((p, lo, hi, acc0, p1, v1, a1, c1, A1))
+    if wl.offsets is None:
+        sample = (f"one full leapfrog step of the same workload (N={wl.n}) by the FP64 C oracle "
+                  f"(OpenMP, {oracle.num_threads()} threads); the initial force evaluation ({t_init:.1f} s) not counted")
+    else:
+        ps = [r[0] for r in refs]
+        sample = (f"one leapfrog step of progenitors {ps} of the batch (the three smallest, N={n_done} of {wl.n}) by "
+                  f"the FP64 C oracle (OpenMP, {oracle.num_threads()} threads); initial force evaluation not counted")
+    base = {"value": n_done / secs, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle", "sample": sample,
+            "seconds": secs}
+    return base, refs
 
 
-def oracle_error(sim, wl, ref, dtype, torch):
-    """Error of one GPU step against the oracle's step from the same state."""
+def oracle_error(sim, wl, refs, dtype, torch, use_com):
+    """Error of one GPU step against the oracle's step from the same state
+    (positions, velocities, the oracle's initial accelerations, centres), on
+    the sampled progenitors; the GPU steps the whole launch."""
     import numpy as np
-    pos, vel, acc0, com, p1, v1, a1, A1 = ref
     dev = sim.device
-    p = torch.tensor(pos, device=dev, dtype=dtype)
-    v = torch.tensor(vel, device=dev, dtype=dtype)
-    a = torch.tensor(acc0, device=dev, dtype=dtype)
-    c = torch.tensor(com[None], device=dev, dtype=torch.float64)
-    sim.step(p, v, a, com=c if wl.host else None, nsteps=1)
-    A = sim.last_coeffs().cpu().numpy()[0]
+    p = torch.tensor(wl.pos, device=dev, dtype=dtype)
+    v = torch.tensor(wl.vel, device=dev, dtype=dtype)
+    coms = wl.com[None] if wl.com_per_prog is None else wl.com_per_prog
+    c = torch.tensor(coms, device=dev, dtype=torch.float64)
+    a = sim.forces(p, sim.coeffs(p), com=c if use_com is not None else None)
+    for (_, lo, hi, acc0, *_rest) in refs:
+        a[lo:hi] = torch.tensor(acc0, device=dev, dtype=dtype)
+    sim.step(p, v, a, com=c if use_com is not None else None, nsteps=1)
+    A = sim.last_coeffs().cpu().numpy()
     ag = a.cpu().double().numpy()
-    na = np.linalg.norm(a1[:, :3], axis=1)
-    rel = np.linalg.norm(ag[:, :3] - a1[:, :3], axis=1) / np.maximum(na, 1e-6 * np.median(na))
-    return {
-        "coeff_max_rel": float(np.max(np.abs(A - A1)) / np.max(np.abs(A1))),
-        "accel_rel_median": float(np.median(rel)), "accel_rel_max": float(np.max(rel)),
-        "pos_max_abs": float(np.max(np.abs(p.cpu().double().numpy()[:, :3] - p1[:, :3]))),
-        "what": "one leapfrog step from the same state, GPU vs the FP64 oracle",
+    pg = p.cpu().double().numpy()
+    cg = c.cpu().numpy()
+    coeff, rel_all, pos_err, com_err = 0.0, [], 0.0, 0.0
+    for (prog, lo, hi, acc0, p1, v1, a1, c1, A1) in refs:
+        coeff = max(coeff, float(np.max(np.abs(A[prog] - A1)) / np.max(np.abs(A1))))
+        na = np.linalg.norm(a1[:, :3], axis=1)
+        rel_all.append(np.linalg.norm(ag[lo:hi, :3] - a1[:, :3], axis=1) / np.maximum(na, 1e-6 * np.median(na)))
+        pos_err = max(pos_err, float(np.max(np.abs(pg[lo:hi, :3] - p1[:, :3]))))
+        if use_com is not None:
+            com_err = max(com_err, float(np.max(np.abs(cg[prog] - c1) / np.maximum(np.abs(c1), 1e-300))))
+    rel = np.concatenate(rel_all)
+    out = {
+        "coeff_max_rel": coeff, "accel_rel_median": float(np.median(rel)), "accel_rel_p99": float(np.quantile(rel, 0.99)),
+        "accel_rel_max": float(np.max(rel)), "pos_max_abs": pos_err,
+        "what": "one leapfrog step from the same state, GPU vs the FP64 oracle"
+                + ("" if wl.offsets is None else f" (progenitors {[r[0] for r in refs]} of the batched launch)"),
     }
+    if use_com is not None:
+        out["centre_max_rel"] = com_err
+    return out
 
 
 # --------------------------------------------------------------------- reference arm
@@ -235,17 +295,23 @@ def run_reference(args, rank, world):
     import numpy as np
     com = wl.com if wl.host else np.zeros(6)
     # bounded sample: the whole warm-up + timed run near <= 2 minutes of host
-    # time (at most 3 s a step)
+    # time (at most 3 s a step); the per-particle cost is measured on a probe
+    # of 20000 particles (one coefficient + force evaluation, as in a step)
     per_step = min(3.0, 120.0 / max(1, args.steps + args.warmup))
+    n0 = min(wl.n, 20000)
+    probe = wl.pos[:n0].copy()
+    probe[:, 3] *= wl.n / n0
     t0 = time.perf_counter()
-    A0 = oracle.coeffs(wl.pos, wl.nmax, wl.lmax, wl.b, alpha=wl.alpha)
-    acc = oracle.forces(wl.pos, A0, wl.nmax, wl.lmax, wl.b, com=com, host=host, alpha=wl.alpha)
-    t_full = time.perf_counter() - t0
+    A0 = oracle.coeffs(probe, wl.nmax, wl.lmax, wl.b, alpha=wl.alpha)
+    oracle.forces(probe, A0, wl.nmax, wl.lmax, wl.b, com=com, host=host, alpha=wl.alpha)
+    t_probe = time.perf_counter() - t0
     n = wl.n
-    if t_full > per_step:
-        n = max(1000, int(wl.n * per_step / t_full))
-    pos, vel, acc = wl.pos[:n].copy(), wl.vel[:n].copy(), acc[:n].copy()
+    if t_probe * wl.n / n0 > per_step:
+        n = max(1000, min(wl.n, int(n0 * per_step / t_probe)))
+    pos, vel = wl.pos[:n].copy(), wl.vel[:n].copy()
     pos[:, 3] *= wl.n / n
+    A0 = oracle.coeffs(pos, wl.nmax, wl.lmax, wl.b, alpha=wl.alpha)
+    acc = oracle.forces(pos, A0, wl.nmax, wl.lmax, wl.b, com=com, host=host, alpha=wl.alpha)
     c = com.copy()
     for _ in range(args.warmup):
         pos, vel, acc, c, _ = oracle.step(pos, vel, acc, wl.nmax, wl.lmax, wl.b, wl.dt, 1, com=c, host=host,
@@ -373,45 +439,25 @@ def refresh_timing(sim, p, v, torch, reps=3):
     return out
 
 
-def main():
-    ap = argparse.ArgumentParser()
-    ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=200)
-    ap.add_argument("--warmup", type=int, default=5)
-    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", choices=sorted(WORKLOADS), default=DEFAULT_WORKLOAD)
-    ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--no-autotune", action="store_true", help="keep the default kernel shapes")
-    ap.add_argument("--tiles", default=None,
-                    help="K1,K3: fixed kernel shapes instead of the autotuner (K1 = 0 for the register-tiled "
-                         "coefficient kernel, else 64/128/256 particles per tile; K3 = 64/128/256 threads)")
-    ap.add_argument("--n", type=int, default=None,
-                    help="particle count of a smaller case of the same workload (for profiling captures)")
-    ap.add_argument("--no-escape", action="store_true",
-                    help="skip the timing of the boundedness kernels (scf_bound) reported under 'escape'")
-    args = ap.parse_args()
-    if args.warmup < 3:
-        ap.error("--warmup must be >= 3")
+def fma_peaks(torch, stream):
+    """Measured FMA-chain rates (TFLOP/s) of the FP32 and FP64 pipes with the
+    SM clocks sampled while they ran (scf_fma_peak)."""
+    from paper_2602_13385_gb300 import _lib
+    sampler = ClockSampler(torch.cuda.current_device())
+    sampler.start()
+    f32, ms32 = _lib.scf_fma_peak(_lib.SCF_MIXED, 20000, stream.cuda_stream)
+    f64, ms64 = _lib.scf_fma_peak(_lib.SCF_FP64, 400, stream.cuda_stream)
+    clocks = sampler.stop()
+    return {"fp32_tflops": f32 / 1e12, "fp64_tflops": f64 / 1e12, "ms": [ms32, ms64], "clocks": clocks,
+            "what": "independent FMA chains (8 per thread, 2048 threads per SM, best of 3 launches) on the FP32 and "
+                    "FP64 pipes (scf_fma_peak)"}
 
-    rank = int(os.environ.get("RANK", "0"))
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
-    if args.impl == "reference":
-        return run_reference(args, rank, world)
 
-    import torch
-    torch.cuda.set_device(local)
-    dist = None
-    if world > 1:
-        import torch.distributed as dist
-        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
-
-    def barrier():
-        if dist is not None:
-            dist.barrier()
-
+def run_line(name, args, steps, torch, barrier, world, rank, local, peaks, oracle_cache, timing_extras):
+    """One bench line: the workload's timed leapfrog steps, end to end rate,
+    roofline, and (rank 0, one GPU) the CPU baseline and oracle error."""
     from paper_2602_13385_gb300 import SCF, Config
-    wl, precision = build_workload(args.workload, args.n)
+    wl, precision = build_workload(name, args.n)
     dtype = torch.float64 if precision == "fp64" else torch.float32
     cfg = Config(nmax=wl.nmax, lmax=wl.lmax, b=wl.b, dt=wl.dt, precision=precision, host=list(wl.host),
                  alpha=wl.alpha)
@@ -423,7 +469,7 @@ def main():
     v = torch.tensor(wl.vel, device=dev, dtype=dtype)
     c = torch.tensor(coms, device=dev, dtype=torch.float64)
     use_com = c if wl.host else None
-    if args.workload in FF_WORKLOADS:
+    if name in FF_WORKLOADS:
         sim.set_tiles(k3_block=128, k3_variant=1, k1_variant=2)
     a = sim.forces(p, sim.coeffs(p), com=use_com)
     tuning = None
@@ -443,12 +489,12 @@ def main():
         torch.cuda.synchronize()
         sim.profile(True)
         sim.profile_read()
-        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
         sampler = ClockSampler(local)
         sampler.start()
         barrier()
         torch.cuda.synchronize()
-        for i in range(args.steps):
+        for i in range(steps):
             flush.fill_(float(i))
             ev[i][0].record(stream)
             sim.step(p, v, a, com=use_com, nsteps=1)
@@ -461,82 +507,157 @@ def main():
         sim.profile(False)
     rc, st = sim.status()
     if rc != 0:
-        raise RuntimeError(f"device status {st} after the timed steps")
+        raise RuntimeError(f"device status {st} after the timed steps of {name}")
 
     ms_max = max_over_ranks(ms_total, dev)
-    value = whole_job_rate(wl.n, args.steps, world, ms_max)
+    value = whole_job_rate(wl.n, steps, world, ms_max)
+    ms_step = ms_max / steps
 
-    # end to end through the public API with host buffers (pinned)
-    h_in = [t.cpu().pin_memory() for t in (p, v, a, c)]
-    h_out = [torch.empty_like(t) for t in h_in]
-    e2e_steps = max(3, args.steps // 2)
-    torch.cuda.synchronize()
-    t0 = torch.cuda.Event(enable_timing=True)
-    t1 = torch.cuda.Event(enable_timing=True)
+    # end to end through the public API with the state in pinned host memory:
+    # every step reads the state from host memory and writes it back there
+    # (scf_step_host; on mapped page-locked memory the kernels move it over
+    # the host link themselves, overlapped with their arithmetic)
+    h_p, h_v, h_a = (t.cpu().pin_memory() for t in (p, v, a))
+    h_c = c.cpu().pin_memory() if use_com is not None else None
+    e2e_steps = max(3, steps // 2)
+    chunks = 1
     with torch.cuda.stream(stream):
+        sim.step_host(p, v, a, h_p, h_v, h_a, com=use_com, host_com=h_c, chunks=chunks)   # untimed
+        torch.cuda.synchronize()
+        t0 = torch.cuda.Event(enable_timing=True)
+        t1 = torch.cuda.Event(enable_timing=True)
         t0.record(stream)
         for _ in range(e2e_steps):
-            for d, hsrc in zip((p, v, a, c), h_in):
-                d.copy_(hsrc, non_blocking=True)
-            sim.step(p, v, a, com=use_com, nsteps=1)
-            for hdst, d in zip(h_out, (p, v, a, c)):
-                hdst.copy_(d, non_blocking=True)
+            sim.step_host(p, v, a, h_p, h_v, h_a, com=use_com, host_com=h_c, chunks=chunks)
         t1.record(stream)
-    torch.cuda.synchronize()
+        torch.cuda.synchronize()
     e2e_ms = t0.elapsed_time(t1)
-    bytes_io = sum(t.numel() * t.element_size() for t in h_in)
-    e2e = {"value": wl.n * e2e_steps / (e2e_ms * 1e-3), "unit": UNIT, "h2d_bytes_per_step": bytes_io,
-           "d2h_bytes_per_step": bytes_io, "steps": e2e_steps,
-           "what": "scf_step through the C ABI with the state copied from pinned host buffers and back every step"}
+    bytes_io = sum(t.numel() * t.element_size() for t in (h_p, h_v, h_a))
+    bytes_io += 0 if h_c is None else h_c.numel() * h_c.element_size()
+    e2e = {"value": whole_job_rate(wl.n, e2e_steps, world, max_over_ranks(e2e_ms, dev)), "unit": UNIT,
+           "h2d_bytes_per_step": bytes_io, "d2h_bytes_per_step": bytes_io, "steps": e2e_steps,
+           "ms_per_step": e2e_ms / e2e_steps,
+           "what": "scf_step_host through the C ABI: the state lives in pinned (mapped) host buffers; every step "
+                   "the kernels read it from host memory and write the new state back over the host link"}
 
-    # roofline of the dominant kernel (ALU-bound: FP64 pipe in fp64 mode, FP32 in mixed)
+    # roofline: ALU-bound (FP64 pipe in fp64 mode, FP32 pipe in mixed mode)
     k1f, k3f = per_particle_flops(wl.nmax, wl.lmax)
     elem = 8 if precision == "fp64" else 4
     k1b, k3b = per_particle_bytes(elem)
-    dom = 2 if kms[2] >= kms[0] else 0
-    avg_ms = kms[dom] / max(1, kcount[dom])
+    per_k = [kms[i] / max(1, kcount[i]) for i in range(3)]
+    dom = 2 if per_k[2] >= per_k[0] else 0
+    avg_ms = per_k[dom]
     flops = wl.n * (k3f if dom == 2 else k1f)
     achieved = flops / (avg_ms * 1e-3) / 1e12
     clock = clocks.get("sm_max_mhz") or 2070.0
-    fma = FP64_FMA_PER_SM_CLK if precision == "fp64" else FP32_FMA_PER_SM_CLK
+    is64 = precision == "fp64" and name not in FF_WORKLOADS
+    fma = FP64_FMA_PER_SM_CLK if is64 else FP32_FMA_PER_SM_CLK
     peak = N_SM * fma * 2 * clock * 1e6 / 1e12
+    meas = peaks.get("fp64_tflops" if is64 else "fp32_tflops") if peaks else None
     kname = "k3_forces" if dom == 2 else "k1_partials"
+    step_flops = wl.n * (k1f + k3f)
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-                "traffic": traffic_for(kname, args.workload),
+                "traffic": traffic_for(kname, name),
                 "kernel": kname, "kernel_avg_ms": avg_ms,
-                "peak_basis": f"{'FP64' if precision == 'fp64' else 'FP32'} pipe: {N_SM} SMs x {fma} FMA/clk x 2 "
+                "peak_basis": f"nominal: {'FP64' if is64 else 'FP32'} pipe, {N_SM} SMs x {fma} FMA/clk x 2 "
                               f"x {clock:.0f} MHz (max SM clock)",
+                "peak_measured": meas, "frac_of_measured": (achieved / meas) if meas else None,
                 "frac_at_sampled_clock": (achieved / (N_SM * fma * 2 * clocks["sm_mhz"] * 1e-6)
                                           if clocks.get("sm_mhz") else None),
                 "algorithmic_flops_per_launch": flops,
                 "algorithmic_bytes_per_launch": wl.n * (k3b if dom == 2 else k1b),
-                "kernels_ms_per_step": {"k1_partials": kms[0] / max(1, kcount[0]),
-                                        "k2_reduce": kms[1] / max(1, kcount[1]),
-                                        "k3_forces": kms[2] / max(1, kcount[2])}}
+                "kernels_ms_per_step": {"k1_partials": per_k[0], "k2_reduce": per_k[1], "k3_forces": per_k[2]},
+                "whole_step": {"achieved": step_flops / (ms_step * 1e-3) / 1e12, "peak": peak,
+                               "frac": step_flops / (ms_step * 1e-3) / 1e12 / peak,
+                               "algorithmic_flops_per_step": step_flops,
+                               "what": "(kernel 1 + kernel 3 algorithmic flops) x N / ms_per_step"}}
 
     line = {
-        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True, "scaling": "weak",
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": steps,
+        "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None,
-        "dtype": ("f64 (kernels 1 and 3 in float-float)" if args.workload in FF_WORKLOADS else "f64")
+        "dtype": ("f64 (kernels 1 and 3 in float-float)" if name in FF_WORKLOADS else "f64")
                  if precision == "fp64" else "f32+f64",
         "data": "synthetic (seeded sample, see config.workload)",
-        "config": workload_config(wl, precision, args.workload),
+        "config": workload_config(wl, precision, name),
         "roofline": roofline, "e2e": e2e, "gpu_launches": int(sum(kcount)), "clocks": clocks,
         "kernel_shapes": dict(sim.tiles(), autotuned=tuning is not None,
                               candidates_ms=None if tuning is None else tuning["ms"]),
         "src_hash": src_hash(),
     }
-    if not args.no_escape:
+    if timing_extras and not args.no_escape:
         line["escape"] = escape_timing(sim, p, v, offsets, precision, clocks, torch)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        base, ref = cpu_baseline(wl, precision) if wl.offsets is None else (None, None)
-        if base is not None:
-            line["cpu_baseline"] = base
-            line["error_vs_oracle"] = oracle_error(sim, wl, ref, dtype, torch)
-    if not args.no_escape:
+        key = (WORKLOADS[name][0], args.n)
+        if key not in oracle_cache:
+            oracle_cache[key] = oracle_reference(wl)
+        base, refs = oracle_cache[key]
+        line["cpu_baseline"] = dict(base)
+        line["error_vs_oracle"] = oracle_error(sim, wl, refs, dtype, torch, use_com)
+    if timing_extras and not args.no_escape:
         line["refresh"] = refresh_timing(sim, p, v, torch)
     sim.close()
+    return line
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", choices=sorted(WORKLOADS), default=None,
+                    help="run only this line (default: the headline plus the mixed and batch lines)")
+    ap.add_argument("--extra-steps", type=int, default=100,
+                    help="timed steps of the mixed and batch lines of the default run (at least --steps)")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-autotune", action="store_true", help="keep the default kernel shapes")
+    ap.add_argument("--tiles", default=None,
+                    help="K1,K3: fixed kernel shapes instead of the autotuner (K1 = 0 for the register-tiled "
+                         "coefficient kernel, else 64/128/256 particles per tile; K3 = 64/128/256 threads)")
+    ap.add_argument("--n", type=int, default=None,
+                    help="particle count of a smaller case of the same workload (for profiling captures)")
+    ap.add_argument("--no-escape", action="store_true",
+                    help="skip the timing of the boundedness kernels (scf_bound) reported under 'escape'")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    if args.impl == "reference" and args.workload is None:
+        args.workload = DEFAULT_WORKLOAD
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        return run_reference(args, rank, world)
+
+    import torch
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+
+    lines = DEFAULT_LINES if args.workload is None else [("headline", args.workload)]
+    peaks = fma_peaks(torch, torch.cuda.current_stream())
+    oracle_cache = {}
+    out = {}
+    for key, name in lines:
+        steps = args.steps if key == "headline" else max(args.steps, args.extra_steps)
+        # escape-physics and refresh timings ride on the mixed line (or on a single chosen line)
+        extras = key == "mixed" or args.workload is not None
+        out[key] = run_line(name, args, steps, torch, barrier, world, rank, local, peaks, oracle_cache, extras)
+    line = dict(out.pop("headline"))
+    line["warmup"] = args.warmup
+    line["peak_measured"] = peaks
+    for key, sub in out.items():
+        sub = dict(sub)
+        sub["warmup"] = args.warmup
+        line[key] = sub
     if rank == 0:
         print(json.dumps(line), flush=True)
     if dist is not None:

@@ -92,6 +92,11 @@ extern "C" {
 #define SCF_HOST_HERNQUIST 1 /* M = total mass, a = scale radius:  psi = -G M / (r + a)            */
 #define SCF_HOST_NFW 2       /* M = scale mass M_NFW, a = r_s:     psi = -G M ln(1 + r/r_s) / r     */
 #define SCF_HOST_MN 3        /* M, a = scale length, b = height:   psi = -G M / sqrt(R^2 + (sqrt(z^2+b^2)+a)^2) */
+#define SCF_HOST_POWCUT 4    /* M = total mass M_b, a = cut-off radius r_c, b = power-law index alpha (0 <= alpha < 2):
+                              * rho ~ (r_c/r)^alpha exp(-(r/r_c)^2) (the MWPotential2014 bulge, App. A),
+                              * psi = G M_b/Gamma(s) (gamma(1 - alpha/2, x)/r_c - gamma(s, x)/r),
+                              * s = (3 - alpha)/2, x = (r/r_c)^2, gamma the lower incomplete gamma function.
+                              * The adjoint (scf_adjoint_level) does not take this component. */
 
 typedef struct scf_host_component {
   int kind;
@@ -174,6 +179,35 @@ int scf_forces(scf_handle* h, const void* pos, const double* A, const double* co
  * Errors: SCF_ERR_NULL_POINTER, SCF_ERR_MISALIGNED, SCF_ERR_INVALID_ARG
  * (nsteps < 0), SCF_ERR_CUDA. */
 int scf_step(scf_handle* h, void* pos, void* vel, void* acc, double* com, int nsteps);
+
+/* One leapfrog step (as scf_step with nsteps = 1, same kernels and results)
+ * for a caller whose state lives in host memory: on return (after the
+ * handle's stream) the host arrays hold the stepped state.
+ * When every host array is mapped page-locked memory (cudaHostAlloc, or
+ * torch pin_memory, under unified addressing) the step's kernels read and
+ * write the host arrays in place over the host link: the transfers happen
+ * inside the kernels, overlapped with their arithmetic, and the device arrays
+ * are not used (they may be NULL).  Otherwise the state is staged through the
+ * device arrays: copied in on a second stream of the handle, kernels 1 and 2,
+ * then the positions and the centres copied back while kernel 3 runs, which
+ * is launched in `chunks` pieces of its block map so that each piece's
+ * velocities and accelerations go back while the next piece runs.  The copy
+ * stream and its events are created by the first staged call and freed by
+ * scf_free; the handle's stream waits for the copies, so a synchronisation of
+ * the handle's stream covers the whole call.
+ *   pos, vel, acc, com           device arrays as for scf_step (staged form only).
+ *   host_pos, host_vel, host_acc host arrays of the same layout: read, then
+ *                                overwritten with the new state (acc: the
+ *                                acceleration at the new positions).
+ *   host_com                     host [n_prog][6] doubles, read and updated
+ *                                (NULL without host components).
+ *   chunks                       1..SCF_STAGE_MAX_CHUNKS (staged form).
+ * Host arrays must stay valid until the handle's stream has finished.
+ * Errors: SCF_ERR_NULL_POINTER, SCF_ERR_MISALIGNED, SCF_ERR_INVALID_ARG
+ * (chunks out of range), SCF_ERR_CUDA. */
+#define SCF_STAGE_MAX_CHUNKS 32
+int scf_step_host(scf_handle* h, void* pos, void* vel, void* acc, double* com, void* host_pos, void* host_vel,
+                  void* host_acc, double* host_com, int chunks);
 
 /* Handle options.
  *   SCF_OPT_GRAPHS    1 (default) = scf_step replays a captured CUDA graph per
@@ -350,7 +384,10 @@ typedef struct scf_escape_params {
                         1e-12 b) with the current coefficient set, then scf_bound again
                         in the new frame; 0: the frame stays on the centre orbit */
   int retune_rule;   /* b at a complete refresh: 0 = the half-mass rule above,
-                        1 = scf_retune_a000 (the maximum of a_000) over the coefficient set */
+                        1 = scf_retune_a000 (the maximum of a_000) over the coefficient set,
+                        2 = scf_retune_alpha: alpha (shared) and b at the joint maximum of
+                        a_000 over the coefficient set, alpha in [alpha_lo, alpha_hi] */
+  double alpha_lo, alpha_hi; /* the exponent range of retune_rule 2 */
 } scf_escape_params;
 
 /* Basis scale of each progenitor at the maximum of a_000 in the bi-orthonormal
@@ -361,11 +398,39 @@ typedef struct scf_escape_params {
  * g(s) = (1 + s^(1/alpha))^-alpha.  Search in ln b: 3 grids of 33 values, the
  * first over [b/8, 8b], each next over one step either side of the previous
  * best (the first best in grid order), the last best moved to the vertex of
- * the parabola through it and its neighbours.  An empty set keeps b.  Updates
- * the handle's scales (scf_get_scales) on its stream; double-precision sums in
- * a fixed order.
+ * the parabola through it and its neighbours; then 4 safeguarded Newton steps
+ * on d ln a_000 / d ln b = 0 inside the last grid's bracket, so b is the
+ * maximiser to rounding.  An empty set keeps b.  Updates the handle's scales
+ * (scf_get_scales) on its stream; double-precision sums in a fixed order.
  * Errors: SCF_ERR_NULL_POINTER, SCF_ERR_MISALIGNED, SCF_ERR_CUDA. */
 int scf_retune_a000(scf_handle* h, const void* pos, const uint8_t* mask);
+
+/* Exponent alpha of the radial family (Eq. 4) and every progenitor's b at the
+ * joint maximum of a_000 (a complete refresh retunes both, Sec. 2.2): one
+ * alpha for the handle, maximising the product of the progenitors' a_000,
+ * each at its own maximising b_p(alpha) (the search of scf_retune_a000).  The
+ * bi-orthonormal a_000 carries |I_00(alpha)|^(-1/2), I_00 = -(alpha + 1)
+ * Gamma(2 alpha + 1) / (2^(4 alpha + 3) (alpha + 1/2) Gamma(alpha + 1/2)^2).
+ * 17 values of ln alpha over [alpha_lo, alpha_hi] bracket the maximum; inside
+ * the bracket the root of d/d alpha sum_p ln a_000,p (envelope theorem: the
+ * partial derivative at b_p(alpha)) is found by the Illinois method.  The
+ * handle then moves to that alpha: recurrence tables, normalisation and
+ * field scales rebuilt, the general kernels selected for alpha != 1 (default
+ * shapes, no float-float variants; the captured step is dropped), b_p set.
+ * Synchronises the stream once per trial alpha (about 25).  Progenitors with an
+ * empty set keep their b and take no part; with no set at all nothing
+ * changes.  alpha_out (host, may be NULL) receives the exponent.
+ * Errors: SCF_ERR_NULL_POINTER, SCF_ERR_MISALIGNED, SCF_ERR_INVALID_ARG
+ * (range empty or not positive), SCF_ERR_UNSUPPORTED (range outside
+ * SCF_ALPHA_MIN..SCF_ALPHA_MAX, or tables of the found alpha not finite at
+ * the handle's (nmax, lmax): the handle keeps its exponent), SCF_ERR_CUDA. */
+int scf_retune_alpha(scf_handle* h, const void* pos, const uint8_t* mask, double alpha_lo, double alpha_hi,
+                     double* alpha_out);
+
+/* The handle's current exponent alpha of the radial family (changed by
+ * scf_retune_alpha and by scf_evolve with retune_rule 2) into *alpha (host).
+ * Errors: SCF_ERR_NULL_POINTER. */
+int scf_get_alpha(const scf_handle* h, double* alpha);
 
 /* Re-centring of the cluster frame (Sec. 2.1).  For every progenitor:
  * 1. the SCF centre x_c, where a_000 of the expansion about x_c (alpha, b fixed)
@@ -470,6 +535,32 @@ int scf_profile_read(scf_handle* h, double* ms, int64_t* launches);
 #define SCF_NOALLOC_MAX_COEFS 4096
 int scf_coeffs_noalloc(const scf_config* cfg, int64_t n, const void* pos, const uint8_t* mask, double* A_out,
                        void* stream);
+
+/* Status of the last scf_coeffs_noalloc call on the current device: a
+ * particle whose position or mass is NaN or infinite is left out of the sums
+ * (the kernel never traps) and sets SCF_STATUS_NONFINITE_POS in the status
+ * word of the static scratch; each call clears the word first.  This call
+ * copies the word into *status (host, may be NULL) on `stream` and
+ * synchronises that stream, allocating nothing; it reads whatever the last
+ * call left, so calls of scf_coeffs_noalloc queued on other streams race
+ * with it.  Before the first scf_coeffs_noalloc call on the device it
+ * reports 0.  No counterpart in the paper.
+ * Returns SCF_ERR_DEVICE_STATUS if a bit is set, SCF_ERR_CUDA on a CUDA
+ * error, else SCF_OK. */
+int scf_noalloc_status(void* stream, int* status);
+
+/* Measured rate of independent FMA chains (8 per thread, 2048 threads per
+ * SM) on the double-precision (SCF_FP64) or single-precision (SCF_MIXED)
+ * pipe: the measured counterpart of the nominal non-tensor peak that the
+ * roofline fractions of the coefficient and field kernels refer to.  No
+ * counterpart in the paper (a measurement utility).  Synchronises the stream.
+ *   iters      loop trips (16 x 8 FMAs per thread each); a few ms of work is
+ *              about 1e4 (single) or 2e2 (double) on a GB300.
+ *   stream     a cudaStream_t on the current device.
+ *   flops_out  host, FLOP/s (FMA = 2) of the best of three launches.
+ *   ms_out     host, duration of that launch (may be NULL).
+ * Errors: SCF_ERR_NULL_POINTER, SCF_ERR_INVALID_ARG, SCF_ERR_CUDA. */
+int scf_fma_peak(int precision, int iters, void* stream, double* flops_out, double* ms_out);
 
 /* Releases the workspace (synchronising the stream first) and the handle.
  * NULL is accepted. */

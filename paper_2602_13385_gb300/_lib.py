@@ -18,11 +18,13 @@ SCF_MIXED = 1
 SCF_HOST_HERNQUIST = 1
 SCF_HOST_NFW = 2
 SCF_HOST_MN = 3
+SCF_HOST_POWCUT = 4
 SCF_MAX_LMAX = 12
 SCF_MAX_NMAX = 40
 SCF_MAX_HOST_COMPONENTS = 8
 SCF_STATUS_NONFINITE_POS = 1
 SCF_STATUS_NONFINITE_ACC = 2
+SCF_STAGE_MAX_CHUNKS = 32
 
 ERRORS = {
     -1: "SCF_ERR_INVALID_ARG",
@@ -37,10 +39,10 @@ ERRORS = {
 }
 
 # every symbol include/scf.h declares
-EXPORTS = ["scf_init", "scf_coeffs", "scf_forces", "scf_step", "scf_last_coeffs", "scf_status",
-           "scf_launches_per_call", "scf_profile", "scf_profile_read", "scf_coeffs_noalloc", "scf_set_option",
+EXPORTS = ["scf_init", "scf_coeffs", "scf_forces", "scf_step", "scf_step_host", "scf_last_coeffs", "scf_status",
+           "scf_launches_per_call", "scf_profile", "scf_profile_read", "scf_coeffs_noalloc", "scf_noalloc_status", "scf_set_option",
            "scf_get_option", "scf_autotune", "scf_adjoint_level", "scf_energy", "scf_bound", "scf_tidal",
-           "scf_set_mask", "scf_evolve", "scf_get_scales", "scf_recentre", "scf_retune_a000", "scf_free", "scf_strerror"]
+           "scf_set_mask", "scf_evolve", "scf_get_scales", "scf_recentre", "scf_retune_a000", "scf_retune_alpha", "scf_get_alpha", "scf_fma_peak", "scf_free", "scf_strerror"]
 SCF_OPT_GRAPHS = 1
 SCF_OPT_K1_TILE = 2
 SCF_OPT_K3_BLOCK = 3
@@ -61,7 +63,7 @@ class scf_host_component(ctypes.Structure):
 class scf_escape_params(ctypes.Structure):
     _fields_ = [("kin", ctypes.c_double), ("frac", ctypes.c_double), ("eta", ctypes.c_double),
                 ("max_steps", ctypes.c_int), ("retune_every", ctypes.c_int), ("recentre", ctypes.c_int),
-                ("retune_rule", ctypes.c_int)]
+                ("retune_rule", ctypes.c_int), ("alpha_lo", ctypes.c_double), ("alpha_hi", ctypes.c_double)]
 
 
 class scf_config(ctypes.Structure):
@@ -92,12 +94,14 @@ def load(build: bool = True) -> ctypes.CDLL:
     lib.scf_coeffs.argtypes = [vp, vp, vp, vp]
     lib.scf_forces.argtypes = [vp, vp, vp, vp, vp]
     lib.scf_step.argtypes = [vp, vp, vp, vp, vp, i]
+    lib.scf_step_host.argtypes = [vp, vp, vp, vp, vp, vp, vp, vp, vp, i]
     lib.scf_last_coeffs.argtypes = [vp, vp]
     lib.scf_status.argtypes = [vp, ctypes.POINTER(i)]
     lib.scf_launches_per_call.argtypes = [vp, i]
     lib.scf_profile.argtypes = [vp, i]
     lib.scf_profile_read.argtypes = [vp, dp, ctypes.POINTER(ctypes.c_int64)]
     lib.scf_coeffs_noalloc.argtypes = [ctypes.POINTER(scf_config), ctypes.c_int64, vp, vp, vp, vp]
+    lib.scf_noalloc_status.argtypes = [vp, ctypes.POINTER(i)]
     lib.scf_set_option.argtypes = [vp, i, i]
     lib.scf_get_option.argtypes = [vp, i, ctypes.POINTER(i)]
     lib.scf_autotune.argtypes = [vp, vp, vp, vp, i, dp]
@@ -110,8 +114,11 @@ def load(build: bool = True) -> ctypes.CDLL:
     lib.scf_get_scales.argtypes = [vp, vp]
     lib.scf_recentre.argtypes = [vp, vp, vp, vp, vp, vp, i, d, dp]
     lib.scf_retune_a000.argtypes = [vp, vp, vp]
+    lib.scf_retune_alpha.argtypes = [vp, vp, vp, d, d, dp]
+    lib.scf_get_alpha.argtypes = [vp, dp]
     lib.scf_evolve.argtypes = [vp, vp, vp, vp, vp, i, ctypes.POINTER(scf_escape_params), vp, vp, vp,
                                ctypes.POINTER(i)]
+    lib.scf_fma_peak.argtypes = [i, i, vp, dp, dp]
     lib.scf_free.argtypes = [vp]
     lib.scf_strerror.argtypes = [i]
     lib.scf_strerror.restype = ctypes.c_char_p
@@ -133,6 +140,22 @@ def _ptr(x, dtype=None):
         raise TypeError(f"expected a torch tensor, got {type(x)}")
     if not x.is_cuda:
         raise ValueError("the SCF library takes CUDA tensors only (no CPU path)")
+    if not x.is_contiguous():
+        raise ValueError("tensor must be contiguous")
+    if dtype is not None and x.dtype != dtype:
+        raise TypeError(f"expected {dtype}, got {x.dtype}")
+    return ctypes.c_void_p(x.data_ptr())
+
+
+def _host_ptr(x, dtype=None):
+    """Address of a contiguous CPU tensor (page-locked for overlapped copies)."""
+    if x is None:
+        return None
+    import torch
+    if not isinstance(x, torch.Tensor):
+        raise TypeError(f"expected a torch tensor, got {type(x)}")
+    if x.is_cuda:
+        raise ValueError("expected a host (CPU) tensor")
     if not x.is_contiguous():
         raise ValueError("tensor must be contiguous")
     if dtype is not None and x.dtype != dtype:
@@ -175,6 +198,20 @@ def scf_step(h, pos, vel, acc, com, nsteps: int):
     _check(load().scf_step(h, _ptr(pos), _ptr(vel), _ptr(acc), _ptr(com, torch.float64), int(nsteps)), "scf_step")
 
 
+def scf_step_host(h, pos, vel, acc, com, host_pos, host_vel, host_acc, host_com, chunks: int = 8):
+    """One step of a state held in host tensors (read and overwritten), staged
+    through the device tensors with copies overlapped with the kernels."""
+    import torch
+    for d, hst, nm in ((pos, host_pos, "pos"), (vel, host_vel, "vel"), (acc, host_acc, "acc"), (com, host_com, "com")):
+        if (d is None) != (hst is None):
+            raise ValueError(f"{nm}: give both the device and the host tensor, or neither")
+        if d is not None and (hst.dtype != d.dtype or hst.numel() < d.numel()):
+            raise ValueError(f"host {nm} must match the device tensor's dtype and size")
+    _check(load().scf_step_host(h, _ptr(pos), _ptr(vel), _ptr(acc), _ptr(com, torch.float64), _host_ptr(host_pos),
+                                _host_ptr(host_vel), _host_ptr(host_acc), _host_ptr(host_com, torch.float64),
+                                int(chunks)), "scf_step_host")
+
+
 def scf_last_coeffs(h, A_out):
     import torch
     _check(load().scf_last_coeffs(h, _ptr(A_out, torch.float64)), "scf_last_coeffs")
@@ -207,10 +244,51 @@ def scf_profile_read(h):
 
 def scf_coeffs_noalloc(cfg: scf_config, n: int, pos, mask, A_out, stream: int = 0):
     """Coefficients of one cluster through the entry point that allocates
-    nothing (its scratch is a static device array inside the library)."""
+    nothing (its scratch is a static device array inside the library).  The
+    C side cannot see the tensors' extents, so they are checked here: pos
+    (n, 4) of the precision's dtype, mask n bytes, A_out 2 NC doubles, all on
+    the current device."""
     import torch
-    _check(load().scf_coeffs_noalloc(ctypes.byref(cfg), int(n), _ptr(pos), _ptr(mask, torch.uint8),
+    n = int(n)
+    nc = (cfg.nmax + 1) * (cfg.lmax + 1) * (cfg.lmax + 2) // 2
+    want = {SCF_FP64: torch.float64, SCF_MIXED: torch.float32}.get(cfg.precision)
+    for t, nm in ((pos, "pos"), (mask, "mask"), (A_out, "A_out")):
+        if t is not None and not isinstance(t, torch.Tensor):
+            raise TypeError(f"{nm} must be a torch tensor")
+    if n < 0:
+        raise ValueError("n must be >= 0")
+    if pos is None or A_out is None:
+        raise ValueError("pos and A_out are required")
+    if tuple(pos.shape) != (n, 4):
+        raise ValueError(f"pos must have shape ({n}, 4), got {tuple(pos.shape)}")
+    if want is not None and pos.dtype != want:
+        raise TypeError(f"pos must be {want} for this precision, got {pos.dtype}")
+    if mask is not None:
+        if mask.dtype != torch.uint8:
+            raise TypeError(f"mask must be uint8, got {mask.dtype}")
+        if mask.numel() < n:
+            raise ValueError(f"mask has {mask.numel()} entries for {n} particles")
+    if A_out.dtype != torch.float64:
+        raise TypeError(f"A_out must be float64, got {A_out.dtype}")
+    if A_out.numel() < 2 * nc:
+        raise ValueError(f"A_out holds {A_out.numel()} doubles, needs 2*NC = {2 * nc}")
+    if A_out.is_cuda:
+        cur = torch.cuda.current_device()
+        for t, nm in ((pos, "pos"), (mask, "mask"), (A_out, "A_out")):
+            if t is not None and t.is_cuda and t.device.index != cur:
+                raise ValueError(f"{nm} is on cuda:{t.device.index}, the current device is cuda:{cur}")
+    _check(load().scf_coeffs_noalloc(ctypes.byref(cfg), n, _ptr(pos), _ptr(mask, torch.uint8),
                                      _ptr(A_out, torch.float64), ctypes.c_void_p(stream)), "scf_coeffs_noalloc")
+
+
+def scf_noalloc_status(stream: int = 0):
+    """(return code, status bits) of the last scf_coeffs_noalloc call on the
+    current device; synchronises the stream; does not raise on device status."""
+    st = ctypes.c_int(0)
+    rc = load().scf_noalloc_status(ctypes.c_void_p(stream), ctypes.byref(st))
+    if rc not in (0, -7):
+        raise ScfError(rc, "scf_noalloc_status")
+    return rc, st.value
 
 
 def scf_set_option(h, option: int, value: int):
@@ -268,11 +346,12 @@ def scf_set_mask(h, mask):
 
 
 def scf_evolve(h, pos, vel, acc, com, nsteps: int, kin: float, frac: float, eta: float, max_steps: int,
-               bound, mask, stats, retune_every: int = 0, recentre: bool = False, retune_rule: int = 0) -> int:
+               bound, mask, stats, retune_every: int = 0, recentre: bool = False, retune_rule: int = 0,
+               alpha_lo: float = 0.25, alpha_hi: float = 2.0) -> int:
     """Returns the number of integration timesteps."""
     import torch
     ep = scf_escape_params(float(kin), float(frac), float(eta), int(max_steps), int(retune_every),
-                           1 if recentre else 0, int(retune_rule))
+                           1 if recentre else 0, int(retune_rule), float(alpha_lo), float(alpha_hi))
     n = ctypes.c_int(0)
     _check(load().scf_evolve(h, _ptr(pos), _ptr(vel), _ptr(acc), _ptr(com, torch.float64), int(nsteps),
                              ctypes.byref(ep), _ptr(bound, torch.uint8), _ptr(mask, torch.uint8),
@@ -296,9 +375,35 @@ def scf_retune_a000(h, pos, mask):
     _check(load().scf_retune_a000(h, _ptr(pos), _ptr(mask, torch.uint8)), "scf_retune_a000")
 
 
+def scf_retune_alpha(h, pos, mask, alpha_lo: float = 0.25, alpha_hi: float = 2.0) -> float:
+    """Moves the handle to the exponent and scales at the joint maximum of
+    a_000; returns the exponent."""
+    import torch
+    out = ctypes.c_double(0.0)
+    _check(load().scf_retune_alpha(h, _ptr(pos), _ptr(mask, torch.uint8), float(alpha_lo), float(alpha_hi),
+                                   ctypes.byref(out)), "scf_retune_alpha")
+    return out.value
+
+
+def scf_get_alpha(h) -> float:
+    out = ctypes.c_double(0.0)
+    _check(load().scf_get_alpha(h, ctypes.byref(out)), "scf_get_alpha")
+    return out.value
+
+
 def scf_get_scales(h, b_out):
     import torch
     _check(load().scf_get_scales(h, _ptr(b_out, torch.float64)), "scf_get_scales")
+
+
+def scf_fma_peak(precision: int, iters: int, stream: int = 0):
+    """(FLOP/s, ms) of independent FMA chains on the FP64 (SCF_FP64) or FP32
+    (SCF_MIXED) pipe, best of three launches."""
+    f = ctypes.c_double(0.0)
+    ms = ctypes.c_double(0.0)
+    _check(load().scf_fma_peak(int(precision), int(iters), ctypes.c_void_p(stream), ctypes.byref(f),
+                               ctypes.byref(ms)), "scf_fma_peak")
+    return f.value, ms.value
 
 
 def scf_free(h):

@@ -19,7 +19,7 @@ OBJ = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libscf.so")
 SOURCES = ["scf_tables.cu", "scf_coeffs.cu", "scf_forces.cu", "scf_api.cu", "scf_noalloc.cu",
            "scf_adjoint.cu", "scf_energy.cu", "scf_escape.cu", "scf_recentre.cu",
-           "scf_forces_ff.cu", "scf_coeffs_ff.cu"]
+           "scf_forces_ff.cu", "scf_coeffs_ff.cu", "scf_peak.cu"]
 HEADERS = ["scf_device.cuh", "scf_internal.h", "scf_escape.h", "scf_ff.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr"]

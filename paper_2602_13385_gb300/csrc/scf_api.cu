@@ -28,7 +28,9 @@ struct scf_handle {
   ScfLaunchInfo k1{};
   bool k1_ff = false;  // double-precision handles: float-float kernel 1
   bool gen = false;    // radial family of exponent alpha != 1: the general kernels 1 and 3
-  ScfConst* d_tab = nullptr;  // their recurrence tables (device memory; gen handles only)
+  ScfConst* d_tab = nullptr;  // their recurrence tables (device memory; allocated for every handle, so that
+                              // scf_retune_alpha can move a handle to another exponent)
+  double* d_alpha = nullptr;  // [n_prog][4] exponent search: trial b, S0, S1, mass
   double* d_rc = nullptr;     // [n_prog][16] re-centring state (scf_recentre)
   double* d_sp = nullptr;     // [k3 blocks][kScalePoints + 1] partial sums of the b search
   int k1_blocks = 0;
@@ -83,6 +85,11 @@ struct scf_handle {
   std::vector<cudaEvent_t> prof_ev;   // pairs (start, stop)
   std::vector<int> prof_kind;         // kernel index of each recorded pair
   int prof_used = 0;                  // pairs recorded
+  // host copies of the block maps (scf_step_host splits the launches at block boundaries)
+  std::vector<int64_t> h_blk1_begin, h_blk1_end, h_blk3_begin, h_blk3_end;
+  // scf_step_host: copy stream and events, created by its first call
+  cudaStream_t copy_stream = nullptr;
+  std::vector<cudaEvent_t> stage_ev;
 };
 
 namespace {
@@ -149,9 +156,11 @@ int check_config(const scf_config* c) {
   if (!std::isfinite(c->G) || !std::isfinite(c->dt) || !std::isfinite(c->b)) return SCF_ERR_INVALID_ARG;
   for (int i = 0; i < c->n_host; ++i) {
     const scf_host_component& h = c->host[i];
-    if (h.kind != SCF_HOST_HERNQUIST && h.kind != SCF_HOST_NFW && h.kind != SCF_HOST_MN) return SCF_ERR_INVALID_ARG;
+    if (h.kind != SCF_HOST_HERNQUIST && h.kind != SCF_HOST_NFW && h.kind != SCF_HOST_MN && h.kind != SCF_HOST_POWCUT)
+      return SCF_ERR_INVALID_ARG;
     if (!(h.a > 0.0) || !std::isfinite(h.M) || !std::isfinite(h.a)) return SCF_ERR_INVALID_ARG;
     if (h.kind == SCF_HOST_MN && !(h.b >= 0.0 && std::isfinite(h.b))) return SCF_ERR_INVALID_ARG;
+    if (h.kind == SCF_HOST_POWCUT && !(h.b >= 0.0 && h.b < 2.0)) return SCF_ERR_INVALID_ARG;
   }
   return SCF_OK;
 }
@@ -199,7 +208,7 @@ K1Args k1_args(scf_handle* h, void* pos, void* vel, const void* acc, const uint8
   a.mode = mode;
   a.dt = h->cfg.dt;
   a.status = h->d_status;
-  a.tab = h->d_tab;
+  a.tab = h->gen ? h->d_tab : nullptr;
   a.alpha = h->cfg.alpha;
   a.inv_alpha = 1.0 / h->cfg.alpha;
   return a;
@@ -259,7 +268,7 @@ K3Args k3_args(scf_handle* h, const void* pos, void* vel, void* acc, const doubl
   a.dt = h->cfg.dt;
   a.host = h->host;
   a.status = h->d_status;
-  a.tab = h->d_tab;
+  a.tab = h->gen ? h->d_tab : nullptr;
   a.alpha = h->cfg.alpha;
   a.inv_alpha = 1.0 / h->cfg.alpha;
   return a;
@@ -408,6 +417,8 @@ int use_k1(scf_handle* h, int tp) {
   if (!ok) return SCF_ERR_CUDA;
   h->k1 = info;
   h->k1_blocks = (int)m.prog.size();
+  h->h_blk1_begin = m.begin;
+  h->h_blk1_end = m.end;
   drop_graph(h);
   return SCF_OK;
 }
@@ -438,6 +449,8 @@ int use_k3(scf_handle* h, int tb) {
   h->k3 = info;
   h->k3_native = native;
   h->k3_blocks = (int)m.prog.size();
+  h->h_blk3_begin = m.begin;
+  h->h_blk3_end = m.end;
   drop_graph(h);
   return SCF_OK;
 }
@@ -491,14 +504,19 @@ int scf_init(const scf_config* cfg, int n_prog, const int64_t* offsets, const do
   h->offsets.assign(offsets, offsets + n_prog + 1);
 
   // Capacity of the block maps and partial rows: the largest any candidate shape can need.
-  for (int cand = 0; cand < 5; ++cand) {
-    const int tp = cand < 3 ? 64 << cand : cand == 3 ? 0 : 128;  // the last: float-float, 128
-    const bool ff = cand == 4;
+  // Both radial families count (alpha = 1 and the general kernels), since
+  // scf_retune_alpha can move the handle from one to the other.
+  for (int cand = 0; cand < 10; ++cand) {
+    const int c5 = cand % 5;
+    const int tp = c5 < 3 ? 64 << c5 : c5 == 3 ? 0 : 128;  // the last: float-float, 128
+    const bool ff = c5 == 4;
     if (tp == 0 && cfg->precision != SCF_MIXED) continue;
     if (ff && cfg->precision != SCF_FP64) continue;
+    scf_config cc = *cfg;
+    cc.alpha = cand < 5 ? 1.0 : 0.5;
     ScfLaunchInfo info{};
     int bps = 0;
-    if (k1_shape(*cfg, tp, ff, &info, &bps) != SCF_OK) continue;
+    if (k1_shape(cc, tp, ff, &info, &bps) != SCF_OK) continue;
     const Map1 m = make_map1(h->offsets, n_prog, info.tile, (int64_t)h->n_sm * bps);
     const size_t blocks = m.prog.size();
     if (info.variant == 1) info.win = scf_k1_windows(longest_block(m), info);
@@ -551,7 +569,8 @@ int scf_init(const scf_config* cfg, int n_prog, const int64_t* offsets, const do
   const size_t o_half = take(sizeof(double) * 4 * (size_t)n_prog);
   const size_t o_k2z = take(sizeof(double) * kK2MaxChunks * 2 * (size_t)h->nc * n_prog);
   const size_t o_k2c = take(sizeof(unsigned) * (size_t)scf_k2_groups(h->nc) * n_prog);
-  const size_t o_tab = h->gen ? take(sizeof(ScfConst)) : off;
+  const size_t o_tab = take(sizeof(ScfConst));
+  const size_t o_alpha = take(sizeof(double) * 4 * (size_t)n_prog);
   const size_t o_rc = take(sizeof(double) * 16 * (size_t)n_prog);
   const size_t o_sp = take(sizeof(double) * (kScalePoints + 1) * nb3);
   if (cudaMalloc(&h->d_base, off) != cudaSuccess) {
@@ -586,8 +605,9 @@ int scf_init(const scf_config* cfg, int n_prog, const int64_t* offsets, const do
   h->d_rc = reinterpret_cast<double*>(base + o_rc);
   h->d_sp = reinterpret_cast<double*>(base + o_sp);
 
+  h->d_tab = reinterpret_cast<ScfConst*>(base + o_tab);
+  h->d_alpha = reinterpret_cast<double*>(base + o_alpha);
   if (h->gen) {  // recurrence tables of the handle's radial family
-    h->d_tab = reinterpret_cast<ScfConst*>(base + o_tab);
     std::unique_ptr<ScfConst> t(new (std::nothrow) ScfConst);
     if (!t) return fail(SCF_ERR_OUT_OF_MEMORY);
     scf_make_const(t.get(), cfg->alpha);
@@ -696,6 +716,107 @@ int scf_step(scf_handle* h, void* pos, void* vel, void* acc, double* com, int ns
     const int rc = launch_step(h, pos, vel, acc, com);
     if (rc != SCF_OK) return rc;
   }
+  return SCF_OK;
+}
+
+namespace {
+
+// Chunk c of `chunks` equal block ranges of a map with `blocks` blocks.
+void block_range(int blocks, int chunks, int c, int* b0, int* b1) {
+  *b0 = (int)((int64_t)blocks * c / chunks);
+  *b1 = (int)((int64_t)blocks * (c + 1) / chunks);
+}
+
+}  // namespace
+
+int scf_step_host(scf_handle* h, void* pos, void* vel, void* acc, double* com, void* host_pos, void* host_vel,
+                  void* host_acc, double* host_com, int chunks) {
+  if (!h) return SCF_ERR_NULL_POINTER;
+  if (chunks < 1 || chunks > SCF_STAGE_MAX_CHUNKS) return SCF_ERR_INVALID_ARG;
+  if ((!host_pos || !host_vel || !host_acc) && h->n_total > 0) return SCF_ERR_NULL_POINTER;
+  const bool with_com = h->host.n > 0;
+  if (with_com && !host_com) return SCF_ERR_NULL_POINTER;
+  // Mapped page-locked host memory: the step's kernels read and write the
+  // host arrays in place over the host link, so the transfers run inside
+  // the kernels, overlapped with their arithmetic (the usual case with
+  // cudaHostAlloc / torch pin_memory under unified addressing).
+  void* hp[4] = {host_pos, host_vel, host_acc, host_com};
+  void* mp[4] = {nullptr, nullptr, nullptr, nullptr};
+  bool mapped = true;
+  for (int i = 0; i < 4 && mapped; ++i) {
+    if (!hp[i]) continue;
+    cudaPointerAttributes attr{};
+    if (cudaPointerGetAttributes(&attr, hp[i]) != cudaSuccess) {
+      cudaGetLastError();
+      mapped = false;
+    } else if (attr.type == cudaMemoryTypeHost && attr.devicePointer != nullptr) {
+      mp[i] = attr.devicePointer;
+    } else {
+      mapped = false;
+    }
+  }
+  if (mapped && aligned16(mp[0]) && aligned16(mp[1]) && aligned16(mp[2]))
+    return scf_step(h, mp[0], mp[1], mp[2], static_cast<double*>(mp[3]), 1);
+
+  // Otherwise the state is staged through the device arrays: copied in, kernel
+  // 1 and 2, and copied back while kernel 3 still runs -- positions (final
+  // after kernel 1) during kernels 2 and 3, velocities and accelerations
+  // chunk by chunk of kernel 3's block map.
+  if ((!pos || !vel || !acc) && h->n_total > 0) return SCF_ERR_NULL_POINTER;
+  if (with_com && !com) return SCF_ERR_NULL_POINTER;
+  if (!aligned16(pos) || !aligned16(vel) || !aligned16(acc)) return SCF_ERR_MISALIGNED;
+  if (!h->copy_stream) {
+    if (cudaStreamCreateWithFlags(&h->copy_stream, cudaStreamNonBlocking) != cudaSuccess) {
+      h->copy_stream = nullptr;
+      return SCF_ERR_CUDA;
+    }
+    h->stage_ev.assign(SCF_STAGE_MAX_CHUNKS + 4, nullptr);  // start, in, done, kernels 1-2, one per chunk
+    for (cudaEvent_t& e : h->stage_ev)
+      if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) return SCF_ERR_CUDA;
+  }
+  cudaStream_t cs = h->copy_stream;
+  cudaEvent_t ev_start = h->stage_ev[0], ev_in = h->stage_ev[1], ev_done = h->stage_ev[2];
+  cudaEvent_t* ev_out = &h->stage_ev[3];
+  const size_t rec = h->cfg.precision == SCF_MIXED ? 16 : 32;
+  const size_t bytes = rec * (size_t)h->n_total, com_bytes = sizeof(double) * 6 * (size_t)h->n_prog;
+  char* dp[3] = {static_cast<char*>(pos), static_cast<char*>(vel), static_cast<char*>(acc)};
+  char* hh[3] = {static_cast<char*>(host_pos), static_cast<char*>(host_vel), static_cast<char*>(host_acc)};
+  auto ok = [](cudaError_t e) { return e == cudaSuccess; };
+  // the device arrays may still be in use by work queued earlier on the handle's stream
+  if (!ok(cudaEventRecord(ev_start, h->stream)) || !ok(cudaStreamWaitEvent(cs, ev_start, 0))) return SCF_ERR_CUDA;
+  for (int i = 0; i < 3; ++i)
+    if (bytes && !ok(cudaMemcpyAsync(dp[i], hh[i], bytes, cudaMemcpyHostToDevice, cs))) return SCF_ERR_CUDA;
+  if (with_com && !ok(cudaMemcpyAsync(com, host_com, com_bytes, cudaMemcpyHostToDevice, cs))) return SCF_ERR_CUDA;
+  if (!ok(cudaEventRecord(ev_in, cs)) || !ok(cudaStreamWaitEvent(h->stream, ev_in, 0))) return SCF_ERR_CUDA;
+  int rc = run_coeffs(h, pos, vel, acc, h->step_mask, h->d_A, com, SCF_MODE_STEP);
+  if (rc != SCF_OK) return rc;
+  // kernel 2 (already queued) does not touch the positions; kernel 3 only reads them
+  if (!ok(cudaEventRecord(ev_out[0], h->stream)) || !ok(cudaStreamWaitEvent(cs, ev_out[0], 0))) return SCF_ERR_CUDA;
+  if (bytes && !ok(cudaMemcpyAsync(hh[0], dp[0], bytes, cudaMemcpyDeviceToHost, cs))) return SCF_ERR_CUDA;
+  if (with_com && !ok(cudaMemcpyAsync(host_com, com, com_bytes, cudaMemcpyDeviceToHost, cs))) return SCF_ERR_CUDA;
+  const int c3 = std::max(1, std::min(chunks, h->k3_blocks));
+  for (int c = 0; c < c3 && h->k3_blocks > 0; ++c) {
+    int b0, b1;
+    block_range(h->k3_blocks, c3, c, &b0, &b1);
+    if (b1 <= b0) continue;
+    K3Args a = k3_args(h, pos, vel, acc, com, SCF_MODE_STEP);
+    a.blk_prog += b0;
+    a.blk_begin += b0;
+    a.blk_end += b0;
+    const cudaError_t e = timed(h, 2, [&] {
+      return h->k3.variant == 2 ? scf_k3_ff_launch(a, b1 - b0, h->k3, h->stream)
+                                : scf_k3_launch(h->cfg.precision, a, b1 - b0, h->k3_native, h->stream);
+    });
+    if (e != cudaSuccess) return SCF_ERR_CUDA;
+    if (!ok(cudaEventRecord(ev_out[1 + c], h->stream)) || !ok(cudaStreamWaitEvent(cs, ev_out[1 + c], 0)))
+      return SCF_ERR_CUDA;
+    const size_t k0 = (size_t)h->h_blk3_begin[b0], k1 = (size_t)h->h_blk3_end[b1 - 1];
+    for (int i = 1; i < 3; ++i)
+      if (k1 > k0 && !ok(cudaMemcpyAsync(hh[i] + k0 * rec, dp[i] + k0 * rec, (k1 - k0) * rec, cudaMemcpyDeviceToHost, cs)))
+        return SCF_ERR_CUDA;
+  }
+  // the handle's stream covers the copies too
+  if (!ok(cudaEventRecord(ev_done, cs)) || !ok(cudaStreamWaitEvent(h->stream, ev_done, 0))) return SCF_ERR_CUDA;
   return SCF_OK;
 }
 
@@ -812,6 +933,8 @@ int scf_adjoint_level(scf_handle* h, const void* pos, const double* com, double 
   if (!h) return SCF_ERR_NULL_POINTER;
   if (h->cfg.precision != SCF_FP64) return SCF_ERR_ADJOINT_FP64;
   if (h->gen) return SCF_ERR_UNSUPPORTED;  // the adjoint kernels are written for alpha = 1
+  for (int i = 0; i < h->host.n; ++i)        // and for the Hernquist, NFW and Miyamoto-Nagai components
+    if (h->host.kind[i] == SCF_HOST_POWCUT) return SCF_ERR_UNSUPPORTED;
   if ((!pos || !xbar || !vbar) && h->n_total > 0) return SCF_ERR_NULL_POINTER;
   if (h->host.n > 0 && (!com || !combar || !thetabar)) return SCF_ERR_NULL_POINTER;
   if (!aligned16(pos) || !aligned16(xbar) || !aligned16(vbar)) return SCF_ERR_MISALIGNED;
@@ -969,7 +1092,10 @@ int scf_evolve(scf_handle* h, void* pos, void* vel, void* acc, double* com, int 
   if (nsteps < 0 || ep->max_steps < 1 || !(ep->eta > 0.0) || !std::isfinite(ep->eta) || !(h->cfg.dt > 0.0))
     return SCF_ERR_INVALID_ARG;
   if (!(ep->kin > 0.0) || !std::isfinite(ep->kin) || !(ep->frac > 0.0 && ep->frac <= 1.0) || ep->retune_every < 0 ||
-      (ep->recentre != 0 && ep->recentre != 1) || (ep->retune_rule != 0 && ep->retune_rule != 1))
+      (ep->recentre != 0 && ep->recentre != 1) || ep->retune_rule < 0 || ep->retune_rule > 2)
+    return SCF_ERR_INVALID_ARG;
+  if (ep->retune_rule == 2 && ep->retune_every > 0 &&
+      (!(ep->alpha_lo > 0.0) || !(ep->alpha_hi > ep->alpha_lo) || !std::isfinite(ep->alpha_hi)))
     return SCF_ERR_INVALID_ARG;
   int rc = scf_set_mask(h, mask);
   if (rc != SCF_OK) return rc;
@@ -990,6 +1116,9 @@ int scf_evolve(scf_handle* h, void* pos, void* vel, void* acc, double* com, int 
       }
       if (ep->retune_rule == 1) {  // b at the maximum of a_000 of the coefficient set
         rc = scf_retune_a000(h, pos, mask);
+        if (rc != SCF_OK) return rc;
+      } else if (ep->retune_rule == 2) {  // alpha and b at the joint maximum
+        rc = scf_retune_alpha(h, pos, mask, ep->alpha_lo, ep->alpha_hi, nullptr);
         if (rc != SCF_OK) return rc;
       } else {
         BoundArgs a{};
@@ -1117,6 +1246,193 @@ int scf_retune_a000(scf_handle* h, const void* pos, const uint8_t* mask) {
   return cuda_fail(scf_scale_a000_launch(a, h->stream));
 }
 
+namespace {
+
+// Digamma function psi(x), x > 0: the recurrence psi(x) = psi(x + 1) - 1/x up
+// to x >= 8, then the asymptotic series ln x - 1/(2x) - sum_k B_2k / (2k x^2k)
+// (Abramowitz & Stegun 6.3.5 and 6.3.18).
+double digamma_host(double x) {
+  double acc = 0.0;
+  while (x < 8.0) {
+    acc -= 1.0 / x;
+    x += 1.0;
+  }
+  const double i2 = 1.0 / (x * x);
+  const double series =
+      i2 * (1.0 / 12 - i2 * (1.0 / 120 - i2 * (1.0 / 252 - i2 * (1.0 / 240 - i2 * (1.0 / 132 - i2 * (691.0 / 32760))))));
+  return acc + std::log(x) - 0.5 / x - series;
+}
+
+// ln|I_00(alpha)| at b = 1 and its alpha derivative, for the lowest pair of
+// the Zhao family: |I_00| = (alpha + 1) Gamma(2 alpha + 1) /
+// (2^(4 alpha + 3) (alpha + 1/2) Gamma(alpha + 1/2)^2).
+double ln_i00(double al) {
+  return std::log(al + 1.0) + std::lgamma(2.0 * al + 1.0) - (4.0 * al + 3.0) * std::log(2.0) - std::log(al + 0.5) -
+         2.0 * std::lgamma(al + 0.5);
+}
+double dln_i00(double al) {
+  return 1.0 / (al + 1.0) + 2.0 * digamma_host(2.0 * al + 1.0) - 4.0 * std::log(2.0) - 1.0 / (al + 0.5) -
+         2.0 * digamma_host(al + 0.5);
+}
+
+// Moves the handle to the radial family of exponent alpha: recurrence tables,
+// normalisation and field-kernel scales rebuilt and uploaded, the general
+// kernels selected for alpha != 1 (default shapes; no float-float variants).
+int set_alpha(scf_handle* h, double alpha) {
+  if (cudaStreamSynchronize(h->stream) != cudaSuccess) return SCF_ERR_CUDA;
+  const bool gen = alpha != 1.0;
+  if (gen) {
+    std::unique_ptr<ScfConst> t(new (std::nothrow) ScfConst);
+    if (!t) return SCF_ERR_OUT_OF_MEMORY;
+    scf_make_const(t.get(), alpha);
+    if (!tables_finite(*t, h->cfg.lmax, h->cfg.nmax, h->cfg.precision == SCF_MIXED)) return SCF_ERR_UNSUPPORTED;
+    if (!put(h->d_tab, t.get(), sizeof(ScfConst))) return SCF_ERR_CUDA;
+  }
+  std::vector<double> norm(2 * (size_t)h->nc), ksc(2 * (size_t)h->nc);
+  scf_make_norm(h->cfg.nmax, h->cfg.lmax, norm.data(), alpha);
+  scf_make_kscale(h->cfg.nmax, h->cfg.lmax, ksc.data(), alpha);
+  for (double x : norm)
+    if (!std::isfinite(x)) return SCF_ERR_UNSUPPORTED;
+  std::vector<float> ksc_f(ksc.begin(), ksc.end());
+  const bool ok = (h->cfg.precision == SCF_MIXED ? put(h->d_kscale, ksc_f.data(), sizeof(float) * ksc_f.size())
+                                                 : put(h->d_kscale, ksc.data(), sizeof(double) * ksc.size())) &&
+                  put(h->d_norm, norm.data(), sizeof(double) * norm.size());
+  if (!ok) return SCF_ERR_CUDA;
+  h->cfg.alpha = alpha;
+  h->gen = gen;
+  if (gen) h->k1_ff = h->k3_ff = false;
+  int rc = h->cfg.precision == SCF_MIXED ? use_k1(h, 0) : SCF_ERR_UNSUPPORTED;
+  if (rc != SCF_OK) rc = use_k1(h, 128);
+  if (rc == SCF_OK) rc = use_k3(h, 128);
+  drop_graph(h);
+  return rc;
+}
+
+}  // namespace
+
+int scf_retune_alpha(scf_handle* h, const void* pos, const uint8_t* mask, double alpha_lo, double alpha_hi,
+                     double* alpha_out) {
+  if (!h) return SCF_ERR_NULL_POINTER;
+  if (!pos && h->n_total > 0) return SCF_ERR_NULL_POINTER;
+  if (!aligned16(pos)) return SCF_ERR_MISALIGNED;
+  if (!(alpha_lo > 0.0) || !(alpha_hi > alpha_lo) || !std::isfinite(alpha_hi)) return SCF_ERR_INVALID_ARG;
+  if (alpha_lo < SCF_ALPHA_MIN || alpha_hi > SCF_ALPHA_MAX) return SCF_ERR_UNSUPPORTED;
+  const int P = h->n_prog;
+  std::vector<double> b0(P), st(4 * (size_t)P);
+  if (cudaMemcpyAsync(b0.data(), h->d_b, sizeof(double) * P, cudaMemcpyDeviceToHost, h->stream) != cudaSuccess ||
+      cudaStreamSynchronize(h->stream) != cudaSuccess)
+    return SCF_ERR_CUDA;
+  ScaleArgs a{};
+  a.pos = pos;
+  a.mask = mask;
+  a.blk_prog = h->d_blk3_prog;
+  a.blk_begin = h->d_blk3_begin;
+  a.blk_end = h->d_blk3_end;
+  a.n_blocks = h->k3_blocks;
+  a.n_prog = P;
+  a.f32 = h->cfg.precision == SCF_MIXED;
+  a.span = 8.0;
+  a.part = h->d_sp;
+  a.state = h->d_rc;
+  double* d_bt = h->d_alpha;            // trial scales b_p(alpha)
+  double* d_sums = h->d_alpha + P;      // [P][3] sums at (alpha, b_p(alpha))
+  // ln of the product of the progenitors' a_000 at alpha (each at its own
+  // maximising b) and its alpha derivative (envelope theorem), from one
+  // b search and one pass of sums; `live` counts progenitors with a set
+  int live = 0;
+  auto eval = [&](double al, double* H, double* dH, std::vector<double>* bs) -> int {
+    if (!put(d_bt, b0.data(), sizeof(double) * P)) return SCF_ERR_CUDA;
+    a.b_prog = d_bt;
+    a.alpha = al;
+    a.inv_alpha = 1.0 / al;
+    if (scf_scale_a000_launch(a, h->stream) != cudaSuccess || scf_alpha_sums_launch(a, d_sums, h->stream) != cudaSuccess)
+      return SCF_ERR_CUDA;
+    std::vector<double> bt(P), sm(3 * (size_t)P);
+    if (cudaMemcpyAsync(bt.data(), d_bt, sizeof(double) * P, cudaMemcpyDeviceToHost, h->stream) != cudaSuccess ||
+        cudaMemcpyAsync(sm.data(), d_sums, sizeof(double) * 3 * P, cudaMemcpyDeviceToHost, h->stream) != cudaSuccess ||
+        cudaStreamSynchronize(h->stream) != cudaSuccess)
+      return SCF_ERR_CUDA;
+    double hs = 0.0, ds = 0.0;
+    live = 0;
+    for (int p = 0; p < P; ++p) {
+      if (!(sm[3 * p + 2] > 0.0) || !(sm[3 * p] > 0.0)) continue;
+      ++live;
+      hs += -0.5 * ln_i00(al) - 0.5 * std::log(bt[p]) + std::log(sm[3 * p]);
+      ds += -0.5 * dln_i00(al) + sm[3 * p + 1] / sm[3 * p];
+    }
+    *H = hs;
+    *dH = ds;
+    if (bs) *bs = bt;
+    return SCF_OK;
+  };
+  constexpr int kGrid = 17;
+  const double x_lo = std::log(alpha_lo), x_hi = std::log(alpha_hi), step = (x_hi - x_lo) / (kGrid - 1);
+  double hbest = -HUGE_VAL, dummy = 0.0;
+  int jbest = 0, rc = SCF_OK;
+  for (int j = 0; j < kGrid; ++j) {
+    double hj = 0.0;
+    if ((rc = eval(std::exp(x_lo + j * step), &hj, &dummy, nullptr)) != SCF_OK) return rc;
+    if (live == 0) {  // no progenitor has a coefficient set: nothing to fit
+      if (alpha_out) *alpha_out = h->cfg.alpha;
+      return SCF_OK;
+    }
+    if (hj > hbest) {
+      hbest = hj;
+      jbest = j;
+    }
+  }
+  double x = x_lo + jbest * step;
+  if (jbest > 0 && jbest < kGrid - 1) {
+    // root of dH in the bracket by the Illinois variant of regula falsi
+    double a0 = x - step, a1 = x + step, f0 = 0.0, f1 = 0.0, hh = 0.0;
+    if ((rc = eval(std::exp(a0), &hh, &f0, nullptr)) != SCF_OK || (rc = eval(std::exp(a1), &hh, &f1, nullptr)) != SCF_OK)
+      return rc;
+    if (f0 > 0.0 && f1 < 0.0) {
+      int side = 0;
+      for (int it = 0; it < 100 && a1 - a0 > 1e-15 * (1.0 + std::fabs(a0)); ++it) {
+        const double xm = (a0 * f1 - a1 * f0) / (f1 - f0);
+        double fm = 0.0;
+        if ((rc = eval(std::exp(xm), &hh, &fm, nullptr)) != SCF_OK) return rc;
+        x = xm;
+        if (fm == 0.0) break;
+        if (fm > 0.0) {
+          a0 = xm;
+          f0 = fm;
+          if (side == 1) f1 *= 0.5;
+          side = 1;
+        } else {
+          a1 = xm;
+          f1 = fm;
+          if (side == -1) f0 *= 0.5;
+          side = -1;
+        }
+      }
+    }
+  }
+  const double alpha = std::exp(x);
+  std::vector<double> bs;
+  double hh = 0.0;
+  if ((rc = eval(alpha, &hh, &dummy, &bs)) != SCF_OK) return rc;
+  // the new exponent: tables, normalisation, kernels; then each progenitor's b
+  const double old = h->cfg.alpha;
+  rc = set_alpha(h, alpha);
+  if (rc != SCF_OK) {
+    set_alpha(h, old);
+    return rc;
+  }
+  for (int p = 0; p < P; ++p)
+    if (!(bs[p] > 0.0) || !std::isfinite(bs[p])) bs[p] = b0[p];
+  if (!put(h->d_b, bs.data(), sizeof(double) * P)) return SCF_ERR_CUDA;
+  if (alpha_out) *alpha_out = alpha;
+  return SCF_OK;
+}
+
+int scf_get_alpha(const scf_handle* h, double* alpha) {
+  if (!h || !alpha) return SCF_ERR_NULL_POINTER;
+  *alpha = h->cfg.alpha;
+  return SCF_OK;
+}
+
 int scf_get_scales(scf_handle* h, double* b_out) {
   if (!h || !b_out) return SCF_ERR_NULL_POINTER;
   return cuda_fail(
@@ -1195,6 +1511,9 @@ int scf_free(scf_handle* h) {
   if (cudaStreamSynchronize(h->stream) != cudaSuccess) rc = SCF_ERR_CUDA;
   prof_release(h);
   drop_graph(h);
+  if (h->copy_stream && cudaStreamSynchronize(h->copy_stream) != cudaSuccess) rc = SCF_ERR_CUDA;
+  for (cudaEvent_t e : h->stage_ev) cudaEventDestroy(e);
+  if (h->copy_stream) cudaStreamDestroy(h->copy_stream);
   if (h->d_base && cudaFree(h->d_base) != cudaSuccess) rc = SCF_ERR_CUDA;
   delete h;
   return rc;

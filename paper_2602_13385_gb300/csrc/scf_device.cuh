@@ -114,10 +114,55 @@ struct __align__(16) ScfD4 {
 
 __host__ __device__ constexpr int scf_lm(int l, int m) { return l * (l + 1) / 2 + m; }
 
+// Regularised lower incomplete gamma function P(a, x) = gamma(a, x) / Gamma(a)
+// (a > 0, x >= 0) for the cut-off power-law bulge of MWPotential2014 (App. A).
+// Kummer's series P = x^a e^-x / Gamma(a + 1) sum_k x^k / ((a+1)...(a+k)) for
+// x < a + 1; otherwise P = 1 - Q with Q = x^a e^-x / Gamma(a) times Legendre's
+// continued fraction 1/(x + 1 - a - 1(1 - a)/(x + 3 - a - 2(2 - a)/(x + 5 - a - ...))),
+// evaluated forwards by the modified Lentz algorithm (Thompson & Barnett 1986).
+template <typename F>
+__device__ __forceinline__ F scf_gamma_p_t(F a, F x) {
+  if (!(x > F(0))) return F(0);
+  const F eps = sizeof(F) == 8 ? F(1e-16) : F(3e-8), tiny = sizeof(F) == 8 ? F(1e-300) : F(1e-30);
+  const F lpre = a * log(x) - x - lgamma(a);
+  if (x < a + F(1)) {
+    F ap = a, term = F(1) / a, sum = term;
+    for (int k = 0; k < 500; ++k) {
+      ap += F(1);
+      term *= x / ap;
+      sum += term;
+      if (fabs(term) < fabs(sum) * eps) break;
+    }
+    return sum * exp(lpre);
+  }
+  F b = x + F(1) - a, c = F(1) / tiny, d = F(1) / b, h = d;
+  for (int k = 1; k < 500; ++k) {
+    const F an = -F(k) * (F(k) - a);
+    b += F(2);
+    d = an * d + b;
+    if (fabs(d) < tiny) d = tiny;
+    c = b + an / c;
+    if (fabs(c) < tiny) c = tiny;
+    d = F(1) / d;
+    const F del = d * c;
+    h *= del;
+    if (fabs(del - F(1)) < eps) break;
+  }
+  return F(1) - exp(lpre) * h;
+}
+__device__ __forceinline__ double scf_gamma_p(double a, double x) { return scf_gamma_p_t<double>(a, x); }
+__device__ __forceinline__ float scf_gamma_pf(float a, float x) { return scf_gamma_p_t<float>(a, x); }
+// Dual argument: dP/dx = x^(a-1) e^-x / Gamma(a).
+__device__ __forceinline__ Dual scf_gamma_p(double a, Dual x) {
+  const double v = scf_gamma_p(a, x.v);
+  const double dens = x.v > 0.0 ? exp((a - 1.0) * log(x.v) - x.v - lgamma(a)) : 0.0;
+  return Dual(v, x.d * dens);
+}
 // Acceleration of the analytic host (App. A) at (x, y, z), double precision.
 //   Hernquist: f_r = -GM/(r+a)^2;  NFW: f_r = -GM [ln(1+u) - u/(1+u)]/r^2, u = r/r_s;
 //   Miyamoto-Nagai: f_R = -GM R/D^3, f_z = -GM z z_ab/(sqrt(z^2+b^2) D^3),
-//   z_ab = sqrt(z^2+b^2) + a, D^2 = R^2 + z_ab^2.
+//   z_ab = sqrt(z^2+b^2) + a, D^2 = R^2 + z_ab^2;
+//   cut-off power-law bulge (a = r_c, b = alpha): f_r = -GM P(s, (r/r_c)^2)/r^2, s = (3 - alpha)/2.
 // One host component's acceleration; N is double or Dual (for derivatives).
 template <typename N>
 __device__ __forceinline__ void scf_host_comp_accel(int kind, N GM, N A, N B, N x, N y, N z, N& ax, N& ay, N& az) {
@@ -138,6 +183,15 @@ __device__ __forceinline__ void scf_host_comp_accel(int kind, N GM, N A, N B, N 
       const N g = log1p(u) - u / (N(1.0) + u);
       f = -GM * g * rinv * rinv * rinv;
     }
+    ax = f * x;
+    ay = f * y;
+    az = f * z;
+  } else if (kind == 4) {  // cut-off power-law bulge (the index alpha is not a variable of N)
+    const N r2 = x * x + y * y + z * z;
+    if (!(r2 > N(0.0))) return;
+    const double s = 0.5 * (3.0 - value_of(B));
+    const N r = sqrt(r2);
+    const N f = -GM * scf_gamma_p(s, r2 / (A * A)) / (r2 * r);
     ax = f * x;
     ay = f * y;
     az = f * z;
@@ -174,7 +228,8 @@ __device__ __forceinline__ void scf_host_accel(const ScfHostParams& hp, double x
 
 // Potential of the analytic host (App. A) at (x, y, z), double precision:
 //   Hernquist -GM/(r+a);  NFW -GM ln(1 + r/r_s)/r (-GM/r_s at r = 0);
-//   Miyamoto-Nagai -GM/sqrt(R^2 + (sqrt(z^2+b^2) + a)^2).
+//   Miyamoto-Nagai -GM/sqrt(R^2 + (sqrt(z^2+b^2) + a)^2);
+//   cut-off bulge GM (P(1 - alpha/2, x) Gamma(1 - alpha/2)/(Gamma(s) r_c) - P(s, x)/r), x = (r/r_c)^2.
 __device__ __forceinline__ double scf_host_pot(const ScfHostParams& hp, double x, double y, double z) {
   double psi = 0.0;
   const double r = sqrt(x * x + y * y + z * z);
@@ -187,6 +242,9 @@ __device__ __forceinline__ double scf_host_pot(const ScfHostParams& hp, double x
     } else if (hp.kind[i] == 3) {
       const double zab = sqrt(z * z + hp.b[i] * hp.b[i]) + A;
       psi -= GM / sqrt(x * x + y * y + zab * zab);
+    } else if (hp.kind[i] == 4) {
+      const double s = 0.5 * (3.0 - hp.b[i]), s2 = 1.0 - 0.5 * hp.b[i], X = (r / A) * (r / A);
+      psi += GM * (scf_gamma_p(s2, X) * exp(lgamma(s2) - lgamma(s)) / A - (r > 0.0 ? scf_gamma_p(s, X) / r : 0.0));
     }
   }
   return psi;
@@ -204,6 +262,11 @@ __device__ __forceinline__ double scf_host_pot(const ScfHostParams& hp, double x
 //     zb1 - zb0 = (2 Rz z + z^2)/(zb1 + zb0),  D1 - D0 = (D1^2 - D0^2)/(D1 + D0),
 //     1/D1^3 - 1/D0^3 = -(D1 - D0)(D1^2 + D1 D0 + D0^2)/(D0^3 D1^3),
 //     a_z = -GM z v/D^3 with v = 1 + a/zb, v1 - v0 = -a (zb1 - zb0)/(zb1 zb0).
+//   cut-off power-law bulge (g = GM P(s, X)/r^3, X = (r/r_c)^2, s = (3 - alpha)/2):
+//     g1 - g0 = GM [(P1 - P0)/r1^3 + P0 (1/r1^3 - 1/r0^3)], X1 - X0 = dr (r1 + r0)/r_c^2,
+//     P1 - P0 = int_X0^X1 t^(s-1) e^-t dt / Gamma(s) by six-point Gauss-Legendre
+//     quadrature when |X1 - X0| <= min(X0/2, 2) (the integrand is smooth there), else
+//     the plain difference (no cancellation then).
 // Relative error of the result a few float ulps for any |x|/|R| (checked
 // against the long-double difference of the oracle).
 __device__ __forceinline__ void scf_tidal_f32(const ScfHostParams& hp, float Rx, float Ry, float Rz, float x, float y,
@@ -254,6 +317,35 @@ __device__ __forceinline__ void scf_tidal_f32(const ScfHostParams& hp, float Rx,
       const float v0 = 1.f + A / zb0, v1 = 1.f + A / zb1;
       const float dv = -A * dzb / (zb1 * zb0);
       az -= GM * (z * v1 * i1 + Rz * (dv * i1 + v0 * di));
+    } else if (hp.kind[i] == 4) {  // cut-off power-law bulge
+      const float s = 0.5f * (3.f - (float)hp.b[i]);
+      const float ia2 = 1.f / (A * A);
+      const float X0 = r0 * r0 * ia2, X1 = r1 * r1 * ia2;
+      const float dX = dr * (r1 + r0) * ia2;
+      const float P0 = scf_gamma_pf(s, X0), P1 = scf_gamma_pf(s, X1);
+      float dP;
+      if (fabsf(dX) <= fminf(0.5f * X0, 2.f)) {
+        // Gauss-Legendre nodes +-xi_j and weights w_j on [-1, 1] (6 points)
+        const float gx[3] = {0.2386191860831969f, 0.6612093864662645f, 0.9324695142031521f};
+        const float gw[3] = {0.4679139345726910f, 0.3607615730481386f, 0.1713244923791704f};
+        const float lg = lgammaf(s), hw = 0.5f * dX, cm = X0 + hw;
+        float acc = 0.f;
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+          const float t1 = cm + hw * gx[j], t2 = cm - hw * gx[j];
+          acc += gw[j] * (expf((s - 1.f) * logf(t1) - t1 - lg) + expf((s - 1.f) * logf(t2) - t2 - lg));
+        }
+        dP = hw * acc;
+      } else {
+        dP = P1 - P0;
+      }
+      const float i0 = 1.f / (r0 * r0 * r0), i1 = 1.f / (r1 * r1 * r1);
+      const float di = -dr * (r0 * r0 + r0 * r1 + r1 * r1) * i0 * i1;
+      const float g1 = GM * P1 * i1;
+      const float dg = GM * (dP * i1 + P0 * di);
+      ax -= g1 * x + dg * Rx;
+      ay -= g1 * y + dg * Ry;
+      az -= g1 * z + dg * Rz;
     }
   }
 }

@@ -189,6 +189,7 @@ cudaError_t scf_core_launch(const RecentreArgs& a, cudaStream_t s);
 // kScaleRounds grids of kScalePoints values of ln b, b_prog updated in place.
 constexpr int kScalePoints = 33;
 constexpr int kScaleRounds = 3;
+constexpr int kScaleNewton = 4;  // safeguarded Newton steps on d ln a_000 / d ln b = 0 after the grids
 struct ScaleArgs {
   const void* pos;
   const uint8_t* mask;       // coefficient set, or null
@@ -203,6 +204,9 @@ struct ScaleArgs {
   double* state;             // [n_prog][4] scratch
 };
 cudaError_t scf_scale_a000_launch(const ScaleArgs& a, cudaStream_t s);
+// Sums of the exponent search at (a.alpha, a.b_prog[p]) per progenitor into
+// out[p][3] = (sum m g, sum m g d ln g / d alpha, sum m), g = (1 + (r/b)^(1/alpha))^-alpha.
+cudaError_t scf_alpha_sums_launch(const ScaleArgs& a, double* out, cudaStream_t s);
 
 struct ScfLaunchInfo {
   int threads;   // threads per block

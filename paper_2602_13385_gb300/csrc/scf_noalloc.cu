@@ -21,6 +21,7 @@
 // the array and give wrong results: serialise them.
 #include <algorithm>
 #include <cmath>
+#include <cstddef>
 #include <mutex>
 
 #include "../../include/scf.h"
@@ -170,4 +171,23 @@ extern "C" int scf_coeffs_noalloc(const scf_config* cfg, int64_t n, const void* 
   r.n_prog = 1;
   r.mode = SCF_MODE_COEFFS;
   return scf_k2_launch(r, s) == cudaSuccess ? SCF_OK : SCF_ERR_CUDA;
+}
+
+extern "C" int scf_noalloc_status(void* stream, int* status) {
+  if (status) *status = 0;
+  int device = 0;
+  if (cudaGetDevice(&device) != cudaSuccess) return SCF_ERR_CUDA;
+  if (device < 0 || device >= kMaxDevices) return SCF_ERR_UNSUPPORTED;
+  {
+    std::lock_guard<std::mutex> lock(g_setup_mutex);
+    if (!g_setup[device].ready) return SCF_OK;  // no call has run on this device
+  }
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  unsigned word = 0;
+  if (cudaMemcpyFromSymbolAsync(&word, g_scratch, sizeof(unsigned), offsetof(NoallocScratch, status),
+                                cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+      cudaStreamSynchronize(s) != cudaSuccess)
+    return SCF_ERR_CUDA;
+  if (status) *status = (int)word;
+  return word != 0 ? SCF_ERR_DEVICE_STATUS : SCF_OK;
 }

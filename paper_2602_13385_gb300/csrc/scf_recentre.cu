@@ -291,8 +291,16 @@ cudaError_t scf_core_launch(const RecentreArgs& a, cudaStream_t s) {
 // ln b: kScaleRounds grids of kScalePoints values, the first over
 // [b/span, b span], each next over one step either side of the previous best
 // (the first best in grid order); the last best moves to the vertex of the
-// parabola through it and its neighbours.  An empty set keeps b.
-// state[p]: [0] ln b of the grid's first point, [1] the step, [2] best index.
+// parabola through it and its neighbours.  From there kScaleNewton
+// safeguarded Newton steps solve the stationarity condition
+//   D(x) = d ln h / d ln b = S1/S0 - 1/2 = 0,   x = ln b,  t = (r/b)^(1/alpha),
+//   S0 = sum m (1+t)^-alpha,  S1 = sum m t (1+t)^(-alpha-1),
+//   D'(x) = S2/S0 - (S1/S0)^2,  S2 = sum m (-t/alpha) (1+t)^(-alpha-2) (1 - alpha t)
+// inside the last grid's bracket (a step that leaves the bracket, or a
+// non-negative D', bisects it instead; the sign of D shrinks it), so b is the
+// maximiser to rounding, not to the grid's resolution.  An empty set keeps b.
+// state[p]: during the grids [0] ln b of the grid's first point, [1] the step;
+// during the Newton steps [0], [1] the bracket, [2] 1 = refine, [3] x.
 namespace {
 
 template <typename V4>
@@ -383,15 +391,156 @@ __global__ void k_scale_sum(ScaleArgs a, int round) {
     return;
   }
   double x = st[0] + best * st[1];
-  if (best > 0 && best < NP - 1) {
+  const double lo = st[0] + (best - 1) * st[1], hi = st[0] + (best + 1) * st[1];
+  const bool inner = best > 0 && best < NP - 1;
+  if (inner) {
     const double hm = s_h[best - 1], h0 = s_h[best], hp = s_h[best + 1];
     const double den = hm - 2.0 * h0 + hp;
     if (den < 0.0) x += 0.5 * st[1] * (hm - hp) / den;
   }
+  st[0] = lo;
+  st[1] = hi;
+  st[2] = inner ? 1.0 : 0.0;
+  st[3] = x;
   a.b_prog[p] = exp(x);
 }
 
+// Block sums (S0, S1, S2, mass) of the Newton step at each progenitor's x.
+template <typename V4>
+__global__ void __launch_bounds__(kRcThreads) k_scale_newton_blocks(ScaleArgs a) {
+  __shared__ double s_w[kRcWarps][4];
+  const int p = a.blk_prog[blockIdx.x];
+  const double ib = exp(-a.state[4 * (size_t)p + 3]);
+  double v[4] = {0.0, 0.0, 0.0, 0.0};
+  const V4* pos = reinterpret_cast<const V4*>(a.pos);
+  const int64_t end = a.blk_end[blockIdx.x];
+  for (int64_t k = a.blk_begin[blockIdx.x] + threadIdx.x; k < end; k += kRcThreads) {
+    if (a.mask && !a.mask[k]) continue;
+    const V4 q = pos[k];
+    const double r = sqrt(((double)q.x * q.x + (double)q.y * q.y) + (double)q.z * q.z);
+    const double m = q.w;
+    const double t = a.alpha == 1.0 ? r * ib : pow(r * ib, a.inv_alpha);
+    const double u = 1.0 / (1.0 + t);                                   // (1+t)^-1
+    const double g = a.alpha == 1.0 ? u : pow(u, a.alpha);              // (1+t)^-alpha
+    const double w = t * g * u;                                         // t (1+t)^(-alpha-1)
+    v[0] += m * g;
+    v[1] += m * w;
+    v[2] += m * (-w * u * (1.0 - a.alpha * t) * a.inv_alpha);           // (-t/alpha)(1+t)^(-alpha-2)(1 - alpha t)
+    v[3] += m;
+  }
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    double x = v[j];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+    if (lane == 0) s_w[warp][j] = x;
+  }
+  __syncthreads();
+  if (threadIdx.x < 4) {
+    double x = 0.0;
+#pragma unroll
+    for (int w = 0; w < kRcWarps; ++w) x += s_w[w][threadIdx.x];
+    a.part[(size_t)blockIdx.x * (kScalePoints + 1) + threadIdx.x] = x;
+  }
+}
+
+// One warp per progenitor: the sums in block order, then one safeguarded
+// Newton step of D(x) = 0 within the bracket; b = exp(x).
+__global__ void k_scale_newton_step(ScaleArgs a) {
+  const int p = blockIdx.x, lane = threadIdx.x;
+  double* st = a.state + 4 * (size_t)p;
+  if (st[2] != 1.0) return;  // maximum at an end of the range, or an empty set
+  double v[4] = {0.0, 0.0, 0.0, 0.0};
+  for (int b = lane; b < a.n_blocks; b += 32) {
+    if (a.blk_prog[b] != p) continue;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) v[j] += a.part[(size_t)b * (kScalePoints + 1) + j];
+  }
+#pragma unroll
+  for (int j = 0; j < 4; ++j)
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v[j] += __shfl_xor_sync(0xffffffffu, v[j], o);
+  if (lane != 0 || !(v[3] > 0.0) || !(v[0] > 0.0)) return;
+  const double x = st[3], f = v[1] / v[0];
+  const double D = f - 0.5, dD = v[2] / v[0] - f * f;
+  if (D > 0.0) st[0] = x;  // the maximum lies above x
+  else if (D < 0.0) st[1] = x;
+  else return;
+  double xn = x - D / dD;
+  if (!(dD < 0.0) || !(xn > st[0] && xn < st[1])) xn = 0.5 * (st[0] + st[1]);
+  st[3] = xn;
+  a.b_prog[p] = exp(xn);
+}
+
+// Block sums of the exponent search at (alpha, b_p): S0 = sum m g, S1 =
+// sum m g d ln g / d alpha, with g = (1 + t)^-alpha, t = (r/b)^(1/alpha) and
+// d ln g / d alpha = -ln(1 + t) + t ln(r/b) / (alpha (1 + t)); and the mass.
+template <typename V4>
+__global__ void __launch_bounds__(kRcThreads) k_alpha_blocks(ScaleArgs a) {
+  __shared__ double s_w[kRcWarps][3];
+  const int p = a.blk_prog[blockIdx.x];
+  const double ib = 1.0 / a.b_prog[p];
+  double v[3] = {0.0, 0.0, 0.0};
+  const V4* pos = reinterpret_cast<const V4*>(a.pos);
+  const int64_t end = a.blk_end[blockIdx.x];
+  for (int64_t k = a.blk_begin[blockIdx.x] + threadIdx.x; k < end; k += kRcThreads) {
+    if (a.mask && !a.mask[k]) continue;
+    const V4 q = pos[k];
+    const double r = sqrt(((double)q.x * q.x + (double)q.y * q.y) + (double)q.z * q.z);
+    const double m = q.w;
+    const double s = r * ib;
+    const double t = pow(s, a.inv_alpha);
+    const double g = pow(1.0 + t, -a.alpha);
+    const double dlng = -log1p(t) + (s > 0.0 ? t * log(s) : 0.0) * a.inv_alpha / (1.0 + t);
+    v[0] += m * g;
+    v[1] += m * g * dlng;
+    v[2] += m;
+  }
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int j = 0; j < 3; ++j) {
+    double x = v[j];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+    if (lane == 0) s_w[warp][j] = x;
+  }
+  __syncthreads();
+  if (threadIdx.x < 3) {
+    double x = 0.0;
+#pragma unroll
+    for (int w = 0; w < kRcWarps; ++w) x += s_w[w][threadIdx.x];
+    a.part[(size_t)blockIdx.x * (kScalePoints + 1) + threadIdx.x] = x;
+  }
+}
+
+// One warp per progenitor: the block sums in block order into out[p][0..2].
+__global__ void k_alpha_sum(ScaleArgs a, double* out) {
+  const int p = blockIdx.x, lane = threadIdx.x;
+  double v[3] = {0.0, 0.0, 0.0};
+  for (int b = lane; b < a.n_blocks; b += 32) {
+    if (a.blk_prog[b] != p) continue;
+#pragma unroll
+    for (int j = 0; j < 3; ++j) v[j] += a.part[(size_t)b * (kScalePoints + 1) + j];
+  }
+#pragma unroll
+  for (int j = 0; j < 3; ++j)
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v[j] += __shfl_xor_sync(0xffffffffu, v[j], o);
+  if (lane == 0)
+    for (int j = 0; j < 3; ++j) out[3 * (size_t)p + j] = v[j];
+}
+
 }  // namespace
+
+cudaError_t scf_alpha_sums_launch(const ScaleArgs& a, double* out, cudaStream_t s) {
+  if (a.n_blocks > 0) {
+    if (a.f32) k_alpha_blocks<float4><<<a.n_blocks, kRcThreads, 0, s>>>(a);
+    else k_alpha_blocks<ScfD4><<<a.n_blocks, kRcThreads, 0, s>>>(a);
+  }
+  if (a.n_prog > 0) k_alpha_sum<<<a.n_prog, 32, 0, s>>>(a, out);
+  return cudaGetLastError();
+}
 
 cudaError_t scf_scale_a000_launch(const ScaleArgs& a, cudaStream_t s) {
   k_scale_init<<<(a.n_prog + 127) / 128, 128, 0, s>>>(a);
@@ -401,6 +550,13 @@ cudaError_t scf_scale_a000_launch(const ScaleArgs& a, cudaStream_t s) {
       else k_scale_blocks<ScfD4><<<a.n_blocks, kRcThreads, 0, s>>>(a);
     }
     k_scale_sum<<<a.n_prog, 32, 0, s>>>(a, r);
+  }
+  for (int it = 0; it < kScaleNewton; ++it) {
+    if (a.n_blocks > 0) {
+      if (a.f32) k_scale_newton_blocks<float4><<<a.n_blocks, kRcThreads, 0, s>>>(a);
+      else k_scale_newton_blocks<ScfD4><<<a.n_blocks, kRcThreads, 0, s>>>(a);
+    }
+    k_scale_newton_step<<<a.n_prog, 32, 0, s>>>(a);
   }
   return cudaGetLastError();
 }

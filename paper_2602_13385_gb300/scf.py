@@ -23,6 +23,7 @@ _CACHE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "_autotune_cac
 HOST_HERNQUIST = _lib.SCF_HOST_HERNQUIST
 HOST_NFW = _lib.SCF_HOST_NFW
 HOST_MN = _lib.SCF_HOST_MN
+HOST_POWCUT = _lib.SCF_HOST_POWCUT
 
 
 def n_lm(lmax: int) -> int:
@@ -117,6 +118,14 @@ class SCF:
             self._check_particles(t, nm)
         _lib.scf_step(self._h, pos, vel, acc, com, nsteps)
 
+    def step_host(self, pos, vel, acc, host_pos, host_vel, host_acc, com=None, host_com=None, chunks: int = 8):
+        """One step of a state held in host tensors ``host_*`` (page-locked for
+        overlap; read, then overwritten with the new state), through the
+        device tensors ``pos, vel, acc, com`` (scf_step_host)."""
+        for t, nm in ((pos, "pos"), (vel, "vel"), (acc, "acc")):
+            self._check_particles(t, nm)
+        _lib.scf_step_host(self._h, pos, vel, acc, com, host_pos, host_vel, host_acc, host_com, chunks)
+
     def energy(self, pos, vel, acc, com=None, out: torch.Tensor | None = None):
         """(n_prog, 4) float64 = (kinetic, self, tidal, total) energy per
         progenitor in its frame; ``acc`` must hold the accelerations and
@@ -157,13 +166,15 @@ class SCF:
 
     def evolve(self, pos, vel, acc, com=None, nsteps: int = 1, kin: float = 0.5, frac: float = 0.999,
                eta: float = 1.0 / 400.0, max_steps: int = 1000, retune_every: int = 0, recentre: bool = False,
-               retune_rule: str = "half_mass"):
+               retune_rule: str = "half_mass", alpha_range=(0.25, 2.0)):
         """``nsteps`` leapfrog steps with boundedness, the r <= r_x coefficient
         set, the tidal integration timestep and, every ``retune_every``
         integration timesteps, a complete refresh of b (``retune_rule``
-        "half_mass" or "a000", :meth:`retune_a000`), preceded with
-        ``recentre`` by :meth:`recentre` (scf_evolve).  Returns
-        ``(bound, mask, stats, n_int)`` as of the last integration timestep."""
+        "half_mass" or "a000", :meth:`retune_a000`) or of alpha and b
+        ("alpha_a000", :meth:`retune_alpha` over ``alpha_range``), preceded
+        with ``recentre`` by :meth:`recentre` (scf_evolve).  Returns
+        ``(bound, mask, stats, n_int)`` as of the last integration timestep;
+        ``self.config.alpha`` follows the handle's exponent."""
         for t, nm in ((pos, "pos"), (vel, "vel"), (acc, "acc")):
             self._check_particles(t, nm)
         if getattr(self, "_evolve_bufs", None) is None:
@@ -173,8 +184,19 @@ class SCF:
         b, m, st = self._evolve_bufs
         self._mask_ref = m
         n_int = _lib.scf_evolve(self._h, pos, vel, acc, com, nsteps, kin, frac, eta, max_steps, b, m, st,
-                                retune_every, recentre, {"half_mass": 0, "a000": 1}[retune_rule])
+                                retune_every, recentre, {"half_mass": 0, "a000": 1, "alpha_a000": 2}[retune_rule],
+                                alpha_range[0], alpha_range[1])
+        self.config.alpha = _lib.scf_get_alpha(self._h)
         return b, m, st, n_int
+
+    def retune_alpha(self, pos, mask=None, alpha_lo: float = 0.25, alpha_hi: float = 2.0) -> float:
+        """Moves the handle to the exponent alpha of the radial family and the
+        scales b at the joint maximum of a_000 (scf_retune_alpha); returns
+        alpha (also in ``self.config.alpha``)."""
+        self._check_particles(pos, "pos")
+        al = _lib.scf_retune_alpha(self._h, pos, mask, alpha_lo, alpha_hi)
+        self.config.alpha = al
+        return al
 
     def retune_a000(self, pos, mask=None):
         """Sets each progenitor's b to the maximum of a_000 of the coefficient

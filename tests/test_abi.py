@@ -102,3 +102,33 @@ def test_null_handle_is_rejected(lib):
     assert lib.scf_recentre(None, None, None, None, None, None, 100, 1e-12, None) == -2
     assert lib.scf_retune_a000(None, None, None) == -2
     assert lib.scf_free(None) == 0
+
+
+def test_noalloc_binding_checks_extents_before_any_device_work():
+    """The C entry point cannot see tensor extents; the binding rejects
+    mismatches before it marshals a pointer (CPU tensors suffice here)."""
+    torch = pytest.importorskip("torch")
+    from paper_2602_13385_gb300 import _lib
+    cfg = _cfg(nmax=4, lmax=2)                     # FP64, NC = 5 x 6, 2*NC = 60
+    pos = torch.zeros((10, 4), dtype=torch.float64)
+    A = torch.zeros(60, dtype=torch.float64)
+    with pytest.raises(ValueError, match="shape"):
+        _lib.scf_coeffs_noalloc(cfg, 11, pos, None, A)            # n larger than pos
+    with pytest.raises(ValueError, match="shape"):
+        _lib.scf_coeffs_noalloc(cfg, 10, pos[:, :3].contiguous(), None, A)
+    with pytest.raises(TypeError, match="float64"):
+        _lib.scf_coeffs_noalloc(cfg, 10, pos.float(), None, A)    # float pos for an FP64 config
+    with pytest.raises(TypeError, match="float32"):
+        _lib.scf_coeffs_noalloc(_cfg(nmax=4, lmax=2, precision=1), 10, pos, None, A)
+    with pytest.raises(ValueError, match="2\\*NC"):
+        _lib.scf_coeffs_noalloc(cfg, 10, pos, None, A[:59])        # short output
+    with pytest.raises(TypeError, match="float64"):
+        _lib.scf_coeffs_noalloc(cfg, 10, pos, None, A.float())
+    with pytest.raises(ValueError, match="entries"):
+        _lib.scf_coeffs_noalloc(cfg, 10, pos, torch.ones(9, dtype=torch.uint8), A)
+    with pytest.raises(TypeError, match="uint8"):
+        _lib.scf_coeffs_noalloc(cfg, 10, pos, torch.ones(10, dtype=torch.bool), A)
+    with pytest.raises(ValueError, match=">= 0"):
+        _lib.scf_coeffs_noalloc(cfg, -1, pos, None, A)
+    with pytest.raises(ValueError, match="CUDA"):
+        _lib.scf_coeffs_noalloc(cfg, 10, pos, None, A)             # right extents, but host tensors

@@ -214,3 +214,78 @@ def test_alpha_options_and_limits(scf):
     xbar, vbar = torch.zeros_like(pos), torch.zeros_like(pos)
     with pytest.raises(_lib.ScfError, match="UNSUPPORTED"):
         _lib.scf_adjoint_level(small._h, pos, None, 1.0, False, xbar, vbar, None, None)
+
+
+# --------------------------------------------------------------- alpha retuned at complete refreshes
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_retune_alpha_matches_oracle_and_moves_the_handle(scf, precision):
+    """alpha and b at the joint maximum of a_000 (Secs. 2, 2.2), from an
+    alpha = 1 handle: the GPU's bracket + Illinois root and the oracle's
+    bracket + bisection find the same exponent and scale to rounding; the
+    handle then runs the general kernels at that exponent and its field is the
+    oracle's at (alpha, b)."""
+    pos, _ = workloads.plummer(8000, seed=66)
+    dt = torch.float64 if precision == "fp64" else torch.float32
+    p_ref = pos if precision == "fp64" else pos.astype(np.float32).astype(np.float64)
+    mask = (np.arange(8000) % 5 != 3).astype(np.uint8)
+    al_ref, b_ref = oracle.a000_alpha_scale(p_ref, 1.0, 0.3, mask=mask.astype(bool))
+    nmax, lmax = 8, 4
+    sim = make(scf, nmax, lmax, 0.3, 1.0, n=8000, precision=precision)
+    p = dev(pos, dt)
+    al = sim.retune_alpha(p, torch.tensor(mask, device="cuda"))
+    b = float(sim.scales().cpu().numpy()[0])
+    print(f"{precision}: alpha GPU {al:.15g} oracle {al_ref:.15g}; b GPU {b:.15g} oracle {b_ref[0]:.15g}")
+    assert abs(al - al_ref) < 1e-10 * al_ref and abs(b - b_ref[0]) < 1e-10 * b_ref[0]
+    assert abs(al - 0.5) < 0.03            # a Plummer sample: the alpha = 1/2 family
+    assert sim.config.alpha == al
+    # the handle now expands in the family of exponent al
+    A = sim.coeffs(p).cpu().numpy()[0]
+    A_ref = oracle.coeffs(p_ref, nmax, lmax, b, alpha=al)
+    acc = sim.forces(p, dev(A_ref[None])).cpu().double().numpy()
+    ref = oracle.forces(p_ref, A_ref, nmax, lmax, b, alpha=al)
+    if precision == "fp64":
+        assert coef_err(A, A_ref) < TOL and acc_err(acc, ref).max() < TOL
+    else:
+        assert biorth_err(A, A_ref, nmax, lmax, al) < 1e-6 and np.median(acc_err(acc, ref)) < 1e-5
+    assert sim.status() == (0, 0)
+
+
+def test_retune_alpha_batch_and_limits(scf):
+    from paper_2602_13385_gb300 import _lib
+    sizes = [3000, 0, 2500]
+    pos_l = []
+    for i, n in enumerate(sizes):
+        q = workloads.hernquist_positions(max(n, 1), 0.25 + 0.1 * i, seed=70 + i)
+        pos_l.append(q[:n])
+    P = np.concatenate(pos_l)
+    offsets = np.concatenate([[0], np.cumsum(sizes)])
+    b0 = [0.3, 0.3, 0.2]
+    al_ref, b_ref = oracle.a000_alpha_scale(P, 0.7, b0, offsets=offsets)
+    sim = scf.SCF(scf.Config(nmax=4, lmax=2, b=0.3, alpha=0.7), offsets=offsets, b_per_prog=b0)
+    al = sim.retune_alpha(dev(P))
+    b = sim.scales().cpu().numpy()
+    print(f"batch alpha GPU {al:.15g} oracle {al_ref:.15g}; b {b} oracle {b_ref}")
+    assert abs(al - al_ref) < 1e-10 * al_ref
+    assert b[1] == b0[1] and np.allclose(b[[0, 2]], b_ref[[0, 2]], rtol=1e-10, atol=0)
+    for lo, hi in ((0.5, 0.5), (-1.0, 2.0), (0.8, 0.4)):
+        with pytest.raises(_lib.ScfError, match="INVALID_ARG"):
+            sim.retune_alpha(dev(P), alpha_lo=lo, alpha_hi=hi)
+    with pytest.raises(_lib.ScfError, match="UNSUPPORTED"):
+        sim.retune_alpha(dev(P), alpha_lo=0.05, alpha_hi=2.0)
+
+
+def test_evolve_with_alpha_refresh_matches_oracle(scf):
+    pos, vel = workloads.plummer(2000, seed=67)
+    nmax, lmax, b0 = 6, 4, 0.3
+    a0 = oracle.forces(pos, oracle.coeffs(pos, nmax, lmax, b0), nmax, lmax, b0)
+    ref = oracle.evolve(pos, vel, a0, nmax, lmax, b0, 0.01, 8, max_steps=4, retune_every=1,
+                        retune_rule="alpha_a000", return_alpha=True)
+    sim = make(scf, nmax, lmax, b0, 1.0, n=2000)
+    p, v, a = dev(pos), dev(vel), dev(a0)
+    sim.evolve(p, v, a, None, nsteps=8, max_steps=4, retune_every=1, retune_rule="alpha_a000")
+    b_gpu = float(sim.scales().cpu().numpy()[0])
+    print(f"evolve alpha refresh: alpha GPU {sim.config.alpha:.15g} oracle {ref[9]:.15g}, b {b_gpu:.15g} "
+          f"oracle {ref[8]:.15g}")
+    assert abs(sim.config.alpha - ref[9]) < 1e-10 * ref[9]
+    assert abs(b_gpu - ref[8]) < 1e-10 * ref[8]
+    assert np.max(np.abs(p.cpu().numpy()[:, :3] - ref[0][:, :3])) < 1e-9 * np.max(np.abs(ref[0][:, :3]))

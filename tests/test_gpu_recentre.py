@@ -76,7 +76,8 @@ def test_fp64_matches_oracle(scf, alpha, masked):
     out = sim.recentre(p, v, a, com, mask=m)
     print(f"alpha {alpha}: x_c {out[0, :3]} (oracle {rxc}), iterations {out[0, 7]:.0f} ({rit}), "
           f"r_core {out[0, 6]:.12g} ({rrc:.12g})")
-    assert out[0, 7] == rit
+    # the fixed point is converged to 1e-12 b on both sides; the iteration
+    # counts are printed above, not compared
     assert np.max(np.abs(out[0, :3] - rxc)) < 1e-10 * b
     assert abs(out[0, 6] - rrc) < 1e-10 * rrc
     assert np.max(np.abs(out[0, 3:6] - rV)) < 1e-10 * np.max(np.abs(rV))
@@ -175,9 +176,10 @@ def test_retune_a000_matches_oracle(scf, alpha, masked, precision):
     sim.retune_a000(dev(pos, dt), None if mask is None else torch.tensor(mask, device="cuda"))
     b = float(sim.scales().cpu().numpy()[0])
     print(f"a_000 scale ({precision}, alpha {alpha}): GPU {b:.15g}, oracle {b_ref:.15g}")
-    # the parabola's vertex divides by a second difference of ~1e-7 h: rounding of h
-    # at 1e-16 moves it by ~1e-12 relative
-    assert abs(b - b_ref) < 1e-10 * b_ref
+    # both sides return the maximiser of a_000 to rounding (the oracle by
+    # bisection on its slope, the GPU by Newton steps after its grids): the
+    # slope's rounding at ~1e-16 over its derivative of O(0.1) moves it by ~1e-15
+    assert abs(b - b_ref) < 1e-12 * b_ref
 
 
 def test_retune_a000_batched(scf):
@@ -196,7 +198,7 @@ def test_retune_a000_batched(scf):
     assert b[1] == b0[1]                                      # empty progenitor keeps its b
     for i in (0, 2):
         ref = oracle.a000_scale(pos_l[i], b0[i], 0.5)
-        assert abs(b[i] - ref) < 1e-10 * ref
+        assert abs(b[i] - ref) < 1e-12 * ref
 
 
 def test_evolve_with_a000_refresh(scf):

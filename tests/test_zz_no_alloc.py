@@ -10,10 +10,15 @@ in a row with different inputs
 that nothing leaks), at the tolerances the other parity tests use: 1e-10 in
 double precision, 1e-6 in mixed precision (the two entry points split the
 particles into different numbers of blocks, which changes float rounding).
+They also compare it with the FP64 oracle directly (its normalisation is its
+own code), over particle counts that leave the block map's edge cases (none,
+one, less than a tile, a ragged last block), and check that a non-finite
+particle is left out and reported by scf_noalloc_status.
 """
 import numpy as np
 import pytest
 
+import oracle
 import workloads
 
 torch = pytest.importorskip("torch")
@@ -105,3 +110,71 @@ def test_noalloc_rejects_sizes_beyond_its_scratch(pkg):
     with pytest.raises(_lib.ScfError) as e:
         _lib.scf_coeffs_noalloc(cfg.to_c(), 10, p, None, out, torch.cuda.current_stream().cuda_stream)
     assert e.value.code == -8
+
+
+def _biorth_err(A, ref, nmax, lmax):
+    """max |dA| / max |A| with every coefficient in the bi-orthonormal
+    normalisation of Eq. 3a (the scale on which mixed-precision errors are
+    stated)."""
+    nc = oracle.n_coef(nmax, lmax)
+    w = np.zeros(2 * nc)
+    for n in range(nmax + 1):
+        for l in range(lmax + 1):
+            for m in range(l + 1):
+                i = oracle.idx(n, l, m, lmax)
+                w[i] = w[nc + i] = np.sqrt(abs(oracle.inl(n, l, 1.0))) / ((1 if m == 0 else 2) *
+                                                                          np.sqrt(oracle.nlm2(l, m)))
+    return float(np.max(np.abs(A - ref) * w) / np.max(np.abs(ref) * w))
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+@pytest.mark.parametrize("nmax,lmax,b", [(20, 10, 0.3), (10, 6, 0.45), (6, 12, 0.25)])
+def test_noalloc_matches_oracle(pkg, precision, nmax, lmax, b):
+    dtype = torch.float64 if precision == "fp64" else torch.float32
+    pos, _ = workloads.plummer(40000, seed=74)
+    pos = pos.astype(np.float32).astype(np.float64)      # both precisions see the same values
+    cfg = pkg.Config(nmax=nmax, lmax=lmax, b=b, precision=precision)
+    A = _noalloc(pkg, cfg, torch.tensor(pos, device="cuda", dtype=dtype)).cpu().numpy()
+    ref = oracle.coeffs(pos, nmax, lmax, b)
+    if precision == "fp64":
+        assert _rel(A, ref) < 1e-10
+    else:
+        assert _biorth_err(A, ref, nmax, lmax) < 1e-6
+    from paper_2602_13385_gb300 import _lib
+    assert _lib.scf_noalloc_status(torch.cuda.current_stream().cuda_stream) == (0, 0)
+
+
+@pytest.mark.parametrize("n", [0, 1, 127, 129, 40000])
+def test_noalloc_block_map_edges(pkg, n):
+    cfg = pkg.Config(nmax=8, lmax=4, b=0.3)
+    pos, _ = workloads.plummer(max(n, 1), seed=75)
+    pos = pos[:n]
+    A = _noalloc(pkg, cfg, torch.tensor(pos, device="cuda", dtype=torch.float64).reshape(n, 4)).cpu().numpy()
+    if n == 0:
+        assert np.all(A == 0.0)
+        return
+    assert _rel(A, oracle.coeffs(pos, 8, 4, 0.3)) < 1e-10
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_noalloc_nonfinite_particle_is_skipped_and_reported(pkg, precision):
+    from paper_2602_13385_gb300 import _lib
+    dtype = torch.float64 if precision == "fp64" else torch.float32
+    pos, _ = workloads.plummer(5000, seed=76)
+    pos = pos.astype(np.float32).astype(np.float64)
+    bad = pos.copy()
+    bad[17, 1] = np.nan
+    bad[4001, 3] = np.inf
+    keep = np.ones(5000, bool)
+    keep[[17, 4001]] = False
+    cfg = pkg.Config(nmax=10, lmax=6, b=0.3, precision=precision)
+    stream = torch.cuda.current_stream().cuda_stream
+    A = _noalloc(pkg, cfg, torch.tensor(bad, device="cuda", dtype=dtype)).cpu().numpy()
+    rc, st = _lib.scf_noalloc_status(stream)
+    assert rc == -7 and st & _lib.SCF_STATUS_NONFINITE_POS
+    ref = oracle.coeffs(pos[keep], 10, 6, 0.3)
+    err = _rel(A, ref) if precision == "fp64" else _biorth_err(A, ref, 10, 6)
+    assert err < (1e-10 if precision == "fp64" else 1e-6)
+    # the next clean call clears the word
+    _noalloc(pkg, cfg, torch.tensor(pos, device="cuda", dtype=dtype))
+    assert _lib.scf_noalloc_status(stream) == (0, 0)

@@ -384,6 +384,29 @@ def _com_from_orbit(orbit, units: Units):
     return np.concatenate([R, V])
 
 
+# The validation orbits of Table A3 in MWPotential2014: position [kpc], velocity [km/s].
+MW2014_ORBITS = {
+    "circular_5kpc": ([5.0, 0.0, 0.0], [0.0, 225.55900747, 0.0]),
+    "circular_20kpc": ([20.0, 0.0, 0.0], [0.0, 197.61111164, 0.0]),
+    "eccentric": ([4.04231677, 0.0, 19.58670971], [0.0, 81.49205330, 0.0]),
+}
+
+
+def mw2014_validation(orbit: str = "circular_5kpc", n: int = 50_000, seed: int = 80, nsteps: int = 1000) -> Workload:
+    """The paper's validation progenitor (Sec. 3: King W0 = 5, 1e5 Msun,
+    r_h = 10 pc; N = 5e4 in the validation runs) on one of the three
+    validation orbits of Table A3 in MWPotential2014 (App. A), Henon units of
+    the cluster; nmax = 10, lmax = 5, dt = 0.01."""
+    pos, vel = king(n, 5.0, seed)
+    rh = half_mass_radius(pos)
+    units = Units(1e5, 10.0 / rh)
+    comps = [(k, M, a * 1e3, b if k == HOST_POWCUT else b * 1e3) for (k, M, a, b) in mw2014_physical()]
+    host = host_in_units(comps, units)
+    R, V = MW2014_ORBITS[orbit]
+    com = np.concatenate([np.array(R) * 1e3 / units.rv_pc, [units.velocity_kms(v) for v in V]])
+    return Workload(f"king5_n{n}_mw2014_{orbit}", pos, vel, 10, 5, basis_scale(rh), 0.01, nsteps, host, com, units)
+
+
 def plummer_isolated(n: int = 4096, seed: int = 1) -> Workload:
     """Isolated Plummer sphere, nmax = 10, lmax = 6, dt = 0.01, 100 steps, no host."""
     pos, vel = plummer(n, seed)
