@@ -232,7 +232,7 @@ K2Args k2_args(scf_handle* h, double* A_out, double* com, int mode) {
   a.dt = h->cfg.dt;
   a.com = com;
   a.host = h->host;
-  a.sub = h->k1.variant == 1 ? h->k1.sub * h->k1.win : 0;
+  a.sub = h->k1.variant == 1 ? h->k1.win : 0;  // register-tiled kernel 1: float rows, one per window
   // split each column group's rows over z blocks when the groups alone would
   // leave SMs idle (about four blocks per SM), at least 32 rows per chunk
   const int groups = scf_k2_groups(h->nc);
@@ -390,9 +390,9 @@ int k1_shape(const scf_config& cfg, int tp, bool ff, ScfLaunchInfo* info, int* b
 }
 
 // Partial rows in units of 2*NC doubles: one per block, or for the
-// register-tiled kernel sub * win float rows per block (two per double row).
+// register-tiled kernel win float rows per block (two per double row).
 size_t k1_rows(const ScfLaunchInfo& info, size_t blocks) {
-  return info.variant == 1 ? (blocks * info.sub * info.win + 1) / 2 : blocks;
+  return info.variant == 1 ? (blocks * info.win + 1) / 2 : blocks;
 }
 
 int64_t longest_block(const Map1& m) {

@@ -267,29 +267,36 @@ __host__ __device__ constexpr int chunk_base(int l) {  // chunks of the degrees 
   return k;
 }
 __host__ __device__ constexpr int y_row(int l, int mm) { return YCH * (chunk_base(l) + mm / TM) + mm % TM; }
+// Shared memory: [gen: the Gegenbauer steps gbeta[l][n] of the handle's radial
+// family] then the staging rows; at window ends the staging rows hold the
+// worker tiles (at most MAX_THREADS tiles of TN x TM floats) for the
+// cross-sub-group sums.
+constexpr size_t kRedFloats = (size_t)MAX_THREADS * TN * TM;
 inline size_t smem_bytes(int nmax, int lmax, bool gen = false) {
   const size_t rows = (size_t)(lmax + 1) * (nmax + 1) + (TN - 1) + (size_t)YCH * chunk_base(lmax + 1);
-  // gen: then the Gegenbauer steps gbeta[l][n] of the handle's radial family
-  return sizeof(float) * (TPP * rows + (gen ? (size_t)(lmax + 1) * (nmax + 1) : 0));
+  const size_t sg = gen ? (size_t)(lmax + 1) * (nmax + 1) : 0;
+  return sizeof(float) * (((sg + 3) & ~size_t(3)) + std::max(TPP * rows, kRedFloats));
 }
 
-// Stores a worker's register sums (times the constant gscale of the staged
-// C_n) into its window slot and clears them; zero = true stores zeros.  tab:
-// the tables of a radial family with alpha != 1 (null: the constant bank's).
-__device__ __forceinline__ void store_tile(float (&acc)[TN][TM], float* __restrict__ out, bool zero, int l, int n0,
-                                           int mm0, int nn, int nlm, int nc, const ScfConst* tab) {
-#pragma unroll
-  for (int j = 0; j < TM; ++j) {
-    const int mm = mm0 + j;
-    const int col = mm <= l ? scf_lm(l, mm) : nc + scf_lm(l, mm - l);
-    const bool jok = mm <= 2 * l;
-#pragma unroll
-    for (int i = 0; i < TN; ++i) {
-      if (jok && n0 + i < nn) {
-        const float gs = tab ? __ldg(&tab->gscalef[l][n0 + i]) : c_tab.gscalef[l][n0 + i];
-        out[(n0 + i) * nlm + col] = zero ? 0.f : acc[i][j] * gs;
-      }
-      acc[i][j] = 0.f;
+// At the end of a window: every worker has written its tile to red[(sgrp *
+// items + item) * TN * TM + i * TM + j]; the block adds the sub-groups' tiles
+// in sub-group order and writes the window's row (times the constant gscale of
+// the staged C_n) to dst: one float row of 2 NC per window and block, T_nl0
+// not written (kernel 2 reads it as 0).  tab: the tables of a radial family
+// with alpha != 1 (null: the constant bank's).
+__device__ __forceinline__ void store_window(const float* __restrict__ red, float* __restrict__ dst, int items, int sub,
+                                             const short (*item_lnm)[3], int nn, int nlm, int nc,
+                                             const ScfConst* tab) {
+  constexpr int E = TN * TM;
+  for (int e = threadIdx.x; e < items * E; e += blockDim.x) {
+    const int it = e / E, r = e - it * E, i = r / TM, j = r - i * TM;
+    const int l = item_lnm[it][0], n = item_lnm[it][1] + i, mm = item_lnm[it][2] + j;
+    if (n < nn && mm <= 2 * l) {
+      float v = 0.f;
+      for (int sg = 0; sg < sub; ++sg) v += red[(size_t)(sg * items + it) * E + r];
+      const float gs = tab ? __ldg(&tab->gscalef[l][n]) : c_tab.gscalef[l][n];
+      const int col = mm <= l ? scf_lm(l, mm) : nc + scf_lm(l, mm - l);
+      dst[n * nlm + col] = v * gs;
     }
   }
 }
@@ -470,18 +477,26 @@ struct BasisFixed {
 template <class B>  // basis policy: BasisGeneric<NCH> or BasisFixed<NN, L>
 __global__ void __maxnreg__(128) k1_tiled(K1Args a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ short item_lnm[MAX_THREADS][3];       // (l, n0, mm0) of every output tile
   const int NN = a.nmax + 1, L = a.lmax;
   const int rR = (L + 1) * NN;
-  float* Rs = reinterpret_cast<float*>(smem_raw);  // [rR + TN - 1][TPP]
+  const int sg_floats = B::kGen ? ((rR + 3) & ~3) : 0;
+  float* SG = reinterpret_cast<float*>(smem_raw);  // [L + 1][NN] Gegenbauer steps (radial family alpha != 1)
+  float* Rs = SG + sg_floats;                      // [rR + TN - 1][TPP]
   float* Ys = Rs + (rR + TN - 1) * TPP;            // [YCH * chunks][TPP]
+  float* red = Rs;                                 // window ends: the worker tiles
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  // padding rows and the angular rows past 2l of each degree's last chunk are never written by the basis
-  for (int i = tid; i < (TN - 1) * TPP; i += blockDim.x) Rs[rR * TPP + i] = 0.f;
-  for (int i = tid; i < YCH * chunk_base(L + 1) * TPP; i += blockDim.x) Ys[i] = 0.f;
-  float* SG = Ys + YCH * chunk_base(L + 1) * TPP;  // [L + 1][NN] Gegenbauer steps (radial family alpha != 1)
+  // padding rows and the angular rows past 2l of each degree's last chunk are
+  // never written by the basis; they feed only accumulators that are never
+  // stored, and are cleared once so that they hold no stale values
+  {
+    const int ny4 = YCH * chunk_base(L + 1) * (TPP / 4);
+    const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
+    for (int i = tid; i < (TN - 1) * (TPP / 4); i += blockDim.x) reinterpret_cast<float4*>(Rs + rR * TPP)[i] = z4;
+    for (int i = tid; i < ny4; i += blockDim.x) reinterpret_cast<float4*>(Ys)[i] = z4;
+  }
   if constexpr (B::kGen)
     for (int i = tid; i < rR; i += blockDim.x) SG[i] = a.tab->gbetaf[i / NN][i % NN];
-  __syncthreads();
 
   // contraction role: item (l, c, d) = output tile, sgrp = particle sub-group
   const bool worker = tid < a.items * a.sub;
@@ -502,6 +517,12 @@ __global__ void __maxnreg__(128) k1_tiled(K1Args a) {
     }
   }
   const int n0 = ic * TN, mm0 = id * TM;
+  if (worker && sgrp == 0) {
+    item_lnm[item][0] = (short)il;
+    item_lnm[item][1] = (short)n0;
+    item_lnm[item][2] = (short)mm0;
+  }
+  __syncthreads();
   const float* Rrow = Rs + (il * NN + n0) * TPP;
   const float* Yrow = Ys + y_row(il, mm0) * TPP;
   float acc[TN][TM];
@@ -509,8 +530,9 @@ __global__ void __maxnreg__(128) k1_tiled(K1Args a) {
   for (int i = 0; i < TN; ++i)
 #pragma unroll
     for (int j = 0; j < TM; ++j) acc[i][j] = 0.f;
-  // window slots of this worker: rows (block, sub-group, window) of 2 NC floats
-  float* out = reinterpret_cast<float*>(a.partials) + ((size_t)blockIdx.x * a.sub + sgrp) * a.win * 2 * a.nc;
+  // window rows of this block: [window][2 NC] floats
+  float* out = reinterpret_cast<float*>(a.partials) + (size_t)blockIdx.x * a.win * 2 * a.nc;
+  const ScfConst* tabp = B::kGen ? a.tab : nullptr;
   int win = 0;
 
   const int prog = a.blk_prog[blockIdx.x];
@@ -552,12 +574,15 @@ __global__ void __maxnreg__(128) k1_tiled(K1Args a) {
           atomicOr(a.status, 1u);
         }
       }
-      const float r = sqrtf(x * x + y * y + z * z);
-      const float rinv = r > 0.f ? 1.f / r : 0.f;
+      // the hardware reciprocal square root and reciprocal (a few ulp, no
+      // slow-path branches; every thread of the particle's four repeats this)
+      const float r2 = x * x + y * y + z * z;
+      const float rinv = r2 > 0.f ? rsqrtf(r2) : 0.f;
+      const float r = r2 * rinv;
       const float u = x * rinv, v = y * rinv, c = z * rinv;
       const float s = r * binv;
       // alpha != 1: t = s^(1/alpha) in q and xi, q^alpha in the prefactor
-      const float qq = 1.f / (1.f + (B::kGen ? powf(s, (float)a.inv_alpha) : s));
+      const float qq = __fdividef(1.f, 1.f + (B::kGen ? powf(s, (float)a.inv_alpha) : s));
       const float xi = 1.f - 2.f * qq;
       const float qv = B::kGen ? powf(qq, (float)a.alpha) : qq;
       const float sq2 = s * qv * qv;
@@ -590,17 +615,31 @@ __global__ void __maxnreg__(128) k1_tiled(K1Args a) {
           }
         }
       }
-      if (++tiles == a.win_tiles || last) {
-        store_tile(acc, out + (size_t)win * 2 * a.nc, false, il, n0, mm0, NN, a.nlm, a.nc, B::kGen ? a.tab : nullptr);
-        ++win;
-        tiles = 0;
-      }
     }
     __syncthreads();
+    if (++tiles == a.win_tiles || last) {  // the same on every thread of the block
+      // end of a window: the worker tiles through shared memory, one row per window
+      if (worker) {
+        float* mine = red + (size_t)(sgrp * a.items + item) * (TN * TM);
+#pragma unroll
+        for (int i = 0; i < TN; ++i)
+#pragma unroll
+          for (int j = 0; j < TM; j += 4) {
+            *reinterpret_cast<float4*>(mine + i * TM + j) =
+                make_float4(acc[i][j], acc[i][j + 1], acc[i][j + 2], acc[i][j + 3]);
+            acc[i][j] = acc[i][j + 1] = acc[i][j + 2] = acc[i][j + 3] = 0.f;
+          }
+      }
+      __syncthreads();
+      store_window(red, out + (size_t)win * 2 * a.nc, a.items, a.sub, item_lnm, NN, a.nlm, a.nc, tabp);
+      __syncthreads();  // the staging rows are the next tile's
+      ++win;
+      tiles = 0;
+    }
   }
-  if (worker)  // windows this block did not fill (fewer tiles than the longest block)
-    for (; win < a.win; ++win)
-      store_tile(acc, out + (size_t)win * 2 * a.nc, true, il, n0, mm0, NN, a.nlm, a.nc, B::kGen ? a.tab : nullptr);
+  // windows this block did not fill (fewer tiles than the longest block)
+  for (; win < a.win; ++win)
+    for (int i = tid; i < 2 * a.nc; i += blockDim.x) out[(size_t)win * 2 * a.nc + i] = 0.f;
 }
 
 template <class B>

@@ -79,10 +79,21 @@ __global__ void __launch_bounds__(K3_TB) k3_forces(K3Args a) {
   constexpr bool kF2 = sizeof(T) == 4;
   V4* F = reinterpret_cast<V4*>(smem_raw);
   V2* F2 = reinterpret_cast<V2*>(smem_raw);
+  // single precision: the per-(l, n) recurrence constants (gbeta, hbeta,
+  // hratio) staged beside the coefficients, one broadcast shared load per
+  // radial step instead of three constant-bank loads with runtime indices
+  float4* CS = reinterpret_cast<float4*>(smem_raw + ((sizeof(V2) * (size_t)a.nc + 15) & ~size_t(15)));
   __shared__ double s_R[3], s_aR[3];
   const int tid = threadIdx.x;
   const int prog = a.blk_prog[blockIdx.x];
   const double b = a.b_prog[prog];
+  if constexpr (kF2) {
+    const int nn = a.nmax + 1;
+    for (int i = tid; i < (a.lmax + 1) * nn; i += K3_TB) {
+      const int l = i / nn, n = i - l * nn;
+      CS[i] = make_float4(k3_gbeta<float, GEN>(a, l, n), k3_hbeta<float, GEN>(a, l, n), k3_hratio<GEN>(a, l, n), 0.f);
+    }
+  }
   {
     const V2* Fg = reinterpret_cast<const V2*>(a.F) + (size_t)prog * a.nc;
     const V2* Sg = reinterpret_cast<const V2*>(a.kscale);
@@ -205,11 +216,23 @@ __global__ void __launch_bounds__(K3_TB) k3_forces(K3Args a) {
       // runs the radial loop unrolled by two (measured 3% faster there); every
       // other instantiation keeps the compiler's choice (unrolling measured
       // slower at lmax 8 and for alpha != 1).
+      const float4* CSl = CS + l * NN;
       auto radial_step = [&](int n) {
-        const T cn = xi * c0 - k3_gbeta<T, GEN>(a, l, n) * cm1;
+        T gbn, hbn;
+        float hrn = 0.f;
+        if constexpr (kF2) {
+          const float4 cst = CSl[n];
+          gbn = cst.x;
+          hbn = cst.y;
+          hrn = cst.z;
+        } else {
+          gbn = k3_gbeta<T, GEN>(a, l, n);
+          hbn = k3_hbeta<T, GEN>(a, l, n);
+        }
+        const T cn = xi * c0 - gbn * cm1;
         const int o = n * a.nlm + lm0;
         if constexpr (kF2) {
-          const T dd = d0 * k3_hratio<GEN>(a, l, n);
+          const T dd = d0 * hrn;
 #pragma unroll
           for (int m = 0; m <= l; ++m) {
             const V2 fv = F2[o + m];
@@ -228,7 +251,7 @@ __global__ void __launch_bounds__(K3_TB) k3_forces(K3Args a) {
             Z1s[m] += fv.w * d0;
           }
         }
-        const T dn = xi * d0 - k3_hbeta<T, GEN>(a, l, n) * dm1;
+        const T dn = xi * d0 - hbn * dm1;
         cm1 = c0;
         c0 = cn;
         dm1 = d0;
@@ -246,23 +269,36 @@ __global__ void __launch_bounds__(K3_TB) k3_forces(K3Args a) {
     const T k1 = (l >= 1) ? binv * sl1q : (T)0;                                  // G/r per Z0
     const T k2a = binv * ((l >= 1 ? (T)l * sl1q : (T)0) - (T)(2 * l + 1) * slq * w);  // G' per Z0
     const T k2b = binv * al4 * slq * q * w;                                       // G' per Z1
+    // The radial factors of degree l (slq, k1, k2a, k2b) multiply whole sums
+    // over m, so the sums over m are formed first:
+    //   Q0 = Z0c W_c + Z0s W_s, Q1 = Z1c W_c + Z1s W_s (W = W_m), and
+    //   psi += slq sum Pl Q0,  A_n += k2a sum Pl Q0 + k2b sum Pl Q1 - k1 sum (c Pd + m Pl) Q0,
+    //   A_z += k1 sum Pd Q0,  A_x += k1 sum m Pl (Z0c W_c,m-1 + Z0s W_s,m-1),
+    //   A_y -= k1 sum m Pl (Z0c W_s,m-1 - Z0s W_c,m-1).
+    T sP0 = 0, sP1 = 0, sE = 0, sZ = 0, sX = 0, sY = 0;
 #pragma unroll
     for (int m = 0; m <= l; ++m) {
-      const T g0c = slq * Z0c[m], g0s = slq * Z0s[m];
-      const T g1c = k1 * Z0c[m], g1s = k1 * Z0s[m];
-      const T g2c = k2a * Z0c[m] + k2b * Z1c[m], g2s = k2a * Z0s[m] + k2b * Z1s[m];
-      const T E = g1c * Wc[m] + g1s * Ws[m];
-      const T D = g2c * Wc[m] + g2s * Ws[m];
+      const T Q0 = Z0c[m] * Wc[m] + Z0s[m] * Ws[m];
+      const T Q1 = Z1c[m] * Wc[m] + Z1s[m] * Ws[m];
       const T Pl = P[m];
       const T Pd = (m < l) ? -tlk<T>(scf_lm(l, m)) * P[m + 1] : (T)0;
-      pot += Pl * (g0c * Wc[m] + g0s * Ws[m]);
-      An += Pl * D - (c * Pd + (T)m * Pl) * E;
-      Az += Pd * E;
+      sP0 += Pl * Q0;
+      sP1 += Pl * Q1;
+      sZ += Pd * Q0;
       if (m >= 1) {
-        Ax += (T)m * Pl * (g1c * Wc[m - 1] + g1s * Ws[m - 1]);
-        Ay -= (T)m * Pl * (g1c * Ws[m - 1] - g1s * Wc[m - 1]);
+        const T mPl = (T)m * Pl;
+        sE += (c * Pd + mPl) * Q0;
+        sX += mPl * (Z0c[m] * Wc[m - 1] + Z0s[m] * Ws[m - 1]);
+        sY += mPl * (Z0c[m] * Ws[m - 1] - Z0s[m] * Wc[m - 1]);
+      } else {
+        sE += c * Pd * Q0;
       }
     }
+    pot += slq * sP0;
+    An += k2a * sP0 + k2b * sP1 - k1 * sE;
+    Az += k1 * sZ;
+    Ax += k1 * sX;
+    Ay -= k1 * sY;
     }  // degree owned by this half
     slq *= sq2;
     if (l >= 1) sl1q *= sq2;
@@ -402,8 +438,11 @@ cudaError_t prepare_t(int lmax, int nmax, int tb, ScfLaunchInfo* info, int* bloc
     info->threads = tb;
     info->tile = sizeof(T) == 8 ? tb / 2 : tb;  // double: two warps share a particle (split degrees)
     info->variant = GEN ? 3 : 0;
-    // scaled (cosine, sine) per coefficient; double also the alpha + 1 family's
-    info->smem = sizeof(T) * (sizeof(T) == 4 ? 2 : 4) * (size_t)nc;
+    // scaled (cosine, sine) per coefficient; double also the alpha + 1 family's;
+    // single also the per-(l, n) recurrence constants (a float4 each)
+    info->smem = sizeof(T) == 4 ? ((sizeof(float) * 2 * (size_t)nc + 15) & ~size_t(15)) +
+                                      sizeof(float4) * (size_t)(lmax + 1) * (nmax + 1)
+                                : sizeof(T) * 4 * (size_t)nc;
     cudaError_t e = cudaFuncSetAttribute(KK::fn(), cudaFuncAttributeMaxDynamicSharedMemorySize, (int)info->smem);
     if (e != cudaSuccess) return e;
     return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, KK::fn(), info->threads, info->smem);

@@ -78,7 +78,8 @@ struct K2Args {
   double G;
   double* aR_out;           // [n_prog][4], or null
   // partials layout: sub == 0: [blocks][2*NC] doubles; sub > 0: [blocks][sub][2*NC]
-  // floats without the T_nl0 entries (read as 0)
+  // floats (sub rows per block, one per window of the register-tiled kernel 1)
+  // without the T_nl0 entries (read as 0)
   int sub;
   // optional second level: z > 1 blocks per column group each add a chunk of
   // the rows into zpart ([n_prog][z][2*NC] doubles); the last to finish (per

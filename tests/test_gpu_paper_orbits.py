@@ -9,7 +9,8 @@ batched GPU workload (`workloads.paper_orbits`).
   shares (max_steps below every dt_int), one batched scf_evolve of the ten
   clusters gives each cluster's state as the ten single-cluster runs do.
 * 400 Myr of the ten streams in both precisions (same schedule, same
-  centres, unbound counts within 5%).
+  centres, unbound counts within 5%, the Sec. 3.3 statistics of the tails
+  that hold 300 stars within sampling noise per bin).
 """
 import os
 
@@ -124,7 +125,12 @@ def test_paper_orbit_streams_mixed_against_fp64(scf):
     and centres and unbind the same numbers of stars within 5% (+10): the
     marginal stars differ once the trajectories separate.  The per-orbit
     counts and, where a tail holds 300 stars, the Sec. 3.3 statistics on
-    bins of >= 150 are printed."""
+    bins of >= 150 are printed and compared within sampling noise: per bin of
+    n stars, density and track (in widths) within 4 sqrt(2/n), width and
+    sigma within 4/sqrt(n) (the two runs' escapers are, after chaos has
+    separated the trajectories, two samples of the same stream; the 1%
+    per-bin bound of the stream-forming workload would need bins of ~1e5
+    stars, i.e. tails that only relaxation-driven mass loss over Gyr builds)."""
     from paper_2602_13385_gb300 import streams
     wl = workloads.paper_orbits(n_per=20_000, nsteps=20_000)
     out = {}
@@ -156,4 +162,11 @@ def test_paper_orbit_streams_mixed_against_fp64(scf):
             st_m = streams.stream_stats(X[1], V[1], m[2][i, :3], m[2][i, 3:], m[3][s], edges=edges)
             d, _ = streams.compare(st_f, st_m)
             line += f", {len(edges) - 1} bins, differences " + ", ".join(f"{k} {val:.1e}" for k, val in d.items())
+            occ = st_f["n"] > 0
+            n = st_f["n"][occ]
+            noise2, noise1 = 4.0 * np.sqrt(2.0 / n), 4.0 / np.sqrt(n)
+            assert np.all(np.abs(st_m["rho"][occ] - st_f["rho"][occ]) <= noise2 * st_f["rho"][occ]), line
+            assert np.all(np.abs(st_m["track"][occ] - st_f["track"][occ]) <= noise2 * st_f["width"][occ]), line
+            assert np.all(np.abs(st_m["width"][occ] - st_f["width"][occ]) <= noise1 * st_f["width"][occ]), line
+            assert np.all(np.abs(st_m["sigma"][occ] - st_f["sigma"][occ]) <= noise1 * st_f["sigma"][occ]), line
         print(line)
