@@ -215,7 +215,8 @@ int scf_step_host(scf_handle* h, void* pos, void* vel, void* acc, double* com, v
  *   SCF_OPT_K1_TILE   particles per tile (= threads per block) of the
  *                     coefficient kernel: 64, 128 (default) or 256.
  *   SCF_OPT_K3_BLOCK  threads per block of the field kernel: 64, 128
- *                     (default) or 256.
+ *                     (default), 256, or (SCF_MIXED only, else
+ *                     SCF_ERR_UNSUPPORTED) 320.
  *   SCF_OPT_K1_VARIANT 0 = the coefficient kernel with one thread per output
  *                     and SCF_OPT_K1_TILE particles per tile (the double-
  *                     precision default); 1 = the register-tiled kernel
@@ -235,6 +236,13 @@ int scf_step_host(scf_handle* h, void* pos, void* vel, void* acc, double* com, v
  *                     SCF_OPT_K3_BLOCK values return SCF_ERR_UNSUPPORTED
  *                     while it is selected).  The adjoint always uses the
  *                     double kernel.  The autotuner keeps the variant.
+ *   SCF_OPT_CENTRE_AHEAD 1 (default) = scf_step computes the next step's
+ *                     centre kick-drift-kick (Sec. 2.1, the orbit of R) on a
+ *                     second stream beside kernel 3, and kernel 2 of the next
+ *                     step takes it when the state it steps is bitwise the
+ *                     one that was stepped ahead (same dt); 0 = kernel 2
+ *                     always computes it.  Either way the results are
+ *                     bitwise the same.
  * Setting a tile or block size synchronises the stream and rewrites the block
  * maps in the workspace (sized in scf_init for every allowed value).
  * Errors: SCF_ERR_NULL_POINTER, SCF_ERR_INVALID_ARG (unknown option or value),
@@ -244,6 +252,7 @@ int scf_step_host(scf_handle* h, void* pos, void* vel, void* acc, double* com, v
 #define SCF_OPT_K3_BLOCK 3
 #define SCF_OPT_K1_VARIANT 4
 #define SCF_OPT_K3_VARIANT 5
+#define SCF_OPT_CENTRE_AHEAD 6
 int scf_set_option(scf_handle* h, int option, int value);
 int scf_get_option(const scf_handle* h, int option, int* value);
 
@@ -252,9 +261,10 @@ int scf_get_option(const scf_handle* h, int option, int* value);
  * each, CUDA events on the handle's stream) on the caller's particles, and
  * keeps the fastest of each (in SCF_MIXED the register-tiled kernel 1 is a
  * fourth candidate).  pos, com as for scf_forces; acc is overwritten.
- * ms_out (host, nullable) receives 7 average times in milliseconds
+ * ms_out (host, nullable) receives 8 average times in milliseconds
  * (tiles 64, 128, 256 of kernel 1, then blocks 64, 128, 256 of kernel 3, then
- * the register-tiled kernel 1; 0 for a shape that does not fit or apply).  Synchronises the stream; creates CUDA events.
+ * the register-tiled kernel 1, then blocks of 320 of kernel 3; 0 for a shape
+ * that does not fit or apply).  Synchronises the stream; creates CUDA events.
  * Errors: SCF_ERR_NULL_POINTER, SCF_ERR_MISALIGNED, SCF_ERR_INVALID_ARG
  * (reps < 1), SCF_ERR_CUDA. */
 int scf_autotune(scf_handle* h, const void* pos, const double* com, void* acc, int reps, double* ms_out);

@@ -48,6 +48,7 @@ SCF_OPT_K1_TILE = 2
 SCF_OPT_K3_BLOCK = 3
 SCF_OPT_K1_VARIANT = 4
 SCF_OPT_K3_VARIANT = 5
+SCF_OPT_CENTRE_AHEAD = 6
 
 
 class ScfError(RuntimeError):
@@ -302,11 +303,12 @@ def scf_get_option(h, option: int) -> int:
 
 
 def scf_autotune(h, pos, com, acc, reps: int = 5):
-    """Times the allowed kernel shapes and keeps the fastest; returns the seven
+    """Times the allowed kernel shapes and keeps the fastest; returns the eight
     average times (ms): kernel-1 tiles 64/128/256, kernel-3 blocks 64/128/256,
-    then the register-tiled kernel 1 (0 where a shape does not apply)."""
+    the register-tiled kernel 1, kernel-3 blocks of 320 (0 where a shape does
+    not apply)."""
     import torch
-    ms = (ctypes.c_double * 7)()
+    ms = (ctypes.c_double * 8)()
     _check(load().scf_autotune(h, _ptr(pos), _ptr(com, torch.float64), _ptr(acc), int(reps), ms), "scf_autotune")
     return list(ms)
 

@@ -90,6 +90,12 @@ struct scf_handle {
   // scf_step_host: copy stream and events, created by its first call
   cudaStream_t copy_stream = nullptr;
   std::vector<cudaEvent_t> stage_ev;
+  // the centre's next kick-drift-kick computed beside kernel 3 (SCF_OPT_CENTRE_AHEAD)
+  bool centre_ahead = true;
+  double* d_cnext = nullptr;             // [n_prog][kCentreW], keys NaN until computed
+  cudaStream_t side_stream = nullptr;                 // created at the greatest stream priority
+  int side_priority = 0;
+  cudaEvent_t side_ev[2] = {nullptr, nullptr};
 };
 
 namespace {
@@ -243,6 +249,7 @@ K2Args k2_args(scf_handle* h, double* A_out, double* com, int mode) {
   a.z = z;
   a.zpart = h->d_k2z;
   a.counters = h->d_k2cnt;
+  a.cnext = mode == SCF_MODE_STEP && h->centre_ahead ? h->d_cnext : nullptr;
   return a;
 }
 
@@ -455,8 +462,6 @@ int use_k3(scf_handle* h, int tb) {
   return SCF_OK;
 }
 
-const int kTiles[3] = {64, 128, 256};
-
 }  // namespace
 
 extern "C" {
@@ -573,6 +578,7 @@ int scf_init(const scf_config* cfg, int n_prog, const int64_t* offsets, const do
   const size_t o_alpha = take(sizeof(double) * 4 * (size_t)n_prog);
   const size_t o_rc = take(sizeof(double) * 16 * (size_t)n_prog);
   const size_t o_sp = take(sizeof(double) * (kScalePoints + 1) * nb3);
+  const size_t o_cn = take(sizeof(double) * kCentreW * (size_t)n_prog);
   if (cudaMalloc(&h->d_base, off) != cudaSuccess) {
     cudaGetLastError();
     return fail(SCF_ERR_OUT_OF_MEMORY);
@@ -604,6 +610,7 @@ int scf_init(const scf_config* cfg, int n_prog, const int64_t* offsets, const do
   h->d_k2cnt = reinterpret_cast<unsigned*>(base + o_k2c);
   h->d_rc = reinterpret_cast<double*>(base + o_rc);
   h->d_sp = reinterpret_cast<double*>(base + o_sp);
+  h->d_cnext = reinterpret_cast<double*>(base + o_cn);
 
   h->d_tab = reinterpret_cast<ScfConst*>(base + o_tab);
   h->d_alpha = reinterpret_cast<double*>(base + o_alpha);
@@ -627,6 +634,7 @@ int scf_init(const scf_config* cfg, int n_prog, const int64_t* offsets, const do
             put(h->d_off, h->offsets.data(), sizeof(int64_t) * (n_prog + 1)) &&
             cudaMemset(h->d_k2cnt, 0, sizeof(unsigned) * (size_t)scf_k2_groups(h->nc) * n_prog) == cudaSuccess &&
             cudaMemset(h->d_status, 0, sizeof(unsigned) * 4) == cudaSuccess &&
+            cudaMemset(h->d_cnext, 0xff, sizeof(double) * kCentreW * (size_t)n_prog) == cudaSuccess &&  // NaN keys
             cudaMemset(h->d_A, 0, sizeof(double) * 2 * (size_t)h->nc * n_prog) == cudaSuccess;
   if (!ok) return fail(SCF_ERR_CUDA);
   // default shapes: the register-tiled kernel 1 in mixed precision (128-particle
@@ -661,7 +669,38 @@ namespace {
 int launch_step(scf_handle* h, void* pos, void* vel, void* acc, double* com) {
   int rc = run_coeffs(h, pos, vel, acc, h->step_mask, h->d_A, com, SCF_MODE_STEP);
   if (rc != SCF_OK) return rc;
-  return run_forces(h, pos, vel, acc, com, SCF_MODE_STEP);
+  // the next step's centre kick-drift-kick, on a second stream beside kernel 3
+  // (its FP64 dependency chain then leaves kernel 2's critical path); joined
+  // back before the step ends
+  const bool ahead = h->centre_ahead && h->host.n > 0 && com != nullptr;
+  if (ahead) {
+    if (!h->side_stream) {
+      int least = 0, greatest = 0;
+      if (cudaDeviceGetStreamPriorityRange(&least, &greatest) != cudaSuccess) return SCF_ERR_CUDA;
+      h->side_priority = greatest;
+      if (cudaStreamCreateWithPriority(&h->side_stream, cudaStreamNonBlocking, greatest) != cudaSuccess) {
+        h->side_stream = nullptr;
+        return SCF_ERR_CUDA;
+      }
+      for (cudaEvent_t& e : h->side_ev)
+        if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) return SCF_ERR_CUDA;
+    }
+    CentreArgs c{};
+    c.com = com;
+    c.aR = h->d_aR;
+    c.cnext = h->d_cnext;
+    c.dt = h->cfg.dt;
+    c.n_prog = h->n_prog;
+    c.host = h->host;
+    if (cudaEventRecord(h->side_ev[0], h->stream) != cudaSuccess ||
+        cudaStreamWaitEvent(h->side_stream, h->side_ev[0], 0) != cudaSuccess ||
+        scf_centre_next_launch(c, h->side_priority, h->side_stream) != cudaSuccess ||
+        cudaEventRecord(h->side_ev[1], h->side_stream) != cudaSuccess)
+      return SCF_ERR_CUDA;
+  }
+  rc = run_forces(h, pos, vel, acc, com, SCF_MODE_STEP);
+  if (ahead && cudaStreamWaitEvent(h->stream, h->side_ev[1], 0) != cudaSuccess) return SCF_ERR_CUDA;
+  return rc;
 }
 
 // Captures one step on the handle's stream into an executable graph.  Returns
@@ -678,7 +717,7 @@ bool capture_step(scf_handle* h, void* pos, void* vel, void* acc, double* com) {
   cudaGraph_t g = nullptr;
   const cudaError_t e = cudaStreamEndCapture(h->stream, &g);
   bool ok = rc == SCF_OK && e == cudaSuccess && g != nullptr &&
-            cudaGraphInstantiate(&h->step_exec, g, 0) == cudaSuccess;
+            cudaGraphInstantiate(&h->step_exec, g, cudaGraphInstantiateFlagUseNodePriority) == cudaSuccess;
   if (g) cudaGraphDestroy(g);
   if (!ok) {
     cudaGetLastError();
@@ -827,8 +866,16 @@ int scf_set_option(scf_handle* h, int option, int value) {
     if (!h->graphs) drop_graph(h);
     return SCF_OK;
   }
+  if (option == SCF_OPT_CENTRE_AHEAD) {
+    if (value != 0 && value != 1) return SCF_ERR_INVALID_ARG;
+    if (cudaStreamSynchronize(h->stream) != cudaSuccess) return SCF_ERR_CUDA;
+    h->centre_ahead = value == 1;
+    drop_graph(h);
+    return SCF_OK;
+  }
   if (option == SCF_OPT_K1_TILE || option == SCF_OPT_K3_BLOCK) {
-    if (value != 64 && value != 128 && value != 256) return SCF_ERR_INVALID_ARG;
+    if (value != 64 && value != 128 && value != 256 && !(option == SCF_OPT_K3_BLOCK && value == 320))
+      return SCF_ERR_INVALID_ARG;
     if (cudaStreamSynchronize(h->stream) != cudaSuccess) return SCF_ERR_CUDA;
     return option == SCF_OPT_K1_TILE ? use_k1(h, value) : use_k3(h, value);
   }
@@ -862,6 +909,7 @@ int scf_get_option(const scf_handle* h, int option, int* value) {
   else if (option == SCF_OPT_K1_VARIANT) *value = h->k1.variant;
   else if (option == SCF_OPT_K3_BLOCK) *value = h->k3.threads;
   else if (option == SCF_OPT_K3_VARIANT) *value = h->k3_ff ? 1 : 0;
+  else if (option == SCF_OPT_CENTRE_AHEAD) *value = h->centre_ahead ? 1 : 0;
   else return SCF_ERR_INVALID_ARG;
   return SCF_OK;
 }
@@ -895,7 +943,7 @@ int scf_autotune(scf_handle* h, const void* pos, const double* com, void* acc, i
   double best1 = 1e30, best3 = 1e30;
   int tp_best = h->k1.variant == 1 ? 0 : h->k1.tile, tb_best = h->k3.threads;
   if (ms_out)
-    for (int i = 0; i < 7; ++i) ms_out[i] = 0.0;
+    for (int i = 0; i < 8; ++i) ms_out[i] = 0.0;
   const int k1_candidates[4] = {64, 128, 256, 0};
   const int k1_slot[4] = {0, 1, 2, 6};
   for (int i = 0; i < 4 && rc == SCF_OK; ++i) {
@@ -911,14 +959,16 @@ int scf_autotune(scf_handle* h, const void* pos, const double* com, void* acc, i
   if (rc == SCF_OK) rc = use_k1(h, tp_best);
   if (rc == SCF_OK) rc = run_coeffs(h, p, nullptr, nullptr, nullptr, h->d_A, nullptr, SCF_MODE_COEFFS);
   if (rc == SCF_OK) rc = run_prep(h, h->d_A, com);
-  for (int i = 0; i < 3 && rc == SCF_OK; ++i) {
-    if (use_k3(h, kTiles[i]) != SCF_OK) continue;
+  const int k3_candidates[4] = {64, 128, 256, 320};
+  const int k3_slot[4] = {3, 4, 5, 7};
+  for (int i = 0; i < 4 && rc == SCF_OK; ++i) {
+    if (use_k3(h, k3_candidates[i]) != SCF_OK) continue;
     double ms = 0.0;
     rc = time_it([&] { return run_forces(h, pos, nullptr, acc, com, SCF_MODE_COEFFS); }, &ms);
-    if (ms_out) ms_out[3 + i] = ms;
+    if (ms_out) ms_out[k3_slot[i]] = ms;
     if (rc == SCF_OK && ms < best3) {
       best3 = ms;
-      tb_best = kTiles[i];
+      tb_best = k3_candidates[i];
     }
   }
   if (rc == SCF_OK) rc = use_k3(h, tb_best);
@@ -1514,6 +1564,10 @@ int scf_free(scf_handle* h) {
   if (h->copy_stream && cudaStreamSynchronize(h->copy_stream) != cudaSuccess) rc = SCF_ERR_CUDA;
   for (cudaEvent_t e : h->stage_ev) cudaEventDestroy(e);
   if (h->copy_stream) cudaStreamDestroy(h->copy_stream);
+  if (h->side_stream && cudaStreamSynchronize(h->side_stream) != cudaSuccess) rc = SCF_ERR_CUDA;
+  for (cudaEvent_t e : h->side_ev)
+    if (e) cudaEventDestroy(e);
+  if (h->side_stream) cudaStreamDestroy(h->side_stream);
   if (h->d_base && cudaFree(h->d_base) != cudaSuccess) rc = SCF_ERR_CUDA;
   delete h;
   return rc;

@@ -699,13 +699,14 @@ __device__ void host_accel_warp(const ScfHostParams& hp, double x, double y, dou
 }
 
 // Kick-drift-kick of the centre (R, V) in the host field by one warp (every
-// lane holds the same state); returns a_host at the new R in a_new.
-__device__ void com_kdk(const ScfHostParams& hp, double* c, double dt, double* a_new) {
+// lane holds the same state), given a0 = a_host(R); returns a_host at the new
+// R in a_new.
+__device__ __forceinline__ void com_kdk_from(const ScfHostParams& hp, double* c, double dt, const double* a0,
+                                             double* a_new) {
   double ax, ay, az;
-  host_accel_warp(hp, c[0], c[1], c[2], ax, ay, az);
-  c[3] += 0.5 * dt * ax;
-  c[4] += 0.5 * dt * ay;
-  c[5] += 0.5 * dt * az;
+  c[3] += 0.5 * dt * a0[0];
+  c[4] += 0.5 * dt * a0[1];
+  c[5] += 0.5 * dt * a0[2];
   c[0] += dt * c[3];
   c[1] += dt * c[4];
   c[2] += dt * c[5];
@@ -716,6 +717,34 @@ __device__ void com_kdk(const ScfHostParams& hp, double* c, double dt, double* a
   a_new[0] = ax;
   a_new[1] = ay;
   a_new[2] = az;
+}
+
+__device__ void com_kdk(const ScfHostParams& hp, double* c, double dt, double* a_new) {
+  double a0[3];
+  host_accel_warp(hp, c[0], c[1], c[2], a0[0], a0[1], a0[2]);
+  com_kdk_from(hp, c, dt, a0, a_new);
+}
+
+__device__ __forceinline__ bool same_bits(double x, double y) {
+  return __double_as_longlong(x) == __double_as_longlong(y);
+}
+
+// The next step's centre kick-drift-kick, one warp per progenitor, from the
+// state and a_host(R) that kernel 2 of this step left (see CentreArgs).
+__global__ void __launch_bounds__(32) k_centre_next(CentreArgs a) {
+  const int p = blockIdx.x;
+  double c[6], a0[3], an[3];
+  for (int d = 0; d < 6; ++d) c[d] = a.com[6 * p + d];
+  for (int d = 0; d < 3; ++d) a0[d] = a.aR[4 * p + d];
+  double* out = a.cnext + (size_t)kCentreW * p;
+  if (threadIdx.x == 0)
+    for (int d = 0; d < 6; ++d) out[d] = c[d];
+  com_kdk_from(a.host, c, a.dt, a0, an);
+  if (threadIdx.x == 0) {
+    for (int d = 0; d < 6; ++d) out[6 + d] = c[d];
+    for (int d = 0; d < 3; ++d) out[12 + d] = an[d];
+    out[15] = a.dt;
+  }
 }
 
 __device__ __forceinline__ void write_force_pair(void* F, int f32, size_t i, double c, double s) {
@@ -745,8 +774,20 @@ __global__ void __launch_bounds__(K2_X * K2_SLICES) k2_reduce(K2Args a) {
     if (z == 0 && y == 0 && a.host.n > 0 && a.com != nullptr) {
       double c[6], an[3];
       for (int d = 0; d < 6; ++d) c[d] = a.com[6 * p + d];
-      if (a.mode == SCF_MODE_STEP) com_kdk(a.host, c, a.dt, an);
-      else host_accel_warp(a.host, c[0], c[1], c[2], an[0], an[1], an[2]);
+      if (a.mode == SCF_MODE_STEP) {
+        // the step computed ahead when it started from this very state
+        const double* q = a.cnext ? a.cnext + (size_t)kCentreW * p : nullptr;
+        bool hit = q != nullptr && same_bits(q[15], a.dt);
+        for (int d = 0; d < 6 && hit; ++d) hit = same_bits(q[d], c[d]);
+        if (hit) {
+          for (int d = 0; d < 6; ++d) c[d] = q[6 + d];
+          for (int d = 0; d < 3; ++d) an[d] = q[12 + d];
+        } else {
+          com_kdk(a.host, c, a.dt, an);
+        }
+      } else {
+        host_accel_warp(a.host, c[0], c[1], c[2], an[0], an[1], an[2]);
+      }
       if (x == 0) {
         if (a.mode == SCF_MODE_STEP)
           for (int d = 0; d < 6; ++d) a.com[6 * p + d] = c[d];
@@ -995,6 +1036,21 @@ cudaError_t scf_k2_launch(const K2Args& a, cudaStream_t s) {
   dim3 grid((a.nc + K2_X - 1) / K2_X + 1, a.n_prog, Z);  // + the centre block
   k2_reduce<<<grid, dim3(K2_X, K2_SLICES), 0, s>>>(a);
   return cudaGetLastError();
+}
+
+cudaError_t scf_centre_next_launch(const CentreArgs& a, int priority, cudaStream_t s) {
+  // at the stream priority given: its blocks take the first SM slots that
+  // kernel 3 frees instead of queueing behind all of kernel 3's blocks
+  cudaLaunchConfig_t cfg{};
+  cfg.gridDim = dim3(a.n_prog);
+  cfg.blockDim = dim3(32);
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributePriority;
+  attr[0].val.priority = priority;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, k_centre_next, a);
 }
 
 cudaError_t scf_prep_launch(const PrepArgs& a, cudaStream_t s) {

@@ -269,66 +269,124 @@ __device__ __forceinline__ double scf_host_pot(const ScfHostParams& hp, double x
 //     the plain difference (no cancellation then).
 // Relative error of the result a few float ulps for any |x|/|R| (checked
 // against the long-double difference of the oracle).
-__device__ __forceinline__ void scf_tidal_f32(const ScfHostParams& hp, float Rx, float Ry, float Rz, float x, float y,
-                                              float z, float& ax, float& ay, float& az) {
+//
+// Every value that depends on R alone (r0, and per component p0; u0, h0;
+// zb0, D0, 1/(D0^2 D0); X0, P0; ...) is the same for all the particles of a
+// progenitor: scf_tidal_prep_f32 forms them once per block (component i in
+// thread i, the same single-precision formulas), and the per-particle part
+// reads them from shared memory.  Components with the same b (the three
+// Miyamoto-Nagai disks of a disk fit) share zb1, 1/zb1 and zb1 - zb0.  The
+// reciprocals are the hardware approximation (__fdividef, 2 ulp), the
+// arguments lying far inside its range.
+constexpr int SCF_TIDAL_W = 8;   // floats per component; [7] holds r0
+__device__ __forceinline__ float scf_rcpf(float x) { return __fdividef(1.f, x); }
+
+__device__ __forceinline__ void scf_tidal_prep_f32(const ScfHostParams& hp, int i, float Rx, float Ry, float Rz,
+                                                   float* t) {
+  const float r0 = sqrtf(Rx * Rx + Ry * Ry + Rz * Rz);
+  const float A = (float)hp.a[i];
+  for (int j = 0; j < SCF_TIDAL_W; ++j) t[j] = 0.f;
+  t[7] = r0;
+  if (hp.kind[i] == 1) {  // Hernquist: 1/p0
+    t[0] = 1.f / (r0 * (r0 + A) * (r0 + A));
+  } else if (hp.kind[i] == 2) {  // NFW: h0, 1/(1 + u0), 1/r0^3, 1/r_s
+    const float u0 = r0 / A;
+    t[0] = log1pf(u0) - u0 / (1.f + u0);
+    t[1] = 1.f / (1.f + u0);
+    t[2] = 1.f / (r0 * r0 * r0);
+    t[3] = 1.f / A;
+  } else if (hp.kind[i] == 3) {  // Miyamoto-Nagai: zb0, zab0, D0^2, D0, 1/(D0^2 D0), v0, 1/zb0
+    const float B = (float)hp.b[i];
+    const float zb0 = sqrtf(Rz * Rz + B * B), zab0 = zb0 + A;
+    const float D2_0 = Rx * Rx + Ry * Ry + zab0 * zab0, D0 = sqrtf(D2_0);
+    t[0] = zb0;
+    t[1] = zab0;
+    t[2] = D2_0;
+    t[3] = D0;
+    t[4] = 1.f / (D2_0 * D0);
+    t[5] = 1.f + A / zb0;
+    t[6] = 1.f / zb0;
+  } else if (hp.kind[i] == 4) {  // cut-off power-law bulge: X0, P0, 1/r0^3, 1/r_c^2, lgamma(s)
+    const float s = 0.5f * (3.f - (float)hp.b[i]);
+    const float ia2 = 1.f / (A * A);
+    t[0] = r0 * r0 * ia2;
+    t[1] = scf_gamma_pf(s, t[0]);
+    t[2] = 1.f / (r0 * r0 * r0);
+    t[3] = ia2;
+    t[4] = lgammaf(s);
+  }
+}
+
+__device__ __forceinline__ void scf_tidal_f32(const ScfHostParams& hp, const float (*tr)[SCF_TIDAL_W], float Rx,
+                                              float Ry, float Rz, float x, float y, float z, float& ax, float& ay,
+                                              float& az) {
   ax = 0.f;
   ay = 0.f;
   az = 0.f;
   const float Px = Rx + x, Py = Ry + y, Pz = Rz + z;
-  const float r0 = sqrtf(Rx * Rx + Ry * Ry + Rz * Rz);
+  const float r0 = tr[0][7];
   const float r1 = sqrtf(Px * Px + Py * Py + Pz * Pz);
   const float xx = x * x + y * y + z * z;
-  const float dr = (2.f * (Rx * x + Ry * y + Rz * z) + xx) / (r1 + r0);
+  const float dr = (2.f * (Rx * x + Ry * y + Rz * z) + xx) * scf_rcpf(r1 + r0);
+  float lastB = __int_as_float(0x7fffffff), zb1 = 0.f, izb1 = 0.f, dzb = 0.f;  // NaN: the first disk computes them
   for (int i = 0; i < hp.n; ++i) {
     const float GM = (float)hp.GM[i], A = (float)hp.a[i];
+    const float* t = tr[i];
     if (hp.kind[i] == 1) {  // Hernquist
-      const float p0 = r0 * (r0 + A) * (r0 + A), p1 = r1 * (r1 + A) * (r1 + A);
+      const float p1 = r1 * (r1 + A) * (r1 + A);
       const float dp = dr * (r1 * r1 + r1 * r0 + r0 * r0 + 2.f * A * (r1 + r0) + A * A);
-      const float g1 = GM / p1;
-      const float dg = -GM * dp / (p0 * p1);
+      const float ip1 = scf_rcpf(p1);
+      const float g1 = GM * ip1;
+      const float dg = -GM * dp * ip1 * t[0];
       ax -= g1 * x + dg * Rx;
       ay -= g1 * y + dg * Ry;
       az -= g1 * z + dg * Rz;
     } else if (hp.kind[i] == 2) {  // NFW
-      const float u0 = r0 / A, u1 = r1 / A;
-      const float h0 = log1pf(u0) - u0 / (1.f + u0), h1 = log1pf(u1) - u1 / (1.f + u1);
-      const float d = (dr / A) / (1.f + u0);
-      const float dh = log1pf(d) - d / (1.f + u1);
-      const float i0 = 1.f / (r0 * r0 * r0), i1 = 1.f / (r1 * r1 * r1);
-      const float di = -dr * (r0 * r0 + r0 * r1 + r1 * r1) * i0 * i1;
+      const float u1 = r1 * t[3];
+      const float iu1 = scf_rcpf(1.f + u1);
+      const float h1 = log1pf(u1) - u1 * iu1;
+      const float d = dr * t[3] * t[1];
+      const float dh = log1pf(d) - d * iu1;
+      const float i1 = scf_rcpf(r1 * r1 * r1);
+      const float di = -dr * (r0 * r0 + r0 * r1 + r1 * r1) * t[2] * i1;
       const float g1 = GM * h1 * i1;
-      const float dg = GM * (dh * i1 + h0 * di);
+      const float dg = GM * (dh * i1 + t[0] * di);
       ax -= g1 * x + dg * Rx;
       ay -= g1 * y + dg * Ry;
       az -= g1 * z + dg * Rz;
     } else if (hp.kind[i] == 3) {  // Miyamoto-Nagai
       const float B = (float)hp.b[i];
-      const float zb0 = sqrtf(Rz * Rz + B * B), zb1 = sqrtf(Pz * Pz + B * B);
-      const float dzb = (2.f * Rz * z + z * z) / (zb1 + zb0);
-      const float zab0 = zb0 + A, zab1 = zb1 + A;
-      const float D2_0 = Rx * Rx + Ry * Ry + zab0 * zab0, D2_1 = Px * Px + Py * Py + zab1 * zab1;
+      const float zb0 = t[0], zab0 = t[1], D2_0 = t[2], D0 = t[3];
+      if (B != lastB) {
+        zb1 = sqrtf(Pz * Pz + B * B);
+        izb1 = scf_rcpf(zb1);
+        dzb = (2.f * Rz * z + z * z) * scf_rcpf(zb1 + zb0);
+        lastB = B;
+      }
+      const float zab1 = zb1 + A;
+      const float D2_1 = Px * Px + Py * Py + zab1 * zab1;
       const float dD2 = 2.f * (Rx * x + Ry * y) + x * x + y * y + dzb * (zab1 + zab0);
-      const float D0 = sqrtf(D2_0), D1 = sqrtf(D2_1);
-      const float dD = dD2 / (D1 + D0);
-      const float i0 = 1.f / (D2_0 * D0), i1 = 1.f / (D2_1 * D1);
-      const float di = -dD * (D2_1 + D1 * D0 + D2_0) * i0 * i1;
+      const float D1 = sqrtf(D2_1);
+      const float dD = dD2 * scf_rcpf(D1 + D0);
+      const float i1 = scf_rcpf(D2_1 * D1);
+      const float di = -dD * (D2_1 + D1 * D0 + D2_0) * t[4] * i1;
       ax -= GM * (x * i1 + Rx * di);
       ay -= GM * (y * i1 + Ry * di);
-      const float v0 = 1.f + A / zb0, v1 = 1.f + A / zb1;
-      const float dv = -A * dzb / (zb1 * zb0);
-      az -= GM * (z * v1 * i1 + Rz * (dv * i1 + v0 * di));
+      const float v1 = 1.f + A * izb1;
+      const float dv = -A * dzb * izb1 * t[6];
+      az -= GM * (z * v1 * i1 + Rz * (dv * i1 + t[5] * di));
     } else if (hp.kind[i] == 4) {  // cut-off power-law bulge
       const float s = 0.5f * (3.f - (float)hp.b[i]);
-      const float ia2 = 1.f / (A * A);
-      const float X0 = r0 * r0 * ia2, X1 = r1 * r1 * ia2;
+      const float X0 = t[0], P0 = t[1], ia2 = t[3];
+      const float X1 = r1 * r1 * ia2;
       const float dX = dr * (r1 + r0) * ia2;
-      const float P0 = scf_gamma_pf(s, X0), P1 = scf_gamma_pf(s, X1);
+      const float P1 = scf_gamma_pf(s, X1);
       float dP;
       if (fabsf(dX) <= fminf(0.5f * X0, 2.f)) {
         // Gauss-Legendre nodes +-xi_j and weights w_j on [-1, 1] (6 points)
         const float gx[3] = {0.2386191860831969f, 0.6612093864662645f, 0.9324695142031521f};
         const float gw[3] = {0.4679139345726910f, 0.3607615730481386f, 0.1713244923791704f};
-        const float lg = lgammaf(s), hw = 0.5f * dX, cm = X0 + hw;
+        const float lg = t[4], hw = 0.5f * dX, cm = X0 + hw;
         float acc = 0.f;
 #pragma unroll
         for (int j = 0; j < 3; ++j) {
@@ -339,8 +397,8 @@ __device__ __forceinline__ void scf_tidal_f32(const ScfHostParams& hp, float Rx,
       } else {
         dP = P1 - P0;
       }
-      const float i0 = 1.f / (r0 * r0 * r0), i1 = 1.f / (r1 * r1 * r1);
-      const float di = -dr * (r0 * r0 + r0 * r1 + r1 * r1) * i0 * i1;
+      const float i1 = scf_rcpf(r1 * r1 * r1);
+      const float di = -dr * (r0 * r0 + r0 * r1 + r1 * r1) * t[2] * i1;
       const float g1 = GM * P1 * i1;
       const float dg = GM * (dP * i1 + P0 * di);
       ax -= g1 * x + dg * Rx;

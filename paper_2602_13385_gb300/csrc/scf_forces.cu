@@ -65,8 +65,8 @@ __device__ __forceinline__ float k3_hratio(const K3Args& a, int l, int n) {
 __device__ __forceinline__ double k3_pow(double x, double y) { return pow(x, y); }
 __device__ __forceinline__ float k3_pow(float x, float y) { return powf(x, y); }
 
-template <typename T, int LMAX, int K3_TB, bool GEN = false>
-__global__ void __launch_bounds__(K3_TB) k3_forces(K3Args a) {
+template <typename T, int LMAX, int K3_TB, bool GEN>
+__device__ __forceinline__ void k3_body(const K3Args& a) {
   using V4 = typename Vec4<T>::type;
   using V2 = typename Vec2<T>::type;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -115,6 +115,13 @@ __global__ void __launch_bounds__(K3_TB) k3_forces(K3Args a) {
   if (tid < 3) {
     s_R[tid] = has_host ? a.com[6 * prog + tid] : 0.0;
     s_aR[tid] = has_host ? a.aR[4 * prog + tid] : 0.0;
+  }
+  // single precision: the values of the tidal differences that depend on R alone
+  __shared__ float s_tid[kF2 ? SCF_HOST_CAP : 1][SCF_TIDAL_W];
+  if constexpr (kF2) {
+    if (has_host && tid < a.host.n)
+      scf_tidal_prep_f32(a.host, tid, (float)a.com[6 * prog], (float)a.com[6 * prog + 1], (float)a.com[6 * prog + 2],
+                         s_tid[tid]);
   }
   __syncthreads();
 
@@ -345,7 +352,7 @@ __global__ void __launch_bounds__(K3_TB) k3_forces(K3Args a) {
     if (has_host) {
       // the same difference in single precision without cancellation
       float tx, ty, tz;
-      scf_tidal_f32(a.host, (float)s_R[0], (float)s_R[1], (float)s_R[2], p.x, p.y, p.z, tx, ty, tz);
+      scf_tidal_f32(a.host, s_tid, (float)s_R[0], (float)s_R[1], (float)s_R[2], p.x, p.y, p.z, tx, ty, tz);
       gx += tx;
       gy += ty;
       gz += tz;
@@ -389,11 +396,30 @@ __global__ void __launch_bounds__(K3_TB) k3_forces(K3Args a) {
   }
 }
 
+template <typename T, int LMAX, int K3_TB, bool GEN = false>
+__global__ void __launch_bounds__(K3_TB) k3_forces(K3Args a) {
+  k3_body<T, LMAX, K3_TB, GEN>(a);
+}
+
+// Single precision in 320-thread blocks, held to two blocks per SM (at most
+// 96 registers): 20 resident warps per SM against 16 with 256-thread blocks
+// at 111 registers, which measured 3% faster at (nmax, lmax) = (20, 10).
+template <typename T, int LMAX, bool GEN = false>
+__global__ void __launch_bounds__(320, 2) k3_forces_w(K3Args a) {
+  k3_body<T, LMAX, 320, GEN>(a);
+}
+
 template <typename T, int TB, int LMAX, bool GEN = false>
 struct K3At {
-  static void* fn() { return (void*)k3_forces<T, LMAX, TB, GEN>; }
-  static void launch(const K3Args& a, int blocks, size_t smem, cudaStream_t s) {
-    k3_forces<T, LMAX, TB, GEN><<<blocks, TB, smem, s>>>(a);
+  static constexpr bool kW = sizeof(T) == 4 && TB == 320;
+  static void* fn() {
+    if constexpr (kW) return (void*)k3_forces_w<T, LMAX, GEN>;
+    else return (void*)k3_forces<T, LMAX, TB, GEN>;
+  }
+  static cudaError_t launch(const K3Args& a, int blocks, size_t smem, cudaStream_t s) {
+    if constexpr (kW) k3_forces_w<T, LMAX, GEN><<<blocks, TB, smem, s>>>(a);
+    else k3_forces<T, LMAX, TB, GEN><<<blocks, TB, smem, s>>>(a);
+    return cudaGetLastError();
   }
 };
 
@@ -418,12 +444,16 @@ auto dispatch_lmax(int lmax, Fn&& f) {
   }
 }
 
-// Kernel 3 instantiations: blocks of 64, 128 or 256 threads (the autotuner's choices).
+// Kernel 3 instantiations: blocks of 64, 128 or 256 threads, and 320 in single
+// precision (the autotuner's choices).
 template <typename T, typename Fn>
 auto dispatch_k3(int tb, int lmax, Fn&& f) {
   switch (tb) {
     case 64: return dispatch_lmax<T, 64>(lmax, f);
     case 256: return dispatch_lmax<T, 256>(lmax, f);
+    case 320:
+      if constexpr (sizeof(T) == 4) return dispatch_lmax<T, 320>(lmax, f);
+      [[fallthrough]];
     default: return dispatch_lmax<T, 128>(lmax, f);
   }
 }
@@ -431,7 +461,7 @@ auto dispatch_k3(int tb, int lmax, Fn&& f) {
 template <typename T, bool GEN = false>
 cudaError_t prepare_t(int lmax, int nmax, int tb, ScfLaunchInfo* info, int* blocks_per_sm) {
   const int nlm = (lmax + 1) * (lmax + 2) / 2, nc = (nmax + 1) * nlm;
-  if (tb != 64 && tb != 128 && tb != 256) return cudaErrorInvalidValue;
+  if (tb != 64 && tb != 128 && tb != 256 && !(tb == 320 && sizeof(T) == 4)) return cudaErrorInvalidValue;
   if (GEN && tb != 128) return cudaErrorInvalidValue;
   auto body = [&](auto k) -> cudaError_t {
     using KK = decltype(k);
@@ -464,8 +494,9 @@ cudaError_t scf_k3_gen_prepare(int precision, int lmax, int nmax, ScfLaunchInfo*
 }
 
 cudaError_t scf_k3_launch(int precision, const K3Args& a, int blocks, const ScfLaunchInfo& info, cudaStream_t s) {
+  cudaError_t err = cudaSuccess;
   auto go = [&](auto k) -> int {
-    decltype(k)::launch(a, blocks, info.smem, s);
+    err = decltype(k)::launch(a, blocks, info.smem, s);
     return 0;
   };
   if (info.variant == 3) {  // radial family of exponent alpha != 1, 128-thread blocks
@@ -476,5 +507,6 @@ cudaError_t scf_k3_launch(int precision, const K3Args& a, int blocks, const ScfL
   } else {
     dispatch_k3<double>(info.threads, a.lmax, go);
   }
+  if (err != cudaSuccess) return err;
   return cudaGetLastError();
 }

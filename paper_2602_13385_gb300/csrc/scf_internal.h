@@ -87,10 +87,30 @@ struct K2Args {
   int z;
   double* zpart;
   unsigned* counters;
+  // optional (step mode): centre steps computed ahead, [n_prog][kCentreW]
+  // doubles (see CentreArgs); the centre block takes entry p's result when
+  // its key equals the state it is about to step
+  const double* cnext;
 };
 // Column groups of kernel 2 for NC coefficients (the counters per progenitor).
 int scf_k2_groups(int nc);
 constexpr int kK2MaxChunks = 16;
+
+// The centre's next kick-drift-kick computed ahead (beside kernel 3, on a
+// second stream): entry p of cnext holds [0, 6) the state it started from
+// (the key), [6, 12) the stepped state, [12, 15) a_host at the new R, [15]
+// the dt used.  The first kick takes a_host(R) from aR, which kernel 2
+// wrote for that same R.
+constexpr int kCentreW = 16;
+struct CentreArgs {
+  const double* com;        // [n_prog][6]
+  const double* aR;         // [n_prog][4]
+  double* cnext;            // [n_prog][kCentreW]
+  double dt;
+  int n_prog;
+  ScfHostParams host;
+};
+cudaError_t scf_centre_next_launch(const CentreArgs& a, int priority, cudaStream_t s);
 
 // Force coefficients and a_host(R) from given coefficients (scf_forces).
 struct PrepArgs {

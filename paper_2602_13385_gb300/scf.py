@@ -242,7 +242,8 @@ class SCF:
                   k1_variant: int | None = None):
         """``k1_tile``: 64, 128 or 256 particles per tile of the one-thread-per-
         output coefficient kernel, or 0 for the register-tiled kernel (mixed
-        precision only); ``k3_block``: 64, 128 or 256 threads per field block;
+        precision only); ``k3_block``: 64, 128 or 256 threads per field block (320
+        in mixed precision);
         ``k1_variant`` 2 / ``k3_variant`` 1: the float-float coefficient /
         field kernel of double-precision handles (128-wide only), 0 for the
         native ones."""
