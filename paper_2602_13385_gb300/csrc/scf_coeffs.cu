@@ -13,6 +13,7 @@
 // order, so the result does not depend on scheduling.
 #include <algorithm>
 #include <cstdio>
+#include <type_traits>
 
 #include "scf_device.cuh"
 #include "scf_internal.h"
@@ -217,14 +218,17 @@ size_t k1_smem(int nmax, int nc) {
 // over particles p, with only (nmax+1)(2l+1) outputs.  Reading both operands
 // from shared memory for every FMA (the form above) ties it to shared-memory
 // bandwidth: one wavefront per operand against four FMA instructions per
-// clock.  Here every worker thread owns one 7 x 8 tile of outputs (degree l,
-// seven radial orders, eight angular columns) for the block's lifetime, and
-// one of `sub` particle sub-groups; per group of four particles it reads
-// 7 + 8 float4 rows and issues 224 FMAs into registers.
+// clock.  Here every worker thread owns one TN x TM tile of outputs (degree l,
+// TN radial orders, TM angular columns) for the block's lifetime, and one of
+// `sub` particle sub-groups; per group of four particles it reads TN + TM
+// float4 rows and issues 4 TN TM FMAs into registers.  The tile shape follows
+// the expansion: all 21 radial orders by 3 columns at nmax = 20 (the 2l + 1
+// columns of a degree then pad to a multiple of 3, not of 8: 132 instead of
+// 168 columns at lmax = 10), 11 by 5 at nmax = 10, 7 by 8 otherwise.
 //
 // The basis of each 60-particle tile is staged as rows [l][n] (the scaled
 // Gegenbauer values Ch_n(xi) = C_n(xi) / gscale[l][n], see ScfConst) and
-// [chunk (l, mm / 8)][mm % 8] (angular factors m s^l q^(2l+1) Pb_lm C_m and
+// [chunk (l, mm / TM)][mm % TM] (angular factors m s^l q^(2l+1) Pb_lm C_m and
 // ... Pb_lm S_m), particle index fastest; the constant gscale is applied when
 // the sums are flushed.  Eight warps compute it, four threads
 // per particle: thread set q runs the Gegenbauer chains of the degrees
@@ -245,38 +249,50 @@ namespace tiled {
 constexpr int TP = 60;           // particles per tile (two basis halves of 30 lanes)
 constexpr int TPP = TP;          // staged row stride in floats: 15 float4s, an odd number, so
                                  // float4 reads of rows that differ mod 8 hit different bank groups
-constexpr int TN = 7, TM = 8;    // output tile: radial orders x angular columns
 constexpr int BASIS_WARPS = 8;   // 2 particle halves x 4 chain sets
 constexpr int WINDOW_TILES = 64; // tiles summed in registers before a window's sums are stored
 constexpr int MAX_THREADS = 256;
 
-__host__ __device__ inline int n_chunks(int nn) { return (nn + TN - 1) / TN; }
-__host__ __device__ inline int m_chunks(int l) { return (2 * l + 1 + TM - 1) / TM; }
-inline int n_items(int nmax, int lmax) {
-  int c = 0;
-  for (int l = 0; l <= lmax; ++l) c += m_chunks(l);
-  return c * n_chunks(nmax + 1);
-}
-// Angular rows are stored by output chunk: chunk k = (l, mm / TM) occupies the
-// TM rows starting at 9k (one spare row per chunk), so the chunks that the
-// lanes of a warp read together start in different bank groups.
-constexpr int YCH = TM + 1;
-__host__ __device__ constexpr int chunk_base(int l) {  // chunks of the degrees below l
-  int k = 0;
-  for (int i = 0; i < l; ++i) k += (2 * i + 1 + TM - 1) / TM;
-  return k;
-}
-__host__ __device__ constexpr int y_row(int l, int mm) { return YCH * (chunk_base(l) + mm / TM) + mm % TM; }
-// Shared memory: [gen: the Gegenbauer steps gbeta[l][n] of the handle's radial
-// family] then the staging rows; at window ends the staging rows hold the
-// worker tiles (at most MAX_THREADS tiles of TN x TM floats) for the
-// cross-sub-group sums.
-constexpr size_t kRedFloats = (size_t)MAX_THREADS * TN * TM;
-inline size_t smem_bytes(int nmax, int lmax, bool gen = false) {
-  const size_t rows = (size_t)(lmax + 1) * (nmax + 1) + (TN - 1) + (size_t)YCH * chunk_base(lmax + 1);
-  const size_t sg = gen ? (size_t)(lmax + 1) * (nmax + 1) : 0;
-  return sizeof(float) * (((sg + 3) & ~size_t(3)) + std::max(TPP * rows, kRedFloats));
-}
+// Output tile of a worker: TN radial orders x TM angular columns.
+template <int TN_, int TM_>
+struct Tile {
+  static constexpr int TN = TN_, TM = TM_;
+  static_assert(TN * TM <= 64, "the register budget holds at most 64 accumulators");
+  static __host__ __device__ constexpr int n_chunks(int nn) { return (nn + TN - 1) / TN; }
+  static __host__ __device__ constexpr int m_chunks(int l) { return (2 * l + 1 + TM - 1) / TM; }
+  // zero rows after the last degree's radial rows that its last chunk reads
+  static __host__ __device__ constexpr int pad_rows(int nn) { return n_chunks(nn) * TN - nn; }
+  static int n_items(int nmax, int lmax) {
+    int c = 0;
+    for (int l = 0; l <= lmax; ++l) c += m_chunks(l);
+    return c * n_chunks(nmax + 1);
+  }
+  // Angular rows are stored by output chunk: chunk k = (l, mm / TM) occupies
+  // the TM rows from YCH k, YCH the smallest odd count >= TM, so that the
+  // chunks that the lanes of a warp read together (15 YCH float4s apart, an
+  // odd number) start in different bank groups.
+  static constexpr int YCH = TM | 1;
+  static __host__ __device__ constexpr int chunk_base(int l) {  // chunks of the degrees below l
+    int k = 0;
+    for (int i = 0; i < l; ++i) k += m_chunks(i);
+    return k;
+  }
+  static __host__ __device__ constexpr int y_row(int l, int mm) { return YCH * (chunk_base(l) + mm / TM) + mm % TM; }
+  // Shared memory: [gen: the Gegenbauer steps gbeta[l][n] of the handle's
+  // radial family] then the staging rows; at window ends the staging rows hold
+  // the worker tiles (at most MAX_THREADS tiles of TN x TM floats) for the
+  // cross-sub-group sums.
+  static constexpr size_t kRedFloats = (size_t)MAX_THREADS * TN * TM;
+  static size_t smem_bytes(int nmax, int lmax, bool gen) {
+    const size_t rows = (size_t)(lmax + 1) * (nmax + 1) + pad_rows(nmax + 1) + (size_t)YCH * chunk_base(lmax + 1);
+    const size_t sg = gen ? (size_t)(lmax + 1) * (nmax + 1) : 0;
+    return sizeof(float) * (((sg + 3) & ~size_t(3)) + std::max(TPP * rows, kRedFloats));
+  }
+};
+using TileGeneric = Tile<7, 8>;
+// the tile of a compile-time shape: all radial orders where they fit
+template <int NN>
+using TileFor = std::conditional_t<NN == 21, Tile<21, 3>, std::conditional_t<NN == 11, Tile<11, 5>, TileGeneric>>;
 
 // At the end of a window: every worker has written its tile to red[(sgrp *
 // items + item) * TN * TM + i * TM + j]; the block adds the sub-groups' tiles
@@ -284,10 +300,11 @@ inline size_t smem_bytes(int nmax, int lmax, bool gen = false) {
 // the staged C_n) to dst: one float row of 2 NC per window and block, T_nl0
 // not written (kernel 2 reads it as 0).  tab: the tables of a radial family
 // with alpha != 1 (null: the constant bank's).
+template <class S>
 __device__ __forceinline__ void store_window(const float* __restrict__ red, float* __restrict__ dst, int items, int sub,
                                              const short (*item_lnm)[3], int nn, int nlm, int nc,
                                              const ScfConst* tab) {
-  constexpr int E = TN * TM;
+  constexpr int TM = S::TM, E = S::TN * S::TM;
   for (int e = threadIdx.x; e < items * E; e += blockDim.x) {
     const int it = e / E, r = e - it * E, i = r / TM, j = r - i * TM;
     const int l = item_lnm[it][0], n = item_lnm[it][1] + i, mm = item_lnm[it][2] + j;
@@ -309,6 +326,7 @@ __device__ __forceinline__ void store_window(const float* __restrict__ red, floa
 template <int NCH, bool GEN = false>
 struct BasisGeneric {
   static constexpr bool kGen = GEN;
+  using S = TileGeneric;
   static __device__ __forceinline__ void run(int q, float* Rs, float* Ys, int t, int NN, int L, float mass, float u,
                                              float v, float c, float qv, float xi, float sq2, const float* sg) {
       // radial chains of the degrees l = q + 4j: R[l][n] = Ch_n(xi)
@@ -374,8 +392,8 @@ struct BasisGeneric {
             P1[j] = P;
             const float Pp = P * pre[j];
             pre[j] *= sq2;
-            Ys[y_row(l, m) * TPP + t] = Pp * Wc[j];
-            if (m >= 1) Ys[y_row(l, l + m) * TPP + t] = Pp * Ws[j];
+            Ys[S::y_row(l, m) * TPP + t] = Pp * Wc[j];
+            if (m >= 1) Ys[S::y_row(l, l + m) * TPP + t] = Pp * Ws[j];
           }
         }
       }
@@ -385,7 +403,7 @@ struct BasisGeneric {
 
 // The same with the shape fixed at compile time: every recurrence constant is
 // an immediate constant-bank operand and every staged row an immediate offset.
-template <int Q, int NN, int L, bool GEN>
+template <int Q, int NN, int L, bool GEN, class S>
 __device__ __forceinline__ void basis_fixed(float* Rs, float* Ys, int t, float mass, float u, float v, float c,
                                             float qv, float xi, float sq2, const float* sg) {
   constexpr int NJ = Q <= L ? (L - Q) / 4 + 1 : 0;
@@ -449,8 +467,8 @@ __device__ __forceinline__ void basis_fixed(float* Rs, float* Ys, int t, float m
           P1[j] = P;
           const float Pp = P * pre[j];
           pre[j] *= sq2;
-          Ys[y_row(l, m) * TPP + t] = Pp * Wc[j];
-          if (m >= 1) Ys[y_row(l, l + m) * TPP + t] = Pp * Ws[j];
+          Ys[S::y_row(l, m) * TPP + t] = Pp * Wc[j];
+          if (m >= 1) Ys[S::y_row(l, l + m) * TPP + t] = Pp * Ws[j];
         }
       }
     }
@@ -460,39 +478,42 @@ __device__ __forceinline__ void basis_fixed(float* Rs, float* Ys, int t, float m
 template <int NN_, int L_, bool GEN = false>
 struct BasisFixed {
   static constexpr bool kGen = GEN;
+  using S = TileFor<NN_>;
   static __device__ __forceinline__ void run(int q, float* Rs, float* Ys, int t, int, int, float mass, float u,
                                              float v, float c, float qv, float xi, float sq2, const float* sg) {
     switch (q) {  // warp-uniform
-      case 0: basis_fixed<0, NN_, L_, GEN>(Rs, Ys, t, mass, u, v, c, qv, xi, sq2, sg); break;
-      case 1: basis_fixed<1, NN_, L_, GEN>(Rs, Ys, t, mass, u, v, c, qv, xi, sq2, sg); break;
-      case 2: basis_fixed<2, NN_, L_, GEN>(Rs, Ys, t, mass, u, v, c, qv, xi, sq2, sg); break;
-      default: basis_fixed<3, NN_, L_, GEN>(Rs, Ys, t, mass, u, v, c, qv, xi, sq2, sg); break;
+      case 0: basis_fixed<0, NN_, L_, GEN, S>(Rs, Ys, t, mass, u, v, c, qv, xi, sq2, sg); break;
+      case 1: basis_fixed<1, NN_, L_, GEN, S>(Rs, Ys, t, mass, u, v, c, qv, xi, sq2, sg); break;
+      case 2: basis_fixed<2, NN_, L_, GEN, S>(Rs, Ys, t, mass, u, v, c, qv, xi, sq2, sg); break;
+      default: basis_fixed<3, NN_, L_, GEN, S>(Rs, Ys, t, mass, u, v, c, qv, xi, sq2, sg); break;
     }
   }
 };
 
 // 128 registers: each quarter of the SM holds 16384, i.e. four warps of 128
-// registers, so two blocks of 8 warps share an SM; the 56 accumulators and
-// 7 float4 operands fit without spilling.
+// registers, so two blocks of 8 warps share an SM; the (at most 64)
+// accumulators and the operands of the shorter tile side fit without spilling.
 template <class B>  // basis policy: BasisGeneric<NCH> or BasisFixed<NN, L>
 __global__ void __maxnreg__(128) k1_tiled(K1Args a) {
+  using S = typename B::S;
+  constexpr int TN = S::TN, TM = S::TM;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ short item_lnm[MAX_THREADS][3];       // (l, n0, mm0) of every output tile
   const int NN = a.nmax + 1, L = a.lmax;
-  const int rR = (L + 1) * NN;
+  const int rR = (L + 1) * NN, pad = S::pad_rows(NN);
   const int sg_floats = B::kGen ? ((rR + 3) & ~3) : 0;
   float* SG = reinterpret_cast<float*>(smem_raw);  // [L + 1][NN] Gegenbauer steps (radial family alpha != 1)
-  float* Rs = SG + sg_floats;                      // [rR + TN - 1][TPP]
-  float* Ys = Rs + (rR + TN - 1) * TPP;            // [YCH * chunks][TPP]
+  float* Rs = SG + sg_floats;                      // [rR + pad][TPP]
+  float* Ys = Rs + (rR + pad) * TPP;               // [YCH * chunks][TPP]
   float* red = Rs;                                 // window ends: the worker tiles
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   // padding rows and the angular rows past 2l of each degree's last chunk are
   // never written by the basis; they feed only accumulators that are never
   // stored, and are cleared once so that they hold no stale values
   {
-    const int ny4 = YCH * chunk_base(L + 1) * (TPP / 4);
+    const int ny4 = S::YCH * S::chunk_base(L + 1) * (TPP / 4);
     const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
-    for (int i = tid; i < (TN - 1) * (TPP / 4); i += blockDim.x) reinterpret_cast<float4*>(Rs + rR * TPP)[i] = z4;
+    for (int i = tid; i < pad * (TPP / 4); i += blockDim.x) reinterpret_cast<float4*>(Rs + rR * TPP)[i] = z4;
     for (int i = tid; i < ny4; i += blockDim.x) reinterpret_cast<float4*>(Ys)[i] = z4;
   }
   if constexpr (B::kGen)
@@ -503,10 +524,10 @@ __global__ void __maxnreg__(128) k1_tiled(K1Args a) {
   const int item = tid % a.items, sgrp = tid / a.items;
   int il = 0, ic = 0, id = 0;
   {
-    const int ncn = n_chunks(NN);
+    const int ncn = S::n_chunks(NN);
     int r = item;
     for (int l = 0; l <= L; ++l) {
-      const int cnt = m_chunks(l) * ncn;
+      const int cnt = S::m_chunks(l) * ncn;
       if (r < cnt) {
         il = l;
         id = r / ncn;
@@ -524,7 +545,7 @@ __global__ void __maxnreg__(128) k1_tiled(K1Args a) {
   }
   __syncthreads();
   const float* Rrow = Rs + (il * NN + n0) * TPP;
-  const float* Yrow = Ys + y_row(il, mm0) * TPP;
+  const float* Yrow = Ys + S::y_row(il, mm0) * TPP;
   float acc[TN][TM];
 #pragma unroll
   for (int i = 0; i < TN; ++i)
@@ -600,18 +621,35 @@ __global__ void __maxnreg__(128) k1_tiled(K1Args a) {
     if (worker) {
       for (int g = sgrp; g < TP / 4; g += a.sub) {
         const int t0 = 4 * g;
-        float4 rv[TN];
+        if constexpr (TN <= TM) {  // the radial rows in registers, the angular ones streamed
+          float4 rv[TN];
 #pragma unroll
-        for (int i = 0; i < TN; ++i) rv[i] = *reinterpret_cast<const float4*>(Rrow + i * TPP + t0);
+          for (int i = 0; i < TN; ++i) rv[i] = *reinterpret_cast<const float4*>(Rrow + i * TPP + t0);
 #pragma unroll
-        for (int j = 0; j < TM; ++j) {
-          const float4 yv = *reinterpret_cast<const float4*>(Yrow + j * TPP + t0);
+          for (int j = 0; j < TM; ++j) {
+            const float4 yv = *reinterpret_cast<const float4*>(Yrow + j * TPP + t0);
+#pragma unroll
+            for (int i = 0; i < TN; ++i) {
+              acc[i][j] = fmaf(rv[i].x, yv.x, acc[i][j]);
+              acc[i][j] = fmaf(rv[i].y, yv.y, acc[i][j]);
+              acc[i][j] = fmaf(rv[i].z, yv.z, acc[i][j]);
+              acc[i][j] = fmaf(rv[i].w, yv.w, acc[i][j]);
+            }
+          }
+        } else {  // the angular rows in registers, the radial ones streamed
+          float4 yv[TM];
+#pragma unroll
+          for (int j = 0; j < TM; ++j) yv[j] = *reinterpret_cast<const float4*>(Yrow + j * TPP + t0);
 #pragma unroll
           for (int i = 0; i < TN; ++i) {
-            acc[i][j] = fmaf(rv[i].x, yv.x, acc[i][j]);
-            acc[i][j] = fmaf(rv[i].y, yv.y, acc[i][j]);
-            acc[i][j] = fmaf(rv[i].z, yv.z, acc[i][j]);
-            acc[i][j] = fmaf(rv[i].w, yv.w, acc[i][j]);
+            const float4 rv = *reinterpret_cast<const float4*>(Rrow + i * TPP + t0);
+#pragma unroll
+            for (int j = 0; j < TM; ++j) {
+              acc[i][j] = fmaf(rv.x, yv[j].x, acc[i][j]);
+              acc[i][j] = fmaf(rv.y, yv[j].y, acc[i][j]);
+              acc[i][j] = fmaf(rv.z, yv[j].z, acc[i][j]);
+              acc[i][j] = fmaf(rv.w, yv[j].w, acc[i][j]);
+            }
           }
         }
       }
@@ -621,17 +659,27 @@ __global__ void __maxnreg__(128) k1_tiled(K1Args a) {
       // end of a window: the worker tiles through shared memory, one row per window
       if (worker) {
         float* mine = red + (size_t)(sgrp * a.items + item) * (TN * TM);
+        if constexpr (TM % 4 == 0) {
 #pragma unroll
-        for (int i = 0; i < TN; ++i)
+          for (int i = 0; i < TN; ++i)
 #pragma unroll
-          for (int j = 0; j < TM; j += 4) {
-            *reinterpret_cast<float4*>(mine + i * TM + j) =
-                make_float4(acc[i][j], acc[i][j + 1], acc[i][j + 2], acc[i][j + 3]);
-            acc[i][j] = acc[i][j + 1] = acc[i][j + 2] = acc[i][j + 3] = 0.f;
-          }
+            for (int j = 0; j < TM; j += 4) {
+              *reinterpret_cast<float4*>(mine + i * TM + j) =
+                  make_float4(acc[i][j], acc[i][j + 1], acc[i][j + 2], acc[i][j + 3]);
+              acc[i][j] = acc[i][j + 1] = acc[i][j + 2] = acc[i][j + 3] = 0.f;
+            }
+        } else {  // an odd tile (TN TM words per thread): word stores, no bank conflicts
+#pragma unroll
+          for (int i = 0; i < TN; ++i)
+#pragma unroll
+            for (int j = 0; j < TM; ++j) {
+              mine[i * TM + j] = acc[i][j];
+              acc[i][j] = 0.f;
+            }
+        }
       }
       __syncthreads();
-      store_window(red, out + (size_t)win * 2 * a.nc, a.items, a.sub, item_lnm, NN, a.nlm, a.nc, tabp);
+      store_window<S>(red, out + (size_t)win * 2 * a.nc, a.items, a.sub, item_lnm, NN, a.nlm, a.nc, tabp);
       __syncthreads();  // the staging rows are the next tile's
       ++win;
       tiles = 0;
@@ -644,6 +692,7 @@ __global__ void __maxnreg__(128) k1_tiled(K1Args a) {
 
 template <class B>
 struct K1Tiled {
+  using S = typename B::S;
   static void* fn() { return (void*)k1_tiled<B>; }
   static void launch(const K1Args& a, int blocks, int threads, size_t smem, cudaStream_t s) {
     k1_tiled<B><<<blocks, threads, smem, s>>>(a);
@@ -973,20 +1022,21 @@ cudaError_t scf_k1_gen_prepare(int precision, int lmax, int nmax, ScfLaunchInfo*
 
 cudaError_t scf_k1_tiled_prepare(int lmax, int nmax, ScfLaunchInfo* info, int* blocks_per_sm, bool gen) {
   using namespace tiled;
-  const int items = n_items(nmax, lmax);
-  if (items > MAX_THREADS) return cudaErrorInvalidConfiguration;
-  const int sub = std::min(TP / 4, std::max(1, MAX_THREADS / items));
-  info->items = items;
-  info->sub = sub;
-  info->threads = std::max(BASIS_WARPS * 32, 32 * ((items * sub + 31) / 32));
-  info->tile = TP;
-  info->variant = 1;
-  info->win = 1;  // set from the block map by the caller (scf_k1_windows)
-  info->win_tiles = WINDOW_TILES;
-  info->smem = smem_bytes(nmax, lmax, gen);
-  if (info->smem > 227 * 1024) return cudaErrorInvalidConfiguration;
   return dispatch_tiled(nmax, lmax, [&](auto k) -> cudaError_t {
     using KK = decltype(k);
+    using S = typename KK::S;
+    const int items = S::n_items(nmax, lmax);
+    if (items > MAX_THREADS) return cudaErrorInvalidConfiguration;
+    const int sub = std::min(TP / 4, std::max(1, MAX_THREADS / items));
+    info->items = items;
+    info->sub = sub;
+    info->threads = std::max(BASIS_WARPS * 32, 32 * ((items * sub + 31) / 32));
+    info->tile = TP;
+    info->variant = 1;
+    info->win = 1;  // set from the block map by the caller (scf_k1_windows)
+    info->win_tiles = WINDOW_TILES;
+    info->smem = S::smem_bytes(nmax, lmax, gen);
+    if (info->smem > 227 * 1024) return cudaErrorInvalidConfiguration;
     cudaError_t e = cudaFuncSetAttribute(KK::fn(), cudaFuncAttributeMaxDynamicSharedMemorySize, (int)info->smem);
     if (e != cudaSuccess) return e;
     // two ~100 KB blocks per SM need the largest shared-memory carveout

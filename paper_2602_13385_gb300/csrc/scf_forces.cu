@@ -65,7 +65,11 @@ __device__ __forceinline__ float k3_hratio(const K3Args& a, int l, int n) {
 __device__ __forceinline__ double k3_pow(double x, double y) { return pow(x, y); }
 __device__ __forceinline__ float k3_pow(float x, float y) { return powf(x, y); }
 
-template <typename T, int LMAX, int K3_TB, bool GEN>
+// NNF > 0: the shape (nmax, lmax) = (NNF - 1, LMAX) fixed at compile time
+// (single precision, alpha = 1): every coefficient offset is an immediate
+// and the radial loop is unrolled by kK3Unroll without a remainder.
+constexpr int kK3Unroll = 4;
+template <typename T, int LMAX, int K3_TB, bool GEN, int NNF>
 __device__ __forceinline__ void k3_body(const K3Args& a) {
   using V4 = typename Vec4<T>::type;
   using V2 = typename Vec2<T>::type;
@@ -188,11 +192,12 @@ __device__ __forceinline__ void k3_body(const K3Args& a) {
   T An = 0, Ax = 0, Ay = 0, Az = 0, pot = 0;
   T slq = qa;              // s^l q^((2l+1) alpha)
   T sl1q = qa * qa * qa;    // s^(l-1) q^((2l+1) alpha) for l >= 1 (set at l = 1)
-  const int NN = a.nmax + 1;
+  const int NN = NNF > 0 ? NNF : a.nmax + 1;
+  const int NLM = NNF > 0 ? (LMAX + 1) * (LMAX + 2) / 2 : a.nlm;
 
 #pragma unroll
   for (int l = 0; l <= LMAX; ++l) {
-    if (l > a.lmax) break;
+    if (NNF == 0 && l > a.lmax) break;
     if (SPLIT == 2 && half == 1 && l >= Ls) break;
 #pragma unroll
     for (int m = 0; m + 2 <= l; ++m) P[m] = tla<T>(scf_lm(l, m)) * c * P1[m] - tlb<T>(scf_lm(l, m)) * P2[m];
@@ -237,7 +242,7 @@ __device__ __forceinline__ void k3_body(const K3Args& a) {
           hbn = k3_hbeta<T, GEN>(a, l, n);
         }
         const T cn = xi * c0 - gbn * cm1;
-        const int o = n * a.nlm + lm0;
+        const int o = n * NLM + lm0;
         if constexpr (kF2) {
           const T dd = d0 * hrn;
 #pragma unroll
@@ -264,7 +269,11 @@ __device__ __forceinline__ void k3_body(const K3Args& a) {
         dm1 = d0;
         d0 = dn;
       };
-      if constexpr (kF2 && !GEN && LMAX == 10) {
+      if constexpr (NNF > 0) {
+        static_assert((NNF - 1) % kK3Unroll == 0, "the radial loop has no remainder");
+#pragma unroll kK3Unroll
+        for (int n = 1; n < NNF; ++n) radial_step(n);
+      } else if constexpr (kF2 && !GEN && LMAX == 10) {
 #pragma unroll 2
         for (int n = 1; n < NN; ++n) radial_step(n);
       } else {
@@ -396,29 +405,29 @@ __device__ __forceinline__ void k3_body(const K3Args& a) {
   }
 }
 
-template <typename T, int LMAX, int K3_TB, bool GEN = false>
+template <typename T, int LMAX, int K3_TB, bool GEN = false, int NNF = 0>
 __global__ void __launch_bounds__(K3_TB) k3_forces(K3Args a) {
-  k3_body<T, LMAX, K3_TB, GEN>(a);
+  k3_body<T, LMAX, K3_TB, GEN, NNF>(a);
 }
 
 // Single precision in 320-thread blocks, held to two blocks per SM (at most
 // 96 registers): 20 resident warps per SM against 16 with 256-thread blocks
 // at 111 registers, which measured 3% faster at (nmax, lmax) = (20, 10).
-template <typename T, int LMAX, bool GEN = false>
+template <typename T, int LMAX, bool GEN = false, int NNF = 0>
 __global__ void __launch_bounds__(320, 2) k3_forces_w(K3Args a) {
-  k3_body<T, LMAX, 320, GEN>(a);
+  k3_body<T, LMAX, 320, GEN, NNF>(a);
 }
 
-template <typename T, int TB, int LMAX, bool GEN = false>
+template <typename T, int TB, int LMAX, bool GEN = false, int NNF = 0>
 struct K3At {
   static constexpr bool kW = sizeof(T) == 4 && TB == 320;
   static void* fn() {
-    if constexpr (kW) return (void*)k3_forces_w<T, LMAX, GEN>;
-    else return (void*)k3_forces<T, LMAX, TB, GEN>;
+    if constexpr (kW) return (void*)k3_forces_w<T, LMAX, GEN, NNF>;
+    else return (void*)k3_forces<T, LMAX, TB, GEN, NNF>;
   }
   static cudaError_t launch(const K3Args& a, int blocks, size_t smem, cudaStream_t s) {
-    if constexpr (kW) k3_forces_w<T, LMAX, GEN><<<blocks, TB, smem, s>>>(a);
-    else k3_forces<T, LMAX, TB, GEN><<<blocks, TB, smem, s>>>(a);
+    if constexpr (kW) k3_forces_w<T, LMAX, GEN, NNF><<<blocks, TB, smem, s>>>(a);
+    else k3_forces<T, LMAX, TB, GEN, NNF><<<blocks, TB, smem, s>>>(a);
     return cudaGetLastError();
   }
 };
@@ -432,8 +441,12 @@ int lmax_bucket(int lmax) {
   return 12;
 }
 
+// (nmax, lmax) = (20, 10) in single precision with alpha = 1 runs the
+// compile-time shape.
 template <typename T, int TB, typename Fn, bool GEN = false>
-auto dispatch_lmax(int lmax, Fn&& f) {
+auto dispatch_lmax(int lmax, Fn&& f, int nmax = -1) {
+  if constexpr (sizeof(T) == 4 && !GEN)
+    if (lmax == 10 && nmax == 20) return f(K3At<T, TB, 10, GEN, 21>());
   switch (lmax_bucket(lmax)) {
     case 2: return f(K3At<T, TB, 2, GEN>());
     case 4: return f(K3At<T, TB, 4, GEN>());
@@ -447,14 +460,14 @@ auto dispatch_lmax(int lmax, Fn&& f) {
 // Kernel 3 instantiations: blocks of 64, 128 or 256 threads, and 320 in single
 // precision (the autotuner's choices).
 template <typename T, typename Fn>
-auto dispatch_k3(int tb, int lmax, Fn&& f) {
+auto dispatch_k3(int tb, int lmax, int nmax, Fn&& f) {
   switch (tb) {
-    case 64: return dispatch_lmax<T, 64>(lmax, f);
-    case 256: return dispatch_lmax<T, 256>(lmax, f);
+    case 64: return dispatch_lmax<T, 64>(lmax, f, nmax);
+    case 256: return dispatch_lmax<T, 256>(lmax, f, nmax);
     case 320:
-      if constexpr (sizeof(T) == 4) return dispatch_lmax<T, 320>(lmax, f);
+      if constexpr (sizeof(T) == 4) return dispatch_lmax<T, 320>(lmax, f, nmax);
       [[fallthrough]];
-    default: return dispatch_lmax<T, 128>(lmax, f);
+    default: return dispatch_lmax<T, 128>(lmax, f, nmax);
   }
 }
 
@@ -478,7 +491,7 @@ cudaError_t prepare_t(int lmax, int nmax, int tb, ScfLaunchInfo* info, int* bloc
     return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, KK::fn(), info->threads, info->smem);
   };
   if constexpr (GEN) return dispatch_lmax<T, 128, decltype(body)&, true>(lmax, body);
-  else return dispatch_k3<T>(tb, lmax, body);
+  else return dispatch_k3<T>(tb, lmax, nmax, body);
 }
 
 }  // namespace
@@ -503,9 +516,9 @@ cudaError_t scf_k3_launch(int precision, const K3Args& a, int blocks, const ScfL
     if (precision == 1) dispatch_lmax<float, 128, decltype(go)&, true>(a.lmax, go);
     else dispatch_lmax<double, 128, decltype(go)&, true>(a.lmax, go);
   } else if (precision == 1) {
-    dispatch_k3<float>(info.threads, a.lmax, go);
+    dispatch_k3<float>(info.threads, a.lmax, a.nmax, go);
   } else {
-    dispatch_k3<double>(info.threads, a.lmax, go);
+    dispatch_k3<double>(info.threads, a.lmax, a.nmax, go);
   }
   if (err != cudaSuccess) return err;
   return cudaGetLastError();
