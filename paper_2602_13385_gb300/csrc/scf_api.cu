@@ -30,6 +30,8 @@ struct scf_handle {
   bool gen = false;    // radial family of exponent alpha != 1: the general kernels 1 and 3
   ScfConst* d_tab = nullptr;  // their recurrence tables (device memory; allocated for every handle, so that
                               // scf_retune_alpha can move a handle to another exponent)
+  float4* d_cs = nullptr;     // [lmax + 1][nmax + 1] single-precision radial steps of kernel 3 (gbeta, hbeta, hratio)
+  float* d_tidf = nullptr;    // [n_prog][SCF_HOST_CAP][SCF_TIDAL_W] R-only values of the float tidal difference
   double* d_alpha = nullptr;  // [n_prog][4] exponent search: trial b, S0, S1, mass
   double* d_rc = nullptr;     // [n_prog][16] re-centring state (scf_recentre)
   double* d_sp = nullptr;     // [k3 blocks][kScalePoints + 1] partial sums of the b search
@@ -75,9 +77,7 @@ struct scf_handle {
   int bound_split = 1;
   int64_t bound_chunks = 0;              // pair-kernel i-blocks of the largest progenitor
   const uint8_t* step_mask = nullptr;    // coefficient set of scf_step (scf_set_mask)
-  // kernel 2's second level: chunk sums and arrival counters
-  double* d_k2z = nullptr;               // [n_prog][kK2MaxChunks][2*NC]
-  unsigned* d_k2cnt = nullptr;           // [n_prog][groups], zero between launches
+  double* d_Atmp = nullptr;              // [n_prog][2*NC] scratch coefficients
   ScfLaunchInfo k1d{}, k3d{};
   bool adj_ready = false;
   // launch timing (scf_profile)
@@ -225,6 +225,8 @@ K2Args k2_args(scf_handle* h, double* A_out, double* com, int mode) {
   a.nlm = h->nlm;
   a.F_out = h->d_F;
   a.f32 = h->cfg.precision == SCF_MIXED;
+  a.kscale_f = static_cast<const float*>(h->d_kscale);
+  a.tid_out = a.f32 ? h->d_tidf : nullptr;
   a.b_prog = h->d_b;
   a.G = h->cfg.G;
   a.aR_out = h->d_aR;
@@ -239,16 +241,6 @@ K2Args k2_args(scf_handle* h, double* A_out, double* com, int mode) {
   a.com = com;
   a.host = h->host;
   a.sub = h->k1.variant == 1 ? h->k1.win : 0;  // register-tiled kernel 1: float rows, one per window
-  // split each column group's rows over z blocks when the groups alone would
-  // leave SMs idle (about four blocks per SM), at least 32 rows per chunk
-  const int groups = scf_k2_groups(h->nc);
-  const int64_t rows = (int64_t)h->k1_blocks * (a.sub > 0 ? a.sub : 1) / std::max(1, h->n_prog);
-  const int64_t gp = (int64_t)groups * h->n_prog;
-  int z = (int)std::min<int64_t>(kK2MaxChunks, std::max<int64_t>(1, (4 * (int64_t)h->n_sm + gp - 1) / gp));
-  z = (int)std::min<int64_t>(z, std::max<int64_t>(1, rows / 32));
-  a.z = z;
-  a.zpart = h->d_k2z;
-  a.counters = h->d_k2cnt;
   a.cnext = mode == SCF_MODE_STEP && h->centre_ahead ? h->d_cnext : nullptr;
   return a;
 }
@@ -278,6 +270,8 @@ K3Args k3_args(scf_handle* h, const void* pos, void* vel, void* acc, const doubl
   a.tab = h->gen ? h->d_tab : nullptr;
   a.alpha = h->cfg.alpha;
   a.inv_alpha = 1.0 / h->cfg.alpha;
+  a.cs = h->d_cs;
+  a.tid = h->d_tidf;
   return a;
 }
 
@@ -302,6 +296,8 @@ int run_prep(scf_handle* h, const double* A, const double* com) {
   p.com = com;
   p.F_out = h->d_F;
   p.f32 = h->cfg.precision == SCF_MIXED;
+  p.kscale_f = static_cast<const float*>(h->d_kscale);
+  p.tid_out = p.f32 ? h->d_tidf : nullptr;
   p.b_prog = h->d_b;
   p.G = h->cfg.G;
   p.aR_out = h->d_aR;
@@ -368,6 +364,18 @@ Map3 make_map3(const std::vector<int64_t>& off, int n_prog, int64_t tb) {
 
 bool put(void* dst, const void* src, size_t bytes) {
   return bytes == 0 || cudaMemcpy(dst, src, bytes, cudaMemcpyHostToDevice) == cudaSuccess;
+}
+
+// Kernel 3's single-precision radial steps of the family in t, one float4
+// (gbeta, hbeta, hratio, 0) per (l, n): staged by every block with coalesced
+// 16-byte loads.
+bool put_steps(scf_handle* h, const ScfConst& t) {
+  const int nn = h->cfg.nmax + 1;
+  std::vector<float4> cs((size_t)(h->cfg.lmax + 1) * nn);
+  for (int l = 0; l <= h->cfg.lmax; ++l)
+    for (int n = 0; n < nn; ++n)
+      cs[(size_t)l * nn + n] = make_float4(t.gbetaf[l][n], t.hbetaf[l][n], t.hratiof[l][n], 0.f);
+  return put(h->d_cs, cs.data(), sizeof(float4) * cs.size());
 }
 
 // Kernel 1 launch shape: the simple kernel with a particle tile of 64, 128
@@ -572,13 +580,14 @@ int scf_init(const scf_config* cfg, int n_prog, const int64_t* offsets, const do
   const size_t o_key = take(sizeof(unsigned long long) * (size_t)h->n_total);
   const size_t o_tid = take(sizeof(double) * 16 * (size_t)n_prog);
   const size_t o_half = take(sizeof(double) * 4 * (size_t)n_prog);
-  const size_t o_k2z = take(sizeof(double) * kK2MaxChunks * 2 * (size_t)h->nc * n_prog);
-  const size_t o_k2c = take(sizeof(unsigned) * (size_t)scf_k2_groups(h->nc) * n_prog);
+  const size_t o_Atmp = take(sizeof(double) * 2 * (size_t)h->nc * n_prog);
   const size_t o_tab = take(sizeof(ScfConst));
   const size_t o_alpha = take(sizeof(double) * 4 * (size_t)n_prog);
   const size_t o_rc = take(sizeof(double) * 16 * (size_t)n_prog);
   const size_t o_sp = take(sizeof(double) * (kScalePoints + 1) * nb3);
   const size_t o_cn = take(sizeof(double) * kCentreW * (size_t)n_prog);
+  const size_t o_cs = take(sizeof(float4) * (size_t)(cfg->lmax + 1) * (cfg->nmax + 1));
+  const size_t o_tidf = take(sizeof(float) * SCF_HOST_CAP * SCF_TIDAL_W * (size_t)n_prog);
   if (cudaMalloc(&h->d_base, off) != cudaSuccess) {
     cudaGetLastError();
     return fail(SCF_ERR_OUT_OF_MEMORY);
@@ -606,20 +615,23 @@ int scf_init(const scf_config* cfg, int n_prog, const int64_t* offsets, const do
   h->d_key = reinterpret_cast<unsigned long long*>(base + o_key);
   h->d_tid = reinterpret_cast<double*>(base + o_tid);
   h->d_half = reinterpret_cast<double*>(base + o_half);
-  h->d_k2z = reinterpret_cast<double*>(base + o_k2z);
-  h->d_k2cnt = reinterpret_cast<unsigned*>(base + o_k2c);
+  h->d_Atmp = reinterpret_cast<double*>(base + o_Atmp);
   h->d_rc = reinterpret_cast<double*>(base + o_rc);
   h->d_sp = reinterpret_cast<double*>(base + o_sp);
   h->d_cnext = reinterpret_cast<double*>(base + o_cn);
+  h->d_cs = reinterpret_cast<float4*>(base + o_cs);
+  h->d_tidf = reinterpret_cast<float*>(base + o_tidf);
 
   h->d_tab = reinterpret_cast<ScfConst*>(base + o_tab);
   h->d_alpha = reinterpret_cast<double*>(base + o_alpha);
-  if (h->gen) {  // recurrence tables of the handle's radial family
+  {  // recurrence tables of the handle's radial family
     std::unique_ptr<ScfConst> t(new (std::nothrow) ScfConst);
     if (!t) return fail(SCF_ERR_OUT_OF_MEMORY);
     scf_make_const(t.get(), cfg->alpha);
-    if (!tables_finite(*t, cfg->lmax, cfg->nmax, cfg->precision == SCF_MIXED)) return fail(SCF_ERR_UNSUPPORTED);
-    if (!put(h->d_tab, t.get(), sizeof(ScfConst))) return fail(SCF_ERR_CUDA);
+    if (h->gen && !tables_finite(*t, cfg->lmax, cfg->nmax, cfg->precision == SCF_MIXED))
+      return fail(SCF_ERR_UNSUPPORTED);
+    if (h->gen && !put(h->d_tab, t.get(), sizeof(ScfConst))) return fail(SCF_ERR_CUDA);
+    if (!put_steps(h, *t)) return fail(SCF_ERR_CUDA);
   }
   std::vector<double> norm(2 * (size_t)h->nc), ksc(2 * (size_t)h->nc);
   scf_make_norm(cfg->nmax, cfg->lmax, norm.data(), cfg->alpha);
@@ -632,7 +644,6 @@ int scf_init(const scf_config* cfg, int n_prog, const int64_t* offsets, const do
   bool ok = ksc_ok && put(h->d_norm, norm.data(), sizeof(double) * norm.size()) &&
             put(h->d_b, bs.data(), sizeof(double) * n_prog) &&
             put(h->d_off, h->offsets.data(), sizeof(int64_t) * (n_prog + 1)) &&
-            cudaMemset(h->d_k2cnt, 0, sizeof(unsigned) * (size_t)scf_k2_groups(h->nc) * n_prog) == cudaSuccess &&
             cudaMemset(h->d_status, 0, sizeof(unsigned) * 4) == cudaSuccess &&
             cudaMemset(h->d_cnext, 0xff, sizeof(double) * kCentreW * (size_t)n_prog) == cudaSuccess &&  // NaN keys
             cudaMemset(h->d_A, 0, sizeof(double) * 2 * (size_t)h->nc * n_prog) == cudaSuccess;
@@ -1245,10 +1256,10 @@ int scf_recentre(scf_handle* h, void* pos, void* vel, void* acc, double* com, co
   // 2. the set's coefficients about it; the density's potential (K_nl A) in acc.w
   int rc = run_coeffs(h, pos, nullptr, nullptr, mask, h->d_A, nullptr, SCF_MODE_COEFFS);
   if (rc != SCF_OK) return rc;
-  if (cuda_fail(scf_scale_k_launch(h->d_A, h->d_k2z, h->cfg.nmax, h->cfg.lmax, h->n_prog, h->cfg.alpha,
+  if (cuda_fail(scf_scale_k_launch(h->d_A, h->d_Atmp, h->cfg.nmax, h->cfg.lmax, h->n_prog, h->cfg.alpha,
                                    h->stream)) != SCF_OK)
     return SCF_ERR_CUDA;
-  rc = run_prep(h, h->d_k2z, nullptr);
+  rc = run_prep(h, h->d_Atmp, nullptr);
   if (rc == SCF_OK) rc = run_forces(h, pos, nullptr, acc, nullptr, SCF_MODE_COEFFS);
   if (rc != SCF_OK) return rc;
   // 3. core radius and velocity, the frame moved to (x_c, V_core)
@@ -1331,12 +1342,14 @@ double dln_i00(double al) {
 int set_alpha(scf_handle* h, double alpha) {
   if (cudaStreamSynchronize(h->stream) != cudaSuccess) return SCF_ERR_CUDA;
   const bool gen = alpha != 1.0;
-  if (gen) {
+  {
     std::unique_ptr<ScfConst> t(new (std::nothrow) ScfConst);
     if (!t) return SCF_ERR_OUT_OF_MEMORY;
     scf_make_const(t.get(), alpha);
-    if (!tables_finite(*t, h->cfg.lmax, h->cfg.nmax, h->cfg.precision == SCF_MIXED)) return SCF_ERR_UNSUPPORTED;
-    if (!put(h->d_tab, t.get(), sizeof(ScfConst))) return SCF_ERR_CUDA;
+    if (gen && !tables_finite(*t, h->cfg.lmax, h->cfg.nmax, h->cfg.precision == SCF_MIXED))
+      return SCF_ERR_UNSUPPORTED;
+    if (gen && !put(h->d_tab, t.get(), sizeof(ScfConst))) return SCF_ERR_CUDA;
+    if (!put_steps(h, *t)) return SCF_ERR_CUDA;
   }
   std::vector<double> norm(2 * (size_t)h->nc), ksc(2 * (size_t)h->nc);
   scf_make_norm(h->cfg.nmax, h->cfg.lmax, norm.data(), alpha);

@@ -796,31 +796,47 @@ __global__ void __launch_bounds__(32) k_centre_next(CentreArgs a) {
   }
 }
 
-__device__ __forceinline__ void write_force_pair(void* F, int f32, size_t i, double c, double s) {
-  if (f32) reinterpret_cast<float2*>(F)[i] = make_float2((float)c, (float)s);
-  else reinterpret_cast<double2*>(F)[i] = make_double2(c, s);
+// Force-coefficient pair i of progenitor p (pi = p NC + i); single precision
+// carries the field kernel's radial scale gscale (kscale_f[2i]).
+__device__ __forceinline__ void write_force_pair(void* F, int f32, const float* kscale_f, size_t pi, int i, double c,
+                                                 double s) {
+  if (f32) {
+    const double g = kscale_f[2 * i];
+    reinterpret_cast<float2*>(F)[pi] = make_float2((float)(c * g), (float)(s * g));
+  } else {
+    reinterpret_cast<double2*>(F)[pi] = make_double2(c, s);
+  }
 }
 
-// Kernel 2.  Block (groups, p, 0) steps the centre of progenitor p and
+// The R-only values of the single-precision tidal difference at centre c,
+// component `lane` (< host.n) of progenitor p.
+__device__ __forceinline__ void write_tidal_prep(const ScfHostParams& hp, float* tid_out, int p, int lane,
+                                                 const double* c) {
+  if (tid_out && lane < hp.n)
+    scf_tidal_prep_f32(hp, lane, (float)c[0], (float)c[1], (float)c[2],
+                       tid_out + ((size_t)p * SCF_HOST_CAP + lane) * SCF_TIDAL_W);
+}
+
+// Kernel 2.  Block (groups, p) steps the centre of progenitor p and
 // evaluates a_host there (a chain of dependent double-precision operations
-// in one thread), concurrently with the reduction blocks.
-// Block (g < groups, p, z): coefficient pairs 32g .. 32g + 31 (threadIdx.x,
-// one 128-byte row segment per warp load) of progenitor p, over chunk z of
-// the progenitor's partial rows, in K2_SLICES row slices (threadIdx.y): slice
-// y adds rows y, y + K2_SLICES, ... of the chunk in order; the slices are
-// combined by a fixed binary tree.  With more than one chunk, each block
-// stores its chunk sums and the last block of the column group to finish
-// (an arrival counter, nobody waits) adds the chunks in chunk order.  Every
-// sum has a fixed order, so the result is the same on every run.
-constexpr int K2_X = 32, K2_SLICES = 8;
+// in one warp), concurrently with the reduction blocks.
+// Block (g < groups, p): coefficient pairs 32g .. 32g + 31 (threadIdx.x, one
+// 128-byte row segment per warp load) of progenitor p over all its partial
+// rows, in K2_SLICES row slices (threadIdx.y): slice y adds rows y,
+// y + K2_SLICES, ... in order, K2_BATCH rows at a time whose loads are all
+// issued before the first add (the kernel is a chain of memory latencies,
+// not of bandwidth: one round trip per batch, one batch at the usual row
+// counts); the slices are combined by a fixed binary tree.  The epilogue's
+// inputs (normalisation, 1/N_lm, b) are loaded before the rows.  Every sum
+// has a fixed order, so the result is the same on every run.
+constexpr int K2_X = 32, K2_SLICES = 32;
 __global__ void __launch_bounds__(K2_X * K2_SLICES) k2_reduce(K2Args a) {
   __shared__ double s_c[K2_SLICES][K2_X], s_s[K2_SLICES][K2_X];
-  __shared__ int s_last;
-  const int p = blockIdx.y, z = blockIdx.z, Z = gridDim.z;
+  const int p = blockIdx.y;
   const int x = threadIdx.x, y = threadIdx.y;
   const int groups = gridDim.x - 1;
   if ((int)blockIdx.x == groups) {  // the centre block: its first warp
-    if (z == 0 && y == 0 && a.host.n > 0 && a.com != nullptr) {
+    if (y == 0 && a.host.n > 0 && a.com != nullptr) {
       double c[6], an[3];
       for (int d = 0; d < 6; ++d) c[d] = a.com[6 * p + d];
       if (a.mode == SCF_MODE_STEP) {
@@ -843,43 +859,68 @@ __global__ void __launch_bounds__(K2_X * K2_SLICES) k2_reduce(K2Args a) {
         if (a.aR_out)
           for (int d = 0; d < 3; ++d) a.aR_out[4 * p + d] = an[d];
       }
+      write_tidal_prep(a.host, a.tid_out, p, x, c);
     }
     return;
   }
   const int i = blockIdx.x * K2_X + x;
   const size_t stride = 2 * (size_t)a.nc;
+  // the epilogue's factors first: their latency overlaps the row loads
+  double nS = 0.0, nT = 0.0, w = 0.0;
+  if (y == 0 && i < a.nc) {
+    nS = a.norm[i];
+    nT = a.norm[a.nc + i];
+    if (a.F_out) w = -a.G / a.b_prog[p] * c_tab.inv_nlm[i % a.nlm];
+  }
   double sc = 0.0, ss = 0.0;
   if (i < a.nc) {
-    // this block's share of the progenitor's rows: chunk z of Z
     const int mul = a.sub == 0 ? 1 : a.sub;
     const int R0 = a.prog_blk_off[p] * mul, R1 = a.prog_blk_off[p + 1] * mul;
-    const int chunk = (R1 - R0 + Z - 1) / Z;
-    const int r0 = min(R1, R0 + z * chunk), r1 = min(R1, r0 + chunk);
     if (a.sub == 0) {  // double rows, one per block
-#pragma unroll 4
-      for (int r = r0 + y; r < r1; r += K2_SLICES) {
-        const double* src = a.partials + (size_t)r * stride + i;
-        sc += src[0];
-        ss += src[a.nc];
+      constexpr int B = 8;
+      const double* P = a.partials + i;
+      for (int base = R0 + y; base < R1; base += B * K2_SLICES) {
+        double vc[B], vs[B];
+#pragma unroll
+        for (int k = 0; k < B; ++k) {
+          const int r = base + k * K2_SLICES;
+          vc[k] = r < R1 ? P[(size_t)r * stride] : 0.0;
+          vs[k] = r < R1 ? P[(size_t)r * stride + a.nc] : 0.0;
+        }
+#pragma unroll
+        for (int k = 0; k < B; ++k) {
+          sc += vc[k];
+          ss += vs[k];
+        }
       }
     } else {  // float rows, a.sub per block; T_nl0 is not stored
       // a slice's rows are added as an unevaluated float pair (hi, lo) with an
       // error-free two-sum: single-precision arithmetic (the FP64 pipe is 1/64
       // of the FP32 one) at about twice single precision
+      constexpr int B = 16;
       int lm = i % a.nlm, l = 0;
       while ((l + 1) * (l + 2) / 2 <= lm) ++l;
       const bool has_t = lm != scf_lm(l, 0);
-      const float* P = reinterpret_cast<const float*>(a.partials);
+      const float* P = reinterpret_cast<const float*>(a.partials) + i;
       float ch = 0.f, cl = 0.f, th = 0.f, tl = 0.f;
       auto two_sum = [](float& hi, float& lo, float v) {
         const float s = hi + v, bp = s - hi;
         lo += (hi - (s - bp)) + (v - bp);
         hi = s;
       };
-#pragma unroll 4
-      for (int r = r0 + y; r < r1; r += K2_SLICES) {
-        two_sum(ch, cl, P[(size_t)r * stride + i]);
-        if (has_t) two_sum(th, tl, P[(size_t)r * stride + a.nc + i]);
+      for (int base = R0 + y; base < R1; base += B * K2_SLICES) {
+        float vc[B], vs[B];
+#pragma unroll
+        for (int k = 0; k < B; ++k) {
+          const int r = base + k * K2_SLICES;
+          vc[k] = r < R1 ? P[(size_t)r * stride] : 0.f;
+          vs[k] = r < R1 && has_t ? P[(size_t)r * stride + a.nc] : 0.f;
+        }
+#pragma unroll
+        for (int k = 0; k < B; ++k) {
+          two_sum(ch, cl, vc[k]);
+          two_sum(th, tl, vs[k]);
+        }
       }
       sc = (double)ch + (double)cl;
       ss = (double)th + (double)tl;
@@ -896,40 +937,12 @@ __global__ void __launch_bounds__(K2_X * K2_SLICES) k2_reduce(K2Args a) {
     }
     __syncthreads();
   }
-  sc = s_c[0][x];
-  ss = s_s[0][x];
-  if (Z > 1) {
-    double* zp = a.zpart + (size_t)p * Z * stride;
-    if (y == 0 && i < a.nc) {
-      zp[(size_t)z * stride + i] = sc;
-      zp[(size_t)z * stride + a.nc + i] = ss;
-    }
-    __threadfence();
-    __syncthreads();
-    unsigned* cnt = a.counters + (size_t)p * groups + blockIdx.x;
-    if (x == 0 && y == 0) s_last = atomicAdd(cnt, 1u) == (unsigned)(Z - 1);
-    __syncthreads();
-    if (!s_last) return;
-    __threadfence();
-    if (y == 0 && i < a.nc) {
-      sc = __ldcg(zp + i);
-      ss = __ldcg(zp + a.nc + i);
-      for (int k = 1; k < Z; ++k) {
-        sc += __ldcg(zp + (size_t)k * stride + i);
-        ss += __ldcg(zp + (size_t)k * stride + a.nc + i);
-      }
-    }
-    if (x == 0 && y == 0) *cnt = 0u;  // ready for the next launch
-  }
   if (y == 0 && i < a.nc) {
-    const double S = sc * a.norm[i], T = ss * a.norm[a.nc + i];
+    const double S = s_c[0][x] * nS, T = s_s[0][x] * nT;
     double* A = a.A_out + (size_t)p * stride;
     A[i] = S;
     A[a.nc + i] = T;
-    if (a.F_out) {
-      const double w = -a.G / a.b_prog[p] * c_tab.inv_nlm[i % a.nlm];
-      write_force_pair(a.F_out, a.f32, (size_t)p * a.nc + i, w * S, w * T);
-    }
+    if (a.F_out) write_force_pair(a.F_out, a.f32, a.kscale_f, (size_t)p * a.nc + i, i, w * S, w * T);
   }
 }
 
@@ -939,12 +952,15 @@ __global__ void k_prep(PrepArgs a) {
   if (i < a.nc) {
     const double* A = a.A + (size_t)p * 2 * a.nc;
     const double w = -a.G / a.b_prog[p] * c_tab.inv_nlm[i % a.nlm];
-    write_force_pair(a.F_out, a.f32, (size_t)p * a.nc + i, w * A[i], w * A[a.nc + i]);
+    write_force_pair(a.F_out, a.f32, a.kscale_f, (size_t)p * a.nc + i, i, w * A[i], w * A[a.nc + i]);
   }
-  if (blockIdx.x == 0 && threadIdx.x == 0 && a.host.n > 0 && a.com != nullptr) {
+  if (blockIdx.x == 0 && a.host.n > 0 && a.com != nullptr) {
     const double* c = a.com + 6 * p;
-    double* r = a.aR_out + 4 * p;
-    scf_host_accel(a.host, c[0], c[1], c[2], r[0], r[1], r[2]);
+    if (threadIdx.x == 0) {
+      double* r = a.aR_out + 4 * p;
+      scf_host_accel(a.host, c[0], c[1], c[2], r[0], r[1], r[2]);
+    }
+    write_tidal_prep(a.host, a.tid_out, p, threadIdx.x, c);
   }
 }
 
@@ -1079,11 +1095,8 @@ cudaError_t scf_k1_launch(int precision, const K1Args& a, int blocks, const ScfL
   return cudaGetLastError();
 }
 
-int scf_k2_groups(int nc) { return (nc + K2_X - 1) / K2_X; }
-
 cudaError_t scf_k2_launch(const K2Args& a, cudaStream_t s) {
-  const int Z = (a.zpart && a.counters && a.z > 1) ? a.z : 1;
-  dim3 grid((a.nc + K2_X - 1) / K2_X + 1, a.n_prog, Z);  // + the centre block
+  dim3 grid((a.nc + K2_X - 1) / K2_X + 1, a.n_prog);  // + the centre block
   k2_reduce<<<grid, dim3(K2_X, K2_SLICES), 0, s>>>(a);
   return cudaGetLastError();
 }

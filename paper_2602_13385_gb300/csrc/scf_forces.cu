@@ -57,11 +57,6 @@ __device__ __forceinline__ T k3_hbeta(const K3Args& a, int l, int n) {
   if constexpr (GEN) return sizeof(T) == 8 ? (T)__ldg(&a.tab->hbeta[l][n]) : (T)__ldg(&a.tab->hbetaf[l][n]);
   else return thbeta<T>(l, n);
 }
-template <bool GEN>
-__device__ __forceinline__ float k3_hratio(const K3Args& a, int l, int n) {
-  if constexpr (GEN) return __ldg(&a.tab->hratiof[l][n]);
-  else return c_tab.hratiof[l][n];
-}
 __device__ __forceinline__ double k3_pow(double x, double y) { return pow(x, y); }
 __device__ __forceinline__ float k3_pow(float x, float y) { return powf(x, y); }
 
@@ -84,28 +79,24 @@ __device__ __forceinline__ void k3_body(const K3Args& a) {
   V4* F = reinterpret_cast<V4*>(smem_raw);
   V2* F2 = reinterpret_cast<V2*>(smem_raw);
   // single precision: the per-(l, n) recurrence constants (gbeta, hbeta,
-  // hratio) staged beside the coefficients, one broadcast shared load per
-  // radial step instead of three constant-bank loads with runtime indices
+  // hratio) staged beside the coefficients from the handle's table (coalesced
+  // 16-byte loads), one broadcast shared load per radial step instead of
+  // three constant-bank loads with runtime indices
   float4* CS = reinterpret_cast<float4*>(smem_raw + ((sizeof(V2) * (size_t)a.nc + 15) & ~size_t(15)));
   __shared__ double s_R[3], s_aR[3];
   const int tid = threadIdx.x;
   const int prog = a.blk_prog[blockIdx.x];
   const double b = a.b_prog[prog];
-  if constexpr (kF2) {
-    const int nn = a.nmax + 1;
-    for (int i = tid; i < (a.lmax + 1) * nn; i += K3_TB) {
-      const int l = i / nn, n = i - l * nn;
-      CS[i] = make_float4(k3_gbeta<float, GEN>(a, l, n), k3_hbeta<float, GEN>(a, l, n), k3_hratio<GEN>(a, l, n), 0.f);
-    }
-  }
+  if constexpr (kF2)
+    for (int i = tid; i < (a.lmax + 1) * (a.nmax + 1); i += K3_TB) CS[i] = a.cs[i];
   {
     const V2* Fg = reinterpret_cast<const V2*>(a.F) + (size_t)prog * a.nc;
     const V2* Sg = reinterpret_cast<const V2*>(a.kscale);
     for (int i = tid; i < a.nc; i += K3_TB) {
-      const V2 f = Fg[i], sc = Sg[i];
       if constexpr (kF2) {
-        F2[i] = V2{f.x * sc.x, f.y * sc.x};
+        F2[i] = Fg[i];  // kernel 2 wrote them times gscale
       } else {
+        const V2 f = Fg[i], sc = Sg[i];
         V4 q;
         q.x = f.x * sc.x;
         q.y = f.y * sc.x;
@@ -120,12 +111,12 @@ __device__ __forceinline__ void k3_body(const K3Args& a) {
     s_R[tid] = has_host ? a.com[6 * prog + tid] : 0.0;
     s_aR[tid] = has_host ? a.aR[4 * prog + tid] : 0.0;
   }
-  // single precision: the values of the tidal differences that depend on R alone
+  // single precision: the values of the tidal differences that depend on R
+  // alone, formed by kernel 2 (or the force-coefficient set-up) for this R
   __shared__ float s_tid[kF2 ? SCF_HOST_CAP : 1][SCF_TIDAL_W];
   if constexpr (kF2) {
-    if (has_host && tid < a.host.n)
-      scf_tidal_prep_f32(a.host, tid, (float)a.com[6 * prog], (float)a.com[6 * prog + 1], (float)a.com[6 * prog + 2],
-                         s_tid[tid]);
+    if (has_host && tid < a.host.n * SCF_TIDAL_W)
+      (&s_tid[0][0])[tid] = a.tid[(size_t)prog * SCF_HOST_CAP * SCF_TIDAL_W + tid];
   }
   __syncthreads();
 

@@ -71,9 +71,15 @@ struct K2Args {
   double* com;              // [n_prog][6] (step mode with host)
   ScfHostParams host;
   // optional: force coefficients F = -G {S,T} / (b N_lm) as (cos, sin) pairs
-  // of the field kernel's element type, and a_host(R) per progenitor
+  // of the field kernel's element type (single precision: times gscale[l][n],
+  // the scale of the field kernel's radial recurrence), and a_host(R) per
+  // progenitor
   void* F_out;              // [n_prog][NC] float2 (f32) or double2, or null
   int f32;                  // element type of F_out
+  const float* kscale_f;    // f32: [NC] (gscale, hscale) pairs
+  // f32 with a host: the values of the single-precision tidal difference that
+  // depend on R alone, [n_prog][SCF_HOST_CAP][SCF_TIDAL_W] (scf_tidal_prep_f32)
+  float* tid_out;
   const double* b_prog;
   double G;
   double* aR_out;           // [n_prog][4], or null
@@ -81,20 +87,11 @@ struct K2Args {
   // floats (sub rows per block, one per window of the register-tiled kernel 1)
   // without the T_nl0 entries (read as 0)
   int sub;
-  // optional second level: z > 1 blocks per column group each add a chunk of
-  // the rows into zpart ([n_prog][z][2*NC] doubles); the last to finish (per
-  // counters[n_prog][groups], zero between launches) adds the chunks in order
-  int z;
-  double* zpart;
-  unsigned* counters;
   // optional (step mode): centre steps computed ahead, [n_prog][kCentreW]
   // doubles (see CentreArgs); the centre block takes entry p's result when
   // its key equals the state it is about to step
   const double* cnext;
 };
-// Column groups of kernel 2 for NC coefficients (the counters per progenitor).
-int scf_k2_groups(int nc);
-constexpr int kK2MaxChunks = 16;
 
 // The centre's next kick-drift-kick computed ahead (beside kernel 3, on a
 // second stream): entry p of cnext holds [0, 6) the state it started from
@@ -118,6 +115,8 @@ struct PrepArgs {
   const double* com;        // [n_prog][6] or null
   void* F_out;
   int f32;
+  const float* kscale_f;    // as in K2Args
+  float* tid_out;           // as in K2Args
   const double* b_prog;
   double G;
   double* aR_out;
@@ -146,6 +145,11 @@ struct K3Args {
   AdjArgs adj;
   const ScfConst* tab;  // radial family of exponent alpha != 1, as in K1Args
   double alpha, inv_alpha;
+  // single precision: the per-(l, n) radial recurrence constants (gbeta,
+  // hbeta, hratio, 0) of the handle's family, [lmax + 1][nmax + 1], and the
+  // R-only values of the tidal difference that kernel 2 left (see K2Args)
+  const float4* cs;
+  const float* tid;
 };
 
 // Adjoint of the tidal term and of the centre orbit at one level of the reverse sweep.
