@@ -93,6 +93,7 @@ struct scf_handle {
   // the centre's next kick-drift-kick computed beside kernel 3 (SCF_OPT_CENTRE_AHEAD)
   bool centre_ahead = true;
   double* d_cnext = nullptr;             // [n_prog][kCentreW], keys NaN until computed
+  float* d_tidnext = nullptr;            // [n_prog][SCF_HOST_CAP][SCF_TIDAL_W] with d_cnext (single precision)
   cudaStream_t side_stream = nullptr;                 // created at the greatest stream priority
   int side_priority = 0;
   cudaEvent_t side_ev[2] = {nullptr, nullptr};
@@ -242,6 +243,7 @@ K2Args k2_args(scf_handle* h, double* A_out, double* com, int mode) {
   a.host = h->host;
   a.sub = h->k1.variant == 1 ? h->k1.win : 0;  // register-tiled kernel 1: float rows, one per window
   a.cnext = mode == SCF_MODE_STEP && h->centre_ahead ? h->d_cnext : nullptr;
+  a.tid_next = a.cnext && a.f32 ? h->d_tidnext : nullptr;
   return a;
 }
 
@@ -588,6 +590,7 @@ int scf_init(const scf_config* cfg, int n_prog, const int64_t* offsets, const do
   const size_t o_cn = take(sizeof(double) * kCentreW * (size_t)n_prog);
   const size_t o_cs = take(sizeof(float4) * (size_t)(cfg->lmax + 1) * (cfg->nmax + 1));
   const size_t o_tidf = take(sizeof(float) * SCF_HOST_CAP * SCF_TIDAL_W * (size_t)n_prog);
+  const size_t o_tidn = take(sizeof(float) * SCF_HOST_CAP * SCF_TIDAL_W * (size_t)n_prog);
   if (cudaMalloc(&h->d_base, off) != cudaSuccess) {
     cudaGetLastError();
     return fail(SCF_ERR_OUT_OF_MEMORY);
@@ -621,6 +624,7 @@ int scf_init(const scf_config* cfg, int n_prog, const int64_t* offsets, const do
   h->d_cnext = reinterpret_cast<double*>(base + o_cn);
   h->d_cs = reinterpret_cast<float4*>(base + o_cs);
   h->d_tidf = reinterpret_cast<float*>(base + o_tidf);
+  h->d_tidnext = reinterpret_cast<float*>(base + o_tidn);
 
   h->d_tab = reinterpret_cast<ScfConst*>(base + o_tab);
   h->d_alpha = reinterpret_cast<double*>(base + o_alpha);
@@ -700,6 +704,7 @@ int launch_step(scf_handle* h, void* pos, void* vel, void* acc, double* com) {
     c.com = com;
     c.aR = h->d_aR;
     c.cnext = h->d_cnext;
+    c.tid_next = h->cfg.precision == SCF_MIXED ? h->d_tidnext : nullptr;
     c.dt = h->cfg.dt;
     c.n_prog = h->n_prog;
     c.host = h->host;

@@ -778,6 +778,15 @@ __device__ __forceinline__ bool same_bits(double x, double y) {
   return __double_as_longlong(x) == __double_as_longlong(y);
 }
 
+// The R-only values of the single-precision tidal difference at centre c,
+// component `lane` (< host.n) of progenitor p.
+__device__ __forceinline__ void write_tidal_prep(const ScfHostParams& hp, float* tid_out, int p, int lane,
+                                                 const double* c) {
+  if (tid_out && lane < hp.n)
+    scf_tidal_prep_f32(hp, lane, (float)c[0], (float)c[1], (float)c[2],
+                       tid_out + ((size_t)p * SCF_HOST_CAP + lane) * SCF_TIDAL_W);
+}
+
 // The next step's centre kick-drift-kick, one warp per progenitor, from the
 // state and a_host(R) that kernel 2 of this step left (see CentreArgs).
 __global__ void __launch_bounds__(32) k_centre_next(CentreArgs a) {
@@ -789,6 +798,7 @@ __global__ void __launch_bounds__(32) k_centre_next(CentreArgs a) {
   if (threadIdx.x == 0)
     for (int d = 0; d < 6; ++d) out[d] = c[d];
   com_kdk_from(a.host, c, a.dt, a0, an);
+  write_tidal_prep(a.host, a.tid_next, p, threadIdx.x, c);
   if (threadIdx.x == 0) {
     for (int d = 0; d < 6; ++d) out[6 + d] = c[d];
     for (int d = 0; d < 3; ++d) out[12 + d] = an[d];
@@ -797,25 +807,18 @@ __global__ void __launch_bounds__(32) k_centre_next(CentreArgs a) {
 }
 
 // Force-coefficient pair i of progenitor p (pi = p NC + i); single precision
-// carries the field kernel's radial scale gscale (kscale_f[2i]).
+// carries the field kernel's radial scale gscale (kscale_f[2i]; null: already
+// applied by the caller).
 __device__ __forceinline__ void write_force_pair(void* F, int f32, const float* kscale_f, size_t pi, int i, double c,
                                                  double s) {
   if (f32) {
-    const double g = kscale_f[2 * i];
+    const double g = kscale_f ? (double)kscale_f[2 * i] : 1.0;
     reinterpret_cast<float2*>(F)[pi] = make_float2((float)(c * g), (float)(s * g));
   } else {
     reinterpret_cast<double2*>(F)[pi] = make_double2(c, s);
   }
 }
 
-// The R-only values of the single-precision tidal difference at centre c,
-// component `lane` (< host.n) of progenitor p.
-__device__ __forceinline__ void write_tidal_prep(const ScfHostParams& hp, float* tid_out, int p, int lane,
-                                                 const double* c) {
-  if (tid_out && lane < hp.n)
-    scf_tidal_prep_f32(hp, lane, (float)c[0], (float)c[1], (float)c[2],
-                       tid_out + ((size_t)p * SCF_HOST_CAP + lane) * SCF_TIDAL_W);
-}
 
 // Kernel 2.  Block (groups, p) steps the centre of progenitor p and
 // evaluates a_host there (a chain of dependent double-precision operations
@@ -850,8 +853,17 @@ __global__ void __launch_bounds__(K2_X * K2_SLICES) k2_reduce(K2Args a) {
         } else {
           com_kdk(a.host, c, a.dt, an);
         }
+        if (a.tid_out) {  // the tidal difference's R-only values, computed ahead or here
+          constexpr int TW = SCF_HOST_CAP * SCF_TIDAL_W;
+          if (hit && a.tid_next) {
+            for (int k = x; k < TW; k += 32) a.tid_out[(size_t)p * TW + k] = a.tid_next[(size_t)p * TW + k];
+          } else {
+            write_tidal_prep(a.host, a.tid_out, p, x, c);
+          }
+        }
       } else {
         host_accel_warp(a.host, c[0], c[1], c[2], an[0], an[1], an[2]);
+        write_tidal_prep(a.host, a.tid_out, p, x, c);
       }
       if (x == 0) {
         if (a.mode == SCF_MODE_STEP)
@@ -859,7 +871,6 @@ __global__ void __launch_bounds__(K2_X * K2_SLICES) k2_reduce(K2Args a) {
         if (a.aR_out)
           for (int d = 0; d < 3; ++d) a.aR_out[4 * p + d] = an[d];
       }
-      write_tidal_prep(a.host, a.tid_out, p, x, c);
     }
     return;
   }
@@ -870,7 +881,10 @@ __global__ void __launch_bounds__(K2_X * K2_SLICES) k2_reduce(K2Args a) {
   if (y == 0 && i < a.nc) {
     nS = a.norm[i];
     nT = a.norm[a.nc + i];
-    if (a.F_out) w = -a.G / a.b_prog[p] * c_tab.inv_nlm[i % a.nlm];
+    if (a.F_out) {
+      w = -a.G / a.b_prog[p] * c_tab.inv_nlm[i % a.nlm];
+      if (a.f32) w *= (double)a.kscale_f[2 * i];  // single precision: F carries gscale
+    }
   }
   double sc = 0.0, ss = 0.0;
   if (i < a.nc) {
@@ -942,7 +956,7 @@ __global__ void __launch_bounds__(K2_X * K2_SLICES) k2_reduce(K2Args a) {
     double* A = a.A_out + (size_t)p * stride;
     A[i] = S;
     A[a.nc + i] = T;
-    if (a.F_out) write_force_pair(a.F_out, a.f32, a.kscale_f, (size_t)p * a.nc + i, i, w * S, w * T);
+    if (a.F_out) write_force_pair(a.F_out, a.f32, nullptr, (size_t)p * a.nc + i, i, w * S, w * T);
   }
 }
 

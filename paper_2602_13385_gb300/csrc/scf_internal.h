@@ -80,6 +80,7 @@ struct K2Args {
   // f32 with a host: the values of the single-precision tidal difference that
   // depend on R alone, [n_prog][SCF_HOST_CAP][SCF_TIDAL_W] (scf_tidal_prep_f32)
   float* tid_out;
+  const float* tid_next;    // the same for the centre steps computed ahead (with cnext), or null
   const double* b_prog;
   double G;
   double* aR_out;           // [n_prog][4], or null
@@ -103,6 +104,7 @@ struct CentreArgs {
   const double* com;        // [n_prog][6]
   const double* aR;         // [n_prog][4]
   double* cnext;            // [n_prog][kCentreW]
+  float* tid_next;          // f32: the tidal difference's R-only values at the stepped R, or null
   double dt;
   int n_prog;
   ScfHostParams host;
