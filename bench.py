@@ -482,16 +482,14 @@ def run_line(name, args, steps, torch, barrier, world, rank, local, peaks, oracl
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
     stream = sim.stream
 
-    with torch.cuda.stream(stream):
-        for i in range(args.warmup):
-            flush.fill_(float(i))
-            sim.step(p, v, a, com=use_com, nsteps=1)
-        torch.cuda.synchronize()
-        sim.profile(True)
-        sim.profile_read()
+    def timed_steps(profile):
+        # `steps` steps, L2 flushed before each, CUDA events on the handle's
+        # stream around each step; with profile, per-kernel events too (plain
+        # launches: the captured graph of a step holds no timing events)
+        if profile:
+            sim.profile(True)
+            sim.profile_read()
         ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
-        sampler = ClockSampler(local)
-        sampler.start()
         barrier()
         torch.cuda.synchronize()
         for i in range(steps):
@@ -501,10 +499,26 @@ def run_line(name, args, steps, torch, barrier, world, rank, local, peaks, oracl
             ev[i][1].record(stream)
         torch.cuda.synchronize()
         barrier()
-        clocks = sampler.stop()
-        ms_total = sum(e0.elapsed_time(e1) for e0, e1 in ev)
-        kms, kcount = sim.profile_read()
+        ms = sum(e0.elapsed_time(e1) for e0, e1 in ev)
+        if not profile:
+            return ms, None, None
+        kms_, kcount_ = sim.profile_read()
         sim.profile(False)
+        return ms, kms_, kcount_
+
+    with torch.cuda.stream(stream):
+        for i in range(args.warmup):
+            flush.fill_(float(i))
+            sim.step(p, v, a, com=use_com, nsteps=1)
+        torch.cuda.synchronize()
+        sampler = ClockSampler(local)
+        sampler.start()
+        # the step rate: one captured graph per step, as scf_step runs it
+        ms_total, _, _ = timed_steps(False)
+        # the kernels' durations: the same steps again with an event pair
+        # around every kernel launch
+        ms_prof, kms, kcount = timed_steps(True)
+        clocks = sampler.stop()
     rc, st = sim.status()
     if rc != 0:
         raise RuntimeError(f"device status {st} after the timed steps of {name}")
@@ -567,6 +581,9 @@ def run_line(name, args, steps, torch, barrier, world, rank, local, peaks, oracl
                 "algorithmic_flops_per_launch": flops,
                 "algorithmic_bytes_per_launch": wl.n * (k3b if dom == 2 else k1b),
                 "kernels_ms_per_step": {"k1_partials": per_k[0], "k2_reduce": per_k[1], "k3_forces": per_k[2]},
+                "kernel_timing": f"a second timed pass of {steps} steps with a CUDA-event pair around every "
+                                 f"kernel (plain launches, {ms_prof / steps:.4f} ms per step against "
+                                 f"{ms_total / steps:.4f} ms with the captured graph)",
                 "whole_step": {"achieved": step_flops / (ms_step * 1e-3) / 1e12, "peak": peak,
                                "frac": step_flops / (ms_step * 1e-3) / 1e12 / peak,
                                "algorithmic_flops_per_step": step_flops,
@@ -580,7 +597,10 @@ def run_line(name, args, steps, torch, barrier, world, rank, local, peaks, oracl
                  if precision == "fp64" else "f32+f64",
         "data": "synthetic (seeded sample, see config.workload)",
         "config": workload_config(wl, precision, name),
-        "roofline": roofline, "e2e": e2e, "gpu_launches": int(sum(kcount)), "clocks": clocks,
+        "roofline": roofline, "e2e": e2e,
+        # the step kernels of the timed pass (3 per step), plus the centre step
+        # computed ahead on the side stream when there is a host
+        "gpu_launches": int(sum(kcount)) * (4 if use_com is not None else 3) // 3, "clocks": clocks,
         "kernel_shapes": dict(sim.tiles(), autotuned=tuning is not None,
                               candidates_ms=None if tuning is None else tuning["ms"]),
         "src_hash": src_hash(),

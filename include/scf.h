@@ -257,7 +257,8 @@ int scf_set_option(scf_handle* h, int option, int value);
 int scf_get_option(const scf_handle* h, int option, int* value);
 
 /* Autotuner: times every allowed SCF_OPT_K1_TILE with the coefficient pass
- * and every SCF_OPT_K3_BLOCK with the field pass (2 warm-up + reps timed calls
+ * and every SCF_OPT_K3_BLOCK with the field pass of a step (its closing half
+ * kick applied to acc, which stands in for the velocities) (2 warm-up + reps timed calls
  * each, CUDA events on the handle's stream) on the caller's particles, and
  * keeps the fastest of each (in SCF_MIXED the register-tiled kernel 1 is a
  * fourth candidate).  pos, com as for scf_forces; acc is overwritten.

@@ -242,6 +242,7 @@ K2Args k2_args(scf_handle* h, double* A_out, double* com, int mode) {
   a.com = com;
   a.host = h->host;
   a.sub = h->k1.variant == 1 ? h->k1.win : 0;  // register-tiled kernel 1: float rows, one per window
+  a.n_sm = h->n_sm;
   a.cnext = mode == SCF_MODE_STEP && h->centre_ahead ? h->d_cnext : nullptr;
   a.tid_next = a.cnext && a.f32 ? h->d_tidnext : nullptr;
   return a;
@@ -980,7 +981,9 @@ int scf_autotune(scf_handle* h, const void* pos, const double* com, void* acc, i
   for (int i = 0; i < 4 && rc == SCF_OK; ++i) {
     if (use_k3(h, k3_candidates[i]) != SCF_OK) continue;
     double ms = 0.0;
-    rc = time_it([&] { return run_forces(h, pos, nullptr, acc, com, SCF_MODE_COEFFS); }, &ms);
+    // the field pass as a step runs it, with its closing half kick (acc, which
+    // is scratch here, standing in for the velocities)
+    rc = time_it([&] { return run_forces(h, pos, acc, acc, com, SCF_MODE_STEP); }, &ms);
     if (ms_out) ms_out[k3_slot[i]] = ms;
     if (rc == SCF_OK && ms < best3) {
       best3 = ms;

@@ -825,16 +825,19 @@ __device__ __forceinline__ void write_force_pair(void* F, int f32, const float* 
 // in one warp), concurrently with the reduction blocks.
 // Block (g < groups, p): coefficient pairs 32g .. 32g + 31 (threadIdx.x, one
 // 128-byte row segment per warp load) of progenitor p over all its partial
-// rows, in K2_SLICES row slices (threadIdx.y): slice y adds rows y,
-// y + K2_SLICES, ... in order, K2_BATCH rows at a time whose loads are all
+// rows, in SL row slices (threadIdx.y): slice y adds rows y, y + SL, ...
+// in order, a batch of rows at a time whose loads are all
 // issued before the first add (the kernel is a chain of memory latencies,
 // not of bandwidth: one round trip per batch, one batch at the usual row
-// counts); the slices are combined by a fixed binary tree.  The epilogue's
+// counts); the slices are combined by a fixed binary tree.  SL = 32 when
+// the column groups of all progenitors leave most SMs free (one progenitor),
+// else 8 (more, smaller blocks per SM for a batch).  The epilogue's
 // inputs (normalisation, 1/N_lm, b) are loaded before the rows.  Every sum
 // has a fixed order, so the result is the same on every run.
-constexpr int K2_X = 32, K2_SLICES = 32;
-__global__ void __launch_bounds__(K2_X * K2_SLICES) k2_reduce(K2Args a) {
-  __shared__ double s_c[K2_SLICES][K2_X], s_s[K2_SLICES][K2_X];
+constexpr int K2_X = 32;
+template <int SL>
+__global__ void __launch_bounds__(K2_X * SL) k2_reduce(K2Args a) {
+  __shared__ double s_c[SL][K2_X], s_s[SL][K2_X];
   const int p = blockIdx.y;
   const int x = threadIdx.x, y = threadIdx.y;
   const int groups = gridDim.x - 1;
@@ -893,11 +896,11 @@ __global__ void __launch_bounds__(K2_X * K2_SLICES) k2_reduce(K2Args a) {
     if (a.sub == 0) {  // double rows, one per block
       constexpr int B = 8;
       const double* P = a.partials + i;
-      for (int base = R0 + y; base < R1; base += B * K2_SLICES) {
+      for (int base = R0 + y; base < R1; base += B * SL) {
         double vc[B], vs[B];
 #pragma unroll
         for (int k = 0; k < B; ++k) {
-          const int r = base + k * K2_SLICES;
+          const int r = base + k * SL;
           vc[k] = r < R1 ? P[(size_t)r * stride] : 0.0;
           vs[k] = r < R1 ? P[(size_t)r * stride + a.nc] : 0.0;
         }
@@ -922,11 +925,11 @@ __global__ void __launch_bounds__(K2_X * K2_SLICES) k2_reduce(K2Args a) {
         lo += (hi - (s - bp)) + (v - bp);
         hi = s;
       };
-      for (int base = R0 + y; base < R1; base += B * K2_SLICES) {
+      for (int base = R0 + y; base < R1; base += B * SL) {
         float vc[B], vs[B];
 #pragma unroll
         for (int k = 0; k < B; ++k) {
-          const int r = base + k * K2_SLICES;
+          const int r = base + k * SL;
           vc[k] = r < R1 ? P[(size_t)r * stride] : 0.f;
           vs[k] = r < R1 && has_t ? P[(size_t)r * stride + a.nc] : 0.f;
         }
@@ -944,7 +947,7 @@ __global__ void __launch_bounds__(K2_X * K2_SLICES) k2_reduce(K2Args a) {
   s_s[y][x] = ss;
   __syncthreads();
 #pragma unroll
-  for (int h = K2_SLICES / 2; h >= 1; h >>= 1) {
+  for (int h = SL / 2; h >= 1; h >>= 1) {
     if (y < h) {
       s_c[y][x] += s_c[y + h][x];
       s_s[y][x] += s_s[y + h][x];
@@ -1110,8 +1113,10 @@ cudaError_t scf_k1_launch(int precision, const K1Args& a, int blocks, const ScfL
 }
 
 cudaError_t scf_k2_launch(const K2Args& a, cudaStream_t s) {
-  dim3 grid((a.nc + K2_X - 1) / K2_X + 1, a.n_prog);  // + the centre block
-  k2_reduce<<<grid, dim3(K2_X, K2_SLICES), 0, s>>>(a);
+  const int groups = (a.nc + K2_X - 1) / K2_X;
+  dim3 grid(groups + 1, a.n_prog);  // + the centre block
+  if ((int64_t)groups * a.n_prog * 2 <= a.n_sm || a.n_sm == 0) k2_reduce<32><<<grid, dim3(K2_X, 32), 0, s>>>(a);
+  else k2_reduce<8><<<grid, dim3(K2_X, 8), 0, s>>>(a);
   return cudaGetLastError();
 }
 
