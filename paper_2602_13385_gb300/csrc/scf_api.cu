@@ -1,6 +1,7 @@
 // C ABI of the SCF gravity step (declared in include/scf.h): argument
 // validation, workspace ownership, block maps and kernel launches.
 #include <algorithm>
+#include <queue>
 #include <cmath>
 #include <cstring>
 #include <memory>
@@ -330,19 +331,40 @@ struct Map1 {
 Map1 make_map1(const std::vector<int64_t>& off, int n_prog, int64_t tp, int64_t slots) {
   Map1 m;
   m.prog_off.assign(n_prog + 1, 0);
-  int64_t total = 0;
-  std::vector<int64_t> tiles(n_prog);
+  std::vector<int64_t> tiles(n_prog), nb(n_prog, 0);
+  int64_t used = 0;
   for (int p = 0; p < n_prog; ++p) {
     tiles[p] = (off[p + 1] - off[p] + tp - 1) / tp;
-    total += tiles[p];
+    nb[p] = tiles[p] > 0 ? 1 : 0;
+    used += nb[p];
   }
-  const int64_t tpb = std::max<int64_t>(1, (total + slots - 1) / slots);
+  // Blocks per progenitor: one each, then every further block to the
+  // progenitor whose blocks are the longest, while the blocks fit in one wave
+  // (slots).  The longest block sets the kernel's time, and a block beyond
+  // the wave would run after the others: so at most `slots` blocks, with the
+  // smallest longest block.
+  auto longest = [&](int p) { return nb[p] > 0 ? (tiles[p] + nb[p] - 1) / nb[p] : 0; };
+  std::priority_queue<std::pair<int64_t, int>> q;
+  for (int p = 0; p < n_prog; ++p)
+    if (nb[p] > 0) q.push({longest(p), p});
+  while (used < slots && !q.empty()) {
+    const int p = q.top().second;
+    q.pop();
+    if (longest(p) <= 1) break;
+    ++nb[p];
+    ++used;
+    q.push({longest(p), p});
+  }
+  // each progenitor's tiles split into nb[p] contiguous runs as even as possible
   for (int p = 0; p < n_prog; ++p) {
     m.prog_off[p] = (int)m.prog.size();
-    for (int64_t t0 = 0; t0 < tiles[p]; t0 += tpb) {
+    int64_t t0 = 0;
+    for (int64_t b = 0; b < nb[p]; ++b) {
+      const int64_t t1 = tiles[p] * (b + 1) / nb[p];
       m.prog.push_back(p);
       m.begin.push_back(off[p] + t0 * tp);
-      m.end.push_back(std::min(off[p] + (t0 + tpb) * tp, off[p + 1]));
+      m.end.push_back(std::min(off[p] + t1 * tp, off[p + 1]));
+      t0 = t1;
     }
   }
   m.prog_off[n_prog] = (int)m.prog.size();
