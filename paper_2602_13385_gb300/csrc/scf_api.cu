@@ -243,7 +243,6 @@ K2Args k2_args(scf_handle* h, double* A_out, double* com, int mode) {
   a.com = com;
   a.host = h->host;
   a.sub = h->k1.variant == 1 ? h->k1.win : 0;  // register-tiled kernel 1: float rows, one per window
-  a.n_sm = h->n_sm;
   a.cnext = mode == SCF_MODE_STEP && h->centre_ahead ? h->d_cnext : nullptr;
   a.tid_next = a.cnext && a.f32 ? h->d_tidnext : nullptr;
   return a;

@@ -699,7 +699,7 @@ struct K1Tiled {
   }
 };
 
-// Shapes with a compile-time basis: (nmax, lmax) = (20, 10), (20, 8), (10, 6);
+// Shapes with a compile-time basis: (nmax, lmax) = (20, 10), (20, 8), (10, 6), (10, 5);
 // every other shape runs the runtime-indexed basis, and so does a radial
 // family with alpha != 1 (gen), whose steps come from the handle's tables.
 template <typename F>
@@ -708,6 +708,7 @@ auto dispatch_tiled(int nmax, int lmax, F&& f, bool gen = false) {
     if (nmax == 20 && lmax == 10) return f(K1Tiled<BasisFixed<21, 10, true>>());
     if (nmax == 20 && lmax == 8) return f(K1Tiled<BasisFixed<21, 8, true>>());
     if (nmax == 10 && lmax == 6) return f(K1Tiled<BasisFixed<11, 6, true>>());
+    if (nmax == 10 && lmax == 5) return f(K1Tiled<BasisFixed<11, 5, true>>());
     switch ((lmax + 4) / 4) {
       case 1: return f(K1Tiled<BasisGeneric<1, true>>());
       case 2: return f(K1Tiled<BasisGeneric<2, true>>());
@@ -718,6 +719,7 @@ auto dispatch_tiled(int nmax, int lmax, F&& f, bool gen = false) {
   if (nmax == 20 && lmax == 10) return f(K1Tiled<BasisFixed<21, 10>>());
   if (nmax == 20 && lmax == 8) return f(K1Tiled<BasisFixed<21, 8>>());
   if (nmax == 10 && lmax == 6) return f(K1Tiled<BasisFixed<11, 6>>());
+  if (nmax == 10 && lmax == 5) return f(K1Tiled<BasisFixed<11, 5>>());
   switch ((lmax + 4) / 4) {
     case 1: return f(K1Tiled<BasisGeneric<1>>());
     case 2: return f(K1Tiled<BasisGeneric<2>>());
@@ -825,17 +827,15 @@ __device__ __forceinline__ void write_force_pair(void* F, int f32, const float* 
 // in one warp), concurrently with the reduction blocks.
 // Block (g < groups, p): coefficient pairs 32g .. 32g + 31 (threadIdx.x, one
 // 128-byte row segment per warp load) of progenitor p over all its partial
-// rows, in SL row slices (threadIdx.y): slice y adds rows y, y + SL, ...
-// in order, a batch of rows at a time whose loads are all
+// rows, in SL = 8 row slices (threadIdx.y): slice y adds rows y, y + SL,
+// ... in order, a batch of rows at a time whose loads are all
 // issued before the first add (the kernel is a chain of memory latencies,
 // not of bandwidth: one round trip per batch, one batch at the usual row
-// counts); the slices are combined by a fixed binary tree.  SL = 32 when
-// the column groups of all progenitors leave most SMs free (one progenitor),
-// else 8 (more, smaller blocks per SM for a batch).  The epilogue's
+// counts); the slices are combined by a fixed binary tree (32 slices in
+// 1024-thread blocks measured slower everywhere).  The epilogue's
 // inputs (normalisation, 1/N_lm, b) are loaded before the rows.  Every sum
 // has a fixed order, so the result is the same on every run.
-constexpr int K2_X = 32;
-template <int SL>
+constexpr int K2_X = 32, SL = 8;
 __global__ void __launch_bounds__(K2_X * SL) k2_reduce(K2Args a) {
   __shared__ double s_c[SL][K2_X], s_s[SL][K2_X];
   const int p = blockIdx.y;
@@ -1115,8 +1115,7 @@ cudaError_t scf_k1_launch(int precision, const K1Args& a, int blocks, const ScfL
 cudaError_t scf_k2_launch(const K2Args& a, cudaStream_t s) {
   const int groups = (a.nc + K2_X - 1) / K2_X;
   dim3 grid(groups + 1, a.n_prog);  // + the centre block
-  if ((int64_t)groups * a.n_prog * 2 <= a.n_sm || a.n_sm == 0) k2_reduce<32><<<grid, dim3(K2_X, 32), 0, s>>>(a);
-  else k2_reduce<8><<<grid, dim3(K2_X, 8), 0, s>>>(a);
+  k2_reduce<<<grid, dim3(K2_X, SL), 0, s>>>(a);
   return cudaGetLastError();
 }
 

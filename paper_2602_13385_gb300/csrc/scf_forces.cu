@@ -62,8 +62,8 @@ __device__ __forceinline__ float k3_pow(float x, float y) { return powf(x, y); }
 
 // NNF > 0: the shape (nmax, lmax) = (NNF - 1, LMAX) fixed at compile time
 // (single precision, alpha = 1): every coefficient offset is an immediate
-// and the radial loop is unrolled by kK3Unroll without a remainder.
-constexpr int kK3Unroll = 4;
+// and the radial loop is unrolled by 4 (or 5, or 2) without a remainder.
+constexpr int k3_unroll(int nnf) { return (nnf - 1) % 4 == 0 ? 4 : (nnf - 1) % 5 == 0 ? 5 : 2; }
 template <typename T, int LMAX, int K3_TB, bool GEN, int NNF>
 __device__ __forceinline__ void k3_body(const K3Args& a) {
   using V4 = typename Vec4<T>::type;
@@ -261,8 +261,9 @@ __device__ __forceinline__ void k3_body(const K3Args& a) {
         d0 = dn;
       };
       if constexpr (NNF > 0) {
-        static_assert((NNF - 1) % kK3Unroll == 0, "the radial loop has no remainder");
-#pragma unroll kK3Unroll
+        constexpr int U = k3_unroll(NNF);
+        static_assert((NNF - 1) % U == 0, "the radial loop has no remainder");
+#pragma unroll U
         for (int n = 1; n < NNF; ++n) radial_step(n);
       } else if constexpr (kF2 && !GEN && LMAX == 10) {
 #pragma unroll 2
@@ -432,12 +433,14 @@ int lmax_bucket(int lmax) {
   return 12;
 }
 
-// (nmax, lmax) = (20, 10) in single precision with alpha = 1 runs the
-// compile-time shape.
+// (nmax, lmax) = (20, 10) and (10, 5) (the paper's stream model) in single
+// precision with alpha = 1 run the compile-time shape.
 template <typename T, int TB, typename Fn, bool GEN = false>
 auto dispatch_lmax(int lmax, Fn&& f, int nmax = -1) {
-  if constexpr (sizeof(T) == 4 && !GEN)
+  if constexpr (sizeof(T) == 4 && !GEN) {
     if (lmax == 10 && nmax == 20) return f(K3At<T, TB, 10, GEN, 21>());
+    if (lmax == 5 && nmax == 10) return f(K3At<T, TB, 5, GEN, 11>());
+  }
   switch (lmax_bucket(lmax)) {
     case 2: return f(K3At<T, TB, 2, GEN>());
     case 4: return f(K3At<T, TB, 4, GEN>());

@@ -67,7 +67,6 @@ struct K2Args {
   double* A_out;            // [n_prog][2*NC]
   int nc, n_prog, nlm;
   int mode;
-  int n_sm;                 // SMs of the device (0: taken as many; sets the row slices per block)
   double dt;
   double* com;              // [n_prog][6] (step mode with host)
   ScfHostParams host;

@@ -69,7 +69,7 @@ def make(scf, wl, precision="mixed", offsets=None, b_per_prog=None, host=True):
     return scf.SCF(cfg, n=None if offsets is not None else wl.n, offsets=offsets, b_per_prog=b_per_prog)
 
 
-@pytest.mark.parametrize("nmax,lmax,n", [(10, 6, 4096), (20, 8, 20000), (20, 10, 20000)])
+@pytest.mark.parametrize("nmax,lmax,n", [(10, 5, 4096), (10, 6, 4096), (20, 8, 20000), (20, 10, 20000)])
 def test_mixed_coefficients(scf, nmax, lmax, n):
     pos, _ = workloads.plummer(n, seed=200 + lmax)
     b = workloads.basis_scale(workloads.half_mass_radius(pos))
@@ -104,6 +104,26 @@ def test_mixed_forces_and_tidal_term(scf):
     print(f"mixed tidal term error: median {np.median(et):.2e}, max {et.max():.2e}")
     assert np.median(et) < 1e-5
     assert et.max() < 1e-4
+    assert sim.status() == (0, 0)
+
+
+@pytest.mark.parametrize("nmax,lmax", [(10, 5), (10, 6), (20, 10)])
+@pytest.mark.parametrize("block", [64, 128, 256, 320])
+def test_mixed_field_kernel_shapes(scf, nmax, lmax, block):
+    """The field kernel's shapes fixed at compile time ((10,5), (20,10)) and a
+    runtime one ((10,6)), in every block size, against the oracle on the same
+    float-rounded positions, with the host's tidal term and a ragged last block."""
+    wl = workloads.plummer_eccentric(n=7001, seed=40 + lmax, nsteps=1)
+    p32 = wl.pos.astype(np.float32).astype(np.float64)
+    A = oracle.coeffs(p32, nmax, lmax, wl.b)
+    ref = oracle.forces(p32, A, nmax, lmax, wl.b, com=wl.com, host=oracle.host_struct(wl.host))
+    cfg = scf.Config(nmax=nmax, lmax=lmax, b=wl.b, dt=wl.dt, precision="mixed", host=list(wl.host))
+    sim = scf.SCF(cfg, n=wl.n)
+    sim.set_tiles(k3_block=block)
+    acc = sim.forces(f32(wl.pos), f64(A[None]), com=f64(wl.com[None])).cpu().double().numpy()
+    e = rel_acc(acc, ref)
+    print(f"({nmax},{lmax}) block {block}: acceleration median {np.median(e):.2e}, max {e.max():.2e}")
+    assert np.median(e) < 1e-5 and e.max() < 2e-3
     assert sim.status() == (0, 0)
 
 
@@ -174,7 +194,8 @@ def test_full_size_eccentric_mixed_workload(scf):
 
 
 @pytest.mark.parametrize("nmax,lmax,n,masked", [(0, 0, 17, False), (10, 6, 1, False), (10, 6, 63, False),
-                                                (10, 6, 65, True), (20, 8, 5003, False), (20, 10, 30000, True),
+                                                (10, 6, 65, True), (10, 5, 2003, True), (20, 8, 5003, False),
+                                                (20, 10, 30000, True),
                                                 (40, 12, 4099, False), (3, 1, 1000, False)])
 def test_register_tiled_kernel_matches_oracle_and_simple_kernel(scf, nmax, lmax, n, masked):
     """The register-tiled coefficient kernel (the mixed-precision default) on
