@@ -220,7 +220,8 @@ int scf_step_host(scf_handle* h, void* pos, void* vel, void* acc, double* com, v
  *   SCF_OPT_K1_VARIANT 0 = the coefficient kernel with one thread per output
  *                     and SCF_OPT_K1_TILE particles per tile (the double-
  *                     precision default); 1 = the register-tiled kernel
- *                     (7 x 8 output tiles per thread over 64-particle
+ *                     (register output tiles per thread, 21 x 3 at
+ *                     nmax = 20, 11 x 5 at nmax = 10, 7 x 8 otherwise, over 60-particle
  *                     tiles; SCF_MIXED only, its default); 2 = (SCF_FP64
  *                     only) the one-thread-per-output kernel in float-float
  *                     arithmetic on the single-precision pipe (128-particle

@@ -240,7 +240,7 @@ struct ScfLaunchInfo {
   int tile;      // particles per tile (block ranges are whole tiles)
   size_t smem;   // dynamic shared memory per block
   int variant;   // kernel variant chosen by the prepare call (1: register-tiled single precision)
-  int items;     // variant 1: 7 x 8 contraction items per particle sub-group
+  int items;     // variant 1: TN x TM contraction items (output tiles) per particle sub-group
   int sub;       // variant 1: particle sub-groups per block
   int win;       // variant 1: windows per block (partial rows per block = sub * win)
   int win_tiles; // variant 1: tiles per window
