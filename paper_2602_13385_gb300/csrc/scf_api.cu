@@ -65,6 +65,12 @@ struct scf_handle {
   bool graphs = true;
   cudaGraphExec_t step_exec = nullptr;
   const void* step_key[4] = {nullptr, nullptr, nullptr, nullptr};
+  bool step_split = false;      // the graph is of a split-state step (scf_step_host, below)
+  // scf_step_host on mapped host memory (mixed precision, register-tiled
+  // kernel 1): device copies of the drifted positions and the half-kicked
+  // velocities, so that kernel 3 reads them from device memory; allocated by
+  // the first such call
+  void* d_split = nullptr;      // [2][n_total] float4
   // adjoint: per-block tidal partials (double-precision handles only) and
   // the dual kernels' launch shapes (set by the first scf_adjoint_level call)
   double* d_adj_part = nullptr;       // [k3 blocks][SCF_ADJ_Q]
@@ -151,6 +157,7 @@ void drop_graph(scf_handle* h) {
   if (h->step_exec) cudaGraphExecDestroy(h->step_exec);
   h->step_exec = nullptr;
   for (auto& k : h->step_key) k = nullptr;
+  h->step_split = false;
 }
 
 size_t round_up(size_t x) { return (x + 255) & ~size_t(255); }
@@ -279,9 +286,11 @@ K3Args k3_args(scf_handle* h, const void* pos, void* vel, void* acc, const doubl
 }
 
 int run_coeffs(scf_handle* h, void* pos, void* vel, const void* acc, const uint8_t* mask, double* A_out, double* com,
-               int mode) {
+               int mode, void* pos_copy = nullptr, void* vel_out = nullptr) {
   if (h->k1_blocks > 0) {
     K1Args a = k1_args(h, pos, vel, acc, mask, mode);
+    a.pos_copy = pos_copy;
+    a.vel_out = vel_out;
     if (timed(h, 0, [&] {
           return h->k1.variant == 2 ? scf_k1_ff_launch(a, h->k1_blocks, h->k1, h->stream)
                                     : scf_k1_launch(h->cfg.precision, a, h->k1_blocks, h->k1, h->stream);
@@ -312,9 +321,11 @@ int run_prep(scf_handle* h, const double* A, const double* com) {
 }
 
 // Kernel 3 on the handle's F / a_host(R) (from kernel 2 or run_prep).
-int run_forces(scf_handle* h, const void* pos, void* vel, void* acc, const double* com, int mode) {
+int run_forces(scf_handle* h, const void* pos, void* vel, void* acc, const double* com, int mode,
+               const void* vel_in = nullptr) {
   if (h->k3_blocks == 0) return SCF_OK;
   K3Args a = k3_args(h, pos, vel, acc, com, mode);
+  a.vel_in = vel_in;
   if (h->k3.variant == 2 && mode != SCF_MODE_ADJ_J)
     return cuda_fail(timed(h, 2, [&] { return scf_k3_ff_launch(a, h->k3_blocks, h->k3, h->stream); }));
   return cuda_fail(
@@ -703,8 +714,14 @@ int scf_forces(scf_handle* h, const void* pos, const double* A, const double* co
 
 namespace {
 
-int launch_step(scf_handle* h, void* pos, void* vel, void* acc, double* com) {
-  int rc = run_coeffs(h, pos, vel, acc, h->step_mask, h->d_A, com, SCF_MODE_STEP);
+// One step.  split (scf_step_host on mapped host memory): kernel 1 also
+// writes the drifted positions to the device copy and the half-kicked
+// velocities only there, and kernel 3 reads both from it, so the host link
+// carries the state in once and out once.
+int launch_step(scf_handle* h, void* pos, void* vel, void* acc, double* com, bool split = false) {
+  void* spos = split ? h->d_split : nullptr;
+  void* svel = split ? static_cast<char*>(h->d_split) + 16 * (size_t)h->n_total : nullptr;
+  int rc = run_coeffs(h, pos, vel, acc, h->step_mask, h->d_A, com, SCF_MODE_STEP, spos, svel);
   if (rc != SCF_OK) return rc;
   // the next step's centre kick-drift-kick, on a second stream beside kernel 3
   // (its FP64 dependency chain then leaves kernel 2's critical path); joined
@@ -736,7 +753,7 @@ int launch_step(scf_handle* h, void* pos, void* vel, void* acc, double* com) {
         cudaEventRecord(h->side_ev[1], h->side_stream) != cudaSuccess)
       return SCF_ERR_CUDA;
   }
-  rc = run_forces(h, pos, vel, acc, com, SCF_MODE_STEP);
+  rc = split ? run_forces(h, spos, vel, acc, com, SCF_MODE_STEP, svel) : run_forces(h, pos, vel, acc, com, SCF_MODE_STEP);
   if (ahead && cudaStreamWaitEvent(h->stream, h->side_ev[1], 0) != cudaSuccess) return SCF_ERR_CUDA;
   return rc;
 }
@@ -744,14 +761,14 @@ int launch_step(scf_handle* h, void* pos, void* vel, void* acc, double* com) {
 // Captures one step on the handle's stream into an executable graph.  Returns
 // false (and leaves the handle without a graph) when the stream cannot be
 // captured, e.g. the legacy default stream.
-bool capture_step(scf_handle* h, void* pos, void* vel, void* acc, double* com) {
+bool capture_step(scf_handle* h, void* pos, void* vel, void* acc, double* com, bool split) {
   drop_graph(h);
   if (h->stream == nullptr || h->stream == cudaStreamLegacy) return false;
   if (cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
     cudaGetLastError();
     return false;
   }
-  const int rc = launch_step(h, pos, vel, acc, com);
+  const int rc = launch_step(h, pos, vel, acc, com, split);
   cudaGraph_t g = nullptr;
   const cudaError_t e = cudaStreamEndCapture(h->stream, &g);
   bool ok = rc == SCF_OK && e == cudaSuccess && g != nullptr &&
@@ -766,7 +783,27 @@ bool capture_step(scf_handle* h, void* pos, void* vel, void* acc, double* com) {
   h->step_key[1] = vel;
   h->step_key[2] = acc;
   h->step_key[3] = com;
+  h->step_split = split;
   return true;
+}
+
+int step_impl(scf_handle* h, void* pos, void* vel, void* acc, double* com, int nsteps, bool split) {
+  // one graph launch per step when the stream can be captured (the kernels
+  // and their arguments are the same every step); plain launches otherwise
+  if (h->graphs && !h->prof_on) {
+    const bool same = h->step_exec && h->step_key[0] == pos && h->step_key[1] == vel && h->step_key[2] == acc &&
+                      h->step_key[3] == com && h->step_split == split;
+    if (same || capture_step(h, pos, vel, acc, com, split)) {
+      for (int st = 0; st < nsteps; ++st)
+        if (cudaGraphLaunch(h->step_exec, h->stream) != cudaSuccess) return SCF_ERR_CUDA;
+      return SCF_OK;
+    }
+  }
+  for (int st = 0; st < nsteps; ++st) {
+    const int rc = launch_step(h, pos, vel, acc, com, split);
+    if (rc != SCF_OK) return rc;
+  }
+  return SCF_OK;
 }
 
 }  // namespace
@@ -778,22 +815,7 @@ int scf_step(scf_handle* h, void* pos, void* vel, void* acc, double* com, int ns
   if (h->host.n > 0 && !com) return SCF_ERR_NULL_POINTER;
   if (!aligned16(pos) || !aligned16(vel) || !aligned16(acc)) return SCF_ERR_MISALIGNED;
   if (nsteps == 0) return SCF_OK;
-  // one graph launch per step when the stream can be captured (the kernels
-  // and their arguments are the same every step); plain launches otherwise
-  if (h->graphs && !h->prof_on) {
-    const bool same = h->step_exec && h->step_key[0] == pos && h->step_key[1] == vel && h->step_key[2] == acc &&
-                      h->step_key[3] == com;
-    if (same || capture_step(h, pos, vel, acc, com)) {
-      for (int st = 0; st < nsteps; ++st)
-        if (cudaGraphLaunch(h->step_exec, h->stream) != cudaSuccess) return SCF_ERR_CUDA;
-      return SCF_OK;
-    }
-  }
-  for (int st = 0; st < nsteps; ++st) {
-    const int rc = launch_step(h, pos, vel, acc, com);
-    if (rc != SCF_OK) return rc;
-  }
-  return SCF_OK;
+  return step_impl(h, pos, vel, acc, com, nsteps, false);
 }
 
 namespace {
@@ -832,8 +854,21 @@ int scf_step_host(scf_handle* h, void* pos, void* vel, void* acc, double* com, v
       mapped = false;
     }
   }
-  if (mapped && aligned16(mp[0]) && aligned16(mp[1]) && aligned16(mp[2]))
-    return scf_step(h, mp[0], mp[1], mp[2], static_cast<double*>(mp[3]), 1);
+  if (mapped && aligned16(mp[0]) && aligned16(mp[1]) && aligned16(mp[2])) {
+    // mixed precision with the register-tiled kernel 1 and the native kernel
+    // 3: the intermediate state stays on the device (launch_step, split)
+    const bool split = h->cfg.precision == SCF_MIXED && h->k1.variant == 1 && h->k3.variant != 2 &&
+                       h->n_total > 0;
+    if (split && !h->d_split) {
+      if (cudaMalloc(&h->d_split, 2 * 16 * (size_t)h->n_total) != cudaSuccess) {
+        cudaGetLastError();
+        h->d_split = nullptr;
+        return SCF_ERR_OUT_OF_MEMORY;
+      }
+    }
+    if (h->host.n > 0 && !mp[3]) return SCF_ERR_NULL_POINTER;
+    return step_impl(h, mp[0], mp[1], mp[2], static_cast<double*>(mp[3]), 1, split);
+  }
 
   // Otherwise the state is staged through the device arrays: copied in, kernel
   // 1 and 2, and copied back while kernel 3 still runs -- positions (final
@@ -1611,6 +1646,7 @@ int scf_free(scf_handle* h) {
     if (e) cudaEventDestroy(e);
   if (h->side_stream) cudaStreamDestroy(h->side_stream);
   if (h->d_base && cudaFree(h->d_base) != cudaSuccess) rc = SCF_ERR_CUDA;
+  if (h->d_split && cudaFree(h->d_split) != cudaSuccess) rc = SCF_ERR_CUDA;
   delete h;
   return rc;
 }

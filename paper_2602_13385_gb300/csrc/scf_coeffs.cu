@@ -614,7 +614,8 @@ __global__ void __maxnreg__(128) k1_tiled(K1Args a) {
       const int64_t k = base + warp * (TP / 2) + lane;
       if (k < k_end) {
         pos4[k] = p_new;
-        reinterpret_cast<float4*>(a.vel)[k] = v_new;
+        if (a.pos_copy) reinterpret_cast<float4*>(a.pos_copy)[k] = p_new;
+        reinterpret_cast<float4*>(a.vel_out ? a.vel_out : a.vel)[k] = v_new;
       }
     }
     // ---- contraction of the tile into the register tiles

@@ -388,7 +388,7 @@ __device__ __forceinline__ void k3_body(const K3Args& a) {
   reinterpret_cast<V4*>(a.acc)[k] = out;
   if (a.mode == SCF_MODE_STEP) {
     V4* vel4 = reinterpret_cast<V4*>(a.vel);
-    V4 vv = vel4[k];
+    V4 vv = a.vel_in ? reinterpret_cast<const V4*>(a.vel_in)[k] : vel4[k];
     const T h = (T)(0.5 * a.dt);
     vv.x += h * out.x;
     vv.y += h * out.y;

@@ -37,6 +37,10 @@ struct K1Args {
   void* pos;          // [N][4] float or double (read; written in step mode)
   void* vel;          // [N][4] (step mode)
   const void* acc;    // [N][4] (step mode)
+  // step mode, register-tiled kernel, optional: a second copy of the drifted
+  // positions, and where the half-kicked velocities go (null: vel)
+  void* pos_copy;
+  void* vel_out;
   const uint8_t* mask;
   double* partials;   // [n_blocks][2*NC]
   const int* blk_prog;
@@ -131,6 +135,7 @@ struct K3Args {
   const void* pos;
   void* vel;
   void* acc;
+  const void* vel_in;       // step mode, optional: the velocities to kick (null: vel); the result goes to vel
   const void* F;            // [n_prog][NC] (cos, sin) force-coefficient pairs
   const double* com;        // [n_prog][6] or null (R is read)
   const double* aR;         // [n_prog][4] a_host(R)
