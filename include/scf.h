@@ -187,7 +187,11 @@ int scf_step(scf_handle* h, void* pos, void* vel, void* acc, double* com, int ns
  * torch pin_memory, under unified addressing) the step's kernels read and
  * write the host arrays in place over the host link: the transfers happen
  * inside the kernels, overlapped with their arithmetic, and the device arrays
- * are not used (they may be NULL).  Otherwise the state is staged through the
+ * are not used (they may be NULL); in SCF_MIXED with the register-tiled
+ * kernel 1 the drifted positions and half-kicked velocities between kernels
+ * 1 and 3 are kept in a device copy owned by the handle (2 x 16 bytes per
+ * particle, allocated by the first such call, freed by scf_free), so the
+ * host link carries the state in once and out once.  Otherwise the state is staged through the
  * device arrays: copied in on a second stream of the handle, kernels 1 and 2,
  * then the positions and the centres copied back while kernel 3 runs, which
  * is launched in `chunks` pieces of its block map so that each piece's
@@ -204,7 +208,7 @@ int scf_step(scf_handle* h, void* pos, void* vel, void* acc, double* com, int ns
  *   chunks                       1..SCF_STAGE_MAX_CHUNKS (staged form).
  * Host arrays must stay valid until the handle's stream has finished.
  * Errors: SCF_ERR_NULL_POINTER, SCF_ERR_MISALIGNED, SCF_ERR_INVALID_ARG
- * (chunks out of range), SCF_ERR_CUDA. */
+ * (chunks out of range), SCF_ERR_OUT_OF_MEMORY (the device copy), SCF_ERR_CUDA. */
 #define SCF_STAGE_MAX_CHUNKS 32
 int scf_step_host(scf_handle* h, void* pos, void* vel, void* acc, double* com, void* host_pos, void* host_vel,
                   void* host_acc, double* host_com, int chunks);
