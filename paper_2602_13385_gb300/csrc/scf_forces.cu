@@ -61,7 +61,7 @@ __device__ __forceinline__ double k3_pow(double x, double y) { return pow(x, y);
 __device__ __forceinline__ float k3_pow(float x, float y) { return powf(x, y); }
 
 // NNF > 0: the shape (nmax, lmax) = (NNF - 1, LMAX) fixed at compile time
-// (single precision, alpha = 1): every coefficient offset is an immediate
+// (single precision): every coefficient offset is an immediate
 // and the radial loop is unrolled by 4 (or 5, or 2) without a remainder.
 constexpr int k3_unroll(int nnf) { return (nnf - 1) % 4 == 0 ? 4 : (nnf - 1) % 5 == 0 ? 5 : 2; }
 template <typename T, int LMAX, int K3_TB, bool GEN, int NNF>
@@ -434,10 +434,10 @@ int lmax_bucket(int lmax) {
 }
 
 // (nmax, lmax) = (20, 10) and (10, 5) (the paper's stream model) in single
-// precision with alpha = 1 run the compile-time shape.
+// precision run the compile-time shape (any alpha).
 template <typename T, int TB, typename Fn, bool GEN = false>
 auto dispatch_lmax(int lmax, Fn&& f, int nmax = -1) {
-  if constexpr (sizeof(T) == 4 && !GEN) {
+  if constexpr (sizeof(T) == 4) {
     if (lmax == 10 && nmax == 20) return f(K3At<T, TB, 10, GEN, 21>());
     if (lmax == 5 && nmax == 10) return f(K3At<T, TB, 5, GEN, 11>());
   }
@@ -484,7 +484,7 @@ cudaError_t prepare_t(int lmax, int nmax, int tb, ScfLaunchInfo* info, int* bloc
     if (e != cudaSuccess) return e;
     return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, KK::fn(), info->threads, info->smem);
   };
-  if constexpr (GEN) return dispatch_lmax<T, 128, decltype(body)&, true>(lmax, body);
+  if constexpr (GEN) return dispatch_lmax<T, 128, decltype(body)&, true>(lmax, body, nmax);
   else return dispatch_k3<T>(tb, lmax, nmax, body);
 }
 
@@ -507,7 +507,7 @@ cudaError_t scf_k3_launch(int precision, const K3Args& a, int blocks, const ScfL
     return 0;
   };
   if (info.variant == 3) {  // radial family of exponent alpha != 1, 128-thread blocks
-    if (precision == 1) dispatch_lmax<float, 128, decltype(go)&, true>(a.lmax, go);
+    if (precision == 1) dispatch_lmax<float, 128, decltype(go)&, true>(a.lmax, go, a.nmax);
     else dispatch_lmax<double, 128, decltype(go)&, true>(a.lmax, go);
   } else if (precision == 1) {
     dispatch_k3<float>(info.threads, a.lmax, a.nmax, go);

@@ -144,7 +144,8 @@ def test_fp64_batched_progenitors(scf):
         assert coef_err(A[i], oracle.coeffs(pos_l[i], 10, 6, b_l[i], alpha=alpha)) < TOL
 
 
-@pytest.mark.parametrize("alpha,nmax,lmax,n", [(0.5, 20, 10, 20000), (1.5, 12, 6, 5003), (0.75, 40, 12, 3001)])
+@pytest.mark.parametrize("alpha,nmax,lmax,n", [(0.5, 20, 10, 20000), (0.5, 10, 5, 3001), (1.5, 12, 6, 5003),
+                                                  (0.75, 40, 12, 3001)])
 def test_mixed_matches_oracle(scf, alpha, nmax, lmax, n):
     wl = workloads.plummer_eccentric(n=n, seed=640 + n, nsteps=1)
     p32 = wl.pos.astype(np.float32).astype(np.float64)
