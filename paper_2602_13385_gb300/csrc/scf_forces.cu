@@ -196,21 +196,24 @@ __device__ __forceinline__ void k3_body(const K3Args& a) {
     P[l] = tldiag<T>(l);
 
     if (SPLIT == 1 || (half == 0) == (l >= Ls)) {
+    // the (cosine, sine) sums over n of the Ch_n terms (Z0) and of the
+    // Dh_{n-1} terms (Z1): scalars in double precision, packed pairs in single
     T Z0c[LMAX + 1], Z0s[LMAX + 1], Z1c[LMAX + 1], Z1s[LMAX + 1];
+    V2 Z0[LMAX + 1], Z1[LMAX + 1];
     const int lm0 = scf_lm(l, 0);
 #pragma unroll
     for (int m = 0; m <= l; ++m) {  // n = 0: Ch_0 = 1, no Dh_{-1} term
       if constexpr (kF2) {
-        const V2 f0 = F2[lm0 + m];
-        Z0c[m] = f0.x;
-        Z0s[m] = f0.y;
+        Z0[m] = F2[lm0 + m];
+        Z1[m].x = 0;
+        Z1[m].y = 0;
       } else {
         const V4 f0 = F[lm0 + m];
         Z0c[m] = f0.x;
         Z0s[m] = f0.y;
+        Z1c[m] = 0;
+        Z1s[m] = 0;
       }
-      Z1c[m] = 0;
-      Z1s[m] = 0;
     }
     {
       T cm1 = 0, c0 = 1;  // Ch_{n-2}, Ch_{n-1}
@@ -235,14 +238,14 @@ __device__ __forceinline__ void k3_body(const K3Args& a) {
         const T cn = xi * c0 - gbn * cm1;
         const int o = n * NLM + lm0;
         if constexpr (kF2) {
-          const T dd = d0 * hrn;
+          // one packed FMA per (cosine, sine) pair: each lane rounds as the
+          // scalar fmaf, in the same order over n
+          const float2 cc = make_float2(cn, cn), dv = make_float2(d0 * hrn, d0 * hrn);
 #pragma unroll
           for (int m = 0; m <= l; ++m) {
-            const V2 fv = F2[o + m];
-            Z0c[m] += fv.x * cn;
-            Z0s[m] += fv.y * cn;
-            Z1c[m] += fv.x * dd;
-            Z1s[m] += fv.y * dd;
+            const float2 fv = F2[o + m];
+            Z0[m] = __ffma2_rn(fv, cc, Z0[m]);
+            Z1[m] = __ffma2_rn(fv, dv, Z1[m]);
           }
         } else {
 #pragma unroll
@@ -286,8 +289,9 @@ __device__ __forceinline__ void k3_body(const K3Args& a) {
     T sP0 = 0, sP1 = 0, sE = 0, sZ = 0, sX = 0, sY = 0;
 #pragma unroll
     for (int m = 0; m <= l; ++m) {
-      const T Q0 = Z0c[m] * Wc[m] + Z0s[m] * Ws[m];
-      const T Q1 = Z1c[m] * Wc[m] + Z1s[m] * Ws[m];
+      const T z0c = kF2 ? Z0[m].x : Z0c[m], z0s = kF2 ? Z0[m].y : Z0s[m];
+      const T Q0 = z0c * Wc[m] + z0s * Ws[m];
+      const T Q1 = kF2 ? Z1[m].x * Wc[m] + Z1[m].y * Ws[m] : Z1c[m] * Wc[m] + Z1s[m] * Ws[m];
       const T Pl = P[m];
       const T Pd = (m < l) ? -tlk<T>(scf_lm(l, m)) * P[m + 1] : (T)0;
       sP0 += Pl * Q0;
@@ -296,8 +300,8 @@ __device__ __forceinline__ void k3_body(const K3Args& a) {
       if (m >= 1) {
         const T mPl = (T)m * Pl;
         sE += (c * Pd + mPl) * Q0;
-        sX += mPl * (Z0c[m] * Wc[m - 1] + Z0s[m] * Ws[m - 1]);
-        sY += mPl * (Z0c[m] * Ws[m - 1] - Z0s[m] * Wc[m - 1]);
+        sX += mPl * (z0c * Wc[m - 1] + z0s * Ws[m - 1]);
+        sY += mPl * (z0c * Ws[m - 1] - z0s * Wc[m - 1]);
       } else {
         sE += c * Pd * Q0;
       }
