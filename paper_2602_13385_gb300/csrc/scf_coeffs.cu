@@ -224,7 +224,11 @@ size_t k1_smem(int nmax, int nc) {
 // float4 rows and issues 4 TN TM FMAs into registers.  The tile shape follows
 // the expansion: all 21 radial orders by 3 columns at nmax = 20 (the 2l + 1
 // columns of a degree then pad to a multiple of 3, not of 8: 132 instead of
-// 168 columns at lmax = 10), 11 by 5 at nmax = 10, 7 by 8 otherwise.
+// 168 columns at lmax = 10), 11 by 5 at nmax = 10, 7 by 8 otherwise.  At
+// nmax = 20 the radial rows are staged as interleaved pairs of orders and the
+// contraction issues packed FMAs (fma.rn.f32x2), each updating the sums of
+// two radial orders with every lane rounding as fmaf, the particles in the
+// same order (the odd last order in scalar FMAs): half the FMA instructions.
 //
 // The basis of each 60-particle tile is staged as rows [l][n] (the scaled
 // Gegenbauer values Ch_n(xi) = C_n(xi) / gscale[l][n], see ScfConst) and
@@ -254,10 +258,21 @@ constexpr int WINDOW_TILES = 64; // tiles summed in registers before a window's 
 constexpr int MAX_THREADS = 256;
 
 // Output tile of a worker: TN radial orders x TM angular columns.
-template <int TN_, int TM_>
+// PAIRS (tiles that span all radial orders of a degree): the radial rows of a
+// degree are staged as interleaved pairs, pair row p holding (R_2p[t],
+// R_2p+1[t]) for every particle t, so that one float4 load gives the operands
+// of two packed FMAs (fma.rn.f32x2), each updating the accumulators of two
+// radial orders; a degree's block of pair rows is padded by one float4 so that
+// it spans an odd number of float4s and lanes reading different degrees start
+// in different bank groups.
+template <int TN_, int TM_, bool PAIRS_ = false>
 struct Tile {
   static constexpr int TN = TN_, TM = TM_;
+  static constexpr bool kPairs = PAIRS_;
+  static constexpr int TNP = (TN + 1) / 2;               // pair rows of a degree
+  static constexpr int kDegFloats = TNP * 2 * TPP + 4;   // staged floats of a degree (PAIRS)
   static_assert(TN * TM <= 64, "the register budget holds at most 64 accumulators");
+  static_assert(!kPairs || (kDegFloats / 4) % 2 == 1, "a degree's pair rows span an odd number of float4s");
   static __host__ __device__ constexpr int n_chunks(int nn) { return (nn + TN - 1) / TN; }
   static __host__ __device__ constexpr int m_chunks(int l) { return (2 * l + 1 + TM - 1) / TM; }
   // zero rows after the last degree's radial rows that its last chunk reads
@@ -283,16 +298,23 @@ struct Tile {
   // the worker tiles (at most MAX_THREADS tiles of TN x TM floats) for the
   // cross-sub-group sums.
   static constexpr size_t kRedFloats = (size_t)MAX_THREADS * TN * TM;
+  static size_t r_floats(int nmax, int lmax) {  // the staged radial rows
+    return kPairs ? (size_t)(lmax + 1) * kDegFloats
+                  : (size_t)TPP * ((size_t)(lmax + 1) * (nmax + 1) + pad_rows(nmax + 1));
+  }
   static size_t smem_bytes(int nmax, int lmax, bool gen) {
-    const size_t rows = (size_t)(lmax + 1) * (nmax + 1) + pad_rows(nmax + 1) + (size_t)YCH * chunk_base(lmax + 1);
+    const size_t staged = r_floats(nmax, lmax) + (size_t)TPP * YCH * chunk_base(lmax + 1);
     const size_t sg = gen ? (size_t)(lmax + 1) * (nmax + 1) : 0;
-    return sizeof(float) * (((sg + 3) & ~size_t(3)) + std::max(TPP * rows, kRedFloats));
+    return sizeof(float) * (((sg + 3) & ~size_t(3)) + std::max(staged, kRedFloats));
   }
 };
 using TileGeneric = Tile<7, 8>;
 // the tile of a compile-time shape: all radial orders where they fit
 template <int NN>
-using TileFor = std::conditional_t<NN == 21, Tile<21, 3>, std::conditional_t<NN == 11, Tile<11, 5>, TileGeneric>>;
+// (paired radial rows at nmax = 20: 1-3% faster at alpha = 1 and 13% for the
+// general family; at nmax = 10 the 11 x 5 tiles measured 3.6% slower paired)
+using TileFor =
+    std::conditional_t<NN == 21, Tile<21, 3, true>, std::conditional_t<NN == 11, Tile<11, 5>, TileGeneric>>;
 
 // At the end of a window: every worker has written its tile to red[(sgrp *
 // items + item) * TN * TM + i * TM + j]; the block adds the sub-groups' tiles
@@ -407,14 +429,16 @@ template <int Q, int NN, int L, bool GEN, class S>
 __device__ __forceinline__ void basis_fixed(float* Rs, float* Ys, int t, float mass, float u, float v, float c,
                                             float qv, float xi, float sq2, const float* sg) {
   constexpr int NJ = Q <= L ? (L - Q) / 4 + 1 : 0;
+  static_assert(!S::kPairs || S::TN == NN, "paired radial rows: the tile spans all radial orders");
   if constexpr (NJ > 0) {
-    // radial rows Ch_n(xi) of the degrees l = Q + 4j
+    // radial rows Ch_n(xi) of the degrees l = Q + 4j (PAIRS: stored as the
+    // pairs (Ch_n-1, Ch_n) at odd n, and (Ch_NN-1, 0) after the last odd n)
     float c0[NJ], cm1[NJ];
 #pragma unroll
     for (int j = 0; j < NJ; ++j) {
       c0[j] = 1.f;
       cm1[j] = 0.f;
-      Rs[((Q + 4 * j) * NN) * TPP + t] = 1.f;
+      if constexpr (!S::kPairs) Rs[((Q + 4 * j) * NN) * TPP + t] = 1.f;
     }
 #pragma unroll
     for (int n = 1; n < NN; ++n) {
@@ -425,8 +449,19 @@ __device__ __forceinline__ void basis_fixed(float* Rs, float* Ys, int t, float m
         const float cn = fmaf(-gb, cm1[j], xi * c0[j]);
         cm1[j] = c0[j];
         c0[j] = cn;
-        Rs[(l * NN + n) * TPP + t] = cn;
+        if constexpr (S::kPairs) {
+          if (n & 1)
+            *reinterpret_cast<float2*>(Rs + l * S::kDegFloats + (n >> 1) * 2 * TPP + 2 * t) = make_float2(cm1[j], cn);
+        } else {
+          Rs[(l * NN + n) * TPP + t] = cn;
+        }
       }
+    }
+    if constexpr (S::kPairs && NN % 2 == 1) {
+#pragma unroll
+      for (int j = 0; j < NJ; ++j)
+        *reinterpret_cast<float2*>(Rs + (Q + 4 * j) * S::kDegFloats + (NN >> 1) * 2 * TPP + 2 * t) =
+            make_float2(c0[j], 0.f);
     }
     // angular rows m s^l q^(2l+1) Pb_lm {C_m, S_m} of the orders m = Q + 4j
     float wc = 1.f, ws = 0.f, pw = mass * qv;
@@ -503,8 +538,8 @@ __global__ void __maxnreg__(128) k1_tiled(K1Args a) {
   const int rR = (L + 1) * NN, pad = S::pad_rows(NN);
   const int sg_floats = B::kGen ? ((rR + 3) & ~3) : 0;
   float* SG = reinterpret_cast<float*>(smem_raw);  // [L + 1][NN] Gegenbauer steps (radial family alpha != 1)
-  float* Rs = SG + sg_floats;                      // [rR + pad][TPP]
-  float* Ys = Rs + (rR + pad) * TPP;               // [YCH * chunks][TPP]
+  float* Rs = SG + sg_floats;                      // [rR + pad][TPP]; PAIRS: [L + 1][kDegFloats]
+  float* Ys = Rs + (S::kPairs ? (L + 1) * S::kDegFloats : (rR + pad) * TPP);  // [YCH * chunks][TPP]
   float* red = Rs;                                 // window ends: the worker tiles
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   // padding rows and the angular rows past 2l of each degree's last chunk are
@@ -544,13 +579,21 @@ __global__ void __maxnreg__(128) k1_tiled(K1Args a) {
     item_lnm[item][2] = (short)mm0;
   }
   __syncthreads();
-  const float* Rrow = Rs + (il * NN + n0) * TPP;
+  const float* Rrow = S::kPairs ? Rs + il * S::kDegFloats : Rs + (il * NN + n0) * TPP;
   const float* Yrow = Ys + S::y_row(il, mm0) * TPP;
+  // PAIRS: the radial orders (2p, 2p + 1) x TM in packed pairs, an odd last
+  // order (its staged pair is (Ch_TN-1, 0)) in scalars
+  constexpr int TN2 = TN / 2;
   float acc[TN][TM];
+  float2 acc2[TN2][TM];
 #pragma unroll
   for (int i = 0; i < TN; ++i)
 #pragma unroll
     for (int j = 0; j < TM; ++j) acc[i][j] = 0.f;
+#pragma unroll
+  for (int p = 0; p < TN2; ++p)
+#pragma unroll
+    for (int j = 0; j < TM; ++j) acc2[p][j] = make_float2(0.f, 0.f);
   // window rows of this block: [window][2 NC] floats
   float* out = reinterpret_cast<float*>(a.partials) + (size_t)blockIdx.x * a.win * 2 * a.nc;
   const ScfConst* tabp = B::kGen ? a.tab : nullptr;
@@ -637,6 +680,34 @@ __global__ void __maxnreg__(128) k1_tiled(K1Args a) {
               acc[i][j] = fmaf(rv[i].w, yv.w, acc[i][j]);
             }
           }
+        } else if constexpr (S::kPairs) {
+          // the angular rows in registers, the radial pair rows streamed: per
+          // particle one packed FMA (each lane rounding as fmaf, the particles
+          // in the same order) for the two radial orders of a pair
+          // particles t0, t0 + 1 over all pair rows, then t0 + 2, t0 + 3
+#pragma unroll
+          for (int h = 0; h < 2; ++h) {
+            float2 yv[TM];
+#pragma unroll
+            for (int j = 0; j < TM; ++j) yv[j] = *reinterpret_cast<const float2*>(Yrow + j * TPP + t0 + 2 * h);
+#pragma unroll
+            for (int p = 0; p < TN2; ++p) {
+              const float4 r = *reinterpret_cast<const float4*>(Rrow + p * 2 * TPP + 2 * t0 + 4 * h);
+#pragma unroll
+              for (int j = 0; j < TM; ++j) {
+                acc2[p][j] = __ffma2_rn(make_float2(r.x, r.y), make_float2(yv[j].x, yv[j].x), acc2[p][j]);
+                acc2[p][j] = __ffma2_rn(make_float2(r.z, r.w), make_float2(yv[j].y, yv[j].y), acc2[p][j]);
+              }
+            }
+            if constexpr (TN % 2 == 1) {
+              const float4 r = *reinterpret_cast<const float4*>(Rrow + TN2 * 2 * TPP + 2 * t0 + 4 * h);
+#pragma unroll
+              for (int j = 0; j < TM; ++j) {
+                acc[TN - 1][j] = fmaf(r.x, yv[j].x, acc[TN - 1][j]);
+                acc[TN - 1][j] = fmaf(r.z, yv[j].y, acc[TN - 1][j]);
+              }
+            }
+          }
         } else {  // the angular rows in registers, the radial ones streamed
           float4 yv[TM];
 #pragma unroll
@@ -660,7 +731,23 @@ __global__ void __maxnreg__(128) k1_tiled(K1Args a) {
       // end of a window: the worker tiles through shared memory, one row per window
       if (worker) {
         float* mine = red + (size_t)(sgrp * a.items + item) * (TN * TM);
-        if constexpr (TM % 4 == 0) {
+        if constexpr (S::kPairs) {
+#pragma unroll
+          for (int p = 0; p < TN2; ++p)
+#pragma unroll
+            for (int j = 0; j < TM; ++j) {
+              mine[2 * p * TM + j] = acc2[p][j].x;
+              mine[(2 * p + 1) * TM + j] = acc2[p][j].y;
+              acc2[p][j] = make_float2(0.f, 0.f);
+            }
+          if constexpr (TN % 2 == 1) {
+#pragma unroll
+            for (int j = 0; j < TM; ++j) {
+              mine[(TN - 1) * TM + j] = acc[TN - 1][j];
+              acc[TN - 1][j] = 0.f;
+            }
+          }
+        } else if constexpr (TM % 4 == 0) {
 #pragma unroll
           for (int i = 0; i < TN; ++i)
 #pragma unroll
